@@ -1,0 +1,281 @@
+"""CPU oracle for SLM split search with PSO (arXiv 2208.07023).
+
+TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference legs import this package; the product
+path (``paper_2208_07023_gb300``) never does, and the two share no code.
+
+The arithmetic lives in ``slm_oracle.c`` (plain C, gcc, OpenMP over particles);
+this module builds it with ``gcc -O2 -ffp-contract=off`` and wraps it with
+ctypes. Every function takes and returns numpy arrays in host memory.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "slm_oracle.c")
+_HDR = os.path.join(_HERE, "slm_oracle.h")
+
+GINI, ENTROPY, MSE = 0, 1, 2
+F64, F32_MIRROR = 0, 1
+PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2, PURPOSE_BOOTSTRAP = 1, 2, 3, 4, 5
+CRITERIA = {"gini": GINI, "entropy": ENTROPY, "mse": MSE}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("criterion", C.c_int32), ("n_classes", C.c_int32),
+        ("n_particles", C.c_int32), ("n_iters", C.c_int32),
+        ("n_bins", C.c_int32), ("inertia", C.c_float), ("c1", C.c_float),
+        ("c2", C.c_float), ("max_depth", C.c_int32), ("min_leaf", C.c_int32),
+        ("seed", C.c_uint64), ("precision", C.c_int32),
+        ("n_threads", C.c_int32),
+    ]
+
+
+class Eval(C.Structure):
+    _fields_ = [
+        ("zmin", C.c_double), ("zmax", C.c_double), ("inv_w", C.c_double),
+        ("valid", C.c_int32), ("bin", C.c_int32), ("loss", C.c_double),
+        ("q_num", C.c_uint64), ("q_den", C.c_uint64),
+        ("n_left", C.c_double), ("n_right", C.c_double),
+    ]
+
+
+class Split(C.Structure):
+    _fields_ = [
+        ("valid", C.c_int32), ("particle", C.c_int32),
+        ("iter_of_best", C.c_int32), ("bin", C.c_int32),
+        ("zmin", C.c_double), ("inv_w", C.c_double),
+        ("threshold", C.c_double), ("loss", C.c_double),
+        ("q_num", C.c_uint64), ("q_den", C.c_uint64),
+        ("n_left", C.c_double), ("n_right", C.c_double),
+        ("first_near_tie", C.c_int32),
+    ]
+
+
+class _Tree(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in (
+        "kind", "dir", "zmin", "inv_w", "bin", "leaf_class", "leaf_value",
+        "weight", "loss", "n_left", "n_right")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (plain gcc; no CUDA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH) or
+             os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
+                                               os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            P = C.POINTER
+            L.ora_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+            L.ora_swarm_uniforms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32,
+                                             C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+            L.ora_bootstrap.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_void_p]
+            L.ora_pso_step.argtypes = [P(Params), C.c_int32, C.c_int32] + [C.c_void_p] * 6
+            L.ora_eval_swarm.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                         C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+            L.ora_eval_swarm.restype = C.c_int
+            L.ora_node_split.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                         C.c_uint32, C.c_void_p, C.c_void_p, P(Split),
+                                         C.c_void_p, C.c_void_p]
+            L.ora_node_split.restype = C.c_int
+            L.ora_train_tree.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
+                                         C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
+                                         P(_Tree)]
+            L.ora_train_tree.restype = C.c_int
+            L.ora_predict.argtypes = [P(Params), P(_Tree), C.c_void_p, C.c_int64,
+                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.ora_predict.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
+                n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8,
+                min_leaf=1, seed=1, precision=F32_MIRROR, n_threads=0) -> Params:
+    crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
+    return Params(crit, 0 if crit == MSE else n_classes, n_particles, n_iters,
+                  n_bins, inertia, c1, c2, max_depth, min_leaf, seed, precision,
+                  n_threads)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().ora_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def swarm_uniforms(seed, node_uid, t, n_particles, d, purpose) -> np.ndarray:
+    u = np.empty((n_particles, d), dtype=np.float32)
+    lib().ora_swarm_uniforms(seed, node_uid, t, n_particles, d, purpose, _ptr(u))
+    return u
+
+
+def bootstrap(seed, tree_id, n) -> np.ndarray:
+    w = np.empty(n, dtype=np.uint32)
+    lib().ora_bootstrap(seed, tree_id, n, _ptr(w))
+    return w
+
+
+def pso_step(params: Params, x, v, pbest, gbest, r1, r2):
+    x = np.ascontiguousarray(x, dtype=np.float64).copy()
+    v = np.ascontiguousarray(v, dtype=np.float64).copy()
+    pbest = np.ascontiguousarray(pbest, dtype=np.float64)
+    gbest = np.ascontiguousarray(gbest, dtype=np.float64)
+    r1 = np.ascontiguousarray(r1, dtype=np.float64)
+    r2 = np.ascontiguousarray(r2, dtype=np.float64)
+    P, d = x.shape
+    lib().ora_pso_step(C.byref(params), P, d, _ptr(x), _ptr(v), _ptr(pbest),
+                       _ptr(gbest), _ptr(r1), _ptr(r2))
+    return x, v
+
+
+def _node_arrays(X, labels, y, idx, wts):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n = X.shape[0]
+    idx = np.arange(n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, dtype=np.int32)
+    labels = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+    y = None if y is None else np.ascontiguousarray(y, dtype=np.float32)
+    wts = None if wts is None else np.ascontiguousarray(wts, dtype=np.uint32)
+    return X, labels, y, idx, wts
+
+
+def eval_swarm(params: Params, X, labels, y, pos, idx=None, wts=None,
+               want_bins=False, want_z=False):
+    """Score each row of pos[P, d] on the node idx. Returns (list of dict,
+    bins[P, n_idx] or None, z[P, n_idx] or None)."""
+    X, labels, y, idx, wts = _node_arrays(X, labels, y, idx, wts)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    P, d = pos.shape
+    out = (Eval * P)()
+    bins = np.empty((P, idx.size), dtype=np.int32) if want_bins else None
+    z = np.empty((P, idx.size), dtype=np.float64) if want_z else None
+    rc = lib().ora_eval_swarm(C.byref(params), _ptr(X), d, _ptr(labels), _ptr(y),
+                              _ptr(idx), _ptr(wts), idx.size, _ptr(pos), P, out,
+                              _ptr(bins), _ptr(z))
+    if rc:
+        raise ValueError(f"ora_eval_swarm failed: {rc}")
+    return [_struct_dict(e) for e in out], bins, z
+
+
+def _struct_dict(s) -> dict:
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+@dataclass
+class SplitResult:
+    split: dict
+    gbest: np.ndarray
+    direction: np.ndarray
+    trace_loss: np.ndarray
+    trace_particle: np.ndarray
+
+
+def node_split(params: Params, X, labels=None, y=None, idx=None, wts=None,
+               node_uid=0) -> SplitResult:
+    X, labels, y, idx, wts = _node_arrays(X, labels, y, idx, wts)
+    d = X.shape[1]
+    gb = np.zeros(d, dtype=np.float64)
+    dr = np.zeros(d, dtype=np.float64)
+    T = params.n_iters
+    tl = np.zeros(T + 1, dtype=np.float64)
+    tp = np.zeros(T + 1, dtype=np.int32)
+    sp = Split()
+    rc = lib().ora_node_split(C.byref(params), _ptr(X), d, _ptr(labels), _ptr(y),
+                              _ptr(idx), _ptr(wts), idx.size, node_uid, _ptr(gb),
+                              _ptr(dr), C.byref(sp), _ptr(tl), _ptr(tp))
+    if rc:
+        raise ValueError(f"ora_node_split failed: {rc}")
+    return SplitResult(_struct_dict(sp), gb, dr, tl, tp)
+
+
+@dataclass
+class Tree:
+    max_depth: int
+    d: int
+    kind: np.ndarray
+    dir: np.ndarray
+    zmin: np.ndarray
+    inv_w: np.ndarray
+    bin: np.ndarray
+    leaf_class: np.ndarray
+    leaf_value: np.ndarray
+    weight: np.ndarray
+    loss: np.ndarray
+    n_left: np.ndarray
+    n_right: np.ndarray
+
+    def _cstruct(self):
+        return _Tree(*[_ptr(getattr(self, f)) for f, _ in _Tree._fields_])
+
+
+def _empty_tree(max_depth, d) -> Tree:
+    H = (1 << (max_depth + 1)) - 1
+    return Tree(max_depth, d, np.zeros(H, np.int32), np.zeros((H, d), np.float64),
+                np.zeros(H), np.zeros(H), np.zeros(H, np.int32),
+                np.zeros(H, np.int32), np.zeros(H), np.zeros(H), np.zeros(H),
+                np.zeros(H), np.zeros(H))
+
+
+def train_tree(params: Params, X, labels=None, y=None, tree_id=0,
+               bootstrap=False) -> Tree:
+    X, labels, y, _, _ = _node_arrays(X, labels, y, None, None)
+    n, d = X.shape
+    t = _empty_tree(params.max_depth, d)
+    cs = t._cstruct()
+    rc = lib().ora_train_tree(C.byref(params), _ptr(X), n, d, _ptr(labels), _ptr(y),
+                              tree_id, 1 if bootstrap else 0, C.byref(cs))
+    if rc:
+        raise ValueError(f"ora_train_tree failed: {rc}")
+    return t
+
+
+def predict(params: Params, tree: Tree, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, d = X.shape
+    cls = np.empty(n, np.int32)
+    val = np.empty(n, np.float64)
+    leaf = np.empty(n, np.int32)
+    cs = tree._cstruct()
+    rc = lib().ora_predict(C.byref(params), C.byref(cs), _ptr(X), n, d, _ptr(cls),
+                           _ptr(val), _ptr(leaf))
+    if rc:
+        raise ValueError(f"ora_predict failed: {rc}")
+    return cls, val, leaf

@@ -1,0 +1,766 @@
+/*
+ * CPU oracle for SLM split search with particle swarm optimisation
+ * (arXiv 2208.07023). TEST INFRASTRUCTURE ONLY: the tests, the smoke check and
+ * the benchmark's CPU baseline call it; the product path never does.
+ *
+ * Plain, slow and sequential by design; the only parallelism is one OpenMP
+ * loop over particles, whose evaluations are independent (Sec. IV).
+ *
+ * What each part follows:
+ *   projection f(a) = a^T x ............ Sec. II-A, Eq. (1)
+ *   split sets a^T x >= t_b / < t_b ...... Sec. II-A, Eqs. (3)-(4)
+ *   threshold search over split points .. Sec. II-A (DFT) and Sec. IV: every
+ *        candidate split of a projected 1D subspace is scored and the minimum
+ *        kept. The paper gives no bin rule; this oracle uses B uniform bins on
+ *        [zmin, zmax] and the B-1 interior bin edges as candidates.
+ *   swarm update ......................... Sec. III-A, Eq. (pso-1); the
+ *        position is advanced with the NEW velocity (Alg. 1 "Update V_i and
+ *        X_i"); r1, r2 are drawn per particle, dimension and iteration.
+ *   pbest / gbest ........................ Algorithm 1: strict "<".
+ *   tree growth .......................... Algorithm 2 and Sec. II-A (stop
+ *        when pure or too small; majority vote in leaves).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp (no fused multiply-add beyond the
+ * explicit fmaf of the mirror projection).
+ */
+#include "slm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, restated from Salmon, Moraes, Dror and Shaw, "Parallel     */
+/* random numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64  */
+/* multiplies with a Weyl-sequence key schedule.                            */
+
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+  uint64_t p = (uint64_t)a * (uint64_t)b;
+  *hi = (uint32_t)(p >> 32);
+  *lo = (uint32_t)p;
+}
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(M0, c0, &hi0, &lo0);
+    mulhilo32(M1, c2, &hi1, &lo1);
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0;
+    k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24 high bits of a 32-bit draw scaled to [0, 1): exact in float. */
+static float u01(uint32_t r) { return (float)(r >> 8) * (1.0f / 16777216.0f); }
+
+static void seed_key(uint64_t seed, uint32_t key[2]) {
+  key[0] = (uint32_t)seed;
+  key[1] = (uint32_t)(seed >> 32);
+}
+
+/* Counter of a swarm draw: (node uid, iteration, particle, j/4 | purpose<<24),
+ * output lane j mod 4. */
+void ora_swarm_uniforms(uint64_t seed, uint32_t node_uid, uint32_t t,
+                        int32_t n_particles, int32_t d, int32_t purpose,
+                        float* u) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  for (int32_t i = 0; i < n_particles; ++i) {
+    for (int32_t j = 0; j < d; ++j) {
+      uint32_t ctr[4] = {node_uid, t, (uint32_t)i,
+                         ((uint32_t)j >> 2) | ((uint32_t)purpose << 24)};
+      uint32_t r[4];
+      ora_philox4x32_10(ctr, key, r);
+      u[(int64_t)i * d + j] = u01(r[j & 3]);
+    }
+  }
+}
+
+/* Draw k of tree t: counter (t, k/4, 0, purpose<<24), lane k mod 4; the
+ * sample is floor(r * n / 2^32). */
+void ora_bootstrap(uint64_t seed, uint32_t tree_id, int64_t n, uint32_t* w) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  for (int64_t s = 0; s < n; ++s) w[s] = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    uint32_t ctr[4] = {tree_id, (uint32_t)(k >> 2), 0u,
+                       (uint32_t)ORA_PURPOSE_BOOTSTRAP << 24};
+    uint32_t r[4];
+    ora_philox4x32_10(ctr, key, r);
+    uint64_t s = ((uint64_t)r[k & 3] * (uint64_t)n) >> 32;
+    w[s] += 1u;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Swarm update, Eq. (pso-1):                                               */
+/*   v <- omega v + c1 r1 (pB - x) + c2 r2 (gB - x);  x <- x + v             */
+/* evaluated left to right, one rounding per operation.                     */
+
+void ora_pso_step(const ora_params* p, int32_t P, int32_t d, double* x,
+                  double* v, const double* pbest, const double* gbest,
+                  const double* r1, const double* r2) {
+  for (int32_t i = 0; i < P; ++i) {
+    for (int32_t j = 0; j < d; ++j) {
+      int64_t e = (int64_t)i * d + j;
+      if (p->precision == ORA_F32_MIRROR) {
+        float xv = (float)x[e], vv = (float)v[e];
+        float inertia = p->inertia * vv;
+        float cog = (p->c1 * (float)r1[e]) * ((float)pbest[e] - xv);
+        float soc = (p->c2 * (float)r2[e]) * ((float)gbest[j] - xv);
+        float vn = (inertia + cog) + soc;
+        v[e] = vn;
+        x[e] = xv + vn;
+      } else {
+        double inertia = (double)p->inertia * v[e];
+        double cog = ((double)p->c1 * r1[e]) * (pbest[e] - x[e]);
+        double soc = ((double)p->c2 * r2[e]) * (gbest[j] - x[e]);
+        double vn = (inertia + cog) + soc;
+        v[e] = vn;
+        x[e] = x[e] + vn;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scoring one projection vector on one node.                               */
+
+static double xlogx(double c) { return c > 0.0 ? c * log(c) : 0.0; }
+
+#define NEAR_TIE_REL 1e-12
+
+static int near_tie(double a, double b) {
+  if (a == b || !isfinite(a) || !isfinite(b)) return 0;
+  double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+  return fabs(a - b) <= NEAR_TIE_REL * m;
+}
+
+/* Is candidate a strictly better (lower loss) than b? Gini compares the exact
+ * rationals Q = q_num/q_den (larger Q = lower loss); the others compare loss. */
+static int better(int criterion, int a_valid, double a_loss, uint64_t a_num,
+                  uint64_t a_den, int b_valid, double b_loss, uint64_t b_num,
+                  uint64_t b_den) {
+  if (!a_valid) return 0;
+  if (!b_valid) return 1;
+  if (criterion == ORA_GINI) {
+    unsigned __int128 lhs = (unsigned __int128)a_num * b_den;
+    unsigned __int128 rhs = (unsigned __int128)b_num * a_den;
+    return lhs > rhs;
+  }
+  return a_loss < b_loss;
+}
+
+/* Scores one projection vector a (as double; float-valued in mirror mode).
+ * scratch: n_idx doubles for z, n_idx ints for bins, hist buffers. */
+static void eval_one(const ora_params* p, const float* X, int32_t d,
+                     const int32_t* labels, const float* y, const int32_t* idx,
+                     const uint32_t* wts, int64_t n_idx, const double* a,
+                     ora_eval* out, double* z, int32_t* bins, uint64_t* cnt,
+                     double* msum, double* msq, int* tie) {
+  const int B = p->n_bins;
+  const int K = p->n_classes;
+  memset(out, 0, sizeof(*out));
+  out->valid = 0;
+  out->bin = -1;
+  out->loss = INFINITY;
+
+  /* Eq. (1): z = a^T x for every sample of the node. */
+  for (int64_t s = 0; s < n_idx; ++s) {
+    const float* xs = X + (int64_t)idx[s] * d;
+    if (p->precision == ORA_F32_MIRROR) {
+      float acc = 0.0f;
+      for (int32_t j = 0; j < d; ++j) acc = fmaf(xs[j], (float)a[j], acc);
+      z[s] = acc;
+    } else {
+      double acc = 0.0;
+      for (int32_t j = 0; j < d; ++j) acc += (double)xs[j] * a[j];
+      z[s] = acc;
+    }
+  }
+  if (n_idx <= 0) return;
+  double zmin = z[0], zmax = z[0];
+  for (int64_t s = 1; s < n_idx; ++s) {
+    if (z[s] < zmin) zmin = z[s];
+    if (z[s] > zmax) zmax = z[s];
+  }
+  out->zmin = zmin;
+  out->zmax = zmax;
+  if (!(zmax > zmin)) return; /* every sample projects to one point */
+
+  /* Uniform bins on [zmin, zmax]: bin = min(B-1, floor((z-zmin)*inv_w)). */
+  if (p->precision == ORA_F32_MIRROR) {
+    float fzmin = (float)zmin, fzmax = (float)zmax;
+    float width = fzmax - fzmin;
+    float inv_w = (float)B / width;
+    if (!isfinite(inv_w)) return;
+    out->inv_w = inv_w;
+    for (int64_t s = 0; s < n_idx; ++s) {
+      float off = (float)z[s] - fzmin;
+      float pos = off * inv_w;
+      int b = (int)floorf(pos);
+      if (b > B - 1) b = B - 1;
+      if (b < 0) b = 0;
+      bins[s] = b;
+    }
+  } else {
+    double inv_w = (double)B / (zmax - zmin);
+    if (!isfinite(inv_w)) return;
+    out->inv_w = inv_w;
+    for (int64_t s = 0; s < n_idx; ++s) {
+      int b = (int)floor((z[s] - zmin) * inv_w);
+      if (b > B - 1) b = B - 1;
+      if (b < 0) b = 0;
+      bins[s] = b;
+    }
+  }
+
+  /* Histogram over (bin, class) or (bin; weight, sum y, sum y^2). */
+  if (p->criterion == ORA_MSE) {
+    memset(cnt, 0, sizeof(uint64_t) * B);
+    memset(msum, 0, sizeof(double) * B);
+    memset(msq, 0, sizeof(double) * B);
+    for (int64_t s = 0; s < n_idx; ++s) {
+      uint32_t w = wts ? wts[s] : 1u;
+      double ys = (double)y[idx[s]];
+      cnt[bins[s]] += w;
+      msum[bins[s]] += (double)w * ys;
+      msq[bins[s]] += (double)w * ys * ys;
+    }
+  } else {
+    memset(cnt, 0, sizeof(uint64_t) * (size_t)B * K);
+    for (int64_t s = 0; s < n_idx; ++s) {
+      uint32_t w = wts ? wts[s] : 1u;
+      cnt[(int64_t)bins[s] * K + labels[idx[s]]] += w;
+    }
+  }
+
+  /* Threshold scan over the B-1 interior edges: left = bins < b. */
+  if (p->criterion == ORA_MSE) {
+    uint64_t ntot = 0;
+    double stot = 0.0, qtot = 0.0;
+    for (int b = 0; b < B; ++b) {
+      ntot += cnt[b];
+      stot += msum[b];
+      qtot += msq[b];
+    }
+    uint64_t nl = 0;
+    double sl = 0.0, ql = 0.0;
+    for (int b = 1; b < B; ++b) {
+      nl += cnt[b - 1];
+      sl += msum[b - 1];
+      ql += msq[b - 1];
+      uint64_t nr = ntot - nl;
+      if (nl < (uint64_t)p->min_leaf || nr < (uint64_t)p->min_leaf) continue;
+      double sr = stot - sl, qr = qtot - ql;
+      double sse_l = ql - sl * sl / (double)nl;
+      double sse_r = qr - sr * sr / (double)nr;
+      double loss = (sse_l + sse_r) / (double)ntot;
+      if (out->valid && near_tie(loss, out->loss)) *tie = 1;
+      if (!out->valid || loss < out->loss) {
+        out->valid = 1;
+        out->bin = b;
+        out->loss = loss;
+        out->n_left = (double)nl;
+        out->n_right = (double)nr;
+      }
+    }
+    return;
+  }
+
+  uint64_t tot[64];
+  uint64_t left[64];
+  uint64_t ntot = 0;
+  for (int k = 0; k < K; ++k) {
+    tot[k] = 0;
+    left[k] = 0;
+  }
+  for (int b = 0; b < B; ++b)
+    for (int k = 0; k < K; ++k) tot[k] += cnt[(int64_t)b * K + k];
+  for (int k = 0; k < K; ++k) ntot += tot[k];
+
+  for (int b = 1; b < B; ++b) {
+    for (int k = 0; k < K; ++k) left[k] += cnt[(int64_t)(b - 1) * K + k];
+    uint64_t nl = 0;
+    for (int k = 0; k < K; ++k) nl += left[k];
+    uint64_t nr = ntot - nl;
+    if (nl < (uint64_t)p->min_leaf || nr < (uint64_t)p->min_leaf) continue;
+    if (p->criterion == ORA_GINI) {
+      /* n * Gini_w = n - (S_L/n_L + S_R/n_R), S = sum_k n_k^2.
+       * Q = (S_L n_R + S_R n_L) / (n_L n_R); lower loss <=> larger Q. */
+      uint64_t sl = 0, sr = 0;
+      for (int k = 0; k < K; ++k) {
+        uint64_t r = tot[k] - left[k];
+        sl += left[k] * left[k];
+        sr += r * r;
+      }
+      uint64_t num = sl * nr + sr * nl;
+      uint64_t den = nl * nr;
+      uint64_t nden = ntot * den;
+      double loss = (double)(nden - num) / (double)nden;
+      if (better(ORA_GINI, 1, loss, num, den, out->valid, out->loss,
+                 out->q_num, out->q_den)) {
+        out->valid = 1;
+        out->bin = b;
+        out->loss = loss;
+        out->q_num = num;
+        out->q_den = den;
+        out->n_left = (double)nl;
+        out->n_right = (double)nr;
+      }
+    } else {
+      /* n * H_w = (n_L ln n_L - sum_k n_Lk ln n_Lk)
+       *         + (n_R ln n_R - sum_k n_Rk ln n_Rk)  (natural log). */
+      double sl = 0.0, sr = 0.0;
+      for (int k = 0; k < K; ++k) sl += xlogx((double)left[k]);
+      for (int k = 0; k < K; ++k) sr += xlogx((double)(tot[k] - left[k]));
+      double h = (xlogx((double)nl) - sl) + (xlogx((double)nr) - sr);
+      double loss = h / (double)ntot;
+      if (out->valid && near_tie(loss, out->loss)) *tie = 1;
+      if (!out->valid || loss < out->loss) {
+        out->valid = 1;
+        out->bin = b;
+        out->loss = loss;
+        out->n_left = (double)nl;
+        out->n_right = (double)nr;
+      }
+    }
+  }
+}
+
+static int check_params(const ora_params* p, int32_t d) {
+  if (!p || d <= 0 || p->n_bins < 2 || p->min_leaf < 1) return -1;
+  if (p->criterion == ORA_MSE) return 0;
+  if (p->criterion != ORA_GINI && p->criterion != ORA_ENTROPY) return -1;
+  if (p->n_classes < 2 || p->n_classes > 64) return -1;
+  return 0;
+}
+
+static int eval_all(const ora_params* p, const float* X, int32_t d,
+                    const int32_t* labels, const float* y, const int32_t* idx,
+                    const uint32_t* wts, int64_t n_idx, const double* pos,
+                    int32_t P, ora_eval* out, int32_t* bins_out, double* z_out,
+                    int* tie_any) {
+  const int B = p->n_bins;
+  const int K = p->criterion == ORA_MSE ? 1 : p->n_classes;
+  int err = 0;
+  int tie = 0;
+#ifdef _OPENMP
+  int nt = p->n_threads > 0 ? p->n_threads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt) reduction(| : err, tie)
+#endif
+  {
+    double* z = (double*)malloc(sizeof(double) * (size_t)(n_idx > 0 ? n_idx : 1));
+    int32_t* bins = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_idx > 0 ? n_idx : 1));
+    uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)B * K);
+    double* msum = (double*)malloc(sizeof(double) * (size_t)B);
+    double* msq = (double*)malloc(sizeof(double) * (size_t)B);
+    if (!z || !bins || !cnt || !msum || !msq) {
+      err = 1;
+    } else {
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+      for (int32_t i = 0; i < P; ++i) {
+        int t = 0;
+        for (int64_t s = 0; s < n_idx; ++s) bins[s] = -1;
+        eval_one(p, X, d, labels, y, idx, wts, n_idx, pos + (int64_t)i * d,
+                 &out[i], z, bins, cnt, msum, msq, &t);
+        tie |= t;
+        if (bins_out)
+          memcpy(bins_out + (int64_t)i * n_idx, bins, sizeof(int32_t) * (size_t)n_idx);
+        if (z_out) memcpy(z_out + (int64_t)i * n_idx, z, sizeof(double) * (size_t)n_idx);
+      }
+    }
+    free(z);
+    free(bins);
+    free(cnt);
+    free(msum);
+    free(msq);
+  }
+  if (tie_any) *tie_any = tie;
+  return err ? -2 : 0;
+}
+
+int ora_eval_swarm(const ora_params* p, const float* X, int32_t d,
+                   const int32_t* labels, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, const double* pos,
+                   int32_t P, ora_eval* out, int32_t* bins_out,
+                   double* z_out) {
+  if (check_params(p, d) || P < 1 || n_idx < 0 || !X || !idx || !pos || !out)
+    return -1;
+  return eval_all(p, X, d, labels, y, idx, wts, n_idx, pos, P, out, bins_out,
+                  z_out, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (PSO), synchronous form: every particle moves with the gbest  */
+/* held at the end of the previous iteration, then all are scored, then     */
+/* pbest and gbest are updated with strict "<" in increasing particle order. */
+
+static void copy_eval_to_split(const ora_eval* e, ora_split* s) {
+  s->valid = e->valid;
+  s->bin = e->bin;
+  s->zmin = e->zmin;
+  s->inv_w = e->inv_w;
+  s->loss = e->loss;
+  s->q_num = e->q_num;
+  s->q_den = e->q_den;
+  s->n_left = e->n_left;
+  s->n_right = e->n_right;
+}
+
+int ora_node_split(const ora_params* p, const float* X, int32_t d,
+                   const int32_t* labels, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
+                   double* gbest_out, double* dir_out, ora_split* out,
+                   double* trace_loss, int32_t* trace_particle) {
+  if (check_params(p, d) || p->n_particles < 1 || p->n_iters < 0 || n_idx < 0 ||
+      !X || !idx || !out)
+    return -1;
+  const int32_t P = p->n_particles;
+  const int32_t T = p->n_iters;
+  const int64_t PD = (int64_t)P * d;
+  double* x = (double*)calloc((size_t)PD, sizeof(double));
+  double* v = (double*)calloc((size_t)PD, sizeof(double));
+  double* pb = (double*)calloc((size_t)PD, sizeof(double));
+  double* gb = (double*)calloc((size_t)d, sizeof(double));
+  double* r1 = (double*)calloc((size_t)PD, sizeof(double));
+  double* r2 = (double*)calloc((size_t)PD, sizeof(double));
+  float* u = (float*)calloc((size_t)PD, sizeof(float));
+  ora_eval* ev = (ora_eval*)calloc((size_t)P, sizeof(ora_eval));
+  ora_eval* pbe = (ora_eval*)calloc((size_t)P, sizeof(ora_eval));
+  int rc = 0;
+  if (!x || !v || !pb || !gb || !r1 || !r2 || !u || !ev || !pbe) {
+    rc = -2;
+    goto done;
+  }
+  memset(out, 0, sizeof(*out));
+  out->first_near_tie = -1;
+
+  /* Initial swarm: x ~ U[-1,1)^d, v ~ 0.1 * U[-1,1)^d. */
+  ora_swarm_uniforms(p->seed, node_uid, 0, P, d, ORA_PURPOSE_INIT_X, u);
+  for (int64_t e = 0; e < PD; ++e) x[e] = (double)(2.0f * u[e] - 1.0f);
+  ora_swarm_uniforms(p->seed, node_uid, 0, P, d, ORA_PURPOSE_INIT_V, u);
+  for (int64_t e = 0; e < PD; ++e) {
+    if (p->precision == ORA_F32_MIRROR)
+      v[e] = (double)(0.1f * (2.0f * u[e] - 1.0f));
+    else
+      v[e] = 0.1 * (double)(2.0f * u[e] - 1.0f);
+  }
+
+  ora_eval gbe;
+  memset(&gbe, 0, sizeof(gbe));
+  int32_t gpart = 0, giter = 0;
+  for (int32_t t = 0; t <= T; ++t) {
+    if (t > 0) {
+      ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, P, d, ORA_PURPOSE_R1, u);
+      for (int64_t e = 0; e < PD; ++e) r1[e] = u[e];
+      ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, P, d, ORA_PURPOSE_R2, u);
+      for (int64_t e = 0; e < PD; ++e) r2[e] = u[e];
+      ora_pso_step(p, P, d, x, v, pb, gb, r1, r2);
+    }
+    int tie = 0;
+    rc = eval_all(p, X, d, labels, y, idx, wts, n_idx, x, P, ev, NULL, NULL, &tie);
+    if (rc) goto done;
+    for (int32_t i = 0; i < P; ++i) {
+      const ora_eval* e = &ev[i];
+      int improved = 0;
+      if (t == 0) {
+        improved = 1; /* pbest starts at the initial position */
+      } else {
+        if (pbe[i].valid && e->valid && near_tie(e->loss, pbe[i].loss)) tie = 1;
+        improved = better(p->criterion, e->valid, e->loss, e->q_num, e->q_den,
+                          pbe[i].valid, pbe[i].loss, pbe[i].q_num, pbe[i].q_den);
+      }
+      if (!improved) continue;
+      pbe[i] = *e;
+      memcpy(pb + (int64_t)i * d, x + (int64_t)i * d, sizeof(double) * d);
+      int first = (t == 0 && i == 0);
+      if (!first && gbe.valid && e->valid && near_tie(e->loss, gbe.loss)) tie = 1;
+      if (first || better(p->criterion, e->valid, e->loss, e->q_num, e->q_den,
+                          gbe.valid, gbe.loss, gbe.q_num, gbe.q_den)) {
+        gbe = *e;
+        gpart = i;
+        giter = t;
+        memcpy(gb, x + (int64_t)i * d, sizeof(double) * d);
+      }
+    }
+    if (p->criterion == ORA_GINI) tie = 0; /* exact rationals: no near-ties */
+    if (tie && out->first_near_tie < 0) out->first_near_tie = t;
+    if (trace_loss) trace_loss[t] = gbe.valid ? gbe.loss : INFINITY;
+    if (trace_particle) trace_particle[t] = gpart;
+  }
+
+  copy_eval_to_split(&gbe, out);
+  out->particle = gpart;
+  out->iter_of_best = giter;
+  if (gbe.valid) {
+    if (p->precision == ORA_F32_MIRROR)
+      out->threshold = (double)((float)gbe.zmin + (float)gbe.bin / (float)gbe.inv_w);
+    else
+      out->threshold = gbe.zmin + (double)gbe.bin / gbe.inv_w;
+  }
+  if (gbest_out) memcpy(gbest_out, gb, sizeof(double) * d);
+  if (dir_out) {
+    double nrm = 0.0;
+    for (int32_t j = 0; j < d; ++j) nrm += gb[j] * gb[j];
+    nrm = sqrt(nrm);
+    for (int32_t j = 0; j < d; ++j) dir_out[j] = nrm > 0.0 ? gb[j] / nrm : 0.0;
+  }
+
+done:
+  free(x);
+  free(v);
+  free(pb);
+  free(gb);
+  free(r1);
+  free(r2);
+  free(u);
+  free(ev);
+  free(pbe);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 2: grow a binary tree breadth-first.                           */
+
+typedef struct {
+  int32_t* idx;
+  uint32_t* w;
+  int64_t n;
+} node_samples;
+
+/* Bin of sample x under a stored split, in the mode's precision. */
+static int split_bin(const ora_params* p, const double* dir, double zmin,
+                     double inv_w, const float* xs, int32_t d) {
+  const int B = p->n_bins;
+  int b;
+  if (p->precision == ORA_F32_MIRROR) {
+    float acc = 0.0f;
+    for (int32_t j = 0; j < d; ++j) acc = fmaf(xs[j], (float)dir[j], acc);
+    float off = acc - (float)zmin;
+    float pos = off * (float)inv_w;
+    b = (int)floorf(pos);
+  } else {
+    double acc = 0.0;
+    for (int32_t j = 0; j < d; ++j) acc += (double)xs[j] * dir[j];
+    b = (int)floor((acc - zmin) * inv_w);
+  }
+  if (b > B - 1) b = B - 1;
+  if (b < 0) b = 0;
+  return b;
+}
+
+int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,
+                   const int32_t* labels, const float* y, uint32_t tree_id,
+                   int32_t bootstrap, ora_tree* out) {
+  if (check_params(p, d) || n < 1 || !X || !out || p->max_depth < 0 ||
+      p->max_depth > 15)
+    return -1;
+  if (p->criterion == ORA_MSE ? !y : !labels) return -1;
+  const int D = p->max_depth;
+  const int64_t H = ((int64_t)1 << (D + 1)) - 1;
+  const int K = p->n_classes;
+  for (int64_t h = 0; h < H; ++h) {
+    out->kind[h] = -1;
+    out->zmin[h] = out->inv_w[h] = 0.0;
+    out->bin[h] = -1;
+    out->leaf_class[h] = -1;
+    out->leaf_value[h] = 0.0;
+    out->weight[h] = 0.0;
+    out->loss[h] = 0.0;
+    out->n_left[h] = out->n_right[h] = 0.0;
+    for (int32_t j = 0; j < d; ++j) out->dir[h * d + j] = 0.0;
+  }
+  node_samples* ns = (node_samples*)calloc((size_t)H, sizeof(node_samples));
+  if (!ns) return -2;
+  int rc = 0;
+
+  /* Root: every sample (weight 1), or the distinct bootstrap draws with
+   * their multiplicities. */
+  {
+    uint32_t* bw = NULL;
+    int64_t m = n;
+    if (bootstrap) {
+      bw = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+      if (!bw) { free(ns); return -2; }
+      ora_bootstrap(p->seed, tree_id, n, bw);
+      m = 0;
+      for (int64_t s = 0; s < n; ++s) m += bw[s] > 0;
+    }
+    ns[0].idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    ns[0].w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1));
+    if (!ns[0].idx || !ns[0].w) { free(bw); rc = -2; goto done; }
+    int64_t k = 0;
+    for (int64_t s = 0; s < n; ++s) {
+      uint32_t w = bw ? bw[s] : 1u;
+      if (w == 0) continue;
+      ns[0].idx[k] = (int32_t)s;
+      ns[0].w[k] = w;
+      ++k;
+    }
+    ns[0].n = k;
+    free(bw);
+  }
+
+  double* gbest = (double*)malloc(sizeof(double) * d);
+  uint64_t* cls = (uint64_t*)malloc(sizeof(uint64_t) * (K > 0 ? K : 1));
+  if (!gbest || !cls) { free(gbest); free(cls); rc = -2; goto done; }
+
+  for (int depth = 0; depth <= D && rc == 0; ++depth) {
+    int64_t h0 = ((int64_t)1 << depth) - 1, h1 = ((int64_t)1 << (depth + 1)) - 1;
+    for (int64_t h = h0; h < h1 && rc == 0; ++h) {
+      if (!ns[h].idx) continue;
+      node_samples* nd = &ns[h];
+      /* Node statistics: weighted count, class counts or target moments. */
+      uint64_t nw = 0;
+      for (int64_t s = 0; s < nd->n; ++s) nw += nd->w[s];
+      int pure = 0;
+      if (p->criterion == ORA_MSE) {
+        double sy = 0.0;
+        float ymin = INFINITY, ymax = -INFINITY;
+        for (int64_t s = 0; s < nd->n; ++s) {
+          float ys = y[nd->idx[s]];
+          sy += (double)nd->w[s] * (double)ys;
+          if (ys < ymin) ymin = ys;
+          if (ys > ymax) ymax = ys;
+        }
+        out->leaf_value[h] = nw ? sy / (double)nw : 0.0;
+        pure = !(ymax > ymin);
+      } else {
+        for (int k = 0; k < K; ++k) cls[k] = 0;
+        for (int64_t s = 0; s < nd->n; ++s) cls[labels[nd->idx[s]]] += nd->w[s];
+        int best = 0, nonzero = 0;
+        for (int k = 0; k < K; ++k) {
+          if (cls[k] > cls[best]) best = k;
+          nonzero += cls[k] > 0;
+        }
+        out->leaf_class[h] = best;
+        pure = nonzero <= 1;
+      }
+      out->weight[h] = (double)nw;
+      out->kind[h] = 0;
+      if (depth == D || nw < 2 * (uint64_t)p->min_leaf || pure) continue;
+
+      ora_split sp;
+      uint32_t uid = (tree_id << 16) | (uint32_t)h;
+      rc = ora_node_split(p, X, d, labels, y, nd->idx, nd->w, nd->n, uid, gbest,
+                          NULL, &sp, NULL, NULL);
+      if (rc) break;
+      if (!sp.valid) continue;
+
+      /* Partition, Eqs. (3)-(4): right (+) iff bin >= b*, i.e. z >= t_b. */
+      int32_t* side = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nd->n > 0 ? nd->n : 1));
+      if (!side) { rc = -2; break; }
+      int64_t nl = 0;
+      for (int64_t s = 0; s < nd->n; ++s) {
+        int b = split_bin(p, gbest, sp.zmin, sp.inv_w, X + (int64_t)nd->idx[s] * d, d);
+        side[s] = b >= sp.bin;
+        nl += !side[s];
+      }
+      /* Zero gain: a split whose children keep the parent's class mix (or,
+       * for MSE, does not lower the loss) is not made. */
+      int no_gain = 0;
+      if (p->criterion == ORA_MSE) {
+        double sy = 0.0, sq = 0.0;
+        for (int64_t s = 0; s < nd->n; ++s) {
+          double ys = (double)y[nd->idx[s]];
+          sy += (double)nd->w[s] * ys;
+          sq += (double)nd->w[s] * ys * ys;
+        }
+        double parent = (sq - sy * sy / (double)nw) / (double)nw;
+        no_gain = !(sp.loss < parent);
+      } else {
+        uint64_t* lk = (uint64_t*)calloc((size_t)K, sizeof(uint64_t));
+        if (!lk) { free(side); rc = -2; break; }
+        uint64_t wl = 0;
+        for (int64_t s = 0; s < nd->n; ++s)
+          if (!side[s]) {
+            lk[labels[nd->idx[s]]] += nd->w[s];
+            wl += nd->w[s];
+          }
+        no_gain = 1;
+        for (int k = 0; k < K; ++k)
+          if ((unsigned __int128)lk[k] * nw != (unsigned __int128)cls[k] * wl) no_gain = 0;
+        free(lk);
+      }
+      if (no_gain) { free(side); continue; }
+
+      out->kind[h] = 1;
+      for (int32_t j = 0; j < d; ++j) out->dir[h * d + j] = gbest[j];
+      out->zmin[h] = sp.zmin;
+      out->inv_w[h] = sp.inv_w;
+      out->bin[h] = sp.bin;
+      out->loss[h] = sp.loss;
+      out->n_left[h] = sp.n_left;
+      out->n_right[h] = sp.n_right;
+
+      int64_t nr = nd->n - nl;
+      node_samples* L = &ns[2 * h + 1];
+      node_samples* R = &ns[2 * h + 2];
+      L->idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+      L->w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(nl > 0 ? nl : 1));
+      R->idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nr > 0 ? nr : 1));
+      R->w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(nr > 0 ? nr : 1));
+      if (!L->idx || !L->w || !R->idx || !R->w) { free(side); rc = -2; break; }
+      int64_t a = 0, c = 0;
+      for (int64_t s = 0; s < nd->n; ++s) {
+        if (side[s]) {
+          R->idx[c] = nd->idx[s];
+          R->w[c++] = nd->w[s];
+        } else {
+          L->idx[a] = nd->idx[s];
+          L->w[a++] = nd->w[s];
+        }
+      }
+      L->n = a;
+      R->n = c;
+      free(side);
+    }
+  }
+  free(gbest);
+  free(cls);
+
+done:
+  for (int64_t h = 0; h < H; ++h) {
+    free(ns[h].idx);
+    free(ns[h].w);
+  }
+  free(ns);
+  return rc;
+}
+
+int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
+                int64_t n, int32_t d, int32_t* class_out, double* value_out,
+                int32_t* leaf_out) {
+  if (!p || !tree || !X || d <= 0 || n < 0) return -1;
+  const int64_t H = ((int64_t)1 << (p->max_depth + 1)) - 1;
+  for (int64_t s = 0; s < n; ++s) {
+    const float* xs = X + s * d;
+    int64_t h = 0;
+    while (h < H && tree->kind[h] == 1) {
+      int b = split_bin(p, tree->dir + h * d, tree->zmin[h], tree->inv_w[h], xs, d);
+      h = b >= tree->bin[h] ? 2 * h + 2 : 2 * h + 1;
+    }
+    if (class_out) class_out[s] = tree->leaf_class[h];
+    if (value_out) value_out[s] = tree->leaf_value[h];
+    if (leaf_out) leaf_out[s] = (int32_t)h;
+  }
+  return 0;
+}

@@ -1,0 +1,146 @@
+/*
+ * CPU oracle for SLM split search with particle swarm optimisation
+ * (Fu et al., "Acceleration of Subspace Learning Machine via Particle Swarm
+ * Optimization and Parallel Processing", arXiv 2208.07023).
+ *
+ * TEST INFRASTRUCTURE ONLY. This library is the correctness reference for the
+ * CUDA implementation. Only the tests, the smoke check and the benchmark's CPU
+ * baseline load it; the product path never calls it. It shares no code,
+ * header, table or constant with the CUDA library.
+ *
+ * All arrays are row-major and live in host memory. Functions return 0 on
+ * success and a negative number on bad arguments.
+ */
+#ifndef SLM_ORACLE_H
+#define SLM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_GINI = 0, ORA_ENTROPY = 1, ORA_MSE = 2 };
+
+/* Arithmetic mode of the projection, binning and swarm update.
+ * ORA_F64:        every floating-point step in double precision.
+ * ORA_F32_MIRROR: projection as a sequential fmaf over features, binning and
+ *                 swarm update in float with one IEEE rounding per operation;
+ *                 the criterion stays in double / exact integers. */
+enum { ORA_F64 = 0, ORA_F32_MIRROR = 1 };
+
+/* Philox stream purposes (high byte of counter word 3). */
+enum {
+  ORA_PURPOSE_INIT_X = 1,
+  ORA_PURPOSE_INIT_V = 2,
+  ORA_PURPOSE_R1 = 3,
+  ORA_PURPOSE_R2 = 4,
+  ORA_PURPOSE_BOOTSTRAP = 5
+};
+
+typedef struct {
+  int32_t criterion;    /* ORA_GINI / ORA_ENTROPY / ORA_MSE */
+  int32_t n_classes;    /* K >= 2 for classification, 0 for regression */
+  int32_t n_particles;  /* P */
+  int32_t n_iters;      /* T: swarm updates after the initial evaluation */
+  int32_t n_bins;       /* B >= 2 */
+  float inertia;        /* omega */
+  float c1, c2;         /* learning factors */
+  int32_t max_depth;    /* nodes at this depth are leaves */
+  int32_t min_leaf;     /* >= 1, weighted sample count per child */
+  uint64_t seed;        /* Philox key */
+  int32_t precision;    /* ORA_F64 / ORA_F32_MIRROR */
+  int32_t n_threads;    /* 0: OpenMP default */
+} ora_params;
+
+/* Result of scoring one projection vector on one node. */
+typedef struct {
+  double zmin, zmax, inv_w; /* projected range and bins per unit length */
+  int32_t valid;            /* 0: no admissible threshold */
+  int32_t bin;              /* best edge b in [1, B-1]: right iff bin >= b */
+  double loss;              /* weighted child impurity; +inf if invalid */
+  uint64_t q_num, q_den;    /* Gini only: Q = q_num / q_den, larger is better */
+  double n_left, n_right;   /* weighted sample counts of the two children */
+} ora_eval;
+
+/* Result of a PSO split search on one node. */
+typedef struct {
+  int32_t valid;
+  int32_t particle;         /* particle whose position became gbest last */
+  int32_t iter_of_best;     /* iteration at which gbest last improved */
+  int32_t bin;
+  double zmin, inv_w;       /* binning of the gbest projection */
+  double threshold;         /* zmin + bin / inv_w, in units of gB . x */
+  double loss;
+  uint64_t q_num, q_den;
+  double n_left, n_right;
+  int32_t first_near_tie;   /* first iteration with a near-tie, -1 if none */
+} ora_split;
+
+/* Tree in heap layout: node h has children 2h+1 and 2h+2; H = 2^(D+1)-1. */
+typedef struct {
+  int32_t* kind;       /* [H] -1 absent, 0 leaf, 1 internal */
+  double* dir;         /* [H*d] raw gbest position (not normalised) */
+  double* zmin;        /* [H] */
+  double* inv_w;       /* [H] */
+  int32_t* bin;        /* [H] */
+  int32_t* leaf_class; /* [H] majority class (classification) */
+  double* leaf_value;  /* [H] mean target (regression) */
+  double* weight;      /* [H] weighted sample count */
+  double* loss;        /* [H] split loss (internal nodes) */
+  double* n_left;      /* [H] */
+  double* n_right;     /* [H] */
+} ora_tree;
+
+/* Philox4x32-10 block function (Salmon et al., SC'11). */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]);
+
+/* u[i*d + j] = uniform [0,1) draw of the swarm stream `purpose` for particle i,
+ * dimension j at iteration t of node `node_uid`. */
+void ora_swarm_uniforms(uint64_t seed, uint32_t node_uid, uint32_t t,
+                        int32_t n_particles, int32_t d, int32_t purpose,
+                        float* u);
+
+/* Bootstrap multiplicities of tree `tree_id`: n draws with replacement. */
+void ora_bootstrap(uint64_t seed, uint32_t tree_id, int64_t n, uint32_t* w);
+
+/* One synchronous swarm update (Eq. pso-1, then x += v_new), in the mode's
+ * precision. All arrays [P*d] except gbest [d]. */
+void ora_pso_step(const ora_params* p, int32_t n_particles, int32_t d,
+                  double* x, double* v, const double* pbest,
+                  const double* gbest, const double* r1, const double* r2);
+
+/* Score P projection vectors pos[P*d] on the node given by idx[n_idx]
+ * (entry weights wts, NULL = 1). Optional outputs: bins_out[P*n_idx] and
+ * z_out[P*n_idx] (particle-major). */
+int ora_eval_swarm(const ora_params* p, const float* X, int32_t d,
+                   const int32_t* labels, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, const double* pos,
+                   int32_t n_particles, ora_eval* out, int32_t* bins_out,
+                   double* z_out);
+
+/* PSO split search on one node (Algorithm 1 with synchronous updates).
+ * gbest_out[d]: raw position; dir_out[d]: gbest / ||gbest||;
+ * trace_loss[T+1], trace_particle[T+1]: gbest after each evaluation. */
+int ora_node_split(const ora_params* p, const float* X, int32_t d,
+                   const int32_t* labels, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
+                   double* gbest_out, double* dir_out, ora_split* out,
+                   double* trace_loss, int32_t* trace_particle);
+
+/* Grow one tree (Algorithm 2, breadth-first). bootstrap != 0 draws the
+ * tree's bag with ora_bootstrap(seed, tree_id, n). */
+int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,
+                   const int32_t* labels, const float* y, uint32_t tree_id,
+                   int32_t bootstrap, ora_tree* out);
+
+/* Route samples through a tree grown by ora_train_tree. */
+int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
+                int64_t n, int32_t d, int32_t* class_out, double* value_out,
+                int32_t* leaf_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
