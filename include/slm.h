@@ -1,0 +1,240 @@
+/*
+ * libslm -- GB300 (sm_103a) split search for the Subspace Learning Machine
+ * with particle swarm optimisation (Fu et al., arXiv 2208.07023).
+ *
+ * The problem (Sec. II-A, Eqs. 1-4): at a tree node, find a direction a and a
+ * threshold t_b such that the half-spaces a^T x >= t_b (right, "+") and
+ * a^T x < t_b (left, "-") have the lowest weighted child impurity. The
+ * direction is searched by a particle swarm (Sec. III-A, Eq. pso-1,
+ * Algorithm 1); each particle's projection is scored by binning it into B
+ * uniform bins on [min z, max z] and scanning the B-1 interior bin edges as
+ * thresholds (the paper's "loss at each split point", Sec. IV). Trees grow by
+ * repeating the search on the children (Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.    Array arguments may be device pointers or host pointers; the
+ *            library inspects each with cudaPointerGetAttributes. Host inputs
+ *            are staged to the device and host outputs copied back inside the
+ *            call. Every array is row-major and dense.
+ * Ownership. The caller owns every buffer it passes and may free it when the
+ *            call returns, except that slm_forest_begin keeps X / labels / y
+ *            (if device pointers) until slm_forest_free. Forests are owned by
+ *            the library and released with slm_forest_free.
+ * Streams.   Work is issued on the context's stream. Calls that return host
+ *            results synchronise that stream before returning.
+ * Errors.    Every entry point returns an slm_status; no C++ exception
+ *            crosses this boundary. SLM_EINVAL: an argument is out of range
+ *            (nothing was launched). SLM_ECUDA: a CUDA call failed; the
+ *            message is available from slm_last_error. SLM_EUNSUPPORTED: the
+ *            sizes are valid but exceed a compiled limit listed below.
+ * Threads.   A context may be used by one host thread at a time.
+ * Limits.    1 <= d <= 1024; 1 <= P (n_particles) <= 256; 2 <= B (n_bins) <= 256;
+ *            2 <= K (n_classes) <= 32; 0 <= max_depth <= 15; n < 2^31;
+ *            per-particle histogram B*K*4 bytes <= 10240 (classification).
+ */
+#ifndef SLM_H
+#define SLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SLM_OK = 0,
+  SLM_EINVAL = 1,
+  SLM_ENOMEM = 2,
+  SLM_ECUDA = 3,
+  SLM_ETIMEOUT = 4,
+  SLM_EUNSUPPORTED = 5
+} slm_status;
+
+/* Child impurity (Sec. II-A: "lower entropy"; Table 4 reports MSE).
+ * GINI:    loss = sum_side (n_side/n) (1 - sum_k p_k^2).
+ * ENTROPY: loss = sum_side (n_side/n) (-sum_k p_k ln p_k), natural log.
+ * MSE:     loss = (SSE_left + SSE_right) / n. */
+typedef enum { SLM_GINI = 0, SLM_ENTROPY = 1, SLM_MSE = 2 } slm_criterion;
+
+/* Projection arithmetic. FP32: z = sum_j x_j a_j as one fused multiply-add
+ * per feature in increasing j, starting from +0. */
+typedef enum { SLM_PROJ_FP32 = 0, SLM_PROJ_BF16_TOPK = 1 } slm_proj;
+
+typedef struct slm_params {
+  int32_t criterion;   /* slm_criterion */
+  int32_t n_classes;   /* K for GINI / ENTROPY; 0 for MSE */
+  int32_t n_particles; /* P: swarm size (Eq. pso_a) */
+  int32_t n_iters;     /* T: swarm updates after the initial evaluation */
+  int32_t n_bins;      /* B: uniform bins per projection */
+  int32_t topk;        /* SLM_PROJ_BF16_TOPK only (unused otherwise) */
+  float inertia;       /* omega in Eq. pso-1 */
+  float c1, c2;        /* learning factors in Eq. pso-1 */
+  int32_t max_depth;   /* nodes at this depth are leaves */
+  int32_t min_leaf;    /* >= 1: minimum weighted samples in each child */
+  int32_t proj;        /* slm_proj */
+  int32_t n_trees;     /* >= 1; > 1 grows a bagged forest */
+  int32_t bootstrap;   /* 1: tree t trains on a bootstrap bag of the n samples */
+  int32_t reserved;    /* must be 0 */
+  uint64_t seed;       /* Philox-4x32-10 key for every random draw */
+} slm_params;
+
+/* Score of one projection vector on one node (the best of its B-1 edges). */
+typedef struct slm_eval {
+  double loss;         /* +inf if no admissible edge */
+  uint64_t q_num;      /* GINI only: Q = q_num / q_den = S_L/n_L + S_R/n_R; */
+  uint64_t q_den;      /*   loss = 1 - Q/n; larger Q is strictly better */
+  float zmin, inv_w;   /* bin(z) = min(B-1, floor((z - zmin) * inv_w)) */
+  int32_t bin;         /* best edge b in [1, B-1]; right child iff bin(z) >= b */
+  int32_t valid;       /* 0: all projections equal, or no edge leaves
+                          min_leaf samples on both sides */
+  int64_t n_left;      /* weighted sample counts of the children */
+  int64_t n_right;
+} slm_eval;
+
+/* Result of a PSO split search on one node (Algorithm 1). */
+typedef struct slm_split {
+  slm_eval eval;       /* score of the global best position gB */
+  int32_t particle;    /* particle whose position became gB last */
+  int32_t iter_of_best;/* iteration at which gB last improved (0 = init) */
+  float threshold;     /* zmin + bin / inv_w, in units of gB . x */
+  float norm;          /* ||gB||: t_b for the unit direction is threshold/norm */
+} slm_split;
+
+typedef struct slm_ctx slm_ctx;
+typedef struct slm_forest slm_forest;
+
+const char* slm_status_string(slm_status s);
+
+/* Creates a context on `device` issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+slm_status slm_create(slm_ctx** out, int device, void* cuda_stream);
+void slm_destroy(slm_ctx* ctx);
+/* Copies the last error message (NUL-terminated, truncated to len). */
+slm_status slm_last_error(slm_ctx* ctx, char* buf, size_t len);
+
+/* Uniform [0,1) draws of the swarm streams (Sec. III-A: random initial
+ * positions and velocities, r1 and r2 of Eq. pso-1), exposed for
+ * reproducibility checks. u[i*d + j] = (r >> 8) * 2^-24 with r = lane (j mod 4)
+ * of Philox4x32-10(key = seed, counter = {node_uid, t, i, (j>>2) | purpose<<24}).
+ * purpose: 1 initial position, 2 initial velocity, 3 r1, 4 r2. */
+slm_status slm_swarm_uniforms(slm_ctx* ctx, uint64_t seed, uint32_t node_uid,
+                              uint32_t t, int32_t n_particles, int32_t d,
+                              int32_t purpose, float* u);
+
+/* Bootstrap multiplicities of tree `tree_id` (Sec. V, SLM Forest): n draws
+ * with replacement, draw k = floor(r * n / 2^32) with r = lane (k mod 4) of
+ * Philox4x32-10(seed, {tree_id, k>>2, 0, 5<<24}). w[n] receives the counts. */
+slm_status slm_bootstrap(slm_ctx* ctx, uint64_t seed, uint32_t tree_id,
+                         int64_t n, uint32_t* w);
+
+/* Scores n_pos projection vectors (rows of positions[n_pos*d]) on one node:
+ * the node holds rows sample_idx[0..n_idx) of X[n*d] (sample_idx NULL = all
+ * n rows) with multiplicities weights[n_idx] (NULL = 1). Exactly one of
+ * labels[n] (classification) and y[n] (MSE) is non-NULL. out[n_pos] is
+ * written; bins_out[n_pos*n_idx] (optional) receives bin(z) per particle and
+ * node entry. Uses params: criterion, n_classes, n_bins, min_leaf. */
+slm_status slm_evaluate_swarm(slm_ctx* ctx, const slm_params* params,
+                              const float* X, int64_t n, int32_t d,
+                              const int32_t* labels, const float* y,
+                              const int32_t* sample_idx,
+                              const uint32_t* weights, int64_t n_idx,
+                              const float* positions, int32_t n_pos,
+                              slm_eval* out, int32_t* bins_out);
+
+/* PSO split search on one node (Algorithm 1, synchronous updates: every
+ * particle moves with the gB held at the end of the previous iteration; pB
+ * and gB change only on a strictly lower loss, ties to the lower particle
+ * index). node_uid keys the node's Philox streams. direction_out[d]: gB/||gB||
+ * (Eq. 2); gbest_out[d] (optional): gB itself, on which bin(z) is defined;
+ * trace_out[T+1] (optional): gB loss after each evaluation. */
+slm_status slm_node_split(slm_ctx* ctx, const slm_params* params,
+                          const float* X, int64_t n, int32_t d,
+                          const int32_t* labels, const float* y,
+                          const int32_t* sample_idx, const uint32_t* weights,
+                          int64_t n_idx, uint32_t node_uid,
+                          float* direction_out, float* gbest_out,
+                          slm_split* out, double* trace_out);
+
+/* Tree / forest growth (Algorithm 2), level by level. Each call to
+ * slm_grow_level searches every splittable node of the current level of
+ * every tree in one batch (node uid = tree_id << 16 | heap index) and
+ * partitions their samples into the next level. A node is a leaf when it is
+ * at max_depth, holds < 2*min_leaf weighted samples, is pure (one class /
+ * constant target), has no admissible split, or its best split does not lower
+ * the impurity. *n_split_out (optional) = nodes split by this call; 0 means
+ * the forest is complete. */
+slm_status slm_forest_begin(slm_ctx* ctx, const slm_params* params,
+                            const float* X, int64_t n, int32_t d,
+                            const int32_t* labels, const float* y,
+                            slm_forest** out);
+slm_status slm_grow_level(slm_ctx* ctx, slm_forest* forest,
+                          int32_t* n_split_out);
+/* forest_begin + grow_level until complete. */
+slm_status slm_train_tree(slm_ctx* ctx, const slm_params* params,
+                          const float* X, int64_t n, int32_t d,
+                          const int32_t* labels, const float* y,
+                          slm_forest** out);
+void slm_forest_free(slm_forest* forest);
+
+/* Number of trees, heap size H = 2^(max_depth+1) - 1, feature count, and the
+ * particle-sample evaluations performed so far: the sum over searched nodes
+ * of (distinct samples in the node) * P * (T+1). Any pointer may be NULL. */
+slm_status slm_forest_info(const slm_forest* forest, int32_t* n_trees,
+                           int32_t* heap_size, int32_t* d,
+                           int64_t* evaluations);
+
+/* Copies tree `tree` of a forest to host arrays in heap layout (node h has
+ * children 2h+1 and 2h+2); any pointer may be NULL. kind: -1 absent, 0 leaf,
+ * 1 internal. dir[H*d]: raw gB of the split. leaf_class / leaf_value: majority
+ * class (ties to the lowest id) / mean target. */
+slm_status slm_forest_export(slm_ctx* ctx, const slm_forest* forest,
+                             int32_t tree, int32_t* kind, float* dir,
+                             float* zmin, float* inv_w, int32_t* bin,
+                             int32_t* leaf_class, double* leaf_value,
+                             int64_t* weight, double* loss, int64_t* n_left,
+                             int64_t* n_right);
+
+/* Routes X[n*d] through every tree: internal node h sends x right iff
+ * bin_h(gB_h . x) >= bin_h, with bin clamped to [0, B-1]. class_out[n]
+ * (classification): majority vote over trees, ties to the lowest class;
+ * value_out[n] (MSE): mean of the trees' leaf values; leaf_out[n*n_trees]
+ * (optional): heap index of the leaf reached in each tree. */
+slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
+                       int64_t n, int32_t d, int32_t* class_out,
+                       double* value_out, int32_t* leaf_out);
+
+
+/* ---- diagnostics --------------------------------------------------------
+ * Kernels of this library, for per-kernel timing. */
+typedef enum {
+  SLM_K_EVAL_SMALL = 0,   /* fused scoring of nodes held by one CTA */
+  SLM_K_MINMAX_CHUNK = 1, /* range pass of large nodes */
+  SLM_K_HIST_CHUNK = 2,   /* histogram pass of large nodes */
+  SLM_K_REDUCE_SCAN = 3,  /* partial-histogram reduction and scan */
+  SLM_K_SWARM_UPDATE = 4, /* pbest / gbest and Eq. pso-1 */
+  SLM_K_SWARM_INIT = 5,
+  SLM_K_NODE_STATS = 6,
+  SLM_K_PARTITION = 7,
+  SLM_K_COMPACT = 8,
+  SLM_K_OTHER = 9,        /* validation, bootstrap, index setup */
+  SLM_K_COUNT = 10
+} slm_kernel;
+
+/* on != 0 brackets every later launch of the context with CUDA events on its
+ * stream; the counters restart at zero. Timing adds an event record per
+ * launch and is meant for profiling runs. */
+slm_status slm_profile(slm_ctx* ctx, int on);
+/* Totals since slm_profile(ctx, 1) for one kernel: launches, summed event
+ * time (ms; 0 while profiling is off) and particle-sample pairs the launches
+ * scored (scoring kernels; 0 for the others). Synchronises the stream. */
+slm_status slm_kernel_stats(slm_ctx* ctx, int32_t kernel, int64_t* launches,
+                            double* total_ms, double* pairs);
+/* Kernels launched by the context since its creation. */
+slm_status slm_launch_count(slm_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

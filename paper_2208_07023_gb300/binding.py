@@ -1,0 +1,305 @@
+"""ctypes binding of libslm (include/slm.h).
+
+Argument marshalling only: every step of the computation runs inside
+libslm.so. Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+their raw pointers go to the C ABI, which stages host arrays itself. If the
+library is missing or cannot be loaded the import of a Context fails loudly;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+SLM_OK, SLM_EINVAL, SLM_ENOMEM, SLM_ECUDA, SLM_ETIMEOUT, SLM_EUNSUPPORTED = range(6)
+SLM_GINI, SLM_ENTROPY, SLM_MSE = 0, 1, 2
+SLM_PROJ_FP32, SLM_PROJ_BF16_TOPK = 0, 1
+CRITERIA = {"gini": SLM_GINI, "entropy": SLM_ENTROPY, "mse": SLM_MSE}
+PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2 = 1, 2, 3, 4
+KERNELS = ["eval_small", "minmax_chunk", "hist_chunk", "reduce_scan", "swarm_update",
+           "swarm_init", "node_stats", "partition", "compact", "other"]
+
+
+class slm_params(C.Structure):
+    _fields_ = [
+        ("criterion", C.c_int32), ("n_classes", C.c_int32),
+        ("n_particles", C.c_int32), ("n_iters", C.c_int32),
+        ("n_bins", C.c_int32), ("topk", C.c_int32), ("inertia", C.c_float),
+        ("c1", C.c_float), ("c2", C.c_float), ("max_depth", C.c_int32),
+        ("min_leaf", C.c_int32), ("proj", C.c_int32), ("n_trees", C.c_int32),
+        ("bootstrap", C.c_int32), ("reserved", C.c_int32),
+        ("seed", C.c_uint64),
+    ]
+
+
+class slm_eval(C.Structure):
+    _fields_ = [
+        ("loss", C.c_double), ("q_num", C.c_uint64), ("q_den", C.c_uint64),
+        ("zmin", C.c_float), ("inv_w", C.c_float), ("bin", C.c_int32),
+        ("valid", C.c_int32), ("n_left", C.c_int64), ("n_right", C.c_int64),
+    ]
+
+
+class slm_split(C.Structure):
+    _fields_ = [
+        ("eval", slm_eval), ("particle", C.c_int32),
+        ("iter_of_best", C.c_int32), ("threshold", C.c_float),
+        ("norm", C.c_float),
+    ]
+
+
+class SlmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libslm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Loads libslm.so (building it first if stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libslm.so not found at {path}")
+        L = C.CDLL(path)
+        vp, i32, i64, u32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+        P = C.POINTER
+        sig = {
+            "slm_status_string": ([C.c_int], C.c_char_p),
+            "slm_create": ([P(vp), C.c_int, vp], C.c_int),
+            "slm_destroy": ([vp], None),
+            "slm_last_error": ([vp, C.c_char_p, C.c_size_t], C.c_int),
+            "slm_swarm_uniforms": ([vp, u64, u32, u32, i32, i32, i32, vp], C.c_int),
+            "slm_bootstrap": ([vp, u64, u32, i64, vp], C.c_int),
+            "slm_evaluate_swarm": ([vp, P(slm_params), vp, i64, i32, vp, vp, vp, vp,
+                                    i64, vp, i32, vp, vp], C.c_int),
+            "slm_node_split": ([vp, P(slm_params), vp, i64, i32, vp, vp, vp, vp, i64,
+                                u32, vp, vp, P(slm_split), vp], C.c_int),
+            "slm_forest_begin": ([vp, P(slm_params), vp, i64, i32, vp, vp, P(vp)], C.c_int),
+            "slm_grow_level": ([vp, vp, P(i32)], C.c_int),
+            "slm_train_tree": ([vp, P(slm_params), vp, i64, i32, vp, vp, P(vp)], C.c_int),
+            "slm_forest_free": ([vp], None),
+            "slm_forest_info": ([vp, P(i32), P(i32), P(i32), P(i64)], C.c_int),
+            "slm_forest_export": ([vp, vp, i32] + [vp] * 11, C.c_int),
+            "slm_predict": ([vp, vp, vp, i64, i32, vp, vp, vp], C.c_int),
+            "slm_profile": ([vp, C.c_int], C.c_int),
+            "slm_kernel_stats": ([vp, i32, P(i64), P(C.c_double), P(C.c_double)], C.c_int),
+            "slm_launch_count": ([vp, P(i64)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
+                n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8, min_leaf=1,
+                seed=1, n_trees=1, bootstrap=False, proj=SLM_PROJ_FP32,
+                topk=8) -> slm_params:
+    crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
+    return slm_params(crit, 0 if crit == SLM_MSE else n_classes, n_particles,
+                      n_iters, n_bins, topk, inertia, c1, c2, max_depth, min_leaf,
+                      proj, n_trees, 1 if bootstrap else 0, 0, seed)
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw pointer of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _as(a, dtype):
+    if a is None or not isinstance(a, (list, tuple, np.ndarray)):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Forest:
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.handle = C.c_void_p(handle)
+
+    def info(self):
+        nt, hs, d, ev = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        self.ctx._check(lib().slm_forest_info(self.handle, C.byref(nt), C.byref(hs),
+                                              C.byref(d), C.byref(ev)))
+        return {"n_trees": nt.value, "heap_size": hs.value, "d": d.value,
+                "evaluations": ev.value}
+
+    def grow_level(self) -> int:
+        n = C.c_int32()
+        self.ctx._check(lib().slm_grow_level(self.ctx.handle, self.handle, C.byref(n)))
+        return n.value
+
+    def export(self, tree: int = 0) -> dict:
+        inf = self.info()
+        H, d = inf["heap_size"], inf["d"]
+        out = {"kind": np.empty(H, np.int32), "dir": np.empty((H, d), np.float32),
+               "zmin": np.empty(H, np.float32), "inv_w": np.empty(H, np.float32),
+               "bin": np.empty(H, np.int32), "leaf_class": np.empty(H, np.int32),
+               "leaf_value": np.empty(H, np.float64), "weight": np.empty(H, np.int64),
+               "loss": np.empty(H, np.float64), "n_left": np.empty(H, np.int64),
+               "n_right": np.empty(H, np.int64)}
+        self.ctx._check(lib().slm_forest_export(
+            self.ctx.handle, self.handle, tree,
+            *[_ptr(out[k]) for k in ("kind", "dir", "zmin", "inv_w", "bin", "leaf_class",
+                                     "leaf_value", "weight", "loss", "n_left", "n_right")]))
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().slm_forest_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One libslm context (device + stream)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        h = C.c_void_p()
+        st = lib().slm_create(C.byref(h), device, stream)
+        if st != SLM_OK:
+            raise SlmError(st, "slm_create failed")
+        self.handle = h
+
+    def _check(self, st: int):
+        if st != SLM_OK:
+            buf = C.create_string_buffer(512)
+            lib().slm_last_error(self.handle, buf, 512)
+            raise SlmError(st, buf.value.decode(errors="replace"))
+
+    def close(self):
+        if self.handle:
+            lib().slm_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- diagnostics -------------------------------------------------------
+    def profile(self, on: bool):
+        self._check(lib().slm_profile(self.handle, 1 if on else 0))
+
+    def kernel_stats(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNELS):
+            n, ms, pairs = C.c_int64(), C.c_double(), C.c_double()
+            self._check(lib().slm_kernel_stats(self.handle, k, C.byref(n), C.byref(ms),
+                                               C.byref(pairs)))
+            out[name] = {"launches": n.value, "ms": ms.value, "pairs": pairs.value}
+        return out
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(lib().slm_launch_count(self.handle, C.byref(n)))
+        return n.value
+
+    # -- raw draws -------------------------------------------------------
+    def swarm_uniforms(self, seed, node_uid, t, n_particles, d, purpose):
+        u = np.empty((n_particles, d), np.float32)
+        self._check(lib().slm_swarm_uniforms(self.handle, seed, node_uid, t,
+                                             n_particles, d, purpose, _ptr(u)))
+        return u
+
+    def bootstrap(self, seed, tree_id, n):
+        w = np.empty(n, np.uint32)
+        self._check(lib().slm_bootstrap(self.handle, seed, tree_id, n, _ptr(w)))
+        return w
+
+    # -- scoring and search ------------------------------------------------
+    def evaluate_swarm(self, params, X, positions, labels=None, y=None,
+                       sample_idx=None, weights=None, want_bins=False):
+        X = _as(X, np.float32)
+        positions = _as(positions, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
+        n, d = X.shape
+        n_pos = positions.shape[0]
+        n_idx = n if sample_idx is None else sample_idx.shape[0]
+        out = (slm_eval * n_pos)()
+        bins = np.empty((n_pos, n_idx), np.int32) if want_bins else None
+        self._check(lib().slm_evaluate_swarm(
+            self.handle, C.byref(params), _ptr(X), n, d, _ptr(labels), _ptr(y),
+            _ptr(sample_idx), _ptr(weights), n_idx, _ptr(positions), n_pos, out,
+            _ptr(bins)))
+        return [_eval_dict(e) for e in out], bins
+
+    def node_split(self, params, X, labels=None, y=None, sample_idx=None,
+                   weights=None, node_uid=0, want_trace=False):
+        X = _as(X, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
+        n, d = X.shape
+        n_idx = n if sample_idx is None else sample_idx.shape[0]
+        direction = np.empty(d, np.float32)
+        gbest = np.empty(d, np.float32)
+        trace = np.empty(params.n_iters + 1, np.float64) if want_trace else None
+        sp = slm_split()
+        self._check(lib().slm_node_split(
+            self.handle, C.byref(params), _ptr(X), n, d, _ptr(labels), _ptr(y),
+            _ptr(sample_idx), _ptr(weights), n_idx, node_uid, _ptr(direction),
+            _ptr(gbest), C.byref(sp), _ptr(trace)))
+        res = _eval_dict(sp.eval)
+        res.update(particle=sp.particle, iter_of_best=sp.iter_of_best,
+                   threshold=sp.threshold, norm=sp.norm, direction=direction,
+                   gbest=gbest, trace=trace)
+        return res
+
+    def forest_begin(self, params, X, labels=None, y=None) -> Forest:
+        X = _as(X, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        n, d = X.shape
+        h = C.c_void_p()
+        self._check(lib().slm_forest_begin(self.handle, C.byref(params), _ptr(X), n, d,
+                                           _ptr(labels), _ptr(y), C.byref(h)))
+        return Forest(self, h.value)
+
+    def train_tree(self, params, X, labels=None, y=None) -> Forest:
+        X = _as(X, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        n, d = X.shape
+        h = C.c_void_p()
+        self._check(lib().slm_train_tree(self.handle, C.byref(params), _ptr(X), n, d,
+                                         _ptr(labels), _ptr(y), C.byref(h)))
+        return Forest(self, h.value)
+
+    def predict(self, forest: Forest, X, want_leaf=False):
+        X = _as(X, np.float32)
+        n, d = X.shape
+        nt = forest.info()["n_trees"]
+        cls = np.empty(n, np.int32)
+        val = np.empty(n, np.float64)
+        leaf = np.empty((n, nt), np.int32) if want_leaf else None
+        self._check(lib().slm_predict(self.handle, forest.handle, _ptr(X), n, d,
+                                      _ptr(cls), _ptr(val), _ptr(leaf)))
+        return cls, val, leaf
+
+
+def _eval_dict(e: slm_eval) -> dict:
+    return {name: getattr(e, name) for name, _ in e._fields_}

@@ -1,0 +1,1056 @@
+// C ABI of libslm (include/slm.h): argument checks, staging of host arrays,
+// the batched swarm search driver, and level-by-level tree growth.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "slm_internal.cuh"
+
+using namespace slm;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+enum Slot {
+  W_X, W_LAB, W_Y, W_IDX, W_W, W_POS_IN, W_BINS,
+  S_POS, S_VEL, S_PBEST, S_GBEST, S_CUR, S_PB, S_GB, S_GPART, S_GITER,
+  S_TRACE, S_ZMM, S_PART, S_PART_S, S_PART_Q,
+  S_NODES, S_LIST, S_ITEMS, S_BIG, S_STATUS, S_OUT,
+  N_SLOTS
+};
+
+}  // namespace
+
+struct slm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  DevBuf ws[N_SLOTS];
+  // launch accounting and optional per-kernel CUDA-event timing
+  int64_t launches = 0;
+  bool prof = false;
+  struct Pending {
+    int kid;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  int64_t k_launches[SLM_K_COUNT] = {};
+  double k_ms[SLM_K_COUNT] = {};
+  double k_pairs[SLM_K_COUNT] = {};
+};
+
+struct slm_forest {
+  slm_ctx* ctx = nullptr;  // creating context (not owned; may be gone at free)
+  int device = 0;
+  slm_params params{};
+  int64_t n = 0;
+  int d = 0;
+  int H = 0;
+  int n_trees = 0;
+  int K = 0;
+  const float* X = nullptr;
+  const int32_t* labels = nullptr;
+  const float* y = nullptr;
+  DevBuf own_X, own_lab, own_y;
+  TreeArrays tr{};
+  DevBuf tree_mem;
+  DevBuf idx[2], w[2], side;
+  int cur = 0;
+  bool weighted = false;
+  std::vector<LevelNode> level;  // nodes of the level to grow next
+  int depth = 0;
+  bool done = false;
+  int64_t evaluations = 0;
+  DevBuf lvl_nodes, lvl_split, lvl_cls, lvl_par, snodes, smap, out3, dst;
+};
+
+namespace {
+
+slm_status fail(slm_ctx* c, slm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+slm_status cuda_fail(slm_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return SLM_ECUDA;
+}
+
+#define CK(expr)                                    \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
+  } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (bytes <= b.cap) return cudaSuccess;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (e) return e;
+  }
+  const size_t want = bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e) {
+    b.p = nullptr;
+    return e;
+  }
+  b.cap = want;
+  return cudaSuccess;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself, or a staged copy.
+template <typename T>
+slm_status stage_in(slm_ctx* c, const T* src, size_t count, DevBuf& buf,
+                    const T** out) {
+  if (!src || count == 0) {
+    *out = src;
+    return SLM_OK;
+  }
+  if (is_device_ptr(src)) {
+    *out = src;
+    return SLM_OK;
+  }
+  CK(ensure(buf, sizeof(T) * count));
+  CK(cudaMemcpyAsync(buf.p, src, sizeof(T) * count, cudaMemcpyHostToDevice,
+                     c->stream));
+  *out = static_cast<const T*>(buf.p);
+  return SLM_OK;
+}
+
+slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
+                        bool need_swarm) {
+  if (!p) return fail(c, SLM_EINVAL, "params is NULL");
+  if (p->criterion < SLM_GINI || p->criterion > SLM_MSE)
+    return fail(c, SLM_EINVAL, "criterion out of range");
+  if (p->criterion != SLM_MSE && (p->n_classes < 2 || p->n_classes > kMaxClasses))
+    return fail(c, SLM_EINVAL, "n_classes must be in [2, 32]");
+  if (p->n_bins < 2 || p->n_bins > kMaxBins)
+    return fail(c, SLM_EINVAL, "n_bins must be in [2, 256]");
+  if (p->criterion != SLM_MSE &&
+      (int64_t)p->n_bins * p->n_classes * 4 > kMaxHistBytesPerParticle)
+    return fail(c, SLM_EUNSUPPORTED, "n_bins * n_classes * 4 exceeds 10240");
+  if (p->min_leaf < 1) return fail(c, SLM_EINVAL, "min_leaf must be >= 1");
+  if (d < 1 || d > kMaxD) return fail(c, SLM_EINVAL, "d must be in [1, 1024]");
+  if (need_swarm) {
+    if (p->n_particles < 1 || p->n_particles > kMaxParticles)
+      return fail(c, SLM_EINVAL, "n_particles must be in [1, 256]");
+    if (p->n_iters < 0) return fail(c, SLM_EINVAL, "n_iters must be >= 0");
+    if (p->proj != SLM_PROJ_FP32)
+      return fail(c, SLM_EUNSUPPORTED, "only SLM_PROJ_FP32 is implemented");
+    if (!std::isfinite(p->inertia) || !std::isfinite(p->c1) ||
+        !std::isfinite(p->c2))
+      return fail(c, SLM_EINVAL, "inertia / c1 / c2 must be finite");
+  }
+  return SLM_OK;
+}
+
+Problem make_problem(const slm_params* p, const float* X, int d,
+                     const int32_t* labels, const float* y, const int32_t* idx,
+                     const uint32_t* w, int P) {
+  Problem pr{};
+  pr.X = X;
+  pr.labels = labels;
+  pr.y = y;
+  pr.idx = idx;
+  pr.w = w;
+  pr.d = d;
+  pr.crit = p->criterion;
+  pr.K = p->criterion == SLM_MSE ? 1 : p->n_classes;
+  pr.B = p->n_bins;
+  pr.min_leaf = p->min_leaf;
+  pr.P = P;
+  pr.Pp = (P + kPG - 1) / kPG * kPG;
+  pr.G = pr.Pp / kPG;
+  return pr;
+}
+
+// Work lists of a batch: nodes small enough for one CTA, and the chunked
+// work items of the others.
+struct Batch {
+  std::vector<int32_t> small;
+  std::vector<ChunkItem> items;
+  std::vector<BigNode> big;
+};
+
+Batch plan_batch(const std::vector<NodeDesc>& nodes) {
+  Batch b;
+  for (int a = 0; a < (int)nodes.size(); ++a) {
+    const int len = nodes[a].seg_len;
+    if (len <= kSmallMax) {
+      b.small.push_back(a);
+      continue;
+    }
+    BigNode bn{a, (int32_t)b.items.size(), 0, 0};
+    for (int s = 0; s < len; s += kChunk) {
+      ChunkItem it{a, s, std::min(kChunk, len - s), s == 0};
+      b.items.push_back(it);
+      ++bn.n_items;
+    }
+    b.big.push_back(bn);
+  }
+  return b;
+}
+
+cudaEvent_t take_event(slm_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Runs one kernel launch, counting it and (when profiling) bracketing it with
+// events on the context's stream. pairs: particle-sample pairs it scores.
+template <class F>
+cudaError_t launch(slm_ctx* c, int kid, double pairs, F&& fn) {
+  c->launches += 1;
+  c->k_launches[kid] += 1;
+  c->k_pairs[kid] += pairs;
+  if (!c->prof) return fn();
+  cudaEvent_t ea = take_event(c), eb = take_event(c);
+  if (ea) cudaEventRecord(ea, c->stream);
+  cudaError_t e = fn();
+  if (eb) cudaEventRecord(eb, c->stream);
+  if (ea && eb) c->pending.push_back({kid, ea, eb});
+  return e;
+}
+
+cudaError_t collect_profile(slm_ctx* c) {
+  if (c->pending.empty()) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return e;
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->k_ms[p.kid] += ms;
+    c->free_events.push_back(p.a);
+    c->free_events.push_back(p.b);
+  }
+  c->pending.clear();
+  return cudaSuccess;
+}
+
+template <typename T>
+T* ws_ptr(slm_ctx* c, Slot s) {
+  return static_cast<T*>(c->ws[s].p);
+}
+
+// Allocates the swarm buffers of A nodes and the batch lists, uploads them.
+slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T,
+                       bool want_trace, const std::vector<NodeDesc>& nodes,
+                       const Batch& b, Swarm* sw) {
+  const size_t apd = (size_t)A * pr.Pp * pr.d;
+  CK(ensure(c->ws[S_POS], sizeof(float) * apd));
+  CK(ensure(c->ws[S_VEL], sizeof(float) * apd));
+  CK(ensure(c->ws[S_PBEST], sizeof(float) * apd));
+  CK(ensure(c->ws[S_GBEST], sizeof(float) * (size_t)A * pr.d));
+  CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * (size_t)A * pr.Pp));
+  CK(ensure(c->ws[S_PB], sizeof(EvalRes) * (size_t)A * pr.Pp));
+  CK(ensure(c->ws[S_GB], sizeof(EvalRes) * (size_t)A));
+  CK(ensure(c->ws[S_GPART], sizeof(int32_t) * (size_t)A));
+  CK(ensure(c->ws[S_GITER], sizeof(int32_t) * (size_t)A));
+  CK(ensure(c->ws[S_ZMM], sizeof(int32_t) * 2 * (size_t)A * pr.Pp));
+  if (want_trace) CK(ensure(c->ws[S_TRACE], sizeof(double) * (size_t)A * (T + 1)));
+  const size_t words = pr.crit == SLM_MSE ? (size_t)pr.B : (size_t)pr.B * pr.K;
+  const size_t pw = b.items.size() * pr.Pp * words;
+  CK(ensure(c->ws[S_PART], sizeof(uint32_t) * pw));
+  if (pr.crit == SLM_MSE) {
+    CK(ensure(c->ws[S_PART_S], sizeof(double) * pw));
+    CK(ensure(c->ws[S_PART_Q], sizeof(double) * pw));
+  }
+  CK(ensure(c->ws[S_NODES], sizeof(NodeDesc) * nodes.size()));
+  CK(ensure(c->ws[S_LIST], sizeof(int32_t) * b.small.size()));
+  CK(ensure(c->ws[S_ITEMS], sizeof(ChunkItem) * b.items.size()));
+  CK(ensure(c->ws[S_BIG], sizeof(BigNode) * b.big.size()));
+  CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc) * nodes.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  if (!b.small.empty())
+    CK(cudaMemcpyAsync(c->ws[S_LIST].p, b.small.data(), sizeof(int32_t) * b.small.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  if (!b.items.empty())
+    CK(cudaMemcpyAsync(c->ws[S_ITEMS].p, b.items.data(),
+                       sizeof(ChunkItem) * b.items.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  if (!b.big.empty())
+    CK(cudaMemcpyAsync(c->ws[S_BIG].p, b.big.data(), sizeof(BigNode) * b.big.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  Swarm s{};
+  s.pos = ws_ptr<float>(c, S_POS);
+  s.vel = ws_ptr<float>(c, S_VEL);
+  s.pbest = ws_ptr<float>(c, S_PBEST);
+  s.gbest = ws_ptr<float>(c, S_GBEST);
+  s.cur = ws_ptr<EvalRes>(c, S_CUR);
+  s.pb = ws_ptr<EvalRes>(c, S_PB);
+  s.gb = ws_ptr<EvalRes>(c, S_GB);
+  s.gpart = ws_ptr<int32_t>(c, S_GPART);
+  s.giter = ws_ptr<int32_t>(c, S_GITER);
+  s.trace = want_trace ? ws_ptr<double>(c, S_TRACE) : nullptr;
+  s.zmm = ws_ptr<int32_t>(c, S_ZMM);
+  s.part = ws_ptr<uint32_t>(c, S_PART);
+  s.part_s = ws_ptr<double>(c, S_PART_S);
+  s.part_q = ws_ptr<double>(c, S_PART_Q);
+  s.T = T;
+  *sw = s;
+  CK(prepare_eval_kernels(pr));
+  return SLM_OK;
+}
+
+// PSO search of every node of a batch (Algorithm 1, synchronous updates).
+slm_status run_search(slm_ctx* c, const slm_params* p, const Problem& pr,
+                      const std::vector<NodeDesc>& nodes, bool want_trace,
+                      Swarm* sw_out) {
+  const int A = (int)nodes.size();
+  const Batch b = plan_batch(nodes);
+  Swarm sw;
+  slm_status s = setup_swarm(c, pr, A, p->n_iters, want_trace, nodes, b, &sw);
+  if (s) return s;
+  const SwarmCoef co{p->inertia, p->c1, p->c2, p->seed};
+  const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
+  double small_pairs = 0.0, big_pairs = 0.0;
+  for (int32_t a : b.small) small_pairs += (double)nodes[a].seg_len * pr.P;
+  for (const BigNode& bn : b.big) big_pairs += (double)nodes[bn.node].seg_len * pr.P;
+  CK(launch(c, SLM_K_SWARM_INIT, 0.0,
+            [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
+  const int n_small = (int)b.small.size(), n_items = (int)b.items.size();
+  const int n_big = (int)b.big.size();
+  const int32_t* dl = ws_ptr<int32_t>(c, S_LIST);
+  const ChunkItem* di = ws_ptr<ChunkItem>(c, S_ITEMS);
+  const BigNode* db = ws_ptr<BigNode>(c, S_BIG);
+  for (int t = 0; t <= p->n_iters; ++t) {
+    if (n_small)
+      CK(launch(c, SLM_K_EVAL_SMALL, small_pairs, [&] {
+        return launch_eval_small(pr, sw, dn, dl, n_small, c->stream);
+      }));
+    if (n_items) {
+      CK(launch(c, SLM_K_MINMAX_CHUNK, big_pairs, [&] {
+        return launch_minmax_chunk(pr, sw, dn, di, n_items, c->stream);
+      }));
+      CK(launch(c, SLM_K_HIST_CHUNK, big_pairs, [&] {
+        return launch_hist_chunk(pr, sw, dn, di, n_items, c->stream);
+      }));
+      CK(launch(c, SLM_K_REDUCE_SCAN, 0.0, [&] {
+        return launch_reduce_scan(pr, sw, db, n_big, c->stream);
+      }));
+    }
+    CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
+              [&] { return launch_swarm_update(pr, sw, dn, A, t, co, c->stream); }));
+  }
+  *sw_out = sw;
+  return SLM_OK;
+}
+
+slm_status read_status(slm_ctx* c, int32_t* out) {
+  CK(cudaMemcpyAsync(out, c->ws[S_STATUS].p, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status reset_status(slm_ctx* c) {
+  CK(ensure(c->ws[S_STATUS], sizeof(int32_t)));
+  CK(cudaMemsetAsync(c->ws[S_STATUS].p, 0, sizeof(int32_t), c->stream));
+  return SLM_OK;
+}
+
+// Validates labels / sample indices on the device.
+slm_status validate_inputs(slm_ctx* c, const int32_t* labels, int64_t n, int K,
+                           const int32_t* idx, int64_t n_idx) {
+  slm_status s = reset_status(c);
+  if (s) return s;
+  CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+    return launch_validate(labels, labels ? n : 0, K, idx, idx ? n_idx : 0,
+                           ws_ptr<int32_t>(c, S_STATUS), c->stream);
+  }));
+  int32_t st = 0;
+  if ((s = read_status(c, &st))) return s;
+  if (st) return fail(c, SLM_EINVAL, "label outside [0, K) or sample index outside [0, n)");
+  return SLM_OK;
+}
+
+template <typename T>
+slm_status copy_out(slm_ctx* c, T* dst, const T* src, size_t count) {
+  if (!dst || count == 0) return SLM_OK;
+  CK(cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDefault, c->stream));
+  return SLM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* slm_status_string(slm_status s) {
+  switch (s) {
+    case SLM_OK: return "ok";
+    case SLM_EINVAL: return "invalid argument";
+    case SLM_ENOMEM: return "out of device memory";
+    case SLM_ECUDA: return "CUDA error";
+    case SLM_ETIMEOUT: return "device wait timed out";
+    case SLM_EUNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown status";
+}
+
+slm_status slm_create(slm_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SLM_EINVAL;
+  *out = nullptr;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return SLM_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return SLM_ECUDA;
+  slm_ctx* c = new (std::nothrow) slm_ctx();
+  if (!c) return SLM_ENOMEM;
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return SLM_OK;
+}
+
+void slm_destroy(slm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& b : c->ws) release(b);
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
+  delete c;
+}
+
+slm_status slm_last_error(slm_ctx* c, char* buf, size_t len) {
+  if (!c || !buf || len == 0) return SLM_EINVAL;
+  std::snprintf(buf, len, "%s", c->err.c_str());
+  return SLM_OK;
+}
+
+slm_status slm_swarm_uniforms(slm_ctx* c, uint64_t seed, uint32_t node_uid,
+                              uint32_t t, int32_t n_particles, int32_t d,
+                              int32_t purpose, float* u) {
+  if (!c || !u || n_particles < 1 || d < 1 || purpose < 1 || purpose > 255)
+    return fail(c, SLM_EINVAL, "bad arguments to slm_swarm_uniforms");
+  CK(cudaSetDevice(c->device));
+  const size_t cnt = (size_t)n_particles * d;
+  float* dst = u;
+  const bool dev = is_device_ptr(u);
+  if (!dev) {
+    CK(ensure(c->ws[S_OUT], sizeof(float) * cnt));
+    dst = ws_ptr<float>(c, S_OUT);
+  }
+  CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+    return launch_swarm_uniforms(seed, node_uid, t, n_particles, d, (uint32_t)purpose, dst,
+                                 c->stream);
+  }));
+  if (!dev) {
+    if (slm_status s = copy_out(c, u, dst, cnt)) return s;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_bootstrap(slm_ctx* c, uint64_t seed, uint32_t tree_id, int64_t n,
+                         uint32_t* w) {
+  if (!c || !w || n < 1 || n > INT32_MAX)
+    return fail(c, SLM_EINVAL, "bad arguments to slm_bootstrap");
+  CK(cudaSetDevice(c->device));
+  uint32_t* dst = w;
+  const bool dev = is_device_ptr(w);
+  if (!dev) {
+    CK(ensure(c->ws[S_OUT], sizeof(uint32_t) * n));
+    dst = ws_ptr<uint32_t>(c, S_OUT);
+  }
+  CK(launch(c, SLM_K_OTHER, 0.0,
+            [&] { return launch_bootstrap(seed, tree_id, n, dst, c->stream); }));
+  if (!dev) {
+    if (slm_status s = copy_out(c, w, dst, (size_t)n)) return s;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
+                              int64_t n, int32_t d, const int32_t* labels,
+                              const float* y, const int32_t* sample_idx,
+                              const uint32_t* weights, int64_t n_idx,
+                              const float* positions, int32_t n_pos,
+                              slm_eval* out, int32_t* bins_out) {
+  if (!c) return SLM_EINVAL;
+  if (slm_status s = check_params(c, p, d, false)) return s;
+  if (!X || n < 1 || n > INT32_MAX || !positions || n_pos < 1 ||
+      n_pos > kMaxParticles || !out)
+    return fail(c, SLM_EINVAL, "bad arrays or sizes");
+  if ((p->criterion == SLM_MSE) != (y != nullptr) || (labels != nullptr) == (y != nullptr))
+    return fail(c, SLM_EINVAL, "exactly one of labels / y, matching the criterion");
+  if (!sample_idx) n_idx = n;
+  if (n_idx < 0 || n_idx > INT32_MAX) return fail(c, SLM_EINVAL, "n_idx out of range");
+  CK(cudaSetDevice(c->device));
+  const float *dX, *dy;
+  const int32_t *dlab, *didx;
+  const uint32_t* dw;
+  slm_status s;
+  if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return s;
+  if ((s = stage_in(c, labels, (size_t)n, c->ws[W_LAB], &dlab))) return s;
+  if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return s;
+  if ((s = stage_in(c, weights, (size_t)n_idx, c->ws[W_W], &dw))) return s;
+  if (sample_idx) {
+    if ((s = stage_in(c, sample_idx, (size_t)n_idx, c->ws[W_IDX], &didx))) return s;
+  } else {
+    CK(ensure(c->ws[W_IDX], sizeof(int32_t) * n_idx));
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_iota(ws_ptr<int32_t>(c, W_IDX), n_idx, 1, c->stream); }));
+    didx = ws_ptr<int32_t>(c, W_IDX);
+  }
+  if ((s = validate_inputs(c, dlab, n, p->n_classes, sample_idx ? didx : nullptr, n_idx)))
+    return s;
+  Problem pr = make_problem(p, dX, d, dlab, dy, didx, dw, n_pos);
+  // positions padded to Pp rows
+  CK(ensure(c->ws[S_POS], sizeof(float) * pr.Pp * d));
+  CK(cudaMemsetAsync(c->ws[S_POS].p, 0, sizeof(float) * pr.Pp * d, c->stream));
+  CK(cudaMemcpyAsync(c->ws[S_POS].p, positions, sizeof(float) * n_pos * d,
+                     cudaMemcpyDefault, c->stream));
+  std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, 0u, -1}};
+  Batch b = plan_batch(nodes);
+  CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * pr.Pp));
+  CK(ensure(c->ws[S_ZMM], sizeof(int32_t) * 2 * pr.Pp));
+  std::vector<int32_t> zinit(2 * pr.Pp);
+  for (int i = 0; i < pr.Pp; ++i) {
+    zinit[2 * i] = INT32_MAX;
+    zinit[2 * i + 1] = INT32_MIN;
+  }
+  CK(cudaMemcpyAsync(c->ws[S_ZMM].p, zinit.data(), sizeof(int32_t) * zinit.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  const size_t words = pr.crit == SLM_MSE ? (size_t)pr.B : (size_t)pr.B * pr.K;
+  CK(ensure(c->ws[S_PART], sizeof(uint32_t) * b.items.size() * pr.Pp * words));
+  if (pr.crit == SLM_MSE) {
+    CK(ensure(c->ws[S_PART_S], sizeof(double) * b.items.size() * pr.Pp * words));
+    CK(ensure(c->ws[S_PART_Q], sizeof(double) * b.items.size() * pr.Pp * words));
+  }
+  CK(ensure(c->ws[S_NODES], sizeof(NodeDesc)));
+  CK(ensure(c->ws[S_ITEMS], sizeof(ChunkItem) * b.items.size()));
+  CK(ensure(c->ws[S_BIG], sizeof(BigNode) * (b.big.size() + 1)));
+  CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc),
+                     cudaMemcpyHostToDevice, c->stream));
+  if (!b.items.empty()) {
+    CK(cudaMemcpyAsync(c->ws[S_ITEMS].p, b.items.data(), sizeof(ChunkItem) * b.items.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->ws[S_BIG].p, b.big.data(), sizeof(BigNode) * b.big.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+  Swarm sw{};
+  sw.pos = ws_ptr<float>(c, S_POS);
+  sw.cur = ws_ptr<EvalRes>(c, S_CUR);
+  sw.zmm = ws_ptr<int32_t>(c, S_ZMM);
+  sw.part = ws_ptr<uint32_t>(c, S_PART);
+  sw.part_s = ws_ptr<double>(c, S_PART_S);
+  sw.part_q = ws_ptr<double>(c, S_PART_Q);
+  CK(prepare_eval_kernels(pr));
+  int32_t* dbins = bins_out;
+  const bool bins_dev = bins_out && is_device_ptr(bins_out);
+  if (bins_out && !bins_dev) {
+    CK(ensure(c->ws[W_BINS], sizeof(int32_t) * (size_t)n_pos * n_idx));
+    dbins = ws_ptr<int32_t>(c, W_BINS);
+  }
+  c->launches += b.items.empty() ? 1 : 3;
+  CK(launch_eval_positions(pr, sw, ws_ptr<NodeDesc>(c, S_NODES),
+                           ws_ptr<ChunkItem>(c, S_ITEMS), (int)b.items.size(),
+                           ws_ptr<BigNode>(c, S_BIG), dbins, n_idx, c->stream));
+  static_assert(sizeof(slm_eval) == sizeof(EvalRes), "layout");
+  CK(cudaMemcpyAsync(out, sw.cur, sizeof(EvalRes) * n_pos, cudaMemcpyDefault, c->stream));
+  if (bins_out && !bins_dev)
+    CK(cudaMemcpyAsync(bins_out, dbins, sizeof(int32_t) * (size_t)n_pos * n_idx,
+                       cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_node_split(slm_ctx* c, const slm_params* p, const float* X,
+                          int64_t n, int32_t d, const int32_t* labels,
+                          const float* y, const int32_t* sample_idx,
+                          const uint32_t* weights, int64_t n_idx,
+                          uint32_t node_uid, float* direction_out,
+                          float* gbest_out, slm_split* out, double* trace_out) {
+  if (!c) return SLM_EINVAL;
+  if (slm_status s = check_params(c, p, d, true)) return s;
+  if (!X || n < 1 || n > INT32_MAX || !out || !direction_out)
+    return fail(c, SLM_EINVAL, "bad arrays or sizes");
+  if ((p->criterion == SLM_MSE) != (y != nullptr) || (labels != nullptr) == (y != nullptr))
+    return fail(c, SLM_EINVAL, "exactly one of labels / y, matching the criterion");
+  if (!sample_idx) n_idx = n;
+  if (n_idx < 0 || n_idx > INT32_MAX) return fail(c, SLM_EINVAL, "n_idx out of range");
+  CK(cudaSetDevice(c->device));
+  const float *dX, *dy;
+  const int32_t *dlab, *didx;
+  const uint32_t* dw;
+  slm_status s;
+  if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return s;
+  if ((s = stage_in(c, labels, (size_t)n, c->ws[W_LAB], &dlab))) return s;
+  if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return s;
+  if ((s = stage_in(c, weights, (size_t)n_idx, c->ws[W_W], &dw))) return s;
+  if (sample_idx) {
+    if ((s = stage_in(c, sample_idx, (size_t)n_idx, c->ws[W_IDX], &didx))) return s;
+  } else {
+    CK(ensure(c->ws[W_IDX], sizeof(int32_t) * n_idx));
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_iota(ws_ptr<int32_t>(c, W_IDX), n_idx, 1, c->stream); }));
+    didx = ws_ptr<int32_t>(c, W_IDX);
+  }
+  if ((s = validate_inputs(c, dlab, n, p->n_classes, sample_idx ? didx : nullptr, n_idx)))
+    return s;
+  const Problem pr = make_problem(p, dX, d, dlab, dy, didx, dw, p->n_particles);
+  std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, node_uid, -1}};
+  Swarm sw;
+  if ((s = run_search(c, p, pr, nodes, trace_out != nullptr, &sw))) return s;
+  EvalRes gb;
+  int32_t part = 0, iter = 0;
+  std::vector<float> g(d);
+  CK(cudaMemcpyAsync(&gb, sw.gb, sizeof(EvalRes), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&part, sw.gpart, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&iter, sw.giter, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(g.data(), sw.gbest, sizeof(float) * d, cudaMemcpyDeviceToHost,
+                     c->stream));
+  if (trace_out)
+    CK(cudaMemcpyAsync(trace_out, sw.trace, sizeof(double) * (p->n_iters + 1),
+                       cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memcpy(&out->eval, &gb, sizeof(EvalRes));
+  out->particle = part;
+  out->iter_of_best = iter;
+  out->threshold = gb.valid ? gb.zmin + (float)gb.bin / gb.inv_w : 0.0f;
+  double nrm = 0.0;
+  for (int j = 0; j < d; ++j) nrm += (double)g[j] * g[j];
+  nrm = std::sqrt(nrm);
+  out->norm = (float)nrm;
+  std::vector<float> dir(d);
+  for (int j = 0; j < d; ++j) dir[j] = nrm > 0.0 ? (float)(g[j] / nrm) : 0.0f;
+  CK(cudaMemcpy(direction_out, dir.data(), sizeof(float) * d, cudaMemcpyDefault));
+  if (gbest_out) CK(cudaMemcpy(gbest_out, g.data(), sizeof(float) * d, cudaMemcpyDefault));
+  return SLM_OK;
+}
+
+// ---- forests ------------------------------------------------------------------
+
+static slm_status forest_alloc_trees(slm_ctx* c, slm_forest* f) {
+  const size_t TH = (size_t)f->n_trees * f->H;
+  const size_t bytes = TH * (4 + 4 * (size_t)f->d + 4 + 4 + 4 + 4 + 8 + 8 + 8 + 8 + 8) + 256;
+  CK(ensure(f->tree_mem, bytes));
+  unsigned char* p = static_cast<unsigned char*>(f->tree_mem.p);
+  auto take = [&](size_t sz) {
+    unsigned char* r = p;
+    p += (sz + 15) & ~size_t(15);
+    return r;
+  };
+  f->tr.weight = (int64_t*)take(8 * TH);
+  f->tr.leaf_value = (double*)take(8 * TH);
+  f->tr.loss = (double*)take(8 * TH);
+  f->tr.n_left = (int64_t*)take(8 * TH);
+  f->tr.n_right = (int64_t*)take(8 * TH);
+  f->tr.kind = (int32_t*)take(4 * TH);
+  f->tr.zmin = (float*)take(4 * TH);
+  f->tr.inv_w = (float*)take(4 * TH);
+  f->tr.bin = (int32_t*)take(4 * TH);
+  f->tr.leaf_class = (int32_t*)take(4 * TH);
+  f->tr.dir = (float*)take(4 * TH * f->d);
+  CK(cudaMemsetAsync(f->tree_mem.p, 0, f->tree_mem.cap, c->stream));
+  std::vector<int32_t> minus(TH, -1);
+  CK(cudaMemcpyAsync(f->tr.kind, minus.data(), 4 * TH, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+void slm_forest_free(slm_forest* f) {
+  if (!f) return;
+  cudaSetDevice(f->device);
+  DevBuf* bufs[] = {&f->own_X, &f->own_lab, &f->own_y, &f->tree_mem, &f->idx[0],
+                    &f->idx[1], &f->w[0], &f->w[1], &f->side, &f->lvl_nodes,
+                    &f->lvl_split, &f->lvl_cls, &f->lvl_par, &f->snodes, &f->smap,
+                    &f->out3, &f->dst};
+  for (DevBuf* b : bufs) release(*b);
+  delete f;
+}
+
+slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
+                            int64_t n, int32_t d, const int32_t* labels,
+                            const float* y, slm_forest** out) {
+  if (!c || !out) return fail(c, SLM_EINVAL, "NULL context or output");
+  *out = nullptr;
+  if (slm_status s = check_params(c, p, d, true)) return s;
+  if (!X || n < 1 || n > INT32_MAX)
+    return fail(c, SLM_EINVAL, "bad X or n");
+  if ((p->criterion == SLM_MSE) != (y != nullptr) || (labels != nullptr) == (y != nullptr))
+    return fail(c, SLM_EINVAL, "exactly one of labels / y, matching the criterion");
+  if (p->max_depth < 0 || p->max_depth > 15)
+    return fail(c, SLM_EINVAL, "max_depth must be in [0, 15]");
+  if (p->n_trees < 1 || p->n_trees > 65535)
+    return fail(c, SLM_EINVAL, "n_trees must be in [1, 65535]");
+  if (p->criterion == SLM_GINI && n >= (int64_t(1) << 22))
+    return fail(c, SLM_EUNSUPPORTED, "Gini needs fewer than 2^22 samples per tree");
+  if ((int64_t)n * p->n_trees > INT32_MAX)
+    return fail(c, SLM_EUNSUPPORTED, "n * n_trees must be < 2^31");
+  CK(cudaSetDevice(c->device));
+  slm_forest* f = new (std::nothrow) slm_forest();
+  if (!f) return fail(c, SLM_ENOMEM, "host allocation failed");
+  f->ctx = c;
+  f->device = c->device;
+  f->params = *p;
+  f->n = n;
+  f->d = d;
+  f->H = (1 << (p->max_depth + 1)) - 1;
+  f->n_trees = p->n_trees;
+  f->K = p->criterion == SLM_MSE ? 1 : p->n_classes;
+  slm_status s;
+  auto bail = [&](slm_status st) {
+    slm_forest_free(f);
+    return st;
+  };
+  if ((s = stage_in(c, X, (size_t)n * d, f->own_X, &f->X))) return bail(s);
+  if ((s = stage_in(c, labels, (size_t)n, f->own_lab, &f->labels))) return bail(s);
+  if ((s = stage_in(c, y, (size_t)n, f->own_y, &f->y))) return bail(s);
+  if ((s = validate_inputs(c, f->labels, n, p->n_classes, nullptr, 0))) return bail(s);
+  if ((s = forest_alloc_trees(c, f))) return bail(s);
+  const size_t cap = (size_t)n * f->n_trees;
+  cudaError_t e;
+  if ((e = ensure(f->idx[0], 4 * cap)) || (e = ensure(f->idx[1], 4 * cap)) ||
+      (e = ensure(f->side, cap)))
+    return bail(cuda_fail(c, e, "level buffers"));
+  f->weighted = p->bootstrap != 0;
+  f->level.clear();
+  if (f->weighted) {
+    if ((e = ensure(f->w[0], 4 * cap)) || (e = ensure(f->w[1], 4 * cap)))
+      return bail(cuda_fail(c, e, "weight buffers"));
+    // bags: multiplicities per tree, then the nonzero samples in order
+    DevBuf wall, offs, cnts;
+    auto cleanup = [&]() {
+      release(wall);
+      release(offs);
+      release(cnts);
+    };
+    if ((e = ensure(wall, 4 * cap)) || (e = ensure(offs, 8 * (size_t)f->n_trees)) ||
+        (e = ensure(cnts, 4 * (size_t)f->n_trees))) {
+      cleanup();
+      return bail(cuda_fail(c, e, "bootstrap buffers"));
+    }
+    std::vector<int64_t> off(f->n_trees);
+    for (int t = 0; t < f->n_trees; ++t) {
+      off[t] = (int64_t)t * n;
+      c->launches += 1;
+      e = launch_bootstrap(p->seed, (uint32_t)t, n, static_cast<uint32_t*>(wall.p) + off[t],
+                           c->stream);
+      if (e) {
+        cleanup();
+        return bail(cuda_fail(c, e, "bootstrap"));
+      }
+    }
+    std::vector<int32_t> cnt(f->n_trees);
+    if ((e = cudaMemcpyAsync(offs.p, off.data(), 8 * off.size(), cudaMemcpyHostToDevice,
+                             c->stream)) ||
+        (c->launches += 1, e = launch_compact_nonzero(static_cast<uint32_t*>(wall.p), f->n_trees, n,
+                                    static_cast<int32_t*>(f->idx[1].p),
+                                    static_cast<uint32_t*>(f->w[1].p),
+                                    static_cast<int64_t*>(offs.p),
+                                    static_cast<int32_t*>(cnts.p), c->stream)) ||
+        (e = cudaMemcpyAsync(cnt.data(), cnts.p, 4 * cnt.size(), cudaMemcpyDeviceToHost,
+                             c->stream)) ||
+        (e = cudaStreamSynchronize(c->stream))) {
+      cleanup();
+      return bail(cuda_fail(c, e, "bootstrap compaction"));
+    }
+    // pack the bags contiguously into buffer 0
+    int64_t pos = 0;
+    for (int t = 0; t < f->n_trees; ++t) {
+      if ((e = cudaMemcpyAsync(static_cast<int32_t*>(f->idx[0].p) + pos,
+                               static_cast<int32_t*>(f->idx[1].p) + off[t], 4 * (size_t)cnt[t],
+                               cudaMemcpyDeviceToDevice, c->stream)) ||
+          (e = cudaMemcpyAsync(static_cast<uint32_t*>(f->w[0].p) + pos,
+                               static_cast<uint32_t*>(f->w[1].p) + off[t], 4 * (size_t)cnt[t],
+                               cudaMemcpyDeviceToDevice, c->stream))) {
+        cleanup();
+        return bail(cuda_fail(c, e, "bag packing"));
+      }
+      f->level.push_back(LevelNode{(int32_t)pos, cnt[t], t * f->H, 0});
+      pos += cnt[t];
+    }
+    e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e) return bail(cuda_fail(c, e, "bag packing"));
+  } else {
+    c->launches += 1;
+    if ((e = launch_iota(static_cast<int32_t*>(f->idx[0].p), n, f->n_trees, c->stream)))
+      return bail(cuda_fail(c, e, "iota"));
+    for (int t = 0; t < f->n_trees; ++t)
+      f->level.push_back(LevelNode{(int32_t)(t * n), (int32_t)n, t * f->H, 0});
+  }
+  f->cur = 0;
+  *out = f;
+  return SLM_OK;
+}
+
+slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
+  if (!c || !f) return fail(c, SLM_EINVAL, "NULL context or forest");
+  if (n_split_out) *n_split_out = 0;
+  if (f->done || f->level.empty()) {
+    f->done = true;
+    return SLM_OK;
+  }
+  CK(cudaSetDevice(c->device));
+  const slm_params* p = &f->params;
+  const int L = (int)f->level.size();
+  const int K = f->K;
+  int32_t* idx = static_cast<int32_t*>(f->idx[f->cur].p);
+  uint32_t* w = f->weighted ? static_cast<uint32_t*>(f->w[f->cur].p) : nullptr;
+  Problem pr = make_problem(p, f->X, f->d, f->labels, f->y, idx, w, p->n_particles);
+
+  // 1. statistics and leaf values of every node of the level
+  CK(ensure(f->lvl_nodes, sizeof(LevelNode) * L));
+  CK(ensure(f->lvl_split, sizeof(int32_t) * L));
+  CK(ensure(f->lvl_cls, sizeof(uint32_t) * (size_t)L * K));
+  CK(ensure(f->lvl_par, sizeof(double) * 2 * (size_t)L));
+  CK(cudaMemcpyAsync(f->lvl_nodes.p, f->level.data(), sizeof(LevelNode) * L,
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(launch(c, SLM_K_NODE_STATS, 0.0, [&] {
+    return launch_node_stats(pr, static_cast<LevelNode*>(f->lvl_nodes.p), L, f->tr,
+                             p->max_depth, static_cast<uint32_t*>(f->lvl_cls.p),
+                             static_cast<double*>(f->lvl_par.p),
+                             static_cast<int32_t*>(f->lvl_split.p), c->stream);
+  }));
+  std::vector<int32_t> splittable(L);
+  CK(cudaMemcpyAsync(splittable.data(), f->lvl_split.p, sizeof(int32_t) * L,
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+
+  // 2. swarm search of the splittable nodes, all in one batch
+  std::vector<NodeDesc> snodes;
+  std::vector<int32_t> smap;
+  for (int l = 0; l < L; ++l) {
+    if (!splittable[l]) continue;
+    const LevelNode& ln = f->level[l];
+    const int tree = ln.slot / f->H, h = ln.slot % f->H;
+    snodes.push_back(NodeDesc{ln.seg_start, ln.seg_len,
+                              ((uint32_t)tree << 16) | (uint32_t)h, ln.slot});
+    smap.push_back(l);
+  }
+  const int A = (int)snodes.size();
+  if (A == 0) {
+    f->done = true;
+    f->level.clear();
+    return SLM_OK;
+  }
+  Swarm sw;
+  if (slm_status s = run_search(c, p, pr, snodes, false, &sw)) return s;
+  for (const NodeDesc& nd : snodes)
+    f->evaluations += (int64_t)nd.seg_len * p->n_particles * (p->n_iters + 1);
+
+  // 3. partition on gB, zero-gain test, internal-node fields
+  CK(ensure(f->smap, sizeof(int32_t) * A));
+  CK(ensure(f->out3, sizeof(int32_t) * 3 * A));
+  CK(ensure(f->dst, sizeof(int32_t) * 2 * A));
+  CK(cudaMemcpyAsync(f->smap.p, smap.data(), sizeof(int32_t) * A, cudaMemcpyHostToDevice,
+                     c->stream));
+  if (slm_status s = reset_status(c)) return s;
+  const NodeDesc* dsn = ws_ptr<NodeDesc>(c, S_NODES);
+  CK(launch(c, SLM_K_PARTITION, 0.0, [&] {
+    return launch_partition(pr, sw, dsn, static_cast<int32_t*>(f->smap.p), A,
+                            static_cast<uint32_t*>(f->lvl_cls.p),
+                            static_cast<double*>(f->lvl_par.p), f->tr,
+                            static_cast<uint8_t*>(f->side.p),
+                            static_cast<int32_t*>(f->out3.p),
+                            ws_ptr<int32_t>(c, S_STATUS), c->stream);
+  }));
+  std::vector<int32_t> o3(3 * (size_t)A);
+  CK(cudaMemcpyAsync(o3.data(), f->out3.p, sizeof(int32_t) * 3 * A, cudaMemcpyDeviceToHost,
+                     c->stream));
+  int32_t st = 0;
+  if (slm_status s = read_status(c, &st)) return s;
+  if (st) return fail(c, SLM_ECUDA, "partition disagrees with the scored split");
+
+  // 4. next level: children of split nodes, compacted stably
+  std::vector<LevelNode> next;
+  std::vector<int32_t> dst(2 * (size_t)A, -1);
+  int32_t pos = 0, n_split = 0;
+  for (int a = 0; a < A; ++a) {
+    if (!o3[3 * a]) continue;
+    const LevelNode& ln = f->level[smap[a]];
+    const int tree = ln.slot / f->H, h = ln.slot % f->H;
+    const int32_t nl = o3[3 * a + 1], nr = o3[3 * a + 2];
+    dst[2 * a] = pos;
+    dst[2 * a + 1] = pos + nl;
+    next.push_back(LevelNode{pos, nl, tree * f->H + 2 * h + 1, ln.depth + 1});
+    next.push_back(LevelNode{pos + nl, nr, tree * f->H + 2 * h + 2, ln.depth + 1});
+    pos += nl + nr;
+    ++n_split;
+  }
+  if (n_split) {
+    const int nxt = 1 - f->cur;
+    CK(cudaMemcpyAsync(f->dst.p, dst.data(), sizeof(int32_t) * 2 * A, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(launch(c, SLM_K_COMPACT, 0.0, [&] {
+      return launch_compact(pr, dsn, A, static_cast<uint8_t*>(f->side.p),
+                            static_cast<int32_t*>(f->dst.p),
+                            static_cast<int32_t*>(f->idx[nxt].p),
+                            f->weighted ? static_cast<uint32_t*>(f->w[nxt].p) : nullptr,
+                            c->stream);
+    }));
+    f->cur = nxt;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  f->level.swap(next);
+  ++f->depth;
+  if (f->level.empty()) f->done = true;
+  if (n_split_out) *n_split_out = n_split;
+  return SLM_OK;
+}
+
+slm_status slm_train_tree(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                          int32_t d, const int32_t* labels, const float* y,
+                          slm_forest** out) {
+  slm_forest* f = nullptr;
+  slm_status s = slm_forest_begin(c, p, X, n, d, labels, y, &f);
+  if (s) return s;
+  for (int level = 0; level <= p->max_depth + 1 && !f->done; ++level) {
+    if ((s = slm_grow_level(c, f, nullptr))) {
+      slm_forest_free(f);
+      return s;
+    }
+  }
+  *out = f;
+  return SLM_OK;
+}
+
+slm_status slm_forest_info(const slm_forest* f, int32_t* n_trees, int32_t* heap_size,
+                           int32_t* d, int64_t* evaluations) {
+  if (!f) return SLM_EINVAL;
+  if (n_trees) *n_trees = f->n_trees;
+  if (heap_size) *heap_size = f->H;
+  if (d) *d = f->d;
+  if (evaluations) *evaluations = f->evaluations;
+  return SLM_OK;
+}
+
+slm_status slm_forest_export(slm_ctx* c, const slm_forest* f, int32_t tree,
+                             int32_t* kind, float* dir, float* zmin, float* inv_w,
+                             int32_t* bin, int32_t* leaf_class, double* leaf_value,
+                             int64_t* weight, double* loss, int64_t* n_left,
+                             int64_t* n_right) {
+  if (!c || !f || tree < 0 || tree >= f->n_trees)
+    return fail(c, SLM_EINVAL, "bad forest or tree index");
+  CK(cudaSetDevice(c->device));
+  const size_t o = (size_t)tree * f->H, H = f->H;
+  slm_status s;
+  if ((s = copy_out(c, kind, f->tr.kind + o, H))) return s;
+  if ((s = copy_out(c, dir, f->tr.dir + o * f->d, H * f->d))) return s;
+  if ((s = copy_out(c, zmin, f->tr.zmin + o, H))) return s;
+  if ((s = copy_out(c, inv_w, f->tr.inv_w + o, H))) return s;
+  if ((s = copy_out(c, bin, f->tr.bin + o, H))) return s;
+  if ((s = copy_out(c, leaf_class, f->tr.leaf_class + o, H))) return s;
+  if ((s = copy_out(c, leaf_value, f->tr.leaf_value + o, H))) return s;
+  if ((s = copy_out(c, weight, f->tr.weight + o, H))) return s;
+  if ((s = copy_out(c, loss, f->tr.loss + o, H))) return s;
+  if ((s = copy_out(c, n_left, f->tr.n_left + o, H))) return s;
+  if ((s = copy_out(c, n_right, f->tr.n_right + o, H))) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_predict(slm_ctx* c, const slm_forest* f, const float* X, int64_t n,
+                       int32_t d, int32_t* class_out, double* value_out,
+                       int32_t* leaf_out) {
+  if (!c || !f || !X || n < 0 || d != f->d)
+    return fail(c, SLM_EINVAL, "bad arguments to slm_predict");
+  if (n == 0) return SLM_OK;
+  CK(cudaSetDevice(c->device));
+  const float* dX;
+  slm_status s;
+  if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return s;
+  // outputs: device pointers directly, host pointers through staging
+  int32_t* dc = class_out;
+  double* dv = value_out;
+  int32_t* dl = leaf_out;
+  const bool hc = class_out && !is_device_ptr(class_out);
+  const bool hv = value_out && !is_device_ptr(value_out);
+  const bool hl = leaf_out && !is_device_ptr(leaf_out);
+  size_t off_v = ((hc ? 4 * (size_t)n : 0) + 15) & ~size_t(15);
+  size_t off_l = (off_v + (hv ? 8 * (size_t)n : 0) + 15) & ~size_t(15);
+  size_t total = off_l + (hl ? 4 * (size_t)n * f->n_trees : 0);
+  CK(ensure(c->ws[S_OUT], total));
+  unsigned char* base = static_cast<unsigned char*>(c->ws[S_OUT].p);
+  if (hc) dc = reinterpret_cast<int32_t*>(base);
+  if (hv) dv = reinterpret_cast<double*>(base + off_v);
+  if (hl) dl = reinterpret_cast<int32_t*>(base + off_l);
+  CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+    return launch_predict(dX, n, d, f->tr, f->n_trees, f->H, f->params.n_bins, f->K,
+                          f->params.criterion, dc, dv, dl, c->stream);
+  }));
+  if (hc) CK(cudaMemcpyAsync(class_out, dc, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+  if (hv) CK(cudaMemcpyAsync(value_out, dv, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+  if (hl)
+    CK(cudaMemcpyAsync(leaf_out, dl, 4 * (size_t)n * f->n_trees, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_profile(slm_ctx* c, int on) {
+  if (!c) return SLM_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(collect_profile(c));
+  c->prof = on != 0;
+  for (int k = 0; k < SLM_K_COUNT; ++k) {
+    c->k_launches[k] = 0;
+    c->k_ms[k] = 0.0;
+    c->k_pairs[k] = 0.0;
+  }
+  return SLM_OK;
+}
+
+slm_status slm_kernel_stats(slm_ctx* c, int32_t kernel, int64_t* launches,
+                            double* total_ms, double* pairs) {
+  if (!c || kernel < 0 || kernel >= SLM_K_COUNT) return fail(c, SLM_EINVAL, "bad kernel id");
+  CK(cudaSetDevice(c->device));
+  CK(collect_profile(c));
+  if (launches) *launches = c->k_launches[kernel];
+  if (total_ms) *total_ms = c->k_ms[kernel];
+  if (pairs) *pairs = c->k_pairs[kernel];
+  return SLM_OK;
+}
+
+slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
+  if (!c || !launches) return SLM_EINVAL;
+  *launches = c->launches;
+  return SLM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// Internal declarations of libslm: shared layouts and kernel launchers.
+// Nothing here is part of the public C ABI (include/slm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "slm.h"
+
+namespace slm {
+
+// ---- compile-time tiling ----------------------------------------------------
+constexpr int kThreads = 256;   // threads per CTA for the evaluation kernels
+constexpr int kPG = 16;         // particles per CTA ("particle group")
+constexpr int kTS = 256;        // samples per tile: 8 warps x 32 samples
+constexpr int kKC = 32;         // features per smem chunk of the projection
+constexpr int kXS = kKC + 4;    // padded smem row stride (floats): rows r and
+                                // r+1 start 4 banks apart -> conflict-free
+constexpr int kMaxBins = 256;
+constexpr int kMaxClasses = 32;
+constexpr int kMaxHistBytesPerParticle = 10240;  // B*K*4 (classification)
+constexpr int kMaxParticles = 256;
+constexpr int kMaxD = 1024;
+constexpr int kSmallMax = 2048;  // nodes up to this many entries: fused path
+constexpr int kChunk = 1024;     // entries per work item of larger nodes
+
+// Philox stream purposes (high byte of counter word 3).
+enum Purpose : uint32_t {
+  kInitX = 1,
+  kInitV = 2,
+  kR1 = 3,
+  kR2 = 4,
+  kBootstrap = 5
+};
+
+// Score of one projection on one node. Same meaning as slm_eval.
+struct EvalRes {
+  double loss;
+  uint64_t num, den;
+  float zmin, inv_w;
+  int32_t bin, valid;
+  int64_t nl, nr;
+};
+static_assert(sizeof(EvalRes) == sizeof(slm_eval), "layout");
+
+// One node searched in a batch.
+struct NodeDesc {
+  int32_t seg_start;  // first entry in the level's idx / w arrays
+  int32_t seg_len;    // number of entries (distinct samples)
+  uint32_t uid;       // Philox node uid
+  int32_t slot;       // tree * H + heap index, or -1
+};
+
+// Work item of a node too large for one CTA.
+struct ChunkItem {
+  int32_t node;   // index into the batch's NodeDesc array
+  int32_t start;  // entry offset within the node's segment
+  int32_t len;    // entries
+  int32_t first;  // 1 if first item of its node
+};
+
+struct BigNode {
+  int32_t node;
+  int32_t item0;   // first ChunkItem
+  int32_t n_items;
+  int32_t pad;
+};
+
+// Problem data shared by all nodes of a batch (passed by value).
+struct Problem {
+  const float* X;         // [n, d]
+  const int32_t* labels;  // [n] or null
+  const float* y;         // [n] or null
+  const int32_t* idx;     // [entries] level sample indices
+  const uint32_t* w;      // [entries] multiplicities or null
+  int32_t d;
+  int32_t crit;           // slm_criterion
+  int32_t K;              // classes (1 for MSE)
+  int32_t B;
+  int32_t min_leaf;
+  int32_t P;              // particles
+  int32_t Pp;             // padded to a multiple of kPG
+  int32_t G;              // Pp / kPG
+};
+
+// Device swarm state of A nodes.
+struct Swarm {
+  float* pos;     // [A, Pp, d]
+  float* vel;     // [A, Pp, d]
+  float* pbest;   // [A, Pp, d]
+  float* gbest;   // [A, d]
+  EvalRes* cur;   // [A, Pp]   scores of the current positions
+  EvalRes* pb;    // [A, Pp]   pbest scores
+  EvalRes* gb;    // [A]       gbest score
+  int32_t* gpart; // [A]
+  int32_t* giter; // [A]
+  double* trace;  // [A, T+1] or null
+  int32_t* zmm;   // [A, Pp, 2] ordered-int min/max (large nodes)
+  uint32_t* part; // partial histograms of large nodes
+  double* part_s; // MSE partial sums
+  double* part_q; // MSE partial sums of squares
+  int32_t T;
+};
+
+struct SwarmCoef {
+  float inertia, c1, c2;
+  uint64_t seed;
+};
+
+// ---- launchers (eval_kernels.cu) -------------------------------------------
+size_t eval_smem_bytes(const Problem& pr);
+cudaError_t prepare_eval_kernels(const Problem& pr);
+cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
+                              const NodeDesc* nodes, int A, SwarmCoef co,
+                              cudaStream_t st);
+cudaError_t launch_eval_small(const Problem& pr, const Swarm& sw,
+                              const NodeDesc* nodes, const int32_t* list,
+                              int n_list, cudaStream_t st);
+cudaError_t launch_minmax_chunk(const Problem& pr, const Swarm& sw,
+                                const NodeDesc* nodes, const ChunkItem* items,
+                                int n_items, cudaStream_t st);
+cudaError_t launch_hist_chunk(const Problem& pr, const Swarm& sw,
+                              const NodeDesc* nodes, const ChunkItem* items,
+                              int n_items, cudaStream_t st);
+cudaError_t launch_reduce_scan(const Problem& pr, const Swarm& sw,
+                               const BigNode* big, int n_big, cudaStream_t st);
+cudaError_t launch_swarm_update(const Problem& pr, const Swarm& sw,
+                                const NodeDesc* nodes, int A, int t,
+                                SwarmCoef co, cudaStream_t st);
+// Scores explicit positions (slm_evaluate_swarm): pos [Pp, d] of one node.
+cudaError_t launch_eval_positions(const Problem& pr, const Swarm& sw,
+                                  const NodeDesc* node, const ChunkItem* items,
+                                  int n_items, const BigNode* big,
+                                  int32_t* bins_out, int64_t n_idx,
+                                  cudaStream_t st);
+cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
+                                  int P, int d, uint32_t purpose, float* u,
+                                  cudaStream_t st);
+cudaError_t launch_bootstrap(uint64_t seed, uint32_t tree, int64_t n,
+                             uint32_t* w, cudaStream_t st);
+
+}  // namespace slm
+
+namespace slm {
+
+// ---- tree-level kernels (tree_kernels.cu) ---------------------------------
+
+// One node of the level being grown.
+struct LevelNode {
+  int32_t seg_start, seg_len;
+  int32_t slot;   // tree * H + heap index
+  int32_t depth;
+};
+
+struct TreeArrays {
+  int32_t* kind;      // [T*H]
+  float* dir;         // [T*H*d]
+  float* zmin;        // [T*H]
+  float* inv_w;
+  int32_t* bin;
+  int32_t* leaf_class;
+  double* leaf_value;
+  int64_t* weight;
+  double* loss;
+  int64_t* n_left;
+  int64_t* n_right;
+};
+
+// Per-level node statistics: writes the leaf fields of every level node and
+// splittable[L]; cls[L*K] class counts, par[L*2] (sum w y, sum w y^2).
+cudaError_t launch_node_stats(const Problem& pr, const LevelNode* nodes, int L,
+                              TreeArrays tr, int max_depth, uint32_t* cls,
+                              double* par, int32_t* splittable,
+                              cudaStream_t st);
+// For every searched node: side of each entry under gB, the zero-gain test,
+// and the internal-node fields of split nodes. map[A] = level node of search
+// node a. out3[A*3] = {split?, left entries, right entries}.
+cudaError_t launch_partition(const Problem& pr, const Swarm& sw,
+                             const NodeDesc* snodes, const int32_t* map, int A,
+                             const uint32_t* cls, const double* par,
+                             TreeArrays tr, uint8_t* side, int32_t* out3,
+                             int32_t* status, cudaStream_t st);
+// Stable compaction of split nodes' entries into the next level's arrays.
+// dst[A*2] = start of the left / right child segments (-1: not split).
+cudaError_t launch_compact(const Problem& pr, const NodeDesc* snodes, int A,
+                           const uint8_t* side, const int32_t* dst,
+                           int32_t* idx_next, uint32_t* w_next,
+                           cudaStream_t st);
+// Root entries of bootstrap trees: for tree t, the samples with w > 0 in
+// increasing order and their multiplicities, at offsets off[t]; counts[t].
+cudaError_t launch_compact_nonzero(const uint32_t* w_all, int n_trees,
+                                   int64_t n, int32_t* idx_out,
+                                   uint32_t* w_out, const int64_t* off,
+                                   int32_t* counts, cudaStream_t st);
+cudaError_t launch_iota(int32_t* idx, int64_t n, int copies,
+                        cudaStream_t st);
+// Checks labels in [0, K) and sample indices in [0, n); sets *status = 1 on
+// the first violation.
+cudaError_t launch_validate(const int32_t* labels, int64_t n, int K,
+                            const int32_t* idx, int64_t n_idx,
+                            int32_t* status, cudaStream_t st);
+cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr,
+                           int n_trees, int H, int B, int K, int crit,
+                           int32_t* class_out, double* value_out,
+                           int32_t* leaf_out, cudaStream_t st);
+
+}  // namespace slm
