@@ -209,17 +209,16 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
 /* ---- diagnostics --------------------------------------------------------
  * Kernels of this library, for per-kernel timing. */
 typedef enum {
-  SLM_K_EVAL_SMALL = 0,   /* fused scoring of nodes held by one CTA */
-  SLM_K_MINMAX_CHUNK = 1, /* range pass of large nodes */
-  SLM_K_HIST_CHUNK = 2,   /* histogram pass of large nodes */
-  SLM_K_REDUCE_SCAN = 3,  /* partial-histogram reduction and scan */
-  SLM_K_SWARM_UPDATE = 4, /* pbest / gbest and Eq. pso-1 */
-  SLM_K_SWARM_INIT = 5,
-  SLM_K_NODE_STATS = 6,
-  SLM_K_PARTITION = 7,
-  SLM_K_COMPACT = 8,
-  SLM_K_OTHER = 9,        /* validation, bootstrap, index setup */
-  SLM_K_COUNT = 10
+  SLM_K_PROJECT = 0,      /* z = X_node . x_p for every particle (FP32 FFMA) */
+  SLM_K_HIST_SCAN = 1,    /* binning, histograms and threshold scan */
+  SLM_K_SWARM_UPDATE = 2, /* pbest / gbest and Eq. pso-1 */
+  SLM_K_SWARM_INIT = 3,
+  SLM_K_NODE_STATS = 4,
+  SLM_K_PARTITION = 5,
+  SLM_K_COMPACT = 6,
+  SLM_K_GATHER = 7,       /* rows of a node / root into entry order */
+  SLM_K_OTHER = 8,        /* validation, bootstrap, index setup, prediction */
+  SLM_K_COUNT = 9
 } slm_kernel;
 
 /* on != 0 brackets every later launch of the context with CUDA events on its

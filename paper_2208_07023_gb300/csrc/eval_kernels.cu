@@ -9,17 +9,21 @@
 // Swarm update (Sec. III-A, Eq. pso-1; Algorithm 1):
 //   v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);   x <- x + v
 //
-// Tiling. A CTA scores kPG = 16 particles of one node. Samples are staged in
-// tiles of kTS = 256 rows (gathered through the node's sample index) and the
-// features in chunks of kKC = 32, in shared memory with a padded row stride.
-// Each thread owns a 4 x 4 register tile (samples w*32 + sg + 8i, particles
-// pg + 4j) and accumulates over the features in increasing order, so every z
-// is the same sequence of fused multiply-adds whatever the tiling.
-// Nodes with <= kSmallMax entries are scored by one CTA per particle group
-// in one launch (two passes over the node: range, then histogram and scan).
-// Larger nodes are cut into kChunk-entry work items: a range kernel (global
-// ordered-int atomics), a histogram kernel writing dense per-item partial
-// histograms, and a per-particle reduce-and-scan kernel.
+// Data layout. A batch's rows are stored entry-ordered and contiguous (the
+// level-resident copy X_l[E, d]: each node is a segment of consecutive rows),
+// with entry-aligned labels / targets / multiplicities. One iteration is two
+// kernels plus the swarm update:
+//  * k_project: z[p][e] = X_l[e] . x_p for all entries and particles, once.
+//    A persistent grid walks (tile of kTS = 256 rows, group of kPG = 16
+//    particles) work units; rows and positions stream through shared memory
+//    in kKC = 32-feature chunks with double-buffered cp.async copies. Each
+//    thread owns a 4 x 4 register tile (rows w*32 + sg + 8i, particles
+//    pg + 4j) and accumulates over the features in increasing order, so every
+//    z is the same sequence of fused multiply-adds whatever the tiling. The
+//    per-(node, particle) range is folded in with ordered-int atomics and z is
+//    written to an L2-resident buffer.
+//  * k_hist_scan: one CTA per (node, particle) bins the node's z into
+//    warp-private shared histograms, merges them and scans the edges.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <limits.h>
@@ -109,216 +113,6 @@ __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
   return b < 0 ? 0 : b;
 }
 
-// ---- shared-memory layout of the scoring kernels ------------------------------
-
-struct Smem {
-  float* xs;       // [kTS][kXS]
-  float* as;       // [kPG][kXS]
-  int32_t* tidx;   // [kTS]  global sample index of each tile row
-  int32_t* tlab;   // [kTS]  label (classification)
-  float* ty;       // [kTS]  target (MSE)
-  uint32_t* tw;    // [kTS]  multiplicity
-  int* smin;       // [kPG]  ordered-int range
-  int* smax;       // [kPG]
-  float* zmin;     // [kPG]
-  float* inv_w;    // [kPG]
-  int* ok;         // [kPG]
-  uint32_t* hist;  // classification [kPG][B*K]; MSE counts [kPG][B]
-  double* hs;      // MSE [kPG][B]
-  double* hq;      // MSE [kPG][B]
-};
-
-__host__ __device__ inline size_t hist_bytes(int crit, int B, int K) {
-  return crit == SLM_MSE ? (size_t)kPG * B * (4 + 8 + 8)
-                         : (size_t)kPG * B * K * 4;
-}
-
-__host__ __device__ inline size_t fixed_bytes() {
-  return sizeof(float) * (kTS * kXS + kPG * kXS) + sizeof(int32_t) * kTS * 4 +
-         sizeof(int) * kPG * 5;
-}
-
-__device__ __forceinline__ Smem carve(unsigned char* base, int crit, int B,
-                                      int K) {
-  Smem s;
-  unsigned char* p = base;
-  if (crit == SLM_MSE) {  // doubles first for alignment
-    s.hs = (double*)p;
-    p += sizeof(double) * kPG * B;
-    s.hq = (double*)p;
-    p += sizeof(double) * kPG * B;
-    s.hist = (uint32_t*)p;
-    p += sizeof(uint32_t) * kPG * B;
-  } else {
-    s.hs = s.hq = nullptr;
-    s.hist = (uint32_t*)p;
-    p += sizeof(uint32_t) * kPG * B * K;
-  }
-  p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-  s.xs = (float*)p;
-  p += sizeof(float) * kTS * kXS;
-  s.as = (float*)p;
-  p += sizeof(float) * kPG * kXS;
-  s.tidx = (int32_t*)p;
-  p += sizeof(int32_t) * kTS;
-  s.tlab = (int32_t*)p;
-  s.ty = (float*)p;
-  p += sizeof(int32_t) * kTS;
-  s.tw = (uint32_t*)p;
-  p += sizeof(uint32_t) * kTS;
-  s.smin = (int*)p;
-  p += sizeof(int) * kPG;
-  s.smax = (int*)p;
-  p += sizeof(int) * kPG;
-  s.zmin = (float*)p;
-  p += sizeof(float) * kPG;
-  s.inv_w = (float*)p;
-  p += sizeof(float) * kPG;
-  s.ok = (int*)p;
-  return s;
-}
-
-// Loads tile rows [r0, r0 + n) of a node segment: sample index, label or
-// target, and multiplicity.
-__device__ __forceinline__ void load_tile_meta(const Problem& pr, const Smem& s,
-                                               int64_t e0, int n) {
-  for (int r = threadIdx.x; r < kTS; r += kThreads) {
-    if (r < n) {
-      const int64_t e = e0 + r;
-      const int32_t si = pr.idx[e];
-      s.tidx[r] = si;
-      if (pr.crit == SLM_MSE)
-        s.ty[r] = pr.y[si];
-      else
-        s.tlab[r] = pr.labels[si];
-      s.tw[r] = pr.w ? pr.w[e] : 1u;
-    } else {
-      s.tidx[r] = -1;
-      s.tw[r] = 0;
-      if (pr.crit == SLM_MSE)
-        s.ty[r] = 0.f;
-      else
-        s.tlab[r] = 0;
-    }
-  }
-}
-
-// z for the tile's rows x the group's 16 particles. Requires tile meta loaded
-// and a __syncthreads() since. pos: [kPG, d] positions of the group.
-__device__ __forceinline__ void project_tile(const Problem& pr, const Smem& s,
-                                             const float* __restrict__ pos,
-                                             int n, float acc[4][4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int sg = lane & 7, pg = lane >> 3;
-  const int d = pr.d;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-
-  for (int k0 = 0; k0 < d; k0 += kKC) {
-    const int kc = min(kKC, d - k0);
-    const int kc4 = (kc + 3) & ~3;
-    __syncthreads();  // previous chunk fully consumed
-    for (int e = threadIdx.x; e < kTS * kc4; e += kThreads) {
-      const int r = e / kc4, c = e - r * kc4;
-      float v = 0.0f;
-      if (r < n && c < kc) v = __ldg(pr.X + (int64_t)s.tidx[r] * d + k0 + c);
-      s.xs[r * kXS + c] = v;
-    }
-    for (int e = threadIdx.x; e < kPG * kc4; e += kThreads) {
-      const int p = e / kc4, c = e - p * kc4;
-      s.as[p * kXS + c] = c < kc ? pos[(int64_t)p * d + k0 + c] : 0.0f;
-    }
-    __syncthreads();
-    const float* xr = s.xs + (warp * 32 + sg) * kXS;
-    const float* ar = s.as + pg * kXS;
-    for (int c = 0; c < kc4; c += 4) {
-      float4 xv[4], av[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + c);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + c);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
-          acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
-          acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
-          acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
-        }
-    }
-  }
-}
-
-// Range of each particle over the tile's valid rows, folded into s.smin/smax.
-__device__ __forceinline__ void tile_minmax(const Smem& s, int n,
-                                            const float acc[4][4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int sg = lane & 7, pg = lane >> 3;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    float lo = FLT_MAX, hi = -FLT_MAX;
-    bool any = false;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = warp * 32 + sg + 8 * i;
-      if (r < n) {
-        const float z = acc[i][j];
-        lo = z < lo ? z : lo;
-        hi = z > hi ? z : hi;
-        any = true;
-      }
-    }
-    int olo = any ? f2ord(lo) : INT_MAX, ohi = any ? f2ord(hi) : INT_MIN;
-#pragma unroll
-    for (int off = 1; off < 8; off <<= 1) {
-      olo = min(olo, __shfl_xor_sync(0xffffffffu, olo, off));
-      ohi = max(ohi, __shfl_xor_sync(0xffffffffu, ohi, off));
-    }
-    if (sg == 0 && olo != INT_MAX) {
-      atomicMin(&s.smin[pg + 4 * j], olo);
-      atomicMax(&s.smax[pg + 4 * j], ohi);
-    }
-  }
-}
-
-// Bins the tile's z and adds them to the shared histograms.
-__device__ __forceinline__ void tile_hist(const Problem& pr, const Smem& s,
-                                          int n, int p_base,
-                                          const float acc[4][4],
-                                          int32_t* bins_out, int64_t n_idx,
-                                          int64_t row0) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int sg = lane & 7, pg = lane >> 3;
-  const int B = pr.B, K = pr.K;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int pl = pg + 4 * j;
-    if (p_base + pl >= pr.P || !s.ok[pl]) continue;
-    const float zmin = s.zmin[pl], inv_w = s.inv_w[pl];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = warp * 32 + sg + 8 * i;
-      if (r >= n) continue;
-      const int b = bin_of(acc[i][j], zmin, inv_w, B);
-      const uint32_t w = s.tw[r];
-      if (pr.crit == SLM_MSE) {
-        const double wy = (double)w * (double)s.ty[r];
-        atomicAdd(&s.hist[pl * B + b], w);
-        atomicAdd(&s.hs[pl * B + b], wy);
-        atomicAdd(&s.hq[pl * B + b], wy * (double)s.ty[r]);
-      } else {
-        atomicAdd(&s.hist[(pl * B + b) * K + s.tlab[r]], w);
-      }
-      if (bins_out) bins_out[(int64_t)(p_base + pl) * n_idx + row0 + r] = b;
-    }
-  }
-}
-
 // ---- threshold scans (one warp, one particle) ----------------------------------
 
 constexpr int kMaxBPL = kMaxBins / 32;
@@ -339,6 +133,9 @@ __device__ EvalRes scan_cls(const uint32_t* h, int B, int K, int min_leaf,
     hL[i] = hR[i] = 0.0;
   }
   uint32_t ntot = 0;
+  uint32_t occ[kMaxBPL];  // samples in bin j0 + i (all classes)
+#pragma unroll
+  for (int i = 0; i < kMaxBPL; ++i) occ[i] = 0;
   for (int k = 0; k < K; ++k) {
     uint32_t c[kMaxBPL];
     uint32_t sum = 0;
@@ -361,6 +158,7 @@ __device__ EvalRes scan_cls(const uint32_t* h, int B, int K, int min_leaf,
     for (int i = 0; i < kMaxBPL; ++i) {
       if (i >= BPL) break;
       run += c[i];
+      occ[i] += c[i];
       const uint32_t rr = tot - run;
       nL[i] += run;
       if (crit == SLM_GINI) {
@@ -378,6 +176,7 @@ __device__ EvalRes scan_cls(const uint32_t* h, int B, int K, int min_leaf,
     if (i >= BPL) break;
     const int b = j0 + i + 1;
     if (b > B - 1) break;
+    if (occ[i] == 0) continue;  // same partition as edge b-1
     const uint32_t nl = nL[i], nr = ntot - nl;
     if (nl < (uint32_t)min_leaf || nr < (uint32_t)min_leaf) continue;
     EvalRes c = invalid_res();
@@ -460,6 +259,8 @@ __device__ EvalRes scan_mse(const uint32_t* cnt, const double* s,
     rq += qv[i];
     const int b = j0 + i + 1;
     if (b > B - 1) break;
+    // an empty bin b-1 gives edge b the partition of edge b-1: keep the lower
+    if (c[i] == 0) continue;
     const uint32_t nl = rc, nr = ntot - rc;
     if (nl < (uint32_t)min_leaf || nr < (uint32_t)min_leaf) continue;
     const double sr = stot - rs, qr = qtot - rq;
@@ -481,221 +282,194 @@ __device__ EvalRes scan_mse(const uint32_t* cnt, const double* s,
   return best;
 }
 
-__device__ __forceinline__ void zero_hist(const Problem& pr, const Smem& s) {
-  const int words = pr.crit == SLM_MSE ? kPG * pr.B : kPG * pr.B * pr.K;
-  for (int i = threadIdx.x; i < words; i += kThreads) s.hist[i] = 0u;
-  if (pr.crit == SLM_MSE)
-    for (int i = threadIdx.x; i < kPG * pr.B; i += kThreads) {
-      s.hs[i] = 0.0;
-      s.hq[i] = 0.0;
+// ---- async copies -------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// ---- projection -------------------------------------------------------------------
+
+constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPG * kXS);
+
+// Stages one kKC-feature chunk of a work unit's rows and positions.
+__device__ __forceinline__ void stage_chunk(const Problem& pr, const Swarm& sw,
+                                            const WorkTile& wt, int g, int k0,
+                                            bool vec, float* xb, float* ab) {
+  const int d = pr.d;
+  const int kc = min(kKC, d - k0);
+  const float* pos = sw.pos + ((int64_t)wt.node * pr.Pp + g * kPG) * d;
+  if (vec) {
+    for (int q = threadIdx.x; q < kTS * (kKC / 4); q += kThreads) {
+      const int r = q >> 3, cc = (q & 7) * 4;
+      const bool ok = r < wt.rows && cc < kc;
+      const float* src = ok ? pr.X + (int64_t)(wt.row0 + r) * d + k0 + cc : pr.X;
+      cp_async16(xb + r * kXS + cc, src, ok ? 16 : 0);
     }
-}
-
-// Sets zmin / inv_w / ok of each particle from s.smin / s.smax.
-__device__ __forceinline__ void finish_range(const Problem& pr, const Smem& s) {
-  for (int p = threadIdx.x; p < kPG; p += kThreads) {
-    if (s.smin[p] == INT_MAX) {  // empty node
-      s.ok[p] = 0;
-      s.zmin[p] = 0.f;
-      s.inv_w[p] = 0.f;
-      continue;
-    }
-    const float lo = ord2f(s.smin[p]), hi = ord2f(s.smax[p]);
-    const float width = __fsub_rn(hi, lo);
-    const float inv_w = __fdiv_rn((float)pr.B, width);
-    s.zmin[p] = lo;
-    s.inv_w[p] = inv_w;
-    s.ok[p] = (hi > lo) && isfinite(inv_w);
-  }
-}
-
-// Scans the group's particles (warp w takes particles w, w+8) and writes
-// their scores.
-__device__ __forceinline__ void scan_group(const Problem& pr, const Smem& s,
-                                           EvalRes* out, int p_base) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int pl = warp; pl < kPG; pl += kThreads / 32) {
-    if (p_base + pl >= pr.P) continue;
-    EvalRes r;
-    if (!s.ok[pl]) {
-      r = invalid_res();
-    } else if (pr.crit == SLM_MSE) {
-      r = scan_mse(s.hist + pl * pr.B, s.hs + pl * pr.B, s.hq + pl * pr.B,
-                   pr.B, pr.min_leaf);
-    } else {
-      r = scan_cls(s.hist + (size_t)pl * pr.B * pr.K, pr.B, pr.K, pr.min_leaf,
-                   pr.crit);
-    }
-    r.zmin = s.zmin[pl];
-    r.inv_w = s.ok[pl] ? s.inv_w[pl] : 0.f;
-    if (lane == 0) out[p_base + pl] = r;
-  }
-}
-
-// ---- kernels ---------------------------------------------------------------------
-
-// One CTA = one node with <= kSmallMax entries x one particle group.
-__global__ void __launch_bounds__(kThreads)
-    k_eval_small(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
-                 const int32_t* __restrict__ list, int32_t* bins_out,
-                 int64_t n_idx) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Smem s = carve(smem, pr.crit, pr.B, pr.K);
-  const int a = list ? list[blockIdx.x] : blockIdx.x;
-  const int g = blockIdx.y;
-  const NodeDesc nd = nodes[a];
-  const int p_base = g * kPG;
-  const float* pos = sw.pos + ((int64_t)a * pr.Pp + p_base) * pr.d;
-
-  for (int p = threadIdx.x; p < kPG; p += kThreads) {
-    s.smin[p] = INT_MAX;
-    s.smax[p] = INT_MIN;
-  }
-  float acc[4][4];
-  for (int t0 = 0; t0 < nd.seg_len; t0 += kTS) {
-    const int n = min(kTS, nd.seg_len - t0);
-    __syncthreads();
-    load_tile_meta(pr, s, (int64_t)nd.seg_start + t0, n);
-    project_tile(pr, s, pos, n, acc);
-    tile_minmax(s, n, acc);
-  }
-  __syncthreads();
-  finish_range(pr, s);
-  zero_hist(pr, s);
-  __syncthreads();
-  for (int t0 = 0; t0 < nd.seg_len; t0 += kTS) {
-    const int n = min(kTS, nd.seg_len - t0);
-    __syncthreads();
-    load_tile_meta(pr, s, (int64_t)nd.seg_start + t0, n);
-    project_tile(pr, s, pos, n, acc);
-    tile_hist(pr, s, n, p_base, acc, bins_out, n_idx, t0);
-  }
-  __syncthreads();
-  scan_group(pr, s, sw.cur + (int64_t)a * pr.Pp, p_base);
-}
-
-// Range pass of one work item of a large node.
-__global__ void __launch_bounds__(kThreads)
-    k_minmax_chunk(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
-                   const ChunkItem* __restrict__ items) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Smem s = carve(smem, pr.crit, pr.B, pr.K);
-  const ChunkItem it = items[blockIdx.x];
-  const int g = blockIdx.y;
-  const NodeDesc nd = nodes[it.node];
-  const int p_base = g * kPG;
-  const float* pos = sw.pos + ((int64_t)it.node * pr.Pp + p_base) * pr.d;
-  for (int p = threadIdx.x; p < kPG; p += kThreads) {
-    s.smin[p] = INT_MAX;
-    s.smax[p] = INT_MIN;
-  }
-  float acc[4][4];
-  for (int t0 = 0; t0 < it.len; t0 += kTS) {
-    const int n = min(kTS, it.len - t0);
-    __syncthreads();
-    load_tile_meta(pr, s, (int64_t)nd.seg_start + it.start + t0, n);
-    project_tile(pr, s, pos, n, acc);
-    tile_minmax(s, n, acc);
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < kPG; p += kThreads) {
-    if (s.smin[p] == INT_MAX) continue;
-    int* z = sw.zmm + ((int64_t)it.node * pr.Pp + p_base + p) * 2;
-    atomicMin(z, s.smin[p]);
-    atomicMax(z + 1, s.smax[p]);
-  }
-}
-
-// Histogram pass of one work item: dense partial histogram to global.
-__global__ void __launch_bounds__(kThreads)
-    k_hist_chunk(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
-                 const ChunkItem* __restrict__ items, int32_t* bins_out,
-                 int64_t n_idx) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Smem s = carve(smem, pr.crit, pr.B, pr.K);
-  const ChunkItem it = items[blockIdx.x];
-  const int g = blockIdx.y;
-  const NodeDesc nd = nodes[it.node];
-  const int p_base = g * kPG;
-  const float* pos = sw.pos + ((int64_t)it.node * pr.Pp + p_base) * pr.d;
-  for (int p = threadIdx.x; p < kPG; p += kThreads) {
-    const int* z = sw.zmm + ((int64_t)it.node * pr.Pp + p_base + p) * 2;
-    s.smin[p] = z[0];
-    s.smax[p] = z[1];
-  }
-  __syncthreads();
-  finish_range(pr, s);
-  zero_hist(pr, s);
-  float acc[4][4];
-  for (int t0 = 0; t0 < it.len; t0 += kTS) {
-    const int n = min(kTS, it.len - t0);
-    __syncthreads();
-    load_tile_meta(pr, s, (int64_t)nd.seg_start + it.start + t0, n);
-    project_tile(pr, s, pos, n, acc);
-    tile_hist(pr, s, n, p_base, acc, bins_out, n_idx, it.start + t0);
-  }
-  __syncthreads();
-  // dense copy-out: partial of (item, particle) at ((item*Pp + p) * words)
-  const int64_t item = blockIdx.x;
-  if (pr.crit == SLM_MSE) {
-    const int words = kPG * pr.B;
-    const int64_t off = (item * pr.Pp + p_base) * pr.B;
-    for (int i = threadIdx.x; i < words; i += kThreads) {
-      sw.part[off + i] = s.hist[i];
-      sw.part_s[off + i] = s.hs[i];
-      sw.part_q[off + i] = s.hq[i];
+    for (int q = threadIdx.x; q < kPG * (kKC / 4); q += kThreads) {
+      const int p = q >> 3, cc = (q & 7) * 4;
+      const bool ok = cc < kc;
+      cp_async16(ab + p * kXS + cc, ok ? pos + (int64_t)p * d + k0 + cc : pos, ok ? 16 : 0);
     }
   } else {
-    const int words = kPG * pr.B * pr.K;
-    const int64_t off = (item * pr.Pp + p_base) * (int64_t)pr.B * pr.K;
-    const uint4* src = reinterpret_cast<const uint4*>(s.hist);
-    uint4* dst = reinterpret_cast<uint4*>(sw.part + off);
-    if ((words & 3) == 0 && (off & 3) == 0) {
-      for (int i = threadIdx.x; i < words / 4; i += kThreads) dst[i] = src[i];
-    } else {
-      for (int i = threadIdx.x; i < words; i += kThreads)
-        sw.part[off + i] = s.hist[i];
+    for (int q = threadIdx.x; q < kTS * kKC; q += kThreads) {
+      const int r = q >> 5, cc = q & 31;
+      const bool ok = r < wt.rows && cc < kc;
+      const float* src = ok ? pr.X + (int64_t)(wt.row0 + r) * d + k0 + cc : pr.X;
+      cp_async4(xb + r * kXS + cc, src, ok ? 4 : 0);
     }
+    for (int q = threadIdx.x; q < kPG * kKC; q += kThreads) {
+      const int p = q >> 5, cc = q & 31;
+      const bool ok = cc < kc;
+      cp_async4(ab + p * kXS + cc, ok ? pos + (int64_t)p * d + k0 + cc : pos, ok ? 4 : 0);
+    }
+  }
+  cp_async_commit();
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_project(Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, int n_units) {
+  extern __shared__ __align__(16) float smf[];
+  float* xs0 = smf;
+  float* xs1 = smf + kTS * kXS;
+  float* as0 = smf + 2 * kTS * kXS;
+  float* as1 = as0 + kPG * kXS;
+  if ((int)blockIdx.x >= n_units) return;
+  const int d = pr.d, G = pr.G;
+  const int nk = (d + kKC - 1) / kKC;
+  const bool vec = (d & 3) == 0;
+  const int my_units = (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+  const int n_st = my_units * nk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sg = lane & 7, pg = lane >> 3;
+
+  {
+    const int u = blockIdx.x;
+    stage_chunk(pr, sw, tiles[u / G], u % G, 0, vec, xs0, as0);
+  }
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+
+  for (int s = 0; s < n_st; ++s) {
+    const int ui = s / nk, c = s - ui * nk;
+    const int u = blockIdx.x + ui * gridDim.x;
+    if (s + 1 < n_st) {
+      const int ui1 = (s + 1) / nk, c1 = (s + 1) - ui1 * nk;
+      const int u1 = blockIdx.x + ui1 * gridDim.x;
+      stage_chunk(pr, sw, tiles[u1 / G], u1 % G, c1 * kKC, vec, (s & 1) ? xs0 : xs1,
+                  (s & 1) ? as0 : as1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* xb = (s & 1) ? xs1 : xs0;
+    const float* ab = (s & 1) ? as1 : as0;
+    const int kc4 = (min(kKC, d - c * kKC) + 3) & ~3;
+    const float* xr = xb + (warp * 32 + sg) * kXS;
+    const float* ar = ab + pg * kXS;
+#pragma unroll 2
+    for (int k = 0; k < kc4; k += 4) {
+      float4 xv[4], av[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
+          acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
+          acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
+          acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
+        }
+    }
+    if (c == nk - 1) {
+      // tile complete: fold the range, store z
+      const WorkTile wt = tiles[u / G];
+      const int g = u % G;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = g * kPG + pg + 4 * j;
+        float lo = FLT_MAX, hi = -FLT_MAX;
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = warp * 32 + sg + 8 * i;
+          if (r < wt.rows) {
+            const float z = acc[i][j];
+            lo = z < lo ? z : lo;
+            hi = z > hi ? z : hi;
+            any = true;
+            if (p < pr.P) sw.z[(int64_t)p * pr.E + wt.row0 + r] = z;
+          }
+        }
+        int olo = any ? f2ord(lo) : INT_MAX, ohi = any ? f2ord(hi) : INT_MIN;
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+          olo = min(olo, __shfl_xor_sync(0xffffffffu, olo, off));
+          ohi = max(ohi, __shfl_xor_sync(0xffffffffu, ohi, off));
+        }
+        if (sg == 0 && olo != INT_MAX && p < pr.P) {
+          int* zz = sw.zmm + ((int64_t)wt.node * pr.Pp + p) * 2;
+          atomicMin(zz, olo);
+          atomicMax(zz + 1, ohi);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    }
+    __syncthreads();  // buffer s&1 is refilled by the next stage's copies
   }
 }
 
-// One CTA per (large node, particle): sums the item partials and scans.
+// ---- histogram and scan -------------------------------------------------------------
+
+__host__ __device__ inline size_t hist_copy_bytes(int crit, int B, int K) {
+  return crit == SLM_MSE ? (size_t)B * (4 + 8 + 8) : (size_t)B * K * 4;
+}
+
+// One CTA per (node, particle): bins the node's z, histograms it in `copies`
+// warp-private shared histograms, merges them and scans the edges.
 __global__ void __launch_bounds__(kThreads)
-    k_reduce_scan(Problem pr, Swarm sw, const BigNode* __restrict__ big) {
+    k_hist_scan(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int copies,
+                int32_t* bins_out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const BigNode bn = big[blockIdx.x];
-  const int p = blockIdx.y;
-  if (p >= pr.P) return;
-  const int a = bn.node;
-  const int B = pr.B;
-  const int words = pr.crit == SLM_MSE ? B : B * pr.K;
-  uint32_t* h = reinterpret_cast<uint32_t*>(smem);
-  double* hs = reinterpret_cast<double*>(smem + ((words * 4 + 15) & ~15));
-  double* hq = hs + B;
-  for (int i = threadIdx.x; i < words; i += kThreads) {
-    uint32_t acc = 0;
-    double as = 0.0, aq = 0.0;
-    for (int it = 0; it < bn.n_items; ++it) {
-      const int64_t off = ((int64_t)(bn.item0 + it) * pr.Pp + p) * words + i;
-      acc += sw.part[off];
-      if (pr.crit == SLM_MSE) {
-        as += sw.part_s[off];
-        aq += sw.part_q[off];
-      }
-    }
-    h[i] = acc;
-    if (pr.crit == SLM_MSE) {
-      hs[i] = as;
-      hq[i] = aq;
-    }
-  }
+  const int a = blockIdx.x, p = blockIdx.y;
+  const NodeDesc nd = nodes[a];
+  const int B = pr.B, K = pr.K;
+  const bool mse = pr.crit == SLM_MSE;
+  const int words = mse ? B : B * K;  // u32 counters per copy
+  double* hs = reinterpret_cast<double*>(smem);       // MSE [copies][B]
+  double* hq = hs + (mse ? copies * B : 0);            // MSE [copies][B]
+  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? copies * B : 0));
   __shared__ float s_zmin, s_inv_w;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    int* z = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
-    const int lo_o = z[0], hi_o = z[1];
-    z[0] = INT_MAX;  // reset for the next iteration
-    z[1] = INT_MIN;
+    int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
+    const int lo_o = zz[0], hi_o = zz[1];
+    zz[0] = INT_MAX;  // ready for the next iteration
+    zz[1] = INT_MIN;
     if (lo_o == INT_MAX) {
       s_ok = 0;
       s_zmin = 0.f;
@@ -708,18 +482,67 @@ __global__ void __launch_bounds__(kThreads)
       s_ok = (hi > lo) && isfinite(inv_w);
     }
   }
+  for (int i = threadIdx.x; i < copies * words; i += kThreads) hc[i] = 0u;
+  if (mse)
+    for (int i = threadIdx.x; i < copies * B; i += kThreads) {
+      hs[i] = 0.0;
+      hq[i] = 0.0;
+    }
   __syncthreads();
+  const bool ok = s_ok;
+  const float zmin = s_zmin, inv_w = s_inv_w;
+  if (ok) {
+    const int cp = (threadIdx.x >> 5) % copies;
+    uint32_t* h = hc + cp * words;
+    const float* zrow = sw.z + (int64_t)p * pr.E + nd.seg_start;
+    for (int r = threadIdx.x; r < nd.seg_len; r += kThreads) {
+      const int64_t e = (int64_t)nd.seg_start + r;
+      const int b = bin_of(zrow[r], zmin, inv_w, B);
+      const uint32_t w = pr.w ? pr.w[e] : 1u;
+      if (mse) {
+        const float yv = pr.y[e];
+        const double wy = (double)w * (double)yv;
+        atomicAdd(&h[b], w);
+        atomicAdd(&hs[cp * B + b], wy);
+        atomicAdd(&hq[cp * B + b], wy * (double)yv);
+      } else {
+        atomicAdd(&h[b * K + pr.lab[e]], w);
+      }
+      if (bins_out) bins_out[(int64_t)p * nd.seg_len + r] = b;
+    }
+  }
+  __syncthreads();
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      EvalRes res = invalid_res();
+      sw.cur[(int64_t)a * pr.Pp + p] = res;
+    }
+    return;
+  }
+  if (copies > 1) {
+    for (int i = threadIdx.x; i < words; i += kThreads) {
+      uint32_t v = hc[i];
+      for (int cp = 1; cp < copies; ++cp) v += hc[cp * words + i];
+      hc[i] = v;
+    }
+    if (mse)
+      for (int i = threadIdx.x; i < B; i += kThreads) {
+        double vs = hs[i], vq = hq[i];
+        for (int cp = 1; cp < copies; ++cp) {
+          vs += hs[cp * B + i];
+          vq += hq[cp * B + i];
+        }
+        hs[i] = vs;
+        hq[i] = vq;
+      }
+    __syncthreads();
+  }
   if (threadIdx.x >= 32) return;
-  EvalRes r;
-  if (!s_ok)
-    r = invalid_res();
-  else if (pr.crit == SLM_MSE)
-    r = scan_mse(h, hs, hq, B, pr.min_leaf);
-  else
-    r = scan_cls(h, B, pr.K, pr.min_leaf, pr.crit);
-  r.zmin = s_zmin;
-  r.inv_w = s_ok ? s_inv_w : 0.f;
-  if (threadIdx.x == 0) sw.cur[(int64_t)a * pr.Pp + p] = r;
+  EvalRes res = mse ? scan_mse(hc, hs, hq, B, pr.min_leaf)
+                    : scan_cls(hc, B, K, pr.min_leaf, pr.crit);
+  res.zmin = zmin;
+  res.inv_w = inv_w;
+  if (threadIdx.x == 0) sw.cur[(int64_t)a * pr.Pp + p] = res;
 }
 
 // Initial swarm of each node: x ~ U[-1,1)^d, v ~ 0.1 U[-1,1)^d.
@@ -923,33 +746,23 @@ __global__ void k_bootstrap(uint64_t seed, uint32_t tree, int64_t n,
 
 // ---- launchers ---------------------------------------------------------------------
 
-size_t eval_smem_bytes(const Problem& pr) {
-  return hist_bytes(pr.crit, pr.B, pr.K) + 16 + fixed_bytes();
+int hist_copies(const Problem& pr) {
+  const size_t per = hist_copy_bytes(pr.crit, pr.B, pr.K);
+  int c = (int)((48 * 1024) / per);
+  return c < 1 ? 1 : (c > 8 ? 8 : c);
 }
 
-static size_t reduce_smem_bytes(const Problem& pr) {
-  const int words = pr.crit == SLM_MSE ? pr.B : pr.B * pr.K;
-  return ((words * 4 + 15) & ~15) + (pr.crit == SLM_MSE ? 16 * pr.B : 0);
+static size_t hist_smem_bytes(const Problem& pr) {
+  return hist_copy_bytes(pr.crit, pr.B, pr.K) * hist_copies(pr);
 }
 
 cudaError_t prepare_eval_kernels(const Problem& pr) {
-  const int bytes = (int)eval_smem_bytes(pr);
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_eval_small,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_minmax_chunk,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_hist_chunk,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes)))
-    return e;
-  return cudaFuncSetAttribute(k_reduce_scan,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)reduce_smem_bytes(pr));
+  cudaError_t e = cudaFuncSetAttribute(k_project,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kProjSmem);
+  if (e) return e;
+  return cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)hist_smem_bytes(pr));
 }
 
 cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
@@ -960,58 +773,20 @@ cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
   return cudaGetLastError();
 }
 
-cudaError_t launch_eval_small(const Problem& pr, const Swarm& sw,
-                              const NodeDesc* nodes, const int32_t* list,
-                              int n_list, cudaStream_t st) {
-  if (n_list <= 0) return cudaSuccess;
-  dim3 grid(n_list, pr.G);
-  k_eval_small<<<grid, kThreads, eval_smem_bytes(pr), st>>>(pr, sw, nodes, list,
-                                                            nullptr, 0);
+cudaError_t launch_project(const Problem& pr, const Swarm& sw, const WorkTile* tiles,
+                           int n_tiles, int grid_cap, cudaStream_t st) {
+  const int n_units = n_tiles * pr.G;
+  if (n_units <= 0) return cudaSuccess;
+  const int grid = n_units < grid_cap ? n_units : grid_cap;
+  k_project<<<grid, kThreads, kProjSmem, st>>>(pr, sw, tiles, n_units);
   return cudaGetLastError();
 }
 
-cudaError_t launch_minmax_chunk(const Problem& pr, const Swarm& sw,
-                                const NodeDesc* nodes, const ChunkItem* items,
-                                int n_items, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  k_minmax_chunk<<<dim3(n_items, pr.G), kThreads, eval_smem_bytes(pr), st>>>(
-      pr, sw, nodes, items);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_hist_chunk(const Problem& pr, const Swarm& sw,
-                              const NodeDesc* nodes, const ChunkItem* items,
-                              int n_items, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  k_hist_chunk<<<dim3(n_items, pr.G), kThreads, eval_smem_bytes(pr), st>>>(
-      pr, sw, nodes, items, nullptr, 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_scan(const Problem& pr, const Swarm& sw,
-                               const BigNode* big, int n_big, cudaStream_t st) {
-  if (n_big <= 0) return cudaSuccess;
-  k_reduce_scan<<<dim3(n_big, pr.P), kThreads, reduce_smem_bytes(pr), st>>>(
-      pr, sw, big);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_eval_positions(const Problem& pr, const Swarm& sw,
-                                  const NodeDesc* node, const ChunkItem* items,
-                                  int n_items, const BigNode* big,
-                                  int32_t* bins_out, int64_t n_idx,
-                                  cudaStream_t st) {
-  const size_t sm = eval_smem_bytes(pr);
-  if (n_items == 0) {
-    k_eval_small<<<dim3(1, pr.G), kThreads, sm, st>>>(pr, sw, node, nullptr,
-                                                      bins_out, n_idx);
-    return cudaGetLastError();
-  }
-  dim3 grid(n_items, pr.G);
-  k_minmax_chunk<<<grid, kThreads, sm, st>>>(pr, sw, node, items);
-  k_hist_chunk<<<grid, kThreads, sm, st>>>(pr, sw, node, items, bins_out, n_idx);
-  k_reduce_scan<<<dim3(1, pr.P), kThreads, reduce_smem_bytes(pr), st>>>(pr, sw,
-                                                                        big);
+cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                             int A, int32_t* bins_out, cudaStream_t st) {
+  if (A <= 0) return cudaSuccess;
+  k_hist_scan<<<dim3(A, pr.P), kThreads, hist_smem_bytes(pr), st>>>(
+      pr, sw, nodes, hist_copies(pr), bins_out);
   return cudaGetLastError();
 }
 

@@ -22,10 +22,9 @@ struct DevBuf {
 };
 
 enum Slot {
-  W_X, W_LAB, W_Y, W_IDX, W_W, W_POS_IN, W_BINS,
+  W_X, W_LAB, W_Y, W_IDX, W_W, W_BINS, W_XL, W_LABL, W_YL,
   S_POS, S_VEL, S_PBEST, S_GBEST, S_CUR, S_PB, S_GB, S_GPART, S_GITER,
-  S_TRACE, S_ZMM, S_PART, S_PART_S, S_PART_Q,
-  S_NODES, S_LIST, S_ITEMS, S_BIG, S_STATUS, S_OUT,
+  S_TRACE, S_ZMM, S_Z, S_NODES, S_TILES, S_STATUS, S_OUT,
   N_SLOTS
 };
 
@@ -33,6 +32,7 @@ enum Slot {
 
 struct slm_ctx {
   int device = 0;
+  int n_sm = 1;
   cudaStream_t stream = nullptr;
   std::string err;
   DevBuf ws[N_SLOTS];
@@ -59,20 +59,19 @@ struct slm_forest {
   int H = 0;
   int n_trees = 0;
   int K = 0;
-  const float* X = nullptr;
-  const int32_t* labels = nullptr;
-  const float* y = nullptr;
-  DevBuf own_X, own_lab, own_y;
+  const float* X = nullptr;  // original rows (prediction)
+  DevBuf own_X;
   TreeArrays tr{};
   DevBuf tree_mem;
-  DevBuf idx[2], w[2], side;
+  // level-resident entry arrays, ping-pong
+  DevBuf lX[2], lab[2], ly[2], lw[2], lidx[2], side;
   int cur = 0;
   bool weighted = false;
   std::vector<LevelNode> level;  // nodes of the level to grow next
   int depth = 0;
   bool done = false;
   int64_t evaluations = 0;
-  DevBuf lvl_nodes, lvl_split, lvl_cls, lvl_par, snodes, smap, out3, dst;
+  DevBuf lvl_nodes, lvl_split, lvl_cls, lvl_par, smap, out3, dst;
 };
 
 namespace {
@@ -174,53 +173,6 @@ slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
   return SLM_OK;
 }
 
-Problem make_problem(const slm_params* p, const float* X, int d,
-                     const int32_t* labels, const float* y, const int32_t* idx,
-                     const uint32_t* w, int P) {
-  Problem pr{};
-  pr.X = X;
-  pr.labels = labels;
-  pr.y = y;
-  pr.idx = idx;
-  pr.w = w;
-  pr.d = d;
-  pr.crit = p->criterion;
-  pr.K = p->criterion == SLM_MSE ? 1 : p->n_classes;
-  pr.B = p->n_bins;
-  pr.min_leaf = p->min_leaf;
-  pr.P = P;
-  pr.Pp = (P + kPG - 1) / kPG * kPG;
-  pr.G = pr.Pp / kPG;
-  return pr;
-}
-
-// Work lists of a batch: nodes small enough for one CTA, and the chunked
-// work items of the others.
-struct Batch {
-  std::vector<int32_t> small;
-  std::vector<ChunkItem> items;
-  std::vector<BigNode> big;
-};
-
-Batch plan_batch(const std::vector<NodeDesc>& nodes) {
-  Batch b;
-  for (int a = 0; a < (int)nodes.size(); ++a) {
-    const int len = nodes[a].seg_len;
-    if (len <= kSmallMax) {
-      b.small.push_back(a);
-      continue;
-    }
-    BigNode bn{a, (int32_t)b.items.size(), 0, 0};
-    for (int s = 0; s < len; s += kChunk) {
-      ChunkItem it{a, s, std::min(kChunk, len - s), s == 0};
-      b.items.push_back(it);
-      ++bn.n_items;
-    }
-    b.big.push_back(bn);
-  }
-  return b;
-}
-
 cudaEvent_t take_event(slm_ctx* c) {
   if (!c->free_events.empty()) {
     cudaEvent_t e = c->free_events.back();
@@ -262,68 +214,101 @@ cudaError_t collect_profile(slm_ctx* c) {
   return cudaSuccess;
 }
 
+Problem make_problem(const slm_params* p, const float* X, int d, const int32_t* lab,
+                     const float* y, const uint32_t* w, int64_t E, int P) {
+  Problem pr{};
+  pr.X = X;
+  pr.lab = lab;
+  pr.y = y;
+  pr.w = w;
+  pr.E = E;
+  pr.d = d;
+  pr.crit = p->criterion;
+  pr.K = p->criterion == SLM_MSE ? 1 : p->n_classes;
+  pr.B = p->n_bins;
+  pr.min_leaf = p->min_leaf;
+  pr.P = P;
+  pr.Pp = (P + kPG - 1) / kPG * kPG;
+  pr.G = pr.Pp / kPG;
+  return pr;
+}
+
+// Projection work tiles: every node's segment cut into kTS-row tiles.
+std::vector<WorkTile> plan_tiles(const std::vector<NodeDesc>& nodes) {
+  std::vector<WorkTile> t;
+  for (int a = 0; a < (int)nodes.size(); ++a)
+    for (int s = 0; s < nodes[a].seg_len; s += kTS)
+      t.push_back(WorkTile{a, nodes[a].seg_start + s, std::min(kTS, nodes[a].seg_len - s), 0});
+  return t;
+}
+
 template <typename T>
 T* ws_ptr(slm_ctx* c, Slot s) {
   return static_cast<T*>(c->ws[s].p);
 }
 
-// Allocates the swarm buffers of A nodes and the batch lists, uploads them.
-slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T,
-                       bool want_trace, const std::vector<NodeDesc>& nodes,
-                       const Batch& b, Swarm* sw) {
+// Scoring buffers of A nodes (one batch): z, ranges, node and tile lists.
+slm_status setup_scoring(slm_ctx* c, const Problem& pr, int A,
+                         const std::vector<NodeDesc>& nodes,
+                         const std::vector<WorkTile>& tiles, Swarm* sw) {
+  CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * (size_t)A * pr.Pp));
+  CK(ensure(c->ws[S_ZMM], sizeof(int32_t) * 2 * (size_t)A * pr.Pp));
+  CK(ensure(c->ws[S_Z], sizeof(float) * (size_t)pr.P * (size_t)(pr.E > 0 ? pr.E : 1)));
+  CK(ensure(c->ws[S_NODES], sizeof(NodeDesc) * nodes.size()));
+  CK(ensure(c->ws[S_TILES], sizeof(WorkTile) * tiles.size()));
+  CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc) * nodes.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  if (!tiles.empty())
+    CK(cudaMemcpyAsync(c->ws[S_TILES].p, tiles.data(), sizeof(WorkTile) * tiles.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  sw->cur = ws_ptr<EvalRes>(c, S_CUR);
+  sw->zmm = ws_ptr<int32_t>(c, S_ZMM);
+  sw->z = ws_ptr<float>(c, S_Z);
+  CK(prepare_eval_kernels(pr));
+  return SLM_OK;
+}
+
+// Allocates the swarm buffers of A nodes.
+slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T, bool want_trace,
+                       const std::vector<NodeDesc>& nodes,
+                       const std::vector<WorkTile>& tiles, Swarm* sw) {
+  Swarm s{};
+  if (slm_status st = setup_scoring(c, pr, A, nodes, tiles, &s)) return st;
   const size_t apd = (size_t)A * pr.Pp * pr.d;
   CK(ensure(c->ws[S_POS], sizeof(float) * apd));
   CK(ensure(c->ws[S_VEL], sizeof(float) * apd));
   CK(ensure(c->ws[S_PBEST], sizeof(float) * apd));
   CK(ensure(c->ws[S_GBEST], sizeof(float) * (size_t)A * pr.d));
-  CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * (size_t)A * pr.Pp));
   CK(ensure(c->ws[S_PB], sizeof(EvalRes) * (size_t)A * pr.Pp));
   CK(ensure(c->ws[S_GB], sizeof(EvalRes) * (size_t)A));
   CK(ensure(c->ws[S_GPART], sizeof(int32_t) * (size_t)A));
   CK(ensure(c->ws[S_GITER], sizeof(int32_t) * (size_t)A));
-  CK(ensure(c->ws[S_ZMM], sizeof(int32_t) * 2 * (size_t)A * pr.Pp));
   if (want_trace) CK(ensure(c->ws[S_TRACE], sizeof(double) * (size_t)A * (T + 1)));
-  const size_t words = pr.crit == SLM_MSE ? (size_t)pr.B : (size_t)pr.B * pr.K;
-  const size_t pw = b.items.size() * pr.Pp * words;
-  CK(ensure(c->ws[S_PART], sizeof(uint32_t) * pw));
-  if (pr.crit == SLM_MSE) {
-    CK(ensure(c->ws[S_PART_S], sizeof(double) * pw));
-    CK(ensure(c->ws[S_PART_Q], sizeof(double) * pw));
-  }
-  CK(ensure(c->ws[S_NODES], sizeof(NodeDesc) * nodes.size()));
-  CK(ensure(c->ws[S_LIST], sizeof(int32_t) * b.small.size()));
-  CK(ensure(c->ws[S_ITEMS], sizeof(ChunkItem) * b.items.size()));
-  CK(ensure(c->ws[S_BIG], sizeof(BigNode) * b.big.size()));
-  CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc) * nodes.size(),
-                     cudaMemcpyHostToDevice, c->stream));
-  if (!b.small.empty())
-    CK(cudaMemcpyAsync(c->ws[S_LIST].p, b.small.data(), sizeof(int32_t) * b.small.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-  if (!b.items.empty())
-    CK(cudaMemcpyAsync(c->ws[S_ITEMS].p, b.items.data(),
-                       sizeof(ChunkItem) * b.items.size(), cudaMemcpyHostToDevice,
-                       c->stream));
-  if (!b.big.empty())
-    CK(cudaMemcpyAsync(c->ws[S_BIG].p, b.big.data(), sizeof(BigNode) * b.big.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-  Swarm s{};
   s.pos = ws_ptr<float>(c, S_POS);
   s.vel = ws_ptr<float>(c, S_VEL);
   s.pbest = ws_ptr<float>(c, S_PBEST);
   s.gbest = ws_ptr<float>(c, S_GBEST);
-  s.cur = ws_ptr<EvalRes>(c, S_CUR);
   s.pb = ws_ptr<EvalRes>(c, S_PB);
   s.gb = ws_ptr<EvalRes>(c, S_GB);
   s.gpart = ws_ptr<int32_t>(c, S_GPART);
   s.giter = ws_ptr<int32_t>(c, S_GITER);
   s.trace = want_trace ? ws_ptr<double>(c, S_TRACE) : nullptr;
-  s.zmm = ws_ptr<int32_t>(c, S_ZMM);
-  s.part = ws_ptr<uint32_t>(c, S_PART);
-  s.part_s = ws_ptr<double>(c, S_PART_S);
-  s.part_q = ws_ptr<double>(c, S_PART_Q);
   s.T = T;
   *sw = s;
-  CK(prepare_eval_kernels(pr));
+  return SLM_OK;
+}
+
+// One scoring pass of every (node, particle) of a batch.
+slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw, int A,
+                       int n_tiles, double pairs, int32_t* bins_out) {
+  const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
+  const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
+  const int cap = 2 * c->n_sm;
+  if (n_tiles)
+    CK(launch(c, SLM_K_PROJECT, pairs,
+              [&] { return launch_project(pr, sw, dt, n_tiles, cap, c->stream); }));
+  CK(launch(c, SLM_K_HIST_SCAN, pairs,
+            [&] { return launch_hist_scan(pr, sw, dn, A, bins_out, c->stream); }));
   return SLM_OK;
 }
 
@@ -332,38 +317,18 @@ slm_status run_search(slm_ctx* c, const slm_params* p, const Problem& pr,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
                       Swarm* sw_out) {
   const int A = (int)nodes.size();
-  const Batch b = plan_batch(nodes);
+  const std::vector<WorkTile> tiles = plan_tiles(nodes);
   Swarm sw;
-  slm_status s = setup_swarm(c, pr, A, p->n_iters, want_trace, nodes, b, &sw);
+  slm_status s = setup_swarm(c, pr, A, p->n_iters, want_trace, nodes, tiles, &sw);
   if (s) return s;
   const SwarmCoef co{p->inertia, p->c1, p->c2, p->seed};
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
-  double small_pairs = 0.0, big_pairs = 0.0;
-  for (int32_t a : b.small) small_pairs += (double)nodes[a].seg_len * pr.P;
-  for (const BigNode& bn : b.big) big_pairs += (double)nodes[bn.node].seg_len * pr.P;
+  double pairs = 0.0;
+  for (const NodeDesc& nd : nodes) pairs += (double)nd.seg_len * pr.P;
   CK(launch(c, SLM_K_SWARM_INIT, 0.0,
             [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
-  const int n_small = (int)b.small.size(), n_items = (int)b.items.size();
-  const int n_big = (int)b.big.size();
-  const int32_t* dl = ws_ptr<int32_t>(c, S_LIST);
-  const ChunkItem* di = ws_ptr<ChunkItem>(c, S_ITEMS);
-  const BigNode* db = ws_ptr<BigNode>(c, S_BIG);
   for (int t = 0; t <= p->n_iters; ++t) {
-    if (n_small)
-      CK(launch(c, SLM_K_EVAL_SMALL, small_pairs, [&] {
-        return launch_eval_small(pr, sw, dn, dl, n_small, c->stream);
-      }));
-    if (n_items) {
-      CK(launch(c, SLM_K_MINMAX_CHUNK, big_pairs, [&] {
-        return launch_minmax_chunk(pr, sw, dn, di, n_items, c->stream);
-      }));
-      CK(launch(c, SLM_K_HIST_CHUNK, big_pairs, [&] {
-        return launch_hist_chunk(pr, sw, dn, di, n_items, c->stream);
-      }));
-      CK(launch(c, SLM_K_REDUCE_SCAN, 0.0, [&] {
-        return launch_reduce_scan(pr, sw, db, n_big, c->stream);
-      }));
-    }
+    if ((s = score_batch(c, pr, sw, A, (int)tiles.size(), pairs, nullptr))) return s;
     CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
               [&] { return launch_swarm_update(pr, sw, dn, A, t, co, c->stream); }));
   }
@@ -390,7 +355,7 @@ slm_status validate_inputs(slm_ctx* c, const int32_t* labels, int64_t n, int K,
   slm_status s = reset_status(c);
   if (s) return s;
   CK(launch(c, SLM_K_OTHER, 0.0, [&] {
-    return launch_validate(labels, labels ? n : 0, K, idx, idx ? n_idx : 0,
+    return launch_validate(labels, n, K, idx, idx ? n_idx : 0,
                            ws_ptr<int32_t>(c, S_STATUS), c->stream);
   }));
   int32_t st = 0;
@@ -436,6 +401,9 @@ slm_status slm_create(slm_ctx** out, int device, void* cuda_stream) {
   if (!c) return SLM_ENOMEM;
   c->device = device;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int sms = 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess)
+    c->n_sm = sms > 0 ? sms : 1;
   *out = c;
   return SLM_OK;
 }
@@ -503,22 +471,16 @@ slm_status slm_bootstrap(slm_ctx* c, uint64_t seed, uint32_t tree_id, int64_t n,
   return SLM_OK;
 }
 
-slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
-                              int64_t n, int32_t d, const int32_t* labels,
-                              const float* y, const int32_t* sample_idx,
-                              const uint32_t* weights, int64_t n_idx,
-                              const float* positions, int32_t n_pos,
-                              slm_eval* out, int32_t* bins_out) {
-  if (!c) return SLM_EINVAL;
-  if (slm_status s = check_params(c, p, d, false)) return s;
-  if (!X || n < 1 || n > INT32_MAX || !positions || n_pos < 1 ||
-      n_pos > kMaxParticles || !out)
-    return fail(c, SLM_EINVAL, "bad arrays or sizes");
-  if ((p->criterion == SLM_MSE) != (y != nullptr) || (labels != nullptr) == (y != nullptr))
-    return fail(c, SLM_EINVAL, "exactly one of labels / y, matching the criterion");
-  if (!sample_idx) n_idx = n;
-  if (n_idx < 0 || n_idx > INT32_MAX) return fail(c, SLM_EINVAL, "n_idx out of range");
-  CK(cudaSetDevice(c->device));
+}  // extern "C"
+
+namespace {
+
+// Stages a node given by caller arrays and gathers it into entry order:
+// rows X[idx], labels / targets, multiplicities. Fills *pr for P particles.
+slm_status prepare_node(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                        int32_t d, const int32_t* labels, const float* y,
+                        const int32_t* sample_idx, const uint32_t* weights,
+                        int64_t n_idx, int P, Problem* pr) {
   const float *dX, *dy;
   const int32_t *dlab, *didx;
   const uint32_t* dw;
@@ -537,58 +499,78 @@ slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
   }
   if ((s = validate_inputs(c, dlab, n, p->n_classes, sample_idx ? didx : nullptr, n_idx)))
     return s;
-  Problem pr = make_problem(p, dX, d, dlab, dy, didx, dw, n_pos);
-  // positions padded to Pp rows
+  CK(ensure(c->ws[W_XL], sizeof(float) * (size_t)n_idx * d));
+  CK(ensure(c->ws[W_LABL], sizeof(int32_t) * (size_t)n_idx));
+  CK(ensure(c->ws[W_YL], sizeof(float) * (size_t)n_idx));
+  float* Xl = ws_ptr<float>(c, W_XL);
+  int32_t* ll = dlab ? ws_ptr<int32_t>(c, W_LABL) : nullptr;
+  float* yl = dy ? ws_ptr<float>(c, W_YL) : nullptr;
+  CK(launch(c, SLM_K_GATHER, 0.0, [&] {
+    return launch_gather(dX, dlab, dy, didx, n_idx, d, Xl, ll, yl, c->stream);
+  }));
+  *pr = make_problem(p, Xl, d, ll, yl, dw, n_idx, P);
+  return SLM_OK;
+}
+
+slm_status check_node_args(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                           int32_t d, const int32_t* labels, const float* y,
+                           const int32_t* sample_idx, int64_t* n_idx, bool swarm) {
+  if (slm_status s = check_params(c, p, d, swarm)) return s;
+  if (!X || n < 1 || n > INT32_MAX) return fail(c, SLM_EINVAL, "bad X or n");
+  if ((p->criterion == SLM_MSE) != (y != nullptr) || (labels != nullptr) == (y != nullptr))
+    return fail(c, SLM_EINVAL, "exactly one of labels / y, matching the criterion");
+  if (!sample_idx) *n_idx = n;
+  if (*n_idx < 0 || *n_idx > INT32_MAX) return fail(c, SLM_EINVAL, "n_idx out of range");
+  if (p->criterion == SLM_GINI && *n_idx >= (int64_t(1) << 22))
+    return fail(c, SLM_EUNSUPPORTED, "Gini needs fewer than 2^22 samples per node");
+  return SLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
+                              int64_t n, int32_t d, const int32_t* labels,
+                              const float* y, const int32_t* sample_idx,
+                              const uint32_t* weights, int64_t n_idx,
+                              const float* positions, int32_t n_pos,
+                              slm_eval* out, int32_t* bins_out) {
+  if (!c) return SLM_EINVAL;
+  if (slm_status s = check_node_args(c, p, X, n, d, labels, y, sample_idx, &n_idx, false))
+    return s;
+  if (!positions || n_pos < 1 || n_pos > kMaxParticles || !out)
+    return fail(c, SLM_EINVAL, "bad positions / n_pos / out");
+  CK(cudaSetDevice(c->device));
+  Problem pr;
+  if (slm_status s = prepare_node(c, p, X, n, d, labels, y, sample_idx, weights, n_idx,
+                                  n_pos, &pr))
+    return s;
+  std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, 0u, -1}};
+  const std::vector<WorkTile> tiles = plan_tiles(nodes);
+  Swarm sw{};
+  if (slm_status s = setup_scoring(c, pr, 1, nodes, tiles, &sw)) return s;
   CK(ensure(c->ws[S_POS], sizeof(float) * pr.Pp * d));
   CK(cudaMemsetAsync(c->ws[S_POS].p, 0, sizeof(float) * pr.Pp * d, c->stream));
   CK(cudaMemcpyAsync(c->ws[S_POS].p, positions, sizeof(float) * n_pos * d,
                      cudaMemcpyDefault, c->stream));
-  std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, 0u, -1}};
-  Batch b = plan_batch(nodes);
-  CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * pr.Pp));
-  CK(ensure(c->ws[S_ZMM], sizeof(int32_t) * 2 * pr.Pp));
+  sw.pos = ws_ptr<float>(c, S_POS);
   std::vector<int32_t> zinit(2 * pr.Pp);
   for (int i = 0; i < pr.Pp; ++i) {
     zinit[2 * i] = INT32_MAX;
     zinit[2 * i + 1] = INT32_MIN;
   }
-  CK(cudaMemcpyAsync(c->ws[S_ZMM].p, zinit.data(), sizeof(int32_t) * zinit.size(),
+  CK(cudaMemcpyAsync(sw.zmm, zinit.data(), sizeof(int32_t) * zinit.size(),
                      cudaMemcpyHostToDevice, c->stream));
-  const size_t words = pr.crit == SLM_MSE ? (size_t)pr.B : (size_t)pr.B * pr.K;
-  CK(ensure(c->ws[S_PART], sizeof(uint32_t) * b.items.size() * pr.Pp * words));
-  if (pr.crit == SLM_MSE) {
-    CK(ensure(c->ws[S_PART_S], sizeof(double) * b.items.size() * pr.Pp * words));
-    CK(ensure(c->ws[S_PART_Q], sizeof(double) * b.items.size() * pr.Pp * words));
-  }
-  CK(ensure(c->ws[S_NODES], sizeof(NodeDesc)));
-  CK(ensure(c->ws[S_ITEMS], sizeof(ChunkItem) * b.items.size()));
-  CK(ensure(c->ws[S_BIG], sizeof(BigNode) * (b.big.size() + 1)));
-  CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc),
-                     cudaMemcpyHostToDevice, c->stream));
-  if (!b.items.empty()) {
-    CK(cudaMemcpyAsync(c->ws[S_ITEMS].p, b.items.data(), sizeof(ChunkItem) * b.items.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->ws[S_BIG].p, b.big.data(), sizeof(BigNode) * b.big.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-  }
-  Swarm sw{};
-  sw.pos = ws_ptr<float>(c, S_POS);
-  sw.cur = ws_ptr<EvalRes>(c, S_CUR);
-  sw.zmm = ws_ptr<int32_t>(c, S_ZMM);
-  sw.part = ws_ptr<uint32_t>(c, S_PART);
-  sw.part_s = ws_ptr<double>(c, S_PART_S);
-  sw.part_q = ws_ptr<double>(c, S_PART_Q);
-  CK(prepare_eval_kernels(pr));
   int32_t* dbins = bins_out;
   const bool bins_dev = bins_out && is_device_ptr(bins_out);
   if (bins_out && !bins_dev) {
     CK(ensure(c->ws[W_BINS], sizeof(int32_t) * (size_t)n_pos * n_idx));
     dbins = ws_ptr<int32_t>(c, W_BINS);
   }
-  c->launches += b.items.empty() ? 1 : 3;
-  CK(launch_eval_positions(pr, sw, ws_ptr<NodeDesc>(c, S_NODES),
-                           ws_ptr<ChunkItem>(c, S_ITEMS), (int)b.items.size(),
-                           ws_ptr<BigNode>(c, S_BIG), dbins, n_idx, c->stream));
+  if (slm_status s = score_batch(c, pr, sw, 1, (int)tiles.size(),
+                                 (double)n_idx * n_pos, dbins))
+    return s;
   static_assert(sizeof(slm_eval) == sizeof(EvalRes), "layout");
   CK(cudaMemcpyAsync(out, sw.cur, sizeof(EvalRes) * n_pos, cudaMemcpyDefault, c->stream));
   if (bins_out && !bins_dev)
@@ -605,36 +587,17 @@ slm_status slm_node_split(slm_ctx* c, const slm_params* p, const float* X,
                           uint32_t node_uid, float* direction_out,
                           float* gbest_out, slm_split* out, double* trace_out) {
   if (!c) return SLM_EINVAL;
-  if (slm_status s = check_params(c, p, d, true)) return s;
-  if (!X || n < 1 || n > INT32_MAX || !out || !direction_out)
-    return fail(c, SLM_EINVAL, "bad arrays or sizes");
-  if ((p->criterion == SLM_MSE) != (y != nullptr) || (labels != nullptr) == (y != nullptr))
-    return fail(c, SLM_EINVAL, "exactly one of labels / y, matching the criterion");
-  if (!sample_idx) n_idx = n;
-  if (n_idx < 0 || n_idx > INT32_MAX) return fail(c, SLM_EINVAL, "n_idx out of range");
-  CK(cudaSetDevice(c->device));
-  const float *dX, *dy;
-  const int32_t *dlab, *didx;
-  const uint32_t* dw;
-  slm_status s;
-  if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return s;
-  if ((s = stage_in(c, labels, (size_t)n, c->ws[W_LAB], &dlab))) return s;
-  if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return s;
-  if ((s = stage_in(c, weights, (size_t)n_idx, c->ws[W_W], &dw))) return s;
-  if (sample_idx) {
-    if ((s = stage_in(c, sample_idx, (size_t)n_idx, c->ws[W_IDX], &didx))) return s;
-  } else {
-    CK(ensure(c->ws[W_IDX], sizeof(int32_t) * n_idx));
-    CK(launch(c, SLM_K_OTHER, 0.0,
-              [&] { return launch_iota(ws_ptr<int32_t>(c, W_IDX), n_idx, 1, c->stream); }));
-    didx = ws_ptr<int32_t>(c, W_IDX);
-  }
-  if ((s = validate_inputs(c, dlab, n, p->n_classes, sample_idx ? didx : nullptr, n_idx)))
+  if (slm_status s = check_node_args(c, p, X, n, d, labels, y, sample_idx, &n_idx, true))
     return s;
-  const Problem pr = make_problem(p, dX, d, dlab, dy, didx, dw, p->n_particles);
+  if (!out || !direction_out) return fail(c, SLM_EINVAL, "NULL out or direction_out");
+  CK(cudaSetDevice(c->device));
+  Problem pr;
+  if (slm_status s = prepare_node(c, p, X, n, d, labels, y, sample_idx, weights, n_idx,
+                                  p->n_particles, &pr))
+    return s;
   std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, node_uid, -1}};
   Swarm sw;
-  if ((s = run_search(c, p, pr, nodes, trace_out != nullptr, &sw))) return s;
+  if (slm_status s = run_search(c, p, pr, nodes, trace_out != nullptr, &sw)) return s;
   EvalRes gb;
   int32_t part = 0, iter = 0;
   std::vector<float> g(d);
@@ -695,11 +658,16 @@ static slm_status forest_alloc_trees(slm_ctx* c, slm_forest* f) {
 void slm_forest_free(slm_forest* f) {
   if (!f) return;
   cudaSetDevice(f->device);
-  DevBuf* bufs[] = {&f->own_X, &f->own_lab, &f->own_y, &f->tree_mem, &f->idx[0],
-                    &f->idx[1], &f->w[0], &f->w[1], &f->side, &f->lvl_nodes,
-                    &f->lvl_split, &f->lvl_cls, &f->lvl_par, &f->snodes, &f->smap,
-                    &f->out3, &f->dst};
+  DevBuf* bufs[] = {&f->own_X, &f->tree_mem, &f->side, &f->lvl_nodes, &f->lvl_split,
+                    &f->lvl_cls, &f->lvl_par, &f->smap, &f->out3, &f->dst};
   for (DevBuf* b : bufs) release(*b);
+  for (int i = 0; i < 2; ++i) {
+    release(f->lX[i]);
+    release(f->lab[i]);
+    release(f->ly[i]);
+    release(f->lw[i]);
+    release(f->lidx[i]);
+  }
   delete f;
 }
 
@@ -737,30 +705,29 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
     slm_forest_free(f);
     return st;
   };
-  if ((s = stage_in(c, X, (size_t)n * d, f->own_X, &f->X))) return bail(s);
-  if ((s = stage_in(c, labels, (size_t)n, f->own_lab, &f->labels))) return bail(s);
-  if ((s = stage_in(c, y, (size_t)n, f->own_y, &f->y))) return bail(s);
-  if ((s = validate_inputs(c, f->labels, n, p->n_classes, nullptr, 0))) return bail(s);
+  const float *dX, *dy;
+  const int32_t* dlab;
+  if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return bail(s);
+  if ((s = stage_in(c, labels, (size_t)n, c->ws[W_LAB], &dlab))) return bail(s);
+  if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return bail(s);
+  if ((s = validate_inputs(c, dlab, n, p->n_classes, nullptr, 0))) return bail(s);
   if ((s = forest_alloc_trees(c, f))) return bail(s);
-  const size_t cap = (size_t)n * f->n_trees;
-  cudaError_t e;
-  if ((e = ensure(f->idx[0], 4 * cap)) || (e = ensure(f->idx[1], 4 * cap)) ||
-      (e = ensure(f->side, cap)))
-    return bail(cuda_fail(c, e, "level buffers"));
   f->weighted = p->bootstrap != 0;
   f->level.clear();
+  cudaError_t e;
+  // root entries of every tree: sample ids (+ multiplicities) in lidx[1] / lw[1]
+  int64_t E = 0;
+  const size_t cap = (size_t)n * f->n_trees;
+  if ((e = ensure(f->lidx[1], 4 * cap))) return bail(cuda_fail(c, e, "level buffers"));
   if (f->weighted) {
-    if ((e = ensure(f->w[0], 4 * cap)) || (e = ensure(f->w[1], 4 * cap)))
-      return bail(cuda_fail(c, e, "weight buffers"));
-    // bags: multiplicities per tree, then the nonzero samples in order
     DevBuf wall, offs, cnts;
     auto cleanup = [&]() {
       release(wall);
       release(offs);
       release(cnts);
     };
-    if ((e = ensure(wall, 4 * cap)) || (e = ensure(offs, 8 * (size_t)f->n_trees)) ||
-        (e = ensure(cnts, 4 * (size_t)f->n_trees))) {
+    if ((e = ensure(f->lw[1], 4 * cap)) || (e = ensure(wall, 4 * cap)) ||
+        (e = ensure(offs, 8 * (size_t)f->n_trees)) || (e = ensure(cnts, 4 * (size_t)f->n_trees))) {
       cleanup();
       return bail(cuda_fail(c, e, "bootstrap buffers"));
     }
@@ -776,11 +743,12 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
       }
     }
     std::vector<int32_t> cnt(f->n_trees);
+    c->launches += 1;
     if ((e = cudaMemcpyAsync(offs.p, off.data(), 8 * off.size(), cudaMemcpyHostToDevice,
                              c->stream)) ||
-        (c->launches += 1, e = launch_compact_nonzero(static_cast<uint32_t*>(wall.p), f->n_trees, n,
-                                    static_cast<int32_t*>(f->idx[1].p),
-                                    static_cast<uint32_t*>(f->w[1].p),
+        (e = launch_compact_nonzero(static_cast<uint32_t*>(wall.p), f->n_trees, n,
+                                    static_cast<int32_t*>(f->lidx[1].p),
+                                    static_cast<uint32_t*>(f->lw[1].p),
                                     static_cast<int64_t*>(offs.p),
                                     static_cast<int32_t*>(cnts.p), c->stream)) ||
         (e = cudaMemcpyAsync(cnt.data(), cnts.p, 4 * cnt.size(), cudaMemcpyDeviceToHost,
@@ -789,31 +757,48 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
       cleanup();
       return bail(cuda_fail(c, e, "bootstrap compaction"));
     }
-    // pack the bags contiguously into buffer 0
+    cleanup();
+    for (int t = 0; t < f->n_trees; ++t) E += cnt[t];
+    if ((e = ensure(f->lidx[0], 4 * (size_t)E)) || (e = ensure(f->lw[0], 4 * (size_t)E)))
+      return bail(cuda_fail(c, e, "level buffers"));
     int64_t pos = 0;
     for (int t = 0; t < f->n_trees; ++t) {
-      if ((e = cudaMemcpyAsync(static_cast<int32_t*>(f->idx[0].p) + pos,
-                               static_cast<int32_t*>(f->idx[1].p) + off[t], 4 * (size_t)cnt[t],
+      if ((e = cudaMemcpyAsync(static_cast<int32_t*>(f->lidx[0].p) + pos,
+                               static_cast<int32_t*>(f->lidx[1].p) + off[t], 4 * (size_t)cnt[t],
                                cudaMemcpyDeviceToDevice, c->stream)) ||
-          (e = cudaMemcpyAsync(static_cast<uint32_t*>(f->w[0].p) + pos,
-                               static_cast<uint32_t*>(f->w[1].p) + off[t], 4 * (size_t)cnt[t],
-                               cudaMemcpyDeviceToDevice, c->stream))) {
-        cleanup();
+          (e = cudaMemcpyAsync(static_cast<uint32_t*>(f->lw[0].p) + pos,
+                               static_cast<uint32_t*>(f->lw[1].p) + off[t], 4 * (size_t)cnt[t],
+                               cudaMemcpyDeviceToDevice, c->stream)))
         return bail(cuda_fail(c, e, "bag packing"));
-      }
       f->level.push_back(LevelNode{(int32_t)pos, cnt[t], t * f->H, 0});
       pos += cnt[t];
     }
-    e = cudaStreamSynchronize(c->stream);
-    cleanup();
-    if (e) return bail(cuda_fail(c, e, "bag packing"));
   } else {
+    E = (int64_t)cap;
+    if ((e = ensure(f->lidx[0], 4 * (size_t)E))) return bail(cuda_fail(c, e, "level buffers"));
     c->launches += 1;
-    if ((e = launch_iota(static_cast<int32_t*>(f->idx[0].p), n, f->n_trees, c->stream)))
+    if ((e = launch_iota(static_cast<int32_t*>(f->lidx[0].p), n, f->n_trees, c->stream)))
       return bail(cuda_fail(c, e, "iota"));
     for (int t = 0; t < f->n_trees; ++t)
       f->level.push_back(LevelNode{(int32_t)(t * n), (int32_t)n, t * f->H, 0});
   }
+  // level-resident arrays sized for the root's entries (levels only shrink)
+  for (int i = 0; i < 2; ++i) {
+    if ((e = ensure(f->lX[i], sizeof(float) * (size_t)E * d)) ||
+        (e = ensure(f->lidx[i], sizeof(int32_t) * (size_t)E)) ||
+        (dlab && (e = ensure(f->lab[i], sizeof(int32_t) * (size_t)E))) ||
+        (dy && (e = ensure(f->ly[i], sizeof(float) * (size_t)E))) ||
+        (f->weighted && (e = ensure(f->lw[i], sizeof(uint32_t) * (size_t)E))))
+      return bail(cuda_fail(c, e, "level buffers"));
+  }
+  if ((e = ensure(f->side, (size_t)E))) return bail(cuda_fail(c, e, "level buffers"));
+  c->launches += 1;
+  if ((e = launch_gather(dX, dlab, dy, static_cast<int32_t*>(f->lidx[0].p), E, d,
+                         static_cast<float*>(f->lX[0].p),
+                         dlab ? static_cast<int32_t*>(f->lab[0].p) : nullptr,
+                         dy ? static_cast<float*>(f->ly[0].p) : nullptr, c->stream)) ||
+      (e = cudaStreamSynchronize(c->stream)))
+    return bail(cuda_fail(c, e, "root gather"));
   f->cur = 0;
   *out = f;
   return SLM_OK;
@@ -830,9 +815,15 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   const slm_params* p = &f->params;
   const int L = (int)f->level.size();
   const int K = f->K;
-  int32_t* idx = static_cast<int32_t*>(f->idx[f->cur].p);
-  uint32_t* w = f->weighted ? static_cast<uint32_t*>(f->w[f->cur].p) : nullptr;
-  Problem pr = make_problem(p, f->X, f->d, f->labels, f->y, idx, w, p->n_particles);
+  const int cu = f->cur;
+  const bool mse = p->criterion == SLM_MSE;
+  int64_t E = 0;
+  for (const LevelNode& ln : f->level) E = std::max<int64_t>(E, (int64_t)ln.seg_start + ln.seg_len);
+  Problem pr = make_problem(p, static_cast<float*>(f->lX[cu].p), f->d,
+                            mse ? nullptr : static_cast<int32_t*>(f->lab[cu].p),
+                            mse ? static_cast<float*>(f->ly[cu].p) : nullptr,
+                            f->weighted ? static_cast<uint32_t*>(f->lw[cu].p) : nullptr, E,
+                            p->n_particles);
 
   // 1. statistics and leaf values of every node of the level
   CK(ensure(f->lvl_nodes, sizeof(LevelNode) * L));
@@ -914,17 +905,20 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     ++n_split;
   }
   if (n_split) {
-    const int nxt = 1 - f->cur;
+    const int nx = 1 - cu;
+    LevelArrays la{static_cast<float*>(f->lX[nx].p),
+                   mse ? nullptr : static_cast<int32_t*>(f->lab[nx].p),
+                   mse ? static_cast<float*>(f->ly[nx].p) : nullptr,
+                   f->weighted ? static_cast<uint32_t*>(f->lw[nx].p) : nullptr,
+                   static_cast<int32_t*>(f->lidx[nx].p)};
     CK(cudaMemcpyAsync(f->dst.p, dst.data(), sizeof(int32_t) * 2 * A, cudaMemcpyHostToDevice,
                        c->stream));
     CK(launch(c, SLM_K_COMPACT, 0.0, [&] {
       return launch_compact(pr, dsn, A, static_cast<uint8_t*>(f->side.p),
                             static_cast<int32_t*>(f->dst.p),
-                            static_cast<int32_t*>(f->idx[nxt].p),
-                            f->weighted ? static_cast<uint32_t*>(f->w[nxt].p) : nullptr,
-                            c->stream);
+                            static_cast<int32_t*>(f->lidx[cu].p), la, c->stream);
     }));
-    f->cur = nxt;
+    f->cur = nx;
   }
   CK(cudaStreamSynchronize(c->stream));
   f->level.swap(next);

@@ -21,8 +21,6 @@ constexpr int kMaxClasses = 32;
 constexpr int kMaxHistBytesPerParticle = 10240;  // B*K*4 (classification)
 constexpr int kMaxParticles = 256;
 constexpr int kMaxD = 1024;
-constexpr int kSmallMax = 2048;  // nodes up to this many entries: fused path
-constexpr int kChunk = 1024;     // entries per work item of larger nodes
 
 // Philox stream purposes (high byte of counter word 3).
 enum Purpose : uint32_t {
@@ -51,28 +49,23 @@ struct NodeDesc {
   int32_t slot;       // tree * H + heap index, or -1
 };
 
-// Work item of a node too large for one CTA.
-struct ChunkItem {
-  int32_t node;   // index into the batch's NodeDesc array
-  int32_t start;  // entry offset within the node's segment
-  int32_t len;    // entries
-  int32_t first;  // 1 if first item of its node
-};
-
-struct BigNode {
-  int32_t node;
-  int32_t item0;   // first ChunkItem
-  int32_t n_items;
+// A tile of up to kTS consecutive rows of one node (projection work unit,
+// together with a particle group).
+struct WorkTile {
+  int32_t node;  // index into the batch's NodeDesc array
+  int32_t row0;  // first entry (absolute row of the level arrays)
+  int32_t rows;  // <= kTS
   int32_t pad;
 };
 
-// Problem data shared by all nodes of a batch (passed by value).
+// Problem data shared by all nodes of a batch (passed by value). Rows are
+// stored entry-ordered: node a owns entries [seg_start, seg_start + seg_len).
 struct Problem {
-  const float* X;         // [n, d]
-  const int32_t* labels;  // [n] or null
-  const float* y;         // [n] or null
-  const int32_t* idx;     // [entries] level sample indices
-  const uint32_t* w;      // [entries] multiplicities or null
+  const float* X;         // [E, d] rows of the entries
+  const int32_t* lab;     // [E] labels (classification) or null
+  const float* y;         // [E] targets (MSE) or null
+  const uint32_t* w;      // [E] multiplicities or null (= 1)
+  int64_t E;              // entries in the batch
   int32_t d;
   int32_t crit;           // slm_criterion
   int32_t K;              // classes (1 for MSE)
@@ -95,10 +88,8 @@ struct Swarm {
   int32_t* gpart; // [A]
   int32_t* giter; // [A]
   double* trace;  // [A, T+1] or null
-  int32_t* zmm;   // [A, Pp, 2] ordered-int min/max (large nodes)
-  uint32_t* part; // partial histograms of large nodes
-  double* part_s; // MSE partial sums
-  double* part_q; // MSE partial sums of squares
+  int32_t* zmm;   // [A, Pp, 2] ordered-int range of each projection
+  float* z;       // [P, E] projections of the current iteration
   int32_t T;
 };
 
@@ -108,31 +99,21 @@ struct SwarmCoef {
 };
 
 // ---- launchers (eval_kernels.cu) -------------------------------------------
-size_t eval_smem_bytes(const Problem& pr);
 cudaError_t prepare_eval_kernels(const Problem& pr);
 cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
                               const NodeDesc* nodes, int A, SwarmCoef co,
                               cudaStream_t st);
-cudaError_t launch_eval_small(const Problem& pr, const Swarm& sw,
-                              const NodeDesc* nodes, const int32_t* list,
-                              int n_list, cudaStream_t st);
-cudaError_t launch_minmax_chunk(const Problem& pr, const Swarm& sw,
-                                const NodeDesc* nodes, const ChunkItem* items,
-                                int n_items, cudaStream_t st);
-cudaError_t launch_hist_chunk(const Problem& pr, const Swarm& sw,
-                              const NodeDesc* nodes, const ChunkItem* items,
-                              int n_items, cudaStream_t st);
-cudaError_t launch_reduce_scan(const Problem& pr, const Swarm& sw,
-                               const BigNode* big, int n_big, cudaStream_t st);
+// z and ranges of every (tile, particle group); grid_cap = resident CTAs.
+cudaError_t launch_project(const Problem& pr, const Swarm& sw,
+                           const WorkTile* tiles, int n_tiles, int grid_cap,
+                           cudaStream_t st);
+// Scores of every (node, particle); bins_out[P, seg_len] (one node) or null.
+cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
+                             const NodeDesc* nodes, int A, int32_t* bins_out,
+                             cudaStream_t st);
 cudaError_t launch_swarm_update(const Problem& pr, const Swarm& sw,
                                 const NodeDesc* nodes, int A, int t,
                                 SwarmCoef co, cudaStream_t st);
-// Scores explicit positions (slm_evaluate_swarm): pos [Pp, d] of one node.
-cudaError_t launch_eval_positions(const Problem& pr, const Swarm& sw,
-                                  const NodeDesc* node, const ChunkItem* items,
-                                  int n_items, const BigNode* big,
-                                  int32_t* bins_out, int64_t n_idx,
-                                  cudaStream_t st);
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
                                   int P, int d, uint32_t purpose, float* u,
                                   cudaStream_t st);
@@ -166,6 +147,11 @@ struct TreeArrays {
   int64_t* n_right;
 };
 
+// Gathers rows / labels / targets of sample ids idx[E] into entry order:
+// Xl[e] = X[idx[e]] (labels, y likewise; null arrays are skipped).
+cudaError_t launch_gather(const float* X, const int32_t* labels, const float* y,
+                          const int32_t* idx, int64_t E, int d, float* Xl,
+                          int32_t* lab_l, float* y_l, cudaStream_t st);
 // Per-level node statistics: writes the leaf fields of every level node and
 // splittable[L]; cls[L*K] class counts, par[L*2] (sum w y, sum w y^2).
 cudaError_t launch_node_stats(const Problem& pr, const LevelNode* nodes, int L,
@@ -180,11 +166,20 @@ cudaError_t launch_partition(const Problem& pr, const Swarm& sw,
                              const uint32_t* cls, const double* par,
                              TreeArrays tr, uint8_t* side, int32_t* out3,
                              int32_t* status, cudaStream_t st);
-// Stable compaction of split nodes' entries into the next level's arrays.
-// dst[A*2] = start of the left / right child segments (-1: not split).
+// Level arrays of one side of the ping-pong.
+struct LevelArrays {
+  float* X;
+  int32_t* lab;
+  float* y;
+  uint32_t* w;
+  int32_t* idx;
+};
+// Stable compaction of split nodes' entries (rows, labels / targets,
+// multiplicities, sample ids) into the next level's arrays. dst[A*2] = start
+// of the left / right child segments (-1: not split).
 cudaError_t launch_compact(const Problem& pr, const NodeDesc* snodes, int A,
                            const uint8_t* side, const int32_t* dst,
-                           int32_t* idx_next, uint32_t* w_next,
+                           const int32_t* idx_cur, LevelArrays next,
                            cudaStream_t st);
 // Root entries of bootstrap trees: for tree t, the samples with w > 0 in
 // increasing order and their multiplicities, at offsets off[t]; counts[t].

@@ -84,18 +84,17 @@ __global__ void __launch_bounds__(kTT)
   float lo = INFINITY, hi = -INFINITY;
   for (int r = threadIdx.x; r < nd.seg_len; r += kTT) {
     const int64_t e = (int64_t)nd.seg_start + r;
-    const int32_t si = pr.idx[e];
     const uint32_t w = pr.w ? pr.w[e] : 1u;
     wsum += w;
     if (pr.crit == SLM_MSE) {
-      const float yv = pr.y[si];
+      const float yv = pr.y[e];
       const double wy = (double)w * (double)yv;
       sy += wy;
       sq += wy * (double)yv;
       lo = fminf(lo, yv);
       hi = fmaxf(hi, yv);
     } else {
-      atomicAdd(&s_cnt[pr.labels[si]], (unsigned long long)w);
+      atomicAdd(&s_cnt[pr.lab[e]], (unsigned long long)w);
     }
   }
   atomicAdd(&s_w, wsum);
@@ -173,8 +172,7 @@ __global__ void __launch_bounds__(kTT)
   unsigned long long wl = 0;
   for (int r = threadIdx.x; r < nd.seg_len; r += kTT) {
     const int64_t e = (int64_t)nd.seg_start + r;
-    const int32_t si = pr.idx[e];
-    const float z = project_row(pr.X + (int64_t)si * d, s_g, d);
+    const float z = project_row(pr.X + e * d, s_g, d);
     const int b = bin_of(z, gb.zmin, gb.inv_w, pr.B);
     const int right = b >= gb.bin;
     side[e] = (uint8_t)right;
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(kTT)
       const uint32_t w = pr.w ? pr.w[e] : 1u;
       ++n_left_entries;
       wl += w;
-      if (pr.crit != SLM_MSE) atomicAdd(&s_lk[pr.labels[si]], (unsigned long long)w);
+      if (pr.crit != SLM_MSE) atomicAdd(&s_lk[pr.lab[e]], (unsigned long long)w);
     }
   }
   atomicAdd(&s_wl, wl);
@@ -225,12 +223,14 @@ __global__ void __launch_bounds__(kTT)
 __global__ void __launch_bounds__(kTT)
     k_compact(Problem pr, const NodeDesc* __restrict__ snodes,
               const uint8_t* __restrict__ side, const int32_t* __restrict__ dst,
-              int32_t* idx_next, uint32_t* w_next) {
+              const int32_t* __restrict__ idx_cur, LevelArrays nx) {
   const int a = blockIdx.x;
   const int dl = dst[2 * a], dr = dst[2 * a + 1];
   if (dl < 0) return;
   const NodeDesc nd = snodes[a];
+  const int d = pr.d;
   __shared__ int sbuf[kTT / 32 + 1];
+  __shared__ int s_dst[kTT];
   int base_l = 0, base_r = 0;
   for (int t0 = 0; t0 < nd.seg_len; t0 += kTT) {
     const int r = t0 + threadIdx.x;
@@ -244,11 +244,36 @@ __global__ void __launch_bounds__(kTT)
     const int rank_r = threadIdx.x - rank_l;  // entries before r that went right
     if (in) {
       const int32_t pos = is_left ? dl + base_l + rank_l : dr + base_r + rank_r;
-      idx_next[pos] = pr.idx[e];
-      if (w_next) w_next[pos] = pr.w[e];
+      s_dst[threadIdx.x] = pos;
+      nx.idx[pos] = idx_cur[e];
+      if (nx.lab) nx.lab[pos] = pr.lab[e];
+      if (nx.y) nx.y[pos] = pr.y[e];
+      if (nx.w) nx.w[pos] = pr.w[e];
     }
+    __syncthreads();
+    // rows: coalesced copies, one row per group of threads
+    for (int q = threadIdx.x; q < n_in * d; q += kTT) {
+      const int rr = q / d, j = q - rr * d;
+      nx.X[(int64_t)s_dst[rr] * d + j] = pr.X[((int64_t)nd.seg_start + t0 + rr) * d + j];
+    }
+    __syncthreads();
     base_l += tot_l;
     base_r += n_in - tot_l;
+  }
+}
+
+__global__ void k_gather(const float* __restrict__ X, const int32_t* __restrict__ labels,
+                         const float* __restrict__ y, const int32_t* __restrict__ idx,
+                         int64_t E, int d, float* Xl, int32_t* lab_l, float* y_l) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= E * d) return;
+  const int64_t e = q / d;
+  const int j = (int)(q - e * d);
+  const int64_t s = idx[e];
+  Xl[q] = X[s * d + j];
+  if (j == 0) {
+    if (lab_l) lab_l[e] = labels[s];
+    if (y_l) y_l[e] = y[s];
   }
 }
 
@@ -359,10 +384,20 @@ cudaError_t launch_partition(const Problem& pr, const Swarm& sw,
 
 cudaError_t launch_compact(const Problem& pr, const NodeDesc* snodes, int A,
                            const uint8_t* side, const int32_t* dst,
-                           int32_t* idx_next, uint32_t* w_next,
+                           const int32_t* idx_cur, LevelArrays next,
                            cudaStream_t st) {
   if (A <= 0) return cudaSuccess;
-  k_compact<<<A, kTT, 0, st>>>(pr, snodes, side, dst, idx_next, w_next);
+  k_compact<<<A, kTT, 0, st>>>(pr, snodes, side, dst, idx_cur, next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const float* X, const int32_t* labels, const float* y,
+                          const int32_t* idx, int64_t E, int d, float* Xl,
+                          int32_t* lab_l, float* y_l, cudaStream_t st) {
+  const int64_t total = E * d;
+  if (total <= 0) return cudaSuccess;
+  k_gather<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, labels, y, idx, E, d, Xl,
+                                                           lab_l, y_l);
   return cudaGetLastError();
 }
 
@@ -386,7 +421,7 @@ cudaError_t launch_iota(int32_t* idx, int64_t n, int copies, cudaStream_t st) {
 cudaError_t launch_validate(const int32_t* labels, int64_t n, int K,
                             const int32_t* idx, int64_t n_idx,
                             int32_t* status, cudaStream_t st) {
-  const int64_t m = n > n_idx ? n : n_idx;
+  const int64_t m = (labels && n > n_idx) ? n : n_idx;
   if (m <= 0) return cudaSuccess;
   k_validate<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(labels, n, K, idx,
                                                           n_idx, status);
