@@ -210,8 +210,9 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
  * Kernels of this library, for per-kernel timing. */
 typedef enum {
   SLM_K_PROJECT = 0,      /* z = X_node . x_p for every particle (FP32 FFMA) */
-  SLM_K_HIST_SCAN = 1,    /* binning, histograms and threshold scan */
-  SLM_K_SWARM_UPDATE = 2, /* pbest / gbest and Eq. pso-1 */
+  SLM_K_HIST_SCAN = 1,    /* binning, histograms, threshold scan and, in a
+                             search, the pbest / gbest steps of Algorithm 1 */
+  SLM_K_SWARM_UPDATE = 2, /* Eq. pso-1 move of every particle */
   SLM_K_SWARM_INIT = 3,
   SLM_K_NODE_STATS = 4,
   SLM_K_PARTITION = 5,

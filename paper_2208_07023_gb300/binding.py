@@ -21,7 +21,7 @@ SLM_GINI, SLM_ENTROPY, SLM_MSE = 0, 1, 2
 SLM_PROJ_FP32, SLM_PROJ_BF16_TOPK = 0, 1
 CRITERIA = {"gini": SLM_GINI, "entropy": SLM_ENTROPY, "mse": SLM_MSE}
 PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2 = 1, 2, 3, 4
-KERNELS = ["project", "hist_scan", "swarm_update", "swarm_init", "node_stats",
+KERNELS = ["project", "hist_scan", "move", "swarm_init", "node_stats",
            "partition", "compact", "gather", "other"]
 
 

@@ -29,6 +29,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "philox.cuh"
 #include "slm_internal.cuh"
 
@@ -37,6 +39,14 @@ namespace slm {
 namespace {
 
 // ---- small helpers -----------------------------------------------------------
+
+// Programmatic dependent launch: the next kernel of the stream may begin
+// launching once every CTA of this grid has passed pdl_trigger(); pdl_wait()
+// blocks until the previous grid has completed and its writes are visible.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 __device__ __forceinline__ int f2ord(float f) {
   int i = __float_as_int(f);
@@ -185,12 +195,10 @@ __device__ EvalRes scan_cls(const uint32_t* h, int B, int K, int min_leaf,
     c.nl = nl;
     c.nr = nr;
     if (crit == SLM_GINI) {
-      const uint64_t num = SL[i] * nr + SR[i] * nl;
-      const uint64_t den = (uint64_t)nl * nr;
-      const uint64_t nden = (uint64_t)ntot * den;
-      c.num = num;
-      c.den = den;
-      c.loss = (double)(nden - num) / (double)nden;
+      // decisions use the exact rational; the double loss is formed once, for
+      // the winning edge (FP64 division is slow on this part)
+      c.num = SL[i] * nr + SR[i] * nl;
+      c.den = (uint64_t)nl * nr;
     } else {
       const double hh = (xlogx(nl) - hL[i]) + (xlogx(nr) - hR[i]);
       c.loss = hh / (double)ntot;
@@ -201,6 +209,10 @@ __device__ EvalRes scan_cls(const uint32_t* h, int B, int K, int min_leaf,
   for (int off = 16; off > 0; off >>= 1) {
     const EvalRes o = shfl_res(best, lane ^ off);
     if (edge_first(o, best, crit)) best = o;
+  }
+  if (crit == SLM_GINI && best.valid) {
+    const uint64_t nden = (uint64_t)ntot * best.den;
+    best.loss = (double)(nden - best.num) / (double)nden;
   }
   return best;
 }
@@ -302,6 +314,52 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// ---- bulk copies (TMA) with mbarrier completion -------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> this CTA's shared memory; 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Waits for phase `parity` of the barrier, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  const uint32_t a = smem_addr(bar);
+  for (int i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr int kWaitPolls = 1 << 20;  // bounded: a lost copy ends the kernel, not the GPU
+
 // ---- projection -------------------------------------------------------------------
 
 constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPG * kXS);
@@ -348,6 +406,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   float* xs1 = smf + kTS * kXS;
   float* as0 = smf + 2 * kTS * kXS;
   float* as1 = as0 + kPG * kXS;
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x >= n_units) return;
   const int d = pr.d, G = pr.G;
   const int nk = (d + kKC - 1) / kKC;
@@ -419,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             lo = z < lo ? z : lo;
             hi = z > hi ? z : hi;
             any = true;
-            if (p < pr.P) sw.z[(int64_t)p * pr.E + wt.row0 + r] = z;
+            if (p < pr.P) sw.z[(int64_t)p * pr.Ez + wt.row0 + r] = z;
           }
         }
         int olo = any ? f2ord(lo) : INT_MAX, ohi = any ? f2ord(hi) : INT_MIN;
@@ -443,106 +503,371 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-// ---- histogram and scan -------------------------------------------------------------
+// ---- swarm update ----------------------------------------------------------------
 
-__host__ __device__ inline size_t hist_copy_bytes(int crit, int B, int K) {
-  return crit == SLM_MSE ? (size_t)B * (4 + 8 + 8) : (size_t)B * K * 4;
+__device__ __forceinline__ EvalRes ldcg_res(const EvalRes* p) {
+  EvalRes r;
+  r.loss = __ldcg(&p->loss);
+  r.num = __ldcg((const unsigned long long*)&p->num);
+  r.den = __ldcg((const unsigned long long*)&p->den);
+  r.zmin = __ldcg(&p->zmin);
+  r.inv_w = __ldcg(&p->inv_w);
+  r.bin = __ldcg(&p->bin);
+  r.valid = __ldcg(&p->valid);
+  r.nl = __ldcg((const long long*)&p->nl);
+  r.nr = __ldcg((const long long*)&p->nr);
+  return r;
 }
 
-// One CTA per (node, particle): bins the node's z, histograms it in `copies`
-// warp-private shared histograms, merges them and scans the edges.
+// Algorithm 1, pbest step of particle p after evaluation t (one warp): strict
+// "<" against the particle's best so far; the position is kept on improvement.
+__device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, int a, int p,
+                                           int t, const EvalRes& cur) {
+  const int lane = threadIdx.x & 31;
+  EvalRes* pb = sw.pb + (int64_t)a * pr.Pp + p;
+  int imp = 0;
+  if (lane == 0) {
+    imp = (t == 0) || better(cur, *pb, pr.crit);
+    if (imp) *pb = cur;
+  }
+  imp = __shfl_sync(0xffffffffu, imp, 0);
+  if (!imp) return;
+  const int64_t o = ((int64_t)a * pr.Pp + p) * pr.d;
+  for (int j = lane; j < pr.d; j += 32) sw.pbest[o + j] = sw.pos[o + j];
+}
+
+// Algorithm 1, gbest step of node a after evaluation t. Run by all threads of
+// the CTA that finished the node's last particle group in this iteration.
+__device__ void node_tail(const Problem& pr, const Swarm& sw, int a, int t) {
+  const int P = pr.P, Pp = pr.Pp, d = pr.d;
+  const int nthr = blockDim.x, nw = nthr >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ EvalRes s_wbest[kThreads / 32];
+  __shared__ int s_widx[kThreads / 32];
+  __shared__ int s_best;
+  const EvalRes* cur = sw.cur + (int64_t)a * Pp;
+  const EvalRes gold = sw.gb[a];
+
+  // gbest candidates = particles strictly better than gold (at t = 0 every
+  // particle; gold is then unset); argmin with ties to the lower index
+  EvalRes ce = invalid_res();
+  int cidx = INT_MAX;
+  for (int p = threadIdx.x; p < P; p += nthr) {
+    const EvalRes e = ldcg_res(cur + p);  // written by other CTAs of this launch
+    if (!(t == 0 || better(e, gold, pr.crit))) continue;
+    if (cidx == INT_MAX || better(e, ce, pr.crit)) {
+      ce = e;
+      cidx = p;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const EvalRes o = shfl_res(ce, lane ^ off);
+    const int oi = __shfl_xor_sync(0xffffffffu, cidx, off);
+    bool take;
+    if (oi == INT_MAX)
+      take = false;
+    else if (cidx == INT_MAX)
+      take = true;
+    else if (better(o, ce, pr.crit))
+      take = true;
+    else if (better(ce, o, pr.crit))
+      take = false;
+    else
+      take = oi < cidx;
+    if (take) {
+      ce = o;
+      cidx = oi;
+    }
+  }
+  if (lane == 0) {
+    s_wbest[warp] = ce;
+    s_widx[warp] = cidx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    EvalRes b = s_wbest[0];
+    int bi = s_widx[0];
+    for (int w = 1; w < nw; ++w) {
+      const EvalRes o = s_wbest[w];
+      const int oi = s_widx[w];
+      if (oi == INT_MAX) continue;
+      if (bi == INT_MAX || better(o, b, pr.crit) || (!better(b, o, pr.crit) && oi < bi)) {
+        b = o;
+        bi = oi;
+      }
+    }
+    s_best = bi == INT_MAX ? -1 : bi;
+    if (bi != INT_MAX) {
+      sw.gb[a] = b;
+      sw.gpart[a] = bi;
+      sw.giter[a] = t;
+    }
+    if (sw.trace) {
+      const EvalRes g = bi != INT_MAX ? b : gold;
+      sw.trace[(int64_t)a * (sw.T + 1) + t] =
+          g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
+    }
+  }
+  __syncthreads();
+  // the new gbest improved its pbest in this iteration, so its pbest row is
+  // its current position (written by another CTA of this launch)
+  const float* pbp = sw.pbest + (int64_t)a * Pp * d;
+  float* gbp = sw.gbest + (int64_t)a * d;
+  const int best = s_best;
+  if (best >= 0)
+    for (int j = threadIdx.x; j < d; j += nthr) gbp[j] = __ldcg(pbp + (int64_t)best * d + j);
+}
+
+// Eq. pso-1, synchronous: every particle moves with the gbest held at the end
+// of iteration t. One thread per (node, particle, 4 dimensions).
+__global__ void __launch_bounds__(128)
+    k_move(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int A, int t,
+           SwarmCoef co) {
+  pdl_trigger();
+  pdl_wait();
+  const int d = pr.d, d4 = (d + 3) >> 2;
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per_node = (int64_t)pr.P * d4;
+  if (item >= per_node * A) return;
+  const int a = (int)(item / per_node);
+  const int rem = (int)(item - (int64_t)a * per_node);
+  const int pi = rem / d4, q = rem - pi * d4;
+  const uint32_t uid = nodes[a].uid;
+  const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
+  const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi, (uint32_t)q | (kR1 << 24),
+                              k0, k1);
+  const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi, (uint32_t)q | (kR2 << 24),
+                              k0, k1);
+  const int64_t row = ((int64_t)a * pr.Pp + pi) * d;
+  float* pos = sw.pos + row;
+  float* vel = sw.vel + row;
+  const float* pbp = sw.pbest + row;
+  const float* gbp = sw.gbest + (int64_t)a * d;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = 4 * q + c;
+    if (j >= d) break;
+    // v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v
+    const float x = pos[j], v = vel[j];
+    const float inertia = __fmul_rn(co.inertia, v);
+    const float cog = __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(pbp[j], x));
+    const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])), __fsub_rn(gbp[j], x));
+    const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
+    vel[j] = vn;
+    pos[j] = __fadd_rn(x, vn);
+  }
+}
+
+// ---- histogram and scan -------------------------------------------------------------
+
+constexpr int kWP = 8;        // particles per CTA of the histogram kernel, one per warp
+constexpr int kPiece = 1024;  // entries per staged piece
+
+__host__ __device__ inline size_t hist_particle_bytes(int crit, int B, int K) {
+  return crit == SLM_MSE ? (size_t)B * (4 + 8 + 8) : (size_t)B * K * 4;
+}
+// One staged piece: z of kWP particles, then labels or targets, then
+// multiplicities (if weighted).
+__host__ __device__ inline size_t stage_bytes(bool weighted) {
+  return (size_t)kPiece * 4 * (kWP + 1 + (weighted ? 1 : 0));
+}
+
+// A cluster of S CTAs per (node, group of kWP particles). Warp w of every
+// CTA owns particle g*kWP + w. The CTA's slice of the node's entries (rank r:
+// the r-th of S slices) streams through shared memory in kPiece-entry pieces:
+// one thread issues bulk (TMA) copies of the kWP z rows, the labels / targets
+// and the multiplicities of a piece, double-buffered on two mbarriers; every
+// warp bins its particle's z from shared memory into its own histogram. Rank
+// q of the cluster then sums one slice of every histogram word over the S
+// CTAs through distributed shared memory into rank 0, whose warps scan the
+// B-1 edges of their particles. In a search (do_update) each warp also takes
+// its particle's pbest step, and the CTA that finishes a node's last particle
+// group (ticket in sw.done) runs the node's gbest step (the move is k_move).
 __global__ void __launch_bounds__(kThreads)
-    k_hist_scan(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int copies,
-                int32_t* bins_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int a = blockIdx.x, p = blockIdx.y;
+    k_hist_scan(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int32_t* bins_out,
+                int t, SwarmCoef co, int do_update) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_last;
+  const cg::cluster_group cl = cg::this_cluster();
+  pdl_trigger();
+  pdl_wait();
+  const int S = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int a = blockIdx.x / S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = blockIdx.y;
+  const int p = g * kWP + warp;
+  const bool live = p < pr.P;
   const NodeDesc nd = nodes[a];
   const int B = pr.B, K = pr.K;
   const bool mse = pr.crit == SLM_MSE;
-  const int words = mse ? B : B * K;  // u32 counters per copy
-  double* hs = reinterpret_cast<double*>(smem);       // MSE [copies][B]
-  double* hq = hs + (mse ? copies * B : 0);            // MSE [copies][B]
-  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? copies * B : 0));
-  __shared__ float s_zmin, s_inv_w;
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
-    const int lo_o = zz[0], hi_o = zz[1];
-    zz[0] = INT_MAX;  // ready for the next iteration
-    zz[1] = INT_MIN;
-    if (lo_o == INT_MAX) {
-      s_ok = 0;
-      s_zmin = 0.f;
-      s_inv_w = 0.f;
-    } else {
-      const float lo = ord2f(lo_o), hi = ord2f(hi_o);
-      const float inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
-      s_zmin = lo;
-      s_inv_w = inv_w;
-      s_ok = (hi > lo) && isfinite(inv_w);
-    }
+  const bool weighted = pr.w != nullptr;
+  const int words = mse ? B : B * K;  // u32 counters per particle
+  // shared memory: histograms, then two stages
+  double* hs = reinterpret_cast<double*>(smem);         // MSE [kWP][B]
+  double* hq = hs + (mse ? kWP * B : 0);                 // MSE [kWP][B]
+  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? kWP * B : 0));  // [kWP][words]
+  unsigned char* stage0 =
+      smem + (((size_t)hist_particle_bytes(pr.crit, B, K) * kWP + 127) & ~(size_t)127);
+  const size_t sbytes = stage_bytes(weighted);
+  uint32_t* h = hc + warp * words;
+  double* hsw = hs + warp * B;
+  double* hqw = hq + warp * B;
+
+  // range of this warp's particle
+  int lo_o = INT_MAX, hi_o = INT_MIN;
+  int* zz = sw.zmm + ((int64_t)a * pr.Pp + (live ? p : 0)) * 2;
+  if (live && lane == 0) {
+    lo_o = zz[0];
+    hi_o = zz[1];
   }
-  for (int i = threadIdx.x; i < copies * words; i += kThreads) hc[i] = 0u;
+  lo_o = __shfl_sync(0xffffffffu, lo_o, 0);
+  hi_o = __shfl_sync(0xffffffffu, hi_o, 0);
+  float zmin = 0.f, inv_w = 0.f;
+  bool ok = false;
+  if (lo_o != INT_MAX) {
+    const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+    inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+    zmin = lo;
+    ok = (hi > lo) && isfinite(inv_w);
+  }
+  for (int i = lane; i < words; i += 32) h[i] = 0u;
   if (mse)
-    for (int i = threadIdx.x; i < copies * B; i += kThreads) {
-      hs[i] = 0.0;
-      hq[i] = 0.0;
+    for (int i = lane; i < B; i += 32) {
+      hsw[i] = 0.0;
+      hqw[i] = 0.0;
     }
-  __syncthreads();
-  const bool ok = s_ok;
-  const float zmin = s_zmin, inv_w = s_inv_w;
-  if (ok) {
-    const int cp = (threadIdx.x >> 5) % copies;
-    uint32_t* h = hc + cp * words;
-    const float* zrow = sw.z + (int64_t)p * pr.E + nd.seg_start;
-    for (int r = threadIdx.x; r < nd.seg_len; r += kThreads) {
-      const int64_t e = (int64_t)nd.seg_start + r;
-      const int b = bin_of(zrow[r], zmin, inv_w, B);
-      const uint32_t w = pr.w ? pr.w[e] : 1u;
-      if (mse) {
-        const float yv = pr.y[e];
-        const double wy = (double)w * (double)yv;
-        atomicAdd(&h[b], w);
-        atomicAdd(&hs[cp * B + b], wy);
-        atomicAdd(&hq[cp * B + b], wy * (double)yv);
-      } else {
-        atomicAdd(&h[b * K + pr.lab[e]], w);
-      }
-      if (bins_out) bins_out[(int64_t)p * nd.seg_len + r] = b;
-    }
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
   }
   __syncthreads();
-  if (!ok) {
-    if (threadIdx.x == 0) {
-      EvalRes res = invalid_res();
-      sw.cur[(int64_t)a * pr.Pp + p] = res;
+
+  // slice of this rank: starts on a multiple of 4 entries (16 bytes)
+  const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
+  const int r_begin = min(nd.seg_len, rank * chunk);
+  const int r_end = min(nd.seg_len, r_begin + chunk);
+  const int n_pieces = (r_end - r_begin + kPiece - 1) / kPiece;
+  const int64_t e0 = nd.seg_start;  // multiple of 4
+  const int n_live = min(kWP, pr.P - g * kWP);
+  auto issue = [&](int k) {
+    const int r = r_begin + k * kPiece;
+    const int n = min(kPiece, r_end - r);
+    const uint32_t bytes = (uint32_t)(((n + 3) & ~3) * 4);
+    unsigned char* st = stage0 + (k & 1) * sbytes;
+    uint64_t* bar = &s_bar[k & 1];
+    fence_proxy_async();
+    mbar_expect_tx(bar, bytes * (uint32_t)(n_live + 1 + (weighted ? 1 : 0)));
+    for (int w = 0; w < n_live; ++w)
+      bulk_g2s(st + (size_t)w * kPiece * 4, sw.z + (int64_t)(g * kWP + w) * pr.Ez + e0 + r,
+               bytes, bar);
+    const void* src = mse ? (const void*)(pr.y + e0 + r) : (const void*)(pr.lab + e0 + r);
+    bulk_g2s(st + (size_t)kWP * kPiece * 4, src, bytes, bar);
+    if (weighted) bulk_g2s(st + (size_t)(kWP + 1) * kPiece * 4, pr.w + e0 + r, bytes, bar);
+  };
+  if (threadIdx.x == 0 && n_pieces > 0) issue(0);
+  bool lost = false;
+  for (int k = 0; k < n_pieces; ++k) {
+    if (threadIdx.x == 0 && k + 1 < n_pieces) issue(k + 1);
+    if (!mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitPolls)) {
+      // a copy did not land: record it, give in-flight copies a bounded
+      // chance to finish, and stop using the stages
+      if (threadIdx.x == 0 && sw.err) atomicExch(sw.err, 3);
+      mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitPolls);
+      if (k + 1 < n_pieces) mbar_wait(&s_bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), kWaitPolls);
+      lost = true;
+      break;
     }
-    return;
-  }
-  if (copies > 1) {
-    for (int i = threadIdx.x; i < words; i += kThreads) {
-      uint32_t v = hc[i];
-      for (int cp = 1; cp < copies; ++cp) v += hc[cp * words + i];
-      hc[i] = v;
-    }
-    if (mse)
-      for (int i = threadIdx.x; i < B; i += kThreads) {
-        double vs = hs[i], vq = hq[i];
-        for (int cp = 1; cp < copies; ++cp) {
-          vs += hs[cp * B + i];
-          vq += hq[cp * B + i];
+    const unsigned char* st = stage0 + (k & 1) * sbytes;
+    const int r = r_begin + k * kPiece;
+    const int n = min(kPiece, r_end - r);
+    if (live && ok) {
+      const float* zs = reinterpret_cast<const float*>(st) + (size_t)warp * kPiece;
+      const int32_t* ls = reinterpret_cast<const int32_t*>(st + (size_t)kWP * kPiece * 4);
+      const float* ys = reinterpret_cast<const float*>(st + (size_t)kWP * kPiece * 4);
+      const uint32_t* ws =
+          reinterpret_cast<const uint32_t*>(st + (size_t)(kWP + 1) * kPiece * 4);
+      for (int i = lane; i < n; i += 32) {
+        const int b = bin_of(zs[i], zmin, inv_w, B);
+        const uint32_t w = weighted ? ws[i] : 1u;
+        if (mse) {
+          const float yv = ys[i];
+          const double wy = (double)w * (double)yv;
+          atomicAdd(&h[b], w);
+          atomicAdd(&hsw[b], wy);
+          atomicAdd(&hqw[b], wy * (double)yv);
+        } else {
+          atomicAdd(&h[b * K + ls[i]], w);
         }
-        hs[i] = vs;
-        hq[i] = vq;
+        if (bins_out) bins_out[(int64_t)p * nd.seg_len + r + i] = b;
       }
-    __syncthreads();
+    }
+    __syncthreads();  // stage k & 1 is refilled by piece k + 2
   }
-  if (threadIdx.x >= 32) return;
-  EvalRes res = mse ? scan_mse(hc, hs, hq, B, pr.min_leaf)
-                    : scan_cls(hc, B, K, pr.min_leaf, pr.crit);
-  res.zmin = zmin;
-  res.inv_w = inv_w;
-  if (threadIdx.x == 0) sw.cur[(int64_t)a * pr.Pp + p] = res;
+  (void)lost;
+  if (S > 1) {
+    cl.sync();  // every CTA's histograms are complete
+    // rank q sums words [q*W/S, (q+1)*W/S) of all kWP histograms into rank 0
+    const int W = kWP * words;
+    const int w0 = (int)((int64_t)W * rank / S), w1 = (int)((int64_t)W * (rank + 1) / S);
+    uint32_t* dst = cl.map_shared_rank(hc, 0);
+    for (int i = w0 + threadIdx.x; i < w1; i += kThreads) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q < S) v += cl.map_shared_rank(hc, q)[i];
+      dst[i] = v;
+    }
+    if (mse) {
+      const int Wd = kWP * B;
+      const int d0 = (int)((int64_t)Wd * rank / S), d1 = (int)((int64_t)Wd * (rank + 1) / S);
+      double* ds = cl.map_shared_rank(hs, 0);
+      double* dq = cl.map_shared_rank(hq, 0);
+      for (int i = d0 + threadIdx.x; i < d1; i += kThreads) {
+        double vs = 0.0, vq = 0.0;
+        for (int q = 0; q < S; ++q) {
+          vs += cl.map_shared_rank(hs, q)[i];
+          vq += cl.map_shared_rank(hq, q)[i];
+        }
+        ds[i] = vs;
+        dq[i] = vq;
+      }
+    }
+    cl.sync();  // rank 0 holds the sums; the others' memory is no longer read
+    if (rank != 0) return;
+  }
+  if (live) {
+    if (lane == 0) {
+      zz[0] = INT_MAX;  // ready for the next iteration
+      zz[1] = INT_MIN;
+    }
+    EvalRes res;
+    if (!ok) {
+      res = invalid_res();
+    } else {
+      res = mse ? scan_mse(h, hsw, hqw, B, pr.min_leaf) : scan_cls(h, B, K, pr.min_leaf, pr.crit);
+      res.zmin = zmin;
+      res.inv_w = inv_w;
+    }
+    if (lane == 0) sw.cur[(int64_t)a * pr.Pp + p] = res;
+    if (do_update) pbest_step(pr, sw, a, p, t, res);
+  }
+  if (!do_update) return;
+  __threadfence();  // this CTA's scores and pbest rows, before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int prev = atomicAdd(&sw.done[a], 1);
+    s_last = prev == (int)gridDim.y - 1;
+    if (s_last) sw.done[a] = 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  node_tail(pr, sw, a, t);
 }
 
 // Initial swarm of each node: x ~ U[-1,1)^d, v ~ 0.1 U[-1,1)^d.
@@ -589,131 +914,12 @@ __global__ void k_swarm_init(Problem pr, Swarm sw,
     sw.gb[a] = invalid_res();
     sw.gpart[a] = 0;
     sw.giter[a] = 0;
+    sw.done[a] = 0;
   }
 }
 
 // Bests after evaluation t (Algorithm 1, strict "<", particles in increasing
 // order), then -- if t < T -- the synchronous move to iteration t+1.
-__global__ void __launch_bounds__(kThreads)
-    k_swarm_update(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
-                   int t, SwarmCoef co) {
-  const int a = blockIdx.x;
-  const int P = pr.P, Pp = pr.Pp, d = pr.d;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ int s_imp[kMaxParticles];
-  __shared__ EvalRes s_wbest[kThreads / 32];
-  __shared__ int s_widx[kThreads / 32];
-  __shared__ int s_best;
-  EvalRes* cur = sw.cur + (int64_t)a * Pp;
-  EvalRes* pb = sw.pb + (int64_t)a * Pp;
-  const EvalRes gold = sw.gb[a];
-
-  // pbest scores; gbest candidates = particles strictly better than gold
-  // (at t = 0 every particle; gold is then unset).
-  const int p = threadIdx.x;
-  EvalRes ce = invalid_res();
-  int cidx = INT_MAX;
-  if (p < P) {
-    ce = cur[p];
-    const bool imp = (t == 0) || better(ce, pb[p], pr.crit);
-    s_imp[p] = imp;
-    if (imp) pb[p] = ce;
-    if (t == 0 || better(ce, gold, pr.crit)) cidx = p;
-  }
-  // argmin over candidates: better score, ties to the lower index
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const EvalRes o = shfl_res(ce, lane ^ off);
-    const int oi = __shfl_xor_sync(0xffffffffu, cidx, off);
-    bool take;
-    if (oi == INT_MAX)
-      take = false;
-    else if (cidx == INT_MAX)
-      take = true;
-    else if (better(o, ce, pr.crit))
-      take = true;
-    else if (better(ce, o, pr.crit))
-      take = false;
-    else
-      take = oi < cidx;
-    if (take) {
-      ce = o;
-      cidx = oi;
-    }
-  }
-  if (lane == 0) {
-    s_wbest[warp] = ce;
-    s_widx[warp] = cidx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    EvalRes b = s_wbest[0];
-    int bi = s_widx[0];
-    for (int w = 1; w < kThreads / 32; ++w) {
-      const EvalRes o = s_wbest[w];
-      const int oi = s_widx[w];
-      if (oi == INT_MAX) continue;
-      if (bi == INT_MAX || better(o, b, pr.crit) ||
-          (!better(b, o, pr.crit) && oi < bi)) {
-        b = o;
-        bi = oi;
-      }
-    }
-    s_best = bi == INT_MAX ? -1 : bi;
-    if (bi != INT_MAX) {
-      sw.gb[a] = b;
-      sw.gpart[a] = bi;
-      sw.giter[a] = t;
-    }
-    if (sw.trace) {
-      const EvalRes g = bi != INT_MAX ? b : gold;
-      sw.trace[(int64_t)a * (sw.T + 1) + t] =
-          g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
-    }
-  }
-  __syncthreads();
-  float* pos = sw.pos + (int64_t)a * Pp * d;
-  float* vel = sw.vel + (int64_t)a * Pp * d;
-  float* pbp = sw.pbest + (int64_t)a * Pp * d;
-  float* gbp = sw.gbest + (int64_t)a * d;
-  const int best = s_best;
-  for (int e = threadIdx.x; e < P * d; e += kThreads) {
-    const int q = e / d;
-    if (s_imp[q]) pbp[e] = pos[e];
-  }
-  if (best >= 0)
-    for (int j = threadIdx.x; j < d; j += kThreads)
-      gbp[j] = pos[(int64_t)best * d + j];
-  if (t >= sw.T) return;
-  __syncthreads();
-
-  // v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v
-  const uint32_t uid = nodes[a].uid;
-  const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
-  const int d4 = (d + 3) >> 2;
-  for (int e = threadIdx.x; e < P * d4; e += kThreads) {
-    const int pi = e / d4, q = e - pi * d4;
-    const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
-                                (uint32_t)q | (kR1 << 24), k0, k1);
-    const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
-                                (uint32_t)q | (kR2 << 24), k0, k1);
-    for (int c = 0; c < 4; ++c) {
-      const int j = 4 * q + c;
-      if (j >= d) break;
-      const int64_t ix = (int64_t)pi * d + j;
-      const float x = pos[ix], v = vel[ix];
-      const float inertia = __fmul_rn(co.inertia, v);
-      const float cog = __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])),
-                                  __fsub_rn(pbp[ix], x));
-      const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])),
-                                  __fsub_rn(gbp[j], x));
-      const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
-      vel[ix] = vn;
-      pos[ix] = __fadd_rn(x, vn);
-    }
-  }
-}
-
 __global__ void k_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
                                  int P, int d, uint32_t purpose, float* u) {
   const int d4 = (d + 3) >> 2;
@@ -746,14 +952,9 @@ __global__ void k_bootstrap(uint64_t seed, uint32_t tree, int64_t n,
 
 // ---- launchers ---------------------------------------------------------------------
 
-int hist_copies(const Problem& pr) {
-  const size_t per = hist_copy_bytes(pr.crit, pr.B, pr.K);
-  int c = (int)((48 * 1024) / per);
-  return c < 1 ? 1 : (c > 8 ? 8 : c);
-}
-
 static size_t hist_smem_bytes(const Problem& pr) {
-  return hist_copy_bytes(pr.crit, pr.B, pr.K) * hist_copies(pr);
+  const size_t hist = (hist_particle_bytes(pr.crit, pr.B, pr.K) * kWP + 127) & ~(size_t)127;
+  return hist + 2 * stage_bytes(pr.w != nullptr);
 }
 
 cudaError_t prepare_eval_kernels(const Problem& pr) {
@@ -761,8 +962,10 @@ cudaError_t prepare_eval_kernels(const Problem& pr) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kProjSmem);
   if (e) return e;
-  return cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)hist_smem_bytes(pr));
+  if ((e = cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)hist_smem_bytes(pr))))
+    return e;
+  return cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
@@ -778,24 +981,81 @@ cudaError_t launch_project(const Problem& pr, const Swarm& sw, const WorkTile* t
   const int n_units = n_tiles * pr.G;
   if (n_units <= 0) return cudaSuccess;
   const int grid = n_units < grid_cap ? n_units : grid_cap;
-  k_project<<<grid, kThreads, kProjSmem, st>>>(pr, sw, tiles, n_units);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kProjSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_project, pr, sw, tiles, n_units);
+}
+
+int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_cluster) {
+  // clusters of S CTAs per (node, particle group): enough CTAs to fill the
+  // GPU twice, slices of at least 1024 entries
+  const int groups = (pr.P + kWP - 1) / kWP;
+  int S = 1;
+  while (2 * S <= max_cluster && (int64_t)A * groups * S < 2LL * n_sm &&
+         max_len / (2 * S) >= 1024)
+    S *= 2;
+  return S;
+}
+
+int hist_max_cluster(const Problem& pr) {
+  // largest power-of-two cluster (<= 16) the device can schedule for this kernel
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = hist_smem_bytes(pr);
+  int n = 0;
+  if (cudaOccupancyMaxPotentialClusterSize(&n, k_hist_scan, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 8;
+  }
+  int S = 1;
+  while (2 * S <= n && 2 * S <= 16) S *= 2;
+  return S;
 }
 
 cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
-                             int A, int32_t* bins_out, cudaStream_t st) {
+                             int A, int S, int32_t* bins_out, int t, SwarmCoef co,
+                             int do_update, cudaStream_t st) {
   if (A <= 0) return cudaSuccess;
-  k_hist_scan<<<dim3(A, pr.P), kThreads, hist_smem_bytes(pr), st>>>(
-      pr, sw, nodes, hist_copies(pr), bins_out);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A * S), (unsigned)((pr.P + kWP - 1) / kWP), 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = hist_smem_bytes(pr);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, bins_out, t, co, do_update);
 }
 
-cudaError_t launch_swarm_update(const Problem& pr, const Swarm& sw,
-                                const NodeDesc* nodes, int A, int t,
-                                SwarmCoef co, cudaStream_t st) {
-  if (A <= 0) return cudaSuccess;
-  k_swarm_update<<<A, kThreads, 0, st>>>(pr, sw, nodes, t, co);
-  return cudaGetLastError();
+cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
+                        int t, SwarmCoef co, cudaStream_t st) {
+  const int64_t items = (int64_t)A * pr.P * ((pr.d + 3) / 4);
+  if (items <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((items + 127) / 128), 1, 1);
+  cfg.blockDim = dim3(128, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_move, pr, sw, nodes, A, t, co);
 }
 
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,

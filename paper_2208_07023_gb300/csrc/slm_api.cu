@@ -24,7 +24,7 @@ struct DevBuf {
 enum Slot {
   W_X, W_LAB, W_Y, W_IDX, W_W, W_BINS, W_XL, W_LABL, W_YL,
   S_POS, S_VEL, S_PBEST, S_GBEST, S_CUR, S_PB, S_GB, S_GPART, S_GITER,
-  S_TRACE, S_ZMM, S_Z, S_NODES, S_TILES, S_STATUS, S_OUT,
+  S_TRACE, S_ZMM, S_Z, S_DONE, S_NODES, S_TILES, S_STATUS, S_ERR, S_OUT,
   N_SLOTS
 };
 
@@ -72,6 +72,7 @@ struct slm_forest {
   bool done = false;
   int64_t evaluations = 0;
   DevBuf lvl_nodes, lvl_split, lvl_cls, lvl_par, smap, out3, dst;
+  DevBuf ltiles, ltile0, acc_w, acc_y, tile_s, stile0, tile_left, tile_base, p_lk, p_wl;
 };
 
 namespace {
@@ -222,6 +223,7 @@ Problem make_problem(const slm_params* p, const float* X, int d, const int32_t* 
   pr.y = y;
   pr.w = w;
   pr.E = E;
+  pr.Ez = (E + 3) / 4 * 4;
   pr.d = d;
   pr.crit = p->criterion;
   pr.K = p->criterion == SLM_MSE ? 1 : p->n_classes;
@@ -231,6 +233,14 @@ Problem make_problem(const slm_params* p, const float* X, int d, const int32_t* 
   pr.Pp = (P + kPG - 1) / kPG * kPG;
   pr.G = pr.Pp / kPG;
   return pr;
+}
+
+int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
+
+// Entries the level arrays need: the root's (padded) entries plus the
+// padding of every node of a level (< 4 each), plus a 16-byte guard.
+int64_t level_capacity(int64_t e_root, int n_trees, int max_depth) {
+  return e_root + 4 * (int64_t)n_trees * ((int64_t)1 << max_depth) + 16;
 }
 
 // Projection work tiles: every node's segment cut into kTS-row tiles.
@@ -253,7 +263,7 @@ slm_status setup_scoring(slm_ctx* c, const Problem& pr, int A,
                          const std::vector<WorkTile>& tiles, Swarm* sw) {
   CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * (size_t)A * pr.Pp));
   CK(ensure(c->ws[S_ZMM], sizeof(int32_t) * 2 * (size_t)A * pr.Pp));
-  CK(ensure(c->ws[S_Z], sizeof(float) * (size_t)pr.P * (size_t)(pr.E > 0 ? pr.E : 1)));
+  CK(ensure(c->ws[S_Z], sizeof(float) * (size_t)pr.P * (size_t)(pr.Ez > 0 ? pr.Ez : 4)));
   CK(ensure(c->ws[S_NODES], sizeof(NodeDesc) * nodes.size()));
   CK(ensure(c->ws[S_TILES], sizeof(WorkTile) * tiles.size()));
   CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc) * nodes.size(),
@@ -261,9 +271,12 @@ slm_status setup_scoring(slm_ctx* c, const Problem& pr, int A,
   if (!tiles.empty())
     CK(cudaMemcpyAsync(c->ws[S_TILES].p, tiles.data(), sizeof(WorkTile) * tiles.size(),
                        cudaMemcpyHostToDevice, c->stream));
+  CK(ensure(c->ws[S_ERR], sizeof(int32_t)));
+  CK(cudaMemsetAsync(c->ws[S_ERR].p, 0, sizeof(int32_t), c->stream));
   sw->cur = ws_ptr<EvalRes>(c, S_CUR);
   sw->zmm = ws_ptr<int32_t>(c, S_ZMM);
   sw->z = ws_ptr<float>(c, S_Z);
+  sw->err = ws_ptr<int32_t>(c, S_ERR);
   CK(prepare_eval_kernels(pr));
   return SLM_OK;
 }
@@ -283,6 +296,7 @@ slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T, bool want_tr
   CK(ensure(c->ws[S_GB], sizeof(EvalRes) * (size_t)A));
   CK(ensure(c->ws[S_GPART], sizeof(int32_t) * (size_t)A));
   CK(ensure(c->ws[S_GITER], sizeof(int32_t) * (size_t)A));
+  CK(ensure(c->ws[S_DONE], sizeof(int32_t) * (size_t)A));
   if (want_trace) CK(ensure(c->ws[S_TRACE], sizeof(double) * (size_t)A * (T + 1)));
   s.pos = ws_ptr<float>(c, S_POS);
   s.vel = ws_ptr<float>(c, S_VEL);
@@ -292,23 +306,40 @@ slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T, bool want_tr
   s.gb = ws_ptr<EvalRes>(c, S_GB);
   s.gpart = ws_ptr<int32_t>(c, S_GPART);
   s.giter = ws_ptr<int32_t>(c, S_GITER);
+  s.done = ws_ptr<int32_t>(c, S_DONE);
   s.trace = want_trace ? ws_ptr<double>(c, S_TRACE) : nullptr;
   s.T = T;
   *sw = s;
   return SLM_OK;
 }
 
-// One scoring pass of every (node, particle) of a batch.
-slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw, int A,
-                       int n_tiles, double pairs, int32_t* bins_out) {
+// One scoring pass of every (node, particle) of a batch; with a swarm
+// (co != null) the pass ends with the swarm update of iteration t.
+// Cluster split of the histogram kernel for a batch.
+int batch_split(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes) {
+  int64_t max_len = 0;
+  for (const NodeDesc& nd : nodes) max_len = std::max<int64_t>(max_len, nd.seg_len);
+  return hist_split(pr, (int)nodes.size(), max_len, c->n_sm, hist_max_cluster(pr));
+}
+
+slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
+                       const std::vector<NodeDesc>& nodes, int n_tiles, double pairs,
+                       int32_t* bins_out, int t, const SwarmCoef* co, int S) {
+  const int A = (int)nodes.size();
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
   const int cap = 2 * c->n_sm;
   if (n_tiles)
     CK(launch(c, SLM_K_PROJECT, pairs,
               [&] { return launch_project(pr, sw, dt, n_tiles, cap, c->stream); }));
-  CK(launch(c, SLM_K_HIST_SCAN, pairs,
-            [&] { return launch_hist_scan(pr, sw, dn, A, bins_out, c->stream); }));
+  const SwarmCoef none{};
+  CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
+    return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? *co : none, co ? 1 : 0,
+                            c->stream);
+  }));
+  if (co && t < sw.T)
+    CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
+              [&] { return launch_move(pr, sw, dn, A, t, *co, c->stream); }));
   return SLM_OK;
 }
 
@@ -327,12 +358,20 @@ slm_status run_search(slm_ctx* c, const slm_params* p, const Problem& pr,
   for (const NodeDesc& nd : nodes) pairs += (double)nd.seg_len * pr.P;
   CK(launch(c, SLM_K_SWARM_INIT, 0.0,
             [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
-  for (int t = 0; t <= p->n_iters; ++t) {
-    if ((s = score_batch(c, pr, sw, A, (int)tiles.size(), pairs, nullptr))) return s;
-    CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
-              [&] { return launch_swarm_update(pr, sw, dn, A, t, co, c->stream); }));
-  }
+  const int S = batch_split(c, pr, nodes);
+  for (int t = 0; t <= p->n_iters; ++t)
+    if ((s = score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S)))
+      return s;
   *sw_out = sw;
+  return SLM_OK;
+}
+
+// Kernel error word of the last scoring batch (stream-synchronising).
+slm_status check_kernel_errors(slm_ctx* c) {
+  int32_t e = 0;
+  CK(cudaMemcpyAsync(&e, c->ws[S_ERR].p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (e) return fail(c, SLM_ETIMEOUT, "a bulk copy of the histogram kernel did not complete");
   return SLM_OK;
 }
 
@@ -488,20 +527,27 @@ slm_status prepare_node(slm_ctx* c, const slm_params* p, const float* X, int64_t
   if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return s;
   if ((s = stage_in(c, labels, (size_t)n, c->ws[W_LAB], &dlab))) return s;
   if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return s;
-  if ((s = stage_in(c, weights, (size_t)n_idx, c->ws[W_W], &dw))) return s;
+  // multiplicities are always copied: the kernels read them 16 bytes at a time
+  dw = nullptr;
+  if (weights && n_idx > 0) {
+    CK(ensure(c->ws[W_W], sizeof(uint32_t) * (size_t)(n_idx + 16)));
+    CK(cudaMemcpyAsync(c->ws[W_W].p, weights, sizeof(uint32_t) * (size_t)n_idx,
+                       cudaMemcpyDefault, c->stream));
+    dw = ws_ptr<uint32_t>(c, W_W);
+  }
   if (sample_idx) {
     if ((s = stage_in(c, sample_idx, (size_t)n_idx, c->ws[W_IDX], &didx))) return s;
   } else {
     CK(ensure(c->ws[W_IDX], sizeof(int32_t) * n_idx));
     CK(launch(c, SLM_K_OTHER, 0.0,
-              [&] { return launch_iota(ws_ptr<int32_t>(c, W_IDX), n_idx, 1, c->stream); }));
+              [&] { return launch_iota(ws_ptr<int32_t>(c, W_IDX), n_idx, n_idx, 1, c->stream); }));
     didx = ws_ptr<int32_t>(c, W_IDX);
   }
   if ((s = validate_inputs(c, dlab, n, p->n_classes, sample_idx ? didx : nullptr, n_idx)))
     return s;
   CK(ensure(c->ws[W_XL], sizeof(float) * (size_t)n_idx * d));
-  CK(ensure(c->ws[W_LABL], sizeof(int32_t) * (size_t)n_idx));
-  CK(ensure(c->ws[W_YL], sizeof(float) * (size_t)n_idx));
+  CK(ensure(c->ws[W_LABL], sizeof(int32_t) * (size_t)(n_idx + 16)));
+  CK(ensure(c->ws[W_YL], sizeof(float) * (size_t)(n_idx + 16)));
   float* Xl = ws_ptr<float>(c, W_XL);
   int32_t* ll = dlab ? ws_ptr<int32_t>(c, W_LABL) : nullptr;
   float* yl = dy ? ws_ptr<float>(c, W_YL) : nullptr;
@@ -568,10 +614,12 @@ slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
     CK(ensure(c->ws[W_BINS], sizeof(int32_t) * (size_t)n_pos * n_idx));
     dbins = ws_ptr<int32_t>(c, W_BINS);
   }
-  if (slm_status s = score_batch(c, pr, sw, 1, (int)tiles.size(),
-                                 (double)n_idx * n_pos, dbins))
+  if (slm_status s = score_batch(c, pr, sw, nodes, (int)tiles.size(),
+                                 (double)n_idx * n_pos, dbins, 0, nullptr,
+                                 batch_split(c, pr, nodes)))
     return s;
   static_assert(sizeof(slm_eval) == sizeof(EvalRes), "layout");
+  if (slm_status s = check_kernel_errors(c)) return s;
   CK(cudaMemcpyAsync(out, sw.cur, sizeof(EvalRes) * n_pos, cudaMemcpyDefault, c->stream));
   if (bins_out && !bins_dev)
     CK(cudaMemcpyAsync(bins_out, dbins, sizeof(int32_t) * (size_t)n_pos * n_idx,
@@ -598,6 +646,7 @@ slm_status slm_node_split(slm_ctx* c, const slm_params* p, const float* X,
   std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, node_uid, -1}};
   Swarm sw;
   if (slm_status s = run_search(c, p, pr, nodes, trace_out != nullptr, &sw)) return s;
+  if (slm_status s = check_kernel_errors(c)) return s;
   EvalRes gb;
   int32_t part = 0, iter = 0;
   std::vector<float> g(d);
@@ -658,8 +707,10 @@ static slm_status forest_alloc_trees(slm_ctx* c, slm_forest* f) {
 void slm_forest_free(slm_forest* f) {
   if (!f) return;
   cudaSetDevice(f->device);
-  DevBuf* bufs[] = {&f->own_X, &f->tree_mem, &f->side, &f->lvl_nodes, &f->lvl_split,
-                    &f->lvl_cls, &f->lvl_par, &f->smap, &f->out3, &f->dst};
+  DevBuf* bufs[] = {&f->own_X,     &f->tree_mem, &f->side,      &f->lvl_nodes, &f->lvl_split,
+                    &f->lvl_cls,   &f->lvl_par,  &f->smap,      &f->out3,      &f->dst,
+                    &f->ltiles,    &f->ltile0,   &f->acc_w,     &f->acc_y,     &f->tile_s,
+                    &f->stile0,    &f->tile_left, &f->tile_base, &f->p_lk,     &f->p_wl};
   for (DevBuf* b : bufs) release(*b);
   for (int i = 0; i < 2; ++i) {
     release(f->lX[i]);
@@ -716,7 +767,7 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   f->level.clear();
   cudaError_t e;
   // root entries of every tree: sample ids (+ multiplicities) in lidx[1] / lw[1]
-  int64_t E = 0;
+  int64_t E = 0, ecap = 0;
   const size_t cap = (size_t)n * f->n_trees;
   if ((e = ensure(f->lidx[1], 4 * cap))) return bail(cuda_fail(c, e, "level buffers"));
   if (f->weighted) {
@@ -758,8 +809,11 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
       return bail(cuda_fail(c, e, "bootstrap compaction"));
     }
     cleanup();
-    for (int t = 0; t < f->n_trees; ++t) E += cnt[t];
-    if ((e = ensure(f->lidx[0], 4 * (size_t)E)) || (e = ensure(f->lw[0], 4 * (size_t)E)))
+    for (int t = 0; t < f->n_trees; ++t) E += round4(cnt[t]);
+    ecap = level_capacity(E, f->n_trees, p->max_depth);
+    if ((e = ensure(f->lidx[0], 4 * (size_t)ecap)) || (e = ensure(f->lw[0], 4 * (size_t)ecap)) ||
+        (e = cudaMemsetAsync(f->lidx[0].p, 0, 4 * (size_t)ecap, c->stream)) ||
+        (e = cudaMemsetAsync(f->lw[0].p, 0, 4 * (size_t)ecap, c->stream)))
       return bail(cuda_fail(c, e, "level buffers"));
     int64_t pos = 0;
     for (int t = 0; t < f->n_trees; ++t) {
@@ -771,29 +825,41 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
                                cudaMemcpyDeviceToDevice, c->stream)))
         return bail(cuda_fail(c, e, "bag packing"));
       f->level.push_back(LevelNode{(int32_t)pos, cnt[t], t * f->H, 0});
-      pos += cnt[t];
+      pos += round4(cnt[t]);
     }
   } else {
-    E = (int64_t)cap;
-    if ((e = ensure(f->lidx[0], 4 * (size_t)E))) return bail(cuda_fail(c, e, "level buffers"));
+    const int64_t n4 = round4(n);
+    E = n4 * f->n_trees;
+    ecap = level_capacity(E, f->n_trees, p->max_depth);
+    if ((e = ensure(f->lidx[0], 4 * (size_t)ecap)) ||
+        (e = cudaMemsetAsync(f->lidx[0].p, 0, 4 * (size_t)ecap, c->stream)))
+      return bail(cuda_fail(c, e, "level buffers"));
     c->launches += 1;
-    if ((e = launch_iota(static_cast<int32_t*>(f->lidx[0].p), n, f->n_trees, c->stream)))
+    if ((e = launch_iota(static_cast<int32_t*>(f->lidx[0].p), n, n4, f->n_trees, c->stream)))
       return bail(cuda_fail(c, e, "iota"));
     for (int t = 0; t < f->n_trees; ++t)
-      f->level.push_back(LevelNode{(int32_t)(t * n), (int32_t)n, t * f->H, 0});
+      f->level.push_back(LevelNode{(int32_t)(t * n4), (int32_t)n, t * f->H, 0});
   }
-  // level-resident arrays sized for the root's entries (levels only shrink)
+  // level-resident arrays; every node segment starts at a multiple of 4
+  // entries (16 bytes), with room for the padding of a full level
   for (int i = 0; i < 2; ++i) {
-    if ((e = ensure(f->lX[i], sizeof(float) * (size_t)E * d)) ||
-        (e = ensure(f->lidx[i], sizeof(int32_t) * (size_t)E)) ||
-        (dlab && (e = ensure(f->lab[i], sizeof(int32_t) * (size_t)E))) ||
-        (dy && (e = ensure(f->ly[i], sizeof(float) * (size_t)E))) ||
-        (f->weighted && (e = ensure(f->lw[i], sizeof(uint32_t) * (size_t)E))))
+    if ((e = ensure(f->lX[i], sizeof(float) * (size_t)ecap * d)) ||
+        (e = ensure(f->lidx[i], sizeof(int32_t) * (size_t)ecap)) ||
+        (dlab && (e = ensure(f->lab[i], sizeof(int32_t) * (size_t)ecap))) ||
+        (dy && (e = ensure(f->ly[i], sizeof(float) * (size_t)ecap))) ||
+        (f->weighted && (e = ensure(f->lw[i], sizeof(uint32_t) * (size_t)ecap))))
       return bail(cuda_fail(c, e, "level buffers"));
   }
-  if ((e = ensure(f->side, (size_t)E))) return bail(cuda_fail(c, e, "level buffers"));
+  for (int i = 0; i < 2; ++i) {  // padding entries hold defined values
+    if ((dlab && (e = cudaMemsetAsync(f->lab[i].p, 0, sizeof(int32_t) * (size_t)ecap, c->stream))) ||
+        (dy && (e = cudaMemsetAsync(f->ly[i].p, 0, sizeof(float) * (size_t)ecap, c->stream))) ||
+        (i == 1 && f->weighted &&
+         (e = cudaMemsetAsync(f->lw[i].p, 0, sizeof(uint32_t) * (size_t)ecap, c->stream))))
+      return bail(cuda_fail(c, e, "level buffers"));
+  }
+  if ((e = ensure(f->side, (size_t)ecap))) return bail(cuda_fail(c, e, "level buffers"));
   c->launches += 1;
-  if ((e = launch_gather(dX, dlab, dy, static_cast<int32_t*>(f->lidx[0].p), E, d,
+  if ((e = launch_gather(dX, dlab, dy, static_cast<int32_t*>(f->lidx[0].p), ecap, d,
                          static_cast<float*>(f->lX[0].p),
                          dlab ? static_cast<int32_t*>(f->lab[0].p) : nullptr,
                          dy ? static_cast<float*>(f->ly[0].p) : nullptr, c->stream)) ||
@@ -825,19 +891,55 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
                             f->weighted ? static_cast<uint32_t*>(f->lw[cu].p) : nullptr, E,
                             p->n_particles);
 
-  // 1. statistics and leaf values of every node of the level
+  // 1. statistics and leaf values of every node of the level (per tile)
+  std::vector<WorkTile> ltiles;
+  std::vector<int32_t> ltile0(L + 1);
+  for (int l = 0; l < L; ++l) {
+    ltile0[l] = (int32_t)ltiles.size();
+    const LevelNode& ln = f->level[l];
+    for (int s = 0; s < ln.seg_len; s += kTS)
+      ltiles.push_back(WorkTile{l, ln.seg_start + s, std::min(kTS, ln.seg_len - s), 0});
+  }
+  ltile0[L] = (int32_t)ltiles.size();
+  const int n_lt = (int)ltiles.size();
   CK(ensure(f->lvl_nodes, sizeof(LevelNode) * L));
   CK(ensure(f->lvl_split, sizeof(int32_t) * L));
-  CK(ensure(f->lvl_cls, sizeof(uint32_t) * (size_t)L * K));
+  CK(ensure(f->lvl_cls, sizeof(unsigned long long) * (size_t)L * K));
   CK(ensure(f->lvl_par, sizeof(double) * 2 * (size_t)L));
+  CK(ensure(f->ltiles, sizeof(WorkTile) * n_lt));
+  CK(ensure(f->ltile0, sizeof(int32_t) * (L + 1)));
+  CK(ensure(f->acc_w, sizeof(unsigned long long) * L));
+  CK(ensure(f->acc_y, sizeof(int32_t) * 2 * L));
+  CK(ensure(f->tile_s, sizeof(double) * 2 * (size_t)n_lt));
   CK(cudaMemcpyAsync(f->lvl_nodes.p, f->level.data(), sizeof(LevelNode) * L,
                      cudaMemcpyHostToDevice, c->stream));
+  if (n_lt)
+    CK(cudaMemcpyAsync(f->ltiles.p, ltiles.data(), sizeof(WorkTile) * n_lt,
+                       cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(f->ltile0.p, ltile0.data(), sizeof(int32_t) * (L + 1),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(f->lvl_cls.p, 0, sizeof(unsigned long long) * (size_t)L * K, c->stream));
+  CK(cudaMemsetAsync(f->acc_w.p, 0, sizeof(unsigned long long) * L, c->stream));
+  {
+    std::vector<int32_t> yinit(2 * (size_t)L);
+    for (int l = 0; l < L; ++l) {
+      yinit[l] = INT32_MAX;
+      yinit[L + l] = INT32_MIN;
+    }
+    CK(cudaMemcpyAsync(f->acc_y.p, yinit.data(), sizeof(int32_t) * 2 * L,
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+  LevelAcc lacc{static_cast<unsigned long long*>(f->lvl_cls.p),
+                static_cast<unsigned long long*>(f->acc_w.p), static_cast<int32_t*>(f->acc_y.p),
+                static_cast<int32_t*>(f->acc_y.p) + L, static_cast<double*>(f->tile_s.p)};
   CK(launch(c, SLM_K_NODE_STATS, 0.0, [&] {
-    return launch_node_stats(pr, static_cast<LevelNode*>(f->lvl_nodes.p), L, f->tr,
-                             p->max_depth, static_cast<uint32_t*>(f->lvl_cls.p),
+    return launch_node_stats(pr, static_cast<LevelNode*>(f->lvl_nodes.p), L,
+                             static_cast<WorkTile*>(f->ltiles.p), n_lt,
+                             static_cast<int32_t*>(f->ltile0.p), lacc, f->tr, p->max_depth,
                              static_cast<double*>(f->lvl_par.p),
                              static_cast<int32_t*>(f->lvl_split.p), c->stream);
   }));
+  c->launches += 1;  // the per-node finishing kernel
   std::vector<int32_t> splittable(L);
   CK(cudaMemcpyAsync(splittable.data(), f->lvl_split.p, sizeof(int32_t) * L,
                      cudaMemcpyDeviceToHost, c->stream));
@@ -846,6 +948,8 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   // 2. swarm search of the splittable nodes, all in one batch
   std::vector<NodeDesc> snodes;
   std::vector<int32_t> smap;
+  std::vector<int32_t> stile0;
+  int32_t n_st = 0;
   for (int l = 0; l < L; ++l) {
     if (!splittable[l]) continue;
     const LevelNode& ln = f->level[l];
@@ -853,7 +957,10 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     snodes.push_back(NodeDesc{ln.seg_start, ln.seg_len,
                               ((uint32_t)tree << 16) | (uint32_t)h, ln.slot});
     smap.push_back(l);
+    stile0.push_back(n_st);
+    n_st += (ln.seg_len + kTS - 1) / kTS;  // the tiles plan_tiles makes
   }
+  stile0.push_back(n_st);
   const int A = (int)snodes.size();
   if (A == 0) {
     f->done = true;
@@ -862,24 +969,43 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   }
   Swarm sw;
   if (slm_status s = run_search(c, p, pr, snodes, false, &sw)) return s;
+  if (slm_status s = check_kernel_errors(c)) return s;
   for (const NodeDesc& nd : snodes)
     f->evaluations += (int64_t)nd.seg_len * p->n_particles * (p->n_iters + 1);
 
-  // 3. partition on gB, zero-gain test, internal-node fields
+  // 3. partition on gB (per tile), zero-gain test and tree fields (per node)
   CK(ensure(f->smap, sizeof(int32_t) * A));
   CK(ensure(f->out3, sizeof(int32_t) * 3 * A));
   CK(ensure(f->dst, sizeof(int32_t) * 2 * A));
+  CK(ensure(f->stile0, sizeof(int32_t) * (A + 1)));
+  CK(ensure(f->tile_left, sizeof(int32_t) * (size_t)n_st));
+  CK(ensure(f->tile_base, sizeof(int32_t) * (size_t)n_st));
+  CK(ensure(f->p_lk, sizeof(unsigned long long) * (size_t)A * K));
+  CK(ensure(f->p_wl, sizeof(unsigned long long) * A));
   CK(cudaMemcpyAsync(f->smap.p, smap.data(), sizeof(int32_t) * A, cudaMemcpyHostToDevice,
                      c->stream));
+  CK(cudaMemcpyAsync(f->stile0.p, stile0.data(), sizeof(int32_t) * (A + 1),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(f->p_lk.p, 0, sizeof(unsigned long long) * (size_t)A * K, c->stream));
+  CK(cudaMemsetAsync(f->p_wl.p, 0, sizeof(unsigned long long) * A, c->stream));
   if (slm_status s = reset_status(c)) return s;
   const NodeDesc* dsn = ws_ptr<NodeDesc>(c, S_NODES);
+  const WorkTile* dst_tiles = ws_ptr<WorkTile>(c, S_TILES);
+  PartAcc pacc{static_cast<unsigned long long*>(f->p_lk.p),
+               static_cast<unsigned long long*>(f->p_wl.p)};
   CK(launch(c, SLM_K_PARTITION, 0.0, [&] {
-    return launch_partition(pr, sw, dsn, static_cast<int32_t*>(f->smap.p), A,
-                            static_cast<uint32_t*>(f->lvl_cls.p),
-                            static_cast<double*>(f->lvl_par.p), f->tr,
-                            static_cast<uint8_t*>(f->side.p),
-                            static_cast<int32_t*>(f->out3.p),
-                            ws_ptr<int32_t>(c, S_STATUS), c->stream);
+    return launch_partition(pr, sw, dst_tiles, n_st, static_cast<uint8_t*>(f->side.p),
+                            static_cast<int32_t*>(f->tile_left.p), pacc, c->stream);
+  }));
+  CK(launch(c, SLM_K_PARTITION, 0.0, [&] {
+    return launch_decide(pr, sw, dsn, static_cast<int32_t*>(f->smap.p),
+                         static_cast<int32_t*>(f->stile0.p), A,
+                         static_cast<int32_t*>(f->tile_left.p),
+                         static_cast<int32_t*>(f->tile_base.p),
+                         static_cast<unsigned long long*>(f->lvl_cls.p),
+                         static_cast<double*>(f->lvl_par.p), pacc, f->tr,
+                         static_cast<int32_t*>(f->out3.p), ws_ptr<int32_t>(c, S_STATUS),
+                         c->stream);
   }));
   std::vector<int32_t> o3(3 * (size_t)A);
   CK(cudaMemcpyAsync(o3.data(), f->out3.p, sizeof(int32_t) * 3 * A, cudaMemcpyDeviceToHost,
@@ -888,7 +1014,7 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   if (slm_status s = read_status(c, &st)) return s;
   if (st) return fail(c, SLM_ECUDA, "partition disagrees with the scored split");
 
-  // 4. next level: children of split nodes, compacted stably
+  // 4. next level: children of split nodes, scattered stably
   std::vector<LevelNode> next;
   std::vector<int32_t> dst(2 * (size_t)A, -1);
   int32_t pos = 0, n_split = 0;
@@ -897,11 +1023,12 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     const LevelNode& ln = f->level[smap[a]];
     const int tree = ln.slot / f->H, h = ln.slot % f->H;
     const int32_t nl = o3[3 * a + 1], nr = o3[3 * a + 2];
+    const int32_t pr_ = (int32_t)round4(pos + nl);  // children start on 16-byte boundaries
     dst[2 * a] = pos;
-    dst[2 * a + 1] = pos + nl;
+    dst[2 * a + 1] = pr_;
     next.push_back(LevelNode{pos, nl, tree * f->H + 2 * h + 1, ln.depth + 1});
-    next.push_back(LevelNode{pos + nl, nr, tree * f->H + 2 * h + 2, ln.depth + 1});
-    pos += nl + nr;
+    next.push_back(LevelNode{pr_, nr, tree * f->H + 2 * h + 2, ln.depth + 1});
+    pos = (int32_t)round4(pr_ + nr);
     ++n_split;
   }
   if (n_split) {
@@ -914,8 +1041,10 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     CK(cudaMemcpyAsync(f->dst.p, dst.data(), sizeof(int32_t) * 2 * A, cudaMemcpyHostToDevice,
                        c->stream));
     CK(launch(c, SLM_K_COMPACT, 0.0, [&] {
-      return launch_compact(pr, dsn, A, static_cast<uint8_t*>(f->side.p),
+      return launch_scatter(pr, dst_tiles, n_st, static_cast<uint8_t*>(f->side.p),
                             static_cast<int32_t*>(f->dst.p),
+                            static_cast<int32_t*>(f->tile_base.p),
+                            static_cast<int32_t*>(f->stile0.p),
                             static_cast<int32_t*>(f->lidx[cu].p), la, c->stream);
     }));
     f->cur = nx;

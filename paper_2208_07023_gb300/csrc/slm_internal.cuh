@@ -66,6 +66,7 @@ struct Problem {
   const float* y;         // [E] targets (MSE) or null
   const uint32_t* w;      // [E] multiplicities or null (= 1)
   int64_t E;              // entries in the batch
+  int64_t Ez;             // row stride of z: E rounded up to a multiple of 4
   int32_t d;
   int32_t crit;           // slm_criterion
   int32_t K;              // classes (1 for MSE)
@@ -90,6 +91,8 @@ struct Swarm {
   double* trace;  // [A, T+1] or null
   int32_t* zmm;   // [A, Pp, 2] ordered-int range of each projection
   float* z;       // [P, E] projections of the current iteration
+  int32_t* done;  // [A] particle groups of the node scored in this iteration
+  int32_t* err;   // kernel error word (3: a bulk copy did not complete)
   int32_t T;
 };
 
@@ -107,13 +110,21 @@ cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
 cudaError_t launch_project(const Problem& pr, const Swarm& sw,
                            const WorkTile* tiles, int n_tiles, int grid_cap,
                            cudaStream_t st);
+// Cluster split S of the histogram kernel for A nodes of at most max_len
+// entries on n_sm SMs, with clusters of at most max_cluster CTAs.
+int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_cluster);
+// Largest power-of-two cluster size (<= 16) of the histogram kernel.
+int hist_max_cluster(const Problem& pr);
 // Scores of every (node, particle); bins_out[P, seg_len] (one node) or null.
+// With do_update, also the swarm update of iteration t (Algorithm 1) by the
+// CTA that finishes each node.
 cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
-                             const NodeDesc* nodes, int A, int32_t* bins_out,
-                             cudaStream_t st);
-cudaError_t launch_swarm_update(const Problem& pr, const Swarm& sw,
-                                const NodeDesc* nodes, int A, int t,
-                                SwarmCoef co, cudaStream_t st);
+                             const NodeDesc* nodes, int A, int S,
+                             int32_t* bins_out, int t, SwarmCoef co,
+                             int do_update, cudaStream_t st);
+// Eq. pso-1 move of every particle of A nodes to iteration t+1.
+cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                        int A, int t, SwarmCoef co, cudaStream_t st);
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
                                   int P, int d, uint32_t purpose, float* u,
                                   cudaStream_t st);
@@ -152,20 +163,20 @@ struct TreeArrays {
 cudaError_t launch_gather(const float* X, const int32_t* labels, const float* y,
                           const int32_t* idx, int64_t E, int d, float* Xl,
                           int32_t* lab_l, float* y_l, cudaStream_t st);
-// Per-level node statistics: writes the leaf fields of every level node and
-// splittable[L]; cls[L*K] class counts, par[L*2] (sum w y, sum w y^2).
-cudaError_t launch_node_stats(const Problem& pr, const LevelNode* nodes, int L,
-                              TreeArrays tr, int max_depth, uint32_t* cls,
-                              double* par, int32_t* splittable,
-                              cudaStream_t st);
-// For every searched node: side of each entry under gB, the zero-gain test,
-// and the internal-node fields of split nodes. map[A] = level node of search
-// node a. out3[A*3] = {split?, left entries, right entries}.
-cudaError_t launch_partition(const Problem& pr, const Swarm& sw,
-                             const NodeDesc* snodes, const int32_t* map, int A,
-                             const uint32_t* cls, const double* par,
-                             TreeArrays tr, uint8_t* side, int32_t* out3,
-                             int32_t* status, cudaStream_t st);
+// Per-node accumulators of the level statistics (zeroed before use, except
+// ylo / yhi which start at INT_MAX / INT_MIN).
+struct LevelAcc {
+  unsigned long long* cls;  // [L, K] weighted class counts
+  unsigned long long* w;    // [L] weight
+  int32_t* ylo;             // [L] ordered-int target range (MSE)
+  int32_t* yhi;
+  double* tile_s;           // [n_tiles, 2] per-tile sum w y, sum w y^2
+};
+// Per-searched-node accumulators of the partition (zeroed before use).
+struct PartAcc {
+  unsigned long long* lk;   // [A, K] weighted left class counts
+  unsigned long long* wl;   // [A] weighted left count
+};
 // Level arrays of one side of the ping-pong.
 struct LevelArrays {
   float* X;
@@ -174,11 +185,32 @@ struct LevelArrays {
   uint32_t* w;
   int32_t* idx;
 };
-// Stable compaction of split nodes' entries (rows, labels / targets,
-// multiplicities, sample ids) into the next level's arrays. dst[A*2] = start
-// of the left / right child segments (-1: not split).
-cudaError_t launch_compact(const Problem& pr, const NodeDesc* snodes, int A,
+
+// Leaf fields of every level node, splittable[L], par[L*2] = parent
+// (sum w y, sum w y^2). tiles / tile0: the level's kTS-row tiles, node l
+// owning tiles [tile0[l], tile0[l+1]).
+cudaError_t launch_node_stats(const Problem& pr, const LevelNode* nodes, int L,
+                              const WorkTile* tiles, int n_tiles,
+                              const int32_t* tile0, LevelAcc acc, TreeArrays tr,
+                              int max_depth, double* par, int32_t* splittable,
+                              cudaStream_t st);
+// Side of each entry of the searched nodes' tiles under gB.
+cudaError_t launch_partition(const Problem& pr, const Swarm& sw,
+                             const WorkTile* tiles, int n_tiles, uint8_t* side,
+                             int32_t* tile_left, PartAcc acc, cudaStream_t st);
+// Per searched node: zero-gain test, tree fields, scatter bases.
+// out3[A*3] = {split?, left entries, right entries}.
+cudaError_t launch_decide(const Problem& pr, const Swarm& sw,
+                          const NodeDesc* snodes, const int32_t* map,
+                          const int32_t* tile0, int A, const int32_t* tile_left,
+                          int32_t* tile_base, const unsigned long long* node_cls,
+                          const double* par, PartAcc acc, TreeArrays tr,
+                          int32_t* out3, int32_t* status, cudaStream_t st);
+// Stable scatter of split nodes' entries into the next level's arrays.
+// dst[A*2] = start of the left / right child segments (-1: not split).
+cudaError_t launch_scatter(const Problem& pr, const WorkTile* tiles, int n_tiles,
                            const uint8_t* side, const int32_t* dst,
+                           const int32_t* tile_base, const int32_t* tile0,
                            const int32_t* idx_cur, LevelArrays next,
                            cudaStream_t st);
 // Root entries of bootstrap trees: for tree t, the samples with w > 0 in
@@ -187,7 +219,8 @@ cudaError_t launch_compact_nonzero(const uint32_t* w_all, int n_trees,
                                    int64_t n, int32_t* idx_out,
                                    uint32_t* w_out, const int64_t* off,
                                    int32_t* counts, cudaStream_t st);
-cudaError_t launch_iota(int32_t* idx, int64_t n, int copies,
+// idx[c * stride + i] = i for i < n, c < copies.
+cudaError_t launch_iota(int32_t* idx, int64_t n, int64_t stride, int copies,
                         cudaStream_t st);
 // Checks labels in [0, K) and sample indices in [0, n); sets *status = 1 on
 // the first violation.

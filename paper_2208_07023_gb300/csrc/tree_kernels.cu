@@ -1,11 +1,16 @@
 // Tree-level kernels: node statistics, partition of searched nodes, stable
-// compaction into the next level, bootstrap bags, prediction.
+// scatter into the next level, gathers, bootstrap bags, prediction.
 //
 // Algorithm 2: a node that meets the split condition is searched, split on
 // gB, and its two children are grown next; otherwise it becomes a leaf.
 // Sec. II-A: leaves predict their majority class (ties: lowest class id);
 // regression leaves predict the mean target. The split sets are Eqs. (3)-(4):
 // right ("+") iff bin(gB . x) >= b*, i.e. z >= t_b.
+//
+// Every per-level pass runs over the same kTS-row tiles of the entry-ordered
+// level arrays (one CTA per tile), followed by a one-thread-per-node kernel
+// where a per-node decision is needed, so shallow levels with a few large
+// nodes keep the whole GPU busy.
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
@@ -16,7 +21,7 @@ namespace slm {
 
 namespace {
 
-constexpr int kTT = 256;  // threads per CTA
+constexpr int kTT = kTS;  // threads per CTA = rows per tile
 
 __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
   const float off = __fsub_rn(z, zmin);
@@ -26,11 +31,15 @@ __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
   return b < 0 ? 0 : b;
 }
 
+__device__ __forceinline__ int f2ord(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
 // gB . x as one fmaf per feature in increasing order from +0, the same
 // sequence the scoring kernels run.
 __device__ __forceinline__ float project_row(const float* __restrict__ x,
-                                             const float* __restrict__ g,
-                                             int d) {
+                                             const float* __restrict__ g, int d) {
   float acc = 0.0f;
   for (int j = 0; j < d; ++j) acc = fmaf(__ldg(x + j), g[j], acc);
   return acc;
@@ -50,7 +59,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total, int* sbuf) {
   if (lane == 31) sbuf[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    int wv = lane < kTT / 32 ? sbuf[lane] : 0;
+    const int wv = lane < kTT / 32 ? sbuf[lane] : 0;
     int wi = wv;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -65,132 +74,183 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total, int* sbuf) {
   return sbuf[warp] + incl - v;
 }
 
+// ---- node statistics (per tile, then per node) ------------------------------------
+
+// Per tile of a level node: weighted class counts and weight (integer global
+// atomics: order-free), target range (ordered-int atomics) and the tile's
+// partial target sums (summed per node in tile order by k_stats_finish).
 __global__ void __launch_bounds__(kTT)
-    k_node_stats(Problem pr, const LevelNode* __restrict__ nodes,
-                 TreeArrays tr, int max_depth, uint32_t* cls, double* par,
-                 int32_t* splittable) {
-  const int l = blockIdx.x;
-  const LevelNode nd = nodes[l];
+    k_stats_tiles(Problem pr, const WorkTile* __restrict__ tiles, LevelAcc acc) {
+  const WorkTile wt = tiles[blockIdx.x];
+  const int K = pr.K;
   __shared__ unsigned long long s_cnt[kMaxClasses];
   __shared__ unsigned long long s_w;
   __shared__ double s_sy[kTT], s_sq[kTT];
-  __shared__ float s_lo[kTT], s_hi[kTT];
-  const int K = pr.K;
+  __shared__ int s_lo, s_hi;
   if (threadIdx.x < kMaxClasses) s_cnt[threadIdx.x] = 0;
-  if (threadIdx.x == 0) s_w = 0;
+  if (threadIdx.x == 0) {
+    s_w = 0;
+    s_lo = INT_MAX;
+    s_hi = INT_MIN;
+  }
   __syncthreads();
-  unsigned long long wsum = 0;
+  const int r = threadIdx.x;
   double sy = 0.0, sq = 0.0;
-  float lo = INFINITY, hi = -INFINITY;
-  for (int r = threadIdx.x; r < nd.seg_len; r += kTT) {
-    const int64_t e = (int64_t)nd.seg_start + r;
+  if (r < wt.rows) {
+    const int64_t e = (int64_t)wt.row0 + r;
     const uint32_t w = pr.w ? pr.w[e] : 1u;
-    wsum += w;
+    atomicAdd(&s_w, (unsigned long long)w);
     if (pr.crit == SLM_MSE) {
       const float yv = pr.y[e];
-      const double wy = (double)w * (double)yv;
-      sy += wy;
-      sq += wy * (double)yv;
-      lo = fminf(lo, yv);
-      hi = fmaxf(hi, yv);
+      sy = (double)w * (double)yv;
+      sq = sy * (double)yv;
+      atomicMin(&s_lo, f2ord(yv));
+      atomicMax(&s_hi, f2ord(yv));
     } else {
       atomicAdd(&s_cnt[pr.lab[e]], (unsigned long long)w);
     }
   }
-  atomicAdd(&s_w, wsum);
   s_sy[threadIdx.x] = sy;
   s_sq[threadIdx.x] = sq;
-  s_lo[threadIdx.x] = lo;
-  s_hi[threadIdx.x] = hi;
   __syncthreads();
-  // fixed-order tree reduction: deterministic sums
-  for (int off = kTT / 2; off > 0; off >>= 1) {
+  for (int off = kTT / 2; off > 0; off >>= 1) {  // fixed order: deterministic
     if (threadIdx.x < off) {
       s_sy[threadIdx.x] += s_sy[threadIdx.x + off];
       s_sq[threadIdx.x] += s_sq[threadIdx.x + off];
-      s_lo[threadIdx.x] = fminf(s_lo[threadIdx.x], s_lo[threadIdx.x + off]);
-      s_hi[threadIdx.x] = fmaxf(s_hi[threadIdx.x], s_hi[threadIdx.x + off]);
     }
     __syncthreads();
   }
+  const int l = wt.node;
+  if (threadIdx.x < K && pr.crit != SLM_MSE && s_cnt[threadIdx.x])
+    atomicAdd(&acc.cls[(int64_t)l * K + threadIdx.x], s_cnt[threadIdx.x]);
   if (threadIdx.x == 0) {
-    const int slot = nd.slot;
-    const unsigned long long nw = s_w;
-    bool pure;
-    if (pr.crit == SLM_MSE) {
-      tr.leaf_value[slot] = nw ? s_sy[0] / (double)nw : 0.0;
-      tr.leaf_class[slot] = -1;
-      pure = !(s_hi[0] > s_lo[0]);
-      par[2 * l] = s_sy[0];
-      par[2 * l + 1] = s_sq[0];
-    } else {
-      int best = 0, nonzero = 0;
-      for (int k = 0; k < K; ++k) {
-        const unsigned long long c = s_cnt[k];
-        cls[(int64_t)l * K + k] = (uint32_t)c;
-        if (c > s_cnt[best]) best = k;
-        nonzero += c > 0;
-      }
-      tr.leaf_class[slot] = best;
-      tr.leaf_value[slot] = 0.0;
-      pure = nonzero <= 1;
+    atomicAdd(&acc.w[l], s_w);
+    acc.tile_s[2 * blockIdx.x] = s_sy[0];
+    acc.tile_s[2 * blockIdx.x + 1] = s_sq[0];
+    if (pr.crit == SLM_MSE && s_lo != INT_MAX) {
+      atomicMin(&acc.ylo[l], s_lo);
+      atomicMax(&acc.yhi[l], s_hi);
     }
-    tr.kind[slot] = 0;
-    tr.weight[slot] = (int64_t)nw;
-    tr.bin[slot] = -1;
-    splittable[l] = (nd.depth < max_depth) &&
-                    nw >= 2ull * (unsigned long long)pr.min_leaf && !pure;
   }
 }
 
+// One thread per level node: leaf value, splittable flag, parent sums.
+__global__ void k_stats_finish(Problem pr, const LevelNode* __restrict__ nodes,
+                               const int32_t* __restrict__ tile0, int L, LevelAcc acc,
+                               TreeArrays tr, int max_depth, double* par,
+                               int32_t* splittable) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  const LevelNode nd = nodes[l];
+  const int K = pr.K;
+  const unsigned long long nw = acc.w[l];
+  const int slot = nd.slot;
+  bool pure;
+  if (pr.crit == SLM_MSE) {
+    double sy = 0.0, sq = 0.0;
+    for (int t = tile0[l]; t < tile0[l + 1]; ++t) {
+      sy += acc.tile_s[2 * t];
+      sq += acc.tile_s[2 * t + 1];
+    }
+    tr.leaf_value[slot] = nw ? sy / (double)nw : 0.0;
+    tr.leaf_class[slot] = -1;
+    pure = !(acc.yhi[l] > acc.ylo[l]);
+    par[2 * l] = sy;
+    par[2 * l + 1] = sq;
+  } else {
+    int best = 0, nonzero = 0;
+    const unsigned long long* c = acc.cls + (int64_t)l * K;
+    for (int k = 0; k < K; ++k) {
+      if (c[k] > c[best]) best = k;
+      nonzero += c[k] > 0;
+    }
+    tr.leaf_class[slot] = best;
+    tr.leaf_value[slot] = 0.0;
+    pure = nonzero <= 1;
+  }
+  tr.kind[slot] = 0;
+  tr.weight[slot] = (int64_t)nw;
+  tr.bin[slot] = -1;
+  splittable[l] = (nd.depth < max_depth) && nw >= 2ull * (unsigned long long)pr.min_leaf &&
+                  !pure;
+}
+
+// ---- partition (per tile), decision (per node), scatter (per tile) --------------
+
+// Side of every entry of a searched node's tile under its gB: right iff
+// bin(gB . x) >= b*. Stores the tile's left-entry count; adds the node's left
+// weight and left class counts.
 __global__ void __launch_bounds__(kTT)
-    k_partition(Problem pr, Swarm sw, const NodeDesc* __restrict__ snodes,
-                const int32_t* __restrict__ map, const uint32_t* cls,
-                const double* par, TreeArrays tr, uint8_t* side, int32_t* out3,
-                int32_t* status) {
-  const int a = blockIdx.x;
-  const NodeDesc nd = snodes[a];
+    k_part_tiles(Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, uint8_t* side,
+                 int32_t* tile_left, PartAcc acc) {
+  const WorkTile wt = tiles[blockIdx.x];
+  const int a = wt.node;
   const EvalRes gb = sw.gb[a];
+  const int d = pr.d, K = pr.K;
   extern __shared__ float s_g[];  // [d]
   __shared__ unsigned long long s_lk[kMaxClasses];
   __shared__ unsigned long long s_wl;
-  __shared__ int s_cnt[kTT / 32 + 1];
-  const int d = pr.d, K = pr.K;
+  __shared__ int s_n;
   if (!gb.valid) {
-    if (threadIdx.x == 0) {
-      out3[3 * a] = 0;
-      out3[3 * a + 1] = 0;
-      out3[3 * a + 2] = 0;
-    }
+    if (threadIdx.x == 0) tile_left[blockIdx.x] = 0;
     return;
   }
   for (int j = threadIdx.x; j < d; j += kTT) s_g[j] = sw.gbest[(int64_t)a * d + j];
   if (threadIdx.x < kMaxClasses) s_lk[threadIdx.x] = 0;
-  if (threadIdx.x == 0) s_wl = 0;
+  if (threadIdx.x == 0) {
+    s_wl = 0;
+    s_n = 0;
+  }
   __syncthreads();
-  int n_left_entries = 0;
-  unsigned long long wl = 0;
-  for (int r = threadIdx.x; r < nd.seg_len; r += kTT) {
-    const int64_t e = (int64_t)nd.seg_start + r;
+  const int r = threadIdx.x;
+  if (r < wt.rows) {
+    const int64_t e = (int64_t)wt.row0 + r;
     const float z = project_row(pr.X + e * d, s_g, d);
     const int b = bin_of(z, gb.zmin, gb.inv_w, pr.B);
     const int right = b >= gb.bin;
     side[e] = (uint8_t)right;
     if (!right) {
       const uint32_t w = pr.w ? pr.w[e] : 1u;
-      ++n_left_entries;
-      wl += w;
+      atomicAdd(&s_n, 1);
+      atomicAdd(&s_wl, (unsigned long long)w);
       if (pr.crit != SLM_MSE) atomicAdd(&s_lk[pr.lab[e]], (unsigned long long)w);
     }
   }
-  atomicAdd(&s_wl, wl);
-  int total_left;
-  block_excl_scan(n_left_entries, &total_left, s_cnt);
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x < K && pr.crit != SLM_MSE && s_lk[threadIdx.x])
+    atomicAdd(&acc.lk[(int64_t)a * K + threadIdx.x], s_lk[threadIdx.x]);
+  if (threadIdx.x == 0) {
+    tile_left[blockIdx.x] = s_n;
+    if (s_wl) atomicAdd(&acc.wl[a], s_wl);
+  }
+}
+
+// One thread per searched node: zero-gain test, internal-node fields, tile
+// bases of the scatter. out3[a] = {split?, left entries, right entries}.
+__global__ void k_decide(Problem pr, Swarm sw, const NodeDesc* __restrict__ snodes,
+                         const int32_t* __restrict__ map, const int32_t* __restrict__ tile0,
+                         int A, const int32_t* __restrict__ tile_left, int32_t* tile_base,
+                         const unsigned long long* __restrict__ node_cls,
+                         const double* __restrict__ par, PartAcc acc, TreeArrays tr,
+                         int32_t* out3, int32_t* status) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= A) return;
+  const NodeDesc nd = snodes[a];
+  const EvalRes gb = sw.gb[a];
+  const int d = pr.d, K = pr.K;
+  int nl_entries = 0;
+  for (int t = tile0[a]; t < tile0[a + 1]; ++t) {
+    tile_base[t] = nl_entries;
+    nl_entries += gb.valid ? tile_left[t] : 0;
+  }
+  out3[3 * a + 1] = nl_entries;
+  out3[3 * a + 2] = nd.seg_len - nl_entries;
+  if (!gb.valid) {
+    out3[3 * a] = 0;
+    return;
+  }
   const int l = map[a];
-  const int slot = nd.slot;
-  const unsigned long long wleft = s_wl;
+  const unsigned long long wleft = acc.wl[a];
   const unsigned long long nw = (unsigned long long)(gb.nl + gb.nr);
   if (wleft != (unsigned long long)gb.nl) atomicExch(status, 2);  // must agree
   // Zero gain: children keep the parent's class mix (Gini and entropy are
@@ -203,15 +263,14 @@ __global__ void __launch_bounds__(kTT)
   } else {
     no_gain = true;
     for (int k = 0; k < K; ++k)
-      if (s_lk[k] * nw != (unsigned long long)cls[(int64_t)l * K + k] * wleft)
+      if (acc.lk[(int64_t)a * K + k] * nw != node_cls[(int64_t)l * K + k] * wleft)
         no_gain = false;
   }
   out3[3 * a] = no_gain ? 0 : 1;
-  out3[3 * a + 1] = total_left;
-  out3[3 * a + 2] = nd.seg_len - total_left;
   if (no_gain) return;
+  const int slot = nd.slot;
   tr.kind[slot] = 1;
-  for (int j = 0; j < d; ++j) tr.dir[(int64_t)slot * d + j] = s_g[j];
+  for (int j = 0; j < d; ++j) tr.dir[(int64_t)slot * d + j] = sw.gbest[(int64_t)a * d + j];
   tr.zmin[slot] = gb.zmin;
   tr.inv_w[slot] = gb.inv_w;
   tr.bin[slot] = gb.bin;
@@ -220,46 +279,65 @@ __global__ void __launch_bounds__(kTT)
   tr.n_right[slot] = gb.nr;
 }
 
+// Stable scatter of a split node's tile into its children's segments:
+// rows, labels / targets, multiplicities and sample ids.
 __global__ void __launch_bounds__(kTT)
-    k_compact(Problem pr, const NodeDesc* __restrict__ snodes,
-              const uint8_t* __restrict__ side, const int32_t* __restrict__ dst,
-              const int32_t* __restrict__ idx_cur, LevelArrays nx) {
-  const int a = blockIdx.x;
+    k_scatter(Problem pr, const WorkTile* __restrict__ tiles, const uint8_t* __restrict__ side,
+              const int32_t* __restrict__ dst, const int32_t* __restrict__ tile_base,
+              const int32_t* __restrict__ tile0, const int32_t* __restrict__ idx_cur,
+              LevelArrays nx) {
+  const WorkTile wt = tiles[blockIdx.x];
+  const int a = wt.node;
   const int dl = dst[2 * a], dr = dst[2 * a + 1];
   if (dl < 0) return;
-  const NodeDesc nd = snodes[a];
   const int d = pr.d;
   __shared__ int sbuf[kTT / 32 + 1];
   __shared__ int s_dst[kTT];
-  int base_l = 0, base_r = 0;
-  for (int t0 = 0; t0 < nd.seg_len; t0 += kTT) {
-    const int r = t0 + threadIdx.x;
-    const bool in = r < nd.seg_len;
-    const int64_t e = (int64_t)nd.seg_start + r;
-    const int right = in ? side[e] : 0;
-    const int is_left = in && !right;
-    int tot_l;
-    const int rank_l = block_excl_scan(is_left, &tot_l, sbuf);
-    const int n_in = min(kTT, nd.seg_len - t0);
-    const int rank_r = threadIdx.x - rank_l;  // entries before r that went right
-    if (in) {
-      const int32_t pos = is_left ? dl + base_l + rank_l : dr + base_r + rank_r;
-      s_dst[threadIdx.x] = pos;
-      nx.idx[pos] = idx_cur[e];
-      if (nx.lab) nx.lab[pos] = pr.lab[e];
-      if (nx.y) nx.y[pos] = pr.y[e];
-      if (nx.w) nx.w[pos] = pr.w[e];
-    }
-    __syncthreads();
-    // rows: coalesced copies, one row per group of threads
-    for (int q = threadIdx.x; q < n_in * d; q += kTT) {
-      const int rr = q / d, j = q - rr * d;
-      nx.X[(int64_t)s_dst[rr] * d + j] = pr.X[((int64_t)nd.seg_start + t0 + rr) * d + j];
-    }
-    __syncthreads();
-    base_l += tot_l;
-    base_r += n_in - tot_l;
+  const int r = threadIdx.x;
+  const bool in = r < wt.rows;
+  const int64_t e = (int64_t)wt.row0 + r;
+  const int is_left = in && !side[e];
+  int tot_l;
+  const int rank_l = block_excl_scan(is_left, &tot_l, sbuf);
+  const int base_l = tile_base[blockIdx.x];
+  const int rows_before = ((int)blockIdx.x - tile0[a]) * kTS;  // full tiles
+  const int base_r = rows_before - base_l;
+  if (in) {
+    const int32_t pos = is_left ? dl + base_l + rank_l : dr + base_r + (r - rank_l);
+    s_dst[r] = pos;
+    nx.idx[pos] = idx_cur[e];
+    if (nx.lab) nx.lab[pos] = pr.lab[e];
+    if (nx.y) nx.y[pos] = pr.y[e];
+    if (nx.w) nx.w[pos] = pr.w[e];
   }
+  __syncthreads();
+  for (int q = threadIdx.x; q < wt.rows * d; q += kTT) {
+    const int rr = q / d, j = q - rr * d;
+    nx.X[(int64_t)s_dst[rr] * d + j] = pr.X[((int64_t)wt.row0 + rr) * d + j];
+  }
+}
+
+__global__ void __launch_bounds__(kTT)
+    k_compact_nonzero(const uint32_t* __restrict__ w_all, int64_t n, int32_t* idx_out,
+                      uint32_t* w_out, const int64_t* __restrict__ off, int32_t* counts) {
+  const int t = blockIdx.x;
+  const uint32_t* w = w_all + (int64_t)t * n;
+  __shared__ int sbuf[kTT / 32 + 1];
+  const int64_t base = off[t];
+  int count = 0;
+  for (int64_t s0 = 0; s0 < n; s0 += kTT) {
+    const int64_t s = s0 + threadIdx.x;
+    const uint32_t ws = s < n ? w[s] : 0u;
+    const int nz = ws > 0;
+    int tot;
+    const int rank = block_excl_scan(nz, &tot, sbuf);
+    if (nz) {
+      idx_out[base + count + rank] = (int32_t)s;
+      w_out[base + count + rank] = ws;
+    }
+    count += tot;
+  }
+  if (threadIdx.x == 0) counts[t] = count;
 }
 
 __global__ void k_gather(const float* __restrict__ X, const int32_t* __restrict__ labels,
@@ -277,37 +355,16 @@ __global__ void k_gather(const float* __restrict__ X, const int32_t* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(kTT)
-    k_compact_nonzero(const uint32_t* __restrict__ w_all, int64_t n,
-                      int32_t* idx_out, uint32_t* w_out,
-                      const int64_t* __restrict__ off, int32_t* counts) {
-  const int t = blockIdx.x;
-  const uint32_t* w = w_all + (int64_t)t * n;
-  __shared__ int sbuf[kTT / 32 + 1];
-  int64_t base = off[t];
-  int count = 0;
-  for (int64_t s0 = 0; s0 < n; s0 += kTT) {
-    const int64_t s = s0 + threadIdx.x;
-    const uint32_t ws = s < n ? w[s] : 0u;
-    const int nz = ws > 0;
-    int tot;
-    const int rank = block_excl_scan(nz, &tot, sbuf);
-    if (nz) {
-      idx_out[base + count + rank] = (int32_t)s;
-      w_out[base + count + rank] = ws;
-    }
-    count += tot;
-  }
-  if (threadIdx.x == 0) counts[t] = count;
-}
-
-__global__ void k_iota(int32_t* idx, int64_t n, int copies) {
+// idx[c * stride + i] = i for i < n, c < copies.
+__global__ void k_iota(int32_t* idx, int64_t n, int64_t stride, int copies) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n * copies) idx[i] = (int32_t)(i % n);
+  if (i >= n * copies) return;
+  const int64_t cpy = i / n, r = i - cpy * n;
+  idx[cpy * stride + r] = (int32_t)r;
 }
 
-__global__ void k_validate(const int32_t* labels, int64_t n, int K,
-                           const int32_t* idx, int64_t n_idx, int32_t* status) {
+__global__ void k_validate(const int32_t* labels, int64_t n, int K, const int32_t* idx,
+                           int64_t n_idx, int32_t* status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (labels && i < n) {
     const int32_t c = labels[i];
@@ -319,10 +376,9 @@ __global__ void k_validate(const int32_t* labels, int64_t n, int K,
   }
 }
 
-__global__ void k_predict(const float* __restrict__ X, int64_t n, int d,
-                          TreeArrays tr, int n_trees, int H, int B, int K,
-                          int crit, int32_t* class_out, double* value_out,
-                          int32_t* leaf_out) {
+__global__ void k_predict(const float* __restrict__ X, int64_t n, int d, TreeArrays tr,
+                          int n_trees, int H, int B, int K, int crit, int32_t* class_out,
+                          double* value_out, int32_t* leaf_out) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const float* x = X + s * d;
@@ -361,39 +417,59 @@ __global__ void k_predict(const float* __restrict__ X, int64_t n, int d,
 }  // namespace
 
 cudaError_t launch_node_stats(const Problem& pr, const LevelNode* nodes, int L,
-                              TreeArrays tr, int max_depth, uint32_t* cls,
-                              double* par, int32_t* splittable,
-                              cudaStream_t st) {
+                              const WorkTile* tiles, int n_tiles, const int32_t* tile0,
+                              LevelAcc acc, TreeArrays tr, int max_depth, double* par,
+                              int32_t* splittable, cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
-  k_node_stats<<<L, kTT, 0, st>>>(pr, nodes, tr, max_depth, cls, par,
-                                  splittable);
+  if (n_tiles > 0) k_stats_tiles<<<n_tiles, kTT, 0, st>>>(pr, tiles, acc);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  k_stats_finish<<<(L + 127) / 128, 128, 0, st>>>(pr, nodes, tile0, L, acc, tr, max_depth,
+                                                  par, splittable);
   return cudaGetLastError();
 }
 
-cudaError_t launch_partition(const Problem& pr, const Swarm& sw,
-                             const NodeDesc* snodes, const int32_t* map, int A,
-                             const uint32_t* cls, const double* par,
-                             TreeArrays tr, uint8_t* side, int32_t* out3,
-                             int32_t* status, cudaStream_t st) {
+cudaError_t launch_partition(const Problem& pr, const Swarm& sw, const WorkTile* tiles,
+                             int n_tiles, uint8_t* side, int32_t* tile_left, PartAcc acc,
+                             cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  k_part_tiles<<<n_tiles, kTT, sizeof(float) * pr.d, st>>>(pr, sw, tiles, side, tile_left,
+                                                            acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide(const Problem& pr, const Swarm& sw, const NodeDesc* snodes,
+                          const int32_t* map, const int32_t* tile0, int A,
+                          const int32_t* tile_left, int32_t* tile_base,
+                          const unsigned long long* node_cls, const double* par,
+                          PartAcc acc, TreeArrays tr, int32_t* out3, int32_t* status,
+                          cudaStream_t st) {
   if (A <= 0) return cudaSuccess;
-  k_partition<<<A, kTT, sizeof(float) * pr.d, st>>>(pr, sw, snodes, map, cls,
-                                                     par, tr, side, out3,
-                                                     status);
+  k_decide<<<(A + 127) / 128, 128, 0, st>>>(pr, sw, snodes, map, tile0, A, tile_left,
+                                            tile_base, node_cls, par, acc, tr, out3, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Problem& pr, const NodeDesc* snodes, int A,
-                           const uint8_t* side, const int32_t* dst,
-                           const int32_t* idx_cur, LevelArrays next,
+cudaError_t launch_scatter(const Problem& pr, const WorkTile* tiles, int n_tiles,
+                           const uint8_t* side, const int32_t* dst, const int32_t* tile_base,
+                           const int32_t* tile0, const int32_t* idx_cur, LevelArrays next,
                            cudaStream_t st) {
-  if (A <= 0) return cudaSuccess;
-  k_compact<<<A, kTT, 0, st>>>(pr, snodes, side, dst, idx_cur, next);
+  if (n_tiles <= 0) return cudaSuccess;
+  k_scatter<<<n_tiles, kTT, 0, st>>>(pr, tiles, side, dst, tile_base, tile0, idx_cur, next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_nonzero(const uint32_t* w_all, int n_trees, int64_t n,
+                                   int32_t* idx_out, uint32_t* w_out, const int64_t* off,
+                                   int32_t* counts, cudaStream_t st) {
+  if (n_trees <= 0) return cudaSuccess;
+  k_compact_nonzero<<<n_trees, kTT, 0, st>>>(w_all, n, idx_out, w_out, off, counts);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const float* X, const int32_t* labels, const float* y,
-                          const int32_t* idx, int64_t E, int d, float* Xl,
-                          int32_t* lab_l, float* y_l, cudaStream_t st) {
+                          const int32_t* idx, int64_t E, int d, float* Xl, int32_t* lab_l,
+                          float* y_l, cudaStream_t st) {
   const int64_t total = E * d;
   if (total <= 0) return cudaSuccess;
   k_gather<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, labels, y, idx, E, d, Xl,
@@ -401,40 +477,28 @@ cudaError_t launch_gather(const float* X, const int32_t* labels, const float* y,
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact_nonzero(const uint32_t* w_all, int n_trees,
-                                   int64_t n, int32_t* idx_out,
-                                   uint32_t* w_out, const int64_t* off,
-                                   int32_t* counts, cudaStream_t st) {
-  if (n_trees <= 0) return cudaSuccess;
-  k_compact_nonzero<<<n_trees, kTT, 0, st>>>(w_all, n, idx_out, w_out, off,
-                                             counts);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_iota(int32_t* idx, int64_t n, int copies, cudaStream_t st) {
+cudaError_t launch_iota(int32_t* idx, int64_t n, int64_t stride, int copies,
+                        cudaStream_t st) {
   const int64_t total = n * copies;
   if (total <= 0) return cudaSuccess;
-  k_iota<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(idx, n, copies);
+  k_iota<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(idx, n, stride, copies);
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate(const int32_t* labels, int64_t n, int K,
-                            const int32_t* idx, int64_t n_idx,
-                            int32_t* status, cudaStream_t st) {
+cudaError_t launch_validate(const int32_t* labels, int64_t n, int K, const int32_t* idx,
+                            int64_t n_idx, int32_t* status, cudaStream_t st) {
   const int64_t m = (labels && n > n_idx) ? n : n_idx;
   if (m <= 0) return cudaSuccess;
-  k_validate<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(labels, n, K, idx,
-                                                          n_idx, status);
+  k_validate<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(labels, n, K, idx, n_idx, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr,
-                           int n_trees, int H, int B, int K, int crit,
-                           int32_t* class_out, double* value_out,
-                           int32_t* leaf_out, cudaStream_t st) {
+cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr, int n_trees,
+                           int H, int B, int K, int crit, int32_t* class_out,
+                           double* value_out, int32_t* leaf_out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_predict<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
-      X, n, d, tr, n_trees, H, B, K, crit, class_out, value_out, leaf_out);
+  k_predict<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(X, n, d, tr, n_trees, H, B, K, crit,
+                                                        class_out, value_out, leaf_out);
   return cudaGetLastError();
 }
 
