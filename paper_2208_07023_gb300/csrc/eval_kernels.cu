@@ -127,171 +127,264 @@ __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
 
 constexpr int kMaxBPL = kMaxBins / 32;
 
-// Classification. h: [B][K] counts of one particle.
-__device__ EvalRes scan_cls(const uint32_t* h, int B, int K, int min_leaf,
-                            int crit) {
-  const int lane = threadIdx.x & 31;
-  const int BPL = (B + 31) >> 5;
-  const int j0 = lane * BPL;
-  uint32_t nL[kMaxBPL];
-  uint64_t SL[kMaxBPL], SR[kMaxBPL];
-  double hL[kMaxBPL], hR[kMaxBPL];
+// Shared scratch of the block-wide scans.
+struct ScanScratch {
+  uint32_t nl[kMaxBins];  // left weight of each edge (classification)
+  uint32_t pc[kMaxBins];  // MSE prefix: weight
+  double ps[kMaxBins];    // MSE prefix: sum w y
+  double pq[kMaxBins];    // MSE prefix: sum w y^2
+  uint64_t wn[kThreads / 32], wd[kThreads / 32];
+  double wl[kThreads / 32];
+  int wb[kThreads / 32];
+  EvalRes res;
+};
+
+// Ties: the lower edge. Gini scores are rationals n/d (larger is better),
+// the others losses (smaller is better).
+template <int CRIT>
+__device__ __forceinline__ bool edge_takes(uint64_t on, uint64_t od, double ol, int ob, uint64_t bn,
+                                           uint64_t bd, double bl, int bb) {
+  if (ob < 0) return false;
+  if (bb < 0) return true;
+  if (CRIT == SLM_GINI) return prod_gt(on, bd, bn, od) || (!prod_gt(bn, od, on, bd) && ob < bb);
+  return ol < bl || (!(bl < ol) && ob < bb);
+}
+
+// Block-wide argmin over the threads' candidates (bb < 0: none); the winner
+// lands in sc.wn[0] / sc.wd[0] / sc.wl[0] / sc.wb[0].
+template <int CRIT>
+__device__ __forceinline__ void block_argmin(uint64_t bn, uint64_t bd, double bl, int bb,
+                                             ScanScratch& sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < kMaxBPL; ++i) {
-    nL[i] = 0;
-    SL[i] = SR[i] = 0;
-    hL[i] = hR[i] = 0.0;
+  for (int off = 16; off > 0; off >>= 1) {
+    const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+    const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+    const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
+    const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
+    if (edge_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
+      bn = on;
+      bd = od;
+      bl = ol;
+      bb = ob;
+    }
   }
-  uint32_t ntot = 0;
-  uint32_t occ[kMaxBPL];  // samples in bin j0 + i (all classes)
+  if (lane == 0) {
+    sc.wn[warp] = bn;
+    sc.wd[warp] = bd;
+    sc.wl[warp] = bl;
+    sc.wb[warp] = bb;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const bool in = lane < kThreads / 32;
+    bn = in ? sc.wn[lane] : 0;
+    bd = in ? sc.wd[lane] : 0;
+    bl = in ? sc.wl[lane] : 0.0;
+    bb = in ? sc.wb[lane] : -1;
 #pragma unroll
-  for (int i = 0; i < kMaxBPL; ++i) occ[i] = 0;
-  for (int k = 0; k < K; ++k) {
-    uint32_t c[kMaxBPL];
+    for (int off = 4; off > 0; off >>= 1) {
+      const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+      const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+      const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
+      const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
+      if (edge_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
+        bn = on;
+        bd = od;
+        bl = ol;
+        bb = ob;
+      }
+    }
+    if (lane == 0) {
+      sc.wn[0] = bn;
+      sc.wd[0] = bd;
+      sc.wl[0] = bl;
+      sc.wb[0] = bb;
+    }
+  }
+  __syncthreads();
+}
+
+// Classification threshold scan of one particle by the whole CTA.
+// h: [B][K] counts in shared memory (turned into per-class prefix sums in
+// place). Edge b splits bins < b from bins >= b; an edge whose bin b-1 is
+// empty repeats edge b-1's partition and is skipped (the lower edge wins).
+template <int CRIT>
+__device__ EvalRes block_scan_cls(uint32_t* h, int B, int K, int min_leaf, ScanScratch& sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // 1. per-class inclusive prefix over bins: warp w takes classes w, w+8, ...;
+  //    lane l owns bins [l*bpl, (l+1)*bpl)
+  const int bpl = (B + 31) >> 5;
+  for (int k = warp; k < K; k += kThreads / 32) {
+    uint32_t v[kMaxBins / 32];
     uint32_t sum = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxBPL; ++i) {
-      const int j = j0 + i;
-      c[i] = (i < BPL && j < B) ? h[j * K + k] : 0u;
-      sum += c[i];
+    for (int i = 0; i < kMaxBins / 32; ++i) {
+      const int j = lane * bpl + i;
+      v[i] = (i < bpl && j < B) ? h[j * K + k] : 0u;
+      sum += v[i];
     }
     uint32_t incl = sum;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += u;
     }
-    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-    ntot += tot;
     uint32_t run = incl - sum;
 #pragma unroll
-    for (int i = 0; i < kMaxBPL; ++i) {
-      if (i >= BPL) break;
-      run += c[i];
-      occ[i] += c[i];
-      const uint32_t rr = tot - run;
-      nL[i] += run;
-      if (crit == SLM_GINI) {
-        SL[i] += (uint64_t)run * run;
-        SR[i] += (uint64_t)rr * rr;
+    for (int i = 0; i < kMaxBins / 32; ++i) {
+      const int j = lane * bpl + i;
+      run += v[i];
+      if (i < bpl && j < B) h[j * K + k] = run;
+    }
+  }
+  __syncthreads();
+  // 2. one thread per edge b = 1 + tid
+  const uint32_t* tot = h + (B - 1) * K;
+  uint32_t ntot = 0;
+  for (int k = 0; k < K; ++k) ntot += tot[k];
+  const int b = 1 + threadIdx.x;
+  uint32_t nl = 0;
+  uint64_t sl = 0, sr = 0;
+  double hl = 0.0, hr = 0.0;
+  if (b < B) {
+    const uint32_t* row = h + (b - 1) * K;
+    for (int k = 0; k < K; ++k) {
+      const uint32_t l = row[k], r = tot[k] - l;
+      nl += l;
+      if (CRIT == SLM_GINI) {
+        sl += (uint64_t)l * l;
+        sr += (uint64_t)r * r;
       } else {
-        hL[i] += xlogx(run);
-        hR[i] += xlogx(rr);
+        hl += xlogx(l);
+        hr += xlogx(r);
+      }
+    }
+    sc.nl[threadIdx.x] = nl;
+  }
+  __syncthreads();
+  const uint32_t prev = (b >= 2 && b < B) ? sc.nl[threadIdx.x - 1] : 0u;
+  const uint32_t nr = ntot - nl;
+  uint64_t bn = 0, bd = 0;
+  double bl = 0.0;
+  int bb = -1;
+  if (b < B && nl != prev && nl >= (uint32_t)min_leaf && nr >= (uint32_t)min_leaf) {
+    bb = b;
+    if (CRIT == SLM_GINI) {
+      bn = sl * nr + sr * nl;
+      bd = (uint64_t)nl * nr;
+    } else {
+      // compared after the division by n, as the criterion is defined
+      bl = ((xlogx(nl) - hl) + (xlogx(nr) - hr)) / (double)ntot;
+    }
+  }
+  block_argmin<CRIT>(bn, bd, bl, bb, sc);
+  if (threadIdx.x == 0) {
+    EvalRes res = invalid_res();
+    const int wb = sc.wb[0];
+    if (wb >= 0) {
+      res.valid = 1;
+      res.bin = wb;
+      res.nl = sc.nl[wb - 1];
+      res.nr = ntot - sc.nl[wb - 1];
+      if (CRIT == SLM_GINI) {
+        res.num = sc.wn[0];
+        res.den = sc.wd[0];
+        const uint64_t nden = (uint64_t)ntot * res.den;
+        res.loss = (double)(nden - res.num) / (double)nden;
+      } else {
+        res.loss = sc.wl[0];
+      }
+    }
+    sc.res = res;
+  }
+  __syncthreads();
+  return sc.res;
+}
+
+// Regression threshold scan of one particle by the whole CTA. cnt/s/q: [B]
+// weight, sum w y, sum w y^2. Prefix sums by warp 0 (sequential within a
+// lane, then across lanes), then one thread per edge.
+__device__ EvalRes block_scan_mse(const uint32_t* cnt, const double* s, const double* q, int B,
+                                  int min_leaf, ScanScratch& sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    const int bpl = (B + 31) >> 5;
+    uint32_t cs = 0;
+    double ss = 0.0, qs = 0.0;
+    for (int i = 0; i < bpl; ++i) {
+      const int j = lane * bpl + i;
+      if (j < B) {
+        cs += cnt[j];
+        ss += s[j];
+        qs += q[j];
+      }
+    }
+    uint32_t ic = cs;
+    double is = ss, iq = qs;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t vc = __shfl_up_sync(0xffffffffu, ic, off);
+      const double vs = __shfl_up_sync(0xffffffffu, is, off);
+      const double vq = __shfl_up_sync(0xffffffffu, iq, off);
+      if (lane >= off) {
+        ic += vc;
+        is = vs + is;
+        iq = vq + iq;
+      }
+    }
+    // exclusive prefix = the previous lane's inclusive sums
+    uint32_t rc = ic - cs;
+    double rs = __shfl_up_sync(0xffffffffu, is, 1);
+    double rq = __shfl_up_sync(0xffffffffu, iq, 1);
+    if (lane == 0) {
+      rs = 0.0;
+      rq = 0.0;
+    }
+    for (int i = 0; i < bpl; ++i) {
+      const int j = lane * bpl + i;
+      if (j < B) {
+        rc += cnt[j];
+        rs += s[j];
+        rq += q[j];
+        sc.pc[j] = rc;
+        sc.ps[j] = rs;
+        sc.pq[j] = rq;
       }
     }
   }
-  EvalRes best = invalid_res();
-#pragma unroll
-  for (int i = 0; i < kMaxBPL; ++i) {
-    if (i >= BPL) break;
-    const int b = j0 + i + 1;
-    if (b > B - 1) break;
-    if (occ[i] == 0) continue;  // same partition as edge b-1
-    const uint32_t nl = nL[i], nr = ntot - nl;
-    if (nl < (uint32_t)min_leaf || nr < (uint32_t)min_leaf) continue;
-    EvalRes c = invalid_res();
-    c.valid = 1;
-    c.bin = b;
-    c.nl = nl;
-    c.nr = nr;
-    if (crit == SLM_GINI) {
-      // decisions use the exact rational; the double loss is formed once, for
-      // the winning edge (FP64 division is slow on this part)
-      c.num = SL[i] * nr + SR[i] * nl;
-      c.den = (uint64_t)nl * nr;
-    } else {
-      const double hh = (xlogx(nl) - hL[i]) + (xlogx(nr) - hR[i]);
-      c.loss = hh / (double)ntot;
-    }
-    if (better(c, best, crit)) best = c;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const EvalRes o = shfl_res(best, lane ^ off);
-    if (edge_first(o, best, crit)) best = o;
-  }
-  if (crit == SLM_GINI && best.valid) {
-    const uint64_t nden = (uint64_t)ntot * best.den;
-    best.loss = (double)(nden - best.num) / (double)nden;
-  }
-  return best;
-}
-
-// Regression. cnt/s/q: [B] weight, sum w y, sum w y^2 of one particle.
-__device__ EvalRes scan_mse(const uint32_t* cnt, const double* s,
-                            const double* q, int B, int min_leaf) {
-  const int lane = threadIdx.x & 31;
-  const int BPL = (B + 31) >> 5;
-  const int j0 = lane * BPL;
-  uint32_t c[kMaxBPL];
-  double sv[kMaxBPL], qv[kMaxBPL];
-  uint32_t cs = 0;
-  double ss = 0.0, qs = 0.0;
-#pragma unroll
-  for (int i = 0; i < kMaxBPL; ++i) {
-    const int j = j0 + i;
-    const bool in = i < BPL && j < B;
-    c[i] = in ? cnt[j] : 0u;
-    sv[i] = in ? s[j] : 0.0;
-    qv[i] = in ? q[j] : 0.0;
-    cs += c[i];
-    ss += sv[i];
-    qs += qv[i];
-  }
-  uint32_t ic = cs;
-  double is = ss, iq = qs;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t vc = __shfl_up_sync(0xffffffffu, ic, off);
-    const double vs = __shfl_up_sync(0xffffffffu, is, off);
-    const double vq = __shfl_up_sync(0xffffffffu, iq, off);
-    if (lane >= off) {
-      ic += vc;
-      is = vs + is;
-      iq = vq + iq;
+  __syncthreads();
+  const uint32_t ntot = sc.pc[B - 1];
+  const double stot = sc.ps[B - 1], qtot = sc.pq[B - 1];
+  const int b = 1 + threadIdx.x;
+  double bl = 0.0;
+  int bb = -1;
+  if (b < B && cnt[b - 1] != 0) {  // empty bin b-1: same partition as edge b-1
+    const uint32_t nl = sc.pc[b - 1], nr = ntot - nl;
+    if (nl >= (uint32_t)min_leaf && nr >= (uint32_t)min_leaf) {
+      const double sl = sc.ps[b - 1], ql = sc.pq[b - 1];
+      const double sr = stot - sl, qr = qtot - ql;
+      const double sse_l = ql - sl * sl / (double)nl;
+      const double sse_r = qr - sr * sr / (double)nr;
+      bl = (sse_l + sse_r) / (double)ntot;
+      bb = b;
     }
   }
-  const uint32_t ntot = __shfl_sync(0xffffffffu, ic, 31);
-  const double stot = __shfl_sync(0xffffffffu, is, 31);
-  const double qtot = __shfl_sync(0xffffffffu, iq, 31);
-  // exclusive prefix = the previous lane's inclusive sums
-  uint32_t rc = ic - cs;
-  double rs = __shfl_up_sync(0xffffffffu, is, 1);
-  double rq = __shfl_up_sync(0xffffffffu, iq, 1);
-  if (lane == 0) {
-    rs = 0.0;
-    rq = 0.0;
+  block_argmin<SLM_MSE>(0, 0, bl, bb, sc);
+  if (threadIdx.x == 0) {
+    EvalRes res = invalid_res();
+    const int wb = sc.wb[0];
+    if (wb >= 0) {
+      res.valid = 1;
+      res.bin = wb;
+      res.nl = sc.pc[wb - 1];
+      res.nr = ntot - sc.pc[wb - 1];
+      res.loss = sc.wl[0];
+    }
+    sc.res = res;
   }
-  EvalRes best = invalid_res();
-#pragma unroll
-  for (int i = 0; i < kMaxBPL; ++i) {
-    if (i >= BPL) break;
-    rc += c[i];
-    rs += sv[i];
-    rq += qv[i];
-    const int b = j0 + i + 1;
-    if (b > B - 1) break;
-    // an empty bin b-1 gives edge b the partition of edge b-1: keep the lower
-    if (c[i] == 0) continue;
-    const uint32_t nl = rc, nr = ntot - rc;
-    if (nl < (uint32_t)min_leaf || nr < (uint32_t)min_leaf) continue;
-    const double sr = stot - rs, qr = qtot - rq;
-    const double sse_l = rq - rs * rs / (double)nl;
-    const double sse_r = qr - sr * sr / (double)nr;
-    EvalRes e = invalid_res();
-    e.valid = 1;
-    e.bin = b;
-    e.nl = nl;
-    e.nr = nr;
-    e.loss = (sse_l + sse_r) / (double)ntot;
-    if (better(e, best, SLM_MSE)) best = e;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const EvalRes o = shfl_res(best, lane ^ off);
-    if (edge_first(o, best, SLM_MSE)) best = o;
-  }
-  return best;
+  __syncthreads();
+  return sc.res;
 }
 
 // ---- async copies -------------------------------------------------------------
@@ -505,19 +598,6 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // ---- swarm update ----------------------------------------------------------------
 
-__device__ __forceinline__ EvalRes ldcg_res(const EvalRes* p) {
-  EvalRes r;
-  r.loss = __ldcg(&p->loss);
-  r.num = __ldcg((const unsigned long long*)&p->num);
-  r.den = __ldcg((const unsigned long long*)&p->den);
-  r.zmin = __ldcg(&p->zmin);
-  r.inv_w = __ldcg(&p->inv_w);
-  r.bin = __ldcg(&p->bin);
-  r.valid = __ldcg(&p->valid);
-  r.nl = __ldcg((const long long*)&p->nl);
-  r.nr = __ldcg((const long long*)&p->nr);
-  return r;
-}
 
 // Algorithm 1, pbest step of particle p after evaluation t (one warp): strict
 // "<" against the particle's best so far; the position is kept on improvement.
@@ -536,338 +616,324 @@ __device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, i
   for (int j = lane; j < pr.d; j += 32) sw.pbest[o + j] = sw.pos[o + j];
 }
 
-// Algorithm 1, gbest step of node a after evaluation t. Run by all threads of
-// the CTA that finished the node's last particle group in this iteration.
-__device__ void node_tail(const Problem& pr, const Swarm& sw, int a, int t) {
-  const int P = pr.P, Pp = pr.Pp, d = pr.d;
-  const int nthr = blockDim.x, nw = nthr >> 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ EvalRes s_wbest[kThreads / 32];
-  __shared__ int s_widx[kThreads / 32];
-  __shared__ int s_best;
-  const EvalRes* cur = sw.cur + (int64_t)a * Pp;
-  const EvalRes gold = sw.gb[a];
-
-  // gbest candidates = particles strictly better than gold (at t = 0 every
-  // particle; gold is then unset); argmin with ties to the lower index
-  EvalRes ce = invalid_res();
-  int cidx = INT_MAX;
-  for (int p = threadIdx.x; p < P; p += nthr) {
-    const EvalRes e = ldcg_res(cur + p);  // written by other CTAs of this launch
+// Algorithm 1, gbest step of node a after evaluation t, as seen by one warp:
+// the particle with the best score strictly better than gold (at t = 0 every
+// particle, gold unset), ties to the lower index; -1 if none. Lane 0 also
+// returns that particle's score in *best_res.
+__device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
+                            EvalRes* best_res) {
+  const int lane = threadIdx.x & 31;
+  int bi = -1;
+  EvalRes be = invalid_res();
+  for (int p = lane; p < pr.P; p += 32) {
+    const EvalRes e = cur[p];
     if (!(t == 0 || better(e, gold, pr.crit))) continue;
-    if (cidx == INT_MAX || better(e, ce, pr.crit)) {
-      ce = e;
-      cidx = p;
+    if (bi < 0 || better(e, be, pr.crit)) {
+      bi = p;
+      be = e;
     }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const EvalRes o = shfl_res(ce, lane ^ off);
-    const int oi = __shfl_xor_sync(0xffffffffu, cidx, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    const EvalRes o = shfl_res(be, lane ^ off);
     bool take;
-    if (oi == INT_MAX)
+    if (oi < 0)
       take = false;
-    else if (cidx == INT_MAX)
+    else if (bi < 0)
       take = true;
-    else if (better(o, ce, pr.crit))
+    else if (better(o, be, pr.crit))
       take = true;
-    else if (better(ce, o, pr.crit))
+    else if (better(be, o, pr.crit))
       take = false;
     else
-      take = oi < cidx;
+      take = oi < bi;
     if (take) {
-      ce = o;
-      cidx = oi;
+      bi = oi;
+      be = o;
     }
   }
-  if (lane == 0) {
-    s_wbest[warp] = ce;
-    s_widx[warp] = cidx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    EvalRes b = s_wbest[0];
-    int bi = s_widx[0];
-    for (int w = 1; w < nw; ++w) {
-      const EvalRes o = s_wbest[w];
-      const int oi = s_widx[w];
-      if (oi == INT_MAX) continue;
-      if (bi == INT_MAX || better(o, b, pr.crit) || (!better(b, o, pr.crit) && oi < bi)) {
-        b = o;
-        bi = oi;
-      }
-    }
-    s_best = bi == INT_MAX ? -1 : bi;
-    if (bi != INT_MAX) {
-      sw.gb[a] = b;
-      sw.gpart[a] = bi;
-      sw.giter[a] = t;
-    }
-    if (sw.trace) {
-      const EvalRes g = bi != INT_MAX ? b : gold;
-      sw.trace[(int64_t)a * (sw.T + 1) + t] =
-          g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
-    }
-  }
-  __syncthreads();
-  // the new gbest improved its pbest in this iteration, so its pbest row is
-  // its current position (written by another CTA of this launch)
-  const float* pbp = sw.pbest + (int64_t)a * Pp * d;
-  float* gbp = sw.gbest + (int64_t)a * d;
-  const int best = s_best;
-  if (best >= 0)
-    for (int j = threadIdx.x; j < d; j += nthr) gbp[j] = __ldcg(pbp + (int64_t)best * d + j);
+  if (lane == 0) *best_res = be;
+  return bi;
 }
 
-// Eq. pso-1, synchronous: every particle moves with the gbest held at the end
-// of iteration t. One thread per (node, particle, 4 dimensions).
+// Algorithm 1's gbest step after evaluation t, then (t < T) the synchronous
+// move of Eq. pso-1: every particle moves with the gbest held at the end of
+// iteration t. Grid: (node, slice of the node's particle x 4-dimension
+// items). Every CTA finds the node's gbest itself; CTA 0 of the node records
+// it. The gbest score is double-buffered by iteration parity (read from
+// gb[(t-1)&1], written to gb[t&1]) so no CTA reads a score another CTA of
+// the launch is writing; the gbest position of a new best is its pbest row.
 __global__ void __launch_bounds__(128)
-    k_move(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int A, int t,
-           SwarmCoef co) {
+    k_move(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int t, SwarmCoef co) {
   pdl_trigger();
   pdl_wait();
-  const int d = pr.d, d4 = (d + 3) >> 2;
-  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t per_node = (int64_t)pr.P * d4;
-  if (item >= per_node * A) return;
-  const int a = (int)(item / per_node);
-  const int rem = (int)(item - (int64_t)a * per_node);
-  const int pi = rem / d4, q = rem - pi * d4;
+  __shared__ int s_best;
+  const int a = blockIdx.x;
+  const int A = gridDim.x;
+  const int d = pr.d, d4 = (d + 3) >> 2, Pp = pr.Pp;
+  const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
+  EvalRes* gnew_buf = sw.gb + (int64_t)(t & 1) * A;
+  if (threadIdx.x < 32) {
+    const EvalRes gold = gold_buf[a];
+    EvalRes be;
+    const int bi = gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t, &be);
+    if (threadIdx.x == 0) {
+      s_best = bi;
+      if (blockIdx.y == 0) {
+        gnew_buf[a] = bi >= 0 ? be : gold;
+        if (bi >= 0) {
+          sw.gpart[a] = bi;
+          sw.giter[a] = t;
+        }
+        if (sw.trace) {
+          const EvalRes g = bi >= 0 ? be : gold;
+          sw.trace[(int64_t)a * (sw.T + 1) + t] =
+              g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int best = s_best;
+  const float* pbp = sw.pbest + (int64_t)a * Pp * d;
+  float* gbp = sw.gbest + (int64_t)a * d;
+  // a new best improved its pbest in this iteration: its pbest row is its
+  // current position; otherwise the recorded gbest stands
+  const float* gsrc = best >= 0 ? pbp + (int64_t)best * d : gbp;
+  if (blockIdx.y == 0 && best >= 0)
+    for (int j = threadIdx.x; j < d; j += blockDim.x) gbp[j] = gsrc[j];
+  if (t >= sw.T) return;
   const uint32_t uid = nodes[a].uid;
   const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
-  const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi, (uint32_t)q | (kR1 << 24),
-                              k0, k1);
-  const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi, (uint32_t)q | (kR2 << 24),
-                              k0, k1);
-  const int64_t row = ((int64_t)a * pr.Pp + pi) * d;
-  float* pos = sw.pos + row;
-  float* vel = sw.vel + row;
-  const float* pbp = sw.pbest + row;
-  const float* gbp = sw.gbest + (int64_t)a * d;
+  for (int item = blockIdx.y * blockDim.x + threadIdx.x; item < pr.P * d4;
+       item += gridDim.y * blockDim.x) {
+    const int pi = item / d4, q = item - pi * d4;
+    const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
+                                (uint32_t)q | (kR1 << 24), k0, k1);
+    const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
+                                (uint32_t)q | (kR2 << 24), k0, k1);
+    const int64_t row = (int64_t)pi * d;
+    float* pos = sw.pos + (int64_t)a * Pp * d + row;
+    float* vel = sw.vel + (int64_t)a * Pp * d + row;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int j = 4 * q + c;
-    if (j >= d) break;
-    // v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v
-    const float x = pos[j], v = vel[j];
-    const float inertia = __fmul_rn(co.inertia, v);
-    const float cog = __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(pbp[j], x));
-    const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])), __fsub_rn(gbp[j], x));
-    const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
-    vel[j] = vn;
-    pos[j] = __fadd_rn(x, vn);
+    for (int c = 0; c < 4; ++c) {
+      const int j = 4 * q + c;
+      if (j >= d) break;
+      // v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v
+      const float x = pos[j], v = vel[j];
+      const float inertia = __fmul_rn(co.inertia, v);
+      const float cog =
+          __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(pbp[row + j], x));
+      const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])), __fsub_rn(gsrc[j], x));
+      const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
+      vel[j] = vn;
+      pos[j] = __fadd_rn(x, vn);
+    }
   }
 }
 
 // ---- histogram and scan -------------------------------------------------------------
 
-constexpr int kWP = 8;        // particles per CTA of the histogram kernel, one per warp
-constexpr int kPiece = 1024;  // entries per staged piece
+constexpr int kPiece = 4096;  // entries per staged piece (bulk copies carry a fixed cost)
+constexpr int kCopies = 4;  // histogram copies, each shared by a pair of warps
+constexpr int kStages = 2;  // staged pieces in flight
 
-__host__ __device__ inline size_t hist_particle_bytes(int crit, int B, int K) {
+__host__ __device__ inline size_t hist_copy_bytes(int crit, int B, int K) {
   return crit == SLM_MSE ? (size_t)B * (4 + 8 + 8) : (size_t)B * K * 4;
 }
-// One staged piece: z of kWP particles, then labels or targets, then
-// multiplicities (if weighted).
+// One staged piece: z of the particle, labels or targets, multiplicities.
 __host__ __device__ inline size_t stage_bytes(bool weighted) {
-  return (size_t)kPiece * 4 * (kWP + 1 + (weighted ? 1 : 0));
+  return (size_t)kPiece * 4 * (2 + (weighted ? 1 : 0));
 }
 
-// A cluster of S CTAs per (node, group of kWP particles). Warp w of every
-// CTA owns particle g*kWP + w. The CTA's slice of the node's entries (rank r:
-// the r-th of S slices) streams through shared memory in kPiece-entry pieces:
-// one thread issues bulk (TMA) copies of the kWP z rows, the labels / targets
-// and the multiplicities of a piece, double-buffered on two mbarriers; every
-// warp bins its particle's z from shared memory into its own histogram. Rank
-// q of the cluster then sums one slice of every histogram word over the S
-// CTAs through distributed shared memory into rank 0, whose warps scan the
-// B-1 edges of their particles. In a search (do_update) each warp also takes
-// its particle's pbest step, and the CTA that finishes a node's last particle
-// group (ticket in sw.done) runs the node's gbest step (the move is k_move).
-__global__ void __launch_bounds__(kThreads)
+// A cluster of S CTAs per (node, particle). Rank r streams the r-th of S
+// slices of the node's entries through shared memory in kPiece-entry pieces:
+// one thread issues bulk (TMA) copies of the particle's z, the labels /
+// targets and the multiplicities of a piece into a ring of kStages stages,
+// each with its own mbarrier; warp w bins its share of each piece into
+// histogram copy w % kCopies. The
+// copies are merged, rank 0 adds the other ranks' histograms through
+// distributed shared memory and the whole CTA scans the B-1 edges. In a
+// search (do_update) rank 0 also takes the particle's pbest step; the gbest
+// step and the move follow in k_move.
+__global__ void __launch_bounds__(kThreads, 3)
     k_hist_scan(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int32_t* bins_out,
-                int t, SwarmCoef co, int do_update) {
+                int t, int do_update) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ int s_last;
+  __shared__ __align__(8) uint64_t s_bar[kStages];
+  __shared__ int s_ok;
+  __shared__ float s_zmin, s_inv_w;
+  __shared__ ScanScratch sc;
   const cg::cluster_group cl = cg::this_cluster();
   pdl_trigger();
   pdl_wait();
   const int S = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int a = blockIdx.x / S;
+  const int p = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = blockIdx.y;
-  const int p = g * kWP + warp;
-  const bool live = p < pr.P;
   const NodeDesc nd = nodes[a];
   const int B = pr.B, K = pr.K;
   const bool mse = pr.crit == SLM_MSE;
   const bool weighted = pr.w != nullptr;
-  const int words = mse ? B : B * K;  // u32 counters per particle
-  // shared memory: histograms, then two stages
-  double* hs = reinterpret_cast<double*>(smem);         // MSE [kWP][B]
-  double* hq = hs + (mse ? kWP * B : 0);                 // MSE [kWP][B]
-  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? kWP * B : 0));  // [kWP][words]
+  const int words = mse ? B : B * K;  // u32 counters per copy
+  // shared memory: kCopies histogram copies, then two stages
+  double* hs = reinterpret_cast<double*>(smem);         // MSE [kCopies][B]
+  double* hq = hs + (mse ? kCopies * B : 0);             // MSE [kCopies][B]
+  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? kCopies * B : 0));  // [kCopies][words]
   unsigned char* stage0 =
-      smem + (((size_t)hist_particle_bytes(pr.crit, B, K) * kWP + 127) & ~(size_t)127);
+      smem + ((hist_copy_bytes(pr.crit, B, K) * kCopies + 127) & ~(size_t)127);
   const size_t sbytes = stage_bytes(weighted);
-  uint32_t* h = hc + warp * words;
-  double* hsw = hs + warp * B;
-  double* hqw = hq + warp * B;
+  const int copy = warp % kCopies;
+  uint32_t* h = hc + copy * words;
+  double* hsw = hs + copy * B;
+  double* hqw = hq + copy * B;
 
-  // range of this warp's particle
-  int lo_o = INT_MAX, hi_o = INT_MIN;
-  int* zz = sw.zmm + ((int64_t)a * pr.Pp + (live ? p : 0)) * 2;
-  if (live && lane == 0) {
-    lo_o = zz[0];
-    hi_o = zz[1];
-  }
-  lo_o = __shfl_sync(0xffffffffu, lo_o, 0);
-  hi_o = __shfl_sync(0xffffffffu, hi_o, 0);
-  float zmin = 0.f, inv_w = 0.f;
-  bool ok = false;
-  if (lo_o != INT_MAX) {
-    const float lo = ord2f(lo_o), hi = ord2f(hi_o);
-    inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
-    zmin = lo;
-    ok = (hi > lo) && isfinite(inv_w);
-  }
-  for (int i = lane; i < words; i += 32) h[i] = 0u;
-  if (mse)
-    for (int i = lane; i < B; i += 32) {
-      hsw[i] = 0.0;
-      hqw[i] = 0.0;
-    }
+  int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
   if (threadIdx.x == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
+    const int lo_o = zz[0], hi_o = zz[1];
+    float zmin = 0.f, inv_w = 0.f;
+    int ok = 0;
+    if (lo_o != INT_MAX) {
+      const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+      inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+      zmin = lo;
+      ok = (hi > lo) && isfinite(inv_w);
+    }
+    s_zmin = zmin;
+    s_inv_w = inv_w;
+    s_ok = ok;
+    for (int i = 0; i < kStages; ++i) mbar_init(&s_bar[i], 1);
     mbar_init_fence();
   }
+  for (int i = threadIdx.x; i < kCopies * words; i += kThreads) hc[i] = 0u;
+  if (mse)
+    for (int i = threadIdx.x; i < kCopies * B; i += kThreads) {
+      hs[i] = 0.0;
+      hq[i] = 0.0;
+    }
   __syncthreads();
+  const bool ok = s_ok;
+  const float zmin = s_zmin, inv_w = s_inv_w;
 
   // slice of this rank: starts on a multiple of 4 entries (16 bytes)
   const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
   const int r_begin = min(nd.seg_len, rank * chunk);
   const int r_end = min(nd.seg_len, r_begin + chunk);
-  const int n_pieces = (r_end - r_begin + kPiece - 1) / kPiece;
+  const int n_pieces = ok ? (r_end - r_begin + kPiece - 1) / kPiece : 0;
   const int64_t e0 = nd.seg_start;  // multiple of 4
-  const int n_live = min(kWP, pr.P - g * kWP);
   auto issue = [&](int k) {
     const int r = r_begin + k * kPiece;
     const int n = min(kPiece, r_end - r);
     const uint32_t bytes = (uint32_t)(((n + 3) & ~3) * 4);
-    unsigned char* st = stage0 + (k & 1) * sbytes;
-    uint64_t* bar = &s_bar[k & 1];
+    unsigned char* st = stage0 + (k % kStages) * sbytes;
+    uint64_t* bar = &s_bar[k % kStages];
     fence_proxy_async();
-    mbar_expect_tx(bar, bytes * (uint32_t)(n_live + 1 + (weighted ? 1 : 0)));
-    for (int w = 0; w < n_live; ++w)
-      bulk_g2s(st + (size_t)w * kPiece * 4, sw.z + (int64_t)(g * kWP + w) * pr.Ez + e0 + r,
-               bytes, bar);
+    mbar_expect_tx(bar, bytes * (uint32_t)(weighted ? 3 : 2));
+    bulk_g2s(st, sw.z + (int64_t)p * pr.Ez + e0 + r, bytes, bar);
     const void* src = mse ? (const void*)(pr.y + e0 + r) : (const void*)(pr.lab + e0 + r);
-    bulk_g2s(st + (size_t)kWP * kPiece * 4, src, bytes, bar);
-    if (weighted) bulk_g2s(st + (size_t)(kWP + 1) * kPiece * 4, pr.w + e0 + r, bytes, bar);
+    bulk_g2s(st + (size_t)kPiece * 4, src, bytes, bar);
+    if (weighted) bulk_g2s(st + (size_t)2 * kPiece * 4, pr.w + e0 + r, bytes, bar);
   };
-  if (threadIdx.x == 0 && n_pieces > 0) issue(0);
-  bool lost = false;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kStages - 1 && k < n_pieces; ++k) issue(k);
   for (int k = 0; k < n_pieces; ++k) {
-    if (threadIdx.x == 0 && k + 1 < n_pieces) issue(k + 1);
-    if (!mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitPolls)) {
-      // a copy did not land: record it, give in-flight copies a bounded
+    // piece k + kStages - 1 reuses the stage of piece k - 1, released by the
+    // barrier at the end of the previous round
+    if (threadIdx.x == 0 && k + kStages - 1 < n_pieces) issue(k + kStages - 1);
+    const uint32_t parity = (uint32_t)((k / kStages) & 1);
+    if (!mbar_wait(&s_bar[k % kStages], parity, kWaitPolls)) {
+      // a copy did not land: record it, give the copies in flight a bounded
       // chance to finish, and stop using the stages
       if (threadIdx.x == 0 && sw.err) atomicExch(sw.err, 3);
-      mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitPolls);
-      if (k + 1 < n_pieces) mbar_wait(&s_bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), kWaitPolls);
-      lost = true;
+      for (int j = k; j < n_pieces && j < k + kStages; ++j)
+        mbar_wait(&s_bar[j % kStages], (uint32_t)((j / kStages) & 1), kWaitPolls);
       break;
     }
-    const unsigned char* st = stage0 + (k & 1) * sbytes;
+    const unsigned char* st = stage0 + (k % kStages) * sbytes;
     const int r = r_begin + k * kPiece;
     const int n = min(kPiece, r_end - r);
-    if (live && ok) {
-      const float* zs = reinterpret_cast<const float*>(st) + (size_t)warp * kPiece;
-      const int32_t* ls = reinterpret_cast<const int32_t*>(st + (size_t)kWP * kPiece * 4);
-      const float* ys = reinterpret_cast<const float*>(st + (size_t)kWP * kPiece * 4);
-      const uint32_t* ws =
-          reinterpret_cast<const uint32_t*>(st + (size_t)(kWP + 1) * kPiece * 4);
-      for (int i = lane; i < n; i += 32) {
-        const int b = bin_of(zs[i], zmin, inv_w, B);
-        const uint32_t w = weighted ? ws[i] : 1u;
-        if (mse) {
-          const float yv = ys[i];
-          const double wy = (double)w * (double)yv;
-          atomicAdd(&h[b], w);
-          atomicAdd(&hsw[b], wy);
-          atomicAdd(&hqw[b], wy * (double)yv);
-        } else {
-          atomicAdd(&h[b * K + ls[i]], w);
-        }
-        if (bins_out) bins_out[(int64_t)p * nd.seg_len + r + i] = b;
+    const float* zs = reinterpret_cast<const float*>(st);
+    const int32_t* ls = reinterpret_cast<const int32_t*>(st + (size_t)kPiece * 4);
+    const float* ys = reinterpret_cast<const float*>(st + (size_t)kPiece * 4);
+    const uint32_t* ws = reinterpret_cast<const uint32_t*>(st + (size_t)2 * kPiece * 4);
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+      const int b = bin_of(zs[i], zmin, inv_w, B);
+      const uint32_t w = weighted ? ws[i] : 1u;
+      if (mse) {
+        const float yv = ys[i];
+        const double wy = (double)w * (double)yv;
+        atomicAdd(&h[b], w);
+        atomicAdd(&hsw[b], wy);
+        atomicAdd(&hqw[b], wy * (double)yv);
+      } else {
+        atomicAdd(&h[b * K + ls[i]], w);
       }
+      if (bins_out) bins_out[(int64_t)p * nd.seg_len + r + i] = b;
     }
-    __syncthreads();  // stage k & 1 is refilled by piece k + 2
+    __syncthreads();  // this stage is refilled by piece k + kStages
   }
-  (void)lost;
-  if (S > 1) {
-    cl.sync();  // every CTA's histograms are complete
-    // rank q sums words [q*W/S, (q+1)*W/S) of all kWP histograms into rank 0
-    const int W = kWP * words;
-    const int w0 = (int)((int64_t)W * rank / S), w1 = (int)((int64_t)W * (rank + 1) / S);
-    uint32_t* dst = cl.map_shared_rank(hc, 0);
-    for (int i = w0 + threadIdx.x; i < w1; i += kThreads) {
-      uint32_t v = 0;
+  // merge the warp copies into copy 0
+  for (int i = threadIdx.x; i < words; i += kThreads) {
+    uint32_t v = 0;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q < S) v += cl.map_shared_rank(hc, q)[i];
-      dst[i] = v;
-    }
-    if (mse) {
-      const int Wd = kWP * B;
-      const int d0 = (int)((int64_t)Wd * rank / S), d1 = (int)((int64_t)Wd * (rank + 1) / S);
-      double* ds = cl.map_shared_rank(hs, 0);
-      double* dq = cl.map_shared_rank(hq, 0);
-      for (int i = d0 + threadIdx.x; i < d1; i += kThreads) {
-        double vs = 0.0, vq = 0.0;
-        for (int q = 0; q < S; ++q) {
-          vs += cl.map_shared_rank(hs, q)[i];
-          vq += cl.map_shared_rank(hq, q)[i];
-        }
-        ds[i] = vs;
-        dq[i] = vq;
+    for (int c = 0; c < kCopies; ++c) v += hc[c * words + i];
+    hc[i] = v;
+  }
+  if (mse)
+    for (int i = threadIdx.x; i < B; i += kThreads) {
+      double vs = 0.0, vq = 0.0;
+#pragma unroll
+      for (int c = 0; c < kCopies; ++c) {
+        vs += hs[c * B + i];
+        vq += hq[c * B + i];
       }
+      hs[i] = vs;
+      hq[i] = vq;
     }
-    cl.sync();  // rank 0 holds the sums; the others' memory is no longer read
+  if (S > 1) {
+    cl.sync();  // every rank's copy 0 is complete
+    if (rank == 0) {
+      for (int i = threadIdx.x; i < words; i += kThreads) {
+        uint32_t v = hc[i];
+#pragma unroll
+        for (int q = 1; q < 16; ++q)
+          if (q < S) v += cl.map_shared_rank(hc, q)[i];
+        hc[i] = v;
+      }
+      if (mse)
+        for (int i = threadIdx.x; i < B; i += kThreads) {
+          double vs = hs[i], vq = hq[i];
+          for (int q = 1; q < S; ++q) {
+            vs += cl.map_shared_rank(hs, q)[i];
+            vq += cl.map_shared_rank(hq, q)[i];
+          }
+          hs[i] = vs;
+          hq[i] = vq;
+        }
+    }
+    cl.sync();  // the other ranks' memory is no longer read
     if (rank != 0) return;
   }
-  if (live) {
-    if (lane == 0) {
-      zz[0] = INT_MAX;  // ready for the next iteration
-      zz[1] = INT_MIN;
-    }
-    EvalRes res;
-    if (!ok) {
-      res = invalid_res();
-    } else {
-      res = mse ? scan_mse(h, hsw, hqw, B, pr.min_leaf) : scan_cls(h, B, K, pr.min_leaf, pr.crit);
-      res.zmin = zmin;
-      res.inv_w = inv_w;
-    }
-    if (lane == 0) sw.cur[(int64_t)a * pr.Pp + p] = res;
-    if (do_update) pbest_step(pr, sw, a, p, t, res);
-  }
-  if (!do_update) return;
-  __threadfence();  // this CTA's scores and pbest rows, before its ticket
   __syncthreads();
+  EvalRes res;
+  if (!ok) {
+    res = invalid_res();
+  } else {
+    res = mse ? block_scan_mse(hc, hs, hq, B, pr.min_leaf, sc)
+              : pr.crit == SLM_GINI ? block_scan_cls<SLM_GINI>(hc, B, K, pr.min_leaf, sc)
+                                    : block_scan_cls<SLM_ENTROPY>(hc, B, K, pr.min_leaf, sc);
+    res.zmin = zmin;
+    res.inv_w = inv_w;
+  }
   if (threadIdx.x == 0) {
-    const int prev = atomicAdd(&sw.done[a], 1);
-    s_last = prev == (int)gridDim.y - 1;
-    if (s_last) sw.done[a] = 0;
+    sw.cur[(int64_t)a * pr.Pp + p] = res;
+    zz[0] = INT_MAX;  // ready for the next iteration
+    zz[1] = INT_MIN;
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  node_tail(pr, sw, a, t);
+  if (do_update && warp == 0) pbest_step(pr, sw, a, p, t, res);
 }
 
 // Initial swarm of each node: x ~ U[-1,1)^d, v ~ 0.1 U[-1,1)^d.
@@ -912,9 +978,9 @@ __global__ void k_swarm_init(Problem pr, Swarm sw,
   }
   if (threadIdx.x == 0) {
     sw.gb[a] = invalid_res();
+    sw.gb[gridDim.x + a] = invalid_res();
     sw.gpart[a] = 0;
     sw.giter[a] = 0;
-    sw.done[a] = 0;
   }
 }
 
@@ -953,8 +1019,8 @@ __global__ void k_bootstrap(uint64_t seed, uint32_t tree, int64_t n,
 // ---- launchers ---------------------------------------------------------------------
 
 static size_t hist_smem_bytes(const Problem& pr) {
-  const size_t hist = (hist_particle_bytes(pr.crit, pr.B, pr.K) * kWP + 127) & ~(size_t)127;
-  return hist + 2 * stage_bytes(pr.w != nullptr);
+  const size_t hist = (hist_copy_bytes(pr.crit, pr.B, pr.K) * kCopies + 127) & ~(size_t)127;
+  return hist + kStages * stage_bytes(pr.w != nullptr);
 }
 
 cudaError_t prepare_eval_kernels(const Problem& pr) {
@@ -995,12 +1061,18 @@ cudaError_t launch_project(const Problem& pr, const Swarm& sw, const WorkTile* t
 }
 
 int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_cluster) {
-  // clusters of S CTAs per (node, particle group): enough CTAs to fill the
-  // GPU twice, slices of at least 1024 entries
-  const int groups = (pr.P + kWP - 1) / kWP;
+  // clusters of S CTAs per (node, particle): as many as keep the whole grid
+  // resident in one wave, with slices of at least one staged piece
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist_scan, kThreads,
+                                                    hist_smem_bytes(pr)) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * n_sm;
   int S = 1;
-  while (2 * S <= max_cluster && (int64_t)A * groups * S < 2LL * n_sm &&
-         max_len / (2 * S) >= 1024)
+  while (2 * S <= max_cluster && (int64_t)A * pr.P * (2 * S) <= resident &&
+         max_len / (2 * S) >= kPiece)
     S *= 2;
   return S;
 }
@@ -1022,11 +1094,11 @@ int hist_max_cluster(const Problem& pr) {
 }
 
 cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
-                             int A, int S, int32_t* bins_out, int t, SwarmCoef co,
-                             int do_update, cudaStream_t st) {
+                             int A, int S, int32_t* bins_out, int t, int do_update,
+                             cudaStream_t st) {
   if (A <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(A * S), (unsigned)((pr.P + kWP - 1) / kWP), 1);
+  cfg.gridDim = dim3((unsigned)(A * S), (unsigned)pr.P, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = hist_smem_bytes(pr);
   cfg.stream = st;
@@ -1039,15 +1111,16 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc*
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, bins_out, t, co, do_update);
+  return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, bins_out, t, do_update);
 }
 
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
                         int t, SwarmCoef co, cudaStream_t st) {
-  const int64_t items = (int64_t)A * pr.P * ((pr.d + 3) / 4);
-  if (items <= 0) return cudaSuccess;
+  if (A <= 0) return cudaSuccess;
+  const int items = pr.P * ((pr.d + 3) / 4);
+  const int per_node = t >= sw.T ? 1 : (items + 127) / 128;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((items + 127) / 128), 1, 1);
+  cfg.gridDim = dim3((unsigned)A, (unsigned)per_node, 1);
   cfg.blockDim = dim3(128, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1055,7 +1128,7 @@ cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* node
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_move, pr, sw, nodes, A, t, co);
+  return cudaLaunchKernelEx(&cfg, k_move, pr, sw, nodes, t, co);
 }
 
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,

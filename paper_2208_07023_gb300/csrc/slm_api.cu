@@ -293,7 +293,7 @@ slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T, bool want_tr
   CK(ensure(c->ws[S_PBEST], sizeof(float) * apd));
   CK(ensure(c->ws[S_GBEST], sizeof(float) * (size_t)A * pr.d));
   CK(ensure(c->ws[S_PB], sizeof(EvalRes) * (size_t)A * pr.Pp));
-  CK(ensure(c->ws[S_GB], sizeof(EvalRes) * (size_t)A));
+  CK(ensure(c->ws[S_GB], sizeof(EvalRes) * 2 * (size_t)A));
   CK(ensure(c->ws[S_GPART], sizeof(int32_t) * (size_t)A));
   CK(ensure(c->ws[S_GITER], sizeof(int32_t) * (size_t)A));
   CK(ensure(c->ws[S_DONE], sizeof(int32_t) * (size_t)A));
@@ -332,12 +332,10 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
   if (n_tiles)
     CK(launch(c, SLM_K_PROJECT, pairs,
               [&] { return launch_project(pr, sw, dt, n_tiles, cap, c->stream); }));
-  const SwarmCoef none{};
   CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
-    return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? *co : none, co ? 1 : 0,
-                            c->stream);
+    return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
   }));
-  if (co && t < sw.T)
+  if (co)
     CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
               [&] { return launch_move(pr, sw, dn, A, t, *co, c->stream); }));
   return SLM_OK;
@@ -362,6 +360,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, const Problem& pr,
   for (int t = 0; t <= p->n_iters; ++t)
     if ((s = score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S)))
       return s;
+  sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
   *sw_out = sw;
   return SLM_OK;
 }

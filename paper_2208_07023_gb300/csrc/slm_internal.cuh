@@ -85,7 +85,7 @@ struct Swarm {
   float* gbest;   // [A, d]
   EvalRes* cur;   // [A, Pp]   scores of the current positions
   EvalRes* pb;    // [A, Pp]   pbest scores
-  EvalRes* gb;    // [A]       gbest score
+  EvalRes* gb;    // [2, A]    gbest score after iteration t in gb[(t & 1) * A + a]
   int32_t* gpart; // [A]
   int32_t* giter; // [A]
   double* trace;  // [A, T+1] or null
@@ -116,13 +116,13 @@ int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_clus
 // Largest power-of-two cluster size (<= 16) of the histogram kernel.
 int hist_max_cluster(const Problem& pr);
 // Scores of every (node, particle); bins_out[P, seg_len] (one node) or null.
-// With do_update, also the swarm update of iteration t (Algorithm 1) by the
-// CTA that finishes each node.
+// With do_update, also each particle's pbest step of iteration t.
 cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
                              const NodeDesc* nodes, int A, int S,
-                             int32_t* bins_out, int t, SwarmCoef co,
-                             int do_update, cudaStream_t st);
-// Eq. pso-1 move of every particle of A nodes to iteration t+1.
+                             int32_t* bins_out, int t, int do_update,
+                             cudaStream_t st);
+// gbest step of iteration t and (t < T) the Eq. pso-1 move of every particle
+// of A nodes to iteration t+1.
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                         int A, int t, SwarmCoef co, cudaStream_t st);
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
