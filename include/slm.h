@@ -143,6 +143,44 @@ slm_status slm_evaluate_swarm(slm_ctx* ctx, const slm_params* params,
                               const float* positions, int32_t n_pos,
                               slm_eval* out, int32_t* bins_out);
 
+/* Size of the fixed device array behind slm_evaluate_swarm_noalloc. */
+#define SLM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* slm_evaluate_swarm for callers that must not allocate device memory: code
+ * whose device memory is reserved up front and then handed out by its own
+ * pool (a host application or plugin framework that forbids cudaMalloc
+ * inside its work loop, since an allocation can block, synchronise the
+ * device or fail once memory is committed), or code running where the
+ * caching allocator is unavailable. The paper has no counterpart to this
+ * entry point.
+ *
+ * It performs no cudaMalloc / cudaFree and calls no allocating library
+ * routine. Its scratch is one fixed array of SLM_NOALLOC_SCRATCH_BYTES in the
+ * library's device memory, which every GPU that loads the library holds until
+ * the process exits. A call needs about 4 * (n_idx * (d + n_pos + 4) + P' * d)
+ * bytes of it, P' = n_pos rounded up to a multiple of 16 (each part rounded up
+ * to 256 bytes); larger calls return SLM_EUNSUPPORTED and do nothing.
+ *
+ * Same meaning as slm_evaluate_swarm, except: X, labels / y, sample_idx,
+ * weights and positions must be device pointers, and out[n_pos] is a device
+ * buffer the call fills; work runs on `cuda_stream` of `device`, and the call
+ * returns after that stream has finished it. The first call on a device looks
+ * up the array's device address (once per device); make that first call
+ * before any stream capture. Every call overwrites the array (the call resets
+ * what must start fresh), so calls whose work overlaps on the GPU -- on other
+ * streams or from other host threads -- race and must be serialised by the
+ * caller. Errors: SLM_EINVAL bad arguments, labels or sample indices;
+ * SLM_EUNSUPPORTED sizes beyond the array; SLM_ECUDA a CUDA call failed;
+ * SLM_ETIMEOUT a staged copy did not complete. */
+slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
+                                      const slm_params* params, const float* X,
+                                      int64_t n, int32_t d,
+                                      const int32_t* labels, const float* y,
+                                      const int32_t* sample_idx,
+                                      const uint32_t* weights, int64_t n_idx,
+                                      const float* positions, int32_t n_pos,
+                                      slm_eval* out);
+
 /* PSO split search on one node (Algorithm 1, synchronous updates: every
  * particle moves with the gB held at the end of the previous iteration; pB
  * and gB change only on a strictly lower loss, ties to the lower particle

@@ -93,6 +93,8 @@ def lib():
             "slm_profile": ([vp, C.c_int], C.c_int),
             "slm_kernel_stats": ([vp, i32, P(i64), P(C.c_double), P(C.c_double)], C.c_int),
             "slm_launch_count": ([vp, P(i64)], C.c_int),
+            "slm_evaluate_swarm_noalloc": ([C.c_int, vp, P(slm_params), vp, i64, i32, vp, vp,
+                                            vp, vp, i64, vp, i32, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
