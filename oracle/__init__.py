@@ -26,7 +26,7 @@ _SRC = os.path.join(_HERE, "slm_oracle.c")
 _HDR = os.path.join(_HERE, "slm_oracle.h")
 
 GINI, ENTROPY, MSE = 0, 1, 2
-F64, F32_MIRROR = 0, 1
+F64, F32_MIRROR, BF16_TOPK = 0, 1, 2
 PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2, PURPOSE_BOOTSTRAP = 1, 2, 3, 4, 5
 CRITERIA = {"gini": GINI, "entropy": ENTROPY, "mse": MSE}
 
@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("n_bins", C.c_int32), ("inertia", C.c_float), ("c1", C.c_float),
         ("c2", C.c_float), ("max_depth", C.c_int32), ("min_leaf", C.c_int32),
         ("seed", C.c_uint64), ("precision", C.c_int32),
-        ("n_threads", C.c_int32),
+        ("n_threads", C.c_int32), ("topk", C.c_int32),
     ]
 
 
@@ -105,6 +105,10 @@ def lib():
                                          C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
             L.ora_eval_swarm.restype = C.c_int
+            L.ora_score_bins.argtypes = [P(Params), C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_int64, C.c_void_p, P(Eval)]
+            L.ora_score_bins.restype = C.c_int
+            L.ora_bf16_round.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
             L.ora_node_split.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                          C.c_uint32, C.c_void_p, C.c_void_p, P(Split),
@@ -127,11 +131,12 @@ def _ptr(a: Optional[np.ndarray]):
 
 def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
                 n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8,
-                min_leaf=1, seed=1, precision=F32_MIRROR, n_threads=0) -> Params:
+                min_leaf=1, seed=1, precision=F32_MIRROR, n_threads=0,
+                topk=0) -> Params:
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
     return Params(crit, 0 if crit == MSE else n_classes, n_particles, n_iters,
                   n_bins, inertia, c1, c2, max_depth, min_leaf, seed, precision,
-                  n_threads)
+                  n_threads, topk)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -193,6 +198,30 @@ def eval_swarm(params: Params, X, labels, y, pos, idx=None, wts=None,
     if rc:
         raise ValueError(f"ora_eval_swarm failed: {rc}")
     return [_struct_dict(e) for e in out], bins, z
+
+
+def score_bins(params: Params, labels, y, bins, idx=None, wts=None) -> dict:
+    """Histogram + threshold scan of given bins[n_idx] of the node idx."""
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    n_idx = bins.size
+    idx = np.arange(n_idx, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, dtype=np.int32)
+    labels = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+    y = None if y is None else np.ascontiguousarray(y, dtype=np.float32)
+    wts = None if wts is None else np.ascontiguousarray(wts, dtype=np.uint32)
+    e = Eval()
+    rc = lib().ora_score_bins(C.byref(params), _ptr(labels), _ptr(y), _ptr(idx), _ptr(wts),
+                              n_idx, _ptr(bins), C.byref(e))
+    if rc:
+        raise ValueError(f"ora_score_bins failed: {rc}")
+    return _struct_dict(e)
+
+
+def bf16_round(a) -> np.ndarray:
+    """Nearest bfloat16 of each float32 (ties to even), as float32."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    out = np.empty_like(a)
+    lib().ora_bf16_round(_ptr(a), _ptr(out), a.size)
+    return out
 
 
 def _struct_dict(s) -> dict:

@@ -118,7 +118,7 @@ void ora_pso_step(const ora_params* p, int32_t P, int32_t d, double* x,
   for (int32_t i = 0; i < P; ++i) {
     for (int32_t j = 0; j < d; ++j) {
       int64_t e = (int64_t)i * d + j;
-      if (p->precision == ORA_F32_MIRROR) {
+      if (p->precision != ORA_F64) {
         float xv = (float)x[e], vv = (float)v[e];
         float inertia = p->inertia * vv;
         float cog = (p->c1 * (float)r1[e]) * ((float)pbest[e] - xv);
@@ -166,71 +166,56 @@ static int better(int criterion, int a_valid, double a_loss, uint64_t a_num,
   return a_loss < b_loss;
 }
 
-/* Scores one projection vector a (as double; float-valued in mirror mode).
- * scratch: n_idx doubles for z, n_idx ints for bins, hist buffers. */
-static void eval_one(const ora_params* p, const float* X, int32_t d,
-                     const int32_t* labels, const float* y, const int32_t* idx,
-                     const uint32_t* wts, int64_t n_idx, const double* a,
-                     ora_eval* out, double* z, int32_t* bins, uint64_t* cnt,
-                     double* msum, double* msq, int* tie) {
+/* Rounds a float to the nearest bfloat16 (8 significant bits), ties to even:
+ * add half of the dropped 16 bits (minus one unless the kept part is odd) and
+ * truncate. Infinities pass; NaNs stay NaN. */
+static float bf16_round(float f) {
+  uint32_t u;
+  memcpy(&u, &f, sizeof(u));
+  if ((u & 0x7f800000u) == 0x7f800000u) {
+    if (u & 0x007fffffu) u |= 0x00400000u; /* keep a NaN a NaN */
+  } else {
+    u += 0x7fffu + ((u >> 16) & 1u);
+  }
+  u &= 0xffff0000u;
+  memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
+void ora_bf16_round(const float* in, float* out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = bf16_round(in[i]);
+}
+
+/* Projection arithmetic of one scoring pass. */
+enum { PROJ_F64 = 0, PROJ_F32 = 1, PROJ_BF16 = 2 };
+
+/* Position of the lowest set bit of a finite non-zero double. */
+static int lsb_exponent(double t) {
+  int e;
+  double m = frexp(fabs(t), &e); /* t = m 2^e, m in [0.5, 1) */
+  uint64_t mi = (uint64_t)ldexp(m, 53);
+  int tz = 0;
+  while (!(mi & 1u)) {
+    mi >>= 1;
+    ++tz;
+  }
+  return e - 53 + tz;
+}
+
+/* Histogram over (bin, class) or (bin; weight, sum y, sum y^2), then the
+ * threshold scan over the B-1 interior edges (left = bins < b). */
+static void score_bins_into(const ora_params* p, const int32_t* labels,
+                            const float* y, const int32_t* idx,
+                            const uint32_t* wts, int64_t n_idx,
+                            const int32_t* bins, ora_eval* out, uint64_t* cnt,
+                            double* msum, double* msq, int* tie) {
   const int B = p->n_bins;
   const int K = p->n_classes;
-  memset(out, 0, sizeof(*out));
   out->valid = 0;
   out->bin = -1;
   out->loss = INFINITY;
-
-  /* Eq. (1): z = a^T x for every sample of the node. */
-  for (int64_t s = 0; s < n_idx; ++s) {
-    const float* xs = X + (int64_t)idx[s] * d;
-    if (p->precision == ORA_F32_MIRROR) {
-      float acc = 0.0f;
-      for (int32_t j = 0; j < d; ++j) acc = fmaf(xs[j], (float)a[j], acc);
-      z[s] = acc;
-    } else {
-      double acc = 0.0;
-      for (int32_t j = 0; j < d; ++j) acc += (double)xs[j] * a[j];
-      z[s] = acc;
-    }
-  }
-  if (n_idx <= 0) return;
-  double zmin = z[0], zmax = z[0];
-  for (int64_t s = 1; s < n_idx; ++s) {
-    if (z[s] < zmin) zmin = z[s];
-    if (z[s] > zmax) zmax = z[s];
-  }
-  out->zmin = zmin;
-  out->zmax = zmax;
-  if (!(zmax > zmin)) return; /* every sample projects to one point */
-
-  /* Uniform bins on [zmin, zmax]: bin = min(B-1, floor((z-zmin)*inv_w)). */
-  if (p->precision == ORA_F32_MIRROR) {
-    float fzmin = (float)zmin, fzmax = (float)zmax;
-    float width = fzmax - fzmin;
-    float inv_w = (float)B / width;
-    if (!isfinite(inv_w)) return;
-    out->inv_w = inv_w;
-    for (int64_t s = 0; s < n_idx; ++s) {
-      float off = (float)z[s] - fzmin;
-      float pos = off * inv_w;
-      int b = (int)floorf(pos);
-      if (b > B - 1) b = B - 1;
-      if (b < 0) b = 0;
-      bins[s] = b;
-    }
-  } else {
-    double inv_w = (double)B / (zmax - zmin);
-    if (!isfinite(inv_w)) return;
-    out->inv_w = inv_w;
-    for (int64_t s = 0; s < n_idx; ++s) {
-      int b = (int)floor((z[s] - zmin) * inv_w);
-      if (b > B - 1) b = B - 1;
-      if (b < 0) b = 0;
-      bins[s] = b;
-    }
-  }
-
-  /* Histogram over (bin, class) or (bin; weight, sum y, sum y^2). */
+  out->q_num = out->q_den = 0;
+  out->n_left = out->n_right = 0.0;
   if (p->criterion == ORA_MSE) {
     memset(cnt, 0, sizeof(uint64_t) * B);
     memset(msum, 0, sizeof(double) * B);
@@ -250,7 +235,6 @@ static void eval_one(const ora_params* p, const float* X, int32_t d,
     }
   }
 
-  /* Threshold scan over the B-1 interior edges: left = bins < b. */
   if (p->criterion == ORA_MSE) {
     uint64_t ntot = 0;
     double stot = 0.0, qtot = 0.0;
@@ -343,6 +327,111 @@ static void eval_one(const ora_params* p, const float* X, int32_t d,
   }
 }
 
+/* Scores one projection vector a (as double; float-valued in the float
+ * modes) with projection arithmetic `proj`. scratch: n_idx doubles for z,
+ * n_idx doubles for the error bounds of PROJ_BF16, n_idx ints for bins, hist
+ * buffers. *tie: a near-tie of double losses; *event: (PROJ_BF16) a sample
+ * whose dot product another exact-product, float-accumulating evaluation
+ * could round differently lies close enough to a bin edge to change bins. */
+static void eval_one(const ora_params* p, int proj, const float* X, int32_t d,
+                     const int32_t* labels, const float* y, const int32_t* idx,
+                     const uint32_t* wts, int64_t n_idx, const double* a,
+                     ora_eval* out, double* z, double* zb, int32_t* bins,
+                     uint64_t* cnt, double* msum, double* msq, int* tie,
+                     int* event) {
+  const int B = p->n_bins;
+  memset(out, 0, sizeof(*out));
+  out->valid = 0;
+  out->bin = -1;
+  out->loss = INFINITY;
+
+  /* Eq. (1): z = a^T x for every sample of the node. */
+  double bmax = 0.0;
+  for (int64_t s = 0; s < n_idx; ++s) {
+    const float* xs = X + (int64_t)idx[s] * d;
+    if (proj == PROJ_F32) {
+      float acc = 0.0f;
+      for (int32_t j = 0; j < d; ++j) acc = fmaf(xs[j], (float)a[j], acc);
+      z[s] = acc;
+    } else if (proj == PROJ_BF16) {
+      /* bfloat16 products are exact in double; their sum is formed in double
+       * and rounded once to float. Exact when every term is a multiple of
+       * 2^L and sum |terms| < 2^(L+24): then every partial sum is a float. */
+      double acc = 0.0, sabs = 0.0;
+      int L = 1 << 20;
+      for (int32_t j = 0; j < d; ++j) {
+        double t = (double)bf16_round(xs[j]) * (double)bf16_round((float)a[j]);
+        acc += t;
+        sabs += fabs(t);
+        if (t != 0.0) {
+          int l = lsb_exponent(t);
+          if (l < L) L = l;
+        }
+      }
+      z[s] = (double)(float)acc;
+      double bound = 0.0;
+      if (sabs > 0.0 && !(sabs < ldexp(1.0, L + 24)))
+        bound = (double)((d + 15) / 16 + 1) * ldexp(sabs, -22);
+      zb[s] = bound;
+      if (bound > bmax) bmax = bound;
+    } else {
+      double acc = 0.0;
+      for (int32_t j = 0; j < d; ++j) acc += (double)xs[j] * a[j];
+      z[s] = acc;
+    }
+  }
+  if (n_idx <= 0) return;
+  double zmin = z[0], zmax = z[0];
+  for (int64_t s = 1; s < n_idx; ++s) {
+    if (z[s] < zmin) zmin = z[s];
+    if (z[s] > zmax) zmax = z[s];
+  }
+  out->zmin = zmin;
+  out->zmax = zmax;
+  if (!(zmax > zmin)) {
+    if (proj == PROJ_BF16 && bmax > 0.0) *event = 1;
+    return; /* every sample projects to one point */
+  }
+
+  /* Uniform bins on [zmin, zmax]: bin = min(B-1, floor((z-zmin)*inv_w)). */
+  if (proj != PROJ_F64) {
+    float fzmin = (float)zmin, fzmax = (float)zmax;
+    float width = fzmax - fzmin;
+    float inv_w = (float)B / width;
+    if (!isfinite(inv_w)) return;
+    out->inv_w = inv_w;
+    for (int64_t s = 0; s < n_idx; ++s) {
+      float off = (float)z[s] - fzmin;
+      float pos = off * inv_w;
+      int b = (int)floorf(pos);
+      if (b > B - 1) b = B - 1;
+      if (b < 0) b = 0;
+      bins[s] = b;
+      if (proj == PROJ_BF16 && bmax > 0.0) {
+        /* edges move with zmin / zmax by at most bmax each */
+        double margin = (zb[s] + 2.0 * bmax) * (double)inv_w + ldexp((double)B, -21);
+        double k = floor((double)pos + 0.5);
+        if (k >= 1.0 && k <= (double)(B - 1) && fabs((double)pos - k) <= margin) *event = 1;
+      }
+    }
+  } else {
+    double inv_w = (double)B / (zmax - zmin);
+    if (!isfinite(inv_w)) return;
+    out->inv_w = inv_w;
+    for (int64_t s = 0; s < n_idx; ++s) {
+      int b = (int)floor((z[s] - zmin) * inv_w);
+      if (b > B - 1) b = B - 1;
+      if (b < 0) b = 0;
+      bins[s] = b;
+    }
+  }
+  double keep_zmin = out->zmin, keep_zmax = out->zmax, keep_inv = out->inv_w;
+  score_bins_into(p, labels, y, idx, wts, n_idx, bins, out, cnt, msum, msq, tie);
+  out->zmin = keep_zmin;
+  out->zmax = keep_zmax;
+  out->inv_w = keep_inv;
+}
+
 static int check_params(const ora_params* p, int32_t d) {
   if (!p || d <= 0 || p->n_bins < 2 || p->min_leaf < 1) return -1;
   if (p->criterion == ORA_MSE) return 0;
@@ -351,50 +440,95 @@ static int check_params(const ora_params* p, int32_t d) {
   return 0;
 }
 
-static int eval_all(const ora_params* p, const float* X, int32_t d,
+/* Scores particles sel[0..m) (sel NULL: 0..m-1) of pos[*, d]; out[q] is
+ * the score of particle sel[q]. */
+static int eval_all(const ora_params* p, int proj, const float* X, int32_t d,
                     const int32_t* labels, const float* y, const int32_t* idx,
                     const uint32_t* wts, int64_t n_idx, const double* pos,
-                    int32_t P, ora_eval* out, int32_t* bins_out, double* z_out,
-                    int* tie_any) {
+                    const int32_t* sel, int32_t m, ora_eval* out,
+                    int32_t* bins_out, double* z_out, int* tie_any,
+                    int* event_any) {
   const int B = p->n_bins;
   const int K = p->criterion == ORA_MSE ? 1 : p->n_classes;
   int err = 0;
-  int tie = 0;
+  int tie = 0, event = 0;
 #ifdef _OPENMP
   int nt = p->n_threads > 0 ? p->n_threads : omp_get_max_threads();
-#pragma omp parallel num_threads(nt) reduction(| : err, tie)
+#pragma omp parallel num_threads(nt) reduction(| : err, tie, event)
 #endif
   {
-    double* z = (double*)malloc(sizeof(double) * (size_t)(n_idx > 0 ? n_idx : 1));
-    int32_t* bins = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_idx > 0 ? n_idx : 1));
+    size_t nz = (size_t)(n_idx > 0 ? n_idx : 1);
+    double* z = (double*)malloc(sizeof(double) * nz);
+    double* zb = (double*)malloc(sizeof(double) * nz);
+    int32_t* bins = (int32_t*)malloc(sizeof(int32_t) * nz);
     uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)B * K);
     double* msum = (double*)malloc(sizeof(double) * (size_t)B);
     double* msq = (double*)malloc(sizeof(double) * (size_t)B);
-    if (!z || !bins || !cnt || !msum || !msq) {
+    if (!z || !zb || !bins || !cnt || !msum || !msq) {
       err = 1;
     } else {
 #ifdef _OPENMP
 #pragma omp for schedule(static)
 #endif
-      for (int32_t i = 0; i < P; ++i) {
-        int t = 0;
+      for (int32_t q = 0; q < m; ++q) {
+        const int32_t i = sel ? sel[q] : q;
+        int t = 0, ev = 0;
         for (int64_t s = 0; s < n_idx; ++s) bins[s] = -1;
-        eval_one(p, X, d, labels, y, idx, wts, n_idx, pos + (int64_t)i * d,
-                 &out[i], z, bins, cnt, msum, msq, &t);
+        eval_one(p, proj, X, d, labels, y, idx, wts, n_idx, pos + (int64_t)i * d,
+                 &out[q], z, zb, bins, cnt, msum, msq, &t, &ev);
         tie |= t;
+        event |= ev;
         if (bins_out)
-          memcpy(bins_out + (int64_t)i * n_idx, bins, sizeof(int32_t) * (size_t)n_idx);
-        if (z_out) memcpy(z_out + (int64_t)i * n_idx, z, sizeof(double) * (size_t)n_idx);
+          memcpy(bins_out + (int64_t)q * n_idx, bins, sizeof(int32_t) * (size_t)n_idx);
+        if (z_out) memcpy(z_out + (int64_t)q * n_idx, z, sizeof(double) * (size_t)n_idx);
       }
     }
     free(z);
+    free(zb);
     free(bins);
     free(cnt);
     free(msum);
     free(msq);
   }
   if (tie_any) *tie_any = tie;
+  if (event_any) *event_any = event;
   return err ? -2 : 0;
+}
+
+static int proj_of(const ora_params* p) {
+  return p->precision == ORA_F64 ? PROJ_F64
+                                 : p->precision == ORA_F32_MIRROR ? PROJ_F32 : PROJ_BF16;
+}
+
+/* The k particles with the best scores ev[0..P), ties to the lower index,
+ * returned in increasing particle order. *tie: the k-th and the (k+1)-th
+ * best are a near-tie of double losses. */
+static void select_topk(const ora_params* p, const ora_eval* ev, int32_t P,
+                        int32_t k, int32_t* sel, int* tie) {
+  char* taken = (char*)calloc((size_t)P, 1);
+  int32_t last = -1;
+  for (int32_t q = 0; q <= k && q < P; ++q) {
+    int32_t best = -1;
+    for (int32_t i = 0; i < P; ++i) {
+      if (taken[i]) continue;
+      if (best < 0 || better(p->criterion, ev[i].valid, ev[i].loss, ev[i].q_num,
+                             ev[i].q_den, ev[best].valid, ev[best].loss,
+                             ev[best].q_num, ev[best].q_den))
+        best = i;
+    }
+    if (q == k) { /* first one left out */
+      if (p->criterion != ORA_GINI && last >= 0 && ev[best].valid && ev[last].valid &&
+          near_tie(ev[best].loss, ev[last].loss))
+        *tie = 1;
+      break;
+    }
+    taken[best] = 1;
+    last = best;
+  }
+  int32_t c = 0;
+  for (int32_t i = 0; i < P && c < k; ++i)
+    if (taken[i]) sel[c++] = i;
+  free(taken);
 }
 
 int ora_eval_swarm(const ora_params* p, const float* X, int32_t d,
@@ -404,8 +538,51 @@ int ora_eval_swarm(const ora_params* p, const float* X, int32_t d,
                    double* z_out) {
   if (check_params(p, d) || P < 1 || n_idx < 0 || !X || !idx || !pos || !out)
     return -1;
-  return eval_all(p, X, d, labels, y, idx, wts, n_idx, pos, P, out, bins_out,
-                  z_out, NULL);
+  int rc = eval_all(p, proj_of(p), X, d, labels, y, idx, wts, n_idx, pos, NULL, P,
+                    out, bins_out, z_out, NULL, NULL);
+  if (rc || p->precision != ORA_BF16_TOPK || p->topk <= 0) return rc;
+  const int32_t k = p->topk < P ? p->topk : P;
+  int32_t* sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  ora_eval* ef = (ora_eval*)malloc(sizeof(ora_eval) * (size_t)k);
+  if (!sel || !ef) {
+    free(sel);
+    free(ef);
+    return -2;
+  }
+  int tie = 0;
+  select_topk(p, out, P, k, sel, &tie);
+  rc = eval_all(p, PROJ_F32, X, d, labels, y, idx, wts, n_idx, pos, sel, k, ef,
+                NULL, NULL, NULL, NULL);
+  for (int32_t q = 0; q < k && !rc; ++q) out[sel[q]] = ef[q];
+  free(sel);
+  free(ef);
+  return rc;
+}
+
+int ora_score_bins(const ora_params* p, const int32_t* labels, const float* y,
+                   const int32_t* idx, const uint32_t* wts, int64_t n_idx,
+                   const int32_t* bins, ora_eval* out) {
+  if (check_params(p, 1) || n_idx < 0 || !idx || !bins || !out) return -1;
+  if (p->criterion == ORA_MSE ? !y : !labels) return -1;
+  for (int64_t s = 0; s < n_idx; ++s)
+    if (bins[s] < 0 || bins[s] >= p->n_bins) return -1;
+  const int B = p->n_bins;
+  const int K = p->criterion == ORA_MSE ? 1 : p->n_classes;
+  uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)B * K);
+  double* msum = (double*)malloc(sizeof(double) * (size_t)B);
+  double* msq = (double*)malloc(sizeof(double) * (size_t)B);
+  int rc = 0;
+  if (!cnt || !msum || !msq) {
+    rc = -2;
+  } else {
+    int tie = 0;
+    memset(out, 0, sizeof(*out));
+    score_bins_into(p, labels, y, idx, wts, n_idx, bins, out, cnt, msum, msq, &tie);
+  }
+  free(cnt);
+  free(msum);
+  free(msq);
+  return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -431,7 +608,7 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
                    double* gbest_out, double* dir_out, ora_split* out,
                    double* trace_loss, int32_t* trace_particle) {
   if (check_params(p, d) || p->n_particles < 1 || p->n_iters < 0 || n_idx < 0 ||
-      !X || !idx || !out)
+      !X || !idx || !out || (p->precision == ORA_BF16_TOPK && p->topk < 1))
     return -1;
   const int32_t P = p->n_particles;
   const int32_t T = p->n_iters;
@@ -445,8 +622,12 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
   float* u = (float*)calloc((size_t)PD, sizeof(float));
   ora_eval* ev = (ora_eval*)calloc((size_t)P, sizeof(ora_eval));
   ora_eval* pbe = (ora_eval*)calloc((size_t)P, sizeof(ora_eval));
+  const int bf16 = p->precision == ORA_BF16_TOPK;
+  const int32_t k = bf16 ? (p->topk < P ? p->topk : P) : 0;
+  int32_t* sel = (int32_t*)calloc((size_t)(k > 0 ? k : 1), sizeof(int32_t));
+  ora_eval* ef = (ora_eval*)calloc((size_t)(k > 0 ? k : 1), sizeof(ora_eval));
   int rc = 0;
-  if (!x || !v || !pb || !gb || !r1 || !r2 || !u || !ev || !pbe) {
+  if (!x || !v || !pb || !gb || !r1 || !r2 || !u || !ev || !pbe || !sel || !ef) {
     rc = -2;
     goto done;
   }
@@ -458,7 +639,7 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
   for (int64_t e = 0; e < PD; ++e) x[e] = (double)(2.0f * u[e] - 1.0f);
   ora_swarm_uniforms(p->seed, node_uid, 0, P, d, ORA_PURPOSE_INIT_V, u);
   for (int64_t e = 0; e < PD; ++e) {
-    if (p->precision == ORA_F32_MIRROR)
+    if (p->precision != ORA_F64)
       v[e] = (double)(0.1f * (2.0f * u[e] - 1.0f));
     else
       v[e] = 0.1 * (double)(2.0f * u[e] - 1.0f);
@@ -475,9 +656,21 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
       for (int64_t e = 0; e < PD; ++e) r2[e] = u[e];
       ora_pso_step(p, P, d, x, v, pb, gb, r1, r2);
     }
-    int tie = 0;
-    rc = eval_all(p, X, d, labels, y, idx, wts, n_idx, x, P, ev, NULL, NULL, &tie);
+    int tie = 0, event = 0;
+    rc = eval_all(p, proj_of(p), X, d, labels, y, idx, wts, n_idx, x, NULL, P, ev,
+                  NULL, NULL, &tie, &event);
     if (rc) goto done;
+    if (bf16) {
+      /* re-score the k best on the float projection; their scores replace
+       * the bfloat16 ones */
+      int tie2 = 0;
+      select_topk(p, ev, P, k, sel, &tie);
+      rc = eval_all(p, PROJ_F32, X, d, labels, y, idx, wts, n_idx, x, sel, k, ef,
+                    NULL, NULL, &tie2, NULL);
+      if (rc) goto done;
+      tie |= tie2;
+      for (int32_t q = 0; q < k; ++q) ev[sel[q]] = ef[q];
+    }
     for (int32_t i = 0; i < P; ++i) {
       const ora_eval* e = &ev[i];
       int improved = 0;
@@ -491,6 +684,7 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
       if (!improved) continue;
       pbe[i] = *e;
       memcpy(pb + (int64_t)i * d, x + (int64_t)i * d, sizeof(double) * d);
+      if (bf16) continue; /* gbest below, from the re-scored particles */
       int first = (t == 0 && i == 0);
       if (!first && gbe.valid && e->valid && near_tie(e->loss, gbe.loss)) tie = 1;
       if (first || better(p->criterion, e->valid, e->loss, e->q_num, e->q_den,
@@ -501,8 +695,21 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
         memcpy(gb, x + (int64_t)i * d, sizeof(double) * d);
       }
     }
+    for (int32_t q = 0; bf16 && q < k; ++q) {
+      const int32_t i = sel[q];
+      const ora_eval* e = &ev[i];
+      int first = (t == 0 && q == 0);
+      if (!first && gbe.valid && e->valid && near_tie(e->loss, gbe.loss)) tie = 1;
+      if (first || better(p->criterion, e->valid, e->loss, e->q_num, e->q_den,
+                          gbe.valid, gbe.loss, gbe.q_num, gbe.q_den)) {
+        gbe = *e;
+        gpart = i;
+        giter = t;
+        memcpy(gb, x + (int64_t)i * d, sizeof(double) * d);
+      }
+    }
     if (p->criterion == ORA_GINI) tie = 0; /* exact rationals: no near-ties */
-    if (tie && out->first_near_tie < 0) out->first_near_tie = t;
+    if ((tie || event) && out->first_near_tie < 0) out->first_near_tie = t;
     if (trace_loss) trace_loss[t] = gbe.valid ? gbe.loss : INFINITY;
     if (trace_particle) trace_particle[t] = gpart;
   }
@@ -511,7 +718,7 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
   out->particle = gpart;
   out->iter_of_best = giter;
   if (gbe.valid) {
-    if (p->precision == ORA_F32_MIRROR)
+    if (p->precision != ORA_F64)
       out->threshold = (double)((float)gbe.zmin + (float)gbe.bin / (float)gbe.inv_w);
     else
       out->threshold = gbe.zmin + (double)gbe.bin / gbe.inv_w;
@@ -534,6 +741,8 @@ done:
   free(u);
   free(ev);
   free(pbe);
+  free(sel);
+  free(ef);
   return rc;
 }
 
@@ -551,7 +760,7 @@ static int split_bin(const ora_params* p, const double* dir, double zmin,
                      double inv_w, const float* xs, int32_t d) {
   const int B = p->n_bins;
   int b;
-  if (p->precision == ORA_F32_MIRROR) {
+  if (p->precision != ORA_F64) {
     float acc = 0.0f;
     for (int32_t j = 0; j < d; ++j) acc = fmaf(xs[j], (float)dir[j], acc);
     float off = acc - (float)zmin;

@@ -26,8 +26,17 @@ enum { ORA_GINI = 0, ORA_ENTROPY = 1, ORA_MSE = 2 };
  * ORA_F64:        every floating-point step in double precision.
  * ORA_F32_MIRROR: projection as a sequential fmaf over features, binning and
  *                 swarm update in float with one IEEE rounding per operation;
- *                 the criterion stays in double / exact integers. */
-enum { ORA_F64 = 0, ORA_F32_MIRROR = 1 };
+ *                 the criterion stays in double / exact integers.
+ * ORA_BF16_TOPK:  every particle is first scored on a reduced-precision
+ *                 projection: row and position rounded to bfloat16 (round to
+ *                 nearest even), their dot product formed exactly and rounded
+ *                 once to float. The `topk` particles with the lowest such
+ *                 loss (ties to the lower index) are re-scored on the
+ *                 ORA_F32_MIRROR projection. pbest takes the float score of
+ *                 the re-scored particles and the bfloat16 score of the rest;
+ *                 gbest is chosen among the re-scored particles only. Binning,
+ *                 swarm update and partition follow ORA_F32_MIRROR. */
+enum { ORA_F64 = 0, ORA_F32_MIRROR = 1, ORA_BF16_TOPK = 2 };
 
 /* Philox stream purposes (high byte of counter word 3). */
 enum {
@@ -49,8 +58,9 @@ typedef struct {
   int32_t max_depth;    /* nodes at this depth are leaves */
   int32_t min_leaf;     /* >= 1, weighted sample count per child */
   uint64_t seed;        /* Philox key */
-  int32_t precision;    /* ORA_F64 / ORA_F32_MIRROR */
+  int32_t precision;    /* ORA_F64 / ORA_F32_MIRROR / ORA_BF16_TOPK */
   int32_t n_threads;    /* 0: OpenMP default */
+  int32_t topk;         /* ORA_BF16_TOPK: particles re-scored per evaluation */
 } ora_params;
 
 /* Result of scoring one projection vector on one node. */
@@ -74,7 +84,11 @@ typedef struct {
   double loss;
   uint64_t q_num, q_den;
   double n_left, n_right;
-  int32_t first_near_tie;   /* first iteration with a near-tie, -1 if none */
+  int32_t first_near_tie;   /* first iteration at which another correct
+                               implementation may take a different path: a
+                               near-tie of double losses, or (ORA_BF16_TOPK) a
+                               sample whose bfloat16 dot product is not exact
+                               in float and lies near a bin edge; -1 if none */
 } ora_split;
 
 /* Tree in heap layout: node h has children 2h+1 and 2h+2; H = 2^(D+1)-1. */
@@ -113,12 +127,24 @@ void ora_pso_step(const ora_params* p, int32_t n_particles, int32_t d,
 
 /* Score P projection vectors pos[P*d] on the node given by idx[n_idx]
  * (entry weights wts, NULL = 1). Optional outputs: bins_out[P*n_idx] and
- * z_out[P*n_idx] (particle-major). */
+ * z_out[P*n_idx] (particle-major). In ORA_BF16_TOPK mode bins / z are those
+ * of the bfloat16 projection, and out[] holds the scores one search
+ * iteration passes to pbest: the float re-score of the `topk` best particles
+ * (none when topk == 0), the bfloat16 score of the others. */
 int ora_eval_swarm(const ora_params* p, const float* X, int32_t d,
                    const int32_t* labels, const float* y, const int32_t* idx,
                    const uint32_t* wts, int64_t n_idx, const double* pos,
                    int32_t n_particles, ora_eval* out, int32_t* bins_out,
                    double* z_out);
+
+/* Histogram and threshold scan of given bins (bins[s] in [0, B)) of the node
+ * idx[n_idx]: fills valid, bin, loss, q_num, q_den, n_left, n_right of *out. */
+int ora_score_bins(const ora_params* p, const int32_t* labels, const float* y,
+                   const int32_t* idx, const uint32_t* wts, int64_t n_idx,
+                   const int32_t* bins, ora_eval* out);
+
+/* Round each float to the nearest bfloat16 (ties to even), returned as float. */
+void ora_bf16_round(const float* in, float* out, int64_t n);
 
 /* PSO split search on one node (Algorithm 1 with synchronous updates).
  * gbest_out[d]: raw position; dir_out[d]: gbest / ||gbest||;
