@@ -32,6 +32,7 @@
  * Limits.    1 <= d <= 1024; 1 <= P (n_particles) <= 256; 2 <= B (n_bins) <= 256;
  *            2 <= K (n_classes) <= 32; 0 <= max_depth <= 15; n < 2^31;
  *            per-particle histogram B*K*4 bytes <= 10240 (classification).
+ *            SLM_PROJ_BF16_TOPK: round16(P) * round16(d) * 2 <= 131072.
  */
 #ifndef SLM_H
 #define SLM_H
@@ -59,7 +60,16 @@ typedef enum {
 typedef enum { SLM_GINI = 0, SLM_ENTROPY = 1, SLM_MSE = 2 } slm_criterion;
 
 /* Projection arithmetic. FP32: z = sum_j x_j a_j as one fused multiply-add
- * per feature in increasing j, starting from +0. */
+ * per feature in increasing j, starting from +0.
+ * BF16_TOPK: every particle is first scored on z~ = sum_j bf16(x_j) bf16(a_j)
+ * (bfloat16 operands rounded to nearest even, exact products, FP32
+ * accumulation in the tensor cores' order); per node the `topk` particles
+ * with the best such score (ties to the lower index) are re-scored on the
+ * FP32 projection. pbest takes the FP32 score of a re-scored particle and the
+ * bfloat16 score of the others; gbest is chosen among the re-scored
+ * particles only, so every gB score and every split is an FP32 score. This
+ * mode is not in the paper: it trades the projection's precision for tensor-
+ * core throughput and keeps the split decisions in FP32. */
 typedef enum { SLM_PROJ_FP32 = 0, SLM_PROJ_BF16_TOPK = 1 } slm_proj;
 
 typedef struct slm_params {
@@ -68,7 +78,9 @@ typedef struct slm_params {
   int32_t n_particles; /* P: swarm size (Eq. pso_a) */
   int32_t n_iters;     /* T: swarm updates after the initial evaluation */
   int32_t n_bins;      /* B: uniform bins per projection */
-  int32_t topk;        /* SLM_PROJ_BF16_TOPK only (unused otherwise) */
+  int32_t topk;        /* SLM_PROJ_BF16_TOPK: particles re-scored in FP32 per
+                          node and iteration, 1..P (slm_evaluate_swarm: 0..P,
+                          0 = none); unused otherwise */
   float inertia;       /* omega in Eq. pso-1 */
   float c1, c2;        /* learning factors in Eq. pso-1 */
   int32_t max_depth;   /* nodes at this depth are leaves */
@@ -134,7 +146,10 @@ slm_status slm_bootstrap(slm_ctx* ctx, uint64_t seed, uint32_t tree_id,
  * n rows) with multiplicities weights[n_idx] (NULL = 1). Exactly one of
  * labels[n] (classification) and y[n] (MSE) is non-NULL. out[n_pos] is
  * written; bins_out[n_pos*n_idx] (optional) receives bin(z) per particle and
- * node entry. Uses params: criterion, n_classes, n_bins, min_leaf. */
+ * node entry. Uses params: criterion, n_classes, n_bins, min_leaf, proj,
+ * topk. With SLM_PROJ_BF16_TOPK, bins_out holds the bfloat16 projection's
+ * bins and out[] the scores one search iteration passes to pbest: the FP32
+ * re-score of the topk best particles, the bfloat16 score of the others. */
 slm_status slm_evaluate_swarm(slm_ctx* ctx, const slm_params* params,
                               const float* X, int64_t n, int32_t d,
                               const int32_t* labels, const float* y,
@@ -257,7 +272,10 @@ typedef enum {
   SLM_K_COMPACT = 6,
   SLM_K_GATHER = 7,       /* rows of a node / root into entry order */
   SLM_K_OTHER = 8,        /* validation, bootstrap, index setup, prediction */
-  SLM_K_COUNT = 9
+  SLM_K_PROJECT_MMA = 9,  /* z in bfloat16 on the tensor cores (BF16_TOPK) */
+  SLM_K_TOPK = 10,        /* BF16_TOPK: position conversion, top-k selection,
+                             score merge with the pbest / gbest steps */
+  SLM_K_COUNT = 11
 } slm_kernel;
 
 /* on != 0 brackets every later launch of the context with CUDA events on its

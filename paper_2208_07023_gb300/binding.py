@@ -22,7 +22,7 @@ SLM_PROJ_FP32, SLM_PROJ_BF16_TOPK = 0, 1
 CRITERIA = {"gini": SLM_GINI, "entropy": SLM_ENTROPY, "mse": SLM_MSE}
 PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2 = 1, 2, 3, 4
 KERNELS = ["project", "hist_scan", "move", "swarm_init", "node_stats",
-           "partition", "compact", "gather", "other"]
+           "partition", "compact", "gather", "other", "project_mma", "topk"]
 
 
 class slm_params(C.Structure):

@@ -1,0 +1,144 @@
+// Device helpers shared by the kernels of libslm: programmatic dependent
+// launch, ordered-int floats, score comparison, bulk copies with bounded
+// mbarrier waits, and the pbest step of Algorithm 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "slm_internal.cuh"
+
+namespace slm {
+namespace {
+
+// ---- small helpers -----------------------------------------------------------
+
+// Programmatic dependent launch: the next kernel of the stream may begin
+// launching once every CTA of this grid has passed pdl_trigger(); pdl_wait()
+// blocks until the previous grid has completed and its writes are visible.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+__device__ __forceinline__ int f2ord(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) {
+  return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// a*b > c*d on unsigned 128-bit products.
+__device__ __forceinline__ bool prod_gt(uint64_t a, uint64_t b, uint64_t c,
+                                        uint64_t d) {
+  const uint64_t h1 = __umul64hi(a, b), l1 = a * b;
+  const uint64_t h2 = __umul64hi(c, d), l2 = c * d;
+  return h1 > h2 || (h1 == h2 && l1 > l2);
+}
+
+// Strictly lower loss? Gini compares the exact rationals Q = num/den (larger
+// Q = lower loss); entropy and MSE compare the double loss.
+__device__ __forceinline__ bool better(const EvalRes& a, const EvalRes& b,
+                                       int crit) {
+  if (!a.valid) return false;
+  if (!b.valid) return true;
+  if (crit == SLM_GINI) return prod_gt(a.num, b.den, b.num, a.den);
+  return a.loss < b.loss;
+}
+
+__device__ __forceinline__ EvalRes invalid_res() {
+  EvalRes r;
+  r.loss = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+  r.num = 0;
+  r.den = 0;
+  r.zmin = 0.f;
+  r.inv_w = 0.f;
+  r.bin = -1;
+  r.valid = 0;
+  r.nl = 0;
+  r.nr = 0;
+  return r;
+}
+
+__device__ __forceinline__ EvalRes shfl_res(const EvalRes& a, int src) {
+  EvalRes r;
+  r.loss = __shfl_sync(0xffffffffu, a.loss, src);
+  r.num = __shfl_sync(0xffffffffu, a.num, src);
+  r.den = __shfl_sync(0xffffffffu, a.den, src);
+  r.zmin = __shfl_sync(0xffffffffu, a.zmin, src);
+  r.inv_w = __shfl_sync(0xffffffffu, a.inv_w, src);
+  r.bin = __shfl_sync(0xffffffffu, a.bin, src);
+  r.valid = __shfl_sync(0xffffffffu, a.valid, src);
+  r.nl = __shfl_sync(0xffffffffu, a.nl, src);
+  r.nr = __shfl_sync(0xffffffffu, a.nr, src);
+  return r;
+}
+
+
+// ---- bulk copies (TMA) with mbarrier completion -------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> this CTA's shared memory; 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Waits for phase `parity` of the barrier, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  const uint32_t a = smem_addr(bar);
+  for (int i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr int kWaitPolls = 1 << 20;  // bounded: a lost copy ends the kernel, not the GPU
+
+
+// Algorithm 1, pbest step of particle p after evaluation t (one warp): strict
+// "<" against the particle's best so far; the position is kept on improvement.
+__device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, int a, int p,
+                                           int t, const EvalRes& cur) {
+  const int lane = threadIdx.x & 31;
+  EvalRes* pb = sw.pb + (int64_t)a * pr.Pp + p;
+  int imp = 0;
+  if (lane == 0) {
+    imp = (t == 0) || better(cur, *pb, pr.crit);
+    if (imp) *pb = cur;
+  }
+  imp = __shfl_sync(0xffffffffu, imp, 0);
+  if (!imp) return;
+  const int64_t o = ((int64_t)a * pr.Pp + p) * pr.d;
+  for (int j = lane; j < pr.d; j += 32) sw.pbest[o + j] = sw.pos[o + j];
+}
+
+}  // namespace
+}  // namespace slm

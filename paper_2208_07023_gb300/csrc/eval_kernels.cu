@@ -33,82 +33,11 @@
 
 #include "philox.cuh"
 #include "slm_internal.cuh"
+#include "device_util.cuh"
 
 namespace slm {
 
 namespace {
-
-// ---- small helpers -----------------------------------------------------------
-
-// Programmatic dependent launch: the next kernel of the stream may begin
-// launching once every CTA of this grid has passed pdl_trigger(); pdl_wait()
-// blocks until the previous grid has completed and its writes are visible.
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-
-__device__ __forceinline__ int f2ord(float f) {
-  int i = __float_as_int(f);
-  return i >= 0 ? i : i ^ 0x7fffffff;
-}
-__device__ __forceinline__ float ord2f(int i) {
-  return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
-}
-
-// a*b > c*d on unsigned 128-bit products.
-__device__ __forceinline__ bool prod_gt(uint64_t a, uint64_t b, uint64_t c,
-                                        uint64_t d) {
-  const uint64_t h1 = __umul64hi(a, b), l1 = a * b;
-  const uint64_t h2 = __umul64hi(c, d), l2 = c * d;
-  return h1 > h2 || (h1 == h2 && l1 > l2);
-}
-
-// Strictly lower loss? Gini compares the exact rationals Q = num/den (larger
-// Q = lower loss); entropy and MSE compare the double loss.
-__device__ __forceinline__ bool better(const EvalRes& a, const EvalRes& b,
-                                       int crit) {
-  if (!a.valid) return false;
-  if (!b.valid) return true;
-  if (crit == SLM_GINI) return prod_gt(a.num, b.den, b.num, a.den);
-  return a.loss < b.loss;
-}
-
-__device__ __forceinline__ EvalRes invalid_res() {
-  EvalRes r;
-  r.loss = __longlong_as_double(0x7ff0000000000000LL);  // +inf
-  r.num = 0;
-  r.den = 0;
-  r.zmin = 0.f;
-  r.inv_w = 0.f;
-  r.bin = -1;
-  r.valid = 0;
-  r.nl = 0;
-  r.nr = 0;
-  return r;
-}
-
-__device__ __forceinline__ EvalRes shfl_res(const EvalRes& a, int src) {
-  EvalRes r;
-  r.loss = __shfl_sync(0xffffffffu, a.loss, src);
-  r.num = __shfl_sync(0xffffffffu, a.num, src);
-  r.den = __shfl_sync(0xffffffffu, a.den, src);
-  r.zmin = __shfl_sync(0xffffffffu, a.zmin, src);
-  r.inv_w = __shfl_sync(0xffffffffu, a.inv_w, src);
-  r.bin = __shfl_sync(0xffffffffu, a.bin, src);
-  r.valid = __shfl_sync(0xffffffffu, a.valid, src);
-  r.nl = __shfl_sync(0xffffffffu, a.nl, src);
-  r.nr = __shfl_sync(0xffffffffu, a.nr, src);
-  return r;
-}
-
-// Lexicographic (score, bin): the lowest edge among equal scores.
-__device__ __forceinline__ bool edge_first(const EvalRes& a, const EvalRes& b,
-                                           int crit) {
-  if (better(a, b, crit)) return true;
-  if (better(b, a, crit)) return false;
-  return a.valid && b.valid && a.bin < b.bin;
-}
 
 __device__ __forceinline__ double xlogx(uint32_t c) {
   const double x = (double)c;
@@ -124,8 +53,6 @@ __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
 }
 
 // ---- threshold scans (one warp, one particle) ----------------------------------
-
-constexpr int kMaxBPL = kMaxBins / 32;
 
 // Shared scratch of the block-wide scans.
 struct ScanScratch {
@@ -407,52 +334,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// ---- bulk copies (TMA) with mbarrier completion -------------------------------
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// 1D bulk copy global -> this CTA's shared memory; 16-byte aligned, bytes % 16 == 0.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-// Waits for phase `parity` of the barrier, at most `limit` polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
-  const uint32_t a = smem_addr(bar);
-  for (int i = 0; i < limit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-constexpr int kWaitPolls = 1 << 20;  // bounded: a lost copy ends the kernel, not the GPU
-
 // ---- projection -------------------------------------------------------------------
 
 constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPG * kXS);
@@ -599,22 +480,6 @@ __global__ void __launch_bounds__(kThreads, 2)
 // ---- swarm update ----------------------------------------------------------------
 
 
-// Algorithm 1, pbest step of particle p after evaluation t (one warp): strict
-// "<" against the particle's best so far; the position is kept on improvement.
-__device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, int a, int p,
-                                           int t, const EvalRes& cur) {
-  const int lane = threadIdx.x & 31;
-  EvalRes* pb = sw.pb + (int64_t)a * pr.Pp + p;
-  int imp = 0;
-  if (lane == 0) {
-    imp = (t == 0) || better(cur, *pb, pr.crit);
-    if (imp) *pb = cur;
-  }
-  imp = __shfl_sync(0xffffffffu, imp, 0);
-  if (!imp) return;
-  const int64_t o = ((int64_t)a * pr.Pp + p) * pr.d;
-  for (int j = lane; j < pr.d; j += 32) sw.pbest[o + j] = sw.pos[o + j];
-}
 
 // Algorithm 1, gbest step of node a after evaluation t, as seen by one warp:
 // the particle with the best score strictly better than gold (at t = 0 every
@@ -674,7 +539,8 @@ __global__ void __launch_bounds__(128)
   const int d = pr.d, d4 = (d + 3) >> 2, Pp = pr.Pp;
   const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
   EvalRes* gnew_buf = sw.gb + (int64_t)(t & 1) * A;
-  if (threadIdx.x < 32) {
+  // with a re-scored subset (sw.sel) k_merge took the gbest step already
+  if (!sw.sel && threadIdx.x < 32) {
     const EvalRes gold = gold_buf[a];
     EvalRes be;
     const int bi = gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t, &be);
@@ -695,7 +561,7 @@ __global__ void __launch_bounds__(128)
     }
   }
   __syncthreads();
-  const int best = s_best;
+  const int best = sw.sel ? -1 : s_best;
   const float* pbp = sw.pbest + (int64_t)a * Pp * d;
   float* gbp = sw.gbest + (int64_t)a * d;
   // a new best improved its pbest in this iteration: its pbest row is its
@@ -773,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int rank = (int)cl.block_rank();
   const int a = blockIdx.x / S;
   const int p = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   const NodeDesc nd = nodes[a];
   const int B = pr.B, K = pr.K;
   const bool mse = pr.crit == SLM_MSE;

@@ -25,6 +25,8 @@ enum Slot {
   W_X, W_LAB, W_Y, W_IDX, W_W, W_BINS, W_XL, W_LABL, W_YL,
   S_POS, S_VEL, S_PBEST, S_GBEST, S_CUR, S_PB, S_GB, S_GPART, S_GITER,
   S_TRACE, S_ZMM, S_Z, S_DONE, S_NODES, S_TILES, S_STATUS, S_ERR, S_OUT,
+  // SLM_PROJ_BF16_TOPK
+  W_XB, S_POSB, S_MTILES, S_SEL, S_INV, S_POSK, S_Z2, S_ZMM2, S_CUR2,
   N_SLOTS
 };
 
@@ -65,6 +67,8 @@ struct slm_forest {
   DevBuf tree_mem;
   // level-resident entry arrays, ping-pong
   DevBuf lX[2], lab[2], ly[2], lw[2], lidx[2], side;
+  DevBuf lXb;     // bfloat16 rows of the current level (SLM_PROJ_BF16_TOPK)
+  int align = 4;  // node segments start on multiples of this many entries
   int cur = 0;
   bool weighted = false;
   std::vector<LevelNode> level;  // nodes of the level to grow next
@@ -147,6 +151,16 @@ slm_status stage_in(slm_ctx* c, const T* src, size_t count, DevBuf& buf,
   return SLM_OK;
 }
 
+int round16(int v) { return (v + 15) / 16 * 16; }
+
+// The tensor-core pass stages all positions of a node in shared memory.
+slm_status check_bf16_size(slm_ctx* c, int d, int P) {
+  if ((int64_t)round16(P) * round16(d) * 2 > kMmaMaxBBytes)
+    return fail(c, SLM_EUNSUPPORTED,
+                "SLM_PROJ_BF16_TOPK needs round16(n_particles) * round16(d) * 2 <= 131072");
+  return SLM_OK;
+}
+
 slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
                         bool need_swarm) {
   if (!p) return fail(c, SLM_EINVAL, "params is NULL");
@@ -165,8 +179,13 @@ slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
     if (p->n_particles < 1 || p->n_particles > kMaxParticles)
       return fail(c, SLM_EINVAL, "n_particles must be in [1, 256]");
     if (p->n_iters < 0) return fail(c, SLM_EINVAL, "n_iters must be >= 0");
-    if (p->proj != SLM_PROJ_FP32)
-      return fail(c, SLM_EUNSUPPORTED, "only SLM_PROJ_FP32 is implemented");
+    if (p->proj != SLM_PROJ_FP32 && p->proj != SLM_PROJ_BF16_TOPK)
+      return fail(c, SLM_EINVAL, "proj must be SLM_PROJ_FP32 or SLM_PROJ_BF16_TOPK");
+    if (p->proj == SLM_PROJ_BF16_TOPK) {
+      if (p->topk < 1 || p->topk > p->n_particles)
+        return fail(c, SLM_EINVAL, "topk must be in [1, n_particles]");
+      if (slm_status s = check_bf16_size(c, d, p->n_particles)) return s;
+    }
     if (!std::isfinite(p->inertia) || !std::isfinite(p->c1) ||
         !std::isfinite(p->c2))
       return fail(c, SLM_EINVAL, "inertia / c1 / c2 must be finite");
@@ -235,12 +254,18 @@ Problem make_problem(const slm_params* p, const float* X, int d, const int32_t* 
   return pr;
 }
 
-int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
+int64_t round_up(int64_t v, int64_t al) { return (v + al - 1) / al * al; }
 
 // Entries the level arrays need: the root's (padded) entries plus the
-// padding of every node of a level (< 4 each), plus a 16-byte guard.
-int64_t level_capacity(int64_t e_root, int n_trees, int max_depth) {
-  return e_root + 4 * (int64_t)n_trees * ((int64_t)1 << max_depth) + 16;
+// padding of every node of a level (< align each), plus a 16-byte guard. A
+// level holds at most n_trees 2^max_depth nodes, and (unweighted) every node
+// below the root holds at least min_leaf entries.
+int64_t level_capacity(int64_t e_root, int n_trees, int max_depth, int align, int min_leaf,
+                       bool weighted) {
+  int64_t nodes = (int64_t)n_trees << max_depth;
+  const int64_t by_size = weighted ? e_root : n_trees + e_root / (min_leaf > 0 ? min_leaf : 1);
+  if (align > 4 && by_size < nodes) nodes = by_size;
+  return e_root + (int64_t)align * nodes + 16;
 }
 
 // Projection work tiles: every node's segment cut into kTS-row tiles.
@@ -313,8 +338,6 @@ slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T, bool want_tr
   return SLM_OK;
 }
 
-// One scoring pass of every (node, particle) of a batch; with a swarm
-// (co != null) the pass ends with the swarm update of iteration t.
 // Cluster split of the histogram kernel for a batch.
 int batch_split(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes) {
   int64_t max_len = 0;
@@ -322,13 +345,132 @@ int batch_split(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& node
   return hist_split(pr, (int)nodes.size(), max_len, c->n_sm, hist_max_cluster(pr));
 }
 
+// The reduced-precision pass of SLM_PROJ_BF16_TOPK: bfloat16 scores of all
+// particles on the tensor cores, then FP32 re-scores of the k best per node.
+struct Bf16Plan {
+  bool on = false;
+  int k = 0, kp = 0;     // re-scored particles per node; padded to kPG
+  int n_mtiles = 0;      // kMmaRows-row tiles of the batch
+  int grid = 0;          // k_project_mma grid
+  int S_k = 1;           // cluster split of the re-scoring histogram pass
+  double pairs_k = 0.0;
+  Problem pr_k{};        // the re-scoring problem: P = k
+  Swarm sw_k{};          // its view: compact positions, z, ranges, scores
+  uint16_t* posb = nullptr;
+  int32_t* sel = nullptr;
+  int32_t* inv = nullptr;
+};
+
+// Buffers of the reduced-precision pass for A nodes whose segments start on
+// multiples of kMmaRows; sw->sel / sw->k are set for a search.
+slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes,
+                      int k, bool search, Swarm* sw, Bf16Plan* plan) {
+  const int A = (int)nodes.size();
+  Bf16Plan b;
+  b.on = true;
+  b.k = k;
+  b.kp = (k + kPG - 1) / kPG * kPG;
+  std::vector<WorkTile> mt;
+  for (int a = 0; a < A; ++a) {
+    if (nodes[a].seg_start % kMmaRows)
+      return fail(c, SLM_ECUDA, "internal: node segment not aligned for the tensor-core pass");
+    for (int r = 0; r < nodes[a].seg_len; r += kMmaRows)
+      mt.push_back(WorkTile{a, nodes[a].seg_start + r, std::min(kMmaRows, nodes[a].seg_len - r), 0});
+    b.pairs_k += (double)nodes[a].seg_len * k;
+  }
+  b.n_mtiles = (int)mt.size();
+  CK(ensure(c->ws[S_MTILES], sizeof(WorkTile) * mt.size()));
+  if (!mt.empty())
+    CK(cudaMemcpyAsync(c->ws[S_MTILES].p, mt.data(), sizeof(WorkTile) * mt.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  CK(ensure(c->ws[S_POSB], sizeof(uint16_t) * (size_t)A * pr.Pp * pr.dp));
+  b.posb = ws_ptr<uint16_t>(c, S_POSB);
+  CK(prepare_mma_kernels(pr));
+  const int cap = mma_grid_cap(pr, c->n_sm);
+  if (cap < 1) return fail(c, SLM_EUNSUPPORTED, "the tensor-core pass cannot be scheduled");
+  b.grid = std::min(cap, std::max(1, b.n_mtiles));
+  if (k > 0) {
+    CK(ensure(c->ws[S_SEL], sizeof(int32_t) * (size_t)A * k));
+    CK(ensure(c->ws[S_INV], sizeof(int32_t) * (size_t)A * pr.Pp));
+    CK(ensure(c->ws[S_POSK], sizeof(float) * (size_t)A * b.kp * pr.d));
+    CK(ensure(c->ws[S_Z2], sizeof(float) * (size_t)k * (size_t)(pr.Ez > 0 ? pr.Ez : 4)));
+    CK(ensure(c->ws[S_ZMM2], sizeof(int32_t) * 2 * (size_t)A * b.kp));
+    CK(ensure(c->ws[S_CUR2], sizeof(EvalRes) * (size_t)A * b.kp));
+    std::vector<int32_t> zinit(2 * (size_t)A * b.kp);
+    for (size_t i = 0; i < zinit.size(); i += 2) {
+      zinit[i] = INT32_MAX;
+      zinit[i + 1] = INT32_MIN;
+    }
+    CK(cudaMemcpyAsync(c->ws[S_ZMM2].p, zinit.data(), sizeof(int32_t) * zinit.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    b.sel = ws_ptr<int32_t>(c, S_SEL);
+    b.inv = ws_ptr<int32_t>(c, S_INV);
+    b.pr_k = pr;
+    b.pr_k.P = k;
+    b.pr_k.Pp = b.kp;
+    b.pr_k.G = b.kp / kPG;
+    b.sw_k = *sw;
+    b.sw_k.pos = ws_ptr<float>(c, S_POSK);
+    b.sw_k.z = ws_ptr<float>(c, S_Z2);
+    b.sw_k.zmm = ws_ptr<int32_t>(c, S_ZMM2);
+    b.sw_k.cur = ws_ptr<EvalRes>(c, S_CUR2);
+    b.sw_k.sel = nullptr;
+    b.S_k = batch_split(c, b.pr_k, nodes);
+    if (search) {
+      sw->sel = b.sel;
+      sw->k = k;
+    }
+  }
+  *plan = b;
+  return SLM_OK;
+}
+
+// One scoring pass of every (node, particle) of a batch; with a swarm
+// (co != null) the pass ends with the swarm update of iteration t.
 slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
                        const std::vector<NodeDesc>& nodes, int n_tiles, double pairs,
-                       int32_t* bins_out, int t, const SwarmCoef* co, int S) {
+                       int32_t* bins_out, int t, const SwarmCoef* co, int S,
+                       const Bf16Plan* bp = nullptr) {
   const int A = (int)nodes.size();
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
   const int cap = 2 * c->n_sm;
+  if (bp && bp->on) {
+    // bfloat16 scores of every particle on the tensor cores
+    const Bf16Plan& b = *bp;
+    CK(launch(c, SLM_K_TOPK, 0.0, [&] {
+      return launch_to_mma_layout(sw.pos, (int64_t)A * pr.Pp, pr.d, pr.dp, pr.Pp, A, b.posb,
+                                  c->stream);
+    }));
+    if (b.n_mtiles)
+      CK(launch(c, SLM_K_PROJECT_MMA, pairs, [&] {
+        return launch_project_mma(pr, sw, ws_ptr<WorkTile>(c, S_MTILES), b.n_mtiles, b.posb,
+                                  b.grid, c->stream);
+      }));
+    CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
+      return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, 0, c->stream);
+    }));
+    if (b.k > 0) {
+      // FP32 re-scores of the k best of each node replace theirs
+      CK(launch(c, SLM_K_TOPK, 0.0, [&] {
+        return launch_topk(pr, sw, A, b.k, b.kp, b.sel, b.inv, b.sw_k.pos, c->stream);
+      }));
+      if (n_tiles)
+        CK(launch(c, SLM_K_PROJECT, b.pairs_k, [&] {
+          return launch_project(b.pr_k, b.sw_k, dt, n_tiles, cap, c->stream);
+        }));
+      CK(launch(c, SLM_K_HIST_SCAN, b.pairs_k, [&] {
+        return launch_hist_scan(b.pr_k, b.sw_k, dn, A, b.S_k, nullptr, t, 0, c->stream);
+      }));
+      CK(launch(c, SLM_K_TOPK, 0.0, [&] {
+        return launch_merge(pr, sw, A, b.sw_k.cur, b.kp, b.inv, t, co ? 1 : 0, c->stream);
+      }));
+    }
+    if (co)
+      CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
+                [&] { return launch_move(pr, sw, dn, A, t, *co, c->stream); }));
+    return SLM_OK;
+  }
   if (n_tiles)
     CK(launch(c, SLM_K_PROJECT, pairs,
               [&] { return launch_project(pr, sw, dt, n_tiles, cap, c->stream); }));
@@ -354,11 +496,15 @@ slm_status run_search(slm_ctx* c, const slm_params* p, const Problem& pr,
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   double pairs = 0.0;
   for (const NodeDesc& nd : nodes) pairs += (double)nd.seg_len * pr.P;
+  Bf16Plan bp;
+  if (p->proj == SLM_PROJ_BF16_TOPK &&
+      (s = setup_bf16(c, pr, nodes, std::min(p->topk, p->n_particles), true, &sw, &bp)))
+    return s;
   CK(launch(c, SLM_K_SWARM_INIT, 0.0,
             [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
   const int S = batch_split(c, pr, nodes);
   for (int t = 0; t <= p->n_iters; ++t)
-    if ((s = score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S)))
+    if ((s = score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp)))
       return s;
   sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
   *sw_out = sw;
@@ -370,6 +516,7 @@ slm_status check_kernel_errors(slm_ctx* c) {
   int32_t e = 0;
   CK(cudaMemcpyAsync(&e, c->ws[S_ERR].p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (e == 4) return fail(c, SLM_ETIMEOUT, "a tensor-core stage did not complete");
   if (e) return fail(c, SLM_ETIMEOUT, "a bulk copy of the histogram kernel did not complete");
   return SLM_OK;
 }
@@ -554,6 +701,18 @@ slm_status prepare_node(slm_ctx* c, const slm_params* p, const float* X, int64_t
     return launch_gather(dX, dlab, dy, didx, n_idx, d, Xl, ll, yl, c->stream);
   }));
   *pr = make_problem(p, Xl, d, ll, yl, dw, n_idx, P);
+  if (p->proj == SLM_PROJ_BF16_TOPK) {
+    // the node's rows once more, as bfloat16 tensor-core operands
+    const int dp = round16(d);
+    const int64_t nb = std::max<int64_t>(1, (n_idx + kMmaRows - 1) / kMmaRows);
+    CK(ensure(c->ws[W_XB], sizeof(uint16_t) * (size_t)nb * kMmaRows * dp));
+    uint16_t* xb = ws_ptr<uint16_t>(c, W_XB);
+    CK(launch(c, SLM_K_GATHER, 0.0, [&] {
+      return launch_to_mma_layout(Xl, n_idx, d, dp, kMmaRows, nb, xb, c->stream);
+    }));
+    pr->Xb = xb;
+    pr->dp = dp;
+  }
   return SLM_OK;
 }
 
@@ -586,6 +745,12 @@ slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
     return s;
   if (!positions || n_pos < 1 || n_pos > kMaxParticles || !out)
     return fail(c, SLM_EINVAL, "bad positions / n_pos / out");
+  if (p->proj != SLM_PROJ_FP32 && p->proj != SLM_PROJ_BF16_TOPK)
+    return fail(c, SLM_EINVAL, "proj must be SLM_PROJ_FP32 or SLM_PROJ_BF16_TOPK");
+  if (p->proj == SLM_PROJ_BF16_TOPK) {
+    if (p->topk < 0 || p->topk > n_pos) return fail(c, SLM_EINVAL, "topk must be in [0, n_pos]");
+    if (slm_status s = check_bf16_size(c, d, n_pos)) return s;
+  }
   CK(cudaSetDevice(c->device));
   Problem pr;
   if (slm_status s = prepare_node(c, p, X, n, d, labels, y, sample_idx, weights, n_idx,
@@ -600,6 +765,9 @@ slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
   CK(cudaMemcpyAsync(c->ws[S_POS].p, positions, sizeof(float) * n_pos * d,
                      cudaMemcpyDefault, c->stream));
   sw.pos = ws_ptr<float>(c, S_POS);
+  Bf16Plan bp;
+  if (p->proj == SLM_PROJ_BF16_TOPK)
+    if (slm_status s = setup_bf16(c, pr, nodes, p->topk, false, &sw, &bp)) return s;
   std::vector<int32_t> zinit(2 * pr.Pp);
   for (int i = 0; i < pr.Pp; ++i) {
     zinit[2 * i] = INT32_MAX;
@@ -615,7 +783,7 @@ slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
   }
   if (slm_status s = score_batch(c, pr, sw, nodes, (int)tiles.size(),
                                  (double)n_idx * n_pos, dbins, 0, nullptr,
-                                 batch_split(c, pr, nodes)))
+                                 batch_split(c, pr, nodes), &bp))
     return s;
   static_assert(sizeof(slm_eval) == sizeof(EvalRes), "layout");
   if (slm_status s = check_kernel_errors(c)) return s;
@@ -709,7 +877,8 @@ void slm_forest_free(slm_forest* f) {
   DevBuf* bufs[] = {&f->own_X,     &f->tree_mem, &f->side,      &f->lvl_nodes, &f->lvl_split,
                     &f->lvl_cls,   &f->lvl_par,  &f->smap,      &f->out3,      &f->dst,
                     &f->ltiles,    &f->ltile0,   &f->acc_w,     &f->acc_y,     &f->tile_s,
-                    &f->stile0,    &f->tile_left, &f->tile_base, &f->p_lk,     &f->p_wl};
+                    &f->stile0,    &f->tile_left, &f->tile_base, &f->p_lk,     &f->p_wl,
+                    &f->lXb};
   for (DevBuf* b : bufs) release(*b);
   for (int i = 0; i < 2; ++i) {
     release(f->lX[i]);
@@ -750,6 +919,8 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   f->H = (1 << (p->max_depth + 1)) - 1;
   f->n_trees = p->n_trees;
   f->K = p->criterion == SLM_MSE ? 1 : p->n_classes;
+  const bool bf16 = p->proj == SLM_PROJ_BF16_TOPK;
+  f->align = bf16 ? kMmaRows : 4;
   slm_status s;
   auto bail = [&](slm_status st) {
     slm_forest_free(f);
@@ -808,8 +979,8 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
       return bail(cuda_fail(c, e, "bootstrap compaction"));
     }
     cleanup();
-    for (int t = 0; t < f->n_trees; ++t) E += round4(cnt[t]);
-    ecap = level_capacity(E, f->n_trees, p->max_depth);
+    for (int t = 0; t < f->n_trees; ++t) E += round_up(cnt[t], f->align);
+    ecap = level_capacity(E, f->n_trees, p->max_depth, f->align, p->min_leaf, true);
     if ((e = ensure(f->lidx[0], 4 * (size_t)ecap)) || (e = ensure(f->lw[0], 4 * (size_t)ecap)) ||
         (e = cudaMemsetAsync(f->lidx[0].p, 0, 4 * (size_t)ecap, c->stream)) ||
         (e = cudaMemsetAsync(f->lw[0].p, 0, 4 * (size_t)ecap, c->stream)))
@@ -824,12 +995,12 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
                                cudaMemcpyDeviceToDevice, c->stream)))
         return bail(cuda_fail(c, e, "bag packing"));
       f->level.push_back(LevelNode{(int32_t)pos, cnt[t], t * f->H, 0});
-      pos += round4(cnt[t]);
+      pos += round_up(cnt[t], f->align);
     }
   } else {
-    const int64_t n4 = round4(n);
+    const int64_t n4 = round_up(n, f->align);
     E = n4 * f->n_trees;
-    ecap = level_capacity(E, f->n_trees, p->max_depth);
+    ecap = level_capacity(E, f->n_trees, p->max_depth, f->align, p->min_leaf, false);
     if ((e = ensure(f->lidx[0], 4 * (size_t)ecap)) ||
         (e = cudaMemsetAsync(f->lidx[0].p, 0, 4 * (size_t)ecap, c->stream)))
       return bail(cuda_fail(c, e, "level buffers"));
@@ -857,6 +1028,9 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
       return bail(cuda_fail(c, e, "level buffers"));
   }
   if ((e = ensure(f->side, (size_t)ecap))) return bail(cuda_fail(c, e, "level buffers"));
+  if (bf16 && (e = ensure(f->lXb, sizeof(uint16_t) * (size_t)round_up(ecap, kMmaRows) *
+                                      round16(d))))
+    return bail(cuda_fail(c, e, "level buffers"));
   c->launches += 1;
   if ((e = launch_gather(dX, dlab, dy, static_cast<int32_t*>(f->lidx[0].p), ecap, d,
                          static_cast<float*>(f->lX[0].p),
@@ -966,6 +1140,17 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     f->level.clear();
     return SLM_OK;
   }
+  if (p->proj == SLM_PROJ_BF16_TOPK) {
+    // the level's rows as bfloat16 tensor-core operands
+    const int dp = round16(f->d);
+    const int64_t nb = (E + kMmaRows - 1) / kMmaRows;
+    uint16_t* xb = static_cast<uint16_t*>(f->lXb.p);
+    CK(launch(c, SLM_K_GATHER, 0.0, [&] {
+      return launch_to_mma_layout(pr.X, E, f->d, dp, kMmaRows, nb, xb, c->stream);
+    }));
+    pr.Xb = xb;
+    pr.dp = dp;
+  }
   Swarm sw;
   if (slm_status s = run_search(c, p, pr, snodes, false, &sw)) return s;
   if (slm_status s = check_kernel_errors(c)) return s;
@@ -1022,12 +1207,13 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     const LevelNode& ln = f->level[smap[a]];
     const int tree = ln.slot / f->H, h = ln.slot % f->H;
     const int32_t nl = o3[3 * a + 1], nr = o3[3 * a + 2];
-    const int32_t pr_ = (int32_t)round4(pos + nl);  // children start on 16-byte boundaries
+    // children start on 16-byte boundaries (whole tensor-core tiles in BF16 mode)
+    const int32_t pr_ = (int32_t)round_up(pos + nl, f->align);
     dst[2 * a] = pos;
     dst[2 * a + 1] = pr_;
     next.push_back(LevelNode{pos, nl, tree * f->H + 2 * h + 1, ln.depth + 1});
     next.push_back(LevelNode{pr_, nr, tree * f->H + 2 * h + 2, ln.depth + 1});
-    pos = (int32_t)round4(pr_ + nr);
+    pos = (int32_t)round_up(pr_ + nr, f->align);
     ++n_split;
   }
   if (n_split) {

@@ -21,6 +21,9 @@ constexpr int kMaxClasses = 32;
 constexpr int kMaxHistBytesPerParticle = 10240;  // B*K*4 (classification)
 constexpr int kMaxParticles = 256;
 constexpr int kMaxD = 1024;
+// bfloat16 projection on the tensor cores (SLM_PROJ_BF16_TOPK)
+constexpr int kMmaRows = 128;                // rows per MMA tile = TMEM lanes
+constexpr int kMmaMaxBBytes = 128 * 1024;    // staged positions: Pp * dp * 2
 
 // Philox stream purposes (high byte of counter word 3).
 enum Purpose : uint32_t {
@@ -75,6 +78,10 @@ struct Problem {
   int32_t P;              // particles
   int32_t Pp;             // padded to a multiple of kPG
   int32_t G;              // Pp / kPG
+  // SLM_PROJ_BF16_TOPK: the rows in bfloat16, in the tensor-core operand
+  // layout of launch_to_mma_layout (kMmaRows-row blocks), d padded to dp
+  const uint16_t* Xb;
+  int32_t dp;             // d rounded up to a multiple of 16
 };
 
 // Device swarm state of A nodes.
@@ -92,8 +99,13 @@ struct Swarm {
   int32_t* zmm;   // [A, Pp, 2] ordered-int range of each projection
   float* z;       // [P, E] projections of the current iteration
   int32_t* done;  // [A] particle groups of the node scored in this iteration
-  int32_t* err;   // kernel error word (3: a bulk copy did not complete)
+  int32_t* err;   // kernel error word (3: a bulk copy did not complete;
+                  // 4: a tensor-core stage did not complete)
   int32_t T;
+  // SLM_PROJ_BF16_TOPK: sel[A, k] re-scored particles of each node in
+  // increasing order; non-null when the gbest step runs in k_merge
+  const int32_t* sel;
+  int32_t k;
 };
 
 struct SwarmCoef {
@@ -125,6 +137,32 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
 // of A nodes to iteration t+1.
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                         int A, int t, SwarmCoef co, cudaStream_t st);
+// ---- bfloat16 projection on the tensor cores (mma_kernels.cu) -------------
+// Converts n_blocks blocks of R rows of src[*, d] (float, row stride d; rows
+// at or past n_src_rows read as 0) to bfloat16 in the K-major, unswizzled
+// core-matrix layout the MMA reads: block b, feature k, row r lives at
+// element b*R*dp + (k/16)*R*16 + (r/8)*128 + ((k/8)&1)*64 + (r&7)*8 + (k&7).
+cudaError_t launch_to_mma_layout(const float* src, int64_t n_src_rows, int d, int dp, int R,
+                                 int64_t n_blocks, uint16_t* out, cudaStream_t st);
+// Largest resident grid of k_project_mma for a problem (0 if it cannot run).
+int mma_grid_cap(const Problem& pr, int n_sm);
+cudaError_t prepare_mma_kernels(const Problem& pr);
+// z and ranges of every (kMmaRows-row tile, all particles) with the BF16
+// tensor-core MMA; posb[A, Pp*dp] in the MMA layout (R = Pp).
+cudaError_t launch_project_mma(const Problem& pr, const Swarm& sw, const WorkTile* tiles,
+                               int n_tiles, const uint16_t* posb, int grid,
+                               cudaStream_t st);
+// Per node: the k particles with the best scores in sw.cur (ties to the lower
+// index), in increasing order, into sel[A, k]; inv[A, Pp] = rank in sel or -1;
+// their positions into posk[A, kp, d] (rows k..kp-1 zero).
+cudaError_t launch_topk(const Problem& pr, const Swarm& sw, int A, int k, int kp,
+                        int32_t* sel, int32_t* inv, float* posk, cudaStream_t st);
+// Writes the re-scored particles' scores cur2[A, kp] over sw.cur; with
+// do_update, the pbest step of every particle and the gbest step of
+// iteration t among the re-scored particles (Algorithm 1).
+cudaError_t launch_merge(const Problem& pr, const Swarm& sw, int A, const EvalRes* cur2,
+                         int kp, const int32_t* inv, int t, int do_update, cudaStream_t st);
+
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
                                   int P, int d, uint32_t purpose, float* u,
                                   cudaStream_t st);
