@@ -1,14 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: SLM tree training with PSO split search on GB300.
 
-A step is one full tree grown through libslm's C ABI (slm_train_tree): every
-level's nodes searched in one batch by the particle swarm, then partitioned.
-The workload is the classification tree of 50,000 samples x 64 features, 10
-Gaussian-mixture classes, depth <= 8, min leaf 20, P=64 particles, T=100
-iterations, 128 bins, Gini. The metric is particle-sample evaluations per
-second: sum over searched nodes of n_node * P * (T+1), divided by the time.
+A step is one full tree (or bagged forest) grown through libslm's C ABI
+(slm_train_tree): every level's nodes searched in one batch by the particle
+swarm, then partitioned. The default workload is the classification tree of
+50,000 samples x 64 features, 10 Gaussian-mixture classes, depth <= 8, min
+leaf 20, P=64 particles, T=100 iterations, 128 bins, Gini, FP32 projection.
+The metric is particle-sample evaluations per second: sum over searched
+nodes of n_node * P * (T+1), divided by the time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--proj fp32|bf16] [--topk K] [--compare-fp32]
+
+--workload selects another named setting of paper_2208_07023_gb300.workloads
+(regtree_n200k_d128: the regression tree, bfloat16 projection with top-8 FP32
+re-scoring by default; forest64_n100k_d32_k5: 64 bagged trees; node_n2000_d16:
+one node). --compare-fp32 also times the plain FP32 form of the same workload
+and reports both forms' time and training loss.
 
 With N > 1 (torchrun) every rank grows its own tree on its own seed (weak
 scaling, no data exchange); rank 0 prints one JSON line. --impl reference
@@ -34,49 +42,58 @@ from paper_2208_07023_gb300 import workloads as W  # noqa: E402
 
 METRIC = "SLM tree train time & particle-sample evals/s vs plain FP32 PSO at equal loss"
 UNIT = "particle-sample evals/s"
-WORKLOAD = "tree_n50k_d64_k10"
+DEFAULT_WORKLOAD = "tree_n50k_d64_k10"
 # FP32 fused multiply-add peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE_S = 10.0  # CPU work of one oracle baseline sample
 
 
-def _measured_hbm_gbs():
+def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j["bf16_tflops"]), "measured"
     except Exception:
-        return 6800.0  # fallback figure for a GB300 copy
+        return 6800.0, 1900.0, "fallback"
 
 
-HBM_PEAK_GBS = _measured_hbm_gbs()
+HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 
-# DRAM bytes per particle-sample pair from ncu captures of the bench workload
-# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/), valid only for
-# the kernel source they were taken from (sha256 of csrc/eval_kernels.cu).
+# DRAM bytes per particle-sample pair from ncu captures of the default
+# workload (dram__bytes_read.sum + dram__bytes_write.sum, profiles/), valid
+# only for the kernel source they were taken from (sha256 of the .cu file).
 TRAFFIC = {"project": 12849920 / 3.2e6, "hist_scan": 13091328 / 3.2e6}
+TRAFFIC_SOURCE = {"project": "eval_kernels.cu", "hist_scan": "eval_kernels.cu"}
 TRAFFIC_SOURCE_SHA = "ce91b6f59265ae321156e8251a0a80b435982ce0e13bb604e2fb533d1297ceb0"
 
 
-def _kernel_source_sha():
+def _kernel_source_sha(name):
     import hashlib
-    p = os.path.join(ROOT, "paper_2208_07023_gb300", "csrc", "eval_kernels.cu")
+    p = os.path.join(ROOT, "paper_2208_07023_gb300", "csrc", name)
     with open(p, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def traffic_per_launch(name, ks):
+def traffic_per_launch(name, ks, workload):
     """Captured DRAM bytes per pair x the average pairs of a launch, or None
-    once the kernel source differs from the captured one."""
-    if name not in TRAFFIC or TRAFFIC_SOURCE_SHA != _kernel_source_sha():
+    for another workload or once the kernel source differs from the captured
+    one."""
+    if workload != DEFAULT_WORKLOAD or name not in TRAFFIC:
+        return None
+    if TRAFFIC_SOURCE_SHA != _kernel_source_sha(TRAFFIC_SOURCE[name]):
         return None
     return TRAFFIC[name] * ks["pairs"] / max(1, ks["launches"])
 
 
-def config_dict(cfg, extra=None):
-    d = {"workload": WORKLOAD, "n": 50_000, "d": 64, "classes": 10,
+def config_dict(name, cfg, wl, proj, topk, extra=None):
+    d = {"workload": name, "n": wl.n, "d": wl.d, "classes": wl.n_classes,
+         "trees": cfg["n_trees"], "bootstrap": cfg["n_trees"] > 1,
          "max_depth": cfg["max_depth"], "min_leaf": cfg["min_leaf"],
          "particles": cfg["n_particles"], "iters": cfg["n_iters"], "bins": cfg["n_bins"],
-         "criterion": cfg["criterion"], "projection": "fp32 ffma",
+         "criterion": cfg["criterion"],
+         "projection": ("bf16 tcgen05 + top-%d fp32 ffma re-scoring" % topk
+                        if proj == "bf16" else "fp32 ffma"),
          "l2": "flushed between steps (256 MiB write outside the timed events)"}
     if extra:
         d.update(extra)
@@ -142,49 +159,169 @@ def gpu_uuid(dev: int) -> str:
         return vis.split(",")[dev] if vis else str(dev)
 
 
-def oracle_root_sample(cfg, wl, iters):
-    """Times the CPU oracle's swarm search of the root node (all n samples)
-    with `iters` iterations; returns (evals/s, seconds, threads)."""
+# ---------------------------------------------------------------- oracle ----
+
+def oracle_params(cfg, wl, proj, topk, iters):
     import oracle as O
-    p = O.make_params(cfg["criterion"], wl.n_classes, cfg["n_particles"], iters,
-                      cfg["n_bins"], min_leaf=cfg["min_leaf"], seed=1,
-                      precision=O.F32_MIRROR)
+    prec = O.BF16_TOPK if proj == "bf16" else O.F32_MIRROR
+    return O.make_params(cfg["criterion"], wl.n_classes, cfg["n_particles"], iters,
+                         cfg["n_bins"], min_leaf=cfg["min_leaf"], seed=1, precision=prec,
+                         topk=topk if proj == "bf16" else 0)
+
+
+def oracle_root_sample(cfg, wl, proj, topk, iters):
+    """Times the CPU oracle's swarm search of the root node (all n samples)
+    with `iters` iterations; returns (evals/s, seconds, evaluations)."""
+    import oracle as O
+    p = oracle_params(cfg, wl, proj, topk, iters)
     t0 = time.perf_counter()
-    O.node_split(p, wl.X, wl.labels, node_uid=0)
+    O.node_split(p, wl.X, wl.labels, wl.y, node_uid=0)
     dt = time.perf_counter() - t0
     evals = wl.n * cfg["n_particles"] * (iters + 1)
-    return evals / dt, dt, os.cpu_count()
+    return evals / dt, dt, evals
+
+
+def oracle_sample_iters(cfg, wl, proj, topk, budget_s):
+    """Iterations of a root-node search that take about budget_s seconds on
+    the host: one initial evaluation is timed first."""
+    _, dt1, _ = oracle_root_sample(cfg, wl, proj, topk, 0)
+    return int(max(0, min(cfg["n_iters"], budget_s / max(dt1, 1e-6) - 1)))
+
+
+def cpu_baseline(cfg, wl, proj, topk):
+    iters = oracle_sample_iters(cfg, wl, proj, topk, CPU_SAMPLE_S)
+    v, dt, ev = oracle_root_sample(cfg, wl, proj, topk, iters)
+    mode = "bf16 top-%d" % topk if proj == "bf16" else "fp32-mirror"
+    return {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"root-node swarm search of the workload ({wl.n} samples x "
+                       f"{cfg['n_particles']} particles x {iters + 1} evaluations = {ev} "
+                       f"evaluations, {dt:.1f} s; {mode} oracle, OpenMP over particles)")}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cfg = W.SETTINGS[WORKLOAD]
+    cfg = W.SETTINGS[args.workload]
     wl = cfg["builder"](1)
-    iters = 10
+    proj, topk = args.proj, args.topk
+    iters = 10 if args.workload == DEFAULT_WORKLOAD else \
+        oracle_sample_iters(cfg, wl, proj, topk, 20.0)
     for _ in range(args.warmup):
-        oracle_root_sample(cfg, wl, iters)
-    vals, secs = [], []
+        oracle_root_sample(cfg, wl, proj, topk, iters)
+    secs = []
     for _ in range(args.steps):
-        v, dt, cores = oracle_root_sample(cfg, wl, iters)
-        vals.append(v)
+        _, dt, _ = oracle_root_sample(cfg, wl, proj, topk, iters)
         secs.append(dt)
     value = wl.n * cfg["n_particles"] * (iters + 1) * len(secs) / sum(secs)
     sample = (f"root-node swarm search of the same workload: {wl.n} samples x "
               f"{cfg['n_particles']} particles x {iters + 1} evaluations per step "
-              f"(fp32-mirror oracle, OpenMP over particles)")
+              f"({'bf16 top-k' if proj == 'bf16' else 'fp32-mirror'} oracle, OpenMP over "
+              "particles)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(cfg, {"sample": "root node, 11 evaluations"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32" if proj == "bf16" else "f32", "data": "synthetic",
+            "config": config_dict(args.workload, cfg, wl, proj, topk,
+                                  {"sample": f"root node, {iters + 1} evaluations"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------- GPU ----
+
+def tree_loss(ctx, f, wl, X):
+    """Training loss of tree 0 under its criterion (weighted leaf impurity:
+    MSE for regression, Gini for classification; bootstrap weights are not
+    applied) and the ensemble's training MSE / error."""
+    cls, val, leaf = ctx.predict(f, X, want_leaf=True)
+    lf = leaf[:, 0]
+    if wl.y is not None:
+        g = f.export(0)
+        pred = g["leaf_value"][lf]
+        return {"tree0_mse": float(np.mean((pred - wl.y) ** 2)),
+                "ensemble_mse": float(np.mean((val - wl.y) ** 2))}
+    K = wl.n_classes
+    gini = 0.0
+    for h in np.unique(lf):
+        c = np.bincount(wl.labels[lf == h], minlength=K).astype(np.float64)
+        gini += c.sum() - (c ** 2).sum() / c.sum()
+    return {"tree0_gini": gini / wl.n, "ensemble_error": float(np.mean(cls != wl.labels))}
+
+
+def make_params(S, cfg, wl, proj, topk):
+    return S.make_params(cfg["criterion"], wl.n_classes, n_particles=cfg["n_particles"],
+                         n_iters=cfg["n_iters"], n_bins=cfg["n_bins"],
+                         min_leaf=cfg["min_leaf"], max_depth=cfg["max_depth"], seed=1,
+                         n_trees=cfg["n_trees"], bootstrap=cfg["n_trees"] > 1,
+                         proj=S.SLM_PROJ_BF16_TOPK if proj == "bf16" else S.SLM_PROJ_FP32,
+                         topk=topk)
+
+
+def time_steps(ctx, p, X, L, Y, steps, flush, stream):
+    """K timed steps: device time of each from events on the stream."""
+    import torch
+    times, evals = [], 0
+    launches0 = ctx.launch_count()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = ctx.train_tree(p, X, labels=L, y=Y)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        evals += f.info()["evaluations"]
+        f.free()
+    return times, evals, ctx.launch_count() - launches0
+
+
+def rooflines(kst, wl, cfg, proj, topk, workload):
+    """Per-kernel roofline from the profiled pass."""
+    P, d = cfg["n_particles"], wl.d
+    dp = (d + 15) // 16 * 16
+    roofs = {}
+    kp, kh, km = kst["project"], kst["hist_scan"], kst["project_mma"]
+    if kp["ms"] > 0:
+        # FP32 FFMA: 2 d flop per particle-sample pair
+        ach = 2.0 * d * kp["pairs"] / (kp["ms"] / 1e3) / 1e12
+        roofs["project"] = {"kernel": "project", "bound": "alu", "achieved": ach,
+                            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP32_PEAK_TFLOPS,
+                            "traffic": traffic_per_launch("project", kp, workload),
+                            "avg_launch_ms": kp["ms"] / max(1, kp["launches"]),
+                            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    if kh["ms"] > 0:
+        # z (4 B per pair) + labels / targets (+ multiplicities) per entry and
+        # pass; the bf16 form scans P and then k particles per entry
+        per_entry = P if proj != "bf16" else (P + topk) / 2.0
+        weighted = cfg["n_trees"] > 1
+        algo = kh["pairs"] * (4.0 + (8.0 if weighted else 4.0) / per_entry)
+        ach = algo / (kh["ms"] / 1e3) / 1e9
+        roofs["hist_scan"] = {"kernel": "hist_scan", "bound": "hbm", "achieved": ach,
+                              "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
+                              "traffic": traffic_per_launch("hist_scan", kh, workload),
+                              "avg_launch_ms": kh["ms"] / max(1, kh["launches"]),
+                              "peak_source": f"{PEAK_SOURCE} (MEASURED_PEAKS.json hbm_gbs)"}
+    if km["ms"] > 0:
+        # bf16 rows read once per launch: dp * 2 bytes per entry = pairs / P
+        algo = km["pairs"] / P * dp * 2.0
+        ach = algo / (km["ms"] / 1e3) / 1e9
+        tfl = 2.0 * d * km["pairs"] / (km["ms"] / 1e3) / 1e12
+        roofs["project_mma"] = {"kernel": "project_mma", "bound": "hbm", "achieved": ach,
+                                "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                "frac": ach / HBM_PEAK_GBS, "traffic": None,
+                                "avg_launch_ms": km["ms"] / max(1, km["launches"]),
+                                "tensor": {"achieved_tflops": tfl, "peak": BF16_PEAK_TFLOPS,
+                                           "frac": tfl / BF16_PEAK_TFLOPS},
+                                "peak_source": f"{PEAK_SOURCE} (MEASURED_PEAKS.json)"}
+    return roofs
 
 
 def run_ours(args):
@@ -205,56 +342,36 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    cfg = W.SETTINGS[WORKLOAD]
+    name, proj, topk = args.workload, args.proj, args.topk
+    cfg = W.SETTINGS[name]
     wl = cfg["builder"](1 + rank)  # each rank: its own tree
     X = torch.from_numpy(wl.X).cuda()
-    L = torch.from_numpy(wl.labels).cuda()
+    L = torch.from_numpy(wl.labels).cuda() if wl.labels is not None else None
+    Y = torch.from_numpy(wl.y).cuda() if wl.y is not None else None
     stream = torch.cuda.current_stream()
     ctx = S.Context(local, stream.cuda_stream)
-    p = S.make_params(cfg["criterion"], wl.n_classes, n_particles=cfg["n_particles"],
-                      n_iters=cfg["n_iters"], n_bins=cfg["n_bins"],
-                      min_leaf=cfg["min_leaf"], max_depth=cfg["max_depth"], seed=1)
+    p = make_params(S, cfg, wl, proj, topk)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step():
-        f = ctx.train_tree(p, X, labels=L)
-        ev = f.info()["evaluations"]
-        return f, ev
-
     for _ in range(args.warmup):
-        f, _ = step()
-        f.free()
+        ctx.train_tree(p, X, labels=L, y=Y).free()
 
     # timed region: K trees, device time per tree from events on the stream
-    launches0 = ctx.launch_count()
-    times, evals = [], 0
     clocks = ClockSampler(gpu_uuid(local))
     barrier()
     wall0 = time.perf_counter()
     with clocks:
-        for k in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            f, ev = step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            evals += ev
-            f.free()
+        times, evals, launches = time_steps(ctx, p, X, L, Y, args.steps, flush, stream)
         barrier()
     wall = time.perf_counter() - wall0
-    launches = ctx.launch_count() - launches0
 
     # per-kernel timing: the same K trees again, every launch bracketed by
     # CUDA events on the context's stream (kept out of the timed region above,
     # whose launches it would slow)
     ctx.profile(True)
-    for k in range(args.steps):
+    for _ in range(args.steps):
         flush.zero_()
-        f, _ = step()
-        f.free()
+        ctx.train_tree(p, X, labels=L, y=Y).free()
     kst = ctx.kernel_stats()
     ctx.profile(False)
 
@@ -270,71 +387,67 @@ def run_ours(args):
         tot_ms_max, evals_all = tot_ms, float(evals)
     value = evals_all / (tot_ms_max / 1e3)
 
+    # training loss of the trees this form grows
+    f = ctx.train_tree(p, X, labels=L, y=Y)
+    loss = tree_loss(ctx, f, wl, X)
+    f.free()
+
+    extra = {"tree_train_ms": tot_ms_max / args.steps, "evals_per_step": evals // args.steps,
+             "wall_s": wall, "train_loss": loss}
+    if args.compare_fp32 and proj == "bf16":
+        # the plain FP32 form of the same workload, same harness
+        p32 = make_params(S, cfg, wl, "fp32", topk)
+        for _ in range(max(1, args.warmup)):
+            ctx.train_tree(p32, X, labels=L, y=Y).free()
+        t32, e32, _ = time_steps(ctx, p32, X, L, Y, args.steps, flush, stream)
+        f = ctx.train_tree(p32, X, labels=L, y=Y)
+        loss32 = tree_loss(ctx, f, wl, X)
+        f.free()
+        extra["fp32_form"] = {"tree_train_ms": sum(t32) / len(t32),
+                              "value": e32 / (sum(t32) / 1e3), "train_loss": loss32,
+                              "speedup_of_bf16_form": (sum(t32) / len(t32)) /
+                              (tot_ms / args.steps)}
+
     # end to end: host (pinned) inputs in, tree arrays out, through the C ABI
     Xh = torch.from_numpy(wl.X).pin_memory()
-    Lh = torch.from_numpy(wl.labels).pin_memory()
+    Lh = torch.from_numpy(wl.labels).pin_memory() if wl.labels is not None else None
+    Yh = torch.from_numpy(wl.y).pin_memory() if wl.y is not None else None
     e2e_t, e2e_ev, d2h = [], 0, 0
-    for k in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f = ctx.train_tree(p, Xh, labels=Lh)
-        g = f.export(0)
+        f = ctx.train_tree(p, Xh, labels=Lh, y=Yh)
+        exports = [f.export(t) for t in range(cfg["n_trees"])]
         e2e_t.append(time.perf_counter() - t0)
         e2e_ev += f.info()["evaluations"]
-        d2h = sum(v.nbytes for v in g.values())
+        d2h = sum(v.nbytes for g in exports for v in g.values())
         f.free()
     e2e_value = e2e_ev / sum(e2e_t)
-    h2d = wl.X.nbytes + wl.labels.nbytes
+    h2d = wl.X.nbytes + (wl.labels.nbytes if wl.labels is not None else wl.y.nbytes)
 
-    # rooflines: k_project is FP32-FFMA bound (2 d flop per particle-sample
-    # pair); k_hist_scan streams z (4 B per pair) and labels (4 B per entry,
-    # i.e. 4 / P per pair) and is memory bound
-    roofs = {}
-    kp, kh = kst["project"], kst["hist_scan"]
-    if kp["ms"] > 0:
-        ach = 2.0 * wl.d * kp["pairs"] / (kp["ms"] / 1e3) / 1e12
-        roofs["project"] = {"kernel": "project", "bound": "alu", "achieved": ach,
-                            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach / FP32_PEAK_TFLOPS,
-                            "traffic": traffic_per_launch("project", kp),
-                            "avg_launch_ms": kp["ms"] / max(1, kp["launches"]),
-                            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    if kh["ms"] > 0:
-        algo = kh["pairs"] * (4.0 + 4.0 / cfg["n_particles"])
-        ach = algo / (kh["ms"] / 1e3) / 1e9
-        roofs["hist_scan"] = {"kernel": "hist_scan", "bound": "hbm", "achieved": ach,
-                              "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
-                              "traffic": traffic_per_launch("hist_scan", kh),
-                              "avg_launch_ms": kh["ms"] / max(1, kh["launches"]),
-                              "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    dom = max(kst, key=lambda k: kst[k]["ms"])
-    roofline = dict(roofs.get(dom) or next(iter(roofs.values())))
-    roofline["timing"] = "per-launch CUDA events in a second K-tree pass"
-    roofline["others"] = [v for k, v in roofs.items() if k != roofline["kernel"]]
+    roofs = rooflines(kst, wl, cfg, proj, topk, name)
+    dom = max(roofs, key=lambda k: kst[k]["ms"])
+    roofline = dict(roofs[dom])
+    roofline["timing"] = "per-launch CUDA events in a second K-step pass"
+    roofline["others"] = [v for k, v in roofs.items() if k != dom]
     share = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kst.values())), 4)
              for k, v in kst.items() if v["launches"]}
+    extra["kernel_share"] = share
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, cores = oracle_root_sample(cfg, wl, cfg["n_iters"])
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": (f"root-node swarm search of the workload ({wl.n} samples x "
-                          f"{cfg['n_particles']} particles x {cfg['n_iters'] + 1} "
-                          f"evaluations, {dt:.1f} s; fp32-mirror oracle, OpenMP over "
-                          "particles)")}
+        cpu = cpu_baseline(cfg, wl, proj, topk)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded Gaussian mixture)",
-            "config": config_dict(cfg, {"tree_train_ms": tot_ms_max / args.steps,
-                                        "evals_per_tree": evals // args.steps,
-                                        "wall_s": wall,
-                                        "kernel_share": share}),
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32" if proj == "bf16" else "f32",
+            "data": "synthetic (seeded, workloads.py)",
+            "config": config_dict(name, cfg, wl, proj, topk, extra),
             "clocks": clocks.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -355,8 +468,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(W.SETTINGS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--proj", choices=["fp32", "bf16"], default=None)
+    ap.add_argument("--topk", type=int, default=8)
+    ap.add_argument("--compare-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.proj is None:
+        args.proj = W.SETTINGS[args.workload].get("proj", "fp32")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -173,8 +173,9 @@ slm_status slm_evaluate_swarm(slm_ctx* ctx, const slm_params* params,
  * routine. Its scratch is one fixed array of SLM_NOALLOC_SCRATCH_BYTES in the
  * library's device memory, which every GPU that loads the library holds until
  * the process exits. A call needs about 4 * (n_idx * (d + n_pos + 4) + P' * d)
- * bytes of it, P' = n_pos rounded up to a multiple of 16 (each part rounded up
- * to 256 bytes); larger calls return SLM_EUNSUPPORTED and do nothing.
+ * bytes of it, P' = n_pos rounded up to a multiple of 16, plus 16 * n_idx for
+ * MSE (each part rounded up to 256 bytes); larger calls return
+ * SLM_EUNSUPPORTED and do nothing.
  *
  * Same meaning as slm_evaluate_swarm, except: X, labels / y, sample_idx,
  * weights and positions must be device pointers, and out[n_pos] is a device

@@ -58,8 +58,8 @@ __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
 struct ScanScratch {
   uint32_t nl[kMaxBins];  // left weight of each edge (classification)
   uint32_t pc[kMaxBins];  // MSE prefix: weight
-  double ps[kMaxBins];    // MSE prefix: sum w y
-  double pq[kMaxBins];    // MSE prefix: sum w y^2
+  long long ps[kMaxBins];  // MSE prefix: fixed-point sum w (y-c)
+  long long pq[kMaxBins];  // MSE prefix: fixed-point sum w (y-c)^2
   uint64_t wn[kThreads / 32], wd[kThreads / 32];
   double wl[kThreads / 32];
   int wb[kThreads / 32];
@@ -232,13 +232,16 @@ __device__ EvalRes block_scan_cls(uint32_t* h, int B, int K, int min_leaf, ScanS
 // Regression threshold scan of one particle by the whole CTA. cnt/s/q: [B]
 // weight, sum w y, sum w y^2. Prefix sums by warp 0 (sequential within a
 // lane, then across lanes), then one thread per edge.
-__device__ EvalRes block_scan_mse(const uint32_t* cnt, const double* s, const double* q, int B,
-                                  int min_leaf, ScanScratch& sc) {
+// s[b], q[b]: fixed-point sums of w (y-c) and w (y-c)^2 of bin b, worth
+// f1 and f2 per unit; prefix sums stay exact integers and become doubles
+// per edge: SSE of a side = Q - S^2 / n (centred, so little cancels).
+__device__ EvalRes block_scan_mse(const uint32_t* cnt, const long long* s, const long long* q,
+                                  double f1, double f2, int B, int min_leaf, ScanScratch& sc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {
     const int bpl = (B + 31) >> 5;
     uint32_t cs = 0;
-    double ss = 0.0, qs = 0.0;
+    long long ss = 0, qs = 0;
     for (int i = 0; i < bpl; ++i) {
       const int j = lane * bpl + i;
       if (j < B) {
@@ -248,12 +251,12 @@ __device__ EvalRes block_scan_mse(const uint32_t* cnt, const double* s, const do
       }
     }
     uint32_t ic = cs;
-    double is = ss, iq = qs;
+    long long is = ss, iq = qs;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const uint32_t vc = __shfl_up_sync(0xffffffffu, ic, off);
-      const double vs = __shfl_up_sync(0xffffffffu, is, off);
-      const double vq = __shfl_up_sync(0xffffffffu, iq, off);
+      const long long vs = __shfl_up_sync(0xffffffffu, is, off);
+      const long long vq = __shfl_up_sync(0xffffffffu, iq, off);
       if (lane >= off) {
         ic += vc;
         is = vs + is;
@@ -262,11 +265,11 @@ __device__ EvalRes block_scan_mse(const uint32_t* cnt, const double* s, const do
     }
     // exclusive prefix = the previous lane's inclusive sums
     uint32_t rc = ic - cs;
-    double rs = __shfl_up_sync(0xffffffffu, is, 1);
-    double rq = __shfl_up_sync(0xffffffffu, iq, 1);
+    long long rs = __shfl_up_sync(0xffffffffu, is, 1);
+    long long rq = __shfl_up_sync(0xffffffffu, iq, 1);
     if (lane == 0) {
-      rs = 0.0;
-      rq = 0.0;
+      rs = 0;
+      rq = 0;
     }
     for (int i = 0; i < bpl; ++i) {
       const int j = lane * bpl + i;
@@ -282,15 +285,16 @@ __device__ EvalRes block_scan_mse(const uint32_t* cnt, const double* s, const do
   }
   __syncthreads();
   const uint32_t ntot = sc.pc[B - 1];
-  const double stot = sc.ps[B - 1], qtot = sc.pq[B - 1];
+  const long long stot = sc.ps[B - 1], qtot = sc.pq[B - 1];
   const int b = 1 + threadIdx.x;
   double bl = 0.0;
   int bb = -1;
   if (b < B && cnt[b - 1] != 0) {  // empty bin b-1: same partition as edge b-1
     const uint32_t nl = sc.pc[b - 1], nr = ntot - nl;
     if (nl >= (uint32_t)min_leaf && nr >= (uint32_t)min_leaf) {
-      const double sl = sc.ps[b - 1], ql = sc.pq[b - 1];
-      const double sr = stot - sl, qr = qtot - ql;
+      const double sl = (double)sc.ps[b - 1] * f1, ql = (double)sc.pq[b - 1] * f2;
+      const double sr = (double)(stot - sc.ps[b - 1]) * f1;
+      const double qr = (double)(qtot - sc.pq[b - 1]) * f2;
       const double sse_l = ql - sl * sl / (double)nl;
       const double sse_r = qr - sr * sr / (double)nr;
       bl = (sse_l + sse_r) / (double)ntot;
@@ -338,13 +342,14 @@ __device__ __forceinline__ void cp_async_wait() {
 
 constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPG * kXS);
 
-// Stages one kKC-feature chunk of a work unit's rows and positions.
+// Stages one kKC-feature chunk of a work unit's rows and PG positions.
+template <int PG>
 __device__ __forceinline__ void stage_chunk(const Problem& pr, const Swarm& sw,
                                             const WorkTile& wt, int g, int k0,
                                             bool vec, float* xb, float* ab) {
   const int d = pr.d;
   const int kc = min(kKC, d - k0);
-  const float* pos = sw.pos + ((int64_t)wt.node * pr.Pp + g * kPG) * d;
+  const float* pos = sw.pos + ((int64_t)wt.node * pr.Pp + g * PG) * d;
   if (vec) {
     for (int q = threadIdx.x; q < kTS * (kKC / 4); q += kThreads) {
       const int r = q >> 3, cc = (q & 7) * 4;
@@ -352,7 +357,7 @@ __device__ __forceinline__ void stage_chunk(const Problem& pr, const Swarm& sw,
       const float* src = ok ? pr.X + (int64_t)(wt.row0 + r) * d + k0 + cc : pr.X;
       cp_async16(xb + r * kXS + cc, src, ok ? 16 : 0);
     }
-    for (int q = threadIdx.x; q < kPG * (kKC / 4); q += kThreads) {
+    for (int q = threadIdx.x; q < PG * (kKC / 4); q += kThreads) {
       const int p = q >> 3, cc = (q & 7) * 4;
       const bool ok = cc < kc;
       cp_async16(ab + p * kXS + cc, ok ? pos + (int64_t)p * d + k0 + cc : pos, ok ? 16 : 0);
@@ -364,7 +369,7 @@ __device__ __forceinline__ void stage_chunk(const Problem& pr, const Swarm& sw,
       const float* src = ok ? pr.X + (int64_t)(wt.row0 + r) * d + k0 + cc : pr.X;
       cp_async4(xb + r * kXS + cc, src, ok ? 4 : 0);
     }
-    for (int q = threadIdx.x; q < kPG * kKC; q += kThreads) {
+    for (int q = threadIdx.x; q < PG * kKC; q += kThreads) {
       const int p = q >> 5, cc = q & 31;
       const bool ok = cc < kc;
       cp_async4(ab + p * kXS + cc, ok ? pos + (int64_t)p * d + k0 + cc : pos, ok ? 4 : 0);
@@ -373,8 +378,12 @@ __device__ __forceinline__ void stage_chunk(const Problem& pr, const Swarm& sw,
   cp_async_commit();
 }
 
+// PG particles per work unit (16, or 8 for a small re-scored subset): each
+// thread owns 4 rows x PG/4 particles.
+template <int PG>
 __global__ void __launch_bounds__(kThreads, 2)
     k_project(Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, int n_units) {
+  constexpr int PJ = PG / 4;
   extern __shared__ __align__(16) float smf[];
   float* xs0 = smf;
   float* xs1 = smf + kTS * kXS;
@@ -393,13 +402,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   {
     const int u = blockIdx.x;
-    stage_chunk(pr, sw, tiles[u / G], u % G, 0, vec, xs0, as0);
+    stage_chunk<PG>(pr, sw, tiles[u / G], u % G, 0, vec, xs0, as0);
   }
-  float acc[4][4];
+  float acc[4][PJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
 
   for (int s = 0; s < n_st; ++s) {
     const int ui = s / nk, c = s - ui * nk;
@@ -407,8 +416,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (s + 1 < n_st) {
       const int ui1 = (s + 1) / nk, c1 = (s + 1) - ui1 * nk;
       const int u1 = blockIdx.x + ui1 * gridDim.x;
-      stage_chunk(pr, sw, tiles[u1 / G], u1 % G, c1 * kKC, vec, (s & 1) ? xs0 : xs1,
-                  (s & 1) ? as0 : as1);
+      stage_chunk<PG>(pr, sw, tiles[u1 / G], u1 % G, c1 * kKC, vec, (s & 1) ? xs0 : xs1,
+                      (s & 1) ? as0 : as1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -421,15 +430,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     const float* ar = ab + pg * kXS;
 #pragma unroll 2
     for (int k = 0; k < kc4; k += 4) {
-      float4 xv[4], av[4];
+      float4 xv[4], av[PJ];
 #pragma unroll
       for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+      for (int j = 0; j < PJ; ++j) av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < PJ; ++j) {
           acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
           acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
           acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
@@ -441,8 +450,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       const WorkTile wt = tiles[u / G];
       const int g = u % G;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int p = g * kPG + pg + 4 * j;
+      for (int j = 0; j < PJ; ++j) {
+        const int p = g * PG + pg + 4 * j;
         float lo = FLT_MAX, hi = -FLT_MAX;
         bool any = false;
 #pragma unroll
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
     }
     __syncthreads();  // buffer s&1 is refilled by the next stage's copies
   }
@@ -601,16 +610,20 @@ __global__ void __launch_bounds__(128)
 
 // ---- histogram and scan -------------------------------------------------------------
 
-constexpr int kPiece = 4096;  // entries per staged piece (bulk copies carry a fixed cost)
+constexpr int kPiece = 4096;     // entries per staged piece (bulk copies carry a fixed cost)
+constexpr int kPieceMse = 2048;  // MSE pieces also carry two 8-byte moments per entry
 constexpr int kCopies = 4;  // histogram copies, each shared by a pair of warps
 constexpr int kStages = 2;  // staged pieces in flight
 
 __host__ __device__ inline size_t hist_copy_bytes(int crit, int B, int K) {
   return crit == SLM_MSE ? (size_t)B * (4 + 8 + 8) : (size_t)B * K * 4;
 }
-// One staged piece: z of the particle, labels or targets, multiplicities.
-__host__ __device__ inline size_t stage_bytes(bool weighted) {
-  return (size_t)kPiece * 4 * (2 + (weighted ? 1 : 0));
+__host__ __device__ inline int piece_of(int crit) { return crit == SLM_MSE ? kPieceMse : kPiece; }
+// One staged piece: z of the particle; labels (classification) or the two
+// fixed-point moments (MSE); multiplicities.
+__host__ __device__ inline size_t stage_bytes(int crit, bool weighted) {
+  const size_t per = crit == SLM_MSE ? 4 + 8 + 8 : 4 + 4;
+  return (size_t)piece_of(crit) * (per + (weighted ? 4 : 0));
 }
 
 // A cluster of S CTAs per (node, particle). Rank r streams the r-th of S
@@ -645,17 +658,19 @@ __global__ void __launch_bounds__(kThreads, 3)
   const bool mse = pr.crit == SLM_MSE;
   const bool weighted = pr.w != nullptr;
   const int words = mse ? B : B * K;  // u32 counters per copy
-  // shared memory: kCopies histogram copies, then two stages
-  double* hs = reinterpret_cast<double*>(smem);         // MSE [kCopies][B]
-  double* hq = hs + (mse ? kCopies * B : 0);             // MSE [kCopies][B]
+  const int piece = piece_of(pr.crit);
+  // shared memory: kCopies histogram copies, then two stages. MSE bins hold
+  // the weight and the fixed-point sums of w (y-c) and w (y-c)^2.
+  unsigned long long* hs = reinterpret_cast<unsigned long long*>(smem);  // MSE [kCopies][B]
+  unsigned long long* hq = hs + (mse ? kCopies * B : 0);                  // MSE [kCopies][B]
   uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? kCopies * B : 0));  // [kCopies][words]
   unsigned char* stage0 =
       smem + ((hist_copy_bytes(pr.crit, B, K) * kCopies + 127) & ~(size_t)127);
-  const size_t sbytes = stage_bytes(weighted);
+  const size_t sbytes = stage_bytes(pr.crit, weighted);
   const int copy = warp % kCopies;
   uint32_t* h = hc + copy * words;
-  double* hsw = hs + copy * B;
-  double* hqw = hq + copy * B;
+  unsigned long long* hsw = hs + copy * B;
+  unsigned long long* hqw = hq + copy * B;
 
   int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
   if (threadIdx.x == 0) {
@@ -677,8 +692,8 @@ __global__ void __launch_bounds__(kThreads, 3)
   for (int i = threadIdx.x; i < kCopies * words; i += kThreads) hc[i] = 0u;
   if (mse)
     for (int i = threadIdx.x; i < kCopies * B; i += kThreads) {
-      hs[i] = 0.0;
-      hq[i] = 0.0;
+      hs[i] = 0ull;
+      hq[i] = 0ull;
     }
   __syncthreads();
   const bool ok = s_ok;
@@ -688,20 +703,27 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
   const int r_begin = min(nd.seg_len, rank * chunk);
   const int r_end = min(nd.seg_len, r_begin + chunk);
-  const int n_pieces = ok ? (r_end - r_begin + kPiece - 1) / kPiece : 0;
+  const int n_pieces = ok ? (r_end - r_begin + piece - 1) / piece : 0;
   const int64_t e0 = nd.seg_start;  // multiple of 4
+  // stage layout: z [piece] f32 | labels [piece] i32, or moments 2 x [piece]
+  // i64 | multiplicities [piece] u32
+  const size_t off_w = (size_t)piece * (mse ? 4 + 16 : 4 + 4);
   auto issue = [&](int k) {
-    const int r = r_begin + k * kPiece;
-    const int n = min(kPiece, r_end - r);
+    const int r = r_begin + k * piece;
+    const int n = min(piece, r_end - r);
     const uint32_t bytes = (uint32_t)(((n + 3) & ~3) * 4);
     unsigned char* st = stage0 + (k % kStages) * sbytes;
     uint64_t* bar = &s_bar[k % kStages];
     fence_proxy_async();
-    mbar_expect_tx(bar, bytes * (uint32_t)(weighted ? 3 : 2));
+    mbar_expect_tx(bar, bytes * (uint32_t)((mse ? 5 : 2) + (weighted ? 1 : 0)));
     bulk_g2s(st, sw.z + (int64_t)p * pr.Ez + e0 + r, bytes, bar);
-    const void* src = mse ? (const void*)(pr.y + e0 + r) : (const void*)(pr.lab + e0 + r);
-    bulk_g2s(st + (size_t)kPiece * 4, src, bytes, bar);
-    if (weighted) bulk_g2s(st + (size_t)2 * kPiece * 4, pr.w + e0 + r, bytes, bar);
+    if (mse) {
+      bulk_g2s(st + (size_t)piece * 4, pr.m1 + e0 + r, 2 * bytes, bar);
+      bulk_g2s(st + (size_t)piece * 12, pr.m2 + e0 + r, 2 * bytes, bar);
+    } else {
+      bulk_g2s(st + (size_t)piece * 4, pr.lab + e0 + r, bytes, bar);
+    }
+    if (weighted) bulk_g2s(st + off_w, pr.w + e0 + r, bytes, bar);
   };
   if (threadIdx.x == 0)
     for (int k = 0; k < kStages - 1 && k < n_pieces; ++k) issue(k);
@@ -719,21 +741,22 @@ __global__ void __launch_bounds__(kThreads, 3)
       break;
     }
     const unsigned char* st = stage0 + (k % kStages) * sbytes;
-    const int r = r_begin + k * kPiece;
-    const int n = min(kPiece, r_end - r);
+    const int r = r_begin + k * piece;
+    const int n = min(piece, r_end - r);
     const float* zs = reinterpret_cast<const float*>(st);
-    const int32_t* ls = reinterpret_cast<const int32_t*>(st + (size_t)kPiece * 4);
-    const float* ys = reinterpret_cast<const float*>(st + (size_t)kPiece * 4);
-    const uint32_t* ws = reinterpret_cast<const uint32_t*>(st + (size_t)2 * kPiece * 4);
+    const int32_t* ls = reinterpret_cast<const int32_t*>(st + (size_t)piece * 4);
+    const unsigned long long* m1s =
+        reinterpret_cast<const unsigned long long*>(st + (size_t)piece * 4);
+    const unsigned long long* m2s =
+        reinterpret_cast<const unsigned long long*>(st + (size_t)piece * 12);
+    const uint32_t* ws = reinterpret_cast<const uint32_t*>(st + off_w);
     for (int i = threadIdx.x; i < n; i += kThreads) {
       const int b = bin_of(zs[i], zmin, inv_w, B);
       const uint32_t w = weighted ? ws[i] : 1u;
       if (mse) {
-        const float yv = ys[i];
-        const double wy = (double)w * (double)yv;
         atomicAdd(&h[b], w);
-        atomicAdd(&hsw[b], wy);
-        atomicAdd(&hqw[b], wy * (double)yv);
+        atomicAdd(&hsw[b], m1s[i]);  // two's complement: signed sums wrap exactly
+        atomicAdd(&hqw[b], m2s[i]);
       } else {
         atomicAdd(&h[b * K + ls[i]], w);
       }
@@ -750,7 +773,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
   if (mse)
     for (int i = threadIdx.x; i < B; i += kThreads) {
-      double vs = 0.0, vq = 0.0;
+      unsigned long long vs = 0ull, vq = 0ull;
 #pragma unroll
       for (int c = 0; c < kCopies; ++c) {
         vs += hs[c * B + i];
@@ -771,7 +794,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       }
       if (mse)
         for (int i = threadIdx.x; i < B; i += kThreads) {
-          double vs = hs[i], vq = hq[i];
+          unsigned long long vs = hs[i], vq = hq[i];
           for (int q = 1; q < S; ++q) {
             vs += cl.map_shared_rank(hs, q)[i];
             vq += cl.map_shared_rank(hq, q)[i];
@@ -788,7 +811,9 @@ __global__ void __launch_bounds__(kThreads, 3)
   if (!ok) {
     res = invalid_res();
   } else {
-    res = mse ? block_scan_mse(hc, hs, hq, B, pr.min_leaf, sc)
+    res = mse ? block_scan_mse(hc, reinterpret_cast<const long long*>(hs),
+                               reinterpret_cast<const long long*>(hq), pr.mscale[2 * a],
+                               pr.mscale[2 * a + 1], B, pr.min_leaf, sc)
               : pr.crit == SLM_GINI ? block_scan_cls<SLM_GINI>(hc, B, K, pr.min_leaf, sc)
                                     : block_scan_cls<SLM_ENTROPY>(hc, B, K, pr.min_leaf, sc);
     res.zmin = zmin;
@@ -880,20 +905,123 @@ __global__ void k_bootstrap(uint64_t seed, uint32_t tree, int64_t n,
   }
 }
 
+// ---- MSE moments ------------------------------------------------------------------
+
+__global__ void k_mse_init(int A, unsigned long long* acc_w, int32_t* acc_y) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= A) return;
+  acc_w[a] = 0ull;
+  acc_y[2 * a] = INT_MAX;
+  acc_y[2 * a + 1] = INT_MIN;
+}
+
+// One CTA per kTS-row tile: the tile's weight and range of y, folded into its node.
+__global__ void __launch_bounds__(kTS)
+    k_mse_range(Problem pr, const WorkTile* __restrict__ tiles, unsigned long long* acc_w,
+                int32_t* acc_y) {
+  __shared__ unsigned long long s_w[kTS / 32];
+  __shared__ int s_lo[kTS / 32], s_hi[kTS / 32];
+  const WorkTile wt = tiles[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long w = 0ull;
+  int lo = INT_MAX, hi = INT_MIN;
+  if ((int)threadIdx.x < wt.rows) {
+    const int64_t e = wt.row0 + threadIdx.x;
+    w = pr.w ? pr.w[e] : 1u;
+    if (w) lo = hi = f2ord(pr.y[e]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    w += __shfl_xor_sync(0xffffffffu, w, off);
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+  }
+  if (lane == 0) {
+    s_w[warp] = w;
+    s_lo[warp] = lo;
+    s_hi[warp] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kTS / 32; ++i) {
+      w += s_w[i];
+      lo = min(lo, s_lo[i]);
+      hi = max(hi, s_hi[i]);
+    }
+    atomicAdd(&acc_w[wt.node], w);
+    if (lo != INT_MAX) {
+      atomicMin(&acc_y[2 * wt.node], lo);
+      atomicMax(&acc_y[2 * wt.node + 1], hi);
+    }
+  }
+}
+
+// One CTA per tile: the node's centre and scales (every CTA of the node
+// derives the same values), then the fixed-point moments of the tile's rows.
+__global__ void __launch_bounds__(kTS)
+    k_mse_moments(Problem pr, const WorkTile* __restrict__ tiles,
+                  const unsigned long long* __restrict__ acc_w, const int32_t* __restrict__ acc_y,
+                  long long* m1, long long* m2, double* mscale) {
+  const WorkTile wt = tiles[blockIdx.x];
+  const int a = wt.node;
+  const double W = (double)acc_w[a];
+  float c = 0.0f;
+  double D = 0.0;
+  if (acc_y[2 * a] != INT_MAX) {
+    const double ylo = ord2f(acc_y[2 * a]), yhi = ord2f(acc_y[2 * a + 1]);
+    c = (float)(0.5 * (ylo + yhi));
+    // rounding is monotone: every |y - c| below is at most D
+    D = fmax(yhi - (double)c, (double)c - ylo);
+  }
+  int s = 0, t = 0;
+  if (W > 0.0 && D > 0.0) {
+    int e1, e2;
+    frexp(W * D * (1.0 + 0x1p-40), &e1);      // W D < 2^e1
+    frexp(W * D * D * (1.0 + 0x1p-40), &e2);  // W D^2 < 2^e2
+    s = 61 - e1;
+    t = e2 + 2 * s - 61;
+  }
+  if (threadIdx.x == 0) {  // identical from every tile of the node
+    mscale[2 * a] = ldexp(1.0, -s);
+    mscale[2 * a + 1] = ldexp(1.0, t - 2 * s);
+  }
+  if ((int)threadIdx.x >= wt.rows) return;
+  const int64_t e = wt.row0 + threadIdx.x;
+  const double w = pr.w ? (double)pr.w[e] : 1.0;
+  const double v = (double)pr.y[e] - (double)c;
+  m1[e] = llrint(w * v * ldexp(1.0, s));
+  m2[e] = llrint(w * v * v * ldexp(1.0, 2 * s - t));
+}
+
 }  // namespace
 
 // ---- launchers ---------------------------------------------------------------------
 
+cudaError_t launch_mse_moments(const Problem& pr, const WorkTile* tiles, int n_tiles, int A,
+                               unsigned long long* acc_w, int32_t* acc_y, long long* m1,
+                               long long* m2, double* mscale, cudaStream_t st) {
+  if (A <= 0) return cudaSuccess;
+  k_mse_init<<<(A + 255) / 256, 256, 0, st>>>(A, acc_w, acc_y);
+  if (n_tiles > 0) {
+    k_mse_range<<<n_tiles, kTS, 0, st>>>(pr, tiles, acc_w, acc_y);
+    k_mse_moments<<<n_tiles, kTS, 0, st>>>(pr, tiles, acc_w, acc_y, m1, m2, mscale);
+  }
+  return cudaGetLastError();
+}
+
 static size_t hist_smem_bytes(const Problem& pr) {
   const size_t hist = (hist_copy_bytes(pr.crit, pr.B, pr.K) * kCopies + 127) & ~(size_t)127;
-  return hist + kStages * stage_bytes(pr.w != nullptr);
+  return hist + kStages * stage_bytes(pr.crit, pr.w != nullptr);
 }
 
 cudaError_t prepare_eval_kernels(const Problem& pr) {
-  cudaError_t e = cudaFuncSetAttribute(k_project,
+  cudaError_t e = cudaFuncSetAttribute(k_project<16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kProjSmem);
   if (e) return e;
+  if ((e = cudaFuncSetAttribute(k_project<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kProjSmem)))
+    return e;
   if ((e = cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hist_smem_bytes(pr))))
     return e;
@@ -923,7 +1051,8 @@ cudaError_t launch_project(const Problem& pr, const Swarm& sw, const WorkTile* t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_project, pr, sw, tiles, n_units);
+  if (pr.Pp == 8 * pr.G) return cudaLaunchKernelEx(&cfg, k_project<8>, pr, sw, tiles, n_units);
+  return cudaLaunchKernelEx(&cfg, k_project<16>, pr, sw, tiles, n_units);
 }
 
 int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_cluster) {
@@ -938,7 +1067,7 @@ int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_clus
   const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * n_sm;
   int S = 1;
   while (2 * S <= max_cluster && (int64_t)A * pr.P * (2 * S) <= resident &&
-         max_len / (2 * S) >= kPiece)
+         max_len / (2 * S) >= piece_of(pr.crit))
     S *= 2;
   return S;
 }

@@ -145,13 +145,17 @@ __host__ __device__ inline uint32_t mma_tmem_cols(int Pp) {
 // tile is one or more kMmaKC-feature chunks ("items"). Thread 0 streams the
 // items through two shared-memory stages (bulk copies, mbarrier full[s]),
 // issues the MMAs of an item as soon as it lands and commits them to
-// free[s] (stage reusable) and, after the tile's last chunk, to acc (tile
-// complete). The positions of the tile's node are staged once per node.
+// free[s] (stage reusable) and, after the tile's last chunk, to acc[u & 1]:
+// the accumulator is double-buffered in tensor memory, so the MMAs of tile
+// u+1 run while the four warps read tile u back. The positions of a node are
+// staged once per node. Each lane keeps a running range of the columns
+// c = lane (mod 32) over the warp's rows, folded into shared and global
+// memory once per node.
 __global__ void __launch_bounds__(kMmaThreads)
     k_project_mma(Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, int n_tiles,
                   const uint16_t* __restrict__ posb) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_full[2], bar_free[2], bar_acc, bar_b;
+  __shared__ __align__(8) uint64_t bar_full[2], bar_free[2], bar_acc[2], bar_b;
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
   __shared__ int s_lo[kMaxParticles], s_hi[kMaxParticles];
@@ -161,20 +165,20 @@ __global__ void __launch_bounds__(kMmaThreads)
   unsigned char* As = smem;
   unsigned char* Bs = smem + 2 * stage;
   const uint32_t b_bytes = (uint32_t)Pp * (uint32_t)dp * 2u;
-  const uint32_t cols = mma_tmem_cols(Pp);
+  const uint32_t cols = mma_tmem_cols(Pp);  // one accumulator; two are allocated
   const int nch = (dp + kMmaKC - 1) / kMmaKC;
   const uint32_t idesc = mma_idesc(kMmaRows, Pp);
 
   if (warp == 0) {
-    tmem_alloc(&s_tmem, cols);
+    tmem_alloc(&s_tmem, 2 * cols);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&bar_full[0], 1);
-    mbar_init(&bar_full[1], 1);
-    mbar_init(&bar_free[0], 1);
-    mbar_init(&bar_free[1], 1);
-    mbar_init(&bar_acc, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_full[i], 1);
+      mbar_init(&bar_free[i], 1);
+      mbar_init(&bar_acc[i], 1);
+    }
     mbar_init(&bar_b, 1);
     mbar_init_fence();
     s_err = 0;
@@ -193,13 +197,14 @@ __global__ void __launch_bounds__(kMmaThreads)
   const int my_tiles =
       (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int n_items = my_tiles * nch;
+  auto tile_of = [&](int ti) { return tiles[blockIdx.x + ti * gridDim.x]; };
   auto wait_bar = [&](uint64_t* bar, uint32_t parity) {
     if (!mbar_wait(bar, parity, kWaitPolls)) s_err = 1;
   };
   // thread 0: bulk copy of item i into stage i & 1
   auto issue = [&](int i) {
     const int ti = i / nch, c = i - ti * nch;
-    const WorkTile wt = tiles[blockIdx.x + ti * gridDim.x];
+    const WorkTile wt = tile_of(ti);
     const int k0 = c * kMmaKC;
     const int kl = dp - k0 < kMmaKC ? dp - k0 : kMmaKC;
     const uint32_t bytes = (uint32_t)kMmaRows * (uint32_t)kl * 2u;
@@ -207,96 +212,117 @@ __global__ void __launch_bounds__(kMmaThreads)
     mbar_expect_tx(&bar_full[i & 1], bytes);
     bulk_g2s(As + (i & 1) * stage, src, bytes, &bar_full[i & 1]);
   };
-  auto flush = [&](int node) {
-    for (int p = tid; p < P; p += kMmaThreads) {
-      if (s_lo[p] != INT_MAX) {
-        int* zz = sw.zmm + ((int64_t)node * Pp + p) * 2;
-        atomicMin(zz, s_lo[p]);
-        atomicMax(zz + 1, s_hi[p]);
-      }
-      s_lo[p] = INT_MAX;
-      s_hi[p] = INT_MIN;
+  // thread 0: every MMA of tile ti into accumulator ti & 1
+  int b_node = -1;
+  uint32_t b_phase = 0;
+  auto mma_tile = [&](int ti) {
+    const WorkTile wt = tile_of(ti);
+    if (wt.node != b_node) {
+      // the MMAs of tile ti-1 read the staged positions: let them finish
+      if (ti > 0) wait_bar(&bar_acc[(ti - 1) & 1], (uint32_t)(((ti - 1) >> 1) & 1));
+      mbar_expect_tx(&bar_b, b_bytes);
+      bulk_g2s(Bs, posb + (int64_t)wt.node * Pp * dp, b_bytes, &bar_b);
+      wait_bar(&bar_b, b_phase);
+      b_phase ^= 1u;
+      b_node = wt.node;
     }
+    const uint32_t d_tmem = tmem + (uint32_t)(ti & 1) * cols;
+    for (int c = 0; c < nch; ++c) {
+      const int i = ti * nch + c;
+      if (i + 1 < n_items) {
+        // stage (i+1)&1 last held item i-1: wait until its MMAs are done
+        if (i >= 1) wait_bar(&bar_free[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1));
+        issue(i + 1);
+      }
+      wait_bar(&bar_full[i & 1], (uint32_t)((i >> 1) & 1));
+      tc_fence_after();
+      const int k0 = c * kMmaKC;
+      const int kl = dp - k0 < kMmaKC ? dp - k0 : kMmaKC;
+      const uint32_t a0 = smem_addr(As + (i & 1) * stage);
+      const uint32_t b0 = smem_addr(Bs);
+      for (int j = 0; j < kl / 16; ++j) {
+        const uint64_t ad = mma_desc(a0 + (uint32_t)j * (kMmaRows * 32), 128, 256);
+        const uint64_t bd = mma_desc(b0 + (uint32_t)(k0 / 16 + j) * (uint32_t)(Pp * 32), 128, 256);
+        mma_bf16(d_tmem, ad, bd, idesc, (c > 0 || j > 0) ? 1u : 0u);
+      }
+      mma_commit(&bar_free[i & 1]);
+    }
+    mma_commit(&bar_acc[ti & 1]);
   };
 
-  if (tid == 0 && n_items > 0) issue(0);
-  int cur_node = -1;
-  uint32_t b_phase = 0;
+  // running range of the warp's rows: lane l owns columns 32 q + l
+  int run_lo[kMaxParticles / 32], run_hi[kMaxParticles / 32];
+#pragma unroll
+  for (int q = 0; q < kMaxParticles / 32; ++q) {
+    run_lo[q] = INT_MAX;
+    run_hi[q] = INT_MIN;
+  }
+
+  if (tid == 0 && n_items > 0) {
+    issue(0);
+    mma_tile(0);
+  }
   for (int ti = 0; ti < my_tiles; ++ti) {
-    const WorkTile wt = tiles[blockIdx.x + ti * gridDim.x];
-    const bool new_node = wt.node != cur_node;
-    if (new_node) {
-      if (cur_node >= 0) {
-        flush(cur_node);
-        __syncthreads();  // every slot reset before this tile's epilogue folds into it
-      }
-      cur_node = wt.node;
-      // every MMA of the previous node completed before its last epilogue
-      if (tid == 0) {
-        mbar_expect_tx(&bar_b, b_bytes);
-        bulk_g2s(Bs, posb + (int64_t)wt.node * Pp * dp, b_bytes, &bar_b);
-      }
-    }
-    if (tid == 0) {
-      if (new_node) {
-        wait_bar(&bar_b, b_phase);
-        b_phase ^= 1u;
-      }
-      for (int c = 0; c < nch; ++c) {
-        const int i = ti * nch + c;
-        if (i + 1 < n_items) {
-          // stage (i+1)&1 last held item i-1: wait until its MMAs are done
-          if (i >= 1) wait_bar(&bar_free[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1));
-          issue(i + 1);
-        }
-        wait_bar(&bar_full[i & 1], (uint32_t)((i >> 1) & 1));
-        tc_fence_after();
-        const int k0 = c * kMmaKC;
-        const int kl = dp - k0 < kMmaKC ? dp - k0 : kMmaKC;
-        const uint32_t a0 = smem_addr(As + (i & 1) * stage);
-        const uint32_t b0 = smem_addr(Bs);
-        for (int j = 0; j < kl / 16; ++j) {
-          const uint64_t ad = mma_desc(a0 + (uint32_t)j * (kMmaRows * 32), 128, 256);
-          const uint64_t bd = mma_desc(b0 + (uint32_t)(k0 / 16 + j) * (uint32_t)(Pp * 32), 128, 256);
-          mma_bf16(tmem, ad, bd, idesc, (c > 0 || j > 0) ? 1u : 0u);
-        }
-        mma_commit(&bar_free[i & 1]);
-      }
-      mma_commit(&bar_acc);
-    }
-    // epilogue: accumulator row r = 32 warp + lane holds z of every particle
-    if (!mbar_wait(&bar_acc, (uint32_t)(ti & 1), kWaitPolls)) s_err = 1;
+    const WorkTile wt = tile_of(ti);
+    // accumulator (ti+1)&1 was last read in iteration ti-1, before its barrier
+    if (tid == 0 && ti + 1 < my_tiles) mma_tile(ti + 1);
+    if (!mbar_wait(&bar_acc[ti & 1], (uint32_t)((ti >> 1) & 1), kWaitPolls)) s_err = 1;
     tc_fence_after();
+    // epilogue: accumulator row r = 32 warp + lane holds z of every particle
     const int r = warp * 32 + lane;
     const bool rv = r < wt.rows;
     float* zrow = sw.z + wt.row0 + r;
-    for (int cb = 0; cb < Pp / 16; ++cb) {
-      uint32_t v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), v);
+    const uint32_t t_row = tmem + (uint32_t)(ti & 1) * cols + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int p = cb * 16 + j;
-        const float z = __uint_as_float(v[j]);
-        const int oz = f2ord(z);
-        const int lo = __reduce_min_sync(0xffffffffu, rv ? oz : INT_MAX);
-        const int hi = __reduce_max_sync(0xffffffffu, rv ? oz : INT_MIN);
-        if (p < P) {
-          if (rv) zrow[(int64_t)p * pr.Ez] = z;
-          if (lane == 0 && lo != INT_MAX) {
-            atomicMin(&s_lo[p], lo);
-            atomicMax(&s_hi[p], hi);
-          }
+    for (int cb = 0; cb < kMaxParticles / 16; ++cb) {
+      if (cb * 16 < Pp) {
+        uint32_t v[16];
+        tmem_ld16(t_row + (uint32_t)(cb * 16), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int p = cb * 16 + j;
+          const float z = __uint_as_float(v[j]);
+          const int oz = f2ord(z);
+          const int lo = __reduce_min_sync(0xffffffffu, rv ? oz : INT_MAX);
+          const int hi = __reduce_max_sync(0xffffffffu, rv ? oz : INT_MIN);
+          if (rv && p < P) zrow[(int64_t)p * pr.Ez] = z;
+          const bool mine = lane == (p & 31);
+          run_lo[p >> 5] = mine ? min(run_lo[p >> 5], lo) : run_lo[p >> 5];
+          run_hi[p >> 5] = mine ? max(run_hi[p >> 5], hi) : run_hi[p >> 5];
         }
       }
     }
     tc_fence_before();
-    __syncthreads();  // accumulator and range slots free for the next tile
+    const bool last_of_node = ti + 1 == my_tiles || tile_of(ti + 1).node != wt.node;
+    if (last_of_node) {
+      // fold the warps' ranges of this node, then publish them
+#pragma unroll
+      for (int q = 0; q < kMaxParticles / 32; ++q) {
+        const int p = q * 32 + lane;
+        if (p < P && run_lo[q] != INT_MAX) {
+          atomicMin(&s_lo[p], run_lo[q]);
+          atomicMax(&s_hi[p], run_hi[q]);
+        }
+        run_lo[q] = INT_MAX;
+        run_hi[q] = INT_MIN;
+      }
+      __syncthreads();
+      for (int p = tid; p < P; p += kMmaThreads) {
+        if (s_lo[p] != INT_MAX) {
+          int* zz = sw.zmm + ((int64_t)wt.node * Pp + p) * 2;
+          atomicMin(zz, s_lo[p]);
+          atomicMax(zz + 1, s_hi[p]);
+        }
+        s_lo[p] = INT_MAX;
+        s_hi[p] = INT_MIN;
+      }
+    }
+    __syncthreads();  // accumulator ti & 1 and the range slots free again
   }
-  if (cur_node >= 0) flush(cur_node);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, cols);
+  if (warp == 0) tmem_dealloc(tmem, 2 * cols);
   if (tid == 0 && s_err && sw.err) atomicExch(sw.err, 4);
 }
 
@@ -343,6 +369,9 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Grid (node, group of 8 particles): warp w of block y merges particle
+// 8 y + w and takes its pbest step; block y = 0 also takes the node's gbest
+// step among the re-scored particles, from their FP32 scores in cur2.
 __global__ void __launch_bounds__(256)
     k_merge(Problem pr, Swarm sw, const EvalRes* __restrict__ cur2, int kp,
             const int32_t* __restrict__ inv, int t, int do_update) {
@@ -352,14 +381,14 @@ __global__ void __launch_bounds__(256)
   const int a = blockIdx.x, A = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int Pp = pr.Pp, d = pr.d;
-  for (int p = warp; p < pr.P; p += blockDim.x / 32) {
+  const int p = blockIdx.y * 8 + warp;
+  if (p < pr.P) {
     const int q = inv[(int64_t)a * Pp + p];
     const EvalRes e = q >= 0 ? cur2[(int64_t)a * kp + q] : sw.cur[(int64_t)a * Pp + p];
     if (q >= 0 && lane == 0) sw.cur[(int64_t)a * Pp + p] = e;
     if (do_update) pbest_step(pr, sw, a, p, t, e);
   }
-  if (!do_update) return;
-  __syncthreads();
+  if (!do_update || blockIdx.y != 0) return;
   if (warp == 0) {
     // gbest step among the re-scored particles: the best strictly better
     // than the gbest of iteration t-1 (at t = 0 any), ties to the lower index
@@ -367,11 +396,11 @@ __global__ void __launch_bounds__(256)
     int bi = -1;
     EvalRes be = invalid_res();
     for (int q = lane; q < sw.k; q += 32) {
-      const int p = sw.sel[(int64_t)a * sw.k + q];
-      const EvalRes e = sw.cur[(int64_t)a * Pp + p];
+      const int pq = sw.sel[(int64_t)a * sw.k + q];
+      const EvalRes e = cur2[(int64_t)a * kp + q];
       if (!(t == 0 || better(e, gold, pr.crit))) continue;
       if (bi < 0 || better(e, be, pr.crit)) {
-        bi = p;
+        bi = pq;
         be = e;
       }
     }
@@ -417,7 +446,7 @@ __global__ void __launch_bounds__(256)
 
 size_t mma_smem_bytes(const Problem& pr) {
   const size_t need = 2 * (size_t)mma_stage_bytes(pr.dp) + (size_t)pr.Pp * pr.dp * 2;
-  // at most 512 / cols CTAs may share an SM's tensor memory: ask for enough
+  // at most 512 / (2 cols) CTAs fit in an SM's tensor memory: ask for enough
   // shared memory that no more fit
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -426,7 +455,7 @@ size_t mma_smem_bytes(const Problem& pr) {
     cudaGetLastError();
     per_sm = 233472;
   }
-  const int max_ctas = (int)(512u / mma_tmem_cols(pr.Pp));
+  const int max_ctas = (int)(512u / (2 * mma_tmem_cols(pr.Pp)));
   const size_t floor_bytes = ((size_t)per_sm / (size_t)(max_ctas + 1) + 128) & ~(size_t)127;
   return need > floor_bytes ? need : floor_bytes;
 }
@@ -445,8 +474,11 @@ cudaError_t launch_to_mma_layout(const float* src, int64_t n_src_rows, int d, in
 }
 
 cudaError_t prepare_mma_kernels(const Problem& pr) {
-  return cudaFuncSetAttribute(k_project_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)mma_smem_bytes(pr));
+  cudaError_t e = cudaFuncSetAttribute(k_project_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)mma_smem_bytes(pr));
+  if (e) return e;
+  return cudaFuncSetAttribute(k_project_mma, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 int mma_grid_cap(const Problem& pr, int n_sm) {
@@ -496,7 +528,7 @@ cudaError_t launch_merge(const Problem& pr, const Swarm& sw, int A, const EvalRe
                          const int32_t* inv, int t, int do_update, cudaStream_t st) {
   if (A <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)A, 1, 1);
+  cfg.gridDim = dim3((unsigned)A, (unsigned)((pr.P + 7) / 8), 1);
   cfg.blockDim = dim3(256, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

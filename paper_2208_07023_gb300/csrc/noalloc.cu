@@ -37,10 +37,10 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Scratch layout of one call.
 struct Layout {
-  size_t xl, lab, yl, w, idx, z, zmm, pos, nodes, tiles, words, total;
+  size_t xl, lab, yl, w, idx, z, zmm, pos, nodes, tiles, words, m1, m2, macc, mscale, total;
 };
 
-Layout layout(int64_t n_idx, int d, int Pp, int P) {
+Layout layout(int64_t n_idx, int d, int Pp, int P, bool mse) {
   const int64_t ez = (n_idx + 3) / 4 * 4;
   const int64_t tiles = (n_idx + kTS - 1) / kTS;
   Layout l{};
@@ -67,6 +67,16 @@ Layout layout(int64_t n_idx, int d, int Pp, int P) {
   o = align256(o + sizeof(WorkTile) * (size_t)(tiles > 0 ? tiles : 1));
   l.words = o;  // [0] validation status, [1] kernel error word
   o = align256(o + 2 * sizeof(int32_t));
+  if (mse) {  // fixed-point moments of the entries, the node's range and scales
+    l.m1 = o;
+    o = align256(o + sizeof(long long) * (size_t)(ez + 16));
+    l.m2 = o;
+    o = align256(o + sizeof(long long) * (size_t)(ez + 16));
+    l.macc = o;  // weight (u64) and ordered-int range of y
+    o = align256(o + 16);
+    l.mscale = o;
+    o = align256(o + 2 * sizeof(double));
+  }
   l.total = o;
   return l;
 }
@@ -120,7 +130,7 @@ extern "C" slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
   if (n_idx < 0 || n_idx > INT32_MAX) return SLM_EINVAL;
   if (p->criterion == SLM_GINI && n_idx >= (int64_t(1) << 22)) return SLM_EUNSUPPORTED;
   const int Pp = (n_pos + kPG - 1) / kPG * kPG;
-  const Layout L = layout(n_idx, d, Pp, n_pos);
+  const Layout L = layout(n_idx, d, Pp, n_pos, mse);
   if (L.total > (size_t)SLM_NOALLOC_SCRATCH_BYTES) return SLM_EUNSUPPORTED;  // too large
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -191,6 +201,18 @@ extern "C" slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
   sw.zmm = reinterpret_cast<int32_t*>(base + L.zmm);
   sw.z = reinterpret_cast<float*>(base + L.z);
   sw.err = words + 1;
+  if (mse) {
+    pr.m1 = reinterpret_cast<long long*>(base + L.m1);
+    pr.m2 = reinterpret_cast<long long*>(base + L.m2);
+    pr.mscale = reinterpret_cast<double*>(base + L.mscale);
+    if (launch_mse_moments(pr, tiles, n_tiles, 1,
+                           reinterpret_cast<unsigned long long*>(base + L.macc),
+                           reinterpret_cast<int32_t*>(base + L.macc + 8),
+                           reinterpret_cast<long long*>(base + L.m1),
+                           reinterpret_cast<long long*>(base + L.m2),
+                           reinterpret_cast<double*>(base + L.mscale), st) != cudaSuccess)
+      return SLM_ECUDA;
+  }
   if ((e = prepare_eval_kernels(pr))) return SLM_ECUDA;
   int n_sm = 1;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)

@@ -27,6 +27,8 @@ enum Slot {
   S_TRACE, S_ZMM, S_Z, S_DONE, S_NODES, S_TILES, S_STATUS, S_ERR, S_OUT,
   // SLM_PROJ_BF16_TOPK
   W_XB, S_POSB, S_MTILES, S_SEL, S_INV, S_POSK, S_Z2, S_ZMM2, S_CUR2,
+  // MSE moments
+  S_M1, S_M2, S_MACCW, S_MACCY, S_MSCALE,
   N_SLOTS
 };
 
@@ -282,8 +284,9 @@ T* ws_ptr(slm_ctx* c, Slot s) {
   return static_cast<T*>(c->ws[s].p);
 }
 
-// Scoring buffers of A nodes (one batch): z, ranges, node and tile lists.
-slm_status setup_scoring(slm_ctx* c, const Problem& pr, int A,
+// Scoring buffers of A nodes (one batch): z, ranges, node and tile lists;
+// for MSE also the entries' fixed-point moments (pr.m1, pr.m2, pr.mscale).
+slm_status setup_scoring(slm_ctx* c, Problem& pr, int A,
                          const std::vector<NodeDesc>& nodes,
                          const std::vector<WorkTile>& tiles, Swarm* sw) {
   CK(ensure(c->ws[S_CUR], sizeof(EvalRes) * (size_t)A * pr.Pp));
@@ -298,6 +301,24 @@ slm_status setup_scoring(slm_ctx* c, const Problem& pr, int A,
                        cudaMemcpyHostToDevice, c->stream));
   CK(ensure(c->ws[S_ERR], sizeof(int32_t)));
   CK(cudaMemsetAsync(c->ws[S_ERR].p, 0, sizeof(int32_t), c->stream));
+  if (pr.crit == SLM_MSE) {
+    const size_t ne = (size_t)(pr.Ez > 0 ? pr.Ez : 4) + 16;
+    CK(ensure(c->ws[S_M1], sizeof(long long) * ne));
+    CK(ensure(c->ws[S_M2], sizeof(long long) * ne));
+    CK(ensure(c->ws[S_MACCW], sizeof(unsigned long long) * (size_t)A));
+    CK(ensure(c->ws[S_MACCY], sizeof(int32_t) * 2 * (size_t)A));
+    CK(ensure(c->ws[S_MSCALE], sizeof(double) * 2 * (size_t)A));
+    pr.m1 = ws_ptr<long long>(c, S_M1);
+    pr.m2 = ws_ptr<long long>(c, S_M2);
+    pr.mscale = ws_ptr<double>(c, S_MSCALE);
+    CK(launch(c, SLM_K_NODE_STATS, 0.0, [&] {
+      return launch_mse_moments(pr, ws_ptr<WorkTile>(c, S_TILES), (int)tiles.size(), A,
+                                ws_ptr<unsigned long long>(c, S_MACCW),
+                                ws_ptr<int32_t>(c, S_MACCY), ws_ptr<long long>(c, S_M1),
+                                ws_ptr<long long>(c, S_M2), ws_ptr<double>(c, S_MSCALE),
+                                c->stream);
+    }));
+  }
   sw->cur = ws_ptr<EvalRes>(c, S_CUR);
   sw->zmm = ws_ptr<int32_t>(c, S_ZMM);
   sw->z = ws_ptr<float>(c, S_Z);
@@ -307,7 +328,7 @@ slm_status setup_scoring(slm_ctx* c, const Problem& pr, int A,
 }
 
 // Allocates the swarm buffers of A nodes.
-slm_status setup_swarm(slm_ctx* c, const Problem& pr, int A, int T, bool want_trace,
+slm_status setup_swarm(slm_ctx* c, Problem& pr, int A, int T, bool want_trace,
                        const std::vector<NodeDesc>& nodes,
                        const std::vector<WorkTile>& tiles, Swarm* sw) {
   Swarm s{};
@@ -349,7 +370,7 @@ int batch_split(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& node
 // particles on the tensor cores, then FP32 re-scores of the k best per node.
 struct Bf16Plan {
   bool on = false;
-  int k = 0, kp = 0;     // re-scored particles per node; padded to kPG
+  int k = 0, kp = 0;     // re-scored particles per node; padded to 8
   int n_mtiles = 0;      // kMmaRows-row tiles of the batch
   int grid = 0;          // k_project_mma grid
   int S_k = 1;           // cluster split of the re-scoring histogram pass
@@ -369,7 +390,7 @@ slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>
   Bf16Plan b;
   b.on = true;
   b.k = k;
-  b.kp = (k + kPG - 1) / kPG * kPG;
+  b.kp = (k + 7) / 8 * 8;  // the re-scoring projection runs in groups of 8 or 16
   std::vector<WorkTile> mt;
   for (int a = 0; a < A; ++a) {
     if (nodes[a].seg_start % kMmaRows)
@@ -408,7 +429,7 @@ slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>
     b.pr_k = pr;
     b.pr_k.P = k;
     b.pr_k.Pp = b.kp;
-    b.pr_k.G = b.kp / kPG;
+    b.pr_k.G = b.kp % 16 == 0 ? b.kp / 16 : b.kp / 8;
     b.sw_k = *sw;
     b.sw_k.pos = ws_ptr<float>(c, S_POSK);
     b.sw_k.z = ws_ptr<float>(c, S_Z2);
@@ -484,7 +505,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
 }
 
 // PSO search of every node of a batch (Algorithm 1, synchronous updates).
-slm_status run_search(slm_ctx* c, const slm_params* p, const Problem& pr,
+slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
                       Swarm* sw_out) {
   const int A = (int)nodes.size();

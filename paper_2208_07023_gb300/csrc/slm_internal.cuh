@@ -82,6 +82,11 @@ struct Problem {
   // layout of launch_to_mma_layout (kMmaRows-row blocks), d padded to dp
   const uint16_t* Xb;
   int32_t dp;             // d rounded up to a multiple of 16
+  // MSE: per entry, w (y - c) and w (y - c)^2 in fixed point (c = the node's
+  // mid-range); mscale[2a], mscale[2a+1]: value of one unit of each
+  const long long* m1;
+  const long long* m2;
+  const double* mscale;
 };
 
 // Device swarm state of A nodes.
@@ -163,6 +168,14 @@ cudaError_t launch_topk(const Problem& pr, const Swarm& sw, int A, int k, int kp
 cudaError_t launch_merge(const Problem& pr, const Swarm& sw, int A, const EvalRes* cur2,
                          int kp, const int32_t* inv, int t, int do_update, cudaStream_t st);
 
+// MSE moments of the entries of A nodes (tiles: kTS-row tiles with node
+// index): per node the range of y and the weight W (acc_w[A], acc_y[A, 2]),
+// then per entry m1 = round(w (y-c) 2^s), m2 = round(w (y-c)^2 2^(2s-t)),
+// with c the node's mid-range and s, t chosen so each node sum stays below
+// 2^61; mscale[A, 2] = 2^-s, 2^(t-2s).
+cudaError_t launch_mse_moments(const Problem& pr, const WorkTile* tiles, int n_tiles, int A,
+                               unsigned long long* acc_w, int32_t* acc_y, long long* m1,
+                               long long* m2, double* mscale, cudaStream_t st);
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,
                                   int P, int d, uint32_t purpose, float* u,
                                   cudaStream_t st);

@@ -130,7 +130,7 @@ SETTINGS = {
     "regtree_n200k_d128": dict(
         builder=lambda seed=1: tanh_regression(200_000, 128, 8, 0.1, seed),
         criterion="mse", n_particles=64, n_iters=80, n_bins=256,
-        max_depth=10, min_leaf=20, n_trees=1),
+        max_depth=10, min_leaf=20, n_trees=1, proj="bf16", topk=8),
     # bagged forest of 64 trees
     "forest64_n100k_d32_k5": dict(
         builder=lambda seed=1: gmm(100_000, 32, 5, seed),
