@@ -3,6 +3,7 @@
 // mbarrier waits, and the pbest step of Algorithm 1.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -138,6 +139,35 @@ __device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, i
   if (!imp) return;
   const int64_t o = ((int64_t)a * pr.Pp + p) * pr.d;
   for (int j = lane; j < pr.d; j += 32) sw.pbest[o + j] = sw.pos[o + j];
+}
+
+// Score written by another CTA of this grid: read through L2.
+__device__ __forceinline__ EvalRes ldcg_res(const EvalRes* r) {
+  EvalRes o;
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(r);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&o);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(EvalRes) / 8); ++i) d[i] = __ldcg(w + i);
+  return o;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Four consecutive features j0..j0+3 (j0 % 4 == 0) of particle p of node a as
+// bfloat16 MMA operands: posb[a, Pp * dp] in the K-major core-matrix layout
+// (16-feature steps of Pp x 16, 8-row groups of 128 elements, two 8-feature
+// halves of 64, rows of 8).
+__device__ __forceinline__ void store_posb4(uint16_t* posb, int Pp, int dp, int a, int p, int j0,
+                                            const float (&v)[4]) {
+  const int64_t off = (int64_t)a * Pp * dp + (int64_t)(j0 >> 4) * Pp * 16 + (p >> 3) * 128 +
+                      ((j0 >> 3) & 1) * 64 + (p & 7) * 8 + (j0 & 7);
+  uint2 u;
+  u.x = pack_bf16x2(v[0], v[1]);
+  u.y = pack_bf16x2(v[2], v[3]);
+  *reinterpret_cast<uint2*>(posb + off) = u;
 }
 
 }  // namespace

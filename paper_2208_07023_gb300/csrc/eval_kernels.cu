@@ -531,6 +531,40 @@ __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes
   return bi;
 }
 
+// Eq. pso-1 for features 4q..4q+3 of particle pi of node a, to iteration t+1:
+// v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v. pbp: the
+// node's pbest rows, gsrc: gB. With sw.posb the new positions are also
+// written as bfloat16 MMA operands.
+__device__ __forceinline__ void move_item(const Problem& pr, const Swarm& sw, const SwarmCoef& co,
+                                          uint32_t uid, int a, int t, int pi, int q,
+                                          const float* pbp, const float* gsrc) {
+  const int d = pr.d, Pp = pr.Pp;
+  const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
+  const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
+                              (uint32_t)q | (kR1 << 24), k0, k1);
+  const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
+                              (uint32_t)q | (kR2 << 24), k0, k1);
+  const int64_t row = (int64_t)pi * d;
+  float* pos = sw.pos + (int64_t)a * Pp * d + row;
+  float* vel = sw.vel + (int64_t)a * Pp * d + row;
+  float xn[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = 4 * q + c;
+    if (j >= d) break;
+    const float x = pos[j], v = vel[j];
+    const float inertia = __fmul_rn(co.inertia, v);
+    const float cog =
+        __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(pbp[row + j], x));
+    const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])), __fsub_rn(gsrc[j], x));
+    const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
+    vel[j] = vn;
+    xn[c] = __fadd_rn(x, vn);
+    pos[j] = xn[c];
+  }
+  if (sw.posb) store_posb4(sw.posb, Pp, pr.dp, a, pi, 4 * q, xn);
+}
+
 // Algorithm 1's gbest step after evaluation t, then (t < T) the synchronous
 // move of Eq. pso-1: every particle moves with the gbest held at the end of
 // iteration t. Grid: (node, slice of the node's particle x 4-dimension
@@ -580,59 +614,93 @@ __global__ void __launch_bounds__(128)
     for (int j = threadIdx.x; j < d; j += blockDim.x) gbp[j] = gsrc[j];
   if (t >= sw.T) return;
   const uint32_t uid = nodes[a].uid;
-  const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
   for (int item = blockIdx.y * blockDim.x + threadIdx.x; item < pr.P * d4;
-       item += gridDim.y * blockDim.x) {
-    const int pi = item / d4, q = item - pi * d4;
-    const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
-                                (uint32_t)q | (kR1 << 24), k0, k1);
-    const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
-                                (uint32_t)q | (kR2 << 24), k0, k1);
-    const int64_t row = (int64_t)pi * d;
-    float* pos = sw.pos + (int64_t)a * Pp * d + row;
-    float* vel = sw.vel + (int64_t)a * Pp * d + row;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = 4 * q + c;
-      if (j >= d) break;
-      // v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v
-      const float x = pos[j], v = vel[j];
-      const float inertia = __fmul_rn(co.inertia, v);
-      const float cog =
-          __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(pbp[row + j], x));
-      const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])), __fsub_rn(gsrc[j], x));
-      const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
-      vel[j] = vn;
-      pos[j] = __fadd_rn(x, vn);
+       item += gridDim.y * blockDim.x)
+    move_item(pr, sw, co, uid, a, t, item / d4, item % d4, pbp, gsrc);
+}
+
+// ---- top-k selection (SLM_PROJ_BF16_TOPK) ------------------------------------------
+
+// The whole CTA selects node a's tk_k best particles by sw.cur (ties to the
+// lower index; rank = particles strictly better, or equal and lower) and
+// gathers their positions. scratch: P EvalRes + 2 P ints of shared memory.
+__device__ __noinline__ void topk_select(const Problem& pr, const Swarm& sw, int a,
+                                         unsigned char* scratch) {
+  EvalRes* s_sc = reinterpret_cast<EvalRes*>(scratch);
+  int* s_take = reinterpret_cast<int*>(s_sc + pr.P);
+  int* s_sel = s_take + pr.P;
+  const int P = pr.P, Pp = pr.Pp, d = pr.d, k = sw.tk_k, kp = sw.tk_kp;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) s_sc[p] = ldcg_res(sw.cur + (int64_t)a * Pp + p);
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const EvalRes me = s_sc[p];
+    int rank = 0;
+    for (int q = 0; q < P; ++q) {
+      if (q == p) continue;
+      const EvalRes o = s_sc[q];
+      if (better(o, me, pr.crit) || (q < p && !better(me, o, pr.crit))) ++rank;
     }
+    s_take[p] = rank < k;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < Pp; p += blockDim.x) {
+    int q = -1;
+    if (p < P && s_take[p]) {
+      q = 0;
+      for (int j = 0; j < p; ++j) q += s_take[j];
+      s_sel[q] = p;
+      sw.tk_sel[(int64_t)a * k + q] = p;
+    }
+    sw.tk_inv[(int64_t)a * Pp + p] = q;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kp * d; e += blockDim.x) {
+    const int q = e / d, j = e - q * d;
+    sw.tk_pos[((int64_t)a * kp + q) * d + j] =
+        q < k ? sw.pos[((int64_t)a * Pp + s_sel[q]) * d + j] : 0.0f;
   }
 }
 
 // ---- histogram and scan -------------------------------------------------------------
 
-constexpr int kPiece = 4096;     // entries per staged piece (bulk copies carry a fixed cost)
-constexpr int kPieceMse = 2048;  // MSE pieces also carry two 8-byte moments per entry
 constexpr int kCopies = 4;  // histogram copies, each shared by a pair of warps
-constexpr int kStages = 2;  // staged pieces in flight
+constexpr int kStages = 2;  // staged pieces: one in flight while one is binned
+constexpr int kMseMaxPiece = 2048;  // largest MSE piece (8 entries per thread)
 
 __host__ __device__ inline size_t hist_copy_bytes(int crit, int B, int K) {
   return crit == SLM_MSE ? (size_t)B * (4 + 8 + 8) : (size_t)B * K * 4;
 }
-__host__ __device__ inline int piece_of(int crit) { return crit == SLM_MSE ? kPieceMse : kPiece; }
-// One staged piece: z of the particle; labels (classification) or the two
-// fixed-point moments (MSE); multiplicities.
+// Histogram copies: kCopies shared by warp pairs (classification); one for
+// MSE, whose bins are summed by their owner threads after a counting sort.
+__host__ __device__ inline int hist_copies(int crit) { return crit == SLM_MSE ? 1 : kCopies; }
+// MSE counting-sort scratch: per-bin counts and offsets, the sorted piece.
+__host__ __device__ inline size_t sort_bytes(int crit, int B) {
+  return crit == SLM_MSE ? (((size_t)(2 * B + 1) * 4 + (size_t)kMseMaxPiece * 2 + 127) & ~(size_t)127)
+                         : 0;
+}
+// Bytes one entry occupies in a stage: z of the particle; the label
+// (classification) or the two fixed-point moments (MSE); the multiplicity.
+__host__ __device__ inline int entry_bytes(int crit, bool weighted) {
+  return (crit == SLM_MSE ? 4 + 8 + 8 : 4 + 4) + (weighted ? 4 : 0);
+}
+// Entries per staged piece: large pieces (each piece carries fixed costs),
+// sized so the stages of two CTAs fit on an SM; a multiple of 256 entries.
+__host__ __device__ inline int piece_of(int crit, bool weighted) {
+  const int budget = crit == SLM_MSE ? 80 * 1024 : 64 * 1024 + (weighted ? 32 * 1024 : 0);
+  return budget / (kStages * entry_bytes(crit, weighted)) / 256 * 256;
+}
 __host__ __device__ inline size_t stage_bytes(int crit, bool weighted) {
-  const size_t per = crit == SLM_MSE ? 4 + 8 + 8 : 4 + 4;
-  return (size_t)piece_of(crit) * (per + (weighted ? 4 : 0));
+  return (size_t)piece_of(crit, weighted) * entry_bytes(crit, weighted);
 }
 
 // A cluster of S CTAs per (node, particle). Rank r streams the r-th of S
-// slices of the node's entries through shared memory in kPiece-entry pieces:
-// one thread issues bulk (TMA) copies of the particle's z, the labels /
-// targets and the multiplicities of a piece into a ring of kStages stages,
-// each with its own mbarrier; warp w bins its share of each piece into
-// histogram copy w % kCopies. The
-// copies are merged, rank 0 adds the other ranks' histograms through
+// slices of the node's entries through shared memory in pieces: one thread
+// issues bulk (TMA) copies of the particle's z, the labels or fixed-point
+// moments and the multiplicities of a piece into a ring of kStages stages,
+// each with its own mbarrier. Classification: warp w adds its share of a
+// piece into histogram copy w % kCopies with shared atomics. MSE: a counting
+// sort of the piece by bin, then thread b sums bin b's moments in registers.
+// The copies are merged, rank 0 adds the other ranks' histograms through
 // distributed shared memory and the whole CTA scans the B-1 edges. In a
 // search (do_update) rank 0 also takes the particle's pbest step; the gbest
 // step and the move follow in k_move.
@@ -652,25 +720,28 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int rank = (int)cl.block_rank();
   const int a = blockIdx.x / S;
   const int p = blockIdx.y;
-  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const NodeDesc nd = nodes[a];
   const int B = pr.B, K = pr.K;
   const bool mse = pr.crit == SLM_MSE;
   const bool weighted = pr.w != nullptr;
   const int words = mse ? B : B * K;  // u32 counters per copy
-  const int piece = piece_of(pr.crit);
-  // shared memory: kCopies histogram copies, then two stages. MSE bins hold
-  // the weight and the fixed-point sums of w (y-c) and w (y-c)^2.
-  unsigned long long* hs = reinterpret_cast<unsigned long long*>(smem);  // MSE [kCopies][B]
-  unsigned long long* hq = hs + (mse ? kCopies * B : 0);                  // MSE [kCopies][B]
-  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? kCopies * B : 0));  // [kCopies][words]
-  unsigned char* stage0 =
-      smem + ((hist_copy_bytes(pr.crit, B, K) * kCopies + 127) & ~(size_t)127);
+  const int piece = piece_of(pr.crit, weighted);
+  // shared memory: the histogram copies, the MSE sort scratch, two stages.
+  // MSE bins hold the weight and the fixed-point sums of w (y-c) and w (y-c)^2.
+  const int ncopies = hist_copies(pr.crit);
+  unsigned long long* hs = reinterpret_cast<unsigned long long*>(smem);  // MSE [B]
+  unsigned long long* hq = hs + (mse ? B : 0);                            // MSE [B]
+  uint32_t* hc = reinterpret_cast<uint32_t*>(hq + (mse ? B : 0));  // [ncopies][words]
+  unsigned char* sort0 =
+      smem + ((hist_copy_bytes(pr.crit, B, K) * ncopies + 127) & ~(size_t)127);
+  uint32_t* pcnt = reinterpret_cast<uint32_t*>(sort0);  // MSE [B] entries per bin of a piece
+  uint32_t* poff = pcnt + B;                            // MSE [B + 1] their offsets
+  uint16_t* sorted = reinterpret_cast<uint16_t*>(poff + B + 1);  // MSE [piece]
+  unsigned char* stage0 = sort0 + sort_bytes(pr.crit, B);
   const size_t sbytes = stage_bytes(pr.crit, weighted);
-  const int copy = warp % kCopies;
+  const int copy = warp % ncopies;
   uint32_t* h = hc + copy * words;
-  unsigned long long* hsw = hs + copy * B;
-  unsigned long long* hqw = hq + copy * B;
 
   int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
   if (threadIdx.x == 0) {
@@ -689,11 +760,12 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int i = 0; i < kStages; ++i) mbar_init(&s_bar[i], 1);
     mbar_init_fence();
   }
-  for (int i = threadIdx.x; i < kCopies * words; i += kThreads) hc[i] = 0u;
+  for (int i = threadIdx.x; i < ncopies * words; i += kThreads) hc[i] = 0u;
   if (mse)
-    for (int i = threadIdx.x; i < kCopies * B; i += kThreads) {
+    for (int i = threadIdx.x; i < B; i += kThreads) {
       hs[i] = 0ull;
       hq[i] = 0ull;
+      pcnt[i] = 0u;
     }
   __syncthreads();
   const bool ok = s_ok;
@@ -725,6 +797,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     if (weighted) bulk_g2s(st + off_w, pr.w + e0 + r, bytes, bar);
   };
+  unsigned long long acc1 = 0ull, acc2 = 0ull;  // MSE: bin threadIdx.x of this slice
+  uint32_t accw = 0u;
   if (threadIdx.x == 0)
     for (int k = 0; k < kStages - 1 && k < n_pieces; ++k) issue(k);
   for (int k = 0; k < n_pieces; ++k) {
@@ -750,38 +824,86 @@ __global__ void __launch_bounds__(kThreads, 3)
     const unsigned long long* m2s =
         reinterpret_cast<const unsigned long long*>(st + (size_t)piece * 12);
     const uint32_t* ws = reinterpret_cast<const uint32_t*>(st + off_w);
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-      const int b = bin_of(zs[i], zmin, inv_w, B);
-      const uint32_t w = weighted ? ws[i] : 1u;
-      if (mse) {
-        atomicAdd(&h[b], w);
-        atomicAdd(&hsw[b], m1s[i]);  // two's complement: signed sums wrap exactly
-        atomicAdd(&hqw[b], m2s[i]);
-      } else {
-        atomicAdd(&h[b * K + ls[i]], w);
+    if (mse) {
+      // counting sort of the piece by bin (slot = arrival order in the bin),
+      // then thread b sums bin b's moments in registers: no 64-bit atomics
+      int bb[kMseMaxPiece / kThreads], sl[kMseMaxPiece / kThreads];
+#pragma unroll
+      for (int u = 0; u < kMseMaxPiece / kThreads; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        bb[u] = -1;
+        if (i < n) {
+          const int b = bin_of(zs[i], zmin, inv_w, B);
+          bb[u] = b;
+          sl[u] = (int)atomicAdd(&pcnt[b], 1u);
+          if (bins_out) bins_out[(int64_t)p * nd.seg_len + r + i] = b;
+        }
       }
-      if (bins_out) bins_out[(int64_t)p * nd.seg_len + r + i] = b;
+      __syncthreads();
+      if (warp == 0) {  // exclusive prefix of the counts
+        const int bpl = (B + 31) >> 5;
+        uint32_t sum = 0;
+        for (int q = 0; q < bpl; ++q) {
+          const int j = lane * bpl + q;
+          if (j < B) sum += pcnt[j];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, inc, off);
+          if (lane >= off) inc += v;
+        }
+        uint32_t run = inc - sum;
+        for (int q = 0; q < bpl; ++q) {
+          const int j = lane * bpl + q;
+          if (j < B) {
+            poff[j] = run;
+            run += pcnt[j];
+          }
+        }
+        if (lane == 31) poff[B] = inc;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kMseMaxPiece / kThreads; ++u)
+        if (bb[u] >= 0) sorted[poff[bb[u]] + sl[u]] = (uint16_t)(threadIdx.x + u * kThreads);
+      __syncthreads();
+      if ((int)threadIdx.x < B) {
+        const int b = threadIdx.x;
+        const int j1 = (int)poff[b + 1];
+        for (int j = (int)poff[b]; j < j1; ++j) {
+          const int i = sorted[j];
+          acc1 += m1s[i];  // two's complement: signed sums wrap exactly
+          acc2 += m2s[i];
+          accw += weighted ? ws[i] : 1u;
+        }
+        pcnt[b] = 0u;
+      }
+    } else {
+      for (int i = threadIdx.x; i < n; i += kThreads) {
+        const int b = bin_of(zs[i], zmin, inv_w, B);
+        const uint32_t w = weighted ? ws[i] : 1u;
+        atomicAdd(&h[b * K + ls[i]], w);
+        if (bins_out) bins_out[(int64_t)p * nd.seg_len + r + i] = b;
+      }
     }
     __syncthreads();  // this stage is refilled by piece k + kStages
   }
-  // merge the warp copies into copy 0
-  for (int i = threadIdx.x; i < words; i += kThreads) {
-    uint32_t v = 0;
-#pragma unroll
-    for (int c = 0; c < kCopies; ++c) v += hc[c * words + i];
-    hc[i] = v;
+  if (mse && (int)threadIdx.x < B) {  // the owner threads' bins
+    hc[threadIdx.x] = accw;
+    hs[threadIdx.x] = acc1;
+    hq[threadIdx.x] = acc2;
   }
-  if (mse)
-    for (int i = threadIdx.x; i < B; i += kThreads) {
-      unsigned long long vs = 0ull, vq = 0ull;
+  // merge the warp copies into copy 0
+  if (ncopies > 1) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < words; i += kThreads) {
+      uint32_t v = 0;
 #pragma unroll
-      for (int c = 0; c < kCopies; ++c) {
-        vs += hs[c * B + i];
-        vq += hq[c * B + i];
-      }
-      hs[i] = vs;
-      hq[i] = vq;
+      for (int c = 0; c < kCopies; ++c) v += hc[c * words + i];
+      hc[i] = v;
     }
+  }
   if (S > 1) {
     cl.sync();  // every rank's copy 0 is complete
     if (rank == 0) {
@@ -825,6 +947,19 @@ __global__ void __launch_bounds__(kThreads, 3)
     zz[1] = INT_MIN;
   }
   if (do_update && warp == 0) pbest_step(pr, sw, a, p, t, res);
+  if (sw.tk_sel) {
+    // the last particle of the node to be scored selects the node's top k
+    __shared__ int s_last;
+    __threadfence();  // this CTA's score write before the count
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&sw.done[a], 1) == pr.P - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      topk_select(pr, sw, a, stage0);  // the stages are free by now
+      if (threadIdx.x == 0) sw.done[a] = 0;
+    }
+  }
 }
 
 // Initial swarm of each node: x ~ U[-1,1)^d, v ~ 0.1 U[-1,1)^d.
@@ -866,6 +1001,17 @@ __global__ void k_swarm_init(Problem pr, Swarm sw,
     int* z = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
     z[0] = INT_MAX;
     z[1] = INT_MIN;
+  }
+  if (sw.posb) {  // the positions as bfloat16 MMA operands, padding zero
+    __syncthreads();
+    const int dp4 = pr.dp >> 2;
+    for (int e = threadIdx.x; e < pr.Pp * dp4; e += blockDim.x) {
+      const int p = e / dp4, j0 = 4 * (e - p * dp4);
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = j0 + c < d ? pos[(int64_t)p * d + j0 + c] : 0.0f;
+      store_posb4(sw.posb, pr.Pp, pr.dp, a, p, j0, v);
+    }
   }
   if (threadIdx.x == 0) {
     sw.gb[a] = invalid_res();
@@ -1010,8 +1156,9 @@ cudaError_t launch_mse_moments(const Problem& pr, const WorkTile* tiles, int n_t
 }
 
 static size_t hist_smem_bytes(const Problem& pr) {
-  const size_t hist = (hist_copy_bytes(pr.crit, pr.B, pr.K) * kCopies + 127) & ~(size_t)127;
-  return hist + kStages * stage_bytes(pr.crit, pr.w != nullptr);
+  const size_t hist =
+      (hist_copy_bytes(pr.crit, pr.B, pr.K) * hist_copies(pr.crit) + 127) & ~(size_t)127;
+  return hist + sort_bytes(pr.crit, pr.B) + kStages * stage_bytes(pr.crit, pr.w != nullptr);
 }
 
 cudaError_t prepare_eval_kernels(const Problem& pr) {
@@ -1067,7 +1214,7 @@ int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_clus
   const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * n_sm;
   int S = 1;
   while (2 * S <= max_cluster && (int64_t)A * pr.P * (2 * S) <= resident &&
-         max_len / (2 * S) >= piece_of(pr.crit))
+         max_len / (2 * S) >= piece_of(pr.crit, pr.w != nullptr))
     S *= 2;
   return S;
 }

@@ -13,10 +13,11 @@
 // per level, directly into the operand layout, so a tile chunk is one
 // contiguous copy; the positions are converted once per iteration.
 //
-// Then, per node, the k particles with the best such score are re-scored on
-// the FP32 projection (the k_project / k_hist_scan path) and k_merge writes
-// their scores over the reduced ones, takes every particle's pbest step and
-// the gbest step among the re-scored particles (Algorithm 1).
+// Then, per node, the k particles with the best such score (selected by the
+// last histogram CTA of the node) are re-scored on the FP32 projection (the
+// k_project / k_hist_scan path) and k_merge writes their scores over the
+// reduced ones, takes every particle's pbest step and the gbest step among
+// the re-scored particles (Algorithm 1).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <limits.h>
@@ -95,11 +96,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
 // ---- operand layout ----------------------------------------------------------------
 
 // One thread per 16 bytes of output, in output order: block b of R rows,
@@ -148,9 +144,8 @@ __host__ __device__ inline uint32_t mma_tmem_cols(int Pp) {
 // free[s] (stage reusable) and, after the tile's last chunk, to acc[u & 1]:
 // the accumulator is double-buffered in tensor memory, so the MMAs of tile
 // u+1 run while the four warps read tile u back. The positions of a node are
-// staged once per node. Each lane keeps a running range of the columns
-// c = lane (mod 32) over the warp's rows, folded into shared and global
-// memory once per node.
+// staged once per node. Each warp keeps a running range per column in shared
+// memory, folded into global memory once per node.
 __global__ void __launch_bounds__(kMmaThreads)
     k_project_mma(Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, int n_tiles,
                   const uint16_t* __restrict__ posb) {
@@ -158,7 +153,7 @@ __global__ void __launch_bounds__(kMmaThreads)
   __shared__ __align__(8) uint64_t bar_full[2], bar_free[2], bar_acc[2], bar_b;
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
-  __shared__ int s_lo[kMaxParticles], s_hi[kMaxParticles];
+  __shared__ int s_lo[kMmaThreads / 32][kMaxParticles], s_hi[kMmaThreads / 32][kMaxParticles];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int P = pr.P, Pp = pr.Pp, dp = pr.dp;
   const uint32_t stage = mma_stage_bytes(dp);
@@ -183,9 +178,9 @@ __global__ void __launch_bounds__(kMmaThreads)
     mbar_init_fence();
     s_err = 0;
   }
-  for (int p = tid; p < Pp; p += kMmaThreads) {
-    s_lo[p] = INT_MAX;
-    s_hi[p] = INT_MIN;
+  for (int p = lane; p < Pp; p += 32) {  // each warp its own running range
+    s_lo[warp][p] = INT_MAX;
+    s_hi[warp][p] = INT_MIN;
   }
   tc_fence_before();
   __syncthreads();
@@ -250,14 +245,6 @@ __global__ void __launch_bounds__(kMmaThreads)
     mma_commit(&bar_acc[ti & 1]);
   };
 
-  // running range of the warp's rows: lane l owns columns 32 q + l
-  int run_lo[kMaxParticles / 32], run_hi[kMaxParticles / 32];
-#pragma unroll
-  for (int q = 0; q < kMaxParticles / 32; ++q) {
-    run_lo[q] = INT_MAX;
-    run_hi[q] = INT_MIN;
-  }
-
   if (tid == 0 && n_items > 0) {
     issue(0);
     mma_tile(0);
@@ -273,48 +260,46 @@ __global__ void __launch_bounds__(kMmaThreads)
     const bool rv = r < wt.rows;
     float* zrow = sw.z + wt.row0 + r;
     const uint32_t t_row = tmem + (uint32_t)(ti & 1) * cols + ((uint32_t)(warp * 32) << 16);
+    for (int cb = 0; cb < Pp / 16; ++cb) {
+      uint32_t v[16];
+      tmem_ld16(t_row + (uint32_t)(cb * 16), v);
+      int my_lo = INT_MAX, my_hi = INT_MIN;  // lane j < 16: column cb*16 + j
 #pragma unroll
-    for (int cb = 0; cb < kMaxParticles / 16; ++cb) {
-      if (cb * 16 < Pp) {
-        uint32_t v[16];
-        tmem_ld16(t_row + (uint32_t)(cb * 16), v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int p = cb * 16 + j;
-          const float z = __uint_as_float(v[j]);
-          const int oz = f2ord(z);
-          const int lo = __reduce_min_sync(0xffffffffu, rv ? oz : INT_MAX);
-          const int hi = __reduce_max_sync(0xffffffffu, rv ? oz : INT_MIN);
-          if (rv && p < P) zrow[(int64_t)p * pr.Ez] = z;
-          const bool mine = lane == (p & 31);
-          run_lo[p >> 5] = mine ? min(run_lo[p >> 5], lo) : run_lo[p >> 5];
-          run_hi[p >> 5] = mine ? max(run_hi[p >> 5], hi) : run_hi[p >> 5];
-        }
+      for (int j = 0; j < 16; ++j) {
+        const int p = cb * 16 + j;
+        const float z = __uint_as_float(v[j]);
+        const int oz = f2ord(z);
+        const int lo = __reduce_min_sync(0xffffffffu, rv ? oz : INT_MAX);
+        const int hi = __reduce_max_sync(0xffffffffu, rv ? oz : INT_MIN);
+        if (rv && p < P) zrow[(int64_t)p * pr.Ez] = z;
+        my_lo = lane == j ? lo : my_lo;
+        my_hi = lane == j ? hi : my_hi;
+      }
+      if (lane < 16) {
+        const int p = cb * 16 + lane;
+        s_lo[warp][p] = min(s_lo[warp][p], my_lo);
+        s_hi[warp][p] = max(s_hi[warp][p], my_hi);
       }
     }
     tc_fence_before();
     const bool last_of_node = ti + 1 == my_tiles || tile_of(ti + 1).node != wt.node;
     if (last_of_node) {
-      // fold the warps' ranges of this node, then publish them
-#pragma unroll
-      for (int q = 0; q < kMaxParticles / 32; ++q) {
-        const int p = q * 32 + lane;
-        if (p < P && run_lo[q] != INT_MAX) {
-          atomicMin(&s_lo[p], run_lo[q]);
-          atomicMax(&s_hi[p], run_hi[q]);
-        }
-        run_lo[q] = INT_MAX;
-        run_hi[q] = INT_MIN;
-      }
+      // fold the warps' ranges of this node and publish them
       __syncthreads();
       for (int p = tid; p < P; p += kMmaThreads) {
-        if (s_lo[p] != INT_MAX) {
-          int* zz = sw.zmm + ((int64_t)wt.node * Pp + p) * 2;
-          atomicMin(zz, s_lo[p]);
-          atomicMax(zz + 1, s_hi[p]);
+        int lo = INT_MAX, hi = INT_MIN;
+#pragma unroll
+        for (int w = 0; w < kMmaThreads / 32; ++w) {
+          lo = min(lo, s_lo[w][p]);
+          hi = max(hi, s_hi[w][p]);
+          s_lo[w][p] = INT_MAX;
+          s_hi[w][p] = INT_MIN;
         }
-        s_lo[p] = INT_MAX;
-        s_hi[p] = INT_MIN;
+        if (lo != INT_MAX) {
+          int* zz = sw.zmm + ((int64_t)wt.node * Pp + p) * 2;
+          atomicMin(zz, lo);
+          atomicMax(zz + 1, hi);
+        }
       }
     }
     __syncthreads();  // accumulator ti & 1 and the range slots free again
@@ -326,48 +311,7 @@ __global__ void __launch_bounds__(kMmaThreads)
   if (tid == 0 && s_err && sw.err) atomicExch(sw.err, 4);
 }
 
-// ---- top-k selection and merge ---------------------------------------------------------
-
-__global__ void __launch_bounds__(256)
-    k_topk(Problem pr, Swarm sw, int k, int kp, int32_t* __restrict__ sel,
-           int32_t* __restrict__ inv, float* __restrict__ posk) {
-  __shared__ EvalRes s_sc[kMaxParticles];
-  __shared__ int s_take[kMaxParticles];
-  __shared__ int s_sel[kMaxParticles];
-  pdl_trigger();
-  pdl_wait();
-  const int a = blockIdx.x, P = pr.P, Pp = pr.Pp, d = pr.d;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s_sc[p] = sw.cur[(int64_t)a * Pp + p];
-  __syncthreads();
-  // rank = particles ordered before p: strictly better, or equal and lower
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const EvalRes me = s_sc[p];
-    int rank = 0;
-    for (int q = 0; q < P; ++q) {
-      if (q == p) continue;
-      const EvalRes o = s_sc[q];
-      if (better(o, me, pr.crit) || (q < p && !better(me, o, pr.crit))) ++rank;
-    }
-    s_take[p] = rank < k;
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < Pp; p += blockDim.x) {
-    int q = -1;
-    if (p < P && s_take[p]) {
-      q = 0;
-      for (int j = 0; j < p; ++j) q += s_take[j];
-      s_sel[q] = p;
-      sel[(int64_t)a * k + q] = p;
-    }
-    inv[(int64_t)a * Pp + p] = q;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kp * d; e += blockDim.x) {
-    const int q = e / d, j = e - q * d;
-    posk[((int64_t)a * kp + q) * d + j] =
-        q < k ? sw.pos[((int64_t)a * Pp + s_sel[q]) * d + j] : 0.0f;
-  }
-}
+// ---- merge of the re-scored particles ----------------------------------------------------
 
 // Grid (node, group of 8 particles): warp w of block y merges particle
 // 8 y + w and takes its pbest step; block y = 0 also takes the node's gbest
@@ -482,12 +426,21 @@ cudaError_t prepare_mma_kernels(const Problem& pr) {
 }
 
 int mma_grid_cap(const Problem& pr, int n_sm) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_mma, kMmaThreads,
-                                                    mma_smem_bytes(pr)) != cudaSuccess) {
+  // resident CTAs per SM from the kernel's own limits: shared memory (static,
+  // dynamic and the per-block reservation), tensor memory, 16 blocks
+  cudaFuncAttributes fa;
+  int dev = 0, per_sm_smem = 0, reserved = 0;
+  if (cudaFuncGetAttributes(&fa, k_project_mma) != cudaSuccess || cudaGetDevice(&dev) ||
+      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) {
     cudaGetLastError();
     return 0;
   }
+  const size_t per_cta = mma_smem_bytes(pr) + fa.sharedSizeBytes + (size_t)reserved;
+  int per_sm = (int)((size_t)per_sm_smem / per_cta);
+  per_sm = per_sm < (int)(512u / (2 * mma_tmem_cols(pr.Pp))) ? per_sm
+                                                             : (int)(512u / (2 * mma_tmem_cols(pr.Pp)));
+  per_sm = per_sm < 16 ? per_sm : 16;
   return per_sm * n_sm;
 }
 
@@ -507,21 +460,6 @@ cudaError_t launch_project_mma(const Problem& pr, const Swarm& sw, const WorkTil
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_project_mma, pr, sw, tiles, n_tiles, posb);
-}
-
-cudaError_t launch_topk(const Problem& pr, const Swarm& sw, int A, int k, int kp, int32_t* sel,
-                        int32_t* inv, float* posk, cudaStream_t st) {
-  if (A <= 0) return cudaSuccess;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)A, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_topk, pr, sw, k, kp, sel, inv, posk);
 }
 
 cudaError_t launch_merge(const Problem& pr, const Swarm& sw, int A, const EvalRes* cur2, int kp,

@@ -343,6 +343,7 @@ slm_status setup_swarm(slm_ctx* c, Problem& pr, int A, int T, bool want_trace,
   CK(ensure(c->ws[S_GPART], sizeof(int32_t) * (size_t)A));
   CK(ensure(c->ws[S_GITER], sizeof(int32_t) * (size_t)A));
   CK(ensure(c->ws[S_DONE], sizeof(int32_t) * (size_t)A));
+  CK(cudaMemsetAsync(c->ws[S_DONE].p, 0, sizeof(int32_t) * (size_t)A, c->stream));
   if (want_trace) CK(ensure(c->ws[S_TRACE], sizeof(double) * (size_t)A * (T + 1)));
   s.pos = ws_ptr<float>(c, S_POS);
   s.vel = ws_ptr<float>(c, S_VEL);
@@ -424,24 +425,37 @@ slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>
     }
     CK(cudaMemcpyAsync(c->ws[S_ZMM2].p, zinit.data(), sizeof(int32_t) * zinit.size(),
                        cudaMemcpyHostToDevice, c->stream));
+    CK(ensure(c->ws[S_DONE], sizeof(int32_t) * (size_t)A));
+    CK(cudaMemsetAsync(c->ws[S_DONE].p, 0, sizeof(int32_t) * (size_t)A, c->stream));
     b.sel = ws_ptr<int32_t>(c, S_SEL);
     b.inv = ws_ptr<int32_t>(c, S_INV);
     b.pr_k = pr;
     b.pr_k.P = k;
     b.pr_k.Pp = b.kp;
     b.pr_k.G = b.kp % 16 == 0 ? b.kp / 16 : b.kp / 8;
+    // the re-scoring pass: compact positions, its own z, ranges and scores
     b.sw_k = *sw;
     b.sw_k.pos = ws_ptr<float>(c, S_POSK);
     b.sw_k.z = ws_ptr<float>(c, S_Z2);
     b.sw_k.zmm = ws_ptr<int32_t>(c, S_ZMM2);
     b.sw_k.cur = ws_ptr<EvalRes>(c, S_CUR2);
     b.sw_k.sel = nullptr;
+    b.sw_k.tk_sel = nullptr;
+    b.sw_k.posb = nullptr;
     b.S_k = batch_split(c, b.pr_k, nodes);
+    // the reduced pass's histogram kernel selects each node's top k
+    sw->done = ws_ptr<int32_t>(c, S_DONE);
+    sw->tk_sel = b.sel;
+    sw->tk_inv = b.inv;
+    sw->tk_pos = ws_ptr<float>(c, S_POSK);
+    sw->tk_k = k;
+    sw->tk_kp = b.kp;
     if (search) {
       sw->sel = b.sel;
       sw->k = k;
     }
   }
+  if (search) sw->posb = b.posb;  // written by the swarm kernels
   *plan = b;
   return SLM_OK;
 }
@@ -459,10 +473,11 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
   if (bp && bp->on) {
     // bfloat16 scores of every particle on the tensor cores
     const Bf16Plan& b = *bp;
-    CK(launch(c, SLM_K_TOPK, 0.0, [&] {
-      return launch_to_mma_layout(sw.pos, (int64_t)A * pr.Pp, pr.d, pr.dp, pr.Pp, A, b.posb,
-                                  c->stream);
-    }));
+    if (!co)  // a search's positions are converted by its swarm kernels
+      CK(launch(c, SLM_K_TOPK, 0.0, [&] {
+        return launch_to_mma_layout(sw.pos, (int64_t)A * pr.Pp, pr.d, pr.dp, pr.Pp, A, b.posb,
+                                    c->stream);
+      }));
     if (b.n_mtiles)
       CK(launch(c, SLM_K_PROJECT_MMA, pairs, [&] {
         return launch_project_mma(pr, sw, ws_ptr<WorkTile>(c, S_MTILES), b.n_mtiles, b.posb,
@@ -472,10 +487,8 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
       return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, 0, c->stream);
     }));
     if (b.k > 0) {
-      // FP32 re-scores of the k best of each node replace theirs
-      CK(launch(c, SLM_K_TOPK, 0.0, [&] {
-        return launch_topk(pr, sw, A, b.k, b.kp, b.sel, b.inv, b.sw_k.pos, c->stream);
-      }));
+      // FP32 re-scores of the k best of each node (selected by the last
+      // histogram CTA of the node) replace theirs
       if (n_tiles)
         CK(launch(c, SLM_K_PROJECT, b.pairs_k, [&] {
           return launch_project(b.pr_k, b.sw_k, dt, n_tiles, cap, c->stream);

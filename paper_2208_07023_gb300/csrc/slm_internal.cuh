@@ -111,6 +111,17 @@ struct Swarm {
   // increasing order; non-null when the gbest step runs in k_merge
   const int32_t* sel;
   int32_t k;
+  // SLM_PROJ_BF16_TOPK, histogram of the reduced pass: when tk_sel is set,
+  // the last CTA to score a node (counter done[a], left at 0) selects its
+  // tk_k best particles into tk_sel[A, tk_k] (increasing order), tk_inv[A, Pp]
+  // (rank in tk_sel or -1) and their positions into tk_pos[A, tk_kp, d]
+  int32_t* tk_sel;
+  int32_t* tk_inv;
+  float* tk_pos;
+  int32_t tk_k, tk_kp;
+  // when set, the swarm kernels also write the positions as bfloat16 MMA
+  // operands: posb[A, Pp * dp] (layout of launch_to_mma_layout, R = Pp)
+  uint16_t* posb;
 };
 
 struct SwarmCoef {
@@ -157,11 +168,6 @@ cudaError_t prepare_mma_kernels(const Problem& pr);
 cudaError_t launch_project_mma(const Problem& pr, const Swarm& sw, const WorkTile* tiles,
                                int n_tiles, const uint16_t* posb, int grid,
                                cudaStream_t st);
-// Per node: the k particles with the best scores in sw.cur (ties to the lower
-// index), in increasing order, into sel[A, k]; inv[A, Pp] = rank in sel or -1;
-// their positions into posk[A, kp, d] (rows k..kp-1 zero).
-cudaError_t launch_topk(const Problem& pr, const Swarm& sw, int A, int k, int kp,
-                        int32_t* sel, int32_t* inv, float* posk, cudaStream_t st);
 // Writes the re-scored particles' scores cur2[A, kp] over sw.cur; with
 // do_update, the pbest step of every particle and the gbest step of
 // iteration t among the re-scored particles (Algorithm 1).
