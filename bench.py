@@ -462,6 +462,24 @@ def run_ours(args):
     return 0
 
 
+def run_ncu_case(args):
+    """The small case for full ncu captures of the scoring kernels: one search
+    of the workload's root node with 3 iterations, a handful of launches."""
+    import torch
+
+    from paper_2208_07023_gb300 import binding as S
+    cfg = W.SETTINGS[args.workload]
+    wl = cfg["builder"](1)
+    ctx = S.Context(0, torch.cuda.current_stream().cuda_stream)
+    p = make_params(S, cfg, wl, args.proj, args.topk)
+    p.n_iters = 3
+    r = ctx.node_split(p, wl.X, labels=wl.labels, y=wl.y)
+    print(json.dumps({"ncu_case": args.workload, "proj": args.proj, "loss": r["loss"],
+                      "bin": r["bin"]}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -473,11 +491,15 @@ def main():
     ap.add_argument("--topk", type=int, default=8)
     ap.add_argument("--compare-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="one root-node search with 3 iterations (small case for ncu)")
     args = ap.parse_args()
     if args.proj is None:
         args.proj = W.SETTINGS[args.workload].get("proj", "fp32")
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return run_ncu_case(args)
     return run_ours(args)
 
 
