@@ -63,6 +63,17 @@ class Split(C.Structure):
     ]
 
 
+class _Mlp(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+MLP_D, MLP_K, MLP_H, MLP_P = 256, 20, 512, 64
+MLP_IN, MLP_OUT = MLP_D * (MLP_K + 1), MLP_D + MLP_P
+MLP_SHAPES = {"W1": (MLP_IN, MLP_H), "b1": (MLP_H,), "W2": (MLP_H, MLP_H), "b2": (MLP_H,),
+              "W3": (MLP_H, MLP_OUT), "b3": (MLP_OUT,)}
+PURPOSE_SEED = 6
+
+
 class _Tree(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in (
         "kind", "dir", "zmin", "inv_w", "bin", "leaf_class", "leaf_value",
@@ -109,6 +120,21 @@ def lib():
                                          C.c_void_p, C.c_int64, C.c_void_p, P(Eval)]
             L.ora_score_bins.restype = C.c_int
             L.ora_bf16_round.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+            L.ora_node_stats.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                         C.c_void_p]
+            L.ora_node_stats.restype = C.c_int
+            L.ora_mlp_forward.argtypes = [P(_Mlp), C.c_void_p, C.c_int32, C.c_int32,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
+            L.ora_mlp_forward.restype = C.c_int
+            L.ora_mlp_loss_grad.argtypes = [P(_Mlp), C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_int32, C.c_int32, P(C.c_double)] + \
+                [C.c_void_p] * 6
+            L.ora_mlp_loss_grad.restype = C.c_int
+            L.ora_adam_step.argtypes = [C.c_void_p] * 4 + [C.c_int64, C.c_int32, C.c_double,
+                                                           C.c_double, C.c_double, C.c_double]
+            L.ora_swarm_seed.argtypes = [C.c_uint64, C.c_uint32, C.c_int32, C.c_int32,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
             L.ora_node_split.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                          C.c_uint32, C.c_void_p, C.c_void_p, P(Split),
@@ -308,3 +334,68 @@ def predict(params: Params, tree: Tree, X):
     if rc:
         raise ValueError(f"ora_predict failed: {rc}")
     return cls, val, leaf
+
+
+# ---- learned swarm proposal ----------------------------------------------------
+
+def node_stats(X, labels=None, n_classes=0, y=None, idx=None, wts=None) -> np.ndarray:
+    """The network input of one node: class-mean offsets and variances."""
+    X, labels, y, idx, wts = _node_arrays(X, labels, y, idx, wts)
+    out = np.zeros(MLP_IN, np.float64)
+    rc = lib().ora_node_stats(_ptr(X), X.shape[1], _ptr(labels), n_classes, _ptr(y),
+                              _ptr(idx), _ptr(wts), idx.size, _ptr(out))
+    if rc:
+        raise ValueError(f"ora_node_stats failed: {rc}")
+    return out
+
+
+def _mlp_struct(m: dict):
+    arrs = {k: np.ascontiguousarray(m[k], dtype=np.float64).reshape(MLP_SHAPES[k])
+            for k in MLP_SHAPES}
+    return _Mlp(*[_ptr(arrs[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]), arrs
+
+
+def mlp_forward(m: dict, s, bf16=True):
+    """Returns (out[n, OUT], h1[n, H], h2[n, H])."""
+    st, keep = _mlp_struct(m)
+    s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, MLP_IN)
+    n = s.shape[0]
+    out = np.empty((n, MLP_OUT)); h1 = np.empty((n, MLP_H)); h2 = np.empty((n, MLP_H))
+    rc = lib().ora_mlp_forward(C.byref(st), _ptr(s), n, 1 if bf16 else 0, _ptr(h1),
+                               _ptr(h2), _ptr(out))
+    if rc:
+        raise ValueError(f"ora_mlp_forward failed: {rc}")
+    return out, h1, h2
+
+
+def mlp_loss_grad(m: dict, s, dims, a, bf16=True):
+    """Mean loss and the gradient of every parameter (dict like m)."""
+    st, keep = _mlp_struct(m)
+    s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, MLP_IN)
+    n = s.shape[0]
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(n, MLP_D)
+    g = {k: np.empty(MLP_SHAPES[k]) for k in MLP_SHAPES}
+    loss = C.c_double()
+    rc = lib().ora_mlp_loss_grad(C.byref(st), _ptr(s), _ptr(dims), _ptr(a), n,
+                                 1 if bf16 else 0, C.byref(loss),
+                                 *[_ptr(g[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    if rc:
+        raise ValueError(f"ora_mlp_loss_grad failed: {rc}")
+    return loss.value, g
+
+
+def adam_step(w, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step on float64 arrays, in place; returns (w, m, v)."""
+    w, m, v = (np.ascontiguousarray(x, dtype=np.float64) for x in (w, m, v))
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().ora_adam_step(_ptr(w), _ptr(m), _ptr(v), _ptr(g), w.size, t, lr, beta1, beta2, eps)
+    return w, m, v
+
+
+def swarm_seed(seed, node_uid, n_particles, d, mu_hat, rho) -> np.ndarray:
+    mu_hat = np.ascontiguousarray(mu_hat, dtype=np.float32)
+    rho = np.ascontiguousarray(rho, dtype=np.float32)
+    pos = np.empty((n_particles, d), np.float32)
+    lib().ora_swarm_seed(seed, node_uid, n_particles, d, _ptr(mu_hat), _ptr(rho), _ptr(pos))
+    return pos

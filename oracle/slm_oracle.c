@@ -973,3 +973,259 @@ int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned swarm proposal: node statistics, a 3-layer network, its loss and  */
+/* gradient, Adam, and the seeded initial swarm. Written from the            */
+/* definitions in slm_oracle.h, in double (the seeding in float).           */
+
+int ora_node_stats(const float* X, int32_t d, const int32_t* labels,
+                   int32_t n_classes, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, double* stats) {
+  const int D = ORA_MLP_D, KM = ORA_MLP_K;
+  if (!X || !idx || !stats || d < 1 || d > D || n_idx < 0) return -1;
+  const int reg = labels == NULL;
+  if (reg ? !y : (n_classes < 2 || n_classes > KM)) return -1;
+  const int K = reg ? 4 : n_classes;
+  for (int i = 0; i < ORA_MLP_IN; ++i) stats[i] = 0.0;
+  float ylo = INFINITY, yhi = -INFINITY;
+  if (reg)
+    for (int64_t s = 0; s < n_idx; ++s) {
+      float v = y[idx[s]];
+      if (v < ylo) ylo = v;
+      if (v > yhi) yhi = v;
+    }
+  double W = 0.0, Wk[ORA_MLP_K];
+  double* sum = (double*)calloc((size_t)d, sizeof(double));
+  double* csum = (double*)calloc((size_t)K * d, sizeof(double));
+  if (!sum || !csum) {
+    free(sum);
+    free(csum);
+    return -2;
+  }
+  for (int k = 0; k < K; ++k) Wk[k] = 0.0;
+  for (int64_t s = 0; s < n_idx; ++s) {
+    const double w = wts ? (double)wts[s] : 1.0;
+    if (w == 0.0) continue;
+    int k;
+    if (reg) {
+      /* quarter of the node's y range, in float, one rounding per operation */
+      k = 0;
+      if (yhi > ylo) {
+        float f = 4.0f * ((y[idx[s]] - ylo) / (yhi - ylo));
+        k = (int)floorf(f);
+        if (k > 3) k = 3;
+        if (k < 0) k = 0;
+      }
+    } else {
+      k = labels[idx[s]];
+    }
+    const float* xs = X + (int64_t)idx[s] * d;
+    W += w;
+    Wk[k] += w;
+    for (int j = 0; j < d; ++j) {
+      sum[j] += w * (double)xs[j];
+      csum[(int64_t)k * d + j] += w * (double)xs[j];
+    }
+  }
+  if (W > 0.0) {
+    for (int j = 0; j < d; ++j) sum[j] /= W; /* node mean */
+    for (int64_t s = 0; s < n_idx; ++s) {
+      const double w = wts ? (double)wts[s] : 1.0;
+      const float* xs = X + (int64_t)idx[s] * d;
+      for (int j = 0; j < d; ++j) {
+        const double t = (double)xs[j] - sum[j];
+        stats[(int64_t)KM * D + j] += w * t * t;
+      }
+    }
+    for (int j = 0; j < d; ++j) stats[(int64_t)KM * D + j] /= W;
+    for (int k = 0; k < K; ++k)
+      if (Wk[k] > 0.0)
+        for (int j = 0; j < d; ++j)
+          stats[(int64_t)k * D + j] = csum[(int64_t)k * d + j] / Wk[k] - sum[j];
+  }
+  free(sum);
+  free(csum);
+  return 0;
+}
+
+/* weight as the network uses it: optionally rounded to bfloat16 */
+static double mlp_w(double w, int bf16) {
+  return bf16 ? (double)bf16_round((float)w) : w;
+}
+
+static void dense(const double* in, int n_in, const double* W, const double* b,
+                  int n_out, int bf16, int relu, double* out) {
+  for (int o = 0; o < n_out; ++o) {
+    double acc = b[o];
+    for (int i = 0; i < n_in; ++i) acc += in[i] * mlp_w(W[(int64_t)i * n_out + o], bf16);
+    out[o] = relu && acc < 0.0 ? 0.0 : acc;
+  }
+}
+
+int ora_mlp_forward(const ora_mlp* m, const double* s, int32_t n,
+                    int32_t bf16_weights, double* h1, double* h2, double* out) {
+  if (!m || !s || !out || n < 0) return -1;
+  double* a1 = (double*)malloc(sizeof(double) * ORA_MLP_H);
+  double* a2 = (double*)malloc(sizeof(double) * ORA_MLP_H);
+  if (!a1 || !a2) {
+    free(a1);
+    free(a2);
+    return -2;
+  }
+  for (int32_t r = 0; r < n; ++r) {
+    dense(s + (int64_t)r * ORA_MLP_IN, ORA_MLP_IN, m->W1, m->b1, ORA_MLP_H, bf16_weights, 1, a1);
+    dense(a1, ORA_MLP_H, m->W2, m->b2, ORA_MLP_H, bf16_weights, 1, a2);
+    dense(a2, ORA_MLP_H, m->W3, m->b3, ORA_MLP_OUT, bf16_weights, 0,
+          out + (int64_t)r * ORA_MLP_OUT);
+    if (h1) memcpy(h1 + (int64_t)r * ORA_MLP_H, a1, sizeof(double) * ORA_MLP_H);
+    if (h2) memcpy(h2 + (int64_t)r * ORA_MLP_H, a2, sizeof(double) * ORA_MLP_H);
+  }
+  free(a1);
+  free(a2);
+  return 0;
+}
+
+static double softplus(double x) { return x > 30.0 ? x : log1p(exp(x)); }
+static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+/* Loss of one sample and dL/do (do[OUT]). */
+static double sample_loss(const double* o, int dims, const double* a, double* dout) {
+  const int D = ORA_MLP_D, P = ORA_MLP_P;
+  double c = 0.0, mm = 0.0;
+  for (int j = 0; j < dims; ++j) {
+    c += o[j] * a[j];
+    mm += o[j] * o[j];
+  }
+  const double q = mm + 1e-12;
+  double loss = 1.0 - c * c / q;
+  for (int j = 0; j < ORA_MLP_OUT; ++j) dout[j] = 0.0;
+  for (int j = 0; j < dims; ++j) dout[j] = -2.0 * c * a[j] / q + 2.0 * c * c * o[j] / (q * q);
+  /* distance of the unit prediction to the nearer of +-a */
+  double delta = 1.0, nm = 0.0, sg = c >= 0.0 ? 1.0 : -1.0;
+  if (mm > 0.0) {
+    nm = sqrt(mm);
+    double e = 0.0;
+    for (int j = 0; j < dims; ++j) {
+      const double t = o[j] / nm - sg * a[j];
+      e += t * t;
+    }
+    delta = sqrt(e);
+  }
+  double spread = 0.0, dl_ddelta = 0.0;
+  for (int i = 0; i < P; ++i) {
+    const double tau = (i + 0.5) / P;
+    const double x = o[D + i], rho = softplus(x), u = delta - rho;
+    spread += u >= 0.0 ? tau * u : (tau - 1.0) * u;
+    dl_ddelta += (u >= 0.0 ? tau : tau - 1.0) / P;
+    const double dl_drho = (u >= 0.0 ? -tau : 1.0 - tau) / P;
+    dout[D + i] = dl_drho * sigmoid(x);
+  }
+  /* d delta / d mu = (u - mu_hat (mu_hat . u)) / (|mu| delta), u = mu_hat - sg a */
+  if (mm > 0.0 && delta > 0.0) {
+    double hu = 0.0;
+    for (int j = 0; j < dims; ++j) hu += (o[j] / nm) * (o[j] / nm - sg * a[j]);
+    for (int j = 0; j < dims; ++j) {
+      const double mh = o[j] / nm, uj = mh - sg * a[j];
+      dout[j] += dl_ddelta * (uj - mh * hu) / (nm * delta);
+    }
+  }
+  return loss + spread / P;
+}
+
+int ora_mlp_loss_grad(const ora_mlp* m, const double* s, const int32_t* dims,
+                      const double* a, int32_t n, int32_t bf16_weights,
+                      double* loss, double* gW1, double* gb1, double* gW2,
+                      double* gb2, double* gW3, double* gb3) {
+  const int IN = ORA_MLP_IN, H = ORA_MLP_H, OUT = ORA_MLP_OUT;
+  if (!m || !s || !dims || !a || n < 1) return -1;
+  for (int32_t r = 0; r < n; ++r)
+    if (dims[r] < 1 || dims[r] > ORA_MLP_D) return -1;
+  if (gW1) memset(gW1, 0, sizeof(double) * (size_t)IN * H);
+  if (gb1) memset(gb1, 0, sizeof(double) * H);
+  if (gW2) memset(gW2, 0, sizeof(double) * (size_t)H * H);
+  if (gb2) memset(gb2, 0, sizeof(double) * H);
+  if (gW3) memset(gW3, 0, sizeof(double) * (size_t)H * OUT);
+  if (gb3) memset(gb3, 0, sizeof(double) * OUT);
+  double* h1 = (double*)malloc(sizeof(double) * H);
+  double* h2 = (double*)malloc(sizeof(double) * H);
+  double* o = (double*)malloc(sizeof(double) * OUT);
+  double* go = (double*)malloc(sizeof(double) * OUT);
+  double* g2 = (double*)malloc(sizeof(double) * H);
+  double* g1 = (double*)malloc(sizeof(double) * H);
+  if (!h1 || !h2 || !o || !go || !g2 || !g1) {
+    free(h1); free(h2); free(o); free(go); free(g2); free(g1);
+    return -2;
+  }
+  double total = 0.0;
+  const double inv_n = 1.0 / n;
+  for (int32_t r = 0; r < n; ++r) {
+    const double* sr = s + (int64_t)r * IN;
+    dense(sr, IN, m->W1, m->b1, H, bf16_weights, 1, h1);
+    dense(h1, H, m->W2, m->b2, H, bf16_weights, 1, h2);
+    dense(h2, H, m->W3, m->b3, OUT, bf16_weights, 0, o);
+    total += sample_loss(o, dims[r], a + (int64_t)r * ORA_MLP_D, go);
+    for (int j = 0; j < OUT; ++j) go[j] *= inv_n;
+    /* layer 3 */
+    for (int i = 0; i < H; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < OUT; ++j) {
+        if (gW3) gW3[(int64_t)i * OUT + j] += h2[i] * go[j];
+        acc += mlp_w(m->W3[(int64_t)i * OUT + j], bf16_weights) * go[j];
+      }
+      g2[i] = h2[i] > 0.0 ? acc : 0.0;
+    }
+    if (gb3)
+      for (int j = 0; j < OUT; ++j) gb3[j] += go[j];
+    /* layer 2 */
+    for (int i = 0; i < H; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < H; ++j) {
+        if (gW2) gW2[(int64_t)i * H + j] += h1[i] * g2[j];
+        acc += mlp_w(m->W2[(int64_t)i * H + j], bf16_weights) * g2[j];
+      }
+      g1[i] = h1[i] > 0.0 ? acc : 0.0;
+    }
+    if (gb2)
+      for (int j = 0; j < H; ++j) gb2[j] += g2[j];
+    /* layer 1 */
+    if (gW1)
+      for (int i = 0; i < IN; ++i)
+        if (sr[i] != 0.0)
+          for (int j = 0; j < H; ++j) gW1[(int64_t)i * H + j] += sr[i] * g1[j];
+    if (gb1)
+      for (int j = 0; j < H; ++j) gb1[j] += g1[j];
+  }
+  if (loss) *loss = total * inv_n;
+  free(h1); free(h2); free(o); free(go); free(g2); free(g1);
+  return 0;
+}
+
+void ora_adam_step(double* w, double* m, double* v, const double* g, int64_t n,
+                   int32_t t, double lr, double beta1, double beta2, double eps) {
+  const double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
+
+void ora_swarm_seed(uint64_t seed, uint32_t node_uid, int32_t P, int32_t d,
+                    const float* mu_hat, const float* rho, float* pos) {
+  float* u = (float*)malloc(sizeof(float) * (size_t)P * d);
+  if (!u) return;
+  ora_swarm_uniforms(seed, node_uid, 0, P, d, ORA_PURPOSE_SEED, u);
+  for (int32_t i = 0; i < P; ++i) {
+    float* ui = u + (int64_t)i * d;
+    for (int32_t j = 0; j < d; ++j) ui[j] = 2.0f * ui[j] - 1.0f;
+    float acc = 0.0f;
+    for (int32_t j = 0; j < d; ++j) acc = fmaf(ui[j], ui[j], acc);
+    const float nrm = sqrtf(acc);
+    for (int32_t j = 0; j < d; ++j) {
+      const float q = nrm > 0.0f ? ui[j] / nrm : 0.0f;
+      pos[(int64_t)i * d + j] = mu_hat[j] + rho[i] * q;
+    }
+  }
+  free(u);
+}

@@ -44,7 +44,8 @@ enum {
   ORA_PURPOSE_INIT_V = 2,
   ORA_PURPOSE_R1 = 3,
   ORA_PURPOSE_R2 = 4,
-  ORA_PURPOSE_BOOTSTRAP = 5
+  ORA_PURPOSE_BOOTSTRAP = 5,
+  ORA_PURPOSE_SEED = 6
 };
 
 typedef struct {
@@ -160,6 +161,65 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
 int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,
                    const int32_t* labels, const float* y, uint32_t tree_id,
                    int32_t bootstrap, ora_tree* out);
+
+/* ---- learned swarm proposal (a network that seeds the swarm) ------------
+ * Fixed sizes: features padded to D = 256, classes to K = 20, P = 64 radii. */
+enum {
+  ORA_MLP_D = 256,
+  ORA_MLP_K = 20,
+  ORA_MLP_IN = 256 * 21,  /* 5376: K class blocks + one variance block */
+  ORA_MLP_H = 512,
+  ORA_MLP_P = 64,
+  ORA_MLP_OUT = 256 + 64  /* direction, then P radii (before softplus) */
+};
+
+/* Network parameters, row-major, "input x output": W1[IN*H], b1[H],
+ * W2[H*H], b2[H], W3[H*OUT], b3[OUT]. */
+typedef struct {
+  const double *W1, *b1, *W2, *b2, *W3, *b3;
+} ora_mlp;
+
+/* Statistics of one node (entries idx[n_idx], multiplicities wts or NULL),
+ * the network input stats[IN]: block k < K (classes) holds, for j < d, the
+ * class-k weighted mean of feature j minus the node's weighted mean (0 for an
+ * empty class); block K holds the weighted (population) variance of feature j.
+ * Regression (labels NULL): the classes are the four quarters of the node's
+ * y range [ymin, ymax] (group = min(3, floor(4 (y - ymin) / (ymax - ymin)))). */
+int ora_node_stats(const float* X, int32_t d, const int32_t* labels,
+                   int32_t n_classes, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, double* stats);
+
+/* Forward pass for n samples: h1 = relu(s W1 + b1), h2 = relu(h1 W2 + b2),
+ * o = h2 W3 + b3. With bf16_weights, every weight (not bias) is rounded to
+ * bfloat16 first. out[n*OUT]; h1, h2 (optional) [n*H]. */
+int ora_mlp_forward(const ora_mlp* m, const double* s, int32_t n,
+                    int32_t bf16_weights, double* h1, double* h2, double* out);
+
+/* Mean loss over n samples and its gradient. For sample r with feature
+ * count dims[r] and unit target direction a[r*D] (zero past dims[r]):
+ * mu = o[0:dims], L_dir = 1 - (mu.a)^2 / (|mu|^2 + 1e-12); delta = |mu/|mu| -
+ * sign(mu.a) a|; rho_i = softplus(o[D + i]); L_spread =
+ * mean_i pinball_{tau_i}(delta - rho_i), tau_i = (i + 0.5) / P, pinball_tau(u)
+ * = max(tau u, (tau - 1) u). Loss = mean_r (L_dir + L_spread). Gradients of
+ * the loss (weights through the straight-through rule when bf16_weights):
+ * g* arrays like the parameters; any may be NULL. */
+int ora_mlp_loss_grad(const ora_mlp* m, const double* s, const int32_t* dims,
+                      const double* a, int32_t n, int32_t bf16_weights,
+                      double* loss, double* gW1, double* gb1, double* gW2,
+                      double* gb2, double* gW3, double* gb3);
+
+/* One Adam step (Kingma and Ba, 2015) on n parameters at step t >= 1:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void ora_adam_step(double* w, double* m, double* v, const double* g, int64_t n,
+                   int32_t t, double lr, double beta1, double beta2, double eps);
+
+/* Seeded initial positions: x_i = mu_hat + rho_i u_i / |u_i| with u_ij =
+ * 2 U - 1 of the swarm stream (purpose ORA_PURPOSE_SEED = 6, iteration 0),
+ * in float, one rounding per operation; |u_i| = sqrtf of a sequential fmaf
+ * sum of squares. pos[P*d]. */
+void ora_swarm_seed(uint64_t seed, uint32_t node_uid, int32_t n_particles,
+                    int32_t d, const float* mu_hat, const float* rho, float* pos);
 
 /* Route samples through a tree grown by ora_train_tree. */
 int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
