@@ -88,7 +88,8 @@ typedef struct slm_params {
   int32_t proj;        /* slm_proj */
   int32_t n_trees;     /* >= 1; > 1 grows a bagged forest */
   int32_t bootstrap;   /* 1: tree t trains on a bootstrap bag of the n samples */
-  int32_t reserved;    /* must be 0 */
+  int32_t seeded;      /* 1: start each swarm from the context's proposal
+                          (slm_use_proposal) instead of U[-1,1)^d; 0 otherwise */
   uint64_t seed;       /* Philox-4x32-10 key for every random draw */
 } slm_params;
 
@@ -130,7 +131,8 @@ slm_status slm_last_error(slm_ctx* ctx, char* buf, size_t len);
  * positions and velocities, r1 and r2 of Eq. pso-1), exposed for
  * reproducibility checks. u[i*d + j] = (r >> 8) * 2^-24 with r = lane (j mod 4)
  * of Philox4x32-10(key = seed, counter = {node_uid, t, i, (j>>2) | purpose<<24}).
- * purpose: 1 initial position, 2 initial velocity, 3 r1, 4 r2. */
+ * purpose: 1 initial position, 2 initial velocity, 3 r1, 4 r2, 6 seeded
+ * start (slm_swarm_seed). */
 slm_status slm_swarm_uniforms(slm_ctx* ctx, uint64_t seed, uint32_t node_uid,
                               uint32_t t, int32_t n_particles, int32_t d,
                               int32_t purpose, float* u);
@@ -260,6 +262,86 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
                        double* value_out, int32_t* leaf_out);
 
 
+/* ---- learned swarm proposal ----------------------------------------------
+ * Not in the paper, which starts every swarm in a preset range (Sec. III-A):
+ * a network that proposes a starting direction and spread for a node's swarm
+ * from the node's statistics, trained on (statistics, best direction) pairs
+ * that PSO searches produce. Sizes are fixed: features padded to
+ * SLM_PROPOSAL_D, classes to SLM_PROPOSAL_K, SLM_PROPOSAL_P spread radii. */
+#define SLM_PROPOSAL_D 256
+#define SLM_PROPOSAL_K 20
+#define SLM_PROPOSAL_IN (256 * 21)  /* 5376 statistics per node */
+#define SLM_PROPOSAL_H 512          /* hidden width */
+#define SLM_PROPOSAL_P 64
+#define SLM_PROPOSAL_OUT (256 + 64) /* direction, then radii before softplus */
+
+typedef struct slm_proposal slm_proposal;
+
+/* Statistics of one node, the network input stats[SLM_PROPOSAL_IN] (host or
+ * device): for class k < K and feature j < d, stats[k*256 + j] = the class's
+ * weighted mean of feature j minus the node's (0 for an empty class);
+ * stats[20*256 + j] = the node's weighted variance of feature j; all other
+ * entries 0. Regression (labels NULL, y set): the classes are the quarters of
+ * the node's y range. Node and weights as in slm_evaluate_swarm. Limits:
+ * d <= 256, n_classes <= 20. */
+slm_status slm_node_stats(slm_ctx* ctx, const float* X, int64_t n, int32_t d,
+                          const int32_t* labels, int32_t n_classes,
+                          const float* y, const int32_t* sample_idx,
+                          const uint32_t* weights, int64_t n_idx,
+                          float* stats);
+
+/* A network h1 = relu(s W1 + b1), h2 = relu(h1 W2 + b2), o = h2 W3 + b3 with
+ * W1[IN x H], W2[H x H], W3[H x OUT] row-major ("input x output"), computed
+ * with bfloat16-rounded weights and FP32 accumulation. Created with
+ * Glorot-uniform weights from Philox (seed) and zero biases; owned by the
+ * library, freed by slm_proposal_free. */
+slm_status slm_proposal_create(slm_ctx* ctx, uint64_t seed, slm_proposal** out);
+void slm_proposal_free(slm_proposal* prop);
+/* Copies all parameters in (set: also resets the Adam state) or out; arrays
+ * are FP32, host or device, any may be NULL on get. */
+slm_status slm_proposal_set(slm_ctx* ctx, slm_proposal* prop, const float* W1,
+                            const float* b1, const float* W2, const float* b2,
+                            const float* W3, const float* b3);
+slm_status slm_proposal_get(slm_ctx* ctx, const slm_proposal* prop, float* W1,
+                            float* b1, float* W2, float* b2, float* W3,
+                            float* b3);
+/* out[N x OUT] = network(stats[N x IN]). */
+slm_status slm_proposal_forward(slm_ctx* ctx, const slm_proposal* prop,
+                                const float* stats, int32_t n, float* out);
+/* Mean loss over n samples and its gradient (g* like the parameters, FP32,
+ * host or device, any may be NULL). Sample r: d = dims[r] features, unit
+ * target direction targets[r*256 ...] (zero past d); mu = o[0:d],
+ * L = 1 - (mu.a)^2 / (|mu|^2 + 1e-12) + mean_i pinball_{(i+0.5)/64}(delta -
+ * softplus(o[256+i])), delta = |mu/|mu| - sign(mu.a) a|. Gradients pass
+ * straight through the bfloat16 rounding of the weights. */
+slm_status slm_proposal_loss_grad(slm_ctx* ctx, const slm_proposal* prop,
+                                  const float* stats, const int32_t* dims,
+                                  const float* targets, int32_t n, double* loss,
+                                  float* gW1, float* gb1, float* gW2, float* gb2,
+                                  float* gW3, float* gb3);
+/* Trains with Adam (lr, beta 0.9 / 0.999, eps 1e-8) on n samples for
+ * `epochs` passes in minibatches of `batch` (order shuffled per epoch from
+ * `seed`); epoch_loss[epochs] (optional, host) receives each epoch's mean
+ * batch loss. */
+slm_status slm_proposal_train(slm_ctx* ctx, slm_proposal* prop,
+                              const float* stats, const int32_t* dims,
+                              const float* targets, int32_t n, int32_t epochs,
+                              int32_t batch, float lr, uint64_t seed,
+                              double* epoch_loss);
+/* Searches of this context with params.seeded = 1 start each node's swarm
+ * from prop: particle i at mu_hat + rho_i u_i / |u_i|, mu_hat = o[0:d]/|o[0:d]|,
+ * rho_i = softplus(o[256 + i]); requires d <= 256, n_classes <= 20 (or MSE),
+ * n_particles <= 64. The context does not own prop; NULL detaches it. */
+slm_status slm_use_proposal(slm_ctx* ctx, const slm_proposal* prop);
+/* The seeded positions pos[P x d] for given mu_hat[d] and rho[P] (host or
+ * device): x_ij = mu_hat_j + rho_i (u_ij / |u_i|) in float, one rounding per
+ * operation, u_ij = 2 U - 1 with U the swarm draw of purpose 6 at iteration 0
+ * (slm_swarm_uniforms) and |u_i| the correctly rounded square root of a
+ * sequential fused multiply-add sum of squares. */
+slm_status slm_swarm_seed(slm_ctx* ctx, uint64_t seed, uint32_t node_uid,
+                          int32_t n_particles, int32_t d, const float* mu_hat,
+                          const float* rho, float* pos);
+
 /* ---- diagnostics --------------------------------------------------------
  * Kernels of this library, for per-kernel timing. */
 typedef enum {
@@ -276,7 +358,8 @@ typedef enum {
   SLM_K_PROJECT_MMA = 9,  /* z in bfloat16 on the tensor cores (BF16_TOPK) */
   SLM_K_TOPK = 10,        /* BF16_TOPK: position conversion, top-k selection,
                              score merge with the pbest / gbest steps */
-  SLM_K_COUNT = 11
+  SLM_K_PROPOSAL = 11,    /* node statistics, network passes, Adam, seeding */
+  SLM_K_COUNT = 12
 } slm_kernel;
 
 /* on != 0 brackets every later launch of the context with CUDA events on its

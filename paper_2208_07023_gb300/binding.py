@@ -22,7 +22,7 @@ SLM_PROJ_FP32, SLM_PROJ_BF16_TOPK = 0, 1
 CRITERIA = {"gini": SLM_GINI, "entropy": SLM_ENTROPY, "mse": SLM_MSE}
 PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2 = 1, 2, 3, 4
 KERNELS = ["project", "hist_scan", "move", "swarm_init", "node_stats",
-           "partition", "compact", "gather", "other", "project_mma", "topk"]
+           "partition", "compact", "gather", "other", "project_mma", "topk", "proposal"]
 
 
 class slm_params(C.Structure):
@@ -32,7 +32,7 @@ class slm_params(C.Structure):
         ("n_bins", C.c_int32), ("topk", C.c_int32), ("inertia", C.c_float),
         ("c1", C.c_float), ("c2", C.c_float), ("max_depth", C.c_int32),
         ("min_leaf", C.c_int32), ("proj", C.c_int32), ("n_trees", C.c_int32),
-        ("bootstrap", C.c_int32), ("reserved", C.c_int32),
+        ("bootstrap", C.c_int32), ("seeded", C.c_int32),
         ("seed", C.c_uint64),
     ]
 
@@ -95,6 +95,18 @@ def lib():
             "slm_launch_count": ([vp, P(i64)], C.c_int),
             "slm_evaluate_swarm_noalloc": ([C.c_int, vp, P(slm_params), vp, i64, i32, vp, vp,
                                             vp, vp, i64, vp, i32, vp], C.c_int),
+            "slm_node_stats": ([vp, vp, i64, i32, vp, i32, vp, vp, vp, i64, vp], C.c_int),
+            "slm_proposal_create": ([vp, u64, P(vp)], C.c_int),
+            "slm_proposal_free": ([vp], None),
+            "slm_proposal_set": ([vp, vp] + [vp] * 6, C.c_int),
+            "slm_proposal_get": ([vp, vp] + [vp] * 6, C.c_int),
+            "slm_proposal_forward": ([vp, vp, vp, i32, vp], C.c_int),
+            "slm_proposal_loss_grad": ([vp, vp, vp, vp, vp, i32, P(C.c_double)] + [vp] * 6,
+                                       C.c_int),
+            "slm_proposal_train": ([vp, vp, vp, vp, vp, i32, i32, i32, C.c_float, u64, vp],
+                                   C.c_int),
+            "slm_use_proposal": ([vp, vp], C.c_int),
+            "slm_swarm_seed": ([vp, u64, u32, i32, i32, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -107,11 +119,11 @@ def lib():
 def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
                 n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8, min_leaf=1,
                 seed=1, n_trees=1, bootstrap=False, proj=SLM_PROJ_FP32,
-                topk=8) -> slm_params:
+                topk=8, seeded=False) -> slm_params:
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
     return slm_params(crit, 0 if crit == SLM_MSE else n_classes, n_particles,
                       n_iters, n_bins, topk, inertia, c1, c2, max_depth, min_leaf,
-                      proj, n_trees, 1 if bootstrap else 0, 0, seed)
+                      proj, n_trees, 1 if bootstrap else 0, 1 if seeded else 0, seed)
 
 
 def _ptr(a) -> Optional[int]:
@@ -177,6 +189,67 @@ class Forest:
             pass
 
 
+PROP_D, PROP_K, PROP_H, PROP_P = 256, 20, 512, 64
+PROP_IN, PROP_OUT = PROP_D * (PROP_K + 1), PROP_D + PROP_P
+PROP_SHAPES = {"W1": (PROP_IN, PROP_H), "b1": (PROP_H,), "W2": (PROP_H, PROP_H),
+               "b2": (PROP_H,), "W3": (PROP_H, PROP_OUT), "b3": (PROP_OUT,)}
+_PROP_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+class Proposal:
+    """A learned swarm proposal (network) owned by the library."""
+
+    def __init__(self, ctx: "Context", handle):
+        self.ctx, self.handle = ctx, handle
+
+    def free(self):
+        if self.handle:
+            lib().slm_proposal_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def set(self, params: dict):
+        arrs = [_as(np.ascontiguousarray(params[k], dtype=np.float32), np.float32)
+                for k in _PROP_ORDER]
+        self.ctx._check(lib().slm_proposal_set(self.ctx.handle, self.handle,
+                                               *[_ptr(a) for a in arrs]))
+
+    def get(self) -> dict:
+        out = {k: np.empty(PROP_SHAPES[k], np.float32) for k in _PROP_ORDER}
+        self.ctx._check(lib().slm_proposal_get(self.ctx.handle, self.handle,
+                                               *[_ptr(out[k]) for k in _PROP_ORDER]))
+        return out
+
+    def forward(self, stats) -> np.ndarray:
+        stats = np.ascontiguousarray(stats, dtype=np.float32).reshape(-1, PROP_IN)
+        out = np.empty((stats.shape[0], PROP_OUT), np.float32)
+        self.ctx._check(lib().slm_proposal_forward(self.ctx.handle, self.handle, _ptr(stats),
+                                                   stats.shape[0], _ptr(out)))
+        return out
+
+    def loss_grad(self, stats, dims, targets):
+        stats = np.ascontiguousarray(stats, dtype=np.float32).reshape(-1, PROP_IN)
+        n = stats.shape[0]
+        dims = np.ascontiguousarray(dims, dtype=np.int32)
+        targets = np.ascontiguousarray(targets, dtype=np.float32).reshape(n, PROP_D)
+        g = {k: np.empty(PROP_SHAPES[k], np.float32) for k in _PROP_ORDER}
+        loss = C.c_double()
+        self.ctx._check(lib().slm_proposal_loss_grad(
+            self.ctx.handle, self.handle, _ptr(stats), _ptr(dims), _ptr(targets), n,
+            C.byref(loss), *[_ptr(g[k]) for k in _PROP_ORDER]))
+        return loss.value, g
+
+    def train(self, stats, dims, targets, epochs=10, batch=64, lr=1e-3, seed=1):
+        stats = _as(stats, np.float32)
+        dims = _as(dims, np.int32)
+        targets = _as(targets, np.float32)
+        n = int(dims.shape[0])
+        losses = np.zeros(epochs, np.float64)
+        self.ctx._check(lib().slm_proposal_train(
+            self.ctx.handle, self.handle, _ptr(stats), _ptr(dims), _ptr(targets), n, epochs,
+            batch, lr, seed, _ptr(losses)))
+        return losses
+
+
 class Context:
     """One libslm context (device + stream)."""
 
@@ -203,6 +276,35 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    # -- learned proposal ---------------------------------------------------
+    def node_stats(self, X, labels=None, n_classes=0, y=None, sample_idx=None, weights=None):
+        X = _as(X, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
+        n, d = X.shape
+        n_idx = n if sample_idx is None else sample_idx.shape[0]
+        out = np.empty(PROP_IN, np.float32)
+        self._check(lib().slm_node_stats(self.handle, _ptr(X), n, d, _ptr(labels), n_classes,
+                                         _ptr(y), _ptr(sample_idx), _ptr(weights), n_idx,
+                                         _ptr(out)))
+        return out
+
+    def proposal(self, seed: int = 1) -> Proposal:
+        h = C.c_void_p()
+        self._check(lib().slm_proposal_create(self.handle, seed, C.byref(h)))
+        return Proposal(self, h)
+
+    def use_proposal(self, prop: Optional[Proposal]):
+        self._check(lib().slm_use_proposal(self.handle, prop.handle if prop else None))
+
+    def swarm_seed(self, seed, node_uid, n_particles, d, mu_hat, rho) -> np.ndarray:
+        mu_hat = np.ascontiguousarray(mu_hat, dtype=np.float32)
+        rho = np.ascontiguousarray(rho, dtype=np.float32)
+        pos = np.empty((n_particles, d), np.float32)
+        self._check(lib().slm_swarm_seed(self.handle, seed, node_uid, n_particles, d,
+                                         _ptr(mu_hat), _ptr(rho), _ptr(pos)))
+        return pos
 
     # -- diagnostics -------------------------------------------------------
     def profile(self, on: bool):

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -29,6 +31,9 @@ enum Slot {
   W_XB, S_POSB, S_MTILES, S_SEL, S_INV, S_POSK, S_Z2, S_ZMM2, S_CUR2,
   // MSE moments
   S_M1, S_M2, S_MACCW, S_MACCY, S_MSCALE,
+  // learned proposal: node statistics, network work space, training data
+  S_PSTATS, S_PYR, S_PACC, S_PWK, S_PWORK, S_PLOSS, W_PS, W_PD, W_PT, W_PIDX, W_PBS, W_PBD,
+  W_PBT, W_PRHO, W_PMU, W_PPOS,
   N_SLOTS
 };
 
@@ -52,6 +57,18 @@ struct slm_ctx {
   int64_t k_launches[SLM_K_COUNT] = {};
   double k_ms[SLM_K_COUNT] = {};
   double k_pairs[SLM_K_COUNT] = {};
+  const slm_proposal* prop = nullptr;  // seeds searches with params.seeded
+};
+
+// Learned swarm proposal: FP32 parameters, their bfloat16 copies, gradients
+// and Adam moments in one device allocation.
+struct slm_proposal {
+  int device = 0;
+  DevBuf mem;
+  MlpParams m{};
+  MlpGrads g{};
+  MlpState s{};
+  int64_t step = 0;  // Adam steps taken
 };
 
 struct slm_forest {
@@ -191,6 +208,14 @@ slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
     if (!std::isfinite(p->inertia) || !std::isfinite(p->c1) ||
         !std::isfinite(p->c2))
       return fail(c, SLM_EINVAL, "inertia / c1 / c2 must be finite");
+    if (p->seeded != 0 && p->seeded != 1) return fail(c, SLM_EINVAL, "seeded must be 0 or 1");
+    if (p->seeded) {
+      if (!c->prop) return fail(c, SLM_EINVAL, "seeded search without slm_use_proposal");
+      if (d > kPropD || (p->criterion != SLM_MSE && p->n_classes > kPropK) ||
+          p->n_particles > kPropP)
+        return fail(c, SLM_EUNSUPPORTED,
+                    "seeded searches need d <= 256, n_classes <= 20, n_particles <= 64");
+    }
   }
   return SLM_OK;
 }
@@ -517,6 +542,54 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
   return SLM_OK;
 }
 
+// Network work space for a batch of N samples.
+slm_status proposal_work(slm_ctx* c, int N, MlpWork* w) {
+  const size_t nh = (size_t)N * kPropH, no = (size_t)N * kPropOut;
+  CK(ensure(c->ws[S_PWORK], sizeof(float) * (4 * nh + 2 * no)));
+  float* b = ws_ptr<float>(c, S_PWORK);
+  *w = MlpWork{b, b + nh, b + 2 * nh, b + 2 * nh + no, b + 2 * nh + 2 * no,
+               b + 3 * nh + 2 * no};
+  return SLM_OK;
+}
+
+// Statistics of the batch's nodes (already uploaded to S_NODES) into S_PSTATS.
+slm_status batch_stats(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes,
+                       float** stats) {
+  const int A = (int)nodes.size();
+  const int K = pr.lab ? pr.K : 4;
+  int64_t max_len = 0;
+  for (const NodeDesc& nd : nodes) max_len = std::max<int64_t>(max_len, nd.seg_len);
+  CK(ensure(c->ws[S_PSTATS], sizeof(float) * (size_t)A * kPropIn));
+  CK(ensure(c->ws[S_PYR], sizeof(int32_t) * 2 * (size_t)A));
+  CK(ensure(c->ws[S_PACC], sizeof(double) * (size_t)A * (K + 2) * pr.d));
+  CK(ensure(c->ws[S_PWK], sizeof(double) * (size_t)A * K));
+  CK(launch(c, SLM_K_PROPOSAL, 0.0, [&] {
+    return launch_node_stats(pr, ws_ptr<NodeDesc>(c, S_NODES), A, max_len, K,
+                             ws_ptr<int32_t>(c, S_PYR), ws_ptr<double>(c, S_PACC),
+                             ws_ptr<double>(c, S_PWK), ws_ptr<float>(c, S_PSTATS), c->n_sm,
+                             c->stream);
+  }));
+  *stats = ws_ptr<float>(c, S_PSTATS);
+  return SLM_OK;
+}
+
+// Initial swarms from the context's proposal: node statistics, the network,
+// then positions around its direction (Sec. III-A's start, learned).
+slm_status seed_swarms(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes,
+                       const Swarm& sw, SwarmCoef co) {
+  const int A = (int)nodes.size();
+  float* stats = nullptr;
+  if (slm_status s = batch_stats(c, pr, nodes, &stats)) return s;
+  MlpWork w;
+  if (slm_status s = proposal_work(c, A, &w)) return s;
+  CK(launch(c, SLM_K_PROPOSAL, 0.0,
+            [&] { return launch_mlp_forward(c->prop->m, stats, A, w, c->stream); }));
+  CK(launch(c, SLM_K_SWARM_INIT, 0.0, [&] {
+    return launch_swarm_seed_init(pr, sw, ws_ptr<NodeDesc>(c, S_NODES), A, co, w.O, c->stream);
+  }));
+  return SLM_OK;
+}
+
 // PSO search of every node of a batch (Algorithm 1, synchronous updates).
 slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
@@ -534,8 +607,12 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
   if (p->proj == SLM_PROJ_BF16_TOPK &&
       (s = setup_bf16(c, pr, nodes, std::min(p->topk, p->n_particles), true, &sw, &bp)))
     return s;
-  CK(launch(c, SLM_K_SWARM_INIT, 0.0,
-            [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
+  if (p->seeded) {
+    if ((s = seed_swarms(c, pr, nodes, sw, co))) return s;
+  } else {
+    CK(launch(c, SLM_K_SWARM_INIT, 0.0,
+              [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
+  }
   const int S = batch_split(c, pr, nodes);
   for (int t = 0; t <= p->n_iters; ++t)
     if ((s = score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp)))
@@ -1361,6 +1438,281 @@ slm_status slm_predict(slm_ctx* c, const slm_forest* f, const float* X, int64_t 
   if (hl)
     CK(cudaMemcpyAsync(leaf_out, dl, 4 * (size_t)n * f->n_trees, cudaMemcpyDeviceToHost,
                        c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+// ---- learned swarm proposal ------------------------------------------------------
+
+namespace {
+constexpr size_t kNW1 = (size_t)kPropIn * kPropH, kNW2 = (size_t)kPropH * kPropH,
+                 kNW3 = (size_t)kPropH * kPropOut;
+constexpr size_t kNParams = kNW1 + kPropH + kNW2 + kPropH + kNW3 + kPropOut;
+
+// Views of a parameter-sized block: W1, b1, W2, b2, W3, b3 in this order.
+void split_params(float* b, float** W1, float** b1, float** W2, float** b2, float** W3,
+                  float** b3) {
+  *W1 = b;
+  *b1 = *W1 + kNW1;
+  *W2 = *b1 + kPropH;
+  *b2 = *W2 + kNW2;
+  *W3 = *b2 + kPropH;
+  *b3 = *W3 + kNW3;
+}
+}  // namespace
+
+slm_status slm_proposal_create(slm_ctx* c, uint64_t seed, slm_proposal** out) {
+  if (!c || !out) return SLM_EINVAL;
+  *out = nullptr;
+  CK(cudaSetDevice(c->device));
+  slm_proposal* pp = new (std::nothrow) slm_proposal();
+  if (!pp) return fail(c, SLM_ENOMEM, "host allocation failed");
+  pp->device = c->device;
+  // params | grads | Adam m | Adam v (FP32), then the bfloat16 weight copies
+  const size_t bytes = sizeof(float) * 4 * kNParams + 2 * (kNW1 + kNW2 + kNW3) + 256;
+  cudaError_t e = ensure(pp->mem, bytes);
+  if (e) {
+    delete pp;
+    return cuda_fail(c, e, "proposal memory");
+  }
+  float* base = static_cast<float*>(pp->mem.p);
+  MlpParams& m = pp->m;
+  split_params(base, &m.W1, &m.b1, &m.W2, &m.b2, &m.W3, &m.b3);
+  MlpGrads& g = pp->g;
+  split_params(base + kNParams, &g.W1, &g.b1, &g.W2, &g.b2, &g.W3, &g.b3);
+  MlpState& st = pp->s;
+  split_params(base + 2 * kNParams, &st.mW1, &st.mb1, &st.mW2, &st.mb2, &st.mW3, &st.mb3);
+  split_params(base + 3 * kNParams, &st.vW1, &st.vb1, &st.vW2, &st.vb2, &st.vW3, &st.vb3);
+  __nv_bfloat16* bb = reinterpret_cast<__nv_bfloat16*>(base + 4 * kNParams);
+  m.W1b = bb;
+  m.W2b = bb + kNW1;
+  m.W3b = bb + kNW1 + kNW2;
+  if ((e = cudaMemsetAsync(base + 2 * kNParams, 0, sizeof(float) * 2 * kNParams, c->stream)) ||
+      (e = launch_mlp_init(m, seed, c->stream)) || (e = cudaStreamSynchronize(c->stream))) {
+    release(pp->mem);
+    delete pp;
+    return cuda_fail(c, e, "proposal init");
+  }
+  c->launches += 7;
+  *out = pp;
+  return SLM_OK;
+}
+
+void slm_proposal_free(slm_proposal* pp) {
+  if (!pp) return;
+  cudaSetDevice(pp->device);
+  release(pp->mem);
+  delete pp;
+}
+
+slm_status slm_proposal_set(slm_ctx* c, slm_proposal* pp, const float* W1, const float* b1,
+                            const float* W2, const float* b2, const float* W3, const float* b3) {
+  if (!c || !pp || !W1 || !b1 || !W2 || !b2 || !W3 || !b3)
+    return fail(c, SLM_EINVAL, "NULL argument");
+  CK(cudaSetDevice(c->device));
+  const float* src[6] = {W1, b1, W2, b2, W3, b3};
+  float* dst[6] = {pp->m.W1, pp->m.b1, pp->m.W2, pp->m.b2, pp->m.W3, pp->m.b3};
+  const size_t cnt[6] = {kNW1, kPropH, kNW2, kPropH, kNW3, kPropOut};
+  for (int i = 0; i < 6; ++i)
+    CK(cudaMemcpyAsync(dst[i], src[i], sizeof(float) * cnt[i], cudaMemcpyDefault, c->stream));
+  CK(cudaMemsetAsync(pp->s.mW1, 0, sizeof(float) * 2 * kNParams, c->stream));
+  CK(launch(c, SLM_K_PROPOSAL, 0.0, [&] { return launch_mlp_sync_bf16(pp->m, c->stream); }));
+  pp->step = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_proposal_get(slm_ctx* c, const slm_proposal* pp, float* W1, float* b1, float* W2,
+                            float* b2, float* W3, float* b3) {
+  if (!c || !pp) return fail(c, SLM_EINVAL, "NULL argument");
+  CK(cudaSetDevice(c->device));
+  float* dst[6] = {W1, b1, W2, b2, W3, b3};
+  const float* src[6] = {pp->m.W1, pp->m.b1, pp->m.W2, pp->m.b2, pp->m.W3, pp->m.b3};
+  const size_t cnt[6] = {kNW1, kPropH, kNW2, kPropH, kNW3, kPropOut};
+  for (int i = 0; i < 6; ++i)
+    if (dst[i])
+      CK(cudaMemcpyAsync(dst[i], src[i], sizeof(float) * cnt[i], cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_proposal_forward(slm_ctx* c, const slm_proposal* pp, const float* stats,
+                                int32_t n, float* out) {
+  if (!c || !pp || !stats || !out || n < 1) return fail(c, SLM_EINVAL, "bad arguments");
+  CK(cudaSetDevice(c->device));
+  const float* ds;
+  if (slm_status s = stage_in(c, stats, (size_t)n * kPropIn, c->ws[W_PS], &ds)) return s;
+  MlpWork w;
+  if (slm_status s = proposal_work(c, n, &w)) return s;
+  CK(launch(c, SLM_K_PROPOSAL, 0.0, [&] { return launch_mlp_forward(pp->m, ds, n, w, c->stream); }));
+  CK(cudaMemcpyAsync(out, w.O, sizeof(float) * (size_t)n * kPropOut, cudaMemcpyDefault,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+namespace {
+slm_status check_train_args(slm_ctx* c, const float* stats, const int32_t* dims,
+                            const float* targets, int32_t n) {
+  if (!stats || !dims || !targets || n < 1) return fail(c, SLM_EINVAL, "bad arguments");
+  std::vector<int32_t> hd((size_t)n);
+  CK(cudaMemcpy(hd.data(), dims, sizeof(int32_t) * (size_t)n, cudaMemcpyDefault));
+  for (int32_t v : hd)
+    if (v < 1 || v > kPropD) return fail(c, SLM_EINVAL, "dims must be in [1, 256]");
+  return SLM_OK;
+}
+}  // namespace
+
+slm_status slm_proposal_loss_grad(slm_ctx* c, const slm_proposal* pp, const float* stats,
+                                  const int32_t* dims, const float* targets, int32_t n,
+                                  double* loss, float* gW1, float* gb1, float* gW2, float* gb2,
+                                  float* gW3, float* gb3) {
+  if (!c || !pp) return SLM_EINVAL;
+  CK(cudaSetDevice(c->device));
+  if (slm_status s = check_train_args(c, stats, dims, targets, n)) return s;
+  const float *ds, *dt;
+  const int32_t* dd;
+  slm_status s;
+  if ((s = stage_in(c, stats, (size_t)n * kPropIn, c->ws[W_PS], &ds)) ||
+      (s = stage_in(c, dims, (size_t)n, c->ws[W_PD], &dd)) ||
+      (s = stage_in(c, targets, (size_t)n * kPropD, c->ws[W_PT], &dt)))
+    return s;
+  MlpWork w;
+  if ((s = proposal_work(c, n, &w))) return s;
+  CK(ensure(c->ws[S_PLOSS], 2 * sizeof(double)));
+  double* dl = ws_ptr<double>(c, S_PLOSS);
+  CK(launch(c, SLM_K_PROPOSAL, 0.0, [&] {
+    return launch_mlp_loss_grad(pp->m, ds, dd, dt, n, w, pp->g, dl, c->stream);
+  }));
+  if (loss) CK(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  float* dst[6] = {gW1, gb1, gW2, gb2, gW3, gb3};
+  const float* src[6] = {pp->g.W1, pp->g.b1, pp->g.W2, pp->g.b2, pp->g.W3, pp->g.b3};
+  const size_t cnt[6] = {kNW1, kPropH, kNW2, kPropH, kNW3, kPropOut};
+  for (int i = 0; i < 6; ++i)
+    if (dst[i])
+      CK(cudaMemcpyAsync(dst[i], src[i], sizeof(float) * cnt[i], cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_proposal_train(slm_ctx* c, slm_proposal* pp, const float* stats,
+                              const int32_t* dims, const float* targets, int32_t n,
+                              int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                              double* epoch_loss) {
+  if (!c || !pp) return SLM_EINVAL;
+  if (epochs < 0 || batch < 1 || !(lr > 0.0f) || !std::isfinite(lr))
+    return fail(c, SLM_EINVAL, "bad epochs / batch / lr");
+  CK(cudaSetDevice(c->device));
+  if (slm_status s = check_train_args(c, stats, dims, targets, n)) return s;
+  const float *ds, *dt;
+  const int32_t* dd;
+  slm_status s;
+  if ((s = stage_in(c, stats, (size_t)n * kPropIn, c->ws[W_PS], &ds)) ||
+      (s = stage_in(c, dims, (size_t)n, c->ws[W_PD], &dd)) ||
+      (s = stage_in(c, targets, (size_t)n * kPropD, c->ws[W_PT], &dt)))
+    return s;
+  const int b = std::min(batch, n);
+  MlpWork w;
+  if ((s = proposal_work(c, b, &w))) return s;
+  CK(ensure(c->ws[W_PIDX], sizeof(int32_t) * (size_t)n));
+  CK(ensure(c->ws[W_PBS], sizeof(float) * (size_t)b * kPropIn));
+  CK(ensure(c->ws[W_PBD], sizeof(int32_t) * (size_t)b));
+  CK(ensure(c->ws[W_PBT], sizeof(float) * (size_t)b * kPropD));
+  CK(ensure(c->ws[S_PLOSS], 2 * sizeof(double)));
+  double* dl = ws_ptr<double>(c, S_PLOSS);
+  int32_t* didx = ws_ptr<int32_t>(c, W_PIDX);
+  float* bs = ws_ptr<float>(c, W_PBS);
+  int32_t* bd = ws_ptr<int32_t>(c, W_PBD);
+  float* bt = ws_ptr<float>(c, W_PBT);
+  std::vector<int32_t> order((size_t)n);
+  std::mt19937_64 rng(seed);
+  for (int32_t ep = 0; ep < epochs; ++ep) {
+    std::iota(order.begin(), order.end(), 0);
+    std::shuffle(order.begin(), order.end(), rng);
+    CK(cudaMemcpyAsync(didx, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemsetAsync(dl + 1, 0, sizeof(double), c->stream));
+    int nb = 0;
+    for (int32_t r0 = 0; r0 < n; r0 += b, ++nb) {
+      const int bn = std::min(b, n - r0);
+      CK(launch(c, SLM_K_PROPOSAL, 0.0, [&] {
+        cudaError_t e;
+        if ((e = launch_gather_rows(ds, kPropIn, didx + r0, bn, bs, c->stream)) ||
+            (e = launch_gather_rows(dd, 1, didx + r0, bn, bd, c->stream)) ||
+            (e = launch_gather_rows(dt, kPropD, didx + r0, bn, bt, c->stream)))
+          return e;
+        if ((e = launch_mlp_loss_grad(pp->m, bs, bd, bt, bn, w, pp->g, dl, c->stream))) return e;
+        if ((e = launch_adam(pp->m, pp->s, pp->g, (int)++pp->step, lr, c->stream))) return e;
+        return launch_acc_double(dl + 1, dl, c->stream);
+      }));
+    }
+    double tot = 0.0;
+    CK(cudaMemcpyAsync(&tot, dl + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    // the order vector is reused by the next epoch's copy: wait for this one
+    CK(cudaStreamSynchronize(c->stream));
+    if (epoch_loss) epoch_loss[ep] = tot / nb;
+  }
+  return SLM_OK;
+}
+
+slm_status slm_use_proposal(slm_ctx* c, const slm_proposal* pp) {
+  if (!c) return SLM_EINVAL;
+  if (pp && pp->device != c->device) return fail(c, SLM_EINVAL, "proposal on another device");
+  c->prop = pp;
+  return SLM_OK;
+}
+
+slm_status slm_swarm_seed(slm_ctx* c, uint64_t seed, uint32_t node_uid, int32_t P, int32_t d,
+                          const float* mu_hat, const float* rho, float* pos) {
+  if (!c || !mu_hat || !rho || !pos || P < 1 || d < 1 || d > kMaxD)
+    return fail(c, SLM_EINVAL, "bad arguments");
+  CK(cudaSetDevice(c->device));
+  const float *dm, *dr;
+  slm_status s;
+  if ((s = stage_in(c, mu_hat, (size_t)d, c->ws[W_PMU], &dm)) ||
+      (s = stage_in(c, rho, (size_t)P, c->ws[W_PRHO], &dr)))
+    return s;
+  float* dp = pos;
+  const bool dev = is_device_ptr(pos);
+  if (!dev) {
+    CK(ensure(c->ws[W_PPOS], sizeof(float) * (size_t)P * d));
+    dp = ws_ptr<float>(c, W_PPOS);
+  }
+  CK(launch(c, SLM_K_PROPOSAL, 0.0, [&] {
+    return launch_seed_positions(seed, node_uid, P, d, dm, dr, dp, c->stream);
+  }));
+  if (!dev)
+    CK(cudaMemcpyAsync(pos, dp, sizeof(float) * (size_t)P * d, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_node_stats(slm_ctx* c, const float* X, int64_t n, int32_t d,
+                          const int32_t* labels, int32_t n_classes, const float* y,
+                          const int32_t* sample_idx, const uint32_t* weights, int64_t n_idx,
+                          float* stats) {
+  if (!c || !stats) return SLM_EINVAL;
+  slm_params p{};
+  p.criterion = labels ? SLM_GINI : SLM_MSE;
+  p.n_classes = labels ? n_classes : 0;
+  p.n_bins = 2;
+  p.min_leaf = 1;
+  if (d > kPropD || (labels && n_classes > kPropK))
+    return fail(c, SLM_EUNSUPPORTED, "node statistics need d <= 256 and n_classes <= 20");
+  if (slm_status s = check_node_args(c, &p, X, n, d, labels, y, sample_idx, &n_idx, false))
+    return s;
+  CK(cudaSetDevice(c->device));
+  Problem pr;
+  if (slm_status s = prepare_node(c, &p, X, n, d, labels, y, sample_idx, weights, n_idx, 1, &pr))
+    return s;
+  const std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, 0u, -1}};
+  CK(ensure(c->ws[S_NODES], sizeof(NodeDesc)));
+  CK(cudaMemcpyAsync(c->ws[S_NODES].p, nodes.data(), sizeof(NodeDesc), cudaMemcpyHostToDevice,
+                     c->stream));
+  float* ds = nullptr;
+  if (slm_status s = batch_stats(c, pr, nodes, &ds)) return s;
+  CK(cudaMemcpyAsync(stats, ds, sizeof(float) * kPropIn, cudaMemcpyDefault, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return SLM_OK;
 }

@@ -2,6 +2,7 @@
 // Nothing here is part of the public C ABI (include/slm.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,6 +25,9 @@ constexpr int kMaxD = 1024;
 // bfloat16 projection on the tensor cores (SLM_PROJ_BF16_TOPK)
 constexpr int kMmaRows = 128;                // rows per MMA tile = TMEM lanes
 constexpr int kMmaMaxBBytes = 128 * 1024;    // staged positions: Pp * dp * 2
+// learned swarm proposal: inputs padded to 256 features x (20 classes + 1)
+constexpr int kPropD = 256, kPropK = 20, kPropIn = 256 * 21, kPropH = 512, kPropP = 64;
+constexpr int kPropOut = kPropD + kPropP;
 
 // Philox stream purposes (high byte of counter word 3).
 enum Purpose : uint32_t {
@@ -288,5 +292,60 @@ cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr,
                            int n_trees, int H, int B, int K, int crit,
                            int32_t* class_out, double* value_out,
                            int32_t* leaf_out, cudaStream_t st);
+
+// ---- learned swarm proposal (mlp_kernels.cu) --------------------------------
+
+// Parameters, "input x output" row-major, FP32 masters and the bfloat16
+// copies the network computes with.
+struct MlpParams {
+  float *W1, *b1, *W2, *b2, *W3, *b3;
+  __nv_bfloat16 *W1b, *W2b, *W3b;
+};
+struct MlpGrads {
+  float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+// Adam moments of every parameter.
+struct MlpState {
+  float *mW1, *vW1, *mb1, *vb1, *mW2, *vW2, *mb2, *vb2, *mW3, *vW3, *mb3, *vb3;
+};
+// Activations of a batch of N samples: H1, H2, dH1, dH2 [N, H]; O, dO [N, OUT].
+struct MlpWork {
+  float *H1, *H2, *O, *dO, *dH1, *dH2;
+};
+
+// Network inputs of A nodes (entry-ordered rows of pr; K classes, or 4 y
+// groups when pr.lab is null): stats[A, 5376]. Scratch: yr[A, 2],
+// acc[A, K + 2, d], wk[A, K].
+cudaError_t launch_node_stats(const Problem& pr, const NodeDesc* nodes, int A,
+                              int64_t max_len, int K, int32_t* yr, double* acc, double* wk,
+                              float* stats, int n_sm, cudaStream_t st);
+cudaError_t launch_mlp_init(const MlpParams& m, uint64_t seed, cudaStream_t st);
+cudaError_t launch_mlp_sync_bf16(const MlpParams& m, cudaStream_t st);
+// w.O[N, OUT] = network(S[N, 5376]).
+cudaError_t launch_mlp_forward(const MlpParams& m, const float* S, int N, MlpWork w,
+                               cudaStream_t st);
+// *loss = mean loss of the batch; g = its gradient (straight through the
+// bfloat16 rounding of the weights).
+cudaError_t launch_mlp_loss_grad(const MlpParams& m, const float* S, const int32_t* dims,
+                                 const float* targets, int N, MlpWork w, MlpGrads g,
+                                 double* loss, cudaStream_t st);
+// Adam step t (beta 0.9 / 0.999, eps 1e-8) on every parameter; refreshes the
+// bfloat16 copies.
+cudaError_t launch_adam(MlpParams& m, MlpState& s, const MlpGrads& g, int t, float lr,
+                        cudaStream_t st);
+// dst[b, cols] = src rows idx[0..b).
+cudaError_t launch_gather_rows(const float* src, int64_t cols, const int32_t* idx, int b,
+                               float* dst, cudaStream_t st);
+cudaError_t launch_gather_rows(const int32_t* src, int64_t cols, const int32_t* idx, int b,
+                               int32_t* dst, cudaStream_t st);
+// *acc += *v on the device.
+cudaError_t launch_acc_double(double* acc, const double* v, cudaStream_t st);
+// pos[P, d]: the seeded positions around mu_hat with radii rho[P].
+cudaError_t launch_seed_positions(uint64_t seed, uint32_t uid, int P, int d,
+                                  const float* mu_hat, const float* rho, float* pos,
+                                  cudaStream_t st);
+// Initial swarms of A nodes seeded from the network outputs prop[A, OUT].
+cudaError_t launch_swarm_seed_init(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                                   int A, SwarmCoef co, const float* prop, cudaStream_t st);
 
 }  // namespace slm
