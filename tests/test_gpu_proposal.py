@@ -11,9 +11,10 @@ trained network gains.
 * first Adam step: w - lr sign(g) up to eps;
 * seeded positions: bit-exact against the oracle (same stream, same
   correctly rounded operations);
-* gain: after training on (statistics, PSO-best direction) pairs of two-class
-  nodes, seeded searches of held-out nodes start from a lower loss and reach
-  the plain search's final loss in fewer iterations (median).
+* gain: after training on (statistics, PSO-best direction) pairs of
+  single-node problems (planted hyperplane, d = 8..64), seeded searches of
+  held-out nodes start from a lower loss and reach the plain search's final
+  loss in fewer iterations (median).
 """
 import numpy as np
 import pytest
@@ -140,9 +141,11 @@ def test_seed_positions_bitwise(ctx, P, d):
     assert np.array_equal(g.view(np.uint32), r.view(np.uint32))
 
 
-def two_class_node(seed, n, d):
-    """Two Gaussian classes with a shared, rotated covariance."""
-    wl = W.gmm(n, d, 2, seed=seed)
+def planted_node(seed, d):
+    """The single-node pattern: isotropic features, labels by a planted
+    hyperplane with 5 % flipped (the best direction is the class-mean
+    difference, which the statistics carry)."""
+    wl = W.single_node(1000, d, 0.05, seed=seed)
     return wl.X, wl.labels
 
 
@@ -152,10 +155,10 @@ def test_trained_proposal_gains(ctx):
     base = dict(n_particles=P, n_iters=T, n_bins=B, min_leaf=5)
     # training pairs: statistics of a node and the direction plain PSO finds
     stats, dims, targets = [], [], []
-    for i in range(400):
-        d = 8 + (i % 4) * 8
-        X, lab = two_class_node(1000 + i, 800, d)
-        r = ctx.node_split(S.make_params("gini", 2, seed=i + 1, **base), X, labels=lab,
+    for i in range(1500):
+        d = (8, 16, 32, 64)[i % 4]
+        X, lab = planted_node(1000 + i, d)
+        r = ctx.node_split(S.make_params("entropy", 2, seed=i + 1, **base), X, labels=lab,
                            node_uid=i)
         stats.append(ctx.node_stats(X, labels=lab, n_classes=2))
         t = np.zeros(256, np.float32)
@@ -165,16 +168,16 @@ def test_trained_proposal_gains(ctx):
     stats, dims, targets = np.array(stats), np.array(dims, np.int32), np.array(targets)
     prop = ctx.proposal(seed=11)
     try:
-        losses = prop.train(stats, dims, targets, epochs=60, batch=32, lr=1e-3, seed=3)
+        losses = prop.train(stats, dims, targets, epochs=20, batch=64, lr=1e-3, seed=3)
         assert losses[-1] < 0.5 * losses[0]
         ctx.use_proposal(prop)
         first_plain, first_seed, it_plain, it_seed = [], [], [], []
-        for i in range(24):
-            d = 8 + (i % 4) * 8
-            X, lab = two_class_node(9000 + i, 800, d)
-            plain = ctx.node_split(S.make_params("gini", 2, seed=77 + i, **base), X, labels=lab,
-                                   node_uid=i, want_trace=True)
-            seeded = ctx.node_split(S.make_params("gini", 2, seed=77 + i, seeded=True, **base),
+        for i in range(32):
+            d = (8, 16, 32, 64)[i % 4]
+            X, lab = planted_node(90000 + i, d)
+            plain = ctx.node_split(S.make_params("entropy", 2, seed=77 + i, **base), X,
+                                   labels=lab, node_uid=i, want_trace=True)
+            seeded = ctx.node_split(S.make_params("entropy", 2, seed=77 + i, seeded=True, **base),
                                     X, labels=lab, node_uid=i, want_trace=True)
             target = plain["trace"][-1]
             first_plain.append(plain["trace"][0])
