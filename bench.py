@@ -15,7 +15,9 @@ nodes of n_node * P * (T+1), divided by the time.
 --workload selects another named setting of paper_2208_07023_gb300.workloads
 (regtree_n200k_d128: the regression tree, bfloat16 projection with top-8 FP32
 re-scoring by default; forest64_n100k_d32_k5: 64 bagged trees; node_n2000_d16:
-one node). --compare-fp32 also times the plain FP32 form of the same workload
+one node; proposal_n1m_d256_k20: the learned swarm proposal, trained first,
+then PSO iterations to the plain search's loss, seeded vs plain, over the
+first four levels of a 1,000,000 x 256, 20-class mixture). --compare-fp32 also times the plain FP32 form of the same workload
 and reports both forms' time and training loss.
 
 With N > 1 (torchrun) every rank grows its own tree on its own seed (weak
@@ -247,10 +249,11 @@ def tree_loss(ctx, f, wl, X):
         return {"tree0_mse": float(np.mean((pred - wl.y) ** 2)),
                 "ensemble_mse": float(np.mean((val - wl.y) ** 2))}
     K = wl.n_classes
-    gini = 0.0
-    for h in np.unique(lf):
-        c = np.bincount(wl.labels[lf == h], minlength=K).astype(np.float64)
-        gini += c.sum() - (c ** 2).sum() / c.sum()
+    c = np.bincount(lf.astype(np.int64) * K + wl.labels, minlength=(int(lf.max()) + 1) * K)
+    c = c.reshape(-1, K).astype(np.float64)
+    tot = c.sum(axis=1)
+    m = tot > 0
+    gini = float((tot[m] - (c[m] ** 2).sum(axis=1) / tot[m]).sum())
     return {"tree0_gini": gini / wl.n, "ensemble_error": float(np.mean(cls != wl.labels))}
 
 
@@ -324,6 +327,27 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
     return roofs
 
 
+def reduce_over_ranks(ms, evals, world, device):
+    """(the slowest rank's time, the evaluations of all ranks): each rank
+    grows its own trees, so the job's throughput is the total work over the
+    time of the slowest rank."""
+    if world <= 1:
+        return ms, float(evals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(evals)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item()
+
+
+def rank_seed(rank):
+    """Workload seed of a rank: every rank trains on its own data."""
+    return 1 + rank
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -344,7 +368,7 @@ def run_ours(args):
 
     name, proj, topk = args.workload, args.proj, args.topk
     cfg = W.SETTINGS[name]
-    wl = cfg["builder"](1 + rank)  # each rank: its own tree
+    wl = cfg["builder"](rank_seed(rank))  # each rank: its own tree
     X = torch.from_numpy(wl.X).cuda()
     L = torch.from_numpy(wl.labels).cuda() if wl.labels is not None else None
     Y = torch.from_numpy(wl.y).cuda() if wl.y is not None else None
@@ -376,15 +400,7 @@ def run_ours(args):
     ctx.profile(False)
 
     tot_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([tot_ms, float(evals)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        tot_ms_max, evals_all = mx[0].item(), sm[1].item()
-    else:
-        tot_ms_max, evals_all = tot_ms, float(evals)
+    tot_ms_max, evals_all = reduce_over_ranks(tot_ms, evals, world, "cuda")
     value = evals_all / (tot_ms_max / 1e3)
 
     # training loss of the trees this form grows
@@ -462,6 +478,171 @@ def run_ours(args):
     return 0
 
 
+def proposal_training_pairs(ctx, S, seed0, mixture_seed):
+    """(statistics, PSO-best direction) pairs: single-node pattern nodes
+    (d = 16..256), mixture subsets like the classification-tree workload
+    (d = 64, K = 10), and nodes of the evaluated mixture's distribution: the
+    same mixture parameters (means, covariance) with independently drawn
+    samples (sample seeds disjoint from the evaluated data), restricted to
+    random class subsets as a tree's nodes are."""
+    import numpy as np
+    stats, dims, targets = [], [], []
+
+    def add(X, lab, K, p, uid):
+        r = ctx.node_split(p, X, labels=lab, node_uid=uid)
+        st = ctx.node_stats(X, labels=lab, n_classes=K)
+        t = np.zeros(256, np.float32)
+        t[:X.shape[1]] = r["direction"]
+        stats.append(st)
+        dims.append(X.shape[1])
+        targets.append(t)
+
+    def subset(wl, K, rng, lo):
+        keep = rng.choice(K, rng.integers(lo, K + 1), replace=False)
+        m = np.isin(wl.labels, keep)
+        remap = np.full(K, -1, np.int32)
+        remap[np.sort(keep)] = np.arange(keep.size)
+        return wl.X[m], remap[wl.labels[m]]
+
+    rng = np.random.default_rng(seed0)
+    for i in range(300):
+        d = (16, 32, 64, 128, 256)[i % 5]
+        wl = W.single_node(2000, d, 0.05, seed=seed0 + i)
+        add(wl.X, wl.labels, 2, S.make_params("entropy", 2, n_particles=32, n_iters=50,
+                                              n_bins=64, min_leaf=1, seed=i + 1), i)
+    for i in range(100):
+        X, lab = subset(W.gmm(6000, 64, 10, seed=seed0 + 10_000 + i), 10, rng, 2)
+        add(X, lab, 10, S.make_params("gini", 10, n_particles=64, n_iters=50, n_bins=128,
+                                      min_leaf=20, seed=i + 7), i)
+    for i in range(600):
+        wl = W.gmm(20_000, 256, 20, seed=mixture_seed, sample_seed=seed0 + 20_000 + i)
+        X, lab = subset(wl, 20, rng, 12)
+        add(X, lab, 20, S.make_params("gini", 20, n_particles=64, n_iters=50, n_bins=128,
+                                      min_leaf=20, seed=i + 9,
+                                      proj=S.SLM_PROJ_BF16_TOPK, topk=8), i)
+    return (np.array(stats, np.float32), np.array(dims, np.int32),
+            np.array(targets, np.float32))
+
+
+def run_proposal_eval(args):
+    """The learned proposal on a large mixture: PSO iterations (seeded vs
+    plain) to reach the plain search's split loss, median over the internal
+    nodes of the first four levels of the plain tree."""
+    import numpy as np
+    import torch
+
+    from paper_2208_07023_gb300 import binding as S
+    cfg = W.SETTINGS[args.workload]
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(0, stream.cuda_stream)
+    t0 = time.perf_counter()
+    st, dims, tg = proposal_training_pairs(ctx, S, 500_000, mixture_seed=1)
+    t_pairs = time.perf_counter() - t0
+    prop = ctx.proposal(seed=11)
+    t0 = time.perf_counter()
+    losses = prop.train(st, dims, tg, epochs=30, batch=64, lr=1e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    wl = cfg["builder"](1)
+    X = torch.from_numpy(wl.X).cuda()
+    L = torch.from_numpy(wl.labels).cuda()
+    p = make_params(S, cfg, wl, args.proj, args.topk)
+    f = ctx.train_tree(p, X, labels=L)
+    g = f.export(0)
+    _, _, leaf = ctx.predict(f, X, want_leaf=True)
+    f.free()
+    leaf = leaf[:, 0].astype(np.int64)
+    inner = [int(h) for h in np.nonzero(g["kind"] == 1)[0] if h < 15]
+    ctx.use_proposal(prop)
+    rows = []
+    for h in inner:
+        node = leaf.copy()
+        member = node == h
+        while (node > h).any():
+            node = np.where(node > h, (node - 1) // 2, node)
+            member |= node == h
+        idx = torch.from_numpy(np.nonzero(member)[0].astype(np.int32)).cuda()
+        res = {}
+        for seeded in (False, True):
+            ps = make_params(S, cfg, wl, args.proj, args.topk)
+            ps.seeded = 1 if seeded else 0
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = ctx.node_split(ps, X, labels=L, sample_idx=idx, node_uid=h, want_trace=True)
+            e1.record(stream)
+            e1.synchronize()
+            res[seeded] = (r["trace"], e0.elapsed_time(e1))
+        target = res[False][0][-1]
+        it_plain = int(np.argmax(res[False][0] <= target))
+        hit = np.nonzero(res[True][0] <= target)[0]
+        # within 1e-3 of the plain final loss: on separable classes many
+        # class-group splits score within a few 1e-4 of each other
+        near_p = int(np.argmax(res[False][0] <= target + 1e-3))
+        near_s = np.nonzero(res[True][0] <= target + 1e-3)[0]
+        rows.append({"node": h, "n": int(idx.numel()), "iters_plain": it_plain,
+                     "iters_seeded": int(hit[0]) if hit.size else None,
+                     "iters_within_1e-3_plain": near_p,
+                     "iters_within_1e-3_seeded": int(near_s[0]) if near_s.size else None,
+                     "first_plain": float(res[False][0][0]), "first_seeded": float(res[True][0][0]),
+                     "final_plain": float(target), "final_seeded": float(res[True][0][-1]),
+                     "ms_plain": res[False][1], "ms_seeded": res[True][1]})
+    T = cfg["n_iters"]
+
+    def med(key):
+        return float(np.median([r[key] if r[key] is not None else T + 1 for r in rows]))
+
+    # whole trees: plain FP32 and plain BF16 against the seeded BF16 form, at
+    # T iterations and at T / 4
+    trees = {}
+    for name, proj, seeded, iters in (("plain_fp32", "fp32", False, T),
+                                      ("plain_bf16", "bf16", False, T),
+                                      ("seeded_bf16", "bf16", True, T),
+                                      ("seeded_bf16_T/4", "bf16", True, T // 4)):
+        ps = make_params(S, dict(cfg, n_iters=iters), wl, proj, args.topk)
+        ps.seeded = 1 if seeded else 0
+        ctx.train_tree(ps, X, labels=L).free()  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ft = ctx.train_tree(ps, X, labels=L)
+        e1.record(stream)
+        e1.synchronize()
+        trees[name] = dict(tree_loss(ctx, ft, wl, X), ms=e0.elapsed_time(e1), iters=iters,
+                           evaluations=ft.info()["evaluations"])
+        ft.free()
+    ctx.use_proposal(None)
+    prop.free()
+    head = trees["seeded_bf16"]
+    line = {"metric": METRIC, "value": head["evaluations"] / (head["ms"] / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": head["ms"],
+            "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+            "data": "synthetic (seeded, workloads.py)",
+            "config": config_dict(args.workload, cfg, wl, args.proj, args.topk, {
+                "step": "one seeded bf16 tree (the value); plain trees beside it",
+                "proposal": {
+                    "iterations_to_plain_loss_median": {
+                        "plain": med("iters_plain"), "seeded": med("iters_seeded"),
+                        "nodes": "internal nodes of the plain tree's first four levels; "
+                                 "T + 1 = never"},
+                    "iterations_to_within_1e-3_median": {
+                        "plain": med("iters_within_1e-3_plain"),
+                        "seeded": med("iters_within_1e-3_seeded")},
+                    "first_loss_median": {
+                        "plain": float(np.median([r["first_plain"] for r in rows])),
+                        "seeded": float(np.median([r["first_seeded"] for r in rows]))},
+                    "final_loss_median": {
+                        "plain": float(np.median([r["final_plain"] for r in rows])),
+                        "seeded": float(np.median([r["final_seeded"] for r in rows]))},
+                    "trees": trees,
+                    "nodes": rows, "training_pairs": int(dims.size),
+                    "pair_generation_s": t_pairs, "train_s": t_train,
+                    "epoch_loss_first_last": [float(losses[0]), float(losses[-1])]}})}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ncu_case(args):
     """The small case for full ncu captures of the scoring kernels: one search
     of the workload's root node with 3 iterations, a handful of launches."""
@@ -500,6 +681,8 @@ def main():
         return run_reference(args)
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.workload == "proposal_n1m_d256_k20":
+        return run_proposal_eval(args)
     return run_ours(args)
 
 

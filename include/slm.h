@@ -329,15 +329,19 @@ slm_status slm_proposal_train(slm_ctx* ctx, slm_proposal* prop,
                               int32_t batch, float lr, uint64_t seed,
                               double* epoch_loss);
 /* Searches of this context with params.seeded = 1 start each node's swarm
- * from prop: particle i at mu_hat + rho_i u_i / |u_i|, mu_hat = o[0:d]/|o[0:d]|,
- * rho_i = softplus(o[256 + i]); requires d <= 256, n_classes <= 20 (or MSE),
+ * from prop: particle i at sigma (mu_hat + rho_i u_i / |u_i|) (as
+ * slm_swarm_seed), mu_hat = o[0:d]/|o[0:d]|, rho_i = softplus(o[256 + i]);
+ * requires d <= 256, n_classes <= 20 (or MSE),
  * n_particles <= 64. The context does not own prop; NULL detaches it. */
 slm_status slm_use_proposal(slm_ctx* ctx, const slm_proposal* prop);
 /* The seeded positions pos[P x d] for given mu_hat[d] and rho[P] (host or
- * device): x_ij = mu_hat_j + rho_i (u_ij / |u_i|) in float, one rounding per
- * operation, u_ij = 2 U - 1 with U the swarm draw of purpose 6 at iteration 0
- * (slm_swarm_uniforms) and |u_i| the correctly rounded square root of a
- * sequential fused multiply-add sum of squares. */
+ * device): x_ij = sigma (mu_hat_j + rho_i (u_ij / |u_i|)) in float, one
+ * rounding per operation, u_ij = 2 U - 1 with U the swarm draw of purpose 6
+ * at iteration 0 (slm_swarm_uniforms), |u_i| the correctly rounded square
+ * root of a sequential fused multiply-add sum of squares and sigma =
+ * sqrt(d / 3) rounded from d / 3 rounded (the expected norm of a uniform
+ * start in [-1, 1)^d: seeded and random starts then have the same scale, and
+ * the start velocities the same relative size). */
 slm_status slm_swarm_seed(slm_ctx* ctx, uint64_t seed, uint32_t node_uid,
                           int32_t n_particles, int32_t d, const float* mu_hat,
                           const float* rho, float* pos);

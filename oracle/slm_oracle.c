@@ -1216,6 +1216,7 @@ void ora_swarm_seed(uint64_t seed, uint32_t node_uid, int32_t P, int32_t d,
   float* u = (float*)malloc(sizeof(float) * (size_t)P * d);
   if (!u) return;
   ora_swarm_uniforms(seed, node_uid, 0, P, d, ORA_PURPOSE_SEED, u);
+  const float sigma = sqrtf((float)d / 3.0f);
   for (int32_t i = 0; i < P; ++i) {
     float* ui = u + (int64_t)i * d;
     for (int32_t j = 0; j < d; ++j) ui[j] = 2.0f * ui[j] - 1.0f;
@@ -1224,7 +1225,7 @@ void ora_swarm_seed(uint64_t seed, uint32_t node_uid, int32_t P, int32_t d,
     const float nrm = sqrtf(acc);
     for (int32_t j = 0; j < d; ++j) {
       const float q = nrm > 0.0f ? ui[j] / nrm : 0.0f;
-      pos[(int64_t)i * d + j] = mu_hat[j] + rho[i] * q;
+      pos[(int64_t)i * d + j] = sigma * (mu_hat[j] + rho[i] * q);
     }
   }
   free(u);

@@ -214,10 +214,13 @@ int ora_mlp_loss_grad(const ora_mlp* m, const double* s, const int32_t* dims,
 void ora_adam_step(double* w, double* m, double* v, const double* g, int64_t n,
                    int32_t t, double lr, double beta1, double beta2, double eps);
 
-/* Seeded initial positions: x_i = mu_hat + rho_i u_i / |u_i| with u_ij =
- * 2 U - 1 of the swarm stream (purpose ORA_PURPOSE_SEED = 6, iteration 0),
- * in float, one rounding per operation; |u_i| = sqrtf of a sequential fmaf
- * sum of squares. pos[P*d]. */
+/* Seeded initial positions: x_i = sigma (mu_hat + rho_i u_i / |u_i|) with
+ * u_ij = 2 U - 1 of the swarm stream (purpose ORA_PURPOSE_SEED = 6,
+ * iteration 0) and sigma = sqrtf(d / 3.0f), the expected norm of a uniform
+ * start in [-1, 1)^d, so that the start velocities 0.1 U[-1, 1) have the
+ * same size relative to the positions as in a random start (the loss does
+ * not depend on the scale of a direction); in float, one rounding per
+ * operation; |u_i| = sqrtf of a sequential fmaf sum of squares. pos[P*d]. */
 void ora_swarm_seed(uint64_t seed, uint32_t node_uid, int32_t n_particles,
                     int32_t d, const float* mu_hat, const float* rho, float* pos);
 

@@ -6,7 +6,7 @@
 // variances, padded to 256 features x 20 classes + 1: 5376 inputs) to a
 // direction mu (256) and 64 spread radii: h1 = relu(s W1 + b1),
 // h2 = relu(h1 W2 + b2), o = h2 W3 + b3. A search seeded by it starts particle
-// i at mu_hat + rho_i u_i / |u_i| (mu_hat = mu / |mu| over the node's d
+// i at sigma (mu_hat + rho_i u_i / |u_i|) (mu_hat = mu / |mu| over the node's d
 // features, rho_i = softplus(o[256 + i]), u_i uniform in [-1, 1)^d from the
 // swarm stream), instead of uniformly in [-1, 1)^d (Sec. III-A's "preset
 // range"). The paper has no learned proposal; this is a way to start the
@@ -302,9 +302,11 @@ __global__ void k_glorot(float* w, int64_t n, uint32_t layer, float lim, uint64_
 
 // ---- seeded swarm ----------------------------------------------------------------
 
-// Particle i of node uid at mu_hat + rho u / |u|, u_j = 2 U - 1 of the swarm
-// stream (purpose 6, iteration 0): one rounding per operation, |u| = sqrt of
-// a sequential fused multiply-add sum of squares.
+// Particle i of node uid at sigma (mu_hat + rho u / |u|), u_j = 2 U - 1 of
+// the swarm stream (purpose 6, iteration 0), sigma = sqrt(d / 3) (the expected
+// norm of a uniform start in [-1, 1)^d, so the start velocities keep their
+// relative size; the loss is scale-invariant): one rounding per operation,
+// |u| = sqrt of a sequential fused multiply-add sum of squares.
 __device__ void seed_particle(uint64_t seed, uint32_t uid, int i, int d, const float* mu_hat,
                               float rho, float* pos) {
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -317,13 +319,14 @@ __device__ void seed_particle(uint64_t seed, uint32_t uid, int i, int d, const f
     }
   }
   const float nrm = __fsqrt_rn(acc);
+  const float sigma = __fsqrt_rn(__fdiv_rn((float)d, 3.0f));
   for (int q = 0; q < (d + 3) / 4; ++q) {
     const U4 r = philox4x32_10(uid, 0u, (uint32_t)i, (uint32_t)q | (6u << 24), k0, k1);
     for (int c = 0; c < 4 && 4 * q + c < d; ++c) {
       const int j = 4 * q + c;
       const float u = __fsub_rn(__fmul_rn(2.0f, uniform24(r.v[c])), 1.0f);
       const float qv = nrm > 0.0f ? __fdiv_rn(u, nrm) : 0.0f;
-      pos[j] = __fadd_rn(mu_hat[j], __fmul_rn(rho, qv));
+      pos[j] = __fmul_rn(sigma, __fadd_rn(mu_hat[j], __fmul_rn(rho, qv)));
     }
   }
 }
@@ -336,7 +339,7 @@ __global__ void k_seed_positions(uint64_t seed, uint32_t uid, int P, int d,
 }
 
 // The initial swarm of each node from the network's output prop[a][OUT]:
-// positions seeded around mu_hat, velocities 0.1 U[-1,1) as for random
+// positions seeded around sigma mu_hat, velocities 0.1 U[-1,1) as for random
 // starts, ranges / bests reset (as k_swarm_init).
 __global__ void __launch_bounds__(256)
     k_swarm_seed_init(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, SwarmCoef co,

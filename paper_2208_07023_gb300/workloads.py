@@ -73,12 +73,18 @@ def haar_orthogonal(rng: np.random.Generator, d: int) -> np.ndarray:
 
 def gmm(n: int, d: int, n_classes: int, seed: int = 1,
         mean_var: float = 2.0, lam_lo: float = 0.1,
-        lam_hi: float = 10.0) -> Workload:
-    """Gaussian mixture with a shared, randomly rotated covariance."""
+        lam_hi: float = 10.0, sample_seed=None) -> Workload:
+    """Gaussian mixture with a shared, randomly rotated covariance.
+
+    `seed` draws the mixture (means, rotation, spectrum) and, by default, the
+    samples too; a `sample_seed` draws the samples from a stream of their own,
+    so that independent sample sets of one mixture can be drawn."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x6A11]))
     means = rng.normal(0.0, np.sqrt(mean_var), (n_classes, d))
     q = haar_orthogonal(rng, d)
     lam = np.exp(rng.uniform(np.log(lam_lo), np.log(lam_hi), d))
+    if sample_seed is not None:
+        rng = np.random.default_rng(np.random.SeedSequence([seed, sample_seed, 0x5A3]))
     labels = rng.integers(0, n_classes, n).astype(np.int32)
     z = rng.standard_normal((n, d))
     X = means[labels] + (z * np.sqrt(lam)[None, :]) @ q.T
@@ -131,6 +137,12 @@ SETTINGS = {
         builder=lambda seed=1: tanh_regression(200_000, 128, 8, 0.1, seed),
         criterion="mse", n_particles=64, n_iters=80, n_bins=256,
         max_depth=10, min_leaf=20, n_trees=1, proj="bf16", topk=8),
+    # learned proposal evaluated on a large mixture: PSO iterations to reach
+    # the plain search's split loss over the nodes of the first four levels
+    "proposal_n1m_d256_k20": dict(
+        builder=lambda seed=1: gmm(1_000_000, 256, 20, seed),
+        criterion="gini", n_particles=64, n_iters=80, n_bins=128,
+        max_depth=12, min_leaf=20, n_trees=1, proj="bf16", topk=8),
     # bagged forest of 64 trees
     "forest64_n100k_d32_k5": dict(
         builder=lambda seed=1: gmm(100_000, 32, 5, seed),

@@ -201,8 +201,12 @@ def test_swarm_seed_rebuilt_from_the_stream():
     pos = O.swarm_seed(77, 5, P, d, mu, rho)
     u = O.swarm_uniforms(77, 5, 0, P, d, O.PURPOSE_SEED)
     u = (np.float32(2) * u - np.float32(1)).astype(np.float32)
+    sigma = np.sqrt(d / 3.0)  # expected norm of a uniform start in [-1, 1)^d
+    u_plain = O.swarm_uniforms(77, 5, 0, 4000, d, O.PURPOSE_INIT_X) * 2 - 1
+    assert np.linalg.norm(u_plain, axis=1).mean() == pytest.approx(sigma, rel=0.03)
     for i in range(P):
         nrm = np.float32(np.sqrt((u[i].astype(np.float64) ** 2).sum()))
-        want = (mu + rho[i] * (u[i] / nrm)).astype(np.float32)
+        want = (sigma * (mu + rho[i] * (u[i] / nrm))).astype(np.float32)
         assert np.allclose(pos[i], want, rtol=2e-6, atol=2e-6)
-        assert np.linalg.norm(pos[i].astype(np.float64) - mu) == pytest.approx(rho[i], rel=1e-5)
+        assert np.linalg.norm(pos[i].astype(np.float64) / sigma - mu) == pytest.approx(
+            rho[i], rel=1e-5)
