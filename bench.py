@@ -88,7 +88,7 @@ def traffic_per_launch(name, ks, workload):
     return TRAFFIC[name] * ks["pairs"] / max(1, ks["launches"])
 
 
-def config_dict(name, cfg, wl, proj, topk, extra=None):
+def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
     d = {"workload": name, "n": wl.n, "d": wl.d, "classes": wl.n_classes,
          "trees": cfg["n_trees"], "bootstrap": cfg["n_trees"] > 1,
          "max_depth": cfg["max_depth"], "min_leaf": cfg["min_leaf"],
@@ -97,6 +97,9 @@ def config_dict(name, cfg, wl, proj, topk, extra=None):
          "projection": ("bf16 tcgen05 + top-%d fp32 ffma re-scoring" % topk
                         if proj == "bf16" else "fp32 ffma"),
          "l2": "flushed between steps (256 MiB write outside the timed events)"}
+    if args_launch is not None:
+        d["search_loop_graphs"] = args_launch.graphs
+        d["projection_tile_mode"] = args_launch.tiles
     if extra:
         d.update(extra)
     return d
@@ -327,6 +330,15 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
     return roofs
 
 
+def apply_launch_options(ctx, args):
+    ctx.set_graphs(args.graphs == "on")
+    if args.tiles == "fixed":
+        ctx.set_tuning(False)
+    elif args.tiles != "auto":
+        v = [int(x) for x in args.tiles.split(":")]
+        ctx.force_tiles(v[0], v[1], bool(v[2]) if len(v) > 2 else False)
+
+
 def reduce_over_ranks(ms, evals, world, device):
     """(the slowest rank's time, the evaluations of all ranks): each rank
     grows its own trees, so the job's throughput is the total work over the
@@ -374,6 +386,7 @@ def run_ours(args):
     Y = torch.from_numpy(wl.y).cuda() if wl.y is not None else None
     stream = torch.cuda.current_stream()
     ctx = S.Context(local, stream.cuda_stream)
+    apply_launch_options(ctx, args)
     p = make_params(S, cfg, wl, proj, topk)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -409,7 +422,9 @@ def run_ours(args):
     f.free()
 
     extra = {"tree_train_ms": tot_ms_max / args.steps, "evals_per_step": evals // args.steps,
-             "wall_s": wall, "train_loss": loss}
+             "wall_s": wall, "train_loss": loss,
+             "search_loop": dict(ctx.graph_stats(), mode="one CUDA graph per level search"),
+             "projection_tiles": ctx.tuned_shapes()}
     if args.compare_fp32 and proj == "bf16":
         # the plain FP32 form of the same workload, same harness
         p32 = make_params(S, cfg, wl, "fp32", topk)
@@ -463,7 +478,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32" if proj == "bf16" else "f32",
             "data": "synthetic (seeded, workloads.py)",
-            "config": config_dict(name, cfg, wl, proj, topk, extra),
+            "config": config_dict(name, cfg, wl, proj, topk, extra, args),
             "clocks": clocks.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -645,18 +660,28 @@ def run_proposal_eval(args):
 
 def run_ncu_case(args):
     """The small case for full ncu captures of the scoring kernels: one search
-    of the workload's root node with 3 iterations, a handful of launches."""
+    of the workload's root node with 3 iterations, a handful of launches (for
+    a forest: the root level of every tree, one batched search, as the
+    forest's first level runs it, tiles tuned first)."""
     import torch
 
     from paper_2208_07023_gb300 import binding as S
     cfg = W.SETTINGS[args.workload]
     wl = cfg["builder"](1)
     ctx = S.Context(0, torch.cuda.current_stream().cuda_stream)
+    apply_launch_options(ctx, args)
     p = make_params(S, cfg, wl, args.proj, args.topk)
     p.n_iters = 3
-    r = ctx.node_split(p, wl.X, labels=wl.labels, y=wl.y)
-    print(json.dumps({"ncu_case": args.workload, "proj": args.proj, "loss": r["loss"],
-                      "bin": r["bin"]}), flush=True)
+    if cfg["n_trees"] > 1:
+        p.max_depth = 1
+        f = ctx.forest_begin(p, wl.X, labels=wl.labels, y=wl.y)
+        n_split = f.grow_level()
+        f.free()
+        out = {"n_split": n_split, "tiles": ctx.tuned_shapes()}
+    else:
+        r = ctx.node_split(p, wl.X, labels=wl.labels, y=wl.y)
+        out = {"loss": r["loss"], "bin": r["bin"]}
+    print(json.dumps(dict({"ncu_case": args.workload, "proj": args.proj}, **out)), flush=True)
     ctx.close()
     return 0
 
@@ -672,6 +697,11 @@ def main():
     ap.add_argument("--topk", type=int, default=8)
     ap.add_argument("--compare-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graphs", choices=["on", "off"], default="on",
+                    help="record each search's iteration loop as one CUDA graph")
+    ap.add_argument("--tiles", default="auto",
+                    help="projection tiles: auto (tuned), fixed (16 particles, 2 CTAs/SM) "
+                         "or PG:CPS[:GATHER]")
     ap.add_argument("--ncu-case", action="store_true",
                     help="one root-node search with 3 iterations (small case for ncu)")
     args = ap.parse_args()

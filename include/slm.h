@@ -375,8 +375,52 @@ slm_status slm_profile(slm_ctx* ctx, int on);
  * scored (scoring kernels; 0 for the others). Synchronises the stream. */
 slm_status slm_kernel_stats(slm_ctx* ctx, int32_t kernel, int64_t* launches,
                             double* total_ms, double* pairs);
-/* Kernels launched by the context since its creation. */
+/* Kernels launched by the context since its creation (a kernel run as a
+ * node of a graph counts as one launch). */
 slm_status slm_launch_count(slm_ctx* ctx, int64_t* launches);
+
+/* Projection tiles. on = 1 (the default): the FP32 projection of a search
+ * runs with the tile shape (particles per group: 8, 16, 24, 32 or 48 dividing
+ * P rounded up to 16; 1 or 2 CTAs per SM; rows from the level copy or, in
+ * bagged forests, gathered from the base rows) that was fastest when the first
+ * search of the same shape (d, padded P, log2 of the 256-row tiles) timed
+ * every candidate on its own batch; the choice is kept by the context.
+ * on = 0: 16 particles per group, 2 CTAs per SM. Results are identical for
+ * every tile shape. SLM_EINVAL for other values. */
+slm_status slm_set_tuning(slm_ctx* ctx, int32_t on);
+/* Forces one tile shape for later searches (pg = 0 clears); gather = 1 reads
+ * gathered base rows where a forest keeps them (elsewhere the level copy is
+ * the only source). SLM_EINVAL for shapes outside the list above, and from a
+ * search whose padded P pg does not divide. */
+slm_status slm_force_tiles(slm_ctx* ctx, int32_t pg, int32_t ctas_per_sm, int32_t gather);
+/* Shapes tuned so far and the tiles of the last search (any may be NULL). */
+slm_status slm_tuning_stats(slm_ctx* ctx, int64_t* shapes, int32_t* last_pg,
+                            int32_t* last_ctas_per_sm);
+/* The tuned shapes: *n receives their number; the first max are written to
+ * the arrays (any may be NULL): features d, padded P, log2 of the row tiles,
+ * the chosen particles per group, CTAs per SM and row source (1: gathered
+ * from the base rows by sample id, 0: the level's entry-ordered copy), and
+ * the chosen candidate's time for two projections (ms). Bagged forests whose
+ * base rows fit in a quarter of L2 keep a copy of them, which makes the
+ * gathered source a candidate for their levels. */
+slm_status slm_tuned_shapes(slm_ctx* ctx, int32_t max, int32_t* n, int32_t* d,
+                            int32_t* padded_p, int32_t* tiles_log2, int32_t* pg,
+                            int32_t* ctas_per_sm, int32_t* gather, float* ms);
+
+/* on = 1 (the default): the T + 1 scoring passes of every search (one node,
+ * or all nodes of a level across all trees; Algorithm 1's loop) run as one
+ * CUDA graph launch. The context keeps up to 64 executable graphs: a search
+ * with exactly the launch inputs of a kept graph (sizes, parameters, tiles
+ * and buffers) launches it again without recording; otherwise the passes are
+ * recorded and a kept graph with the same launch shapes is updated in place,
+ * or a new one is instantiated. on = 0: the passes are launched one by one.
+ * Results are identical either way; per-launch profiling (slm_profile)
+ * always launches one by one. SLM_EINVAL for other values. */
+slm_status slm_set_graphs(slm_ctx* ctx, int32_t on);
+/* Graph launches of the context: in total, of kept graphs launched again
+ * unchanged, updated in place, and instantiated anew (any may be NULL). */
+slm_status slm_graph_stats(slm_ctx* ctx, int64_t* launches, int64_t* reuses,
+                           int64_t* updates, int64_t* instantiations);
 
 #ifdef __cplusplus
 }

@@ -93,6 +93,12 @@ def lib():
             "slm_profile": ([vp, C.c_int], C.c_int),
             "slm_kernel_stats": ([vp, i32, P(i64), P(C.c_double), P(C.c_double)], C.c_int),
             "slm_launch_count": ([vp, P(i64)], C.c_int),
+            "slm_set_graphs": ([vp, i32], C.c_int),
+            "slm_set_tuning": ([vp, i32], C.c_int),
+            "slm_force_tiles": ([vp, i32, i32, i32], C.c_int),
+            "slm_tuning_stats": ([vp, P(i64), P(i32), P(i32)], C.c_int),
+            "slm_tuned_shapes": ([vp, i32, P(i32), vp, vp, vp, vp, vp, vp, vp], C.c_int),
+            "slm_graph_stats": ([vp, P(i64), P(i64), P(i64), P(i64)], C.c_int),
             "slm_evaluate_swarm_noalloc": ([C.c_int, vp, P(slm_params), vp, i64, i32, vp, vp,
                                             vp, vp, i64, vp, i32, vp], C.c_int),
             "slm_node_stats": ([vp, vp, i64, i32, vp, i32, vp, vp, vp, i64, vp], C.c_int),
@@ -323,6 +329,39 @@ class Context:
         n = C.c_int64()
         self._check(lib().slm_launch_count(self.handle, C.byref(n)))
         return n.value
+
+    def set_tuning(self, on: bool):
+        self._check(lib().slm_set_tuning(self.handle, 1 if on else 0))
+
+    def force_tiles(self, pg: int = 0, ctas_per_sm: int = 0, gather: bool = False):
+        self._check(lib().slm_force_tiles(self.handle, pg, ctas_per_sm, 1 if gather else 0))
+
+    def tuning_stats(self) -> dict:
+        n, pg, cps = C.c_int64(), C.c_int32(), C.c_int32()
+        self._check(lib().slm_tuning_stats(self.handle, C.byref(n), C.byref(pg), C.byref(cps)))
+        return {"shapes": n.value, "last_pg": pg.value, "last_ctas_per_sm": cps.value}
+
+    def tuned_shapes(self) -> list:
+        n = C.c_int32()
+        self._check(lib().slm_tuned_shapes(self.handle, 0, C.byref(n), None, None, None, None,
+                                           None, None, None))
+        m = n.value
+        cols = [np.zeros(m, np.int32) for _ in range(6)] + [np.zeros(m, np.float32)]
+        self._check(lib().slm_tuned_shapes(self.handle, m, C.byref(n),
+                                           *[_ptr(a) for a in cols]))
+        names = ("d", "padded_p", "tiles_log2", "pg", "ctas_per_sm", "gather", "ms")
+        return [{k: (float(a[i]) if k == "ms" else int(a[i])) for k, a in zip(names, cols)}
+                for i in range(m)]
+
+    def set_graphs(self, on: bool):
+        self._check(lib().slm_set_graphs(self.handle, 1 if on else 0))
+
+    def graph_stats(self) -> dict:
+        a, r, b, c = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(lib().slm_graph_stats(self.handle, C.byref(a), C.byref(r), C.byref(b),
+                                          C.byref(c)))
+        return {"launches": a.value, "reuses": r.value, "updates": b.value,
+                "instantiations": c.value}
 
     # -- raw draws -------------------------------------------------------
     def swarm_uniforms(self, seed, node_uid, t, n_particles, d, purpose):

@@ -14,8 +14,8 @@
 // with entry-aligned labels / targets / multiplicities. One iteration is two
 // kernels plus the swarm update:
 //  * k_project: z[p][e] = X_l[e] . x_p for all entries and particles, once.
-//    A persistent grid walks (tile of kTS = 256 rows, group of kPG = 16
-//    particles) work units; rows and positions stream through shared memory
+//    A persistent grid walks (tile of kTS = 256 rows, group of PG = 8..48
+//    particles, picked per problem shape by the autotuner) work units; rows and positions stream through shared memory
 //    in kKC = 32-feature chunks with double-buffered cp.async copies. Each
 //    thread owns a 4 x 4 register tile (rows w*32 + sg + 8i, particles
 //    pg + 4j) and accumulates over the features in increasing order, so every
@@ -340,7 +340,12 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // ---- projection -------------------------------------------------------------------
 
-constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPG * kXS);
+constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPGMax * kXS);
+
+// Row of entry e (e < pr.E): gathered from the base rows when pr.gidx is set.
+__device__ __forceinline__ const float* row_of(const Problem& pr, int64_t e) {
+  return pr.gidx ? pr.Xg + (int64_t)__ldg(pr.gidx + e) * pr.d : pr.X + e * pr.d;
+}
 
 // Stages one kKC-feature chunk of a work unit's rows and PG positions.
 template <int PG>
@@ -354,41 +359,44 @@ __device__ __forceinline__ void stage_chunk(const Problem& pr, const Swarm& sw,
     for (int q = threadIdx.x; q < kTS * (kKC / 4); q += kThreads) {
       const int r = q >> 3, cc = (q & 7) * 4;
       const bool ok = r < wt.rows && cc < kc;
-      const float* src = ok ? pr.X + (int64_t)(wt.row0 + r) * d + k0 + cc : pr.X;
+      const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
       cp_async16(xb + r * kXS + cc, src, ok ? 16 : 0);
     }
     for (int q = threadIdx.x; q < PG * (kKC / 4); q += kThreads) {
       const int p = q >> 3, cc = (q & 7) * 4;
-      const bool ok = cc < kc;
+      const bool ok = cc < kc && g * PG + p < pr.Pp;
       cp_async16(ab + p * kXS + cc, ok ? pos + (int64_t)p * d + k0 + cc : pos, ok ? 16 : 0);
     }
   } else {
     for (int q = threadIdx.x; q < kTS * kKC; q += kThreads) {
       const int r = q >> 5, cc = q & 31;
       const bool ok = r < wt.rows && cc < kc;
-      const float* src = ok ? pr.X + (int64_t)(wt.row0 + r) * d + k0 + cc : pr.X;
+      const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
       cp_async4(xb + r * kXS + cc, src, ok ? 4 : 0);
     }
     for (int q = threadIdx.x; q < PG * kKC; q += kThreads) {
       const int p = q >> 5, cc = q & 31;
-      const bool ok = cc < kc;
+      const bool ok = cc < kc && g * PG + p < pr.Pp;
       cp_async4(ab + p * kXS + cc, ok ? pos + (int64_t)p * d + k0 + cc : pos, ok ? 4 : 0);
     }
   }
   cp_async_commit();
 }
 
-// PG particles per work unit (16, or 8 for a small re-scored subset): each
-// thread owns 4 rows x PG/4 particles.
+// PG particles per work unit (8, 16, 24, 32 or 48; G = Pp / PG groups): each
+// thread owns 4 rows x PG/4 particles. Wider groups read a tile's rows once
+// for more particles (fewer passes over rows that do not stay in L2);
+// narrower ones give more units to spread over the SMs.
 template <int PG>
 __global__ void __launch_bounds__(kThreads, 2)
     k_project(Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, int n_units) {
   constexpr int PJ = PG / 4;
+  static_assert(PG % 8 == 0 && PG <= kPGMax, "particle group");
   extern __shared__ __align__(16) float smf[];
   float* xs0 = smf;
   float* xs1 = smf + kTS * kXS;
   float* as0 = smf + 2 * kTS * kXS;
-  float* as1 = as0 + kPG * kXS;
+  float* as1 = as0 + kPGMax * kXS;
   pdl_trigger();
   pdl_wait();
   if ((int)blockIdx.x >= n_units) return;
@@ -428,22 +436,46 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int kc4 = (min(kKC, d - c * kKC) + 3) & ~3;
     const float* xr = xb + (warp * 32 + sg) * kXS;
     const float* ar = ab + pg * kXS;
+    if constexpr (PJ <= 4) {
 #pragma unroll 2
-    for (int k = 0; k < kc4; k += 4) {
-      float4 xv[4], av[PJ];
+      for (int k = 0; k < kc4; k += 4) {
+        float4 xv[4], av[PJ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
+        for (int i = 0; i < 4; ++i)
+          xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
 #pragma unroll
-      for (int j = 0; j < PJ; ++j) av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+        for (int j = 0; j < PJ; ++j)
+          av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) {
+            acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
+          }
+      }
+    } else {
+      // wide groups: one particle's 4 features at a time keeps the live
+      // registers at the accumulators plus one row and one position vector
+      for (int k = 0; k < kc4; k += 4) {
+        float4 xv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
 #pragma unroll
         for (int j = 0; j < PJ; ++j) {
-          acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
-          acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
-          acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
-          acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
+          const float4 av = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].x, av.x, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].y, av.y, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].z, av.z, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].w, av.w, acc[i][j]);
+          }
         }
+      }
     }
     if (c == nk - 1) {
       // tile complete: fold the range, store z
@@ -1162,13 +1194,13 @@ static size_t hist_smem_bytes(const Problem& pr) {
 }
 
 cudaError_t prepare_eval_kernels(const Problem& pr) {
-  cudaError_t e = cudaFuncSetAttribute(k_project<16>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kProjSmem);
-  if (e) return e;
-  if ((e = cudaFuncSetAttribute(k_project<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kProjSmem)))
-    return e;
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {(const void*)k_project<8>, (const void*)k_project<16>,
+                        (const void*)k_project<24>, (const void*)k_project<32>,
+                        (const void*)k_project<48>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kProjSmem)))
+      return e;
   if ((e = cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hist_smem_bytes(pr))))
     return e;
@@ -1183,8 +1215,18 @@ cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
   return cudaGetLastError();
 }
 
-cudaError_t launch_project(const Problem& pr, const Swarm& sw, const WorkTile* tiles,
-                           int n_tiles, int grid_cap, cudaStream_t st) {
+bool project_group_ok(const Problem& pr, int pg) {
+  return (pg == 8 || pg == 16 || pg == 24 || pg == 32 || pg == 48) && pr.Pp % pg == 0;
+}
+
+cudaError_t launch_project(const Problem& pr_in, const Swarm& sw, const WorkTile* tiles,
+                           int n_tiles, int grid_cap, cudaStream_t st, int pg, bool gather) {
+  Problem pr = pr_in;
+  if (!gather || !pr.Xg) pr.gidx = nullptr;
+  if (pg > 0) {
+    if (!project_group_ok(pr, pg)) return cudaErrorInvalidValue;
+    pr.G = pr.Pp / pg;
+  }
   const int n_units = n_tiles * pr.G;
   if (n_units <= 0) return cudaSuccess;
   const int grid = n_units < grid_cap ? n_units : grid_cap;
@@ -1198,8 +1240,14 @@ cudaError_t launch_project(const Problem& pr, const Swarm& sw, const WorkTile* t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (pr.Pp == 8 * pr.G) return cudaLaunchKernelEx(&cfg, k_project<8>, pr, sw, tiles, n_units);
-  return cudaLaunchKernelEx(&cfg, k_project<16>, pr, sw, tiles, n_units);
+  switch (pr.Pp / pr.G) {
+    case 8: return cudaLaunchKernelEx(&cfg, k_project<8>, pr, sw, tiles, n_units);
+    case 16: return cudaLaunchKernelEx(&cfg, k_project<16>, pr, sw, tiles, n_units);
+    case 24: return cudaLaunchKernelEx(&cfg, k_project<24>, pr, sw, tiles, n_units);
+    case 32: return cudaLaunchKernelEx(&cfg, k_project<32>, pr, sw, tiles, n_units);
+    case 48: return cudaLaunchKernelEx(&cfg, k_project<48>, pr, sw, tiles, n_units);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_cluster) {

@@ -6,10 +6,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <numeric>
 #include <random>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "slm_internal.cuh"
@@ -58,6 +60,37 @@ struct slm_ctx {
   double k_ms[SLM_K_COUNT] = {};
   double k_pairs[SLM_K_COUNT] = {};
   const slm_proposal* prop = nullptr;  // seeds searches with params.seeded
+  // projection tiles: picked per problem shape by timing the candidates on
+  // the first search of that shape (tune = 1), or fixed (tune = 0)
+  struct Tiles {
+    int pg = kPG;        // particles per group
+    int cps = 2;         // CTAs per SM of the persistent grid
+    float ms = 0.f;      // tuned: time of two projections with these tiles
+    bool gather = false; // rows gathered from the base rows by sample id
+  };
+  int tune = 1;
+  Tiles forced{0, 0};
+  std::map<uint64_t, Tiles> tuned;
+  Tiles cur{};   // tiles of the search in flight
+  Tiles last{};  // tiles of the last search
+  // a search's iteration loop as one CUDA graph launch (reused executable)
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;  // records graphs (the caller's stream may
+                                      // be the legacy default stream)
+  // executable graphs by launch signature (every kernel node's function,
+  // grid, block, shared memory and cluster shape, in order): a new capture
+  // with a known signature differs only in kernel arguments and updates that
+  // executable in place
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::string key;            // launch inputs it was last recorded from
+    std::vector<uint64_t> sig;  // launch signature
+    int64_t launches = 0;       // kernel launches per graph launch
+    int64_t k_launches[SLM_K_COUNT] = {};
+    double k_pairs[SLM_K_COUNT] = {};
+  };
+  std::vector<GraphEntry> graph_cache;
+  int64_t graph_launches = 0, graph_reuses = 0, graph_updates = 0, graph_instantiations = 0;
 };
 
 // Learned swarm proposal: FP32 parameters, their bfloat16 copies, gradients
@@ -80,7 +113,10 @@ struct slm_forest {
   int H = 0;
   int n_trees = 0;
   int K = 0;
-  const float* X = nullptr;  // original rows (prediction)
+  // the base rows, kept by bagged forests whose rows fit in a quarter of L2:
+  // a level's FP32 projection may gather them by sample id instead of
+  // reading the level's entry-ordered copy (which holds each tree's rows)
+  const float* X = nullptr;
   DevBuf own_X;
   TreeArrays tr{};
   DevBuf tree_mem;
@@ -494,7 +530,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
   const int A = (int)nodes.size();
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
-  const int cap = 2 * c->n_sm;
+  const int cap = c->cur.cps * c->n_sm;
   if (bp && bp->on) {
     // bfloat16 scores of every particle on the tensor cores
     const Bf16Plan& b = *bp;
@@ -531,8 +567,9 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
     return SLM_OK;
   }
   if (n_tiles)
-    CK(launch(c, SLM_K_PROJECT, pairs,
-              [&] { return launch_project(pr, sw, dt, n_tiles, cap, c->stream); }));
+    CK(launch(c, SLM_K_PROJECT, pairs, [&] {
+      return launch_project(pr, sw, dt, n_tiles, cap, c->stream, c->cur.pg, c->cur.gather);
+    }));
   CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
     return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
   }));
@@ -590,6 +627,230 @@ slm_status seed_swarms(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc
   return SLM_OK;
 }
 
+// Projection tiles of a search's FP32 pass: forced, fixed, cached for the
+// shape (d, padded P, whether base rows can be gathered, log2 of the row
+// tiles), or tuned now: every candidate (particles per group 8 / 16 / 24 / 32
+// / 48 dividing Pp, x 1 or 2 CTAs per SM, x rows from the level copy or
+// gathered from the base rows when the forest keeps them) projects the
+// batch's current positions (once to warm, then twice between events) and
+// the fastest is kept for the shape. The candidates
+// compute the same z and ranges (each z is the same sequence of fused
+// multiply-adds), so the extra passes change nothing the search reads.
+slm_status pick_tiles(slm_ctx* c, const Problem& pr, const Swarm& sw, int n_tiles,
+                      slm_ctx::Tiles* out) {
+  if (c->forced.pg) {
+    if (!project_group_ok(pr, c->forced.pg))
+      return fail(c, SLM_EINVAL, "forced particle group does not divide the padded swarm");
+    *out = c->forced;
+    return SLM_OK;
+  }
+  *out = slm_ctx::Tiles{};
+  if (!c->tune || n_tiles <= 0) return SLM_OK;
+  int lg = 0;
+  while ((1 << lg) < n_tiles) ++lg;
+  const bool can_gather = pr.Xg && pr.gidx;
+  const uint64_t key = ((uint64_t)pr.d << 40) | ((uint64_t)pr.Pp << 16) |
+                       ((uint64_t)can_gather << 15) | (uint64_t)lg;
+  auto it = c->tuned.find(key);
+  if (it != c->tuned.end()) {
+    *out = it->second;
+    return SLM_OK;
+  }
+  const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  if (!e0 || !e1) return fail(c, SLM_ECUDA, "cudaEventCreate");
+  float best = 0.f;
+  slm_ctx::Tiles pick{};
+  bool have = false;
+  slm_status s = SLM_OK;
+  for (int pg : {8, 16, 24, 32, 48}) {
+    if (!project_group_ok(pr, pg)) continue;
+    for (int v = 0; v < (can_gather ? 4 : 2) && !s; ++v) {
+      const int cps = 1 + (v & 1);
+      const bool gather = v >= 2;
+      cudaError_t e = cudaSuccess;
+      for (int r = 0; r < 3 && !e; ++r) {
+        if (r == 1) e = cudaEventRecord(e0, c->stream);
+        if (!e) e = launch_project(pr, sw, dt, n_tiles, cps * c->n_sm, c->stream, pg, gather);
+        c->launches += 1;
+      }
+      if (!e) e = cudaEventRecord(e1, c->stream);
+      if (!e) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e) {
+        s = cuda_fail(c, e, "projection tile tuning");
+        break;
+      }
+      if (!have || ms < best) {
+        best = ms;
+        pick = slm_ctx::Tiles{pg, cps, ms, gather};
+        have = true;
+      }
+    }
+  }
+  c->free_events.push_back(e0);
+  c->free_events.push_back(e1);
+  if (s) return s;
+  c->tuned[key] = pick;
+  *out = pick;
+  return SLM_OK;
+}
+
+constexpr size_t kMaxGraphs = 64;  // executable graphs kept per context
+
+// Launch signature of a captured graph: per node in the graph's order, its
+// type and, for kernels, function, grid, block, dynamic shared memory and
+// cluster shape. Executables are only updated in place from a capture with
+// the same signature, so an update changes kernel arguments and nothing else.
+cudaError_t graph_signature(cudaGraph_t g, std::vector<uint64_t>* sig) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && (e = cudaGraphGetNodes(g, nodes.data(), &n))) return e;
+  sig->clear();
+  sig->reserve(6 * n + 1);
+  sig->push_back(n);
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if ((e = cudaGraphNodeGetType(nd, &ty))) return e;
+    sig->push_back((uint64_t)ty);
+    if (ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp{};
+    if ((e = cudaGraphKernelNodeGetParams(nd, &kp))) return e;
+    cudaLaunchAttributeValue cl{};
+    if ((e = cudaGraphKernelNodeGetAttribute(nd, cudaLaunchAttributeClusterDimension, &cl)))
+      return e;
+    sig->push_back((uint64_t)(uintptr_t)kp.func);
+    sig->push_back(((uint64_t)kp.gridDim.x << 32) | ((uint64_t)kp.gridDim.y << 16) |
+                   kp.gridDim.z);
+    sig->push_back(((uint64_t)kp.blockDim.x << 32) | ((uint64_t)kp.blockDim.y << 16) |
+                   kp.blockDim.z);
+    sig->push_back(((uint64_t)kp.sharedMemBytes << 24) | ((uint64_t)cl.clusterDim.x << 16) |
+                   ((uint64_t)cl.clusterDim.y << 8) | cl.clusterDim.z);
+  }
+  return cudaSuccess;
+}
+
+// The T + 1 scoring passes of a search (Algorithm 1's loop). With graphs on
+// (and per-launch profiling off) the passes run as one CUDA graph launch: the
+// device runs the whole loop of a level without waiting on the host. The
+// context keeps executable graphs: one recorded from the same launch inputs
+// (`key`: every field of the problem, swarm, plan and tiles, and the buffers
+// the launches read) is launched again as it is; otherwise the passes are
+// recorded, and an executable with the same launch signature is updated in
+// place (kernel arguments only), or a new one is instantiated.
+template <class F>
+slm_status run_iterations(slm_ctx* c, int T, const std::string& key, F&& pass) {
+  if (!c->graphs || c->prof) {
+    for (int t = 0; t <= T; ++t)
+      if (slm_status s = pass(t)) return s;
+    return SLM_OK;
+  }
+  for (slm_ctx::GraphEntry& ge : c->graph_cache)
+    if (ge.key == key) {
+      CK(cudaGraphLaunch(ge.exec, c->stream));
+      c->launches += ge.launches;
+      for (int k = 0; k < SLM_K_COUNT; ++k) {
+        c->k_launches[k] += ge.k_launches[k];
+        c->k_pairs[k] += ge.k_pairs[k];
+      }
+      c->graph_launches += 1;
+      c->graph_reuses += 1;
+      return SLM_OK;
+    }
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  // the passes are recorded on the context's own stream (recording runs
+  // nothing) and the graph is launched on the caller's stream
+  slm_ctx::GraphEntry rec;
+  rec.key = key;
+  rec.launches = c->launches;
+  for (int k = 0; k < SLM_K_COUNT; ++k) {
+    rec.k_launches[k] = c->k_launches[k];
+    rec.k_pairs[k] = c->k_pairs[k];
+  }
+  const cudaStream_t user = c->stream;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap_stream;
+  slm_status s = SLM_OK;
+  for (int t = 0; t <= T && !s; ++t) s = pass(t);
+  c->stream = user;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (s || e) {
+    if (g) cudaGraphDestroy(g);
+    return s ? s : cuda_fail(c, e, "cudaStreamEndCapture");
+  }
+  rec.launches = c->launches - rec.launches;
+  for (int k = 0; k < SLM_K_COUNT; ++k) {
+    rec.k_launches[k] = c->k_launches[k] - rec.k_launches[k];
+    rec.k_pairs[k] = c->k_pairs[k] - rec.k_pairs[k];
+  }
+  cudaError_t ei = graph_signature(g, &rec.sig);
+  slm_ctx::GraphEntry* hit = nullptr;
+  if (!ei)
+    for (slm_ctx::GraphEntry& ge : c->graph_cache)
+      if (ge.sig == rec.sig) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ge.exec, g, &info) == cudaSuccess) {
+          rec.exec = ge.exec;
+          ge = std::move(rec);
+          hit = &ge;
+        } else {
+          (void)cudaGetLastError();
+        }
+        break;
+      }
+  if (!ei && !hit) {
+    if (c->graph_cache.size() >= kMaxGraphs) {
+      cudaGraphExecDestroy(c->graph_cache.front().exec);  // freed after in-flight launches
+      c->graph_cache.erase(c->graph_cache.begin());
+    }
+    for (size_t i = 0; i < c->graph_cache.size(); ++i)  // a failed update's entry
+      if (c->graph_cache[i].sig == rec.sig) {
+        cudaGraphExecDestroy(c->graph_cache[i].exec);
+        c->graph_cache.erase(c->graph_cache.begin() + (long)i);
+        break;
+      }
+    ei = cudaGraphInstantiate(&rec.exec, g, 0);
+    if (!ei) {
+      c->graph_cache.push_back(std::move(rec));
+      hit = &c->graph_cache.back();
+      c->graph_instantiations += 1;
+    }
+  } else if (hit) {
+    c->graph_updates += 1;
+  }
+  cudaGraphDestroy(g);
+  if (ei) return cuda_fail(c, ei, "graph instantiation");
+  c->graph_launches += 1;
+  CK(cudaGraphLaunch(hit->exec, c->stream));
+  return SLM_OK;
+}
+
+// Appends the raw bytes of scalars and pointers: the launch inputs of a
+// search, compared whole to find a graph recorded from the same inputs.
+struct KeyWriter {
+  std::string b;
+  template <class T>
+  void put(const T& v) {
+    static_assert(std::is_arithmetic<T>::value || std::is_pointer<T>::value, "scalar");
+    b.append(reinterpret_cast<const char*>(&v), sizeof(T));
+  }
+  void problem(const Problem& p) {
+    put(p.X); put(p.Xg); put(p.gidx); put(p.lab); put(p.y); put(p.w); put(p.E); put(p.Ez);
+    put(p.d); put(p.crit); put(p.K); put(p.B); put(p.min_leaf); put(p.P); put(p.Pp);
+    put(p.G); put(p.Xb); put(p.dp); put(p.m1); put(p.m2); put(p.mscale);
+  }
+  void swarm(const Swarm& w) {
+    put(w.pos); put(w.vel); put(w.pbest); put(w.gbest); put(w.cur); put(w.pb); put(w.gb);
+    put(w.gpart); put(w.giter); put(w.trace); put(w.zmm); put(w.z); put(w.done); put(w.err);
+    put(w.T); put(w.sel); put(w.k); put(w.tk_sel); put(w.tk_inv); put(w.tk_pos);
+    put(w.tk_k); put(w.tk_kp); put(w.posb);
+  }
+};
+
 // PSO search of every node of a batch (Algorithm 1, synchronous updates).
 slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
@@ -614,9 +875,32 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
               [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
   }
   const int S = batch_split(c, pr, nodes);
-  for (int t = 0; t <= p->n_iters; ++t)
-    if ((s = score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp)))
-      return s;
+  slm_ctx::Tiles tl{};
+  if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
+  c->cur = tl;
+  c->last = tl;
+  std::string key;
+  if (c->graphs && !c->prof) {
+    KeyWriter kw;
+    kw.problem(pr);
+    kw.swarm(sw);
+    kw.put(A); kw.put((int)tiles.size()); kw.put(S); kw.put(p->n_iters); kw.put(c->n_sm);
+    kw.put(co.inertia); kw.put(co.c1); kw.put(co.c2); kw.put(co.seed);
+    kw.put(tl.pg); kw.put(tl.cps); kw.put(tl.gather); kw.put(pairs);
+    kw.put(dn); kw.put(ws_ptr<WorkTile>(c, S_TILES)); kw.put(ws_ptr<WorkTile>(c, S_MTILES));
+    kw.put(bp.on); kw.put(bp.k); kw.put(bp.kp); kw.put(bp.n_mtiles); kw.put(bp.grid);
+    kw.put(bp.S_k); kw.put(bp.pairs_k); kw.put(bp.posb); kw.put(bp.sel); kw.put(bp.inv);
+    if (bp.on) {
+      kw.problem(bp.pr_k);
+      kw.swarm(bp.sw_k);
+    }
+    key = std::move(kw.b);
+  }
+  s = run_iterations(c, p->n_iters, key, [&](int t) {
+    return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp);
+  });
+  c->cur = slm_ctx::Tiles{};
+  if (s) return s;
   sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
   *sw_out = sw;
   return SLM_OK;
@@ -714,6 +998,8 @@ void slm_destroy(slm_ctx* c) {
     cudaEventDestroy(p.b);
   }
   for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
+  for (auto& ge : c->graph_cache) cudaGraphExecDestroy(ge.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -1044,6 +1330,14 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return bail(s);
   if ((s = validate_inputs(c, dlab, n, p->n_classes, nullptr, 0))) return bail(s);
   if ((s = forest_alloc_trees(c, f))) return bail(s);
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess) l2 = 0;
+  const size_t xbytes = sizeof(float) * (size_t)n * d;
+  if (!bf16 && p->n_trees > 1 && xbytes <= (size_t)l2 / 4) {
+    CK(ensure(f->own_X, xbytes));
+    CK(cudaMemcpyAsync(f->own_X.p, dX, xbytes, cudaMemcpyDeviceToDevice, c->stream));
+    f->X = static_cast<const float*>(f->own_X.p);
+  }
   f->weighted = p->bootstrap != 0;
   f->level.clear();
   cudaError_t e;
@@ -1174,6 +1468,10 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
                             mse ? static_cast<float*>(f->ly[cu].p) : nullptr,
                             f->weighted ? static_cast<uint32_t*>(f->lw[cu].p) : nullptr, E,
                             p->n_particles);
+  if (f->X) {
+    pr.Xg = f->X;
+    pr.gidx = static_cast<const int32_t*>(f->lidx[cu].p);
+  }
 
   // 1. statistics and leaf values of every node of the level (per tile)
   std::vector<WorkTile> ltiles;
@@ -1744,6 +2042,72 @@ slm_status slm_kernel_stats(slm_ctx* c, int32_t kernel, int64_t* launches,
 slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
   if (!c || !launches) return SLM_EINVAL;
   *launches = c->launches;
+  return SLM_OK;
+}
+
+slm_status slm_set_tuning(slm_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return fail(c, SLM_EINVAL, "tuning must be 0 or 1");
+  c->tune = on;
+  return SLM_OK;
+}
+
+slm_status slm_force_tiles(slm_ctx* c, int32_t pg, int32_t ctas_per_sm, int32_t gather) {
+  if (!c) return SLM_EINVAL;
+  if (pg == 0) {
+    c->forced = slm_ctx::Tiles{0, 0};
+    return SLM_OK;
+  }
+  if ((pg != 8 && pg != 16 && pg != 24 && pg != 32 && pg != 48) ||
+      (ctas_per_sm != 1 && ctas_per_sm != 2) || (gather != 0 && gather != 1))
+    return fail(c, SLM_EINVAL,
+                "tiles: particles per group 8/16/24/32/48, 1 or 2 CTAs per SM, gather 0/1");
+  c->forced = slm_ctx::Tiles{pg, ctas_per_sm, 0.f, gather == 1};
+  return SLM_OK;
+}
+
+slm_status slm_tuning_stats(slm_ctx* c, int64_t* shapes, int32_t* last_pg,
+                            int32_t* last_ctas_per_sm) {
+  if (!c) return SLM_EINVAL;
+  if (shapes) *shapes = (int64_t)c->tuned.size();
+  if (last_pg) *last_pg = c->last.pg;
+  if (last_ctas_per_sm) *last_ctas_per_sm = c->last.cps;
+  return SLM_OK;
+}
+
+slm_status slm_tuned_shapes(slm_ctx* c, int32_t max, int32_t* n, int32_t* d, int32_t* pp,
+                            int32_t* tiles_log2, int32_t* pg, int32_t* ctas_per_sm,
+                            int32_t* gather, float* ms) {
+  if (!c || !n || max < 0) return SLM_EINVAL;
+  int32_t i = 0;
+  for (const auto& kv : c->tuned) {
+    if (i < max) {
+      if (d) d[i] = (int32_t)(kv.first >> 40);
+      if (pp) pp[i] = (int32_t)((kv.first >> 16) & 0xFFFFFF);
+      if (tiles_log2) tiles_log2[i] = (int32_t)(kv.first & 0x7FFF);
+      if (pg) pg[i] = kv.second.pg;
+      if (ctas_per_sm) ctas_per_sm[i] = kv.second.cps;
+      if (gather) gather[i] = kv.second.gather ? 1 : 0;
+      if (ms) ms[i] = kv.second.ms;
+    }
+    ++i;
+  }
+  *n = i;
+  return SLM_OK;
+}
+
+slm_status slm_set_graphs(slm_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return fail(c, SLM_EINVAL, "graphs must be 0 or 1");
+  c->graphs = on != 0;
+  return SLM_OK;
+}
+
+slm_status slm_graph_stats(slm_ctx* c, int64_t* launches, int64_t* reuses, int64_t* updates,
+                           int64_t* instantiations) {
+  if (!c) return SLM_EINVAL;
+  if (launches) *launches = c->graph_launches;
+  if (reuses) *reuses = c->graph_reuses;
+  if (updates) *updates = c->graph_updates;
+  if (instantiations) *instantiations = c->graph_instantiations;
   return SLM_OK;
 }
 

@@ -12,7 +12,8 @@ namespace slm {
 
 // ---- compile-time tiling ----------------------------------------------------
 constexpr int kThreads = 256;   // threads per CTA for the evaluation kernels
-constexpr int kPG = 16;         // particles per CTA ("particle group")
+constexpr int kPG = 16;         // particles per CTA ("particle group"); Pp pads to it
+constexpr int kPGMax = 48;      // widest particle group of the projection
 constexpr int kTS = 256;        // samples per tile: 8 warps x 32 samples
 constexpr int kKC = 32;         // features per smem chunk of the projection
 constexpr int kXS = kKC + 4;    // padded smem row stride (floats): rows r and
@@ -69,6 +70,10 @@ struct WorkTile {
 // stored entry-ordered: node a owns entries [seg_start, seg_start + seg_len).
 struct Problem {
   const float* X;         // [E, d] rows of the entries
+  // optional: the base rows [n, d] and each entry's row in them; the FP32
+  // projection may read entry e's row as Xg[gidx[e]] instead of X[e]
+  const float* Xg;
+  const int32_t* gidx;
   const int32_t* lab;     // [E] labels (classification) or null
   const float* y;         // [E] targets (MSE) or null
   const uint32_t* w;      // [E] multiplicities or null (= 1)
@@ -138,10 +143,14 @@ cudaError_t prepare_eval_kernels(const Problem& pr);
 cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
                               const NodeDesc* nodes, int A, SwarmCoef co,
                               cudaStream_t st);
-// z and ranges of every (tile, particle group); grid_cap = resident CTAs.
+// z and ranges of every (tile, particle group); grid_cap = CTAs launched at
+// most (the grid is persistent); pg = particles per group (0: pr.G's width);
+// gather: read rows through pr.gidx from pr.Xg (when set) instead of pr.X.
 cudaError_t launch_project(const Problem& pr, const Swarm& sw,
                            const WorkTile* tiles, int n_tiles, int grid_cap,
-                           cudaStream_t st);
+                           cudaStream_t st, int pg = 0, bool gather = false);
+// Whether k_project has a pg-particle group variant dividing pr.Pp.
+bool project_group_ok(const Problem& pr, int pg);
 // Cluster split S of the histogram kernel for A nodes of at most max_len
 // entries on n_sm SMs, with clusters of at most max_cluster CTAs.
 int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_cluster);
