@@ -423,7 +423,9 @@ def run_ours(args):
 
     extra = {"tree_train_ms": tot_ms_max / args.steps, "evals_per_step": evals // args.steps,
              "wall_s": wall, "train_loss": loss,
-             "search_loop": dict(ctx.graph_stats(), mode="one CUDA graph per level search"),
+             "search_loop": dict(ctx.graph_stats(), mode=(
+                 "one CUDA graph launch per level search" if args.graphs == "on"
+                 else "PDL-chained stream launches")),
              "projection_tiles": ctx.tuned_shapes()}
     if args.compare_fp32 and proj == "bf16":
         # the plain FP32 form of the same workload, same harness
@@ -697,8 +699,9 @@ def main():
     ap.add_argument("--topk", type=int, default=8)
     ap.add_argument("--compare-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--graphs", choices=["on", "off"], default="on",
-                    help="record each search's iteration loop as one CUDA graph")
+    ap.add_argument("--graphs", choices=["on", "off"], default=None,
+                    help="run each search's iteration loop as one CUDA graph launch "
+                         "(default: the workload's setting, else off)")
     ap.add_argument("--tiles", default="auto",
                     help="projection tiles: auto (tuned), fixed (16 particles, 2 CTAs/SM) "
                          "or PG:CPS[:GATHER]")
@@ -707,6 +710,8 @@ def main():
     args = ap.parse_args()
     if args.proj is None:
         args.proj = W.SETTINGS[args.workload].get("proj", "fp32")
+    if args.graphs is None:
+        args.graphs = "on" if W.SETTINGS[args.workload].get("graphs") else "off"
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:

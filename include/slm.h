@@ -407,13 +407,14 @@ slm_status slm_tuned_shapes(slm_ctx* ctx, int32_t max, int32_t* n, int32_t* d,
                             int32_t* padded_p, int32_t* tiles_log2, int32_t* pg,
                             int32_t* ctas_per_sm, int32_t* gather, float* ms);
 
-/* on = 1 (the default): the T + 1 scoring passes of every search (one node,
- * or all nodes of a level across all trees; Algorithm 1's loop) run as one
- * CUDA graph launch. The context keeps up to 64 executable graphs: a search
+/* on = 1: the T + 1 scoring passes of every search (one node, or all nodes
+ * of a level across all trees; Algorithm 1's loop) run as one CUDA graph
+ * launch. The context keeps up to 64 executable graphs: a search
  * with exactly the launch inputs of a kept graph (sizes, parameters, tiles
  * and buffers) launches it again without recording; otherwise the passes are
  * recorded and a kept graph with the same launch shapes is updated in place,
- * or a new one is instantiated. on = 0: the passes are launched one by one.
+ * or a new one is instantiated. on = 0 (the default): the passes are launched
+ * one by one, chained by programmatic dependent launch.
  * Results are identical either way; per-launch profiling (slm_profile)
  * always launches one by one. SLM_EINVAL for other values. */
 slm_status slm_set_graphs(slm_ctx* ctx, int32_t on);

@@ -74,7 +74,7 @@ struct slm_ctx {
   Tiles cur{};   // tiles of the search in flight
   Tiles last{};  // tiles of the last search
   // a search's iteration loop as one CUDA graph launch (reused executable)
-  bool graphs = true;
+  bool graphs = false;
   cudaStream_t cap_stream = nullptr;  // records graphs (the caller's stream may
                                       // be the legacy default stream)
   // executable graphs by launch signature (every kernel node's function,

@@ -143,9 +143,10 @@ SETTINGS = {
         builder=lambda seed=1: gmm(1_000_000, 256, 20, seed),
         criterion="gini", n_particles=64, n_iters=80, n_bins=128,
         max_depth=12, min_leaf=20, n_trees=1, proj="bf16", topk=8),
-    # bagged forest of 64 trees
+    # bagged forest of 64 trees; every level of all trees searched as one
+    # graph-captured launch
     "forest64_n100k_d32_k5": dict(
         builder=lambda seed=1: gmm(100_000, 32, 5, seed),
         criterion="gini", n_particles=48, n_iters=60, n_bins=128,
-        max_depth=8, min_leaf=20, n_trees=64),
+        max_depth=8, min_leaf=20, n_trees=64, graphs=True),
 }
