@@ -90,7 +90,7 @@ def traffic_per_launch(name, ks, workload):
 
 def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
     d = {"workload": name, "n": wl.n, "d": wl.d, "classes": wl.n_classes,
-         "trees": cfg["n_trees"], "bootstrap": cfg["n_trees"] > 1,
+         "trees": cfg["n_trees"], "bootstrap": cfg.get("bootstrap", cfg["n_trees"] > 1),
          "max_depth": cfg["max_depth"], "min_leaf": cfg["min_leaf"],
          "particles": cfg["n_particles"], "iters": cfg["n_iters"], "bins": cfg["n_bins"],
          "criterion": cfg["criterion"],
@@ -264,7 +264,8 @@ def make_params(S, cfg, wl, proj, topk):
     return S.make_params(cfg["criterion"], wl.n_classes, n_particles=cfg["n_particles"],
                          n_iters=cfg["n_iters"], n_bins=cfg["n_bins"],
                          min_leaf=cfg["min_leaf"], max_depth=cfg["max_depth"], seed=1,
-                         n_trees=cfg["n_trees"], bootstrap=cfg["n_trees"] > 1,
+                         n_trees=cfg["n_trees"],
+                         bootstrap=cfg.get("bootstrap", cfg["n_trees"] > 1),
                          proj=S.SLM_PROJ_BF16_TOPK if proj == "bf16" else S.SLM_PROJ_FP32,
                          topk=topk)
 
@@ -307,7 +308,7 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
         # z (4 B per pair) + labels / targets (+ multiplicities) per entry and
         # pass; the bf16 form scans P and then k particles per entry
         per_entry = P if proj != "bf16" else (P + topk) / 2.0
-        weighted = cfg["n_trees"] > 1
+        weighted = cfg.get("bootstrap", cfg["n_trees"] > 1)
         algo = kh["pairs"] * (4.0 + (8.0 if weighted else 4.0) / per_entry)
         ach = algo / (kh["ms"] / 1e3) / 1e9
         roofs["hist_scan"] = {"kernel": "hist_scan", "bound": "hbm", "achieved": ach,

@@ -388,6 +388,15 @@ slm_status slm_launch_count(slm_ctx* ctx, int64_t* launches);
  * on = 0: 16 particles per group, 2 CTAs per SM. Results are identical for
  * every tile shape. SLM_EINVAL for other values. */
 slm_status slm_set_tuning(slm_ctx* ctx, int32_t on);
+/* Histogram kernels of classification searches (FP32 form): when a level's
+ * nodes of at most max_entries entries (default 4096) give at least
+ * min_pairs (node, particle) pairs (-1, the default: 2 x SMs x 8, enough
+ * warps to fill the GPU), they are scored one warp per (node, particle)
+ * from memory; the other nodes (all nodes otherwise) by clusters of CTAs
+ * staging the node through shared memory. max_entries = 0 sends every node
+ * to the clusters. Scores are identical either way. SLM_EINVAL for
+ * max_entries < 0 or min_pairs < -1. */
+slm_status slm_set_small_nodes(slm_ctx* ctx, int32_t max_entries, int64_t min_pairs);
 /* Forces one tile shape for later searches (pg = 0 clears); gather = 1 reads
  * gathered base rows where a forest keeps them (elsewhere the level copy is
  * the only source). SLM_EINVAL for shapes outside the list above, and from a

@@ -95,6 +95,7 @@ def lib():
             "slm_launch_count": ([vp, P(i64)], C.c_int),
             "slm_set_graphs": ([vp, i32], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
+            "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
             "slm_force_tiles": ([vp, i32, i32, i32], C.c_int),
             "slm_tuning_stats": ([vp, P(i64), P(i32), P(i32)], C.c_int),
             "slm_tuned_shapes": ([vp, i32, P(i32), vp, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -329,6 +330,9 @@ class Context:
         n = C.c_int64()
         self._check(lib().slm_launch_count(self.handle, C.byref(n)))
         return n.value
+
+    def set_small_nodes(self, max_entries: int = 4096, min_pairs: int = -1):
+        self._check(lib().slm_set_small_nodes(self.handle, max_entries, min_pairs))
 
     def set_tuning(self, on: bool):
         self._check(lib().slm_set_tuning(self.handle, 1 if on else 0))

@@ -31,6 +31,9 @@
 
 #include <cooperative_groups.h>
 
+#include <mutex>
+#include <vector>
+
 #include "philox.cuh"
 #include "slm_internal.cuh"
 #include "device_util.cuh"
@@ -42,6 +45,21 @@ namespace {
 __device__ __forceinline__ double xlogx(uint32_t c) {
   const double x = (double)c;
   return c ? x * log(x) : 0.0;
+}
+
+// c ln c for c < kXlogxTab from a table the device builds once with xlogx
+// itself (identical values): the entropy scans then read L2 instead of
+// evaluating double-precision logarithms, which are scarce on this GPU.
+__device__ const double* d_xlogx_tab = nullptr;
+
+__global__ void k_xlogx_table(double* tab, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) tab[i] = xlogx((uint32_t)i);
+}
+
+__device__ __forceinline__ double xlogx_t(uint32_t c) {
+  const double* t = d_xlogx_tab;
+  return (t && c < (uint32_t)kXlogxTab) ? __ldg(t + c) : xlogx(c);
 }
 
 __device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
@@ -183,8 +201,8 @@ __device__ EvalRes block_scan_cls(uint32_t* h, int B, int K, int min_leaf, ScanS
         sl += (uint64_t)l * l;
         sr += (uint64_t)r * r;
       } else {
-        hl += xlogx(l);
-        hr += xlogx(r);
+        hl += xlogx_t(l);
+        hr += xlogx_t(r);
       }
     }
     sc.nl[threadIdx.x] = nl;
@@ -202,7 +220,7 @@ __device__ EvalRes block_scan_cls(uint32_t* h, int B, int K, int min_leaf, ScanS
       bd = (uint64_t)nl * nr;
     } else {
       // compared after the division by n, as the criterion is defined
-      bl = ((xlogx(nl) - hl) + (xlogx(nr) - hr)) / (double)ntot;
+      bl = ((xlogx_t(nl) - hl) + (xlogx_t(nr) - hr)) / (double)ntot;
     }
   }
   block_argmin<CRIT>(bn, bd, bl, bb, sc);
@@ -446,33 +464,56 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int j = 0; j < PJ; ++j)
           av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+        // feature-outer: every accumulator takes features k..k+3 in order,
+        // and consecutive FMAs go to independent accumulators
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < PJ; ++j) {
-            acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
-            acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
-            acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
-            acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
-          }
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
       }
     } else {
-      // wide groups: one particle's 4 features at a time keeps the live
-      // registers at the accumulators plus one row and one position vector
+      // wide groups: two particles' 4 features at a time keep the live
+      // registers at the accumulators plus the rows and two position vectors
       for (int k = 0; k < kc4; k += 4) {
         float4 xv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
 #pragma unroll
-        for (int j = 0; j < PJ; ++j) {
-          const float4 av = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+        for (int j = 0; j < PJ; j += 2) {
+          const float4 a0 = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + k);
+          const float4 a1 = *reinterpret_cast<const float4*>(ar + (j + 1) * 4 * kXS + k);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            acc[i][j] = fmaf(xv[i].x, av.x, acc[i][j]);
-            acc[i][j] = fmaf(xv[i].y, av.y, acc[i][j]);
-            acc[i][j] = fmaf(xv[i].z, av.z, acc[i][j]);
-            acc[i][j] = fmaf(xv[i].w, av.w, acc[i][j]);
+            acc[i][j] = fmaf(xv[i].x, a0.x, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].x, a1.x, acc[i][j + 1]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].y, a0.y, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].y, a1.y, acc[i][j + 1]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].z, a0.z, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].z, a1.z, acc[i][j + 1]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].w, a0.w, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].w, a1.w, acc[i][j + 1]);
           }
         }
       }
@@ -737,8 +778,8 @@ __host__ __device__ inline size_t stage_bytes(int crit, bool weighted) {
 // search (do_update) rank 0 also takes the particle's pbest step; the gbest
 // step and the move follow in k_move.
 __global__ void __launch_bounds__(kThreads, 3)
-    k_hist_scan(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int32_t* bins_out,
-                int t, int do_update) {
+    k_hist_scan(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
+                const int32_t* __restrict__ list, int32_t* bins_out, int t, int do_update) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_bar[kStages];
@@ -750,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   pdl_wait();
   const int S = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int a = blockIdx.x / S;
+  const int a = list ? list[blockIdx.x / S] : (int)blockIdx.x / S;
   const int p = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const NodeDesc nd = nodes[a];
@@ -994,6 +1035,184 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
 }
 
+// Classification threshold scan of one particle by one warp: the arithmetic
+// and tie rules of block_scan_cls (per-class prefix over bins, per-edge
+// counts, Gini rational or entropy loss, repeated partitions skipped, lower
+// edge on ties), so the same score. h: [B][K] counts (prefix sums in place).
+template <int CRIT>
+__device__ EvalRes warp_scan_cls(uint32_t* h, int B, int K, int min_leaf) {
+  const int lane = threadIdx.x & 31;
+  const int bpl = (B + 31) >> 5;
+  for (int k = 0; k < K; ++k) {
+    uint32_t v[kMaxBins / 32];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxBins / 32; ++i) {
+      const int j = lane * bpl + i;
+      v[i] = (i < bpl && j < B) ? h[j * K + k] : 0u;
+      sum += v[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += u;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < kMaxBins / 32; ++i) {
+      const int j = lane * bpl + i;
+      run += v[i];
+      if (i < bpl && j < B) h[j * K + k] = run;
+    }
+  }
+  __syncwarp();
+  const uint32_t* tot = h + (B - 1) * K;
+  uint32_t ntot = 0;
+  for (int k = 0; k < K; ++k) ntot += tot[k];
+  uint64_t bn = 0, bd = 0;
+  double bl = 0.0;
+  int bb = -1;
+  uint32_t bnl = 0;
+  for (int b = 1 + lane; b < B; b += 32) {
+    const uint32_t* row = h + (b - 1) * K;
+    uint32_t nl = 0, prev = 0;
+    uint64_t sl = 0, sr = 0;
+    double hl = 0.0, hr = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const uint32_t l = row[k], r = tot[k] - l;
+      nl += l;
+      if (b >= 2) prev += row[k - K];
+      if (CRIT == SLM_GINI) {
+        sl += (uint64_t)l * l;
+        sr += (uint64_t)r * r;
+      } else {
+        hl += xlogx_t(l);
+        hr += xlogx_t(r);
+      }
+    }
+    const uint32_t nr = ntot - nl;
+    if (nl != prev && nl >= (uint32_t)min_leaf && nr >= (uint32_t)min_leaf) {
+      uint64_t cn = 0, cd = 0;
+      double cl = 0.0;
+      if (CRIT == SLM_GINI) {
+        cn = sl * nr + sr * nl;
+        cd = (uint64_t)nl * nr;
+      } else {
+        cl = ((xlogx_t(nl) - hl) + (xlogx_t(nr) - hr)) / (double)ntot;
+      }
+      if (edge_takes<CRIT>(cn, cd, cl, b, bn, bd, bl, bb)) {
+        bn = cn;
+        bd = cd;
+        bl = cl;
+        bb = b;
+        bnl = nl;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+    const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+    const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
+    const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
+    const uint32_t onl = __shfl_xor_sync(0xffffffffu, bnl, off);
+    if (edge_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
+      bn = on;
+      bd = od;
+      bl = ol;
+      bb = ob;
+      bnl = onl;
+    }
+  }
+  EvalRes res = invalid_res();
+  if (bb >= 0) {
+    res.valid = 1;
+    res.bin = bb;
+    res.nl = bnl;
+    res.nr = ntot - bnl;
+    if (CRIT == SLM_GINI) {
+      res.num = bn;
+      res.den = bd;
+      const uint64_t nden = (uint64_t)ntot * res.den;
+      res.loss = (double)(nden - res.num) / (double)nden;
+    } else {
+      res.loss = bl;
+    }
+  }
+  return res;
+}
+
+// Histogram and threshold scan of the particles of small classification
+// nodes (list[]: their indices), one warp per (node, particle): the warp
+// reads the node's z and labels (and multiplicities) straight from memory
+// (L2-resident at these sizes) into its own shared histogram and scans it
+// with warp_scan_cls. The score, the range reset and the pbest step are
+// those of k_hist_scan; small nodes save its per-CTA staging, copies,
+// merges and block-wide barriers.
+template <int CRIT>
+__global__ void __launch_bounds__(kThreads)
+    k_hist_warp(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
+                const int32_t* __restrict__ list, int n_pairs, int t, int do_update) {
+  extern __shared__ __align__(16) uint32_t hw[];
+  pdl_trigger();
+  pdl_wait();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = (int)blockIdx.x * (kThreads / 32) + warp;
+  if (q >= n_pairs) return;  // the whole warp
+  const int a = list[q / pr.P], p = q % pr.P;
+  const NodeDesc nd = nodes[a];
+  const int B = pr.B, K = pr.K, words = B * K;
+  uint32_t* h = hw + warp * words;
+  int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
+  const int lo_o = zz[0], hi_o = zz[1];
+  float zmin = 0.f, inv_w = 0.f;
+  bool ok = false;
+  if (lo_o != INT_MAX) {
+    const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+    inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+    zmin = lo;
+    ok = (hi > lo) && isfinite(inv_w);
+  }
+  for (int i = lane; i < words; i += 32) h[i] = 0u;
+  __syncwarp();
+  if (ok) {
+    const float* zs = sw.z + (int64_t)p * pr.Ez + nd.seg_start;
+    const int32_t* ls = pr.lab + nd.seg_start;
+    const uint32_t* ws = pr.w ? pr.w + nd.seg_start : nullptr;
+    // four entries per lane in flight before their shared atomics
+    for (int i0 = lane; i0 < nd.seg_len; i0 += 128) {
+      float zv[4];
+      int32_t lv[4];
+      uint32_t wv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + 32 * u;
+        const bool in = i < nd.seg_len;
+        zv[u] = in ? __ldcg(zs + i) : 0.f;
+        lv[u] = in ? __ldg(ls + i) : -1;
+        wv[u] = in && ws ? __ldg(ws + i) : 1u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (lv[u] >= 0) atomicAdd(&h[bin_of(zv[u], zmin, inv_w, B) * K + lv[u]], wv[u]);
+    }
+  }
+  __syncwarp();
+  EvalRes res = invalid_res();
+  if (ok) {
+    res = warp_scan_cls<CRIT>(h, B, K, pr.min_leaf);
+    res.zmin = zmin;
+    res.inv_w = inv_w;
+  }
+  if (lane == 0) {
+    sw.cur[(int64_t)a * pr.Pp + p] = res;
+    zz[0] = INT_MAX;  // ready for the next iteration
+    zz[1] = INT_MIN;
+  }
+  if (do_update) pbest_step(pr, sw, a, p, t, res);
+}
+
 // Initial swarm of each node: x ~ U[-1,1)^d, v ~ 0.1 U[-1,1)^d.
 __global__ void k_swarm_init(Problem pr, Swarm sw,
                              const NodeDesc* __restrict__ nodes,
@@ -1201,6 +1420,10 @@ cudaError_t prepare_eval_kernels(const Problem& pr) {
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kProjSmem)))
       return e;
+  for (const void* f : {(const void*)k_hist_warp<SLM_GINI>, (const void*)k_hist_warp<SLM_ENTROPY>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kHistWarpMaxSmem)))
+      return e;
   if ((e = cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hist_smem_bytes(pr))))
     return e;
@@ -1213,6 +1436,25 @@ cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
   if (A <= 0) return cudaSuccess;
   k_swarm_init<<<A, kThreads, 0, st>>>(pr, sw, nodes, co);
   return cudaGetLastError();
+}
+
+cudaError_t ensure_xlogx_table(int device) {
+  static std::mutex mu;
+  static std::vector<char> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)done.size() <= device) done.resize(device + 1, 0);
+  if (done[device]) return cudaSuccess;
+  double* tab = nullptr;
+  cudaError_t e = cudaMalloc(&tab, sizeof(double) * kXlogxTab);  // kept for the process
+  if (e) return e;
+  cudaStream_t st = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) return e;
+  k_xlogx_table<<<(kXlogxTab + 255) / 256, 256, 0, st>>>(tab, kXlogxTab);
+  if (!(e = cudaGetLastError())) e = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (!e) e = cudaMemcpyToSymbol(d_xlogx_tab, &tab, sizeof(tab));
+  if (!e) done[device] = 1;
+  return e;
 }
 
 bool project_group_ok(const Problem& pr, int pg) {
@@ -1285,7 +1527,7 @@ int hist_max_cluster(const Problem& pr) {
 
 cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                              int A, int S, int32_t* bins_out, int t, int do_update,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int32_t* list) {
   if (A <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A * S), (unsigned)pr.P, 1);
@@ -1301,7 +1543,38 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc*
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, bins_out, t, do_update);
+  return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, list, bins_out, t, do_update);
+}
+
+size_t hist_warp_smem_bytes(const Problem& pr) {
+  return sizeof(uint32_t) * (size_t)(kThreads / 32) * pr.B * pr.K;
+}
+
+bool hist_warp_ok(const Problem& pr) {
+  return pr.crit != SLM_MSE && hist_warp_smem_bytes(pr) <= kHistWarpMaxSmem;
+}
+
+cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                             const int32_t* list, int n_nodes, int t, int do_update,
+                             cudaStream_t st) {
+  const int64_t pairs = (int64_t)n_nodes * pr.P;
+  if (pairs <= 0) return cudaSuccess;
+  if (!hist_warp_ok(pr)) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((pairs + kThreads / 32 - 1) / (kThreads / 32)), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = hist_warp_smem_bytes(pr);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (pr.crit == SLM_GINI)
+    return cudaLaunchKernelEx(&cfg, k_hist_warp<SLM_GINI>, pr, sw, nodes, list, (int)pairs, t,
+                              do_update);
+  return cudaLaunchKernelEx(&cfg, k_hist_warp<SLM_ENTROPY>, pr, sw, nodes, list, (int)pairs, t,
+                            do_update);
 }
 
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,

@@ -36,6 +36,8 @@ enum Slot {
   // learned proposal: node statistics, network work space, training data
   S_PSTATS, S_PYR, S_PACC, S_PWK, S_PWORK, S_PLOSS, W_PS, W_PD, W_PT, W_PIDX, W_PBS, W_PBD,
   W_PBT, W_PRHO, W_PMU, W_PPOS,
+  // node lists of the histogram kernels (large nodes, then small ones)
+  S_HLIST,
   N_SLOTS
 };
 
@@ -69,6 +71,9 @@ struct slm_ctx {
     bool gather = false; // rows gathered from the base rows by sample id
   };
   int tune = 1;
+  int small_node_max = kWarpNodeMax;  // warp-per-particle histograms up to this,
+  int64_t small_min_pairs = -1;       // for at least this many (node, particle)
+                                      // pairs (-1: 2 x SMs x warps per CTA)
   Tiles forced{0, 0};
   std::map<uint64_t, Tiles> tuned;
   Tiles cur{};   // tiles of the search in flight
@@ -444,6 +449,57 @@ struct Bf16Plan {
   int32_t* inv = nullptr;
 };
 
+// Histogram kernels of a classification search: the nodes of at most
+// small_node_max entries go to the warp-per-particle kernel, the others to
+// the cluster kernel.
+struct HistPlan {
+  bool on = false;
+  const int32_t* large = nullptr;
+  int n_large = 0, S_large = 1;
+  double pairs_large = 0.0;
+  const int32_t* small = nullptr;
+  int n_small = 0;
+  double pairs_small = 0.0;
+};
+
+slm_status setup_hist_plan(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes,
+                           HistPlan* plan) {
+  *plan = HistPlan{};
+  if (c->small_node_max <= 0 || !hist_warp_ok(pr)) return SLM_OK;
+  std::vector<int32_t> lst;
+  int64_t max_large = 0;
+  for (int a = 0; a < (int)nodes.size(); ++a)
+    if (nodes[a].seg_len > c->small_node_max) {
+      lst.push_back(a);
+      max_large = std::max<int64_t>(max_large, nodes[a].seg_len);
+      plan->pairs_large += (double)nodes[a].seg_len * pr.P;
+    }
+  plan->n_large = (int)lst.size();
+  for (int a = 0; a < (int)nodes.size(); ++a)
+    if (nodes[a].seg_len <= c->small_node_max) {
+      lst.push_back(a);
+      plan->pairs_small += (double)nodes[a].seg_len * pr.P;
+    }
+  plan->n_small = (int)lst.size() - plan->n_large;
+  // one warp per (node, particle) only pays when the small nodes alone give
+  // every SM several warps; a few small nodes are split across clusters
+  const int64_t min_pairs =
+      c->small_min_pairs >= 0 ? c->small_min_pairs : 2LL * c->n_sm * (kThreads / 32);
+  if ((int64_t)plan->n_small * pr.P < min_pairs) {
+    *plan = HistPlan{};
+    return SLM_OK;
+  }
+  CK(ensure(c->ws[S_HLIST], sizeof(int32_t) * lst.size()));
+  CK(cudaMemcpyAsync(c->ws[S_HLIST].p, lst.data(), sizeof(int32_t) * lst.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  plan->large = static_cast<const int32_t*>(c->ws[S_HLIST].p);
+  plan->small = plan->large + plan->n_large;
+  if (plan->n_large)
+    plan->S_large = hist_split(pr, plan->n_large, max_large, c->n_sm, hist_max_cluster(pr));
+  plan->on = true;
+  return SLM_OK;
+}
+
 // Buffers of the reduced-precision pass for A nodes whose segments start on
 // multiples of kMmaRows; sw->sel / sw->k are set for a search.
 slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes,
@@ -526,7 +582,7 @@ slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>
 slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
                        const std::vector<NodeDesc>& nodes, int n_tiles, double pairs,
                        int32_t* bins_out, int t, const SwarmCoef* co, int S,
-                       const Bf16Plan* bp = nullptr) {
+                       const Bf16Plan* bp = nullptr, const HistPlan* hp = nullptr) {
   const int A = (int)nodes.size();
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
@@ -570,9 +626,20 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
     CK(launch(c, SLM_K_PROJECT, pairs, [&] {
       return launch_project(pr, sw, dt, n_tiles, cap, c->stream, c->cur.pg, c->cur.gather);
     }));
-  CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
-    return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
-  }));
+  if (hp && hp->on && !bins_out) {
+    if (hp->n_large)
+      CK(launch(c, SLM_K_HIST_SCAN, hp->pairs_large, [&] {
+        return launch_hist_scan(pr, sw, dn, hp->n_large, hp->S_large, nullptr, t, co ? 1 : 0,
+                                c->stream, hp->large);
+      }));
+    CK(launch(c, SLM_K_HIST_SCAN, hp->pairs_small, [&] {
+      return launch_hist_warp(pr, sw, dn, hp->small, hp->n_small, t, co ? 1 : 0, c->stream);
+    }));
+  } else {
+    CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
+      return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
+    }));
+  }
   if (co)
     CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
               [&] { return launch_move(pr, sw, dn, A, t, *co, c->stream); }));
@@ -877,6 +944,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
   const int S = batch_split(c, pr, nodes);
   slm_ctx::Tiles tl{};
   if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
+  HistPlan hp;
+  if (!bp.on && (s = setup_hist_plan(c, pr, nodes, &hp))) return s;
   c->cur = tl;
   c->last = tl;
   std::string key;
@@ -890,6 +959,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
     kw.put(dn); kw.put(ws_ptr<WorkTile>(c, S_TILES)); kw.put(ws_ptr<WorkTile>(c, S_MTILES));
     kw.put(bp.on); kw.put(bp.k); kw.put(bp.kp); kw.put(bp.n_mtiles); kw.put(bp.grid);
     kw.put(bp.S_k); kw.put(bp.pairs_k); kw.put(bp.posb); kw.put(bp.sel); kw.put(bp.inv);
+    kw.put(hp.on); kw.put(hp.large); kw.put(hp.n_large); kw.put(hp.S_large);
+    kw.put(hp.pairs_large); kw.put(hp.small); kw.put(hp.n_small); kw.put(hp.pairs_small);
     if (bp.on) {
       kw.problem(bp.pr_k);
       kw.swarm(bp.sw_k);
@@ -897,7 +968,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
     key = std::move(kw.b);
   }
   s = run_iterations(c, p->n_iters, key, [&](int t) {
-    return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp);
+    return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp, &hp);
   });
   c->cur = slm_ctx::Tiles{};
   if (s) return s;
@@ -977,6 +1048,7 @@ slm_status slm_create(slm_ctx** out, int device, void* cuda_stream) {
     return SLM_EINVAL;
   }
   if (cudaSetDevice(device) != cudaSuccess) return SLM_ECUDA;
+  if (ensure_xlogx_table(device) != cudaSuccess) return SLM_ECUDA;
   slm_ctx* c = new (std::nothrow) slm_ctx();
   if (!c) return SLM_ENOMEM;
   c->device = device;
@@ -2042,6 +2114,14 @@ slm_status slm_kernel_stats(slm_ctx* c, int32_t kernel, int64_t* launches,
 slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
   if (!c || !launches) return SLM_EINVAL;
   *launches = c->launches;
+  return SLM_OK;
+}
+
+slm_status slm_set_small_nodes(slm_ctx* c, int32_t max_entries, int64_t min_pairs) {
+  if (!c || max_entries < 0 || min_pairs < -1)
+    return fail(c, SLM_EINVAL, "small nodes: max_entries >= 0, min_pairs >= -1");
+  c->small_node_max = max_entries;
+  c->small_min_pairs = min_pairs;
   return SLM_OK;
 }
 

@@ -138,6 +138,15 @@ struct SwarmCoef {
   uint64_t seed;
 };
 
+// Nodes of at most this many entries are scored by the warp-per-particle
+// histogram kernel in classification searches.
+constexpr int kWarpNodeMax = 4096;
+
+// c ln c is tabulated for counts below this (8 MB of doubles per device).
+constexpr int kXlogxTab = 1 << 20;
+// Builds the device's c ln c table once per process (synchronous).
+cudaError_t ensure_xlogx_table(int device);
+
 // ---- launchers (eval_kernels.cu) -------------------------------------------
 cudaError_t prepare_eval_kernels(const Problem& pr);
 cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
@@ -161,6 +170,13 @@ int hist_max_cluster(const Problem& pr);
 cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
                              const NodeDesc* nodes, int A, int S,
                              int32_t* bins_out, int t, int do_update,
+                             cudaStream_t st, const int32_t* list = nullptr);
+// Small classification nodes: one warp per (node, particle) of the n_nodes
+// nodes list[] names (scores, range reset and pbest step as k_hist_scan).
+constexpr size_t kHistWarpMaxSmem = 160 * 1024;
+bool hist_warp_ok(const Problem& pr);
+cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                             const int32_t* list, int n_nodes, int t, int do_update,
                              cudaStream_t st);
 // gbest step of iteration t and (t < T) the Eq. pso-1 move of every particle
 // of A nodes to iteration t+1.

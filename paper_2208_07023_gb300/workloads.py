@@ -127,6 +127,12 @@ SETTINGS = {
         builder=lambda seed=1: single_node(2000, 16, 0.05, seed),
         criterion="entropy", n_particles=32, n_iters=50, n_bins=64,
         max_depth=1, min_leaf=1, n_trees=1),
+    # the same node searched with 1024 independent seeds in one batch (1024
+    # depth-1 trees without bootstrap: each root has its own swarm stream)
+    "node_n2000_d16_x1024": dict(
+        builder=lambda seed=1: single_node(2000, 16, 0.05, seed),
+        criterion="entropy", n_particles=32, n_iters=50, n_bins=64,
+        max_depth=1, min_leaf=1, n_trees=1024, bootstrap=False),
     # full classification tree, FP32 projection, all nodes of a level batched
     "tree_n50k_d64_k10": dict(
         builder=lambda seed=1: gmm(50_000, 64, 10, seed),

@@ -146,6 +146,39 @@ def test_every_tile_shape_gives_the_same_forest(ctx, P):
     assert st["last_ctas_per_sm"] in (1, 2)
 
 
+@pytest.mark.parametrize("crit,bootstrap", [("gini", True), ("entropy", False),
+                                             ("gini", False), ("entropy", True)])
+def test_small_node_kernel_gives_the_same_forest(ctx, crit, bootstrap):
+    """Warp-per-particle histograms for small nodes against the cluster
+    kernel for every node, and every node small."""
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(6000, 12, 6, seed=21)
+    p = gpu_params(S, crit, 6, 24, 10, 64, min_leaf=8, seed=6, max_depth=6, n_trees=4,
+                   bootstrap=bootstrap)
+    out = []
+    for bound in (0, 4096, 1 << 30):
+        ctx.set_small_nodes(bound, 0)
+        out.append(forest_arrays(ctx, p, wl))
+    ctx.set_small_nodes()
+    same_forest(out[0], out[1])
+    same_forest(out[0], out[2])
+
+
+def test_small_node_kernel_gives_the_same_search(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(3000, 20, 10, seed=22)
+    for crit in ("gini", "entropy"):
+        p = gpu_params(S, crit, 10, 64, 25, 128, min_leaf=3, seed=7)
+        res = []
+        for bound in (0, 1 << 30):
+            ctx.set_small_nodes(bound, 0)
+            res.append(ctx.node_split(p, wl.X, labels=wl.labels, node_uid=5, want_trace=True))
+        ctx.set_small_nodes()
+        assert np.array_equal(res[0]["trace"], res[1]["trace"])
+        assert np.array_equal(res[0]["gbest"].view(np.uint32), res[1]["gbest"].view(np.uint32))
+        assert (res[0]["bin"], res[0]["n_left"]) == (res[1]["bin"], res[1]["n_left"])
+
+
 def test_invalid_tiles_are_rejected(ctx):
     from paper_2208_07023_gb300 import binding as S
     for pg, cps in ((12, 1), (16, 3), (64, 2)):
@@ -163,4 +196,6 @@ def test_invalid_tiles_are_rejected(ctx):
     ctx.force_tiles(0)
     ctx.node_split(p, wl.X, labels=wl.labels)
     assert S.lib().slm_set_graphs(ctx.handle, 2) == 1
+    assert S.lib().slm_set_small_nodes(ctx.handle, -1, 0) == 1
+    assert S.lib().slm_set_small_nodes(ctx.handle, 16, -2) == 1
     assert S.lib().slm_set_tuning(ctx.handle, -1) == 1
