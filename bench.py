@@ -295,6 +295,16 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
     dp = (d + 15) // 16 * 16
     roofs = {}
     kp, kh, km = kst["project"], kst["hist_scan"], kst["project_mma"]
+    kn = kst.get("node_search", {"ms": 0.0})
+    if kn["ms"] > 0:
+        # whole searches of shared-memory-resident nodes: 2 d flop per
+        # particle-sample evaluation (the kernel projects twice: range, bins)
+        ach = 2.0 * d * kn["pairs"] / (kn["ms"] / 1e3) / 1e12
+        roofs["node_search"] = {"kernel": "node_search", "bound": "alu", "achieved": ach,
+                                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                                "avg_launch_ms": kn["ms"] / max(1, kn["launches"]),
+                                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     if kp["ms"] > 0:
         # FP32 FFMA: 2 d flop per particle-sample pair
         ach = 2.0 * d * kp["pairs"] / (kp["ms"] / 1e3) / 1e12

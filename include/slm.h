@@ -363,7 +363,8 @@ typedef enum {
   SLM_K_TOPK = 10,        /* BF16_TOPK: position conversion, top-k selection,
                              score merge with the pbest / gbest steps */
   SLM_K_PROPOSAL = 11,    /* node statistics, network passes, Adam, seeding */
-  SLM_K_COUNT = 12
+  SLM_K_NODE_SEARCH = 12, /* whole searches of nodes held in shared memory */
+  SLM_K_COUNT = 13
 } slm_kernel;
 
 /* on != 0 brackets every later launch of the context with CUDA events on its
@@ -388,6 +389,18 @@ slm_status slm_launch_count(slm_ctx* ctx, int64_t* launches);
  * on = 0: 16 particles per group, 2 CTAs per SM. Results are identical for
  * every tile shape. SLM_EINVAL for other values. */
 slm_status slm_set_tuning(slm_ctx* ctx, int32_t on);
+/* on = 1 (the default): a classification search (FP32 form) whose nodes'
+ * rows, labels and multiplicities all fit in one SM's shared memory (about
+ * n (d + 2) 4 bytes per node, with room for eight B x K histograms) runs all
+ * of Algorithm 1's T + 1 iterations in one persistent launch: a cluster of
+ * up to 8 CTAs per node, the node resident in each CTA's shared memory, one
+ * warp per particle at a time. on = 0: the per-iteration kernels. Scores,
+ * trajectories and trees are identical either way. SLM_EINVAL for other
+ * values. */
+slm_status slm_set_node_search(slm_ctx* ctx, int32_t on);
+/* CTAs per node of the context's last search in the persistent kernel, 0 if
+ * the last search used the per-iteration kernels. */
+slm_status slm_last_node_search(slm_ctx* ctx, int32_t* ctas_per_node);
 /* Histogram kernels of classification searches (FP32 form): when a level's
  * nodes of at most max_entries entries (default 4096) give at least
  * min_pairs (node, particle) pairs (-1, the default: 2 x SMs x 8, enough

@@ -22,7 +22,8 @@ SLM_PROJ_FP32, SLM_PROJ_BF16_TOPK = 0, 1
 CRITERIA = {"gini": SLM_GINI, "entropy": SLM_ENTROPY, "mse": SLM_MSE}
 PURPOSE_INIT_X, PURPOSE_INIT_V, PURPOSE_R1, PURPOSE_R2 = 1, 2, 3, 4
 KERNELS = ["project", "hist_scan", "move", "swarm_init", "node_stats",
-           "partition", "compact", "gather", "other", "project_mma", "topk", "proposal"]
+           "partition", "compact", "gather", "other", "project_mma", "topk", "proposal",
+           "node_search"]
 
 
 class slm_params(C.Structure):
@@ -96,6 +97,8 @@ def lib():
             "slm_set_graphs": ([vp, i32], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
+            "slm_set_node_search": ([vp, i32], C.c_int),
+            "slm_last_node_search": ([vp, P(i32)], C.c_int),
             "slm_force_tiles": ([vp, i32, i32, i32], C.c_int),
             "slm_tuning_stats": ([vp, P(i64), P(i32), P(i32)], C.c_int),
             "slm_tuned_shapes": ([vp, i32, P(i32), vp, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -329,6 +332,14 @@ class Context:
     def launch_count(self) -> int:
         n = C.c_int64()
         self._check(lib().slm_launch_count(self.handle, C.byref(n)))
+        return n.value
+
+    def set_node_search(self, on: bool):
+        self._check(lib().slm_set_node_search(self.handle, 1 if on else 0))
+
+    def last_node_search(self) -> int:
+        n = C.c_int32()
+        self._check(lib().slm_last_node_search(self.handle, C.byref(n)))
         return n.value
 
     def set_small_nodes(self, max_entries: int = 4096, min_pairs: int = -1):

@@ -1213,6 +1213,138 @@ __global__ void __launch_bounds__(kThreads)
   if (do_update) pbest_step(pr, sw, a, p, t, res);
 }
 
+// Persistent search of small classification nodes: all T + 1 iterations of
+// Algorithm 1 in one launch. A cluster of S CTAs per node (grid (S, nodes)):
+// every CTA keeps the node's rows (row stride d | 1, conflict-free per
+// lane), labels and multiplicities in shared memory; warp w of rank r
+// evaluates particles p with p / 8 = r (mod S), p = w (mod 8): z by the
+// same sequential fused multiply-adds as k_project, its exact range, a
+// warp-private histogram and warp_scan_cls (the scores of the
+// per-iteration kernels), then the pbest step. A cluster barrier, the gbest
+// step of k_move (every CTA finds it; rank 0 records it), the move of each
+// CTA's own particles (move_item), and a second barrier before any score or
+// pbest row is written again. The swarm state stays in global memory with
+// the per-iteration kernels' layout and meaning.
+template <int CRIT>
+__global__ void __launch_bounds__(kThreads)
+    k_node_search(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
+                  const int32_t* __restrict__ list, int A, SwarmCoef co) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) float nsm[];
+  __shared__ int s_best;
+  const cg::cluster_group cl = cg::this_cluster();
+  pdl_trigger();
+  pdl_wait();
+  const int S = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int a = list[blockIdx.y];
+  const NodeDesc nd = nodes[a];
+  const int n = nd.seg_len, d = pr.d, ds = d | 1, B = pr.B, K = pr.K, P = pr.P, Pp = pr.Pp;
+  const int d4 = (d + 3) >> 2;
+  const bool weighted = pr.w != nullptr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* xs = nsm;
+  int32_t* ls = reinterpret_cast<int32_t*>(xs + (size_t)n * ds);
+  uint32_t* wsm = reinterpret_cast<uint32_t*>(ls + n);
+  uint32_t* hist = wsm + (weighted ? n : 0);
+  float* spos = reinterpret_cast<float*>(hist + (kThreads / 32) * B * K);
+  const int64_t e0 = nd.seg_start;
+  for (int r = warp; r < n; r += kThreads / 32)
+    for (int k = lane; k < d; k += 32) xs[r * ds + k] = pr.X[(e0 + r) * d + k];
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    ls[i] = pr.lab[e0 + i];
+    if (weighted) wsm[i] = pr.w[e0 + i];
+  }
+  __syncthreads();
+  uint32_t* h = hist + warp * B * K;
+  float* ap = spos + warp * d;
+  const EvalRes* cur = sw.cur + (int64_t)a * Pp;
+  const float* pbp = sw.pbest + (int64_t)a * Pp * d;
+  float* gbp = sw.gbest + (int64_t)a * d;
+  for (int t = 0; t <= sw.T; ++t) {
+    for (int p = rank * 8 + warp; p < P; p += 8 * S) {
+      const float* pos = sw.pos + ((int64_t)a * Pp + p) * d;
+      for (int k = lane; k < d; k += 32) ap[k] = pos[k];
+      __syncwarp();
+      int lo_o = INT_MAX, hi_o = INT_MIN;
+      for (int r = lane; r < n; r += 32) {
+        const float* x = xs + r * ds;
+        float z = 0.0f;
+        for (int k = 0; k < d; ++k) z = fmaf(x[k], ap[k], z);
+        const int o = f2ord(z);
+        lo_o = min(lo_o, o);
+        hi_o = max(hi_o, o);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        lo_o = min(lo_o, __shfl_xor_sync(0xffffffffu, lo_o, off));
+        hi_o = max(hi_o, __shfl_xor_sync(0xffffffffu, hi_o, off));
+      }
+      float zmin = 0.f, inv_w = 0.f;
+      bool ok = false;
+      if (lo_o != INT_MAX) {
+        const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+        inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+        zmin = lo;
+        ok = (hi > lo) && isfinite(inv_w);
+      }
+      for (int i = lane; i < B * K; i += 32) h[i] = 0u;
+      __syncwarp();
+      if (ok)
+        for (int r = lane; r < n; r += 32) {
+          const float* x = xs + r * ds;
+          float z = 0.0f;
+          for (int k = 0; k < d; ++k) z = fmaf(x[k], ap[k], z);
+          atomicAdd(&h[bin_of(z, zmin, inv_w, B) * K + ls[r]], weighted ? wsm[r] : 1u);
+        }
+      __syncwarp();
+      EvalRes res = invalid_res();
+      if (ok) {
+        res = warp_scan_cls<CRIT>(h, B, K, pr.min_leaf);
+        res.zmin = zmin;
+        res.inv_w = inv_w;
+      }
+      if (lane == 0) sw.cur[(int64_t)a * Pp + p] = res;
+      pbest_step(pr, sw, a, p, t, res);
+      __syncwarp();  // ap and h are reused by the warp's next particle
+    }
+    cl.sync();  // every score and pbest row of iteration t is written
+    const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
+    EvalRes* gnew_buf = sw.gb + (int64_t)(t & 1) * A;
+    if (warp == 0) {
+      const EvalRes gold = gold_buf[a];
+      EvalRes be;
+      const int bi = gbest_argmin(pr, cur, gold, t, &be);
+      if (lane == 0) {
+        s_best = bi;
+        if (rank == 0) {
+          gnew_buf[a] = bi >= 0 ? be : gold;
+          if (bi >= 0) {
+            sw.gpart[a] = bi;
+            sw.giter[a] = t;
+          }
+          if (sw.trace) {
+            const EvalRes g = bi >= 0 ? be : gold;
+            sw.trace[(int64_t)a * (sw.T + 1) + t] =
+                g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int best = s_best;
+    const float* gsrc = best >= 0 ? pbp + (int64_t)best * d : gbp;
+    if (rank == 0 && best >= 0)
+      for (int j = threadIdx.x; j < d; j += kThreads) gbp[j] = gsrc[j];
+    if (t < sw.T)
+      for (int item = threadIdx.x; item < P * d4; item += kThreads) {
+        const int p = item / d4;
+        if ((p >> 3) % S != rank) continue;  // another CTA's particle
+        move_item(pr, sw, co, nd.uid, a, t, p, item - p * d4, pbp, gsrc);
+      }
+    cl.sync();  // moves done before scores and pbest rows are rewritten
+  }
+}
+
 // Initial swarm of each node: x ~ U[-1,1)^d, v ~ 0.1 U[-1,1)^d.
 __global__ void k_swarm_init(Problem pr, Swarm sw,
                              const NodeDesc* __restrict__ nodes,
@@ -1420,6 +1552,11 @@ cudaError_t prepare_eval_kernels(const Problem& pr) {
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kProjSmem)))
       return e;
+  for (const void* f : {(const void*)k_node_search<SLM_GINI>,
+                        (const void*)k_node_search<SLM_ENTROPY>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kNodeSearchMaxSmem)))
+      return e;
   for (const void* f : {(const void*)k_hist_warp<SLM_GINI>, (const void*)k_hist_warp<SLM_ENTROPY>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kHistWarpMaxSmem)))
@@ -1544,6 +1681,37 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc*
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, list, bins_out, t, do_update);
+}
+
+size_t node_search_smem(const Problem& pr, int n) {
+  const size_t words = (size_t)n * (pr.d | 1) + (size_t)n * (pr.w ? 2 : 1) +
+                       (size_t)(kThreads / 32) * pr.B * pr.K + (size_t)(kThreads / 32) * pr.d;
+  return (words * 4 + 15) & ~(size_t)15;
+}
+
+cudaError_t launch_node_search(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                               const int32_t* list, int n_nodes, int A, int S, size_t smem,
+                               SwarmCoef co, cudaStream_t st) {
+  if (n_nodes <= 0) return cudaSuccess;
+  if (pr.crit == SLM_MSE || smem > kNodeSearchMaxSmem || S < 1 || S > 8)
+    return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)S, (unsigned)n_nodes, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  if (pr.crit == SLM_GINI)
+    return cudaLaunchKernelEx(&cfg, k_node_search<SLM_GINI>, pr, sw, nodes, list, A, co);
+  return cudaLaunchKernelEx(&cfg, k_node_search<SLM_ENTROPY>, pr, sw, nodes, list, A, co);
 }
 
 size_t hist_warp_smem_bytes(const Problem& pr) {

@@ -71,6 +71,8 @@ struct slm_ctx {
     bool gather = false; // rows gathered from the base rows by sample id
   };
   int tune = 1;
+  bool node_search = true;            // persistent search of batches that fit
+  int last_node_search = 0;           // CTAs per node of the last search (0: none)
   int small_node_max = kWarpNodeMax;  // warp-per-particle histograms up to this,
   int64_t small_min_pairs = -1;       // for at least this many (node, particle)
                                       // pairs (-1: 2 x SMs x warps per CTA)
@@ -941,6 +943,37 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
     CK(launch(c, SLM_K_SWARM_INIT, 0.0,
               [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
   }
+  // a classification batch whose nodes' rows all fit in shared memory runs
+  // its whole search in one persistent launch
+  if (!bp.on && pr.crit != SLM_MSE && c->node_search) {
+    size_t smax = 0;
+    bool fits = true;
+    for (const NodeDesc& nd : nodes) {
+      const size_t sm = node_search_smem(pr, nd.seg_len);
+      smax = std::max(smax, sm);
+      fits = fits && sm <= kNodeSearchMaxSmem;
+    }
+    if (fits) {
+      // CTAs per node: up to one particle per warp while the GPU has room
+      int S = 1;
+      const int want = std::min(8, (pr.P + 7) / 8);
+      while (S * 2 <= want && (int64_t)A * S * 2 <= c->n_sm) S *= 2;
+      std::vector<int32_t> lst(A);
+      std::iota(lst.begin(), lst.end(), 0);
+      CK(ensure(c->ws[S_HLIST], sizeof(int32_t) * A));
+      CK(cudaMemcpyAsync(c->ws[S_HLIST].p, lst.data(), sizeof(int32_t) * A,
+                         cudaMemcpyHostToDevice, c->stream));
+      const int32_t* dl = static_cast<const int32_t*>(c->ws[S_HLIST].p);
+      CK(launch(c, SLM_K_NODE_SEARCH, pairs * (p->n_iters + 1), [&] {
+        return launch_node_search(pr, sw, dn, dl, A, A, S, smax, co, c->stream);
+      }));
+      c->last_node_search = S;
+      sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
+      *sw_out = sw;
+      return SLM_OK;
+    }
+  }
+  c->last_node_search = 0;
   const int S = batch_split(c, pr, nodes);
   slm_ctx::Tiles tl{};
   if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
@@ -2114,6 +2147,18 @@ slm_status slm_kernel_stats(slm_ctx* c, int32_t kernel, int64_t* launches,
 slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
   if (!c || !launches) return SLM_EINVAL;
   *launches = c->launches;
+  return SLM_OK;
+}
+
+slm_status slm_set_node_search(slm_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return fail(c, SLM_EINVAL, "node search must be 0 or 1");
+  c->node_search = on == 1;
+  return SLM_OK;
+}
+
+slm_status slm_last_node_search(slm_ctx* c, int32_t* ctas_per_node) {
+  if (!c || !ctas_per_node) return SLM_EINVAL;
+  *ctas_per_node = c->last_node_search;
   return SLM_OK;
 }
 

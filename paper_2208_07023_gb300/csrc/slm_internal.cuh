@@ -171,6 +171,14 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
                              const NodeDesc* nodes, int A, int S,
                              int32_t* bins_out, int t, int do_update,
                              cudaStream_t st, const int32_t* list = nullptr);
+// Persistent search of classification nodes whose rows fit in shared memory:
+// all T + 1 iterations in one launch, a cluster of S (1..8) CTAs per node of
+// list[n_nodes] (A: the batch's node count, the gbest buffers' stride).
+constexpr size_t kNodeSearchMaxSmem = 226 * 1024;
+size_t node_search_smem(const Problem& pr, int n);
+cudaError_t launch_node_search(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
+                               const int32_t* list, int n_nodes, int A, int S, size_t smem,
+                               SwarmCoef co, cudaStream_t st);
 // Small classification nodes: one warp per (node, particle) of the n_nodes
 // nodes list[] names (scores, range reset and pbest step as k_hist_scan).
 constexpr size_t kHistWarpMaxSmem = 160 * 1024;

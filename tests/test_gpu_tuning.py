@@ -23,6 +23,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctx():
     c = context()
+    c.set_node_search(False)  # the per-iteration kernels these tests vary
     yield c
     c.close()
 
@@ -199,3 +200,51 @@ def test_invalid_tiles_are_rejected(ctx):
     assert S.lib().slm_set_small_nodes(ctx.handle, -1, 0) == 1
     assert S.lib().slm_set_small_nodes(ctx.handle, 16, -2) == 1
     assert S.lib().slm_set_tuning(ctx.handle, -1) == 1
+
+
+@pytest.mark.parametrize("crit,bootstrap", [("gini", True), ("entropy", False),
+                                             ("gini", False), ("entropy", True)])
+def test_persistent_node_search_gives_the_same_forest(ctx, crit, bootstrap):
+    """Whole searches in one launch (nodes resident in shared memory) against
+    the per-iteration kernels: identical trees, also when only the deeper
+    levels fit."""
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(4000, 12, 6, seed=31)
+    p = gpu_params(S, crit, 6, 40, 12, 64, min_leaf=8, seed=3, max_depth=6, n_trees=3,
+                   bootstrap=bootstrap)
+    out = []
+    for on in (False, True):
+        ctx.set_node_search(on)
+        out.append(forest_arrays(ctx, p, wl))
+        if on:
+            assert ctx.last_node_search() >= 1
+    ctx.set_node_search(False)
+    same_forest(out[0], out[1])
+    # rows too large for shared memory at the top levels, resident below
+    wl2 = W.gmm(20000, 48, 4, seed=32)
+    p2 = gpu_params(S, crit, 4, 32, 8, 128, min_leaf=20, seed=4, max_depth=7)
+    out2 = []
+    for on in (False, True):
+        ctx.set_node_search(on)
+        out2.append(forest_arrays(ctx, p2, wl2))
+    ctx.set_node_search(False)
+    same_forest(out2[0], out2[1])
+
+
+@pytest.mark.parametrize("P,n,d", [(32, 2000, 16), (64, 700, 64), (20, 150, 5), (48, 3000, 8)])
+def test_persistent_node_search_gives_the_same_trajectory(ctx, P, n, d):
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(n, d, 4, seed=P + d)
+    for crit in ("gini", "entropy"):
+        p = gpu_params(S, crit, 4, P, 30, 64, min_leaf=2, seed=9)
+        res = []
+        for on in (False, True):
+            ctx.set_node_search(on)
+            res.append(ctx.node_split(p, wl.X, labels=wl.labels, node_uid=11, want_trace=True))
+            assert ctx.last_node_search() == (1 if on else 0) or (on and ctx.last_node_search() > 1)
+        ctx.set_node_search(False)
+        a, b = res
+        assert np.array_equal(a["trace"], b["trace"])
+        assert np.array_equal(a["gbest"].view(np.uint32), b["gbest"].view(np.uint32))
+        assert (a["bin"], a["n_left"], a["iter_of_best"], a["particle"]) == \
+            (b["bin"], b["n_left"], b["iter_of_best"], b["particle"])
