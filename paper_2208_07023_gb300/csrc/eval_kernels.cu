@@ -646,12 +646,12 @@ __device__ __forceinline__ void move_item(const Problem& pr, const Swarm& sw, co
 // gb[(t-1)&1], written to gb[t&1]) so no CTA reads a score another CTA of
 // the launch is writing; the gbest position of a new best is its pbest row.
 __global__ void __launch_bounds__(128)
-    k_move(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int t, SwarmCoef co) {
+    k_move(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int t, SwarmCoef co,
+           const int32_t* __restrict__ list, int A) {
   pdl_trigger();
   pdl_wait();
   __shared__ int s_best;
-  const int a = blockIdx.x;
-  const int A = gridDim.x;
+  const int a = list ? list[blockIdx.x] : (int)blockIdx.x;
   const int d = pr.d, d4 = (d + 3) >> 2, Pp = pr.Pp;
   const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
   EvalRes* gnew_buf = sw.gb + (int64_t)(t & 1) * A;
@@ -1214,17 +1214,29 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // Persistent search of small classification nodes: all T + 1 iterations of
-// Algorithm 1 in one launch. A cluster of S CTAs per node (grid (S, nodes)):
-// every CTA keeps the node's rows (row stride d | 1, conflict-free per
-// lane), labels and multiplicities in shared memory; warp w of rank r
-// evaluates particles p with p / 8 = r (mod S), p = w (mod 8): z by the
-// same sequential fused multiply-adds as k_project, its exact range, a
-// warp-private histogram and warp_scan_cls (the scores of the
-// per-iteration kernels), then the pbest step. A cluster barrier, the gbest
-// step of k_move (every CTA finds it; rank 0 records it), the move of each
-// CTA's own particles (move_item), and a second barrier before any score or
-// pbest row is written again. The swarm state stays in global memory with
-// the per-iteration kernels' layout and meaning.
+// Algorithm 1 in one launch. A cluster of S CTAs per node (grid (S, nodes));
+// rank r evaluates the particle groups g = r, r + S, ... (particles
+// 8g .. 8g+7). Every CTA keeps the node's rows, labels and multiplicities in
+// shared memory. Per group, the whole CTA projects the group's 8 particles
+// onto every row (each thread 4 rows x 8 particles in registers; rows as
+// 16-byte chunks, XOR-swizzled so that lanes on consecutive rows read
+// distinct banks; every z is the sequential fused multiply-add over the
+// features of k_project) into a shared z buffer; then warp w takes particle
+// 8g + w: its exact range, a warp-private histogram, warp_scan_cls (the
+// scores of the per-iteration kernels) and the pbest step. A cluster
+// barrier, the gbest step of k_move (every CTA finds it; rank 0 records it),
+// the move of each CTA's own particles (move_item), and a second barrier
+// before any score or pbest row is written again. The swarm state stays in
+// global memory with the per-iteration kernels' layout and meaning. d must
+// be a multiple of 4.
+
+// Position in a row of 16-byte chunk c (C chunks per row) of row r: rows r
+// .. r+7 then fall in distinct bank groups.
+__device__ __forceinline__ int node_chunk(int r, int c, int C) {
+  const int x = (C & 1) ? 0 : (C & 3) == 2 ? (r >> 2) & 1 : (C & 7) == 4 ? (r >> 1) & 3 : r & 7;
+  return c ^ x;
+}
+
 template <int CRIT>
 __global__ void __launch_bounds__(kThreads)
     k_node_search(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
@@ -1238,74 +1250,116 @@ __global__ void __launch_bounds__(kThreads)
   const int S = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int a = list[blockIdx.y];
   const NodeDesc nd = nodes[a];
-  const int n = nd.seg_len, d = pr.d, ds = d | 1, B = pr.B, K = pr.K, P = pr.P, Pp = pr.Pp;
+  const int n = nd.seg_len, d = pr.d, C = d >> 2, B = pr.B, K = pr.K, P = pr.P, Pp = pr.Pp;
   const int d4 = (d + 3) >> 2;
   const bool weighted = pr.w != nullptr;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* xs = nsm;
-  int32_t* ls = reinterpret_cast<int32_t*>(xs + (size_t)n * ds);
+  float* xs = nsm;                                  // [n][d], swizzled chunks
+  float* zb = xs + (size_t)n * d;                   // [8][n]
+  float* apos = zb + (size_t)8 * n;                 // [8][d]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(apos + 8 * d);  // [8][B * K]
+  int32_t* ls = reinterpret_cast<int32_t*>(hist + (kThreads / 32) * B * K);
   uint32_t* wsm = reinterpret_cast<uint32_t*>(ls + n);
-  uint32_t* hist = wsm + (weighted ? n : 0);
-  float* spos = reinterpret_cast<float*>(hist + (kThreads / 32) * B * K);
   const int64_t e0 = nd.seg_start;
-  for (int r = warp; r < n; r += kThreads / 32)
-    for (int k = lane; k < d; k += 32) xs[r * ds + k] = pr.X[(e0 + r) * d + k];
+  for (int q = threadIdx.x; q < n * C; q += kThreads) {
+    const int r = q / C, c = q - r * C;
+    *reinterpret_cast<float4*>(xs + (size_t)r * d + 4 * node_chunk(r, c, C)) =
+        *reinterpret_cast<const float4*>(pr.X + (e0 + r) * d + 4 * c);
+  }
   for (int i = threadIdx.x; i < n; i += kThreads) {
     ls[i] = pr.lab[e0 + i];
     if (weighted) wsm[i] = pr.w[e0 + i];
   }
   __syncthreads();
   uint32_t* h = hist + warp * B * K;
-  float* ap = spos + warp * d;
   const EvalRes* cur = sw.cur + (int64_t)a * Pp;
   const float* pbp = sw.pbest + (int64_t)a * Pp * d;
   float* gbp = sw.gbest + (int64_t)a * d;
+  const int n_groups = (P + 7) >> 3;
   for (int t = 0; t <= sw.T; ++t) {
-    for (int p = rank * 8 + warp; p < P; p += 8 * S) {
-      const float* pos = sw.pos + ((int64_t)a * Pp + p) * d;
-      for (int k = lane; k < d; k += 32) ap[k] = pos[k];
-      __syncwarp();
-      int lo_o = INT_MAX, hi_o = INT_MIN;
-      for (int r = lane; r < n; r += 32) {
-        const float* x = xs + r * ds;
-        float z = 0.0f;
-        for (int k = 0; k < d; ++k) z = fmaf(x[k], ap[k], z);
-        const int o = f2ord(z);
-        lo_o = min(lo_o, o);
-        hi_o = max(hi_o, o);
+    for (int g = rank; g < n_groups; g += S) {
+      // the group's positions (zero past P)
+      for (int q = threadIdx.x; q < 8 * d; q += kThreads) {
+        const int j = q / d, k = q - j * d;
+        const int p = 8 * g + j;
+        apos[q] = p < P ? sw.pos[((int64_t)a * Pp + p) * d + k] : 0.0f;
       }
+      __syncthreads();
+      // z of the group's 8 particles on every row, 4 rows per thread at once
+      for (int r0 = threadIdx.x; r0 < n; r0 += 4 * kThreads) {
+        float acc[4][8];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        lo_o = min(lo_o, __shfl_xor_sync(0xffffffffu, lo_o, off));
-        hi_o = max(hi_o, __shfl_xor_sync(0xffffffffu, hi_o, off));
-      }
-      float zmin = 0.f, inv_w = 0.f;
-      bool ok = false;
-      if (lo_o != INT_MAX) {
-        const float lo = ord2f(lo_o), hi = ord2f(hi_o);
-        inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
-        zmin = lo;
-        ok = (hi > lo) && isfinite(inv_w);
-      }
-      for (int i = lane; i < B * K; i += 32) h[i] = 0u;
-      __syncwarp();
-      if (ok)
-        for (int r = lane; r < n; r += 32) {
-          const float* x = xs + r * ds;
-          float z = 0.0f;
-          for (int k = 0; k < d; ++k) z = fmaf(x[k], ap[k], z);
-          atomicAdd(&h[bin_of(z, zmin, inv_w, B) * K + ls[r]], weighted ? wsm[r] : 1u);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int c = 0; c < C; ++c) {
+          float4 xv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = r0 + i * kThreads;
+            xv[i] = r < n ? *reinterpret_cast<const float4*>(xs + (size_t)r * d +
+                                                             4 * node_chunk(r, c, C))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 pv = *reinterpret_cast<const float4*>(apos + j * d + 4 * c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              acc[i][j] = fmaf(xv[i].x, pv.x, acc[i][j]);
+              acc[i][j] = fmaf(xv[i].y, pv.y, acc[i][j]);
+              acc[i][j] = fmaf(xv[i].z, pv.z, acc[i][j]);
+              acc[i][j] = fmaf(xv[i].w, pv.w, acc[i][j]);
+            }
+          }
         }
-      __syncwarp();
-      EvalRes res = invalid_res();
-      if (ok) {
-        res = warp_scan_cls<CRIT>(h, B, K, pr.min_leaf);
-        res.zmin = zmin;
-        res.inv_w = inv_w;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = r0 + i * kThreads;
+          if (r < n)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) zb[(size_t)j * n + r] = acc[i][j];
+        }
       }
-      if (lane == 0) sw.cur[(int64_t)a * Pp + p] = res;
-      pbest_step(pr, sw, a, p, t, res);
-      __syncwarp();  // ap and h are reused by the warp's next particle
+      __syncthreads();
+      const int p = 8 * g + warp;
+      if (p < P) {
+        const float* zp = zb + (size_t)warp * n;
+        int lo_o = INT_MAX, hi_o = INT_MIN;
+        for (int r = lane; r < n; r += 32) {
+          const int o = f2ord(zp[r]);
+          lo_o = min(lo_o, o);
+          hi_o = max(hi_o, o);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          lo_o = min(lo_o, __shfl_xor_sync(0xffffffffu, lo_o, off));
+          hi_o = max(hi_o, __shfl_xor_sync(0xffffffffu, hi_o, off));
+        }
+        float zmin = 0.f, inv_w = 0.f;
+        bool ok = false;
+        if (lo_o != INT_MAX) {
+          const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+          inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+          zmin = lo;
+          ok = (hi > lo) && isfinite(inv_w);
+        }
+        for (int i = lane; i < B * K; i += 32) h[i] = 0u;
+        __syncwarp();
+        if (ok)
+          for (int r = lane; r < n; r += 32)
+            atomicAdd(&h[bin_of(zp[r], zmin, inv_w, B) * K + ls[r]], weighted ? wsm[r] : 1u);
+        __syncwarp();
+        EvalRes res = invalid_res();
+        if (ok) {
+          res = warp_scan_cls<CRIT>(h, B, K, pr.min_leaf);
+          res.zmin = zmin;
+          res.inv_w = inv_w;
+        }
+        if (lane == 0) sw.cur[(int64_t)a * Pp + p] = res;
+        pbest_step(pr, sw, a, p, t, res);
+      }
+      __syncthreads();  // zb and apos are refilled by the next group
     }
     cl.sync();  // every score and pbest row of iteration t is written
     const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
@@ -1323,9 +1377,9 @@ __global__ void __launch_bounds__(kThreads)
             sw.giter[a] = t;
           }
           if (sw.trace) {
-            const EvalRes g = bi >= 0 ? be : gold;
+            const EvalRes gr = bi >= 0 ? be : gold;
             sw.trace[(int64_t)a * (sw.T + 1) + t] =
-                g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
+                gr.valid ? gr.loss : __longlong_as_double(0x7ff0000000000000LL);
           }
         }
       }
@@ -1684,8 +1738,9 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc*
 }
 
 size_t node_search_smem(const Problem& pr, int n) {
-  const size_t words = (size_t)n * (pr.d | 1) + (size_t)n * (pr.w ? 2 : 1) +
-                       (size_t)(kThreads / 32) * pr.B * pr.K + (size_t)(kThreads / 32) * pr.d;
+  if (pr.d % 4) return SIZE_MAX;  // 16-byte row chunks
+  const size_t words = (size_t)n * pr.d + (size_t)8 * n + (size_t)8 * pr.d +
+                       (size_t)(kThreads / 32) * pr.B * pr.K + (size_t)n * (pr.w ? 2 : 1);
   return (words * 4 + 15) & ~(size_t)15;
 }
 
@@ -1746,12 +1801,13 @@ cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc*
 }
 
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
-                        int t, SwarmCoef co, cudaStream_t st) {
-  if (A <= 0) return cudaSuccess;
+                        int t, SwarmCoef co, cudaStream_t st, const int32_t* list, int n_list) {
+  const int n_nodes = list ? n_list : A;
+  if (n_nodes <= 0) return cudaSuccess;
   const int items = pr.P * ((pr.d + 3) / 4);
   const int per_node = t >= sw.T ? 1 : (items + 127) / 128;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)A, (unsigned)per_node, 1);
+  cfg.gridDim = dim3((unsigned)n_nodes, (unsigned)per_node, 1);
   cfg.blockDim = dim3(128, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1759,7 +1815,7 @@ cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* node
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_move, pr, sw, nodes, t, co);
+  return cudaLaunchKernelEx(&cfg, k_move, pr, sw, nodes, t, co, list, A);
 }
 
 cudaError_t launch_swarm_uniforms(uint64_t seed, uint32_t uid, uint32_t t,

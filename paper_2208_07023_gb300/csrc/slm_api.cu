@@ -36,8 +36,9 @@ enum Slot {
   // learned proposal: node statistics, network work space, training data
   S_PSTATS, S_PYR, S_PACC, S_PWK, S_PWORK, S_PLOSS, W_PS, W_PD, W_PT, W_PIDX, W_PBS, W_PBD,
   W_PBT, W_PRHO, W_PMU, W_PPOS,
-  // node lists of the histogram kernels (large nodes, then small ones)
-  S_HLIST,
+  // node lists of the histogram kernels (large nodes, then small ones) and
+  // of the persistent search
+  S_HLIST, S_NLIST,
   N_SLOTS
 };
 
@@ -71,8 +72,10 @@ struct slm_ctx {
     bool gather = false; // rows gathered from the base rows by sample id
   };
   int tune = 1;
-  bool node_search = true;            // persistent search of batches that fit
+  bool node_search = true;            // persistent search of the nodes that fit
   int last_node_search = 0;           // CTAs per node of the last search (0: none)
+  cudaStream_t side = nullptr;        // the persistent search beside the others
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int small_node_max = kWarpNodeMax;  // warp-per-particle histograms up to this,
   int64_t small_min_pairs = -1;       // for at least this many (node, particle)
                                       // pairs (-1: 2 x SMs x warps per CTA)
@@ -456,46 +459,69 @@ struct Bf16Plan {
 // the cluster kernel.
 struct HistPlan {
   bool on = false;
-  const int32_t* large = nullptr;
+  const int32_t* large = nullptr;  // cluster kernel
   int n_large = 0, S_large = 1;
   double pairs_large = 0.0;
-  const int32_t* small = nullptr;
+  const int32_t* small = nullptr;  // warp kernel
   int n_small = 0;
   double pairs_small = 0.0;
+  const int32_t* moved = nullptr;  // the swarm update's nodes (null: all)
+  int n_moved = 0;
 };
 
+// Lists of the histogram kernels and the swarm update for the nodes `in`
+// marks (all when empty): set when only some nodes of the batch run the
+// per-iteration kernels, or when enough small nodes take the warp kernel.
 slm_status setup_hist_plan(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>& nodes,
-                           HistPlan* plan) {
+                           const std::vector<char>& in, HistPlan* plan) {
   *plan = HistPlan{};
-  if (c->small_node_max <= 0 || !hist_warp_ok(pr)) return SLM_OK;
-  std::vector<int32_t> lst;
+  const bool subset = !in.empty();
+  auto member = [&](int a) { return !subset || in[a] != 0; };
+  const bool warp_ok = c->small_node_max > 0 && hist_warp_ok(pr);
+  std::vector<int32_t> large, small;
   int64_t max_large = 0;
-  for (int a = 0; a < (int)nodes.size(); ++a)
-    if (nodes[a].seg_len > c->small_node_max) {
-      lst.push_back(a);
+  for (int a = 0; a < (int)nodes.size(); ++a) {
+    if (!member(a)) continue;
+    if (warp_ok && nodes[a].seg_len <= c->small_node_max) {
+      small.push_back(a);
+      plan->pairs_small += (double)nodes[a].seg_len * pr.P;
+    } else {
+      large.push_back(a);
       max_large = std::max<int64_t>(max_large, nodes[a].seg_len);
       plan->pairs_large += (double)nodes[a].seg_len * pr.P;
     }
-  plan->n_large = (int)lst.size();
-  for (int a = 0; a < (int)nodes.size(); ++a)
-    if (nodes[a].seg_len <= c->small_node_max) {
-      lst.push_back(a);
-      plan->pairs_small += (double)nodes[a].seg_len * pr.P;
-    }
-  plan->n_small = (int)lst.size() - plan->n_large;
-  // one warp per (node, particle) only pays when the small nodes alone give
-  // every SM several warps; a few small nodes are split across clusters
+  }
   const int64_t min_pairs =
       c->small_min_pairs >= 0 ? c->small_min_pairs : 2LL * c->n_sm * (kThreads / 32);
-  if ((int64_t)plan->n_small * pr.P < min_pairs) {
-    *plan = HistPlan{};
-    return SLM_OK;
+  if ((int64_t)small.size() * pr.P < min_pairs) {  // too few for the warp kernel
+    for (int32_t a : small) {
+      large.push_back(a);
+      max_large = std::max<int64_t>(max_large, nodes[a].seg_len);
+    }
+    plan->pairs_large += plan->pairs_small;
+    plan->pairs_small = 0.0;
+    small.clear();
+    std::sort(large.begin(), large.end());
   }
+  if (!subset && small.empty()) return SLM_OK;  // the cluster kernel on every node
+  std::vector<int32_t> lst(large);
+  lst.insert(lst.end(), small.begin(), small.end());
+  std::vector<int32_t> moved;
+  for (int a = 0; a < (int)nodes.size(); ++a)
+    if (member(a)) moved.push_back(a);
+  lst.insert(lst.end(), moved.begin(), moved.end());
   CK(ensure(c->ws[S_HLIST], sizeof(int32_t) * lst.size()));
   CK(cudaMemcpyAsync(c->ws[S_HLIST].p, lst.data(), sizeof(int32_t) * lst.size(),
                      cudaMemcpyHostToDevice, c->stream));
-  plan->large = static_cast<const int32_t*>(c->ws[S_HLIST].p);
-  plan->small = plan->large + plan->n_large;
+  const int32_t* base = static_cast<const int32_t*>(c->ws[S_HLIST].p);
+  plan->large = base;
+  plan->n_large = (int)large.size();
+  plan->small = base + large.size();
+  plan->n_small = (int)small.size();
+  if (subset) {
+    plan->moved = base + large.size() + small.size();
+    plan->n_moved = (int)moved.size();
+  }
   if (plan->n_large)
     plan->S_large = hist_split(pr, plan->n_large, max_large, c->n_sm, hist_max_cluster(pr));
   plan->on = true;
@@ -634,17 +660,20 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
         return launch_hist_scan(pr, sw, dn, hp->n_large, hp->S_large, nullptr, t, co ? 1 : 0,
                                 c->stream, hp->large);
       }));
-    CK(launch(c, SLM_K_HIST_SCAN, hp->pairs_small, [&] {
-      return launch_hist_warp(pr, sw, dn, hp->small, hp->n_small, t, co ? 1 : 0, c->stream);
-    }));
+    if (hp->n_small)
+      CK(launch(c, SLM_K_HIST_SCAN, hp->pairs_small, [&] {
+        return launch_hist_warp(pr, sw, dn, hp->small, hp->n_small, t, co ? 1 : 0, c->stream);
+      }));
   } else {
     CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
       return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
     }));
   }
   if (co)
-    CK(launch(c, SLM_K_SWARM_UPDATE, 0.0,
-              [&] { return launch_move(pr, sw, dn, A, t, *co, c->stream); }));
+    CK(launch(c, SLM_K_SWARM_UPDATE, 0.0, [&] {
+      return launch_move(pr, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
+                         hp ? hp->n_moved : 0);
+    }));
   return SLM_OK;
 }
 
@@ -925,14 +954,43 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
                       Swarm* sw_out) {
   const int A = (int)nodes.size();
-  const std::vector<WorkTile> tiles = plan_tiles(nodes);
+  // classification nodes (FP32 form) whose rows fit in shared memory run
+  // their whole search in one persistent launch; the others (`in`) run the
+  // per-iteration kernels, beside it on the context's second stream
+  std::vector<char> resident(A, 0);
+  int n_res = 0;
+  size_t smax = 0;
+  if (c->node_search && p->proj != SLM_PROJ_BF16_TOPK && p->criterion != SLM_MSE)
+    for (int a = 0; a < A; ++a) {
+      const size_t sm = node_search_smem(pr, nodes[a].seg_len);
+      if (sm <= kNodeSearchMaxSmem) {
+        resident[a] = 1;
+        ++n_res;
+        smax = std::max(smax, sm);
+      }
+    }
+  std::vector<char> in;
+  if (n_res > 0 && n_res < A) {
+    in.resize(A);
+    for (int a = 0; a < A; ++a) in[a] = !resident[a];
+  }
+  std::vector<WorkTile> tiles;
+  double pairs = 0.0, pairs_res = 0.0;
+  for (int a = 0; a < A; ++a) {
+    const double np = (double)nodes[a].seg_len * pr.P;
+    if (resident[a]) {
+      pairs_res += np;
+      continue;
+    }
+    pairs += np;
+    for (int r = 0; r < nodes[a].seg_len; r += kTS)
+      tiles.push_back(WorkTile{a, nodes[a].seg_start + r, std::min(kTS, nodes[a].seg_len - r), 0});
+  }
   Swarm sw;
   slm_status s = setup_swarm(c, pr, A, p->n_iters, want_trace, nodes, tiles, &sw);
   if (s) return s;
   const SwarmCoef co{p->inertia, p->c1, p->c2, p->seed};
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
-  double pairs = 0.0;
-  for (const NodeDesc& nd : nodes) pairs += (double)nd.seg_len * pr.P;
   Bf16Plan bp;
   if (p->proj == SLM_PROJ_BF16_TOPK &&
       (s = setup_bf16(c, pr, nodes, std::min(p->topk, p->n_particles), true, &sw, &bp)))
@@ -943,68 +1001,75 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
     CK(launch(c, SLM_K_SWARM_INIT, 0.0,
               [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
   }
-  // a classification batch whose nodes' rows all fit in shared memory runs
-  // its whole search in one persistent launch
-  if (!bp.on && pr.crit != SLM_MSE && c->node_search) {
-    size_t smax = 0;
-    bool fits = true;
-    for (const NodeDesc& nd : nodes) {
-      const size_t sm = node_search_smem(pr, nd.seg_len);
-      smax = std::max(smax, sm);
-      fits = fits && sm <= kNodeSearchMaxSmem;
-    }
-    if (fits) {
-      // CTAs per node: up to one particle per warp while the GPU has room
-      int S = 1;
-      const int want = std::min(8, (pr.P + 7) / 8);
-      while (S * 2 <= want && (int64_t)A * S * 2 <= c->n_sm) S *= 2;
-      std::vector<int32_t> lst(A);
-      std::iota(lst.begin(), lst.end(), 0);
-      CK(ensure(c->ws[S_HLIST], sizeof(int32_t) * A));
-      CK(cudaMemcpyAsync(c->ws[S_HLIST].p, lst.data(), sizeof(int32_t) * A,
-                         cudaMemcpyHostToDevice, c->stream));
-      const int32_t* dl = static_cast<const int32_t*>(c->ws[S_HLIST].p);
-      CK(launch(c, SLM_K_NODE_SEARCH, pairs * (p->n_iters + 1), [&] {
-        return launch_node_search(pr, sw, dn, dl, A, A, S, smax, co, c->stream);
-      }));
-      c->last_node_search = S;
-      sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
-      *sw_out = sw;
-      return SLM_OK;
-    }
-  }
   c->last_node_search = 0;
-  const int S = batch_split(c, pr, nodes);
-  slm_ctx::Tiles tl{};
-  if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
-  HistPlan hp;
-  if (!bp.on && (s = setup_hist_plan(c, pr, nodes, &hp))) return s;
-  c->cur = tl;
-  c->last = tl;
-  std::string key;
-  if (c->graphs && !c->prof) {
-    KeyWriter kw;
-    kw.problem(pr);
-    kw.swarm(sw);
-    kw.put(A); kw.put((int)tiles.size()); kw.put(S); kw.put(p->n_iters); kw.put(c->n_sm);
-    kw.put(co.inertia); kw.put(co.c1); kw.put(co.c2); kw.put(co.seed);
-    kw.put(tl.pg); kw.put(tl.cps); kw.put(tl.gather); kw.put(pairs);
-    kw.put(dn); kw.put(ws_ptr<WorkTile>(c, S_TILES)); kw.put(ws_ptr<WorkTile>(c, S_MTILES));
-    kw.put(bp.on); kw.put(bp.k); kw.put(bp.kp); kw.put(bp.n_mtiles); kw.put(bp.grid);
-    kw.put(bp.S_k); kw.put(bp.pairs_k); kw.put(bp.posb); kw.put(bp.sel); kw.put(bp.inv);
-    kw.put(hp.on); kw.put(hp.large); kw.put(hp.n_large); kw.put(hp.S_large);
-    kw.put(hp.pairs_large); kw.put(hp.small); kw.put(hp.n_small); kw.put(hp.pairs_small);
-    if (bp.on) {
-      kw.problem(bp.pr_k);
-      kw.swarm(bp.sw_k);
+  bool joined = true;
+  if (n_res > 0) {
+    // CTAs per node: up to one particle per warp while the GPU has room
+    int S = 1;
+    const int want = std::min(8, (pr.P + 7) / 8);
+    while (S * 2 <= want && (int64_t)n_res * S * 2 <= c->n_sm) S *= 2;
+    std::vector<int32_t> lst;
+    for (int a = 0; a < A; ++a)
+      if (resident[a]) lst.push_back(a);
+    CK(ensure(c->ws[S_NLIST], sizeof(int32_t) * lst.size()));
+    CK(cudaMemcpyAsync(c->ws[S_NLIST].p, lst.data(), sizeof(int32_t) * lst.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    const int32_t* dl = static_cast<const int32_t*>(c->ws[S_NLIST].p);
+    cudaStream_t st = c->stream;
+    if (n_res < A && !c->prof) {  // overlap with the per-iteration kernels
+      if (!c->side) CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      if (!c->ev_fork) CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      if (!c->ev_join) CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+      CK(cudaEventRecord(c->ev_fork, c->stream));
+      CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      st = c->side;
+      joined = false;
     }
-    key = std::move(kw.b);
+    CK(launch(c, SLM_K_NODE_SEARCH, pairs_res * (p->n_iters + 1), [&] {
+      return launch_node_search(pr, sw, dn, dl, (int)lst.size(), A, S, smax, co, st);
+    }));
+    if (!joined) CK(cudaEventRecord(c->ev_join, st));
+    c->last_node_search = S;
   }
-  s = run_iterations(c, p->n_iters, key, [&](int t) {
-    return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp, &hp);
-  });
-  c->cur = slm_ctx::Tiles{};
-  if (s) return s;
+  if (n_res < A) {
+    const int S = batch_split(c, pr, nodes);
+    slm_ctx::Tiles tl{};
+    if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
+    HistPlan hp;
+    if (!bp.on && (s = setup_hist_plan(c, pr, nodes, in, &hp))) return s;
+    c->cur = tl;
+    c->last = tl;
+    std::string key;
+    if (c->graphs && !c->prof) {
+      KeyWriter kw;
+      kw.problem(pr);
+      kw.swarm(sw);
+      kw.put(A); kw.put((int)tiles.size()); kw.put(S); kw.put(p->n_iters); kw.put(c->n_sm);
+      kw.put(co.inertia); kw.put(co.c1); kw.put(co.c2); kw.put(co.seed);
+      kw.put(tl.pg); kw.put(tl.cps); kw.put(tl.gather); kw.put(pairs);
+      kw.put(dn); kw.put(ws_ptr<WorkTile>(c, S_TILES)); kw.put(ws_ptr<WorkTile>(c, S_MTILES));
+      kw.put(bp.on); kw.put(bp.k); kw.put(bp.kp); kw.put(bp.n_mtiles); kw.put(bp.grid);
+      kw.put(bp.S_k); kw.put(bp.pairs_k); kw.put(bp.posb); kw.put(bp.sel); kw.put(bp.inv);
+      kw.put(hp.on); kw.put(hp.large); kw.put(hp.n_large); kw.put(hp.S_large);
+      kw.put(hp.pairs_large); kw.put(hp.small); kw.put(hp.n_small); kw.put(hp.pairs_small);
+      kw.put(hp.moved); kw.put(hp.n_moved);
+      if (bp.on) {
+        kw.problem(bp.pr_k);
+        kw.swarm(bp.sw_k);
+      }
+      key = std::move(kw.b);
+    }
+    s = run_iterations(c, p->n_iters, key, [&](int t) {
+      return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp,
+                         &hp);
+    });
+    c->cur = slm_ctx::Tiles{};
+    if (!joined) {
+      const cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+      if (!s && e) s = cuda_fail(c, e, "joining the persistent search");
+    }
+    if (s) return s;
+  }
   sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
   *sw_out = sw;
   return SLM_OK;
@@ -1105,6 +1170,12 @@ void slm_destroy(slm_ctx* c) {
   for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
   for (auto& ge : c->graph_cache) cudaGraphExecDestroy(ge.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 
@@ -1688,6 +1759,13 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   CK(cudaMemsetAsync(f->p_wl.p, 0, sizeof(unsigned long long) * A, c->stream));
   if (slm_status s = reset_status(c)) return s;
   const NodeDesc* dsn = ws_ptr<NodeDesc>(c, S_NODES);
+  // every searched node's tiles (the search uploads only the tiles of the
+  // nodes its per-iteration kernels project)
+  const std::vector<WorkTile> ptiles = plan_tiles(snodes);
+  CK(ensure(c->ws[S_TILES], sizeof(WorkTile) * ptiles.size()));
+  if (!ptiles.empty())
+    CK(cudaMemcpyAsync(c->ws[S_TILES].p, ptiles.data(), sizeof(WorkTile) * ptiles.size(),
+                       cudaMemcpyHostToDevice, c->stream));
   const WorkTile* dst_tiles = ws_ptr<WorkTile>(c, S_TILES);
   PartAcc pacc{static_cast<unsigned long long*>(f->p_lk.p),
                static_cast<unsigned long long*>(f->p_wl.p)};

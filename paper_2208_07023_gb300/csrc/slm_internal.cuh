@@ -187,9 +187,10 @@ cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc*
                              const int32_t* list, int n_nodes, int t, int do_update,
                              cudaStream_t st);
 // gbest step of iteration t and (t < T) the Eq. pso-1 move of every particle
-// of A nodes to iteration t+1.
+// of A nodes to iteration t+1 (of the n_list nodes list[] names, when set).
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
-                        int A, int t, SwarmCoef co, cudaStream_t st);
+                        int A, int t, SwarmCoef co, cudaStream_t st,
+                        const int32_t* list = nullptr, int n_list = 0);
 // ---- bfloat16 projection on the tensor cores (mma_kernels.cu) -------------
 // Converts n_blocks blocks of R rows of src[*, d] (float, row stride d; rows
 // at or past n_src_rows read as 0) to bfloat16 in the K-major, unswizzled

@@ -241,7 +241,8 @@ def test_persistent_node_search_gives_the_same_trajectory(ctx, P, n, d):
         for on in (False, True):
             ctx.set_node_search(on)
             res.append(ctx.node_split(p, wl.X, labels=wl.labels, node_uid=11, want_trace=True))
-            assert ctx.last_node_search() == (1 if on else 0) or (on and ctx.last_node_search() > 1)
+            # rows go to shared memory in 16-byte chunks: d a multiple of 4
+            assert (ctx.last_node_search() >= 1) == (on and d % 4 == 0)
         ctx.set_node_search(False)
         a, b = res
         assert np.array_equal(a["trace"], b["trace"])
