@@ -1221,9 +1221,10 @@ __global__ void __launch_bounds__(kThreads)
 // onto every row (each thread 4 rows x 8 particles in registers; rows as
 // 16-byte chunks, XOR-swizzled so that lanes on consecutive rows read
 // distinct banks; every z is the sequential fused multiply-add over the
-// features of k_project) into a shared z buffer; then warp w takes particle
-// 8g + w: its exact range, a warp-private histogram, warp_scan_cls (the
-// scores of the per-iteration kernels) and the pbest step. A cluster
+// features of k_project) into a shared z buffer, folding in each particle's
+// exact range; then warps 2j and 2j+1 bin particle 8g + j's halves of the
+// rows into their own histograms, warp 2j adds them and runs warp_scan_cls
+// (the scores of the per-iteration kernels) and the pbest step. A cluster
 // barrier, the gbest step of k_move (every CTA finds it; rank 0 records it),
 // the move of each CTA's own particles (move_item), and a second barrier
 // before any score or pbest row is written again. The swarm state stays in
@@ -1238,12 +1239,14 @@ __device__ __forceinline__ int node_chunk(int r, int c, int C) {
 }
 
 template <int CRIT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kNodeThreads)
     k_node_search(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
                   const int32_t* __restrict__ list, int A, SwarmCoef co) {
   namespace cg = cooperative_groups;
+  constexpr int kW = kNodeThreads / 32;  // 16 warps: two per particle of a group
   extern __shared__ __align__(16) float nsm[];
   __shared__ int s_best;
+  __shared__ int s_lo[8], s_hi[8];
   const cg::cluster_group cl = cg::this_cluster();
   pdl_trigger();
   pdl_wait();
@@ -1257,101 +1260,131 @@ __global__ void __launch_bounds__(kThreads)
   float* xs = nsm;                                  // [n][d], swizzled chunks
   float* zb = xs + (size_t)n * d;                   // [8][n]
   float* apos = zb + (size_t)8 * n;                 // [8][d]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(apos + 8 * d);  // [8][B * K]
-  int32_t* ls = reinterpret_cast<int32_t*>(hist + (kThreads / 32) * B * K);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(apos + 8 * d);  // [16][B * K]
+  int32_t* ls = reinterpret_cast<int32_t*>(hist + kW * B * K);
   uint32_t* wsm = reinterpret_cast<uint32_t*>(ls + n);
   const int64_t e0 = nd.seg_start;
-  for (int q = threadIdx.x; q < n * C; q += kThreads) {
+  for (int q = threadIdx.x; q < n * C; q += kNodeThreads) {
     const int r = q / C, c = q - r * C;
     *reinterpret_cast<float4*>(xs + (size_t)r * d + 4 * node_chunk(r, c, C)) =
         *reinterpret_cast<const float4*>(pr.X + (e0 + r) * d + 4 * c);
   }
-  for (int i = threadIdx.x; i < n; i += kThreads) {
+  for (int i = threadIdx.x; i < n; i += kNodeThreads) {
     ls[i] = pr.lab[e0 + i];
     if (weighted) wsm[i] = pr.w[e0 + i];
   }
   __syncthreads();
   uint32_t* h = hist + warp * B * K;
+  const int j = warp >> 1, half = warp & 1;  // particle of the group, half of the rows
   const EvalRes* cur = sw.cur + (int64_t)a * Pp;
   const float* pbp = sw.pbest + (int64_t)a * Pp * d;
   float* gbp = sw.gbest + (int64_t)a * d;
   const int n_groups = (P + 7) >> 3;
   for (int t = 0; t <= sw.T; ++t) {
     for (int g = rank; g < n_groups; g += S) {
-      // the group's positions (zero past P)
-      for (int q = threadIdx.x; q < 8 * d; q += kThreads) {
-        const int j = q / d, k = q - j * d;
-        const int p = 8 * g + j;
+      // the group's positions (zero past P); ranges reset; histograms zeroed
+      for (int q = threadIdx.x; q < 8 * d; q += kNodeThreads) {
+        const int jj = q / d, k = q - jj * d;
+        const int p = 8 * g + jj;
         apos[q] = p < P ? sw.pos[((int64_t)a * Pp + p) * d + k] : 0.0f;
       }
+      if (threadIdx.x < 8) {
+        s_lo[threadIdx.x] = INT_MAX;
+        s_hi[threadIdx.x] = INT_MIN;
+      }
+      for (int i = lane; i < B * K; i += 32) h[i] = 0u;
       __syncthreads();
-      // z of the group's 8 particles on every row, 4 rows per thread at once
-      for (int r0 = threadIdx.x; r0 < n; r0 += 4 * kThreads) {
+      // z of the group's 8 particles on every row, 4 rows per thread at once;
+      // the exact range of each particle folded in as ordered integers
+      int lo_t[8], hi_t[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        lo_t[jj] = INT_MAX;
+        hi_t[jj] = INT_MIN;
+      }
+      for (int r0 = threadIdx.x; r0 < n; r0 += 4 * kNodeThreads) {
         float acc[4][8];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+          for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0f;
         for (int c = 0; c < C; ++c) {
           float4 xv[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const int r = r0 + i * kThreads;
+            const int r = r0 + i * kNodeThreads;
             xv[i] = r < n ? *reinterpret_cast<const float4*>(xs + (size_t)r * d +
                                                              4 * node_chunk(r, c, C))
                           : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 pv = *reinterpret_cast<const float4*>(apos + j * d + 4 * c);
+          for (int jj = 0; jj < 8; ++jj) {
+            const float4 pv = *reinterpret_cast<const float4*>(apos + jj * d + 4 * c);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              acc[i][j] = fmaf(xv[i].x, pv.x, acc[i][j]);
-              acc[i][j] = fmaf(xv[i].y, pv.y, acc[i][j]);
-              acc[i][j] = fmaf(xv[i].z, pv.z, acc[i][j]);
-              acc[i][j] = fmaf(xv[i].w, pv.w, acc[i][j]);
+              acc[i][jj] = fmaf(xv[i].x, pv.x, acc[i][jj]);
+              acc[i][jj] = fmaf(xv[i].y, pv.y, acc[i][jj]);
+              acc[i][jj] = fmaf(xv[i].z, pv.z, acc[i][jj]);
+              acc[i][jj] = fmaf(xv[i].w, pv.w, acc[i][jj]);
             }
           }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int r = r0 + i * kThreads;
+          const int r = r0 + i * kNodeThreads;
           if (r < n)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) zb[(size_t)j * n + r] = acc[i][j];
+            for (int jj = 0; jj < 8; ++jj) {
+              zb[(size_t)jj * n + r] = acc[i][jj];
+              const int o = f2ord(acc[i][jj]);
+              lo_t[jj] = min(lo_t[jj], o);
+              hi_t[jj] = max(hi_t[jj], o);
+            }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        int lo = lo_t[jj], hi = hi_t[jj];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+          hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        }
+        if (lane == 0 && lo != INT_MAX) {
+          atomicMin(&s_lo[jj], lo);
+          atomicMax(&s_hi[jj], hi);
         }
       }
       __syncthreads();
-      const int p = 8 * g + warp;
-      if (p < P) {
-        const float* zp = zb + (size_t)warp * n;
-        int lo_o = INT_MAX, hi_o = INT_MIN;
-        for (int r = lane; r < n; r += 32) {
-          const int o = f2ord(zp[r]);
-          lo_o = min(lo_o, o);
-          hi_o = max(hi_o, o);
-        }
+      const int p = 8 * g + j;
+      float zmin = 0.f, inv_w = 0.f;
+      bool ok = false;
+      if (s_lo[j] != INT_MAX) {
+        const float lo = ord2f(s_lo[j]), hi = ord2f(s_hi[j]);
+        inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+        zmin = lo;
+        ok = (hi > lo) && isfinite(inv_w);
+      }
+      if (ok && p < P) {
+        // this warp's half of the rows into its own histogram, four entries
+        // per lane in flight
+        const float* zp = zb + (size_t)j * n;
+        for (int r0 = half * 32 + lane; r0 < n; r0 += 256) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          lo_o = min(lo_o, __shfl_xor_sync(0xffffffffu, lo_o, off));
-          hi_o = max(hi_o, __shfl_xor_sync(0xffffffffu, hi_o, off));
+          for (int u = 0; u < 4; ++u) {
+            const int r = r0 + 64 * u;
+            if (r < n)
+              atomicAdd(&h[bin_of(zp[r], zmin, inv_w, B) * K + ls[r]], weighted ? wsm[r] : 1u);
+          }
         }
-        float zmin = 0.f, inv_w = 0.f;
-        bool ok = false;
-        if (lo_o != INT_MAX) {
-          const float lo = ord2f(lo_o), hi = ord2f(hi_o);
-          inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
-          zmin = lo;
-          ok = (hi > lo) && isfinite(inv_w);
-        }
-        for (int i = lane; i < B * K; i += 32) h[i] = 0u;
-        __syncwarp();
-        if (ok)
-          for (int r = lane; r < n; r += 32)
-            atomicAdd(&h[bin_of(zp[r], zmin, inv_w, B) * K + ls[r]], weighted ? wsm[r] : 1u);
-        __syncwarp();
+      }
+      __syncthreads();
+      if (half == 0 && p < P) {
         EvalRes res = invalid_res();
         if (ok) {
+          const uint32_t* h2 = h + B * K;  // the odd warp's half
+          for (int i = lane; i < B * K; i += 32) h[i] += h2[i];
+          __syncwarp();
           res = warp_scan_cls<CRIT>(h, B, K, pr.min_leaf);
           res.zmin = zmin;
           res.inv_w = inv_w;
@@ -1359,9 +1392,14 @@ __global__ void __launch_bounds__(kThreads)
         if (lane == 0) sw.cur[(int64_t)a * Pp + p] = res;
         pbest_step(pr, sw, a, p, t, res);
       }
-      __syncthreads();  // zb and apos are refilled by the next group
+      __syncthreads();  // zb, apos, ranges and histograms are reset for the next group
     }
-    cl.sync();  // every score and pbest row of iteration t is written
+    // every score and pbest row of iteration t is written (one CTA: a block
+    // barrier orders its own global writes)
+    if (S > 1)
+      cl.sync();
+    else
+      __syncthreads();
     const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
     EvalRes* gnew_buf = sw.gb + (int64_t)(t & 1) * A;
     if (warp == 0) {
@@ -1388,14 +1426,18 @@ __global__ void __launch_bounds__(kThreads)
     const int best = s_best;
     const float* gsrc = best >= 0 ? pbp + (int64_t)best * d : gbp;
     if (rank == 0 && best >= 0)
-      for (int j = threadIdx.x; j < d; j += kThreads) gbp[j] = gsrc[j];
+      for (int jj = threadIdx.x; jj < d; jj += kNodeThreads) gbp[jj] = gsrc[jj];
     if (t < sw.T)
-      for (int item = threadIdx.x; item < P * d4; item += kThreads) {
-        const int p = item / d4;
-        if ((p >> 3) % S != rank) continue;  // another CTA's particle
-        move_item(pr, sw, co, nd.uid, a, t, p, item - p * d4, pbp, gsrc);
+      for (int item = threadIdx.x; item < P * d4; item += kNodeThreads) {
+        const int pp = item / d4;
+        if ((pp >> 3) % S != rank) continue;  // another CTA's particle
+        move_item(pr, sw, co, nd.uid, a, t, pp, item - pp * d4, pbp, gsrc);
       }
-    cl.sync();  // moves done before scores and pbest rows are rewritten
+    // moves done before scores and pbest rows are rewritten
+    if (S > 1)
+      cl.sync();
+    else
+      __syncthreads();
   }
 }
 
@@ -1740,7 +1782,7 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc*
 size_t node_search_smem(const Problem& pr, int n) {
   if (pr.d % 4) return SIZE_MAX;  // 16-byte row chunks
   const size_t words = (size_t)n * pr.d + (size_t)8 * n + (size_t)8 * pr.d +
-                       (size_t)(kThreads / 32) * pr.B * pr.K + (size_t)n * (pr.w ? 2 : 1);
+                       (size_t)(kNodeThreads / 32) * pr.B * pr.K + (size_t)n * (pr.w ? 2 : 1);
   return (words * 4 + 15) & ~(size_t)15;
 }
 
@@ -1752,7 +1794,7 @@ cudaError_t launch_node_search(const Problem& pr, const Swarm& sw, const NodeDes
     return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)S, (unsigned)n_nodes, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(kNodeThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];

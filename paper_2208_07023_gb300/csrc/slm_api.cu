@@ -72,7 +72,7 @@ struct slm_ctx {
     bool gather = false; // rows gathered from the base rows by sample id
   };
   int tune = 1;
-  bool node_search = true;            // persistent search of the nodes that fit
+  bool node_search = false;           // persistent search of the nodes that fit
   int last_node_search = 0;           // CTAs per node of the last search (0: none)
   cudaStream_t side = nullptr;        // the persistent search beside the others
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -175,6 +175,7 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
 // all T + 1 iterations in one launch, a cluster of S (1..8) CTAs per node of
 // list[n_nodes] (A: the batch's node count, the gbest buffers' stride).
 constexpr size_t kNodeSearchMaxSmem = 226 * 1024;
+constexpr int kNodeThreads = 512;  // threads per CTA of the persistent search
 size_t node_search_smem(const Problem& pr, int n);
 cudaError_t launch_node_search(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                                const int32_t* list, int n_nodes, int A, int S, size_t smem,

@@ -385,3 +385,53 @@ def test_grow_level_steps_match_train_tree(ctx):
     for key in a:
         assert np.array_equal(a[key], b[key]), key
     assert splits[0] == 1 and sum(splits) == int((a["kind"] == 1).sum())
+
+
+# ------------------------------------------------ persistent node search -----
+
+@pytest.mark.parametrize("crit,K,B,d,n,P,T", [
+    ("entropy", 2, 64, 16, 2000, 32, 50),   # the single-node setting
+    ("gini", 6, 128, 32, 700, 48, 15),
+    ("gini", 3, 32, 8, 300, 20, 25),        # P not a multiple of 8
+])
+def test_persistent_node_search_matches_oracle(ctx, crit, K, B, d, n, P, T):
+    """The whole search in one launch, the node resident in shared memory:
+    trajectory and split of the fp32-mirror oracle."""
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.single_node(n, d, seed=5) if K == 2 else W.gmm(n, d, K, seed=d)
+    gp = gpu_params(S, crit, K, P, T, B, min_leaf=2, seed=41)
+    ctx.set_node_search(True)
+    try:
+        g = ctx.node_split(gp, wl.X, labels=wl.labels, node_uid=9, want_trace=True)
+        assert ctx.last_node_search() >= 1
+    finally:
+        ctx.set_node_search(False)
+    r = O.node_split(oracle_params(O, crit, K, P, T, B, min_leaf=2, seed=41), wl.X,
+                     wl.labels, node_uid=9)
+    stop = r.split["first_near_tie"]
+    upto = T + 1 if stop < 0 else stop
+    assert np.array_equal(g["trace"][:upto], r.trace_loss[:upto])
+    if stop < 0:
+        assert np.array_equal(g["gbest"].astype(np.float64), r.gbest)
+        assert (g["particle"], g["iter_of_best"], g["bin"]) == \
+            (r.split["particle"], r.split["iter_of_best"], r.split["bin"])
+        assert g["loss"] == r.split["loss"]
+
+
+def test_persistent_node_search_tree_matches_oracle(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    n, d, K, depth, P, T, B = 3000, 8, 4, 5, 16, 15, 32
+    wl = W.gmm(n, d, K, seed=d)
+    gp = gpu_params(S, "gini", K, P, T, B, min_leaf=10, max_depth=depth, seed=3)
+    ctx.set_node_search(True)
+    try:
+        f = ctx.train_tree(gp, wl.X, labels=wl.labels)
+    finally:
+        ctx.set_node_search(False)
+    g = f.export(0)
+    f.free()
+    op = oracle_params(O, "gini", K, P, T, B, min_leaf=10, max_depth=depth, seed=3)
+    r = O.train_tree(op, wl.X, wl.labels)
+    inner, present = _compare_tree(g, r, d)
+    assert np.array_equal(g["loss"][inner], r.loss[inner])
+    assert np.array_equal(g["leaf_class"][present], r.leaf_class[present])

@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctx():
     c = context()
-    c.set_node_search(False)  # the per-iteration kernels these tests vary
+    c.set_node_search(False)  # the per-iteration kernels these tests vary (the default)
     yield c
     c.close()
 
