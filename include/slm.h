@@ -263,7 +263,7 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
 
 
 /* ---- learned swarm proposal ----------------------------------------------
- * Not in the paper, which starts every swarm in a preset range (Sec. III-A):
+ * Not in the paper, which starts every swarm uniformly in a fixed range (Sec. III-A):
  * a network that proposes a starting direction and spread for a node's swarm
  * from the node's statistics, trained on (statistics, best direction) pairs
  * that PSO searches produce. Sizes are fixed: features padded to
