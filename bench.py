@@ -262,13 +262,19 @@ def tree_loss(ctx, f, wl, X):
         pred = g["leaf_value"][lf]
         return {"tree0_mse": float(np.mean((pred - wl.y) ** 2)),
                 "ensemble_mse": float(np.mean((val - wl.y) ** 2))}
-    K = wl.n_classes
-    c = np.bincount(lf.astype(np.int64) * K + wl.labels, minlength=(int(lf.max()) + 1) * K)
+    return {"tree0_gini": leaf_gini(lf, wl.labels, wl.n_classes),
+            "ensemble_error": float(np.mean(cls != wl.labels))}
+
+
+def leaf_gini(leaf, labels, K):
+    """Weighted Gini impurity of a partition into leaves: sum over leaves of
+    n_leaf (1 - sum_k p_k^2), divided by n."""
+    import numpy as np
+    c = np.bincount(leaf.astype(np.int64) * K + labels, minlength=(int(leaf.max()) + 1) * K)
     c = c.reshape(-1, K).astype(np.float64)
     tot = c.sum(axis=1)
     m = tot > 0
-    gini = float((tot[m] - (c[m] ** 2).sum(axis=1) / tot[m]).sum())
-    return {"tree0_gini": gini / wl.n, "ensemble_error": float(np.mean(cls != wl.labels))}
+    return float((tot[m] - (c[m] ** 2).sum(axis=1) / tot[m]).sum()) / leaf.shape[0]
 
 
 def make_params(S, cfg, wl, proj, topk):

@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("n_bins", C.c_int32), ("inertia", C.c_float), ("c1", C.c_float),
         ("c2", C.c_float), ("max_depth", C.c_int32), ("min_leaf", C.c_int32),
         ("seed", C.c_uint64), ("precision", C.c_int32),
-        ("n_threads", C.c_int32), ("topk", C.c_int32),
+        ("n_threads", C.c_int32), ("topk", C.c_int32), ("top_n", C.c_int32),
     ]
 
 
@@ -140,6 +140,11 @@ def lib():
                                          C.c_uint32, C.c_void_p, C.c_void_p, P(Split),
                                          C.c_void_p, C.c_void_p]
             L.ora_node_split.restype = C.c_int
+            L.ora_select_features.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                              C.c_int32, C.c_void_p, C.c_void_p,
+                                              C.c_void_p]
+            L.ora_select_features.restype = C.c_int
             L.ora_train_tree.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                                          P(_Tree)]
@@ -158,11 +163,11 @@ def _ptr(a: Optional[np.ndarray]):
 def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
                 n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8,
                 min_leaf=1, seed=1, precision=F32_MIRROR, n_threads=0,
-                topk=0) -> Params:
+                topk=0, top_n=0) -> Params:
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
     return Params(crit, 0 if crit == MSE else n_classes, n_particles, n_iters,
                   n_bins, inertia, c1, c2, max_depth, min_leaf, seed, precision,
-                  n_threads, topk)
+                  n_threads, topk, top_n)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -224,6 +229,23 @@ def eval_swarm(params: Params, X, labels, y, pos, idx=None, wts=None,
     if rc:
         raise ValueError(f"ora_eval_swarm failed: {rc}")
     return [_struct_dict(e) for e in out], bins, z
+
+
+def select_features(params: Params, X, labels, y, n, idx=None, wts=None):
+    """The node's n best features by their own split loss (increasing
+    feature order), every feature's score, and whether the n-th and the
+    (n+1)-th best are a near-tie."""
+    X, labels, y, idx, wts = _node_arrays(X, labels, y, idx, wts)
+    d = X.shape[1]
+    feat = np.empty(n, dtype=np.int32)
+    ev = (Eval * d)()
+    tie = C.c_int32(0)
+    rc = lib().ora_select_features(C.byref(params), _ptr(X), d, _ptr(labels), _ptr(y),
+                                   _ptr(idx), _ptr(wts), idx.size, n, _ptr(feat), ev,
+                                   C.byref(tie))
+    if rc:
+        raise ValueError(f"ora_select_features failed: {rc}")
+    return feat, [_struct_dict(e) for e in ev], bool(tie.value)
 
 
 def score_bins(params: Params, labels, y, bins, idx=None, wts=None) -> dict:

@@ -602,11 +602,11 @@ static void copy_eval_to_split(const ora_eval* e, ora_split* s) {
   s->n_right = e->n_right;
 }
 
-int ora_node_split(const ora_params* p, const float* X, int32_t d,
-                   const int32_t* labels, const float* y, const int32_t* idx,
-                   const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
-                   double* gbest_out, double* dir_out, ora_split* out,
-                   double* trace_loss, int32_t* trace_particle) {
+static int node_split_full(const ora_params* p, const float* X, int32_t d,
+                           const int32_t* labels, const float* y, const int32_t* idx,
+                           const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
+                           double* gbest_out, double* dir_out, ora_split* out,
+                           double* trace_loss, int32_t* trace_particle) {
   if (check_params(p, d) || p->n_particles < 1 || p->n_iters < 0 || n_idx < 0 ||
       !X || !idx || !out || (p->precision == ORA_BF16_TOPK && p->topk < 1))
     return -1;
@@ -774,6 +774,88 @@ static int split_bin(const ora_params* p, const double* dir, double zmin,
   if (b > B - 1) b = B - 1;
   if (b < 0) b = 0;
   return b;
+}
+
+
+/* Per-node feature pre-screen (Sec. III-B, Algorithm 2): the split loss of
+ * every feature on its own (the projection on the unit vector e_k, scored
+ * like any particle; z = x_k exactly), the n = top_n best kept (ties to the
+ * lower feature, increasing feature order: select_topk's rule). */
+int ora_select_features(const ora_params* p, const float* X, int32_t d,
+                        const int32_t* labels, const float* y, const int32_t* idx,
+                        const uint32_t* wts, int64_t n_idx, int32_t n, int32_t* feat,
+                        ora_eval* ev_out, int32_t* near_tie) {
+  if (check_params(p, d) || n < 1 || n > d || !feat) return -1;
+  double* eye = (double*)calloc((size_t)d * d, sizeof(double));
+  ora_eval* ev = (ora_eval*)calloc((size_t)d, sizeof(ora_eval));
+  int rc = 0;
+  if (!eye || !ev) {
+    rc = -2;
+    goto done;
+  }
+  for (int32_t k = 0; k < d; ++k) eye[(int64_t)k * d + k] = 1.0;
+  int tie = 0, event = 0;
+  rc = eval_all(p, p->precision == ORA_F64 ? PROJ_F64 : PROJ_F32, X, d, labels, y, idx, wts,
+                n_idx, eye, NULL, d, ev, NULL, NULL, &tie, &event);
+  if (rc) goto done;
+  int sel_tie = 0;
+  select_topk(p, ev, d, n, feat, &sel_tie);
+  if (near_tie) *near_tie = sel_tie;
+  if (ev_out) memcpy(ev_out, ev, sizeof(ora_eval) * (size_t)d);
+done:
+  free(eye);
+  free(ev);
+  return rc;
+}
+
+int ora_node_split(const ora_params* p, const float* X, int32_t d,
+                   const int32_t* labels, const float* y, const int32_t* idx,
+                   const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
+                   double* gbest_out, double* dir_out, ora_split* out,
+                   double* trace_loss, int32_t* trace_particle) {
+  const int32_t n = p ? p->top_n : 0;
+  if (n <= 0 || n >= d)
+    return node_split_full(p, X, d, labels, y, idx, wts, n_idx, node_uid, gbest_out, dir_out,
+                           out, trace_loss, trace_particle);
+  /* the swarm searches the n-dimensional subspace of the selected features;
+   * its direction is lifted back with zeros elsewhere */
+  if (check_params(p, d) || !X || !idx || n_idx < 0 || !out) return -1;
+  int32_t* feat = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  int64_t rows = 0;
+  for (int64_t i = 0; i < n_idx; ++i)
+    if ((int64_t)idx[i] + 1 > rows) rows = (int64_t)idx[i] + 1;
+  float* Xs = (float*)calloc((size_t)(rows > 0 ? rows : 1) * n, sizeof(float));
+  double* gs = (double*)calloc((size_t)n, sizeof(double));
+  double* ds = (double*)calloc((size_t)n, sizeof(double));
+  int rc = 0, tie = 0;
+  if (!feat || !Xs || !gs || !ds) {
+    rc = -2;
+    goto done;
+  }
+  rc = ora_select_features(p, X, d, labels, y, idx, wts, n_idx, n, feat, NULL, &tie);
+  if (rc) goto done;
+  for (int64_t i = 0; i < n_idx; ++i) {
+    const int64_t r = idx[i];
+    for (int32_t j = 0; j < n; ++j) Xs[r * n + j] = X[r * d + feat[j]];
+  }
+  rc = node_split_full(p, Xs, n, labels, y, idx, wts, n_idx, node_uid, gs, ds, out, trace_loss,
+                       trace_particle);
+  if (rc) goto done;
+  if (gbest_out)
+    for (int32_t k = 0; k < d; ++k) gbest_out[k] = 0.0;
+  if (dir_out)
+    for (int32_t k = 0; k < d; ++k) dir_out[k] = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    if (gbest_out) gbest_out[feat[j]] = gs[j];
+    if (dir_out) dir_out[feat[j]] = ds[j];
+  }
+  if (tie) out->first_near_tie = 0;  /* another selection is as correct */
+done:
+  free(feat);
+  free(Xs);
+  free(gs);
+  free(ds);
+  return rc;
 }
 
 int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,

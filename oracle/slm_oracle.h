@@ -62,6 +62,9 @@ typedef struct {
   int32_t precision;    /* ORA_F64 / ORA_F32_MIRROR / ORA_BF16_TOPK */
   int32_t n_threads;    /* 0: OpenMP default */
   int32_t topk;         /* ORA_BF16_TOPK: particles re-scored per evaluation */
+  int32_t top_n;        /* 0 or >= d: every feature; else the swarm searches
+                           the subspace of the node's top_n features by their
+                           own split loss (ora_select_features) */
 } ora_params;
 
 /* Result of scoring one projection vector on one node. */
@@ -147,7 +150,24 @@ int ora_score_bins(const ora_params* p, const int32_t* labels, const float* y,
 /* Round each float to the nearest bfloat16 (ties to even), returned as float. */
 void ora_bf16_round(const float* in, float* out, int64_t n);
 
+/* Feature pre-screen of one node (Sec. III-B, Algorithm 2): each feature k
+ * scored as the projection on the unit vector e_k (z = x_k; float mirror or
+ * double projection by p->precision, never bfloat16), the n best kept by the
+ * particle ranking rule (better score, ties to the lower feature), returned
+ * in increasing feature order in feat[n]. ev_out[d] (optional): every
+ * feature's score; *near_tie (optional): the n-th and (n+1)-th scores are a
+ * near-tie of double losses. */
+int ora_select_features(const ora_params* p, const float* X, int32_t d,
+                        const int32_t* labels, const float* y, const int32_t* idx,
+                        const uint32_t* wts, int64_t n_idx, int32_t n, int32_t* feat,
+                        ora_eval* ev_out, int32_t* near_tie);
+
 /* PSO split search on one node (Algorithm 1 with synchronous updates).
+ * With 0 < p->top_n < d the swarm searches the subspace of the node's top_n
+ * features (ora_select_features; particle coordinate j is feature feat[j],
+ * the same swarm streams as a d = top_n search) and the direction is lifted
+ * back to d features with zeros elsewhere; a near-tie at the selection sets
+ * first_near_tie = 0.
  * gbest_out[d]: raw position; dir_out[d]: gbest / ||gbest||;
  * trace_loss[T+1], trace_particle[T+1]: gbest after each evaluation. */
 int ora_node_split(const ora_params* p, const float* X, int32_t d,
