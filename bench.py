@@ -65,9 +65,9 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 # DRAM bytes per particle-sample pair from ncu captures of the default
 # workload (dram__bytes_read.sum + dram__bytes_write.sum, profiles/), valid
 # only for the kernel source they were taken from (sha256 of the .cu file).
-TRAFFIC = {"project": 12849920 / 3.2e6, "hist_scan": 13091328 / 3.2e6}
+TRAFFIC = {"project": 12855040 / 3.2e6, "hist_scan": 13099776 / 3.2e6}
 TRAFFIC_SOURCE = {"project": "eval_kernels.cu", "hist_scan": "eval_kernels.cu"}
-TRAFFIC_SOURCE_SHA = "ce91b6f59265ae321156e8251a0a80b435982ce0e13bb604e2fb533d1297ceb0"
+TRAFFIC_SOURCE_SHA = "24feb279d81ef2e48e98d8695386b960026bdc527015e90909aff142e2beee6e"
 
 
 def _kernel_source_sha(name):
@@ -97,6 +97,8 @@ def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
          "projection": ("bf16 tcgen05 + top-%d fp32 ffma re-scoring" % topk
                         if proj == "bf16" else "fp32 ffma"),
          "l2": "flushed between steps (256 MiB write outside the timed events)"}
+    if cfg.get("top_n"):
+        d["feature_prescreen_top_n"] = cfg["top_n"]
     if args_launch is not None:
         d["search_loop_graphs"] = args_launch.graphs
         d["projection_tile_mode"] = args_launch.tiles
@@ -171,7 +173,7 @@ def oracle_params(cfg, wl, proj, topk, iters):
     prec = O.BF16_TOPK if proj == "bf16" else O.F32_MIRROR
     return O.make_params(cfg["criterion"], wl.n_classes, cfg["n_particles"], iters,
                          cfg["n_bins"], min_leaf=cfg["min_leaf"], seed=1, precision=prec,
-                         topk=topk if proj == "bf16" else 0)
+                         topk=topk if proj == "bf16" else 0, top_n=cfg.get("top_n", 0))
 
 
 def oracle_root_sample(cfg, wl, proj, topk, iters):
@@ -284,7 +286,7 @@ def make_params(S, cfg, wl, proj, topk):
                          n_trees=cfg["n_trees"],
                          bootstrap=cfg.get("bootstrap", cfg["n_trees"] > 1),
                          proj=S.SLM_PROJ_BF16_TOPK if proj == "bf16" else S.SLM_PROJ_FP32,
-                         topk=topk)
+                         topk=topk, top_n=cfg.get("top_n", 0))
 
 
 def time_steps(ctx, p, X, L, Y, steps, flush, stream):
@@ -455,6 +457,19 @@ def run_ours(args):
                  "one CUDA graph launch per level search" if args.graphs == "on"
                  else "PDL-chained stream launches")),
              "projection_tiles": ctx.tuned_shapes()}
+    if args.compare_plain and cfg.get("top_n"):
+        # the same tree without the pre-screen, same harness
+        pp = make_params(S, dict(cfg, top_n=0), wl, proj, topk)
+        for _ in range(max(1, args.warmup)):
+            ctx.train_tree(pp, X, labels=L, y=Y).free()
+        tp, ep, _ = time_steps(ctx, pp, X, L, Y, args.steps, flush, stream)
+        f = ctx.train_tree(pp, X, labels=L, y=Y)
+        lossp = tree_loss(ctx, f, wl, X)
+        f.free()
+        extra["plain_form"] = {"tree_train_ms": sum(tp) / len(tp),
+                               "value": ep / (sum(tp) / 1e3), "train_loss": lossp,
+                               "speedup_of_prescreen": (sum(tp) / len(tp)) /
+                               (tot_ms / args.steps)}
     if args.compare_fp32 and proj == "bf16":
         # the plain FP32 form of the same workload, same harness
         p32 = make_params(S, cfg, wl, "fp32", topk)
@@ -726,6 +741,8 @@ def main():
     ap.add_argument("--proj", choices=["fp32", "bf16"], default=None)
     ap.add_argument("--topk", type=int, default=8)
     ap.add_argument("--compare-fp32", action="store_true")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="pre-screen workloads: also time the tree without the pre-screen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graphs", choices=["on", "off"], default=None,
                     help="run each search's iteration loop as one CUDA graph launch "
