@@ -90,6 +90,18 @@ typedef struct slm_params {
   int32_t bootstrap;   /* 1: tree t trains on a bootstrap bag of the n samples */
   int32_t seeded;      /* 1: start each swarm from the context's proposal
                           (slm_use_proposal) instead of U[-1,1)^d; 0 otherwise */
+  int32_t top_n;       /* 0 or >= d: the swarm searches all d features.
+                          0 < top_n < d (Sec. III-B, Algorithm 2: features
+                          pre-screened per node): every feature k of a node
+                          is first scored on its own (the projection on the
+                          unit vector e_k, scored like a particle), the
+                          top_n best are kept (better score, ties to the
+                          lower feature; in increasing feature order), the
+                          swarm searches their subspace (coordinate j is the
+                          j-th kept feature; the swarm streams of a top_n-
+                          dimensional search) and gB is returned lifted to d
+                          features, zero elsewhere. Needs SLM_PROJ_FP32,
+                          seeded = 0 and d <= 256 (SLM_EUNSUPPORTED) */
   uint64_t seed;       /* Philox-4x32-10 key for every random draw */
 } slm_params;
 

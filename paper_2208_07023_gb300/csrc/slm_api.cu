@@ -39,6 +39,9 @@ enum Slot {
   // node lists of the histogram kernels (large nodes, then small ones) and
   // of the persistent search
   S_HLIST, S_NLIST,
+  // feature pre-screen: unit positions, kept features, the kept columns,
+  // the lifted gbest
+  S_FPOS, S_FEAT, W_XS, S_GFULL,
   N_SLOTS
 };
 
@@ -255,6 +258,12 @@ slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
         !std::isfinite(p->c2))
       return fail(c, SLM_EINVAL, "inertia / c1 / c2 must be finite");
     if (p->seeded != 0 && p->seeded != 1) return fail(c, SLM_EINVAL, "seeded must be 0 or 1");
+    if (p->top_n < 0) return fail(c, SLM_EINVAL, "top_n must be >= 0");
+    if (p->top_n > 0 && p->top_n < d &&
+        (p->proj != SLM_PROJ_FP32 || p->seeded || d > kMaxParticles))
+      return fail(c, SLM_EUNSUPPORTED,
+                  "a feature pre-screen (0 < top_n < d) needs SLM_PROJ_FP32, seeded = 0, "
+                  "d <= 256");
     if (p->seeded) {
       if (!c->prop) return fail(c, SLM_EINVAL, "seeded search without slm_use_proposal");
       if (d > kPropD || (p->criterion != SLM_MSE && p->n_classes > kPropK) ||
@@ -950,9 +959,16 @@ struct KeyWriter {
 };
 
 // PSO search of every node of a batch (Algorithm 1, synchronous updates).
+slm_status prescreen_search(slm_ctx* c, const slm_params* p, Problem& pr,
+                            const std::vector<NodeDesc>& nodes, bool want_trace,
+                            Swarm* sw_out);
+slm_status check_kernel_errors(slm_ctx* c);
+
 slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
                       Swarm* sw_out) {
+  if (p->top_n > 0 && p->top_n < pr.d)
+    return prescreen_search(c, p, pr, nodes, want_trace, sw_out);
   const int A = (int)nodes.size();
   // classification nodes (FP32 form) whose rows fit in shared memory run
   // their whole search in one persistent launch; the others (`in`) run the
@@ -1071,6 +1087,88 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
     if (s) return s;
   }
   sw.gb += (size_t)(p->n_iters & 1) * A;  // the final gbest scores
+  *sw_out = sw;
+  return SLM_OK;
+}
+
+// Host twin of the device ranking: a strictly better score (Gini: the exact
+// rational Q, larger is better; otherwise the loss), invalid scores last.
+bool better_host(const EvalRes& a, const EvalRes& b, int crit) {
+  if (!a.valid) return false;
+  if (!b.valid) return true;
+  if (crit == SLM_GINI)
+    return (unsigned __int128)a.num * b.den > (unsigned __int128)b.num * a.den;
+  return a.loss < b.loss;
+}
+
+// Feature pre-screen (Sec. III-B, Algorithm 2): every feature of every node
+// scored on its own in one batched pass (the unit vectors e_k as particles,
+// so z = x_k), the top_n best kept per node (stable order: ties to the lower
+// feature; then increasing feature order), their columns gathered, the
+// swarm search run on that subspace, and gB lifted back to d features.
+slm_status prescreen_search(slm_ctx* c, const slm_params* p, Problem& pr,
+                            const std::vector<NodeDesc>& nodes, bool want_trace,
+                            Swarm* sw_out) {
+  const int A = (int)nodes.size(), d = pr.d, n = p->top_n;
+  Problem pu = pr;
+  pu.P = d;
+  pu.Pp = (d + kPG - 1) / kPG * kPG;
+  pu.G = pu.Pp / kPG;
+  const std::vector<WorkTile> tiles = plan_tiles(nodes);
+  Swarm su{};
+  if (slm_status s = setup_scoring(c, pu, A, nodes, tiles, &su)) return s;
+  CK(ensure(c->ws[S_FPOS], sizeof(float) * (size_t)A * pu.Pp * d));
+  su.pos = ws_ptr<float>(c, S_FPOS);
+  CK(launch(c, SLM_K_OTHER, 0.0,
+            [&] { return launch_unit_positions(su.pos, A, pu.Pp, d, c->stream); }));
+  CK(launch(c, SLM_K_OTHER, 0.0,
+            [&] { return launch_range_reset(su.zmm, (int64_t)A * pu.Pp, c->stream); }));
+  double pairs = 0.0;
+  for (const NodeDesc& nd : nodes) pairs += (double)nd.seg_len * d;
+  if (slm_status s = score_batch(c, pu, su, nodes, (int)tiles.size(), pairs, nullptr, 0,
+                                 nullptr, batch_split(c, pu, nodes)))
+    return s;
+  if (slm_status s = check_kernel_errors(c)) return s;
+  std::vector<EvalRes> sc((size_t)A * pu.Pp);
+  CK(cudaMemcpyAsync(sc.data(), su.cur, sizeof(EvalRes) * sc.size(), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<int32_t> feat((size_t)A * n), order(d);
+  for (int a = 0; a < A; ++a) {
+    const EvalRes* e = sc.data() + (size_t)a * pu.Pp;
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return better_host(e[x], e[y], pr.crit);
+    });
+    std::sort(order.begin(), order.begin() + n);
+    std::copy(order.begin(), order.begin() + n, feat.begin() + (size_t)a * n);
+  }
+  CK(ensure(c->ws[S_FEAT], sizeof(int32_t) * feat.size()));
+  CK(cudaMemcpyAsync(c->ws[S_FEAT].p, feat.data(), sizeof(int32_t) * feat.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  const int32_t* dfeat = ws_ptr<int32_t>(c, S_FEAT);
+  CK(ensure(c->ws[W_XS], sizeof(float) * (size_t)(pr.E > 0 ? pr.E : 1) * n));
+  float* xs = ws_ptr<float>(c, W_XS);
+  CK(launch(c, SLM_K_GATHER, 0.0, [&] {
+    return launch_gather_cols(pr.X, d, dfeat, n, ws_ptr<WorkTile>(c, S_TILES),
+                              (int)tiles.size(), xs, c->stream);
+  }));
+  Problem ps = pr;
+  ps.X = xs;
+  ps.d = n;
+  ps.Xg = nullptr;
+  ps.gidx = nullptr;
+  ps.Xb = nullptr;
+  ps.dp = (n + 15) / 16 * 16;
+  slm_params q = *p;
+  q.top_n = 0;
+  Swarm sw;
+  if (slm_status s = run_search(c, &q, ps, nodes, want_trace, &sw)) return s;
+  CK(ensure(c->ws[S_GFULL], sizeof(float) * (size_t)A * d));
+  float* gfull = ws_ptr<float>(c, S_GFULL);
+  CK(launch(c, SLM_K_OTHER, 0.0,
+            [&] { return launch_lift(sw.gbest, dfeat, A, n, d, gfull, c->stream); }));
+  sw.gbest = gfull;
   *sw_out = sw;
   return SLM_OK;
 }

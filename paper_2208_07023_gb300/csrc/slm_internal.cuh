@@ -256,6 +256,14 @@ struct TreeArrays {
 
 // Gathers rows / labels / targets of sample ids idx[E] into entry order:
 // Xl[e] = X[idx[e]] (labels, y likewise; null arrays are skipped).
+// Feature pre-screen: unit-vector positions of A nodes; the kept columns of
+// each node's rows (feat[A][n], tiles of the nodes); gB lifted to d features.
+cudaError_t launch_unit_positions(float* pos, int A, int Pp, int d, cudaStream_t st);
+cudaError_t launch_range_reset(int32_t* zmm, int64_t count, cudaStream_t st);
+cudaError_t launch_gather_cols(const float* X, int d, const int32_t* feat, int n,
+                               const WorkTile* tiles, int n_tiles, float* Xs, cudaStream_t st);
+cudaError_t launch_lift(const float* gs, const int32_t* feat, int A, int n, int d, float* gfull,
+                        cudaStream_t st);
 cudaError_t launch_gather(const float* X, const int32_t* labels, const float* y,
                           const int32_t* idx, int64_t E, int d, float* Xl,
                           int32_t* lab_l, float* y_l, cudaStream_t st);

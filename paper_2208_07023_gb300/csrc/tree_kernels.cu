@@ -414,6 +414,52 @@ __global__ void k_predict(const float* __restrict__ X, int64_t n, int d, TreeArr
   }
 }
 
+
+// ---- feature pre-screen (Sec. III-B, Algorithm 2) --------------------------------
+
+// pos[a][p][j] = 1 if p == j else 0: particle k of every node is the unit
+// vector e_k (its projection is feature k itself).
+__global__ void k_unit_positions(float* pos, int A, int Pp, int d) {
+  const int64_t total = (int64_t)A * Pp * d;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pj = i % ((int64_t)Pp * d);
+    pos[i] = (pj / d == pj % d) ? 1.0f : 0.0f;
+  }
+}
+
+// zmm[i] = (INT_MAX, INT_MIN): empty ordered-int ranges.
+__global__ void k_range_reset(int32_t* zmm, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    zmm[2 * i] = INT_MAX;
+    zmm[2 * i + 1] = INT_MIN;
+  }
+}
+
+// Xs[e][j] = X[e][feat[a][j]] for the rows of each tile of node a.
+__global__ void k_gather_cols(const float* __restrict__ X, int d,
+                              const int32_t* __restrict__ feat, int n,
+                              const WorkTile* __restrict__ tiles, float* Xs) {
+  const WorkTile wt = tiles[blockIdx.x];
+  const int32_t* f = feat + (int64_t)wt.node * n;
+  for (int i = threadIdx.x; i < wt.rows * n; i += blockDim.x) {
+    const int r = i / n, j = i - r * n;
+    const int64_t e = (int64_t)wt.row0 + r;
+    Xs[e * n + j] = X[e * d + f[j]];
+  }
+}
+
+// gfull[a][k] = gs[a][j] where feat[a][j] = k, else 0.
+__global__ void k_lift(const float* __restrict__ gs, const int32_t* __restrict__ feat, int n,
+                       int d, float* gfull) {
+  const int a = blockIdx.x;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) gfull[(int64_t)a * d + k] = 0.0f;
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    gfull[(int64_t)a * d + feat[(int64_t)a * n + j]] = gs[(int64_t)a * n + j];
+}
+
 }  // namespace
 
 cudaError_t launch_node_stats(const Problem& pr, const LevelNode* nodes, int L,
@@ -499,6 +545,35 @@ cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr, int 
   if (n <= 0) return cudaSuccess;
   k_predict<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(X, n, d, tr, n_trees, H, B, K, crit,
                                                         class_out, value_out, leaf_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_positions(float* pos, int A, int Pp, int d, cudaStream_t st) {
+  const int64_t total = (int64_t)A * Pp * d;
+  if (total <= 0) return cudaSuccess;
+  const int64_t blocks = (total + 255) / 256;
+  k_unit_positions<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(pos, A, Pp, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_reset(int32_t* zmm, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = (count + 255) / 256;
+  k_range_reset<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(zmm, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cols(const float* X, int d, const int32_t* feat, int n,
+                               const WorkTile* tiles, int n_tiles, float* Xs, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  k_gather_cols<<<(unsigned)n_tiles, 256, 0, st>>>(X, d, feat, n, tiles, Xs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lift(const float* gs, const int32_t* feat, int A, int n, int d, float* gfull,
+                        cudaStream_t st) {
+  if (A <= 0) return cudaSuccess;
+  k_lift<<<(unsigned)A, 256, 0, st>>>(gs, feat, n, d, gfull);
   return cudaGetLastError();
 }
 

@@ -138,6 +138,12 @@ SETTINGS = {
         builder=lambda seed=1: gmm(50_000, 64, 10, seed),
         criterion="gini", n_particles=64, n_iters=100, n_bins=128,
         max_depth=8, min_leaf=20, n_trees=1),
+    # the classification tree with the per-node feature pre-screen: the swarm
+    # searches the subspace of each node's 16 best features
+    "tree_n50k_d64_k10_top16": dict(
+        builder=lambda seed=1: gmm(50_000, 64, 10, seed),
+        criterion="gini", n_particles=64, n_iters=100, n_bins=128,
+        max_depth=8, min_leaf=20, n_trees=1, top_n=16),
     # regression tree
     "regtree_n200k_d128": dict(
         builder=lambda seed=1: tanh_regression(200_000, 128, 8, 0.1, seed),
