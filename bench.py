@@ -456,7 +456,8 @@ def run_ours(args):
              "search_loop": dict(ctx.graph_stats(), mode=(
                  "one CUDA graph launch per level search" if args.graphs == "on"
                  else "PDL-chained stream launches")),
-             "projection_tiles": ctx.tuned_shapes()}
+             "projection_tiles": ctx.tuned_shapes(),
+             "last_hist_cluster": ctx.tuning_stats()["last_hist_cluster"]}
     if args.compare_plain and cfg.get("top_n"):
         # the same tree without the pre-screen, same harness
         pp = make_params(S, dict(cfg, top_n=0), wl, proj, topk)

@@ -397,9 +397,13 @@ slm_status slm_launch_count(slm_ctx* ctx, int64_t* launches);
  * P rounded up to 16; 1 or 2 CTAs per SM; rows from the level copy or, in
  * bagged forests, gathered from the base rows) that was fastest when the first
  * search of the same shape (d, padded P, log2 of the 256-row tiles) timed
- * every candidate on its own batch; the choice is kept by the context.
- * on = 0: 16 particles per group, 2 CTAs per SM. Results are identical for
- * every tile shape. SLM_EINVAL for other values. */
+ * every candidate on its own batch; the choice is kept by the context. The
+ * same first search also times the cluster histogram kernel with 1 to 16
+ * CTAs per (node, particle) and keeps the fastest for the shape (criterion,
+ * bins, classes, particles, multiplicities, log2 of the largest node and of
+ * the node count). on = 0: 16 particles per group, 2 CTAs per SM, and the
+ * largest power-of-two cluster that keeps the histogram grid in one wave.
+ * Results are identical for every choice. SLM_EINVAL for other values. */
 slm_status slm_set_tuning(slm_ctx* ctx, int32_t on);
 /* on = 1: a classification search (FP32 form) whose nodes'
  * rows, labels and multiplicities all fit in one SM's shared memory (about
@@ -428,9 +432,10 @@ slm_status slm_set_small_nodes(slm_ctx* ctx, int32_t max_entries, int64_t min_pa
  * the only source). SLM_EINVAL for shapes outside the list above, and from a
  * search whose padded P pg does not divide. */
 slm_status slm_force_tiles(slm_ctx* ctx, int32_t pg, int32_t ctas_per_sm, int32_t gather);
-/* Shapes tuned so far and the tiles of the last search (any may be NULL). */
+/* Shapes tuned so far, the tiles of the last search and the CTAs per
+ * (node, particle) of its cluster histogram kernel (any may be NULL). */
 slm_status slm_tuning_stats(slm_ctx* ctx, int64_t* shapes, int32_t* last_pg,
-                            int32_t* last_ctas_per_sm);
+                            int32_t* last_ctas_per_sm, int32_t* last_hist_cluster);
 /* The tuned shapes: *n receives their number; the first max are written to
  * the arrays (any may be NULL): features d, padded P, log2 of the row tiles,
  * the chosen particles per group, CTAs per SM and row source (1: gathered

@@ -100,7 +100,7 @@ def lib():
             "slm_set_node_search": ([vp, i32], C.c_int),
             "slm_last_node_search": ([vp, P(i32)], C.c_int),
             "slm_force_tiles": ([vp, i32, i32, i32], C.c_int),
-            "slm_tuning_stats": ([vp, P(i64), P(i32), P(i32)], C.c_int),
+            "slm_tuning_stats": ([vp, P(i64), P(i32), P(i32), P(i32)], C.c_int),
             "slm_tuned_shapes": ([vp, i32, P(i32), vp, vp, vp, vp, vp, vp, vp], C.c_int),
             "slm_graph_stats": ([vp, P(i64), P(i64), P(i64), P(i64)], C.c_int),
             "slm_evaluate_swarm_noalloc": ([C.c_int, vp, P(slm_params), vp, i64, i32, vp, vp,
@@ -353,9 +353,11 @@ class Context:
         self._check(lib().slm_force_tiles(self.handle, pg, ctas_per_sm, 1 if gather else 0))
 
     def tuning_stats(self) -> dict:
-        n, pg, cps = C.c_int64(), C.c_int32(), C.c_int32()
-        self._check(lib().slm_tuning_stats(self.handle, C.byref(n), C.byref(pg), C.byref(cps)))
-        return {"shapes": n.value, "last_pg": pg.value, "last_ctas_per_sm": cps.value}
+        n, pg, cps, hc = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(lib().slm_tuning_stats(self.handle, C.byref(n), C.byref(pg), C.byref(cps),
+                                           C.byref(hc)))
+        return {"shapes": n.value, "last_pg": pg.value, "last_ctas_per_sm": cps.value,
+                "last_hist_cluster": hc.value}
 
     def tuned_shapes(self) -> list:
         n = C.c_int32()

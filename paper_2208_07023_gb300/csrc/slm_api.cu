@@ -75,6 +75,13 @@ struct slm_ctx {
     bool gather = false; // rows gathered from the base rows by sample id
   };
   int tune = 1;
+  // histogram clusters: CTAs per (node, particle), tuned per shape
+  struct Split {
+    int S = 1;
+    float ms = 0.f;
+  };
+  std::map<std::vector<int64_t>, Split> tuned_split;
+  int last_split = 0;
   bool node_search = false;           // persistent search of the nodes that fit
   int last_node_search = 0;           // CTAs per node of the last search (0: none)
   cudaStream_t side = nullptr;        // the persistent search beside the others
@@ -840,6 +847,79 @@ cudaError_t graph_signature(cudaGraph_t g, std::vector<uint64_t>* sig) {
   return cudaSuccess;
 }
 
+// CTAs per (node, particle) of the cluster histogram kernel for a search's
+// FP32 pass: the one-wave rule of hist_split (tuning off), cached for the
+// shape (criterion, bins, classes, particles, multiplicities, log2 of the
+// largest node and of the node count), or tuned now: for every cluster size
+// the device can schedule (1..16, slices of at least 256 entries) the
+// batch is projected once with the search's tiles and histogrammed once
+// between events; the fastest is kept. The histogram pass only reads the
+// projections and writes scores and reset ranges, which the search's first
+// iteration recomputes, so the extra passes change nothing it reads.
+slm_status check_kernel_errors(slm_ctx* c);
+
+slm_status pick_split(slm_ctx* c, const Problem& pr, const Swarm& sw,
+                      const std::vector<NodeDesc>& nodes, int n_tiles,
+                      const slm_ctx::Tiles& tl, int* S_out) {
+  *S_out = batch_split(c, pr, nodes);
+  if (!c->tune || nodes.empty() || n_tiles <= 0) return SLM_OK;
+  int64_t max_len = 0;
+  for (const NodeDesc& nd : nodes) max_len = std::max<int64_t>(max_len, nd.seg_len);
+  auto lg = [](int64_t v) {
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return (int64_t)l;
+  };
+  const std::vector<int64_t> key{pr.crit, pr.B, pr.K, pr.P, pr.w != nullptr, lg(max_len),
+                                 lg((int64_t)nodes.size())};
+  auto it = c->tuned_split.find(key);
+  if (it != c->tuned_split.end()) {
+    *S_out = it->second.S;
+    return SLM_OK;
+  }
+  const int A = (int)nodes.size();
+  const int smax = std::min(16, hist_max_cluster(pr));
+  const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
+  const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  if (!e0 || !e1) return fail(c, SLM_ECUDA, "cudaEventCreate");
+  slm_ctx::Split best{*S_out, 0.f};
+  bool have = false;
+  for (int S = 1; S <= smax; ++S) {
+    if (S > 1 && max_len / S < 256) break;
+    float ms_min = 0.f;
+    bool ok = true;
+    for (int r = 0; r < 2 && ok; ++r) {
+      cudaError_t e =
+          launch_project(pr, sw, dt, n_tiles, tl.cps * c->n_sm, c->stream, tl.pg, tl.gather);
+      if (!e) e = cudaEventRecord(e0, c->stream);
+      if (!e) e = launch_hist_scan(pr, sw, dn, A, S, nullptr, 0, 0, c->stream);
+      if (!e) e = cudaEventRecord(e1, c->stream);
+      if (!e) e = cudaEventSynchronize(e1);
+      c->launches += 2;
+      float ms = 0.f;
+      if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e) {  // a cluster size the device cannot place: skip it
+        (void)cudaGetLastError();
+        ok = false;
+        break;
+      }
+      ms_min = r == 0 ? ms : std::min(ms_min, ms);
+    }
+    if (!ok) continue;
+    if (!have || ms_min < best.ms) {
+      best = slm_ctx::Split{S, ms_min};
+      have = true;
+    }
+  }
+  c->free_events.push_back(e0);
+  c->free_events.push_back(e1);
+  if (slm_status s = check_kernel_errors(c)) return s;
+  c->tuned_split[key] = best;
+  *S_out = best.S;
+  return SLM_OK;
+}
+
 // The T + 1 scoring passes of a search (Algorithm 1's loop). With graphs on
 // (and per-launch profiling off) the passes run as one CUDA graph launch: the
 // device runs the whole loop of a level without waiting on the host. The
@@ -1048,11 +1128,14 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
     c->last_node_search = S;
   }
   if (n_res < A) {
-    const int S = batch_split(c, pr, nodes);
+    int S = batch_split(c, pr, nodes);
     slm_ctx::Tiles tl{};
     if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
     HistPlan hp;
     if (!bp.on && (s = setup_hist_plan(c, pr, nodes, in, &hp))) return s;
+    if (!bp.on && !hp.on && (s = pick_split(c, pr, sw, nodes, (int)tiles.size(), tl, &S)))
+      return s;
+    c->last_split = S;
     c->cur = tl;
     c->last = tl;
     std::string key;
@@ -2367,11 +2450,12 @@ slm_status slm_force_tiles(slm_ctx* c, int32_t pg, int32_t ctas_per_sm, int32_t 
 }
 
 slm_status slm_tuning_stats(slm_ctx* c, int64_t* shapes, int32_t* last_pg,
-                            int32_t* last_ctas_per_sm) {
+                            int32_t* last_ctas_per_sm, int32_t* last_hist_cluster) {
   if (!c) return SLM_EINVAL;
   if (shapes) *shapes = (int64_t)c->tuned.size();
   if (last_pg) *last_pg = c->last.pg;
   if (last_ctas_per_sm) *last_ctas_per_sm = c->last.cps;
+  if (last_hist_cluster) *last_hist_cluster = c->last_split;
   return SLM_OK;
 }
 
