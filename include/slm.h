@@ -405,6 +405,17 @@ slm_status slm_launch_count(slm_ctx* ctx, int64_t* launches);
  * largest power-of-two cluster that keeps the histogram grid in one wave.
  * Results are identical for every choice. SLM_EINVAL for other values. */
 slm_status slm_set_tuning(slm_ctx* ctx, int32_t on);
+/* Test hooks for the failure paths (no GPU fault is made):
+ * first_wait_polls: polls of the histogram kernel's first wait on each
+ * staged piece, for every context on ctx's device (< 0 restores the default
+ * bound; 0 makes every wait give up at once: the kernel drains the copies in
+ * flight, sets the error word and ends, and the call returns SLM_ETIMEOUT).
+ * fail_alloc_after: the fail_alloc_after-th later growth of a library work
+ * buffer fails as if the device were out of memory (SLM_ENOMEM; 0: never);
+ * process-wide. Synchronises ctx's stream. SLM_EINVAL if
+ * fail_alloc_after < 0. */
+slm_status slm_test_hooks(slm_ctx* ctx, int32_t first_wait_polls, int64_t fail_alloc_after);
+
 /* on = 1: a classification search (FP32 form) whose nodes'
  * rows, labels and multiplicities all fit in one SM's shared memory (about
  * n (d + 2) 4 bytes per node, with room for eight B x K histograms) runs all

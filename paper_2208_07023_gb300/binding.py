@@ -98,6 +98,7 @@ def lib():
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
             "slm_set_node_search": ([vp, i32], C.c_int),
+            "slm_test_hooks": ([vp, i32, i64], C.c_int),
             "slm_last_node_search": ([vp, P(i32)], C.c_int),
             "slm_force_tiles": ([vp, i32, i32, i32], C.c_int),
             "slm_tuning_stats": ([vp, P(i64), P(i32), P(i32), P(i32)], C.c_int),
@@ -334,6 +335,9 @@ class Context:
         n = C.c_int64()
         self._check(lib().slm_launch_count(self.handle, C.byref(n)))
         return n.value
+
+    def test_hooks(self, first_wait_polls: int = -1, fail_alloc_after: int = 0):
+        self._check(lib().slm_test_hooks(self.handle, first_wait_polls, fail_alloc_after))
 
     def set_node_search(self, on: bool):
         self._check(lib().slm_set_node_search(self.handle, 1 if on else 0))

@@ -47,6 +47,12 @@ __device__ __forceinline__ double xlogx(uint32_t c) {
   return c ? x * log(x) : 0.0;
 }
 
+// Polls of the histogram kernel's first wait on each staged piece (the
+// drain of copies in flight after a failed wait keeps kWaitPolls). Lowered
+// only to test the timeout path: at 0 every piece's wait gives up at once,
+// the kernel drains its copies, records the error word and ends normally.
+__device__ int d_first_wait_polls = kWaitPolls;
+
 // c ln c for c < kXlogxTab from a table the device builds once with xlogx
 // itself (identical values): the entropy scans then read L2 instead of
 // evaluating double-precision logarithms, which are scarce on this GPU.
@@ -879,7 +885,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     // barrier at the end of the previous round
     if (threadIdx.x == 0 && k + kStages - 1 < n_pieces) issue(k + kStages - 1);
     const uint32_t parity = (uint32_t)((k / kStages) & 1);
-    if (!mbar_wait(&s_bar[k % kStages], parity, kWaitPolls)) {
+    if (!mbar_wait(&s_bar[k % kStages], parity, d_first_wait_polls)) {
       // a copy did not land: record it, give the copies in flight a bounded
       // chance to finish, and stop using the stages
       if (threadIdx.x == 0 && sw.err) atomicExch(sw.err, 3);
@@ -1669,6 +1675,11 @@ cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
   if (A <= 0) return cudaSuccess;
   k_swarm_init<<<A, kThreads, 0, st>>>(pr, sw, nodes, co);
   return cudaGetLastError();
+}
+
+cudaError_t set_first_wait_polls(int polls) {
+  const int v = polls < 0 ? kWaitPolls : polls;
+  return cudaMemcpyToSymbol(d_first_wait_polls, &v, sizeof(v));
 }
 
 cudaError_t ensure_xlogx_table(int device) {

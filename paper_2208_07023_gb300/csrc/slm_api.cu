@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -163,7 +164,7 @@ slm_status fail(slm_ctx* c, slm_status s, const std::string& msg) {
 
 slm_status cuda_fail(slm_ctx* c, cudaError_t e, const char* where) {
   if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
-  return SLM_ECUDA;
+  return e == cudaErrorMemoryAllocation ? SLM_ENOMEM : SLM_ECUDA;
 }
 
 #define CK(expr)                                    \
@@ -172,9 +173,14 @@ slm_status cuda_fail(slm_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
   } while (0)
 
+// Test hook: the next `g_fail_alloc`-th growth of a work buffer fails as if
+// the device were out of memory (0: never).
+std::atomic<int64_t> g_fail_alloc{0};
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (bytes <= b.cap) return cudaSuccess;
+  if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) return cudaErrorMemoryAllocation;
   if (b.p) {
     cudaError_t e = cudaFree(b.p);
     b.p = nullptr;
@@ -1691,8 +1697,9 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess) l2 = 0;
   const size_t xbytes = sizeof(float) * (size_t)n * d;
   if (!bf16 && p->n_trees > 1 && xbytes <= (size_t)l2 / 4) {
-    CK(ensure(f->own_X, xbytes));
-    CK(cudaMemcpyAsync(f->own_X.p, dX, xbytes, cudaMemcpyDeviceToDevice, c->stream));
+    cudaError_t ex = ensure(f->own_X, xbytes);
+    if (!ex) ex = cudaMemcpyAsync(f->own_X.p, dX, xbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (ex) return bail(cuda_fail(c, ex, "base rows"));
     f->X = static_cast<const float*>(f->own_X.p);
   }
   f->weighted = p->bootstrap != 0;
@@ -2406,6 +2413,15 @@ slm_status slm_kernel_stats(slm_ctx* c, int32_t kernel, int64_t* launches,
 slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
   if (!c || !launches) return SLM_EINVAL;
   *launches = c->launches;
+  return SLM_OK;
+}
+
+slm_status slm_test_hooks(slm_ctx* c, int32_t first_wait_polls, int64_t fail_alloc_after) {
+  if (!c || fail_alloc_after < 0) return fail(c, SLM_EINVAL, "bad test hook values");
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(set_first_wait_polls(first_wait_polls));
+  g_fail_alloc.store(fail_alloc_after);
   return SLM_OK;
 }
 

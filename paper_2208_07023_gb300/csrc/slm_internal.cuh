@@ -142,6 +142,9 @@ struct SwarmCoef {
 // histogram kernel in classification searches.
 constexpr int kWarpNodeMax = 4096;
 
+// The histogram kernel's first-wait polls on the current device (< 0: the
+// default bound); a test hook for the timeout path.
+cudaError_t set_first_wait_polls(int polls);
 // c ln c is tabulated for counts below this (8 MB of doubles per device).
 constexpr int kXlogxTab = 1 << 20;
 // Builds the device's c ln c table once per process (synchronous).

@@ -1,0 +1,136 @@
+"""Failure paths and batching, without a GPU fault.
+
+* a bounded wait that gives up (its limit forced to 0 through the test hook):
+  the call returns SLM_ETIMEOUT, the kernel drained its copies and ended, and
+  the same context then runs the search again with the same result;
+* an injected allocation failure at several points of a search and of a
+  tree: SLM_ENOMEM, the context stays usable, and repeated failures do not
+  grow the device memory in use;
+* batched == unbatched: the root level of a bagged forest (every tree's root
+  in one launch) gives each root the result of its own node search with the
+  same node id, bootstrap multiplicities and samples; so do the two nodes of
+  a tree's second level.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_07023_gb300 import workloads as W
+from tests.gpu_util import context, gpu_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = context()
+    yield c
+    c.test_hooks(-1, 0)
+    c.close()
+
+
+def test_wait_timeout_returns_etimeout_and_context_recovers(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(20000, 16, 4, seed=3)
+    p = gpu_params(S, "gini", 4, 32, 3, 64, min_leaf=5, seed=2)
+    ref = ctx.node_split(p, wl.X, labels=wl.labels, node_uid=1)
+    ctx.test_hooks(0, 0)
+    try:
+        with pytest.raises(S.SlmError) as e:
+            ctx.node_split(p, wl.X, labels=wl.labels, node_uid=1)
+        assert e.value.status == S.SLM_ETIMEOUT
+    finally:
+        ctx.test_hooks(-1, 0)
+    again = ctx.node_split(p, wl.X, labels=wl.labels, node_uid=1)
+    assert np.array_equal(ref["gbest"], again["gbest"]) and ref["loss"] == again["loss"]
+
+
+def _used_bytes():
+    import torch
+    free, total = torch.cuda.mem_get_info()
+    return total - free
+
+
+def test_allocation_failure_returns_enomem_and_context_recovers():
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(8000, 24, 5, seed=4)
+    p = gpu_params(S, "gini", 5, 24, 4, 64, min_leaf=10, seed=3, max_depth=4, n_trees=2,
+                   bootstrap=True)
+    c0 = context()
+    ref = c0.train_tree(p, wl.X, labels=wl.labels)
+    want = [ref.export(t) for t in range(2)]
+    ref.free()
+    c0.close()
+    used = None
+    for k in (1, 2, 3, 5, 8, 13):
+        c = context()  # a fresh context grows its work buffers from nothing
+        try:
+            c.test_hooks(-1, k)
+            with pytest.raises(S.SlmError) as e:
+                c.train_tree(p, wl.X, labels=wl.labels)
+            assert e.value.status == S.SLM_ENOMEM
+            c.test_hooks(-1, 0)
+            f = c.train_tree(p, wl.X, labels=wl.labels)
+            got = [f.export(t) for t in range(2)]
+            f.free()
+            for a, b in zip(want, got):
+                for key in a:
+                    assert np.array_equal(a[key], b[key]), key
+        finally:
+            c.test_hooks(-1, 0)
+            c.close()
+        if used is None:
+            used = _used_bytes()
+        else:  # closed contexts give their memory back
+            assert _used_bytes() <= used + (64 << 20)
+
+
+def _members(leaf, h):
+    out = np.zeros(leaf.shape[0], bool)
+    node = leaf.astype(np.int64).copy()
+    while True:
+        out |= node == h
+        if (node <= h).all():
+            break
+        node = np.where(node > h, (node - 1) // 2, node)
+    return np.nonzero(out)[0].astype(np.int32)
+
+
+def test_forest_root_level_equals_separate_searches(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    n, d, K, trees = 6000, 12, 4, 3
+    wl = W.gmm(n, d, K, seed=5)
+    p = gpu_params(S, "gini", K, 24, 15, 64, min_leaf=5, seed=7, max_depth=1, n_trees=trees,
+                   bootstrap=True)
+    f = ctx.train_tree(p, wl.X, labels=wl.labels)
+    g = [f.export(t) for t in range(trees)]
+    f.free()
+    q = gpu_params(S, "gini", K, 24, 15, 64, min_leaf=5, seed=7)
+    for t in range(trees):
+        w = ctx.bootstrap(7, t, n)
+        idx = np.nonzero(w)[0].astype(np.int32)
+        r = ctx.node_split(q, wl.X, labels=wl.labels, sample_idx=idx, weights=w[idx],
+                           node_uid=t << 16)
+        assert np.array_equal(g[t]["dir"][0], r["gbest"])
+        assert (g[t]["bin"][0], g[t]["n_left"][0]) == (r["bin"], r["n_left"])
+
+
+def test_tree_second_level_equals_separate_searches(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    n, d, K = 6000, 10, 3
+    wl = W.gmm(n, d, K, seed=6)
+    p = gpu_params(S, "entropy", K, 16, 12, 64, min_leaf=5, seed=9, max_depth=2)
+    f = ctx.train_tree(p, wl.X, labels=wl.labels)
+    g = f.export(0)
+    _, _, leaf = ctx.predict(f, wl.X, want_leaf=True)
+    f.free()
+    q = gpu_params(S, "entropy", K, 16, 12, 64, min_leaf=5, seed=9)
+    checked = 0
+    for h in (1, 2):
+        if g["kind"][h] != 1:
+            continue
+        idx = _members(leaf[:, 0], h)
+        r = ctx.node_split(q, wl.X, labels=wl.labels, sample_idx=idx, node_uid=h)
+        assert np.array_equal(g["dir"][h], r["gbest"])
+        assert (g["bin"][h], g["n_left"][h]) == (r["bin"], r["n_left"])
+        checked += 1
+    assert checked >= 1
