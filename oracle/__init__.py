@@ -39,7 +39,13 @@ class Params(C.Structure):
         ("c2", C.c_float), ("max_depth", C.c_int32), ("min_leaf", C.c_int32),
         ("seed", C.c_uint64), ("precision", C.c_int32),
         ("n_threads", C.c_int32), ("topk", C.c_int32), ("top_n", C.c_int32),
+        ("apso", C.c_int32),
     ]
+
+
+class Apso(C.Structure):
+    _fields_ = [("f", C.c_float), ("state", C.c_int32), ("c1", C.c_float), ("c2", C.c_float),
+                ("w", C.c_float)]
 
 
 class Eval(C.Structure):
@@ -145,6 +151,9 @@ def lib():
                                               C.c_int32, C.c_void_p, C.c_void_p,
                                               C.c_void_p]
             L.ora_select_features.restype = C.c_int
+            L.ora_apso_step.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                        C.c_float, C.c_float, C.c_float, P(Apso)]
+            L.ora_apso_step.restype = None
             L.ora_train_tree.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                                          P(_Tree)]
@@ -163,11 +172,11 @@ def _ptr(a: Optional[np.ndarray]):
 def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
                 n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8,
                 min_leaf=1, seed=1, precision=F32_MIRROR, n_threads=0,
-                topk=0, top_n=0) -> Params:
+                topk=0, top_n=0, apso=False) -> Params:
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
     return Params(crit, 0 if crit == MSE else n_classes, n_particles, n_iters,
                   n_bins, inertia, c1, c2, max_depth, min_leaf, seed, precision,
-                  n_threads, topk, top_n)
+                  n_threads, topk, top_n, 1 if apso else 0)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -229,6 +238,19 @@ def eval_swarm(params: Params, X, labels, y, pos, idx=None, wts=None,
     if rc:
         raise ValueError(f"ora_eval_swarm failed: {rc}")
     return [_struct_dict(e) for e in out], bins, z
+
+
+APSO_EXPLORE, APSO_EXPLOIT, APSO_CONVERGE, APSO_JUMPOUT = 1, 2, 3, 4
+PURPOSE_APSO = 7
+
+
+def apso_step(x, gpart, prev_state, c1, c2, delta) -> dict:
+    """One adaptive-PSO state update from positions x[P, d]."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    P, d = x.shape
+    out = Apso()
+    lib().ora_apso_step(P, d, _ptr(x), gpart, prev_state, c1, c2, delta, C.byref(out))
+    return {name: getattr(out, name) for name, _ in out._fields_}
 
 
 def select_features(params: Params, X, labels, y, n, idx=None, wts=None):

@@ -138,6 +138,97 @@ void ora_pso_step(const ora_params* p, int32_t P, int32_t d, double* x,
   }
 }
 
+/* Fuzzy memberships of the evolutionary factor in the four states. */
+static float apso_mu(int state, float f) {
+  switch (state) {
+    case ORA_APSO_EXPLORE:
+      if (f <= 0.4f) return 0.0f;
+      if (f <= 0.6f) return 5.0f * f - 2.0f;
+      if (f <= 0.7f) return 1.0f;
+      if (f <= 0.8f) return -10.0f * f + 8.0f;
+      return 0.0f;
+    case ORA_APSO_EXPLOIT:
+      if (f <= 0.2f) return 0.0f;
+      if (f <= 0.3f) return 10.0f * f - 2.0f;
+      if (f <= 0.4f) return 1.0f;
+      if (f <= 0.6f) return -5.0f * f + 3.0f;
+      return 0.0f;
+    case ORA_APSO_CONVERGE:
+      if (f <= 0.1f) return 1.0f;
+      if (f <= 0.3f) return -5.0f * f + 1.5f;
+      return 0.0f;
+    default:
+      if (f <= 0.7f) return 0.0f;
+      if (f <= 0.9f) return 5.0f * f - 3.5f;
+      return 1.0f;
+  }
+}
+
+static float clamp_c(float c) { return c < 1.5f ? 1.5f : c > 2.5f ? 2.5f : c; }
+
+void ora_apso_step(int32_t P, int32_t d, const double* x, int32_t gpart, int32_t prev_state,
+                   float c1, float c2, float delta, ora_apso* out) {
+  float dmin = 0.0f, dmax = 0.0f, dg = 0.0f;
+  for (int32_t i = 0; i < P; ++i) {
+    float acc = 0.0f;
+    for (int32_t j = 0; j < P; ++j) {
+      if (j == i) continue;
+      float s2 = 0.0f;
+      for (int32_t k = 0; k < d; ++k) {
+        const float diff = (float)x[(int64_t)i * d + k] - (float)x[(int64_t)j * d + k];
+        s2 = fmaf(diff, diff, s2);
+      }
+      acc = acc + sqrtf(s2);
+    }
+    const float di = P > 1 ? acc / (float)(P - 1) : 0.0f;
+    if (i == 0 || di < dmin) dmin = di;
+    if (i == 0 || di > dmax) dmax = di;
+    if (i == gpart) dg = di;
+  }
+  const float f = dmax > dmin ? (dg - dmin) / (dmax - dmin) : 0.0f;
+  int cand[4], nc = 0;
+  float mu[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int sidx = 1; sidx <= 4; ++sidx) {
+    mu[sidx] = apso_mu(sidx, f);
+    if (mu[sidx] > 0.0f) cand[nc++] = sidx;
+  }
+  int state = cand[0];
+  if (nc > 1) {
+    const int next = prev_state % 4 + 1;
+    int has_prev = 0, has_next = 0;
+    for (int q = 0; q < nc; ++q) {
+      has_prev |= cand[q] == prev_state;
+      has_next |= cand[q] == next;
+    }
+    if (has_prev)
+      state = prev_state;
+    else if (has_next)
+      state = next;
+    else
+      for (int q = 1; q < nc; ++q)
+        if (mu[cand[q]] > mu[state]) state = cand[q];
+  }
+  const float h = 0.5f * delta;
+  switch (state) {
+    case ORA_APSO_EXPLORE: c1 = c1 + delta; c2 = c2 - delta; break;
+    case ORA_APSO_EXPLOIT: c1 = c1 + h; c2 = c2 - h; break;
+    case ORA_APSO_CONVERGE: c1 = c1 + h; c2 = c2 + h; break;
+    default: c1 = c1 - delta; c2 = c2 + delta; break;
+  }
+  c1 = clamp_c(c1);
+  c2 = clamp_c(c2);
+  const float sum = c1 + c2;
+  if (sum > 4.0f) {
+    c1 = (4.0f * c1) / sum;
+    c2 = (4.0f * c2) / sum;
+  }
+  out->f = f;
+  out->state = state;
+  out->c1 = c1;
+  out->c2 = c2;
+  out->w = (float)(1.0 / (1.0 + 1.5 * exp(-2.6 * (double)f)));
+}
+
 /* ------------------------------------------------------------------------ */
 /* Scoring one projection vector on one node.                               */
 
@@ -648,13 +739,26 @@ static int node_split_full(const ora_params* p, const float* X, int32_t d,
   ora_eval gbe;
   memset(&gbe, 0, sizeof(gbe));
   int32_t gpart = 0, giter = 0;
+  ora_params q = *p;  /* the move's inertia and learning factors */
+  int32_t astate = ORA_APSO_EXPLORE;
   for (int32_t t = 0; t <= T; ++t) {
     if (t > 0) {
+      if (p->apso) {
+        /* the state after evaluation t-1 sets the move to iteration t */
+        float du;
+        ora_swarm_uniforms(p->seed, node_uid, (uint32_t)(t - 1), 1, 1, ORA_PURPOSE_APSO, &du);
+        ora_apso st;
+        ora_apso_step(P, d, x, gpart, astate, q.c1, q.c2, 0.05f + 0.05f * du, &st);
+        astate = st.state;
+        q.c1 = st.c1;
+        q.c2 = st.c2;
+        q.inertia = st.w;
+      }
       ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, P, d, ORA_PURPOSE_R1, u);
       for (int64_t e = 0; e < PD; ++e) r1[e] = u[e];
       ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, P, d, ORA_PURPOSE_R2, u);
       for (int64_t e = 0; e < PD; ++e) r2[e] = u[e];
-      ora_pso_step(p, P, d, x, v, pb, gb, r1, r2);
+      ora_pso_step(&q, P, d, x, v, pb, gb, r1, r2);
     }
     int tie = 0, event = 0;
     rc = eval_all(p, proj_of(p), X, d, labels, y, idx, wts, n_idx, x, NULL, P, ev,

@@ -65,7 +65,36 @@ typedef struct {
   int32_t top_n;        /* 0 or >= d: every feature; else the swarm searches
                            the subspace of the node's top_n features by their
                            own split loss (ora_select_features) */
+  int32_t apso;         /* 1: adaptive PSO (Sec. III-B): inertia, c1 and c2
+                           set before every move by ora_apso_step */
 } ora_params;
+
+/* Adaptive PSO (Sec. III-B; the rules of the cited APSO method): the
+ * swarm's evolutionary state from the particles' mean distances, and the
+ * inertia and learning factors of the next move. */
+enum { ORA_APSO_EXPLORE = 1, ORA_APSO_EXPLOIT = 2, ORA_APSO_CONVERGE = 3,
+       ORA_APSO_JUMPOUT = 4 };
+enum { ORA_PURPOSE_APSO = 7 };
+typedef struct {
+  float f;       /* evolutionary factor (d_g - d_min) / (d_max - d_min) */
+  int32_t state; /* ORA_APSO_* */
+  float c1, c2;  /* learning factors of the next move */
+  float w;       /* inertia of the next move */
+} ora_apso;
+
+/* One state update from positions x[P*d] (float values) and the index of
+ * the particle that holds gbest: d_i = (sum over j != i, in increasing j, of
+ * sqrtf of the sequential fmaf sum over features of (x_ik - x_jk)^2) / (P-1);
+ * f = (d_g - d_min) / (d_max - d_min), 0 if d_max = d_min; the state from
+ * f's fuzzy memberships (overlaps: keep prev_state if it is a candidate,
+ * else the state after it in the ring 1 -> 2 -> 3 -> 4 -> 1, else the larger
+ * membership, ties to the lower state); with delta in [0.05, 0.1]: explore
+ * c1 += delta, c2 -= delta; exploit +0.5 delta, -0.5 delta; converge
+ * +0.5 delta, +0.5 delta; jump out -delta, +delta; each clamped to [1.5,
+ * 2.5], scaled by 4 / (c1 + c2) when the sum exceeds 4; w = 1 / (1 + 1.5
+ * exp(-2.6 f)) in double, rounded to float. All float steps rounded once. */
+void ora_apso_step(int32_t P, int32_t d, const double* x, int32_t gpart, int32_t prev_state,
+                   float c1, float c2, float delta, ora_apso* out);
 
 /* Result of scoring one projection vector on one node. */
 typedef struct {
