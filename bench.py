@@ -99,6 +99,8 @@ def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
          "l2": "flushed between steps (256 MiB write outside the timed events)"}
     if cfg.get("top_n"):
         d["feature_prescreen_top_n"] = cfg["top_n"]
+    if cfg.get("apso"):
+        d["swarm"] = "adaptive PSO (evolutionary-state estimation)"
     if args_launch is not None:
         d["search_loop_graphs"] = args_launch.graphs
         d["projection_tile_mode"] = args_launch.tiles
@@ -279,6 +281,30 @@ def leaf_gini(leaf, labels, K):
     return float((tot[m] - (c[m] ** 2).sum(axis=1) / tot[m]).sum()) / leaf.shape[0]
 
 
+def apso_quality(ctx, S, cfg, wl, proj, topk, X, L, Y, n_ids=32):
+    """Root searches with adaptive and plain PSO from the same initial
+    swarms (node ids 0..n_ids-1): the iteration at which adaptive PSO's gB
+    loss first reaches plain PSO's final loss (None if never), and both
+    final losses."""
+    pa = make_params(S, dict(cfg, max_depth=1), wl, proj, topk)
+    pp = make_params(S, dict(cfg, max_depth=1, apso=False), wl, proj, topk)
+    hit, fa, fp = [], [], []
+    for uid in range(n_ids):
+        a = ctx.node_split(pa, X, labels=L, y=Y, node_uid=uid, want_trace=True)["trace"]
+        b = ctx.node_split(pp, X, labels=L, y=Y, node_uid=uid, want_trace=True)["trace"]
+        reach = np.flatnonzero(a <= b[-1])
+        hit.append(int(reach[0]) if reach.size else None)
+        fa.append(float(a[-1]))
+        fp.append(float(b[-1]))
+    got = [h for h in hit if h is not None]
+    return {"searches": n_ids, "iters": cfg["n_iters"],
+            "reached_plain_final_loss": len(got) / n_ids,
+            "median_iter_to_plain_final_loss": float(np.median(got)) if got else None,
+            "median_final_loss_apso": float(np.median(fa)),
+            "median_final_loss_plain": float(np.median(fp)),
+            "apso_lower_final_loss": float(np.mean(np.array(fa) < np.array(fp)))}
+
+
 def make_params(S, cfg, wl, proj, topk):
     return S.make_params(cfg["criterion"], wl.n_classes, n_particles=cfg["n_particles"],
                          n_iters=cfg["n_iters"], n_bins=cfg["n_bins"],
@@ -286,7 +312,7 @@ def make_params(S, cfg, wl, proj, topk):
                          n_trees=cfg["n_trees"],
                          bootstrap=cfg.get("bootstrap", cfg["n_trees"] > 1),
                          proj=S.SLM_PROJ_BF16_TOPK if proj == "bf16" else S.SLM_PROJ_FP32,
-                         topk=topk, top_n=cfg.get("top_n", 0))
+                         topk=topk, top_n=cfg.get("top_n", 0), apso=cfg.get("apso", False))
 
 
 def time_steps(ctx, p, X, L, Y, steps, flush, stream):
@@ -458,9 +484,9 @@ def run_ours(args):
                  else "PDL-chained stream launches")),
              "projection_tiles": ctx.tuned_shapes(),
              "last_hist_cluster": ctx.tuning_stats()["last_hist_cluster"]}
-    if args.compare_plain and cfg.get("top_n"):
-        # the same tree without the pre-screen, same harness
-        pp = make_params(S, dict(cfg, top_n=0), wl, proj, topk)
+    if args.compare_plain and (cfg.get("top_n") or cfg.get("apso")):
+        # the same tree without the pre-screen / adaptive PSO, same harness
+        pp = make_params(S, dict(cfg, top_n=0, apso=False), wl, proj, topk)
         for _ in range(max(1, args.warmup)):
             ctx.train_tree(pp, X, labels=L, y=Y).free()
         tp, ep, _ = time_steps(ctx, pp, X, L, Y, args.steps, flush, stream)
@@ -469,8 +495,10 @@ def run_ours(args):
         f.free()
         extra["plain_form"] = {"tree_train_ms": sum(tp) / len(tp),
                                "value": ep / (sum(tp) / 1e3), "train_loss": lossp,
-                               "speedup_of_prescreen": (sum(tp) / len(tp)) /
+                               "speedup_of_variant": (sum(tp) / len(tp)) /
                                (tot_ms / args.steps)}
+    if args.compare_plain and cfg.get("apso"):
+        extra["apso_vs_plain_root"] = apso_quality(ctx, S, cfg, wl, proj, topk, X, L, Y)
     if args.compare_fp32 and proj == "bf16":
         # the plain FP32 form of the same workload, same harness
         p32 = make_params(S, cfg, wl, "fp32", topk)
@@ -742,8 +770,11 @@ def main():
     ap.add_argument("--proj", choices=["fp32", "bf16"], default=None)
     ap.add_argument("--topk", type=int, default=8)
     ap.add_argument("--compare-fp32", action="store_true")
+    ap.add_argument("--apso", action="store_true",
+                    help="adaptive PSO (FP32 form): the workload's searches adapt inertia "
+                         "and learning factors to the swarm's evolutionary state")
     ap.add_argument("--compare-plain", action="store_true",
-                    help="pre-screen workloads: also time the tree without the pre-screen")
+                    help="with a pre-screen or --apso: also time the plain tree")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graphs", choices=["on", "off"], default=None,
                     help="run each search's iteration loop as one CUDA graph launch "
@@ -758,6 +789,8 @@ def main():
         args.proj = W.SETTINGS[args.workload].get("proj", "fp32")
     if args.graphs is None:
         args.graphs = "on" if W.SETTINGS[args.workload].get("graphs") else "off"
+    if args.apso:
+        W.SETTINGS[args.workload]["apso"] = True
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:

@@ -102,6 +102,20 @@ typedef struct slm_params {
                           dimensional search) and gB is returned lifted to d
                           features, zero elsewhere. Needs SLM_PROJ_FP32,
                           seeded = 0 and d <= 256 (SLM_EUNSUPPORTED) */
+  int32_t apso;        /* 1: adaptive PSO (Sec. III-B, with the published
+                          rules of the cited APSO method): before every move
+                          each node's evolutionary state is estimated from
+                          the particles' mean distances and the move uses
+                          the state's learning factors (from c1, c2 at the
+                          start) and an inertia from the evolutionary factor
+                          (inertia is then unused); in the convergence state
+                          a copy of gB with one coordinate moved by a
+                          Gaussian step is scored with the next evaluation
+                          and replaces gB if better, else the worst
+                          particle (elitist learning); 0: plain PSO. Needs
+                          SLM_PROJ_FP32 and n_particles < 256 with
+                          (n_particles rounded up to 4) * d * 4 <= 200 KB
+                          (SLM_EUNSUPPORTED) */
   uint64_t seed;       /* Philox-4x32-10 key for every random draw */
 } slm_params;
 

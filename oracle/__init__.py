@@ -65,7 +65,8 @@ class Split(C.Structure):
         ("threshold", C.c_double), ("loss", C.c_double),
         ("q_num", C.c_uint64), ("q_den", C.c_uint64),
         ("n_left", C.c_double), ("n_right", C.c_double),
-        ("first_near_tie", C.c_int32),
+        ("first_near_tie", C.c_int32), ("elite_tries", C.c_int32),
+        ("elite_accepts", C.c_int32),
     ]
 
 
@@ -154,6 +155,13 @@ def lib():
             L.ora_apso_step.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                         C.c_float, C.c_float, C.c_float, P(Apso)]
             L.ora_apso_step.restype = None
+            L.ora_elite_candidate.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32,
+                                              C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                              P(C.c_int32)]
+            L.ora_elite_candidate.restype = None
+            L.ora_elite_apply.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 4 + [
+                P(C.c_double), C.c_int32, C.c_void_p, C.c_void_p, C.c_double, P(C.c_int32)]
+            L.ora_elite_apply.restype = C.c_int32
             L.ora_train_tree.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                                          P(_Tree)]
@@ -251,6 +259,34 @@ def apso_step(x, gpart, prev_state, c1, c2, delta) -> dict:
     out = Apso()
     lib().ora_apso_step(P, d, _ptr(x), gpart, prev_state, c1, c2, delta, C.byref(out))
     return {name: getattr(out, name) for name, _ in out._fields_}
+
+
+def elite_candidate(seed, node_uid, t, T, gb, precision=F32_MIRROR):
+    """Elitist-learning candidate of the adaptive PSO: (e[d], k)."""
+    gb = np.ascontiguousarray(gb, dtype=np.float64)
+    e = np.empty_like(gb)
+    k = C.c_int32(0)
+    lib().ora_elite_candidate(seed, node_uid, t, T, gb.size, _ptr(gb), precision, _ptr(e),
+                              C.byref(k))
+    return e, k.value
+
+
+def elite_apply(x, pb, cur_loss, pb_loss, g_loss, gpart, gb, elite, e_loss):
+    """Elitist-learning acceptance on losses (inf: invalid). Arrays are
+    updated in place; returns (accepted, worst, new gB loss)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    P, d = x.shape
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (pb, cur_loss, pb_loss, gb,
+                                                                  elite)]
+    g = C.c_double(g_loss)
+    w = C.c_int32(-2)
+    rc = lib().ora_elite_apply(P, d, _ptr(x), _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                               C.byref(g), gpart, _ptr(arrs[3]), _ptr(arrs[4]), e_loss,
+                               C.byref(w))
+    if rc < 0:
+        raise ValueError(f"ora_elite_apply failed: {rc}")
+    return dict(accepted=bool(rc), worst=w.value, g_loss=g.value, x=x, pb=arrs[0],
+                cur_loss=arrs[1], pb_loss=arrs[2], gb=arrs[3])
 
 
 def select_features(params: Params, X, labels, y, n, idx=None, wts=None):

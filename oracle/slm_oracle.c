@@ -677,6 +677,102 @@ int ora_score_bins(const ora_params* p, const int32_t* labels, const float* y,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Elitist learning of the adaptive PSO (Sec. III-B; the cited APSO method's  */
+/* rule for the convergence state): a copy of gB with one coordinate moved   */
+/* by a Gaussian step is scored; it becomes gB if better, otherwise it takes */
+/* the place of the worst particle.                                          */
+
+void ora_elite_candidate(uint64_t seed, uint32_t node_uid, uint32_t t, int32_t T, int32_t d,
+                         const double* gb, int32_t precision, double* e, int32_t* k_out) {
+  float u[4];
+  ora_swarm_uniforms(seed, node_uid, t, 1, 4, ORA_PURPOSE_APSO, u);
+  const int32_t k = (int32_t)((double)u[1] * (double)d);
+  const double g = sqrt(-2.0 * log((double)(1.0f - u[2]))) *
+                   cos(6.283185307179586 * (double)u[3]);
+  for (int32_t j = 0; j < d; ++j) e[j] = gb[j];
+  if (precision == ORA_F64) {
+    const double sigma = 1.0 - 0.9 * ((double)t / (double)T);
+    e[k] = gb[k] + 2.0 * sigma * g;
+  } else {
+    const float sigma = 1.0f - 0.9f * ((float)t / (float)T);
+    e[k] = (double)((float)gb[k] + (2.0f * sigma) * (float)g);
+  }
+  if (k_out) *k_out = k;
+}
+
+#define EV_ARGS(e) (e)->valid, (e)->loss, (e)->q_num, (e)->q_den
+
+/* The acceptance step on scored positions: ev / pbe the particles' current
+ * and personal-best scores, gbe gB's score; returns 1 when the candidate
+ * (score ee, position elite) became gB, else 0 with the replaced particle in
+ * *worst. Near-ties of the comparisons that decide are flagged in *tie. */
+static int elite_apply(int crit, int32_t P, int32_t d, double* x, double* pb, ora_eval* ev,
+                       ora_eval* pbe, ora_eval* gbe, int32_t gpart, double* gb,
+                       const double* elite, const ora_eval* ee, int* tie, int32_t* worst) {
+  if (gbe->valid && ee->valid && near_tie(ee->loss, gbe->loss)) *tie = 1;
+  if (better(crit, EV_ARGS(ee), EV_ARGS(gbe))) {
+    *gbe = *ee;
+    pbe[gpart] = *ee;
+    memcpy(gb, elite, sizeof(double) * d);
+    memcpy(pb + (int64_t)gpart * d, elite, sizeof(double) * d);
+    return 1;
+  }
+  int32_t w = 0;
+  for (int32_t i = 1; i < P; ++i)
+    if (better(crit, EV_ARGS(&ev[w]), EV_ARGS(&ev[i]))) w = i; /* i strictly worse */
+  for (int32_t i = 0; i < P; ++i)
+    if (i != w && ev[i].valid && ev[w].valid && near_tie(ev[i].loss, ev[w].loss)) *tie = 1;
+  memcpy(x + (int64_t)w * d, elite, sizeof(double) * d);
+  ev[w] = *ee;
+  if (pbe[w].valid && ee->valid && near_tie(ee->loss, pbe[w].loss)) *tie = 1;
+  if (better(crit, EV_ARGS(ee), EV_ARGS(&pbe[w]))) {
+    pbe[w] = *ee;
+    memcpy(pb + (int64_t)w * d, elite, sizeof(double) * d);
+  }
+  *worst = w;
+  return 0;
+}
+
+static ora_eval loss_eval(double loss) {
+  ora_eval e;
+  memset(&e, 0, sizeof(e));
+  e.valid = isfinite(loss) ? 1 : 0;
+  e.loss = loss;
+  return e;
+}
+
+int32_t ora_elite_apply(int32_t P, int32_t d, double* x, double* pb, double* cur_loss,
+                        double* pb_loss, double* g_loss, int32_t gpart, double* gb,
+                        const double* elite, double e_loss, int32_t* worst_out) {
+  if (P < 1 || d < 1 || gpart < 0 || gpart >= P) return -1;
+  ora_eval* ev = (ora_eval*)calloc((size_t)P, sizeof(ora_eval));
+  ora_eval* pbe = (ora_eval*)calloc((size_t)P, sizeof(ora_eval));
+  if (!ev || !pbe) {
+    free(ev);
+    free(pbe);
+    return -2;
+  }
+  for (int32_t i = 0; i < P; ++i) {
+    ev[i] = loss_eval(cur_loss[i]);
+    pbe[i] = loss_eval(pb_loss[i]);
+  }
+  ora_eval gbe = loss_eval(*g_loss), ee = loss_eval(e_loss);
+  int tie = 0;
+  int32_t w = -1;
+  const int acc = elite_apply(ORA_MSE, P, d, x, pb, ev, pbe, &gbe, gpart, gb, elite, &ee, &tie,
+                              &w);
+  for (int32_t i = 0; i < P; ++i) {
+    cur_loss[i] = ev[i].valid ? ev[i].loss : INFINITY;
+    pb_loss[i] = pbe[i].valid ? pbe[i].loss : INFINITY;
+  }
+  *g_loss = gbe.valid ? gbe.loss : INFINITY;
+  if (worst_out) *worst_out = w;
+  free(ev);
+  free(pbe);
+  return acc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 1 (PSO), synchronous form: every particle moves with the gbest  */
 /* held at the end of the previous iteration, then all are scored, then     */
 /* pbest and gbest are updated with strict "<" in increasing particle order. */
@@ -699,7 +795,8 @@ static int node_split_full(const ora_params* p, const float* X, int32_t d,
                            double* gbest_out, double* dir_out, ora_split* out,
                            double* trace_loss, int32_t* trace_particle) {
   if (check_params(p, d) || p->n_particles < 1 || p->n_iters < 0 || n_idx < 0 ||
-      !X || !idx || !out || (p->precision == ORA_BF16_TOPK && p->topk < 1))
+      !X || !idx || !out || (p->precision == ORA_BF16_TOPK && p->topk < 1) ||
+      (p->apso && p->precision == ORA_BF16_TOPK))
     return -1;
   const int32_t P = p->n_particles;
   const int32_t T = p->n_iters;
@@ -717,8 +814,9 @@ static int node_split_full(const ora_params* p, const float* X, int32_t d,
   const int32_t k = bf16 ? (p->topk < P ? p->topk : P) : 0;
   int32_t* sel = (int32_t*)calloc((size_t)(k > 0 ? k : 1), sizeof(int32_t));
   ora_eval* ef = (ora_eval*)calloc((size_t)(k > 0 ? k : 1), sizeof(ora_eval));
+  double* elite = (double*)calloc((size_t)d, sizeof(double));
   int rc = 0;
-  if (!x || !v || !pb || !gb || !r1 || !r2 || !u || !ev || !pbe || !sel || !ef) {
+  if (!x || !v || !pb || !gb || !r1 || !r2 || !u || !ev || !pbe || !sel || !ef || !elite) {
     rc = -2;
     goto done;
   }
@@ -741,19 +839,9 @@ static int node_split_full(const ora_params* p, const float* X, int32_t d,
   int32_t gpart = 0, giter = 0;
   ora_params q = *p;  /* the move's inertia and learning factors */
   int32_t astate = ORA_APSO_EXPLORE;
+  int pending = 0; /* an elite candidate waits for this evaluation */
   for (int32_t t = 0; t <= T; ++t) {
     if (t > 0) {
-      if (p->apso) {
-        /* the state after evaluation t-1 sets the move to iteration t */
-        float du;
-        ora_swarm_uniforms(p->seed, node_uid, (uint32_t)(t - 1), 1, 1, ORA_PURPOSE_APSO, &du);
-        ora_apso st;
-        ora_apso_step(P, d, x, gpart, astate, q.c1, q.c2, 0.05f + 0.05f * du, &st);
-        astate = st.state;
-        q.c1 = st.c1;
-        q.c2 = st.c2;
-        q.inertia = st.w;
-      }
       ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, P, d, ORA_PURPOSE_R1, u);
       for (int64_t e = 0; e < PD; ++e) r1[e] = u[e];
       ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, P, d, ORA_PURPOSE_R2, u);
@@ -812,10 +900,45 @@ static int node_split_full(const ora_params* p, const float* X, int32_t d,
         memcpy(gb, x + (int64_t)i * d, sizeof(double) * d);
       }
     }
+    if (pending) {
+      /* the elite candidate made after evaluation t-1, scored with this
+       * evaluation, after the particles' pbest and gbest steps */
+      ora_eval ee;
+      int tie_e = 0, event_e = 0;
+      int32_t w;
+      rc = eval_all(p, proj_of(p), X, d, labels, y, idx, wts, n_idx, elite, NULL, 1, &ee, NULL,
+                    NULL, &tie_e, &event_e);
+      if (rc) goto done;
+      tie |= tie_e;
+      event |= event_e;
+      ++out->elite_tries;
+      if (elite_apply(p->criterion, P, d, x, pb, ev, pbe, &gbe, gpart, gb, elite, &ee, &tie,
+                      &w)) {
+        giter = t;
+        ++out->elite_accepts;
+      }
+      pending = 0;
+    }
     if (p->criterion == ORA_GINI) tie = 0; /* exact rationals: no near-ties */
     if ((tie || event) && out->first_near_tie < 0) out->first_near_tie = t;
     if (trace_loss) trace_loss[t] = gbe.valid ? gbe.loss : INFINITY;
     if (trace_particle) trace_particle[t] = gpart;
+    if (p->apso && t < T) {
+      /* the state after evaluation t sets the move to iteration t + 1 */
+      float du;
+      ora_swarm_uniforms(p->seed, node_uid, (uint32_t)t, 1, 1, ORA_PURPOSE_APSO, &du);
+      ora_apso st;
+      ora_apso_step(P, d, x, gpart, astate, q.c1, q.c2, 0.05f + 0.05f * du, &st);
+      astate = st.state;
+      q.c1 = st.c1;
+      q.c2 = st.c2;
+      q.inertia = st.w;
+      if (astate == ORA_APSO_CONVERGE) {
+        ora_elite_candidate(p->seed, node_uid, (uint32_t)t, T, d, gb, p->precision, elite,
+                            NULL);
+        pending = 1;
+      }
+    }
   }
 
   copy_eval_to_split(&gbe, out);
@@ -847,6 +970,7 @@ done:
   free(pbe);
   free(sel);
   free(ef);
+  free(elite);
   return rc;
 }
 

@@ -66,7 +66,11 @@ typedef struct {
                            the subspace of the node's top_n features by their
                            own split loss (ora_select_features) */
   int32_t apso;         /* 1: adaptive PSO (Sec. III-B): inertia, c1 and c2
-                           set before every move by ora_apso_step */
+                           set before every move by ora_apso_step, and in the
+                           convergence state an elite candidate
+                           (ora_elite_candidate) scored with the next
+                           evaluation and applied by ora_elite_apply's rule.
+                           Not with ORA_BF16_TOPK */
 } ora_params;
 
 /* Adaptive PSO (Sec. III-B; the rules of the cited APSO method): the
@@ -96,6 +100,29 @@ typedef struct {
 void ora_apso_step(int32_t P, int32_t d, const double* x, int32_t gpart, int32_t prev_state,
                    float c1, float c2, float delta, ora_apso* out);
 
+/* Elitist learning of the cited APSO method, candidate: gB with one
+ * coordinate k moved by a Gaussian step. From the purpose-7 block at
+ * (node_uid, t, 0, 0) with uniforms u0..u3 (lane 0 is the state update's
+ * delta): k = floor(u1 d) (exact, in double); g = sqrt(-2 ln(1 - u2))
+ * cos(2 pi u3) in double, rounded to float; sigma = 1 - 0.9 (t / T) in
+ * float (the step's standard deviation falls linearly from 1 to 0.1 of the
+ * initial range's width 2 over the search); e_k = gB_k + (2 sigma) g, in
+ * float in the float modes. Writes e[d] and k. */
+void ora_elite_candidate(uint64_t seed, uint32_t node_uid, uint32_t t, int32_t T, int32_t d,
+                         const double* gb, int32_t precision, double* e, int32_t* k_out);
+
+/* Elitist learning, acceptance, on losses (+inf: no admissible split; a
+ * strictly lower loss is better): if the candidate's loss e_loss is below
+ * gB's *g_loss, gB and the personal best of the gB particle gpart become the
+ * candidate (position and loss); otherwise the particle with the worst
+ * current loss (ties to the lower index) takes the candidate's position and
+ * current loss, and its personal best too when the candidate beats it.
+ * Arrays: x, pb [P*d]; cur_loss, pb_loss [P]; gb, elite [d]. Returns 1 when
+ * accepted, else 0 with the replaced particle in *worst_out. */
+int32_t ora_elite_apply(int32_t P, int32_t d, double* x, double* pb, double* cur_loss,
+                        double* pb_loss, double* g_loss, int32_t gpart, double* gb,
+                        const double* elite, double e_loss, int32_t* worst_out);
+
 /* Result of scoring one projection vector on one node. */
 typedef struct {
   double zmin, zmax, inv_w; /* projected range and bins per unit length */
@@ -122,6 +149,8 @@ typedef struct {
                                near-tie of double losses, or (ORA_BF16_TOPK) a
                                sample whose bfloat16 dot product is not exact
                                in float and lies near a bin edge; -1 if none */
+  int32_t elite_tries;      /* adaptive PSO: elite candidates scored */
+  int32_t elite_accepts;    /* ... of which became gB */
 } ora_split;
 
 /* Tree in heap layout: node h has children 2h+1 and 2h+2; H = 2^(D+1)-1. */

@@ -34,7 +34,7 @@ class slm_params(C.Structure):
         ("c1", C.c_float), ("c2", C.c_float), ("max_depth", C.c_int32),
         ("min_leaf", C.c_int32), ("proj", C.c_int32), ("n_trees", C.c_int32),
         ("bootstrap", C.c_int32), ("seeded", C.c_int32), ("top_n", C.c_int32),
-        ("seed", C.c_uint64),
+        ("apso", C.c_int32), ("seed", C.c_uint64),
     ]
 
 
@@ -130,12 +130,12 @@ def lib():
 def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
                 n_bins=64, inertia=0.7, c1=1.5, c2=1.5, max_depth=8, min_leaf=1,
                 seed=1, n_trees=1, bootstrap=False, proj=SLM_PROJ_FP32,
-                topk=8, seeded=False, top_n=0) -> slm_params:
+                topk=8, seeded=False, top_n=0, apso=False) -> slm_params:
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
     return slm_params(crit, 0 if crit == SLM_MSE else n_classes, n_particles,
                       n_iters, n_bins, topk, inertia, c1, c2, max_depth, min_leaf,
                       proj, n_trees, 1 if bootstrap else 0, 1 if seeded else 0, top_n,
-                      seed)
+                      1 if apso else 0, seed)
 
 
 def _ptr(a) -> Optional[int]:

@@ -610,6 +610,42 @@ __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes
   return bi;
 }
 
+// The particle with the worst score of node a (invalid scores worst, ties
+// to the lower index), as seen by one warp; every lane returns it.
+__device__ int worst_argmax(const Problem& pr, const EvalRes* cur) {
+  const int lane = threadIdx.x & 31;
+  int wi = -1;
+  EvalRes we = invalid_res();
+  for (int p = lane; p < pr.P; p += 32) {
+    const EvalRes e = cur[p];
+    if (wi < 0 || better(we, e, pr.crit)) {
+      wi = p;
+      we = e;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
+    const EvalRes o = shfl_res(we, lane ^ off);
+    bool take;
+    if (oi < 0)
+      take = false;
+    else if (wi < 0)
+      take = true;
+    else if (better(we, o, pr.crit))
+      take = true;
+    else if (better(o, we, pr.crit))
+      take = false;
+    else
+      take = oi < wi;
+    if (take) {
+      wi = oi;
+      we = o;
+    }
+  }
+  return wi;
+}
+
 // Eq. pso-1 for features 4q..4q+3 of particle pi of node a, to iteration t+1:
 // v <- omega v + (c1 r1)(pB - x) + (c2 r2)(gB - x);  x <- x + v. pbp: the
 // node's pbest rows, gsrc: gB. With sw.posb the new positions are also
@@ -642,6 +678,299 @@ __device__ __forceinline__ void move_item(const Problem& pr, const Swarm& sw, co
     pos[j] = xn[c];
   }
   if (sw.posb) store_posb4(sw.posb, Pp, pr.dp, a, pi, 4 * q, xn);
+}
+
+// Fuzzy memberships of the evolutionary factor f in the adaptive PSO states
+// (1 exploration, 2 exploitation, 3 convergence, 4 jumping out).
+__device__ float apso_mu(int state, float f) {
+  switch (state) {
+    case 1:
+      if (f <= 0.4f) return 0.0f;
+      if (f <= 0.6f) return __fsub_rn(__fmul_rn(5.0f, f), 2.0f);
+      if (f <= 0.7f) return 1.0f;
+      if (f <= 0.8f) return __fadd_rn(__fmul_rn(-10.0f, f), 8.0f);
+      return 0.0f;
+    case 2:
+      if (f <= 0.2f) return 0.0f;
+      if (f <= 0.3f) return __fsub_rn(__fmul_rn(10.0f, f), 2.0f);
+      if (f <= 0.4f) return 1.0f;
+      if (f <= 0.6f) return __fadd_rn(__fmul_rn(-5.0f, f), 3.0f);
+      return 0.0f;
+    case 3:
+      if (f <= 0.1f) return 1.0f;
+      if (f <= 0.3f) return __fadd_rn(__fmul_rn(-5.0f, f), 1.5f);
+      return 0.0f;
+    default:
+      if (f <= 0.7f) return 0.0f;
+      if (f <= 0.9f) return __fsub_rn(__fmul_rn(5.0f, f), 3.5f);
+      return 1.0f;
+  }
+}
+
+// Adaptive PSO (Sec. III-B; the published rules of the cited APSO method),
+// one CTA per node after evaluation t, in place of k_move:
+// 1. the gbest step (k_move's rule), then the elite candidate scored in this
+//    evaluation (slot P): gB and the gB particle's personal best if strictly
+//    better, else the worst particle's position (and personal best if beaten);
+// for t < T:
+// 2. each particle's mean distance d_i to the others (every squared distance
+//    a sequential fused multiply-add sum over the features, then the square
+//    roots added in increasing j, all in float with one rounding per
+//    operation); f = (d_g - d_min) / (d_max - d_min); the state from f's
+//    memberships (overlaps: keep the previous state, else the next in the
+//    ring 1 -> 2 -> 3 -> 4 -> 1, else the larger membership, ties to the
+//    lower state); the learning factors moved by delta = 0.05 + 0.05 u (u
+//    the swarm draw of purpose 7 at (uid, t, 0, 0)), clamped to [1.5, 2.5]
+//    and scaled to a sum of 4 when above; the inertia 1 / (1 + 1.5
+//    exp(-2.6 f)) in double, rounded to float;
+// 3. in the convergence state the next elite candidate (elitist learning);
+// 4. the move of Eq. pso-1 with these factors.
+//
+// Layout: positions feature-major in shared memory (row k holds feature k of
+// the Pq = P rounded up to 4 particles, 16-byte aligned), so a thread's 4 x 4
+// tile of (i, j) pairs reads two float4 per feature and the lanes of a warp
+// (consecutive j blocks) read consecutive 16-byte words. The rows i are taken
+// in chunks of apso_rows(P, d) whose square roots go to a buffer of stride
+// Pq + 1, from which thread r adds row r without bank conflicts.
+__host__ __device__ inline int apso_pq(int P) { return (P + 3) & ~3; }
+
+__host__ __device__ inline size_t apso_smem(int P, int d, int R) {
+  const int Pq = apso_pq(P);
+  return sizeof(float) * ((size_t)d * Pq + (size_t)R * (Pq + 1));
+}
+
+// Rows per chunk: the largest of 64, 32, 16, 8, 4 (not above Pq) whose
+// buffers fit in 227 KB; 0 if none does.
+inline int apso_rows(int P, int d) {
+  const int Pq = apso_pq(P);
+  for (int R = 64; R >= 4; R >>= 1)
+    if (R <= Pq && apso_smem(P, d, R) <= 227 * 1024) return R;
+  return apso_smem(P, d, 4) <= 227 * 1024 ? 4 : 0;
+}
+
+__global__ void __launch_bounds__(256)
+    k_apso(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes, int t, SwarmCoef co,
+           const int32_t* __restrict__ list, int A, int R) {
+  extern __shared__ __align__(16) float asm_[];
+  __shared__ float s_di[kMaxParticles];
+  __shared__ int s_gp;
+  pdl_trigger();
+  pdl_wait();
+  __shared__ int s_mode, s_w, s_wpb, s_k;
+  __shared__ float s_g, s_c[3];
+  const int a = list ? list[blockIdx.x] : (int)blockIdx.x;
+  const int P = pr.P, d = pr.d, Pp = pr.Pp, Pq = apso_pq(P);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t cb = (int64_t)a * Pp;
+  float* pos = sw.pos + cb * d;
+  float* pbp = sw.pbest + cb * d;
+  float* gbp = sw.gbest + (int64_t)a * d;
+  float* erow = pos + (int64_t)P * d;  // the elite candidate's slot
+  // 1. gbest step of evaluation t (the rule of k_move), then the elite
+  // candidate scored in this evaluation: gB and the gB particle's personal
+  // best if strictly better, else the worst particle's position (and its
+  // personal best if better than it)
+  if (warp == 0) {
+    const EvalRes gold = sw.gb[(int64_t)((t + 1) & 1) * A + a];
+    EvalRes be;
+    const int bi = gbest_argmin(pr, sw.cur + cb, gold, t, &be);
+    const int pending = sw.apso[a].pending;
+    const int wi = pending ? worst_argmax(pr, sw.cur + cb) : -1;
+    if (lane == 0) {
+      EvalRes gnew = bi >= 0 ? be : gold;
+      const int gp = bi >= 0 ? bi : sw.gpart[a];
+      int git = bi >= 0 ? t : sw.giter[a];
+      int mode = bi >= 0 ? 1 : 0, wr = -1, wpb = 0;
+      if (pending) {
+        const EvalRes ee = sw.cur[cb + P];
+        if (better(ee, gnew, pr.crit)) {
+          gnew = ee;
+          git = t;
+          mode = 2;
+          sw.pb[cb + gp] = ee;
+        } else {
+          wr = wi;
+          sw.cur[cb + wi] = ee;
+          if (better(ee, sw.pb[cb + wi], pr.crit)) {
+            sw.pb[cb + wi] = ee;
+            wpb = 1;
+          }
+        }
+        sw.apso[a].pending = 0;
+      }
+      sw.gb[(int64_t)(t & 1) * A + a] = gnew;
+      sw.gpart[a] = gp;
+      sw.giter[a] = git;
+      if (sw.trace)
+        sw.trace[(int64_t)a * (sw.T + 1) + t] =
+            gnew.valid ? gnew.loss : __longlong_as_double(0x7ff0000000000000LL);
+      s_gp = gp;
+      s_mode = mode;
+      s_w = wr;
+      s_wpb = wpb;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    if (s_mode == 1) {
+      gbp[j] = pbp[(int64_t)s_gp * d + j];
+    } else if (s_mode == 2) {
+      gbp[j] = erow[j];
+      pbp[(int64_t)s_gp * d + j] = erow[j];
+    }
+    if (s_w >= 0) {
+      pos[(int64_t)s_w * d + j] = erow[j];
+      if (s_wpb) pbp[(int64_t)s_w * d + j] = erow[j];
+    }
+  }
+  if (t >= sw.T) return;
+  __syncthreads();
+  // 2. the evolutionary state of the current positions
+  float* xt = asm_;             // [d][Pq] current positions, feature-major
+  float* rw = asm_ + d * Pq;    // [R][Pq + 1] square roots of a chunk of rows
+  for (int e = threadIdx.x; e < Pq * d; e += blockDim.x) {
+    const int i = e / d, k = e - i * d;
+    xt[k * Pq + i] = i < P ? pos[e] : 0.0f;
+  }
+  __syncthreads();
+  const int nJ = Pq >> 2, ld = Pq + 1;
+  for (int c0 = 0; c0 < P; c0 += R) {
+    const int rows = min(R, P - c0), nI = (rows + 3) >> 2;
+    for (int u = threadIdx.x; u < nI * nJ; u += blockDim.x) {
+      const int ib = u / nJ, jb = u - ib * nJ;
+      const int i0 = c0 + 4 * ib, j0 = 4 * jb;
+      float s2[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s2[p][q] = 0.0f;
+#pragma unroll 2
+      for (int k = 0; k < d; ++k) {
+        const float4 xi = *reinterpret_cast<const float4*>(xt + k * Pq + i0);
+        const float4 xj = *reinterpret_cast<const float4*>(xt + k * Pq + j0);
+        const float vi[4] = {xi.x, xi.y, xi.z, xi.w}, vj[4] = {xj.x, xj.y, xj.z, xj.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float diff = __fsub_rn(vi[p], vj[q]);
+            s2[p][q] = fmaf(diff, diff, s2[p][q]);
+          }
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (i0 + p < c0 + rows && j0 + q < P)
+            rw[(i0 + p - c0) * ld + j0 + q] = __fsqrt_rn(s2[p][q]);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < rows) {
+      const int i = c0 + threadIdx.x;
+      const float* ri = rw + threadIdx.x * ld;
+      float acc = 0.0f;
+      for (int j = 0; j < P; ++j)
+        if (j != i) acc = __fadd_rn(acc, ri[j]);
+      s_di[i] = P > 1 ? __fdiv_rn(acc, (float)(P - 1)) : 0.0f;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float dmin = s_di[0], dmax = s_di[0];
+    for (int i = 1; i < P; ++i) {
+      dmin = s_di[i] < dmin ? s_di[i] : dmin;
+      dmax = s_di[i] > dmax ? s_di[i] : dmax;
+    }
+    const float dg = s_di[s_gp];
+    const float f = dmax > dmin ? __fdiv_rn(__fsub_rn(dg, dmin), __fsub_rn(dmax, dmin)) : 0.0f;
+    ApsoState st = sw.apso[a];
+    float mu[5];
+    int cand[4], nc = 0;
+    for (int q = 1; q <= 4; ++q) {
+      mu[q] = apso_mu(q, f);
+      if (mu[q] > 0.0f) cand[nc++] = q;
+    }
+    int state = cand[0];
+    if (nc > 1) {
+      const int next = st.state % 4 + 1;
+      bool has_prev = false, has_next = false;
+      for (int q = 0; q < nc; ++q) {
+        has_prev |= cand[q] == st.state;
+        has_next |= cand[q] == next;
+      }
+      if (has_prev) {
+        state = st.state;
+      } else if (has_next) {
+        state = next;
+      } else {
+        for (int q = 1; q < nc; ++q)
+          if (mu[cand[q]] > mu[state]) state = cand[q];
+      }
+    }
+    const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
+    const U4 r = philox4x32_10(nodes[a].uid, (uint32_t)t, 0u, kApso << 24, k0, k1);
+    const float delta = __fadd_rn(0.05f, __fmul_rn(0.05f, uniform24(r.v[0])));
+    const float h = __fmul_rn(0.5f, delta);
+    float c1 = st.c1, c2 = st.c2;
+    if (state == 1) {
+      c1 = __fadd_rn(c1, delta);
+      c2 = __fsub_rn(c2, delta);
+    } else if (state == 2) {
+      c1 = __fadd_rn(c1, h);
+      c2 = __fsub_rn(c2, h);
+    } else if (state == 3) {
+      c1 = __fadd_rn(c1, h);
+      c2 = __fadd_rn(c2, h);
+    } else {
+      c1 = __fsub_rn(c1, delta);
+      c2 = __fadd_rn(c2, delta);
+    }
+    c1 = c1 < 1.5f ? 1.5f : c1 > 2.5f ? 2.5f : c1;
+    c2 = c2 < 1.5f ? 1.5f : c2 > 2.5f ? 2.5f : c2;
+    const float sum = __fadd_rn(c1, c2);
+    if (sum > 4.0f) {
+      c1 = __fdiv_rn(__fmul_rn(4.0f, c1), sum);
+      c2 = __fdiv_rn(__fmul_rn(4.0f, c2), sum);
+    }
+    st.state = state;
+    st.c1 = c1;
+    st.c2 = c2;
+    st.w = (float)__ddiv_rn(1.0, __dadd_rn(1.0, __dmul_rn(1.5, exp(__dmul_rn(-2.6, (double)f)))));
+    st.pending = state == 3;
+    sw.apso[a] = st;
+    s_mode = st.pending;
+    s_c[0] = st.w;
+    s_c[1] = st.c1;
+    s_c[2] = st.c2;
+  } else if (threadIdx.x == 32) {
+    // elitist learning's step, beside thread 0's state update: coordinate
+    // k = floor(u1 d), g = sqrt(-2 ln(1 - u2)) cos(2 pi u3) (Box-Muller, in
+    // double, rounded to float)
+    const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
+    const U4 r = philox4x32_10(nodes[a].uid, (uint32_t)t, 0u, kApso << 24, k0, k1);
+    s_k = (int)__dmul_rn((double)uniform24(r.v[1]), (double)d);
+    s_g = (float)__dmul_rn(sqrt(__dmul_rn(-2.0, log((double)__fsub_rn(1.0f, uniform24(r.v[2]))))),
+                           cos(__dmul_rn(6.283185307179586, (double)uniform24(r.v[3]))));
+  }
+  __syncthreads();
+  // 3. in the convergence state the next elite candidate: gB with
+  // coordinate k moved by (2 sigma) g, sigma = 1 - 0.9 t / T
+  if (s_mode) {
+    const float sigma = __fsub_rn(1.0f, __fmul_rn(0.9f, __fdiv_rn((float)t, (float)sw.T)));
+    for (int j = threadIdx.x; j < d; j += blockDim.x)
+      erow[j] = j == s_k ? __fadd_rn(gbp[j], __fmul_rn(__fmul_rn(2.0f, sigma), s_g)) : gbp[j];
+  }
+  // 4. the move of Eq. pso-1 to iteration t + 1 with the adaptive factors
+  // (k_move's step, here by this node's CTA)
+  SwarmCoef cm = co;
+  cm.inertia = s_c[0];
+  cm.c1 = s_c[1];
+  cm.c2 = s_c[2];
+  const int d4 = (d + 3) >> 2;
+  const uint32_t uid = nodes[a].uid;
+  for (int item = threadIdx.x; item < P * d4; item += blockDim.x)
+    move_item(pr, sw, cm, uid, a, t, item / d4, item - (item / d4) * d4, pbp, gbp);
 }
 
 // Algorithm 1's gbest step after evaluation t, then (t < T) the synchronous
@@ -1503,6 +1832,7 @@ __global__ void k_swarm_init(Problem pr, Swarm sw,
     sw.gb[gridDim.x + a] = invalid_res();
     sw.gpart[a] = 0;
     sw.giter[a] = 0;
+    if (sw.apso) sw.apso[a] = ApsoState{1, 0, co.c1, co.c2, co.inertia};
   }
 }
 
@@ -1851,6 +2181,29 @@ cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc*
                               do_update);
   return cudaLaunchKernelEx(&cfg, k_hist_warp<SLM_ENTROPY>, pr, sw, nodes, list, (int)pairs, t,
                             do_update);
+}
+
+cudaError_t launch_apso(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
+                        int t, SwarmCoef co, cudaStream_t st, const int32_t* list, int n_list) {
+  const int n_nodes = list ? n_list : A;
+  if (n_nodes <= 0 || !sw.apso) return cudaSuccess;
+  const int R = apso_rows(pr.P, pr.d);
+  if (R == 0) return cudaErrorInvalidValue;
+  const size_t smem = apso_smem(pr.P, pr.d, R);
+  cudaError_t e = cudaFuncSetAttribute(k_apso, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n_nodes, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_apso, pr, sw, nodes, t, co, list, A, R);
 }
 
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,

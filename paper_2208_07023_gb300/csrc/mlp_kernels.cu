@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(256)
     sw.gb[gridDim.x + a] = invalid_res();
     sw.gpart[a] = 0;
     sw.giter[a] = 0;
+    if (sw.apso) sw.apso[a] = ApsoState{1, 0, co.c1, co.c2, co.inertia};
   }
 }
 

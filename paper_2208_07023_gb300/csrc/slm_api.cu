@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <new>
@@ -43,6 +44,8 @@ enum Slot {
   // feature pre-screen: unit positions, kept features, the kept columns,
   // the lifted gbest
   S_FPOS, S_FEAT, W_XS, S_GFULL,
+  // adaptive PSO state per node
+  S_APSO,
   N_SLOTS
 };
 
@@ -156,6 +159,10 @@ struct slm_forest {
 };
 
 namespace {
+
+static_assert(sizeof(slm_params) == 80 && offsetof(slm_params, apso) == 64 &&
+                  offsetof(slm_params, seed) == 72,
+              "slm_params layout is part of the ABI (bindings mirror it)");
 
 slm_status fail(slm_ctx* c, slm_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -272,6 +279,12 @@ slm_status check_params(slm_ctx* c, const slm_params* p, int32_t d,
       return fail(c, SLM_EINVAL, "inertia / c1 / c2 must be finite");
     if (p->seeded != 0 && p->seeded != 1) return fail(c, SLM_EINVAL, "seeded must be 0 or 1");
     if (p->top_n < 0) return fail(c, SLM_EINVAL, "top_n must be >= 0");
+    if (p->apso != 0 && p->apso != 1) return fail(c, SLM_EINVAL, "apso must be 0 or 1");
+    if (p->apso && (p->proj != SLM_PROJ_FP32 || p->n_particles >= kMaxParticles ||
+                    (size_t)((p->n_particles + 3) & ~3) * d * 4 > 200 * 1024))
+      return fail(c, SLM_EUNSUPPORTED,
+                  "adaptive PSO needs SLM_PROJ_FP32, n_particles < 256 and (n_particles "
+                  "rounded up to 4) * d * 4 <= 200 KB");
     if (p->top_n > 0 && p->top_n < d &&
         (p->proj != SLM_PROJ_FP32 || p->seeded || d > kMaxParticles))
       return fail(c, SLM_EUNSUPPORTED,
@@ -438,6 +451,7 @@ slm_status setup_swarm(slm_ctx* c, Problem& pr, int A, int T, bool want_trace,
   CK(ensure(c->ws[S_DONE], sizeof(int32_t) * (size_t)A));
   CK(cudaMemsetAsync(c->ws[S_DONE].p, 0, sizeof(int32_t) * (size_t)A, c->stream));
   if (want_trace) CK(ensure(c->ws[S_TRACE], sizeof(double) * (size_t)A * (T + 1)));
+  CK(ensure(c->ws[S_APSO], sizeof(ApsoState) * (size_t)A));
   s.pos = ws_ptr<float>(c, S_POS);
   s.vel = ws_ptr<float>(c, S_VEL);
   s.pbest = ws_ptr<float>(c, S_PBEST);
@@ -691,9 +705,18 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
       return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
     }));
   }
-  if (co)
+  // with adaptive PSO the evaluation scored the swarm's particles and the
+  // elite slot after them; the swarm kernels see the particles only
+  Problem psw = pr;
+  if (sw.apso) psw.P = pr.P - 1;
+  if (co && sw.apso)
     CK(launch(c, SLM_K_SWARM_UPDATE, 0.0, [&] {
-      return launch_move(pr, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
+      return launch_apso(psw, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
+                         hp ? hp->n_moved : 0);
+    }));
+  if (co && !sw.apso)  // k_apso moves the adaptive swarm itself
+    CK(launch(c, SLM_K_SWARM_UPDATE, 0.0, [&] {
+      return launch_move(psw, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
                          hp ? hp->n_moved : 0);
     }));
   return SLM_OK;
@@ -1040,7 +1063,7 @@ struct KeyWriter {
     put(w.pos); put(w.vel); put(w.pbest); put(w.gbest); put(w.cur); put(w.pb); put(w.gb);
     put(w.gpart); put(w.giter); put(w.trace); put(w.zmm); put(w.z); put(w.done); put(w.err);
     put(w.T); put(w.sel); put(w.k); put(w.tk_sel); put(w.tk_inv); put(w.tk_pos);
-    put(w.tk_k); put(w.tk_kp); put(w.posb);
+    put(w.tk_k); put(w.tk_kp); put(w.posb); put(w.apso);
   }
 };
 
@@ -1050,11 +1073,19 @@ slm_status prescreen_search(slm_ctx* c, const slm_params* p, Problem& pr,
                             Swarm* sw_out);
 slm_status check_kernel_errors(slm_ctx* c);
 
-slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
+slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
                       const std::vector<NodeDesc>& nodes, bool want_trace,
                       Swarm* sw_out) {
-  if (p->top_n > 0 && p->top_n < pr.d)
-    return prescreen_search(c, p, pr, nodes, want_trace, sw_out);
+  if (p->top_n > 0 && p->top_n < pr_in.d)
+    return prescreen_search(c, p, pr_in, nodes, want_trace, sw_out);
+  // adaptive PSO scores one more slot per node, its elite candidate (slot
+  // P): pr is the evaluation's problem, psw the swarm kernels' (same layout)
+  Problem pr = pr_in;
+  if (p->apso) {
+    pr.P = pr_in.P + 1;
+    pr.Pp = (pr.P + kPG - 1) / kPG * kPG;
+    pr.G = pr.Pp / kPG;
+  }
   const int A = (int)nodes.size();
   // classification nodes (FP32 form) whose rows fit in shared memory run
   // their whole search in one persistent launch; the others (`in`) run the
@@ -1062,7 +1093,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
   std::vector<char> resident(A, 0);
   int n_res = 0;
   size_t smax = 0;
-  if (c->node_search && p->proj != SLM_PROJ_BF16_TOPK && p->criterion != SLM_MSE)
+  if (c->node_search && p->proj != SLM_PROJ_BF16_TOPK && p->criterion != SLM_MSE && !p->apso)
     for (int a = 0; a < A; ++a) {
       const size_t sm = node_search_smem(pr, nodes[a].seg_len);
       if (sm <= kNodeSearchMaxSmem) {
@@ -1091,6 +1122,13 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
   Swarm sw;
   slm_status s = setup_swarm(c, pr, A, p->n_iters, want_trace, nodes, tiles, &sw);
   if (s) return s;
+  // the scoring set-up's per-batch fields (MSE moments) go back to the caller
+  pr_in.m1 = pr.m1;
+  pr_in.m2 = pr.m2;
+  pr_in.mscale = pr.mscale;
+  Problem psw = pr;
+  psw.P = pr_in.P;
+  sw.apso = p->apso ? ws_ptr<ApsoState>(c, S_APSO) : nullptr;
   const SwarmCoef co{p->inertia, p->c1, p->c2, p->seed};
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   Bf16Plan bp;
@@ -1098,10 +1136,10 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr,
       (s = setup_bf16(c, pr, nodes, std::min(p->topk, p->n_particles), true, &sw, &bp)))
     return s;
   if (p->seeded) {
-    if ((s = seed_swarms(c, pr, nodes, sw, co))) return s;
+    if ((s = seed_swarms(c, psw, nodes, sw, co))) return s;
   } else {
     CK(launch(c, SLM_K_SWARM_INIT, 0.0,
-              [&] { return launch_swarm_init(pr, sw, dn, A, co, c->stream); }));
+              [&] { return launch_swarm_init(psw, sw, dn, A, co, c->stream); }));
   }
   c->last_node_search = 0;
   bool joined = true;

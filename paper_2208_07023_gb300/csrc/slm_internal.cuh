@@ -36,7 +36,8 @@ enum Purpose : uint32_t {
   kInitV = 2,
   kR1 = 3,
   kR2 = 4,
-  kBootstrap = 5
+  kBootstrap = 5,
+  kApso = 7  // the adaptive PSO step size delta, counter (uid, t, 0, 0)
 };
 
 // Score of one projection on one node. Same meaning as slm_eval.
@@ -131,6 +132,22 @@ struct Swarm {
   // when set, the swarm kernels also write the positions as bfloat16 MMA
   // operands: posb[A, Pp * dp] (layout of launch_to_mma_layout, R = Pp)
   uint16_t* posb;
+  // adaptive PSO: per node the state and the next move's inertia and
+  // learning factors (null: the fixed coefficients of SwarmCoef). The
+  // evaluation then scores one slot more than the swarm has particles: slot
+  // P (the swarm's P) holds the elite candidate, and k_apso, not k_move,
+  // takes the gbest step
+  struct ApsoState* apso;
+};
+
+// Adaptive PSO state of one node (Sec. III-B): evolutionary state 1..4
+// (exploration, exploitation, convergence, jumping out), whether an elite
+// candidate waits in slot P for the next evaluation, and the inertia and
+// learning factors of the next move.
+struct ApsoState {
+  int32_t state;
+  int32_t pending;
+  float c1, c2, w;
 };
 
 struct SwarmCoef {
@@ -190,6 +207,16 @@ bool hist_warp_ok(const Problem& pr);
 cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                              const int32_t* list, int n_nodes, int t, int do_update,
                              cudaStream_t st);
+// Adaptive PSO step of each node after evaluation t (sw.apso; pr.P the
+// swarm's particles, the elite candidate in slot pr.P): the gbest step, the
+// elite candidate's acceptance (gB, or the worst particle's place), then
+// for t < T the evolutionary factor of the current positions, the fuzzy
+// state, the learning factors and inertia of the move to t + 1, and in the
+// convergence state the next elite candidate, then the move of Eq. pso-1
+// (k_move is not launched) (of the n_list nodes list[] names, when set).
+cudaError_t launch_apso(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
+                        int t, SwarmCoef co, cudaStream_t st, const int32_t* list = nullptr,
+                        int n_list = 0);
 // gbest step of iteration t and (t < T) the Eq. pso-1 move of every particle
 // of A nodes to iteration t+1 (of the n_list nodes list[] names, when set).
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,

@@ -50,7 +50,9 @@ def test_status_strings_without_gpu():
 
 def test_params_struct_layout_matches_header():
     from paper_2208_07023_gb300 import binding
-    # int32 x 15 (+ padding to 8) then uint64 seed
-    assert ctypes.sizeof(binding.slm_params) == 15 * 4 + 4 + 8
+    # int32 x 17 (+ padding to 8) then uint64 seed; the library asserts the
+    # same size and offset at compile time
+    assert ctypes.sizeof(binding.slm_params) == 17 * 4 + 4 + 8
+    assert binding.slm_params.seed.offset == 72 and binding.slm_params.apso.offset == 64
     assert ctypes.sizeof(binding.slm_eval) == 56
     assert ctypes.sizeof(binding.slm_split) == 56 + 16

@@ -9,8 +9,17 @@ cited APSO method).
   the membership functions, against the ring rule for every previous state;
 * the learning-factor steps, clamping and normalisation, and the inertia's
   end values 1 / 2.5 and 1 / (1 + 1.5 e^-2.6);
+* elitist learning: the candidate differs from gB in exactly one coordinate,
+  whose index is uniform over the features (chi-square) and whose step is
+  Gaussian (Kolmogorov-Smirnov) with a standard deviation falling linearly
+  from 2 (the initial range's width) to 0.2 over the search; the acceptance
+  rule on hand-built swarms: a strictly better candidate becomes gB and the
+  gB particle's personal best, a tie or worse one replaces the worst particle
+  (invalid counts as worst, ties to the lower index) and its personal best
+  only when better;
 * end to end: the planted hyperplane is found, the trajectory differs from
-  plain PSO, and apso = 0 is plain PSO.
+  plain PSO, apso = 0 is plain PSO, and elite candidates are scored in the
+  convergence state, some of them accepted.
 """
 import numpy as np
 import pytest
@@ -112,3 +121,107 @@ def test_apso_search_end_to_end():
     assert a.split["loss"] < 0.24
     c = O.node_split(O.make_params("entropy", 2, 32, 50, 64, min_leaf=1, apso=False), X, labels)
     assert np.array_equal(c.trace_loss, b.trace_loss)
+
+
+def test_elite_candidate_moves_one_coordinate():
+    rng = np.random.default_rng(3)
+    gb = rng.standard_normal(12)
+    for uid in range(50):
+        e, k = O.elite_candidate(9, uid, 4, 20, gb)
+        diff = np.flatnonzero(e != gb)
+        assert 0 <= k < 12 and set(diff.tolist()) <= {k}
+        assert np.array_equal(np.delete(e, k), np.delete(gb, k))
+
+
+def test_elite_candidate_index_is_uniform():
+    from scipy import stats
+    d = 10
+    ks = [O.elite_candidate(5, uid, 0, 10, np.zeros(d))[1] for uid in range(5000)]
+    counts = np.bincount(ks, minlength=d)
+    assert stats.chisquare(counts).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("t,T,sd", [(0, 10, 2.0), (5, 10, 2.0 * 0.55), (9, 9, 0.2)])
+def test_elite_step_is_gaussian_with_linear_schedule(t, T, sd):
+    from scipy import stats
+    steps = []
+    for uid in range(4000):
+        e, k = O.elite_candidate(7, uid, t, T, np.zeros(4))
+        steps.append(e[k])
+    steps = np.array(steps)
+    assert stats.kstest(steps / sd, "norm").pvalue > 1e-3
+    assert np.std(steps) == pytest.approx(sd, rel=0.05)
+    # the float-mode candidate is rounded once per operation, as float
+    assert np.array_equal(steps, steps.astype(np.float32).astype(np.float64))
+
+
+def swarm(P=5, d=3):
+    x = np.arange(P * d, dtype=np.float64).reshape(P, d)
+    pb = x + 100.0
+    return x, pb
+
+
+def test_elite_better_becomes_gbest_and_gbest_particles_pbest():
+    x, pb = swarm()
+    cur = np.array([0.5, 0.3, 0.9, 0.2, 0.4])
+    pbl = np.array([0.4, 0.3, 0.8, 0.2, 0.4])
+    gb = pb[3].copy()
+    el = np.array([-1.0, -2.0, -3.0])
+    r = O.elite_apply(x, pb, cur, pbl, 0.2, 3, gb, el, 0.1)
+    assert r["accepted"] and r["g_loss"] == 0.1
+    assert np.array_equal(r["gb"], el) and np.array_equal(r["pb"][3], el)
+    assert r["pb_loss"][3] == 0.1
+    assert np.array_equal(r["x"], x) and np.array_equal(r["cur_loss"], cur)
+    assert np.array_equal(np.delete(r["pb"], 3, axis=0), np.delete(pb, 3, axis=0))
+
+
+@pytest.mark.parametrize("e_loss,pb_replaced", [(0.2, True), (0.5, True), (0.8, False), (0.85, False)])
+def test_elite_not_better_replaces_the_worst_particle(e_loss, pb_replaced):
+    x, pb = swarm()
+    cur = np.array([0.5, 0.3, 0.9, 0.2, 0.4])
+    pbl = np.array([0.4, 0.3, 0.8, 0.2, 0.4])
+    gb = pb[3].copy()
+    el = np.array([-1.0, -2.0, -3.0])
+    r = O.elite_apply(x, pb, cur, pbl, 0.2, 3, gb, el, e_loss)
+    assert not r["accepted"] and r["worst"] == 2 and r["g_loss"] == 0.2
+    assert np.array_equal(r["x"][2], el) and r["cur_loss"][2] == e_loss
+    assert np.array_equal(np.delete(r["x"], 2, axis=0), np.delete(x, 2, axis=0))
+    assert np.array_equal(r["gb"], gb)
+    assert np.array_equal(r["pb"][2], el if pb_replaced else pb[2])
+    assert r["pb_loss"][2] == (e_loss if pb_replaced else 0.8)
+
+
+def test_elite_worst_ties_and_invalid():
+    x, pb = swarm(4, 2)
+    el = np.array([7.0, 8.0])
+    # equal worst losses: the lower index
+    r = O.elite_apply(x, pb, np.array([0.6, 0.1, 0.6, 0.3]), np.full(4, 0.1), 0.1, 1,
+                      pb[1].copy(), el, 0.7)
+    assert r["worst"] == 0
+    # an invalid particle is the worst; an invalid candidate never becomes a pbest
+    r = O.elite_apply(x, pb, np.array([0.6, 0.1, np.inf, 0.3]), np.full(4, np.inf), 0.1, 1,
+                      pb[1].copy(), el, np.inf)
+    assert r["worst"] == 2 and not r["accepted"]
+    assert np.array_equal(r["x"][2], el) and np.array_equal(r["pb"][2], pb[2])
+
+
+def test_elite_learning_runs_in_the_search():
+    rng = np.random.default_rng(2)
+    n, d = 3000, 8
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    w = rng.standard_normal(d)
+    w /= np.linalg.norm(w)
+    labels = (X.astype(np.float64) @ w >= 0).astype(np.int32)
+    labels[rng.random(n) < 0.05] ^= 1
+    tries = accepts = 0
+    for seed in range(1, 6):
+        r = O.node_split(O.make_params("gini", 2, 32, 50, 64, min_leaf=1, apso=True, seed=seed),
+                         X, labels)
+        assert abs(r.direction @ w) > 0.99
+        assert np.all(np.diff(r.trace_loss) <= 0)
+        tries += r.split["elite_tries"]
+        accepts += r.split["elite_accepts"]
+        plain = O.node_split(O.make_params("gini", 2, 32, 50, 64, min_leaf=1, seed=seed),
+                             X, labels)
+        assert plain.split["elite_tries"] == 0
+    assert tries > 0 and 0 < accepts < tries
