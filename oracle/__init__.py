@@ -162,6 +162,12 @@ def lib():
             L.ora_elite_apply.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 4 + [
                 P(C.c_double), C.c_int32, C.c_void_p, C.c_void_p, C.c_double, P(C.c_int32)]
             L.ora_elite_apply.restype = C.c_int32
+            L.ora_train_boost.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
+                                          C.c_void_p, C.c_int32, C.c_float, P(_Tree),
+                                          P(C.c_float), C.c_void_p, C.c_void_p]
+            L.ora_boost_predict.argtypes = [P(Params), P(_Tree), C.c_int32, C.c_float,
+                                            C.c_float, C.c_void_p, C.c_int64, C.c_int32,
+                                            C.c_void_p]
             L.ora_train_tree.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                                          P(_Tree)]
@@ -400,6 +406,44 @@ def train_tree(params: Params, X, labels=None, y=None, tree_id=0,
     if rc:
         raise ValueError(f"ora_train_tree failed: {rc}")
     return t
+
+
+@dataclass
+class Boost:
+    trees: list
+    base: float
+    learning_rate: float
+    F: np.ndarray          # final boosted predictions of the training rows
+    train_mse: np.ndarray  # after each round
+
+
+def train_boost(params: Params, X, y, n_rounds, learning_rate) -> Boost:
+    """SLR Boost: least-squares gradient boosting of SLR trees."""
+    X, _, y, _, _ = _node_arrays(X, None, y, None, None)
+    n, d = X.shape
+    trees = [_empty_tree(params.max_depth, d) for _ in range(n_rounds)]
+    arr = (_Tree * max(1, n_rounds))(*[t._cstruct() for t in trees])
+    base = C.c_float(0.0)
+    F = np.empty(n, np.float32)
+    mse = np.empty(max(1, n_rounds), np.float64)
+    rc = lib().ora_train_boost(C.byref(params), _ptr(X), n, d, _ptr(y), n_rounds,
+                               learning_rate, arr, C.byref(base), _ptr(F), _ptr(mse))
+    if rc:
+        raise ValueError(f"ora_train_boost failed: {rc}")
+    return Boost(trees, base.value, learning_rate, F, mse[:n_rounds])
+
+
+def boost_predict(params: Params, boost: Boost, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, d = X.shape
+    M = len(boost.trees)
+    arr = (_Tree * max(1, M))(*[t._cstruct() for t in boost.trees])
+    out = np.empty(n, np.float32)
+    rc = lib().ora_boost_predict(C.byref(params), arr, M, boost.base, boost.learning_rate,
+                                 _ptr(X), n, d, _ptr(out))
+    if rc:
+        raise ValueError(f"ora_boost_predict failed: {rc}")
+    return out
 
 
 def predict(params: Params, tree: Tree, X):

@@ -1285,6 +1285,66 @@ int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
 }
 
 /* ------------------------------------------------------------------------ */
+/* SLR Boost: least-squares gradient boosting of SLR trees on residuals.     */
+
+int ora_train_boost(const ora_params* p, const float* X, int64_t n, int32_t d, const float* y,
+                    int32_t M, float eta, ora_tree* trees, float* base_out, float* F,
+                    double* mse_out) {
+  if (!p || p->criterion != ORA_MSE || n < 1 || d < 1 || !X || !y || M < 0 ||
+      !(eta > 0.0f && eta <= 1.0f) || !F || !base_out || (M > 0 && !trees))
+    return -1;
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += (double)y[i];
+  const float base = (float)(s / (double)n);
+  float* r = (float*)malloc(sizeof(float) * (size_t)n);
+  double* v = (double*)malloc(sizeof(double) * (size_t)n);
+  int rc = 0;
+  if (!r || !v) {
+    rc = -2;
+    goto done;
+  }
+  for (int64_t i = 0; i < n; ++i) F[i] = base;
+  ora_params q = *p;
+  for (int32_t m = 1; m <= M; ++m) {
+    for (int64_t i = 0; i < n; ++i) r[i] = y[i] - F[i];
+    q.seed = p->seed + (uint64_t)m;
+    rc = ora_train_tree(&q, X, n, d, NULL, r, 0, 0, &trees[m - 1]);
+    if (rc) goto done;
+    rc = ora_predict(&q, &trees[m - 1], X, n, d, NULL, v, NULL);
+    if (rc) goto done;
+    for (int64_t i = 0; i < n; ++i) F[i] = F[i] + eta * (float)v[i];
+    if (mse_out) {
+      double e = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        const double di = (double)y[i] - (double)F[i];
+        e += di * di;
+      }
+      mse_out[m - 1] = e / (double)n;
+    }
+  }
+  *base_out = base;
+done:
+  free(r);
+  free(v);
+  return rc;
+}
+
+int ora_boost_predict(const ora_params* p, const ora_tree* trees, int32_t M, float base,
+                      float eta, const float* X, int64_t n, int32_t d, float* out) {
+  if (!p || M < 0 || (M > 0 && !trees) || !X || !out || n < 0 || d < 1) return -1;
+  double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!v) return -2;
+  int rc = 0;
+  for (int64_t i = 0; i < n; ++i) out[i] = base;
+  for (int32_t m = 0; m < M && !rc; ++m) {
+    rc = ora_predict(p, &trees[m], X, n, d, NULL, v, NULL);
+    for (int64_t i = 0; i < n && !rc; ++i) out[i] = out[i] + eta * (float)v[i];
+  }
+  free(v);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Learned swarm proposal: node statistics, a 3-layer network, its loss and  */
 /* gradient, Adam, and the seeded initial swarm. Written from the            */
 /* definitions in slm_oracle.h, in double (the seeding in float).           */

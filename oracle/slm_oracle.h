@@ -302,6 +302,23 @@ void ora_adam_step(double* w, double* m, double* v, const double* g, int64_t n,
 void ora_swarm_seed(uint64_t seed, uint32_t node_uid, int32_t n_particles,
                     int32_t d, const float* mu_hat, const float* rho, float* pos);
 
+/* SLR Boost (Sec. V: the boosting ensemble of SLR trees), read as
+ * least-squares gradient boosting: base = (float)(mean of y, summed in
+ * double); F_i = base; for round m = 1..M: r_i = y_i - F_i (float), tree m
+ * grown by ora_train_tree on (X, r) with the Philox key seed + m (tree id 0,
+ * no bootstrap), F_i = F_i + eta * (float)v_i (float, rounded once per
+ * operation) with v_i tree m's leaf value of x_i; mse_out[m-1] = mean over i
+ * of (y_i - F_i)^2 in double after round m (may be NULL). trees[M] are
+ * caller-allocated like ora_train_tree's; F[n] receives the final F.
+ * Needs criterion ORA_MSE and 0 < eta <= 1. */
+int ora_train_boost(const ora_params* p, const float* X, int64_t n, int32_t d, const float* y,
+                    int32_t M, float eta, ora_tree* trees, float* base_out, float* F,
+                    double* mse_out);
+
+/* out[i] = base, then for m = 0..M-1: out[i] = out[i] + eta * (float)v_m(x_i). */
+int ora_boost_predict(const ora_params* p, const ora_tree* trees, int32_t M, float base,
+                      float eta, const float* X, int64_t n, int32_t d, float* out);
+
 /* Route samples through a tree grown by ora_train_tree. */
 int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
                 int64_t n, int32_t d, int32_t* class_out, double* value_out,
