@@ -101,6 +101,10 @@ def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
         d["feature_prescreen_top_n"] = cfg["top_n"]
     if cfg.get("apso"):
         d["swarm"] = "adaptive PSO (evolutionary-state estimation)"
+    if cfg.get("rounds"):
+        d["boost"] = {"rounds": cfg["rounds"], "learning_rate": cfg["lr"],
+                      "step": "one SLR Boost training: every round's tree, residuals, "
+                              "predictions and F updates"}
     if args_launch is not None:
         d["search_loop_graphs"] = args_launch.graphs
         d["projection_tile_mode"] = args_launch.tiles
@@ -315,7 +319,37 @@ def make_params(S, cfg, wl, proj, topk):
                          topk=topk, top_n=cfg.get("top_n", 0), apso=cfg.get("apso", False))
 
 
-def time_steps(ctx, p, X, L, Y, steps, flush, stream):
+class BoostRun:
+    """One SLR Boost training seen as a step: its rounds' evaluations."""
+
+    def __init__(self, boost):
+        self.b = boost
+
+    def info(self):
+        m = self.b.info()["n_rounds"]
+        return {"evaluations": sum(self.b.tree(i).info()["evaluations"] for i in range(m))}
+
+    def free(self):
+        self.b.free()
+
+
+def train_step(ctx, p, cfg, X, L, Y):
+    """One step of the workload: a tree / forest, or a boosting run."""
+    if cfg.get("rounds"):
+        return BoostRun(ctx.train_boost(p, X, Y, cfg["rounds"], cfg["lr"]))
+    return ctx.train_tree(p, X, labels=L, y=Y)
+
+
+def step_loss(ctx, f, wl, X):
+    if isinstance(f, BoostRun):
+        mse = f.b.train_mse
+        y = wl.y.astype(np.float64)
+        return {"boost_train_mse": float(mse[-1]), "mse_of_mean": float(np.var(y)),
+                "train_mse_by_round": [round(float(v), 6) for v in mse]}
+    return tree_loss(ctx, f, wl, X)
+
+
+def time_steps(ctx, p, X, L, Y, steps, flush, stream, cfg=None):
     """K timed steps: device time of each from events on the stream."""
     import torch
     times, evals = [], 0
@@ -325,7 +359,7 @@ def time_steps(ctx, p, X, L, Y, steps, flush, stream):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        f = ctx.train_tree(p, X, labels=L, y=Y)
+        f = train_step(ctx, p, cfg or {}, X, L, Y)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -360,11 +394,13 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
                             "avg_launch_ms": kp["ms"] / max(1, kp["launches"]),
                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     if kh["ms"] > 0:
-        # z (4 B per pair) + labels / targets (+ multiplicities) per entry and
-        # pass; the bf16 form scans P and then k particles per entry
+        # z (4 B per pair) + per entry and pass its label (4 B) or, for MSE,
+        # its two 8-byte fixed-point moments (+ a 4-byte multiplicity when
+        # weighted); the bf16 form scans P and then k particles per entry
         per_entry = P if proj != "bf16" else (P + topk) / 2.0
         weighted = cfg.get("bootstrap", cfg["n_trees"] > 1)
-        algo = kh["pairs"] * (4.0 + (8.0 if weighted else 4.0) / per_entry)
+        entry_b = (16.0 if cfg["criterion"] == "mse" else 4.0) + (4.0 if weighted else 0.0)
+        algo = kh["pairs"] * (4.0 + entry_b / per_entry)
         ach = algo / (kh["ms"] / 1e3) / 1e9
         roofs["hist_scan"] = {"kernel": "hist_scan", "bound": "hbm", "achieved": ach,
                               "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
@@ -447,14 +483,14 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
-        ctx.train_tree(p, X, labels=L, y=Y).free()
+        train_step(ctx, p, cfg, X, L, Y).free()
 
     # timed region: K trees, device time per tree from events on the stream
     clocks = ClockSampler(gpu_uuid(local))
     barrier()
     wall0 = time.perf_counter()
     with clocks:
-        times, evals, launches = time_steps(ctx, p, X, L, Y, args.steps, flush, stream)
+        times, evals, launches = time_steps(ctx, p, X, L, Y, args.steps, flush, stream, cfg)
         barrier()
     wall = time.perf_counter() - wall0
 
@@ -464,7 +500,7 @@ def run_ours(args):
     ctx.profile(True)
     for _ in range(args.steps):
         flush.zero_()
-        ctx.train_tree(p, X, labels=L, y=Y).free()
+        train_step(ctx, p, cfg, X, L, Y).free()
     kst = ctx.kernel_stats()
     ctx.profile(False)
 
@@ -473,8 +509,8 @@ def run_ours(args):
     value = evals_all / (tot_ms_max / 1e3)
 
     # training loss of the trees this form grows
-    f = ctx.train_tree(p, X, labels=L, y=Y)
-    loss = tree_loss(ctx, f, wl, X)
+    f = train_step(ctx, p, cfg, X, L, Y)
+    loss = step_loss(ctx, f, wl, X)
     f.free()
 
     extra = {"tree_train_ms": tot_ms_max / args.steps, "evals_per_step": evals // args.steps,
@@ -522,11 +558,14 @@ def run_ours(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f = ctx.train_tree(p, Xh, labels=Lh, y=Yh)
-        exports = [f.export(t) for t in range(cfg["n_trees"])]
+        f = train_step(ctx, p, cfg, Xh, Lh, Yh)
+        if isinstance(f, BoostRun):  # the per-round training MSE comes back
+            d2h = f.b.train_mse.nbytes
+        else:
+            exports = [f.export(t) for t in range(cfg["n_trees"])]
+            d2h = sum(v.nbytes for g in exports for v in g.values())
         e2e_t.append(time.perf_counter() - t0)
         e2e_ev += f.info()["evaluations"]
-        d2h = sum(v.nbytes for g in exports for v in g.values())
         f.free()
     e2e_value = e2e_ev / sum(e2e_t)
     h2d = wl.X.nbytes + (wl.labels.nbytes if wl.labels is not None else wl.y.nbytes)

@@ -288,6 +288,39 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
                        double* value_out, int32_t* leaf_out);
 
 
+/* ---- SLR Boost -----------------------------------------------------------
+ * The boosting ensemble of SLR trees (Sec. V names SLR Boost beside SLR
+ * Forest), read as least-squares gradient boosting on residuals, in float:
+ *   base = (float)(mean of y, summed in double);  F_i = base;
+ *   round m = 1..n_rounds: r_i = y_i - F_i; one SLR tree grown on (X, r)
+ *   with `params` and the Philox key params->seed + m (tree id 0);
+ *   F_i = F_i + learning_rate * (float)v_i, v_i the tree's leaf value of x_i.
+ * Each float operation is rounded once. */
+typedef struct slm_boost slm_boost;
+
+/* Trains n_rounds >= 0 rounds on X[n*d] and y[n] (host or device; the call
+ * copies host inputs). params: criterion SLM_MSE, n_trees 1, bootstrap 0
+ * (SLM_EINVAL / SLM_EUNSUPPORTED otherwise); 0 < learning_rate <= 1.
+ * train_mse_out[n_rounds] (host, may be NULL): mean of (y - F)^2 in double
+ * after each round. On success *out owns the trees (slm_boost_free). */
+slm_status slm_train_boost(slm_ctx* ctx, const slm_params* params, const float* X,
+                           int64_t n, int32_t d, const float* y, int32_t n_rounds,
+                           float learning_rate, double* train_mse_out,
+                           slm_boost** out);
+/* value_out[n] (host or device): base plus the rounds' learning_rate *
+ * (float) leaf values, added in round order (the training F for the
+ * training rows). */
+slm_status slm_boost_predict(slm_ctx* ctx, const slm_boost* boost, const float* X,
+                             int64_t n, int32_t d, float* value_out);
+/* Rounds, base and learning rate; any pointer may be NULL. */
+slm_status slm_boost_info(const slm_boost* boost, int32_t* n_rounds, float* base,
+                          float* learning_rate);
+/* The tree of round m + 1 (0 <= m < n_rounds), owned by the boost (read it
+ * with slm_forest_export / slm_predict; do not free it); NULL if out of
+ * range. */
+const slm_forest* slm_boost_tree(const slm_boost* boost, int32_t m);
+void slm_boost_free(slm_boost* boost);
+
 /* ---- learned swarm proposal ----------------------------------------------
  * Not in the paper, which starts every swarm uniformly in a fixed range (Sec. III-A):
  * a network that proposes a starting direction and spread for a node's swarm

@@ -118,6 +118,12 @@ def lib():
                                    C.c_int),
             "slm_use_proposal": ([vp, vp], C.c_int),
             "slm_swarm_seed": ([vp, u64, u32, i32, i32, vp, vp, vp], C.c_int),
+            "slm_train_boost": ([vp, P(slm_params), vp, i64, i32, vp, i32, C.c_float, vp,
+                                 P(vp)], C.c_int),
+            "slm_boost_predict": ([vp, vp, vp, i64, i32, vp], C.c_int),
+            "slm_boost_info": ([vp, P(i32), P(C.c_float), P(C.c_float)], C.c_int),
+            "slm_boost_tree": ([vp, i32], vp),
+            "slm_boost_free": ([vp], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -192,6 +198,55 @@ class Forest:
     def free(self):
         if self.handle:
             lib().slm_forest_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _RoundTree(Forest):
+    """A boosting round's tree: owned by its Boost, never freed here."""
+
+    def __init__(self, ctx, handle, owner):
+        super().__init__(ctx, handle)
+        self._owner = owner  # keeps the boost alive while the tree is used
+
+    def free(self):
+        self.handle = C.c_void_p(None)
+
+
+class Boost:
+    """SLR Boost: trees fitted to residuals, owned by the library."""
+
+    def __init__(self, ctx: "Context", handle, train_mse):
+        self.ctx, self.handle = ctx, C.c_void_p(handle)
+        self.train_mse = train_mse
+
+    def info(self) -> dict:
+        m, b, lr = C.c_int32(), C.c_float(), C.c_float()
+        self.ctx._check(lib().slm_boost_info(self.handle, C.byref(m), C.byref(b), C.byref(lr)))
+        return {"n_rounds": m.value, "base": b.value, "learning_rate": lr.value}
+
+    def tree(self, m: int) -> Forest:
+        h = lib().slm_boost_tree(self.handle, m)
+        if not h:
+            raise IndexError(m)
+        return _RoundTree(self.ctx, h, self)
+
+    def predict(self, X) -> np.ndarray:
+        X = _as(X, np.float32)
+        n, d = X.shape
+        out = np.empty(n, np.float32)
+        self.ctx._check(lib().slm_boost_predict(self.ctx.handle, self.handle, _ptr(X), n, d,
+                                                _ptr(out)))
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().slm_boost_free(self.handle)
             self.handle = C.c_void_p(None)
 
     def __del__(self):
@@ -453,6 +508,15 @@ class Context:
         self._check(lib().slm_train_tree(self.handle, C.byref(params), _ptr(X), n, d,
                                          _ptr(labels), _ptr(y), C.byref(h)))
         return Forest(self, h.value)
+
+    def train_boost(self, params, X, y, n_rounds: int, learning_rate: float) -> Boost:
+        X, y = _as(X, np.float32), _as(y, np.float32)
+        n, d = X.shape
+        mse = np.empty(max(1, n_rounds), np.float64)
+        h = C.c_void_p()
+        self._check(lib().slm_train_boost(self.handle, C.byref(params), _ptr(X), n, d, _ptr(y),
+                                          n_rounds, learning_rate, _ptr(mse), C.byref(h)))
+        return Boost(self, h.value, mse[:n_rounds])
 
     def predict(self, forest: Forest, X, want_leaf=False):
         X = _as(X, np.float32)

@@ -9,6 +9,7 @@
 #include <cstddef>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <random>
@@ -2147,6 +2148,176 @@ slm_status slm_predict(slm_ctx* c, const slm_forest* f, const float* X, int64_t 
                        c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return SLM_OK;
+}
+
+// ---- SLR Boost ---------------------------------------------------------------------
+
+struct slm_boost {
+  int device = 0;
+  slm_params params{};
+  int d = 0;
+  float base = 0.0f;
+  float eta = 0.0f;
+  std::vector<slm_forest*> trees;
+};
+
+}  // extern "C"
+
+namespace {
+
+// A finished tree keeps only its arrays: the level state of its growth goes.
+void release_level_state(slm_forest* f) {
+  DevBuf* bufs[] = {&f->own_X,     &f->side,     &f->lvl_nodes, &f->lvl_split, &f->lvl_cls,
+                    &f->lvl_par,   &f->smap,     &f->out3,      &f->dst,       &f->ltiles,
+                    &f->ltile0,    &f->acc_w,    &f->acc_y,     &f->tile_s,    &f->stile0,
+                    &f->tile_left, &f->tile_base, &f->p_lk,     &f->p_wl,      &f->lXb};
+  for (DevBuf* b : bufs) release(*b);
+  for (int i = 0; i < 2; ++i) {
+    release(f->lX[i]);
+    release(f->lab[i]);
+    release(f->ly[i]);
+    release(f->lw[i]);
+    release(f->lidx[i]);
+  }
+  f->X = nullptr;
+  f->level.clear();
+}
+
+// Device buffers of one boosting call, released on every exit.
+struct BoostWork {
+  DevBuf X, y, F, r, v, mse, base;
+  ~BoostWork() {
+    for (DevBuf* b : {&X, &y, &F, &r, &v, &mse, &base}) release(*b);
+  }
+};
+
+template <typename T>
+slm_status own_copy(slm_ctx* c, const T* src, size_t count, DevBuf& buf, const T** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return SLM_OK;
+  }
+  CK(ensure(buf, sizeof(T) * count));
+  CK(cudaMemcpyAsync(buf.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream));
+  *out = static_cast<const T*>(buf.p);
+  return SLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slm_status slm_train_boost(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                           int32_t d, const float* y, int32_t n_rounds, float learning_rate,
+                           double* train_mse_out, slm_boost** out) {
+  if (!c || !p || !X || !y || !out || n < 1 || d < 1 || n_rounds < 0)
+    return fail(c, SLM_EINVAL, "bad arguments to slm_train_boost");
+  *out = nullptr;
+  if (p->criterion != SLM_MSE) return fail(c, SLM_EINVAL, "boosting fits residuals: SLM_MSE");
+  if (!(learning_rate > 0.0f && learning_rate <= 1.0f))
+    return fail(c, SLM_EINVAL, "learning_rate must be in (0, 1]");
+  if (p->n_trees != 1 || p->bootstrap)
+    return fail(c, SLM_EUNSUPPORTED, "boosting grows one tree per round, without bootstrap");
+  CK(cudaSetDevice(c->device));
+  BoostWork w;
+  const float* dX;
+  const float* dy;
+  if (slm_status s = own_copy(c, X, (size_t)n * d, w.X, &dX)) return s;
+  if (slm_status s = own_copy(c, y, (size_t)n, w.y, &dy)) return s;
+  CK(ensure(w.F, sizeof(float) * (size_t)n));
+  CK(ensure(w.r, sizeof(float) * (size_t)n));
+  CK(ensure(w.v, sizeof(double) * (size_t)n));
+  CK(ensure(w.mse, sizeof(double) * (size_t)(n_rounds > 0 ? n_rounds : 1)));
+  CK(ensure(w.base, sizeof(float)));
+  float* F = static_cast<float*>(w.F.p);
+  float* r = static_cast<float*>(w.r.p);
+  double* v = static_cast<double*>(w.v.p);
+  double* mse = static_cast<double*>(w.mse.p);
+  CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+    return launch_boost_init(dy, n, F, static_cast<float*>(w.base.p), c->stream);
+  }));
+  std::unique_ptr<slm_boost, void (*)(slm_boost*)> b(new (std::nothrow) slm_boost,
+                                                     slm_boost_free);
+  if (!b) return fail(c, SLM_ENOMEM, "boost handle");
+  b->device = c->device;
+  b->params = *p;
+  b->d = d;
+  b->eta = learning_rate;
+  for (int32_t m = 1; m <= n_rounds; ++m) {
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_boost_residual(dy, F, r, n, c->stream); }));
+    slm_params q = *p;
+    q.seed = p->seed + (uint64_t)m;
+    slm_forest* f = nullptr;
+    if (slm_status s = slm_train_tree(c, &q, dX, n, d, nullptr, r, &f)) return s;
+    b->trees.push_back(f);
+    release_level_state(f);
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+      return launch_predict(dX, n, d, f->tr, 1, f->H, q.n_bins, 1, SLM_MSE, nullptr, v,
+                            nullptr, c->stream);
+    }));
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_boost_update(F, v, learning_rate, n, c->stream); }));
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_boost_mse(dy, F, n, mse + (m - 1), c->stream); }));
+  }
+  CK(cudaMemcpyAsync(&b->base, w.base.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (train_mse_out && n_rounds > 0)
+    CK(cudaMemcpyAsync(train_mse_out, mse, sizeof(double) * n_rounds, cudaMemcpyDefault,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (slm_status s = check_kernel_errors(c)) return s;
+  *out = b.release();
+  return SLM_OK;
+}
+
+slm_status slm_boost_predict(slm_ctx* c, const slm_boost* b, const float* X, int64_t n,
+                             int32_t d, float* value_out) {
+  if (!c || !b || !X || !value_out || n < 0 || d != b->d)
+    return fail(c, SLM_EINVAL, "bad arguments to slm_boost_predict");
+  if (n == 0) return SLM_OK;
+  CK(cudaSetDevice(c->device));
+  const float* dX;
+  if (slm_status s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX)) return s;
+  const size_t off_f = (sizeof(double) * (size_t)n + 15) & ~size_t(15);
+  CK(ensure(c->ws[S_OUT], off_f + sizeof(float) * (size_t)n));
+  unsigned char* base = static_cast<unsigned char*>(c->ws[S_OUT].p);
+  double* v = reinterpret_cast<double*>(base);
+  float* F = is_device_ptr(value_out) ? value_out : reinterpret_cast<float*>(base + off_f);
+  CK(launch(c, SLM_K_OTHER, 0.0, [&] { return launch_fill_f(F, b->base, n, c->stream); }));
+  for (const slm_forest* f : b->trees) {
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+      return launch_predict(dX, n, d, f->tr, 1, f->H, b->params.n_bins, 1, SLM_MSE, nullptr,
+                            v, nullptr, c->stream);
+    }));
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_boost_update(F, v, b->eta, n, c->stream); }));
+  }
+  if (F != value_out)
+    CK(cudaMemcpyAsync(value_out, F, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
+slm_status slm_boost_info(const slm_boost* b, int32_t* n_rounds, float* base,
+                          float* learning_rate) {
+  if (!b) return SLM_EINVAL;
+  if (n_rounds) *n_rounds = (int32_t)b->trees.size();
+  if (base) *base = b->base;
+  if (learning_rate) *learning_rate = b->eta;
+  return SLM_OK;
+}
+
+const slm_forest* slm_boost_tree(const slm_boost* b, int32_t m) {
+  if (!b || m < 0 || m >= (int32_t)b->trees.size()) return nullptr;
+  return b->trees[m];
+}
+
+void slm_boost_free(slm_boost* b) {
+  if (!b) return;
+  for (slm_forest* f : b->trees) slm_forest_free(f);
+  delete b;
 }
 
 // ---- learned swarm proposal ------------------------------------------------------

@@ -366,6 +366,19 @@ cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr,
                            int32_t* class_out, double* value_out,
                            int32_t* leaf_out, cudaStream_t st);
 
+// SLR Boost rounds: base = (float)(mean of y in double) and F[i] = base (one
+// CTA, a fixed summation order); mean of (y - F)^2 in double (one CTA);
+// r = y - F; F += eta * (float)v; F = v.
+cudaError_t launch_boost_init(const float* y, int64_t n, float* F, float* base_out,
+                              cudaStream_t st);
+cudaError_t launch_boost_mse(const float* y, const float* F, int64_t n, double* out,
+                             cudaStream_t st);
+cudaError_t launch_boost_residual(const float* y, const float* F, float* r, int64_t n,
+                                  cudaStream_t st);
+cudaError_t launch_boost_update(float* F, const double* v, float eta, int64_t n,
+                                cudaStream_t st);
+cudaError_t launch_fill_f(float* F, float v, int64_t n, cudaStream_t st);
+
 // ---- learned swarm proposal (mlp_kernels.cu) --------------------------------
 
 // Parameters, "input x output" row-major, FP32 masters and the bfloat16

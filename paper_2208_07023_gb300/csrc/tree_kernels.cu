@@ -577,4 +577,114 @@ cudaError_t launch_lift(const float* gs, const int32_t* feat, int A, int n, int 
   return cudaGetLastError();
 }
 
+// ---- SLR Boost: the boosting rounds' elementwise steps --------------------------
+
+namespace {
+
+constexpr int kBoostThreads = 1024;
+
+// Sum over one CTA of kBoostThreads in a fixed order: per thread in stride
+// order (done by the caller), then a shuffle tree per warp, then warp 0 over
+// the warps' sums. Thread 0 returns the total.
+__device__ double boost_block_sum(double v) {
+  __shared__ double sh[kBoostThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = threadIdx.x < kBoostThreads / 32 ? sh[threadIdx.x] : 0.0;
+  if (threadIdx.x < 32)
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// base = (float)(mean of y), summed in double; F[i] = base.
+__global__ void __launch_bounds__(kBoostThreads)
+    k_boost_init(const float* __restrict__ y, int64_t n, float* F, float* base_out) {
+  __shared__ float s_base;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kBoostThreads) s += (double)y[i];
+  s = boost_block_sum(s);
+  if (threadIdx.x == 0) {
+    s_base = (float)(s / (double)n);
+    *base_out = s_base;
+  }
+  __syncthreads();
+  const float b = s_base;
+  for (int64_t i = threadIdx.x; i < n; i += kBoostThreads) F[i] = b;
+}
+
+// Mean over i of (y_i - F_i)^2 in double.
+__global__ void __launch_bounds__(kBoostThreads)
+    k_boost_mse(const float* __restrict__ y, const float* __restrict__ F, int64_t n,
+                double* out) {
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kBoostThreads) {
+    const double di = (double)y[i] - (double)F[i];
+    s += di * di;
+  }
+  s = boost_block_sum(s);
+  if (threadIdx.x == 0) *out = s / (double)n;
+}
+
+__global__ void k_boost_residual(const float* __restrict__ y, const float* __restrict__ F,
+                                 float* r, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = __fsub_rn(y[i], F[i]);
+}
+
+// F_i += eta * (float)v_i, one rounding per operation.
+__global__ void k_boost_update(float* F, const double* __restrict__ v, float eta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    F[i] = __fadd_rn(F[i], __fmul_rn(eta, (float)v[i]));
+}
+
+__global__ void k_fill_f(float* F, float v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    F[i] = v;
+}
+
+unsigned elementwise_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+cudaError_t launch_boost_init(const float* y, int64_t n, float* F, float* base_out,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  k_boost_init<<<1, kBoostThreads, 0, st>>>(y, n, F, base_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boost_mse(const float* y, const float* F, int64_t n, double* out,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  k_boost_mse<<<1, kBoostThreads, 0, st>>>(y, F, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boost_residual(const float* y, const float* F, float* r, int64_t n,
+                                  cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_boost_residual<<<elementwise_blocks(n), 256, 0, st>>>(y, F, r, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boost_update(float* F, const double* v, float eta, int64_t n,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_boost_update<<<elementwise_blocks(n), 256, 0, st>>>(F, v, eta, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f(float* F, float v, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_f<<<elementwise_blocks(n), 256, 0, st>>>(F, v, n);
+  return cudaGetLastError();
+}
+
 }  // namespace slm

@@ -155,6 +155,12 @@ SETTINGS = {
         builder=lambda seed=1: gmm(1_000_000, 256, 20, seed),
         criterion="gini", n_particles=64, n_iters=80, n_bins=128,
         max_depth=12, min_leaf=20, n_trees=1, proj="bf16", topk=8),
+    # SLR Boost: 10 rounds of depth-6 SLR trees fitted to the residuals of
+    # the regression target, learning rate 0.3
+    "boost_n200k_d128_r10": dict(
+        builder=lambda seed=1: tanh_regression(200_000, 128, 8, 0.1, seed),
+        criterion="mse", n_particles=64, n_iters=40, n_bins=256,
+        max_depth=6, min_leaf=20, n_trees=1, rounds=10, lr=0.3),
     # bagged forest of 64 trees; every level of all trees searched as one
     # graph-captured launch
     "forest64_n100k_d32_k5": dict(
