@@ -165,6 +165,12 @@ def lib():
             L.ora_train_boost.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                           C.c_void_p, C.c_int32, C.c_float, P(_Tree),
                                           P(C.c_float), C.c_void_p, C.c_void_p]
+            L.ora_train_boost_cls.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
+                                              C.c_void_p, C.c_int32, C.c_int32, C.c_float,
+                                              P(_Tree), C.c_void_p, C.c_void_p]
+            L.ora_boost_predict_cls.argtypes = [P(Params), P(_Tree), C.c_int32, C.c_int32,
+                                                C.c_float, C.c_void_p, C.c_int64, C.c_int32,
+                                                C.c_void_p, C.c_void_p]
             L.ora_boost_predict.argtypes = [P(Params), P(_Tree), C.c_int32, C.c_float,
                                             C.c_float, C.c_void_p, C.c_int64, C.c_int32,
                                             C.c_void_p]
@@ -444,6 +450,46 @@ def boost_predict(params: Params, boost: Boost, X) -> np.ndarray:
     if rc:
         raise ValueError(f"ora_boost_predict failed: {rc}")
     return out
+
+
+@dataclass
+class BoostCls:
+    trees: list            # [round * K + class]
+    n_classes: int
+    learning_rate: float
+    F: np.ndarray          # [n, K] final scores of the training rows
+    train_loss: np.ndarray  # mean cross-entropy after each round
+
+
+def train_boost_cls(params: Params, X, labels, n_classes, n_rounds, learning_rate) -> BoostCls:
+    """SLM Boost: K-class softmax gradient boosting with SLR trees."""
+    X, labels, _, _, _ = _node_arrays(X, labels, None, None, None)
+    n, d = X.shape
+    K = n_classes
+    trees = [_empty_tree(params.max_depth, d) for _ in range(n_rounds * K)]
+    arr = (_Tree * max(1, len(trees)))(*[t._cstruct() for t in trees])
+    F = np.empty((n, K), np.float32)
+    loss = np.empty(max(1, n_rounds), np.float64)
+    rc = lib().ora_train_boost_cls(C.byref(params), _ptr(X), n, d, _ptr(labels), K, n_rounds,
+                                   learning_rate, arr, _ptr(F), _ptr(loss))
+    if rc:
+        raise ValueError(f"ora_train_boost_cls failed: {rc}")
+    return BoostCls(trees, K, learning_rate, F, loss[:n_rounds])
+
+
+def boost_predict_cls(params: Params, boost: BoostCls, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, d = X.shape
+    K = boost.n_classes
+    M = len(boost.trees) // K
+    arr = (_Tree * max(1, len(boost.trees)))(*[t._cstruct() for t in boost.trees])
+    F = np.empty((n, K), np.float32)
+    cls = np.empty(n, np.int32)
+    rc = lib().ora_boost_predict_cls(C.byref(params), arr, M, K, boost.learning_rate,
+                                     _ptr(X), n, d, _ptr(F), _ptr(cls))
+    if rc:
+        raise ValueError(f"ora_boost_predict_cls failed: {rc}")
+    return F, cls
 
 
 def predict(params: Params, tree: Tree, X):

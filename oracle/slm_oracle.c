@@ -1344,6 +1344,101 @@ int ora_boost_predict(const ora_params* p, const ora_tree* trees, int32_t M, flo
   return rc;
 }
 
+/* SLM Boost: K-class softmax gradient boosting with least-squares trees. */
+
+/* Mean cross-entropy of F[n*K] against labels, in double. */
+static double boost_ce(const float* F, const int32_t* labels, int64_t n, int32_t K) {
+  double tot = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const float* f = F + i * K;
+    double mx = (double)f[0];
+    for (int32_t k = 1; k < K; ++k) mx = (double)f[k] > mx ? (double)f[k] : mx;
+    double s = 0.0;
+    for (int32_t k = 0; k < K; ++k) s += exp((double)f[k] - mx);
+    tot += -(((double)f[labels[i]] - mx) - log(s));
+  }
+  return tot / (double)n;
+}
+
+int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t d,
+                        const int32_t* labels, int32_t K, int32_t M, float eta,
+                        ora_tree* trees, float* F, double* loss_out) {
+  if (!p || n < 1 || d < 1 || !X || !labels || K < 2 || K > 64 || M < 0 ||
+      !(eta > 0.0f && eta <= 1.0f) || !F || (M > 0 && !trees))
+    return -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (labels[i] < 0 || labels[i] >= K) return -1;
+  float* R = (float*)malloc(sizeof(float) * (size_t)n * K);
+  double* v = (double*)malloc(sizeof(double) * (size_t)n);
+  double* e = (double*)malloc(sizeof(double) * (size_t)K);
+  int rc = 0;
+  if (!R || !v || !e) {
+    rc = -2;
+    goto done;
+  }
+  for (int64_t i = 0; i < n * K; ++i) F[i] = 0.0f;
+  ora_params q = *p;
+  q.criterion = ORA_MSE;
+  q.n_classes = 0;
+  for (int32_t m = 1; m <= M; ++m) {
+    /* residuals of the softmax, all classes from the same F */
+    for (int64_t i = 0; i < n; ++i) {
+      const float* f = F + i * K;
+      double mx = (double)f[0];
+      for (int32_t k = 1; k < K; ++k) mx = (double)f[k] > mx ? (double)f[k] : mx;
+      double s = 0.0;
+      for (int32_t k = 0; k < K; ++k) {
+        e[k] = exp((double)f[k] - mx);
+        s += e[k];
+      }
+      for (int32_t k = 0; k < K; ++k)
+        R[(int64_t)k * n + i] = (float)((labels[i] == k ? 1.0 : 0.0) - e[k] / s);
+    }
+    for (int32_t k = 0; k < K; ++k) {
+      ora_tree* t = &trees[(int64_t)(m - 1) * K + k];
+      q.seed = p->seed + (uint64_t)((m - 1) * K + k + 1);
+      rc = ora_train_tree(&q, X, n, d, NULL, R + (int64_t)k * n, 0, 0, t);
+      if (rc) goto done;
+      rc = ora_predict(&q, t, X, n, d, NULL, v, NULL);
+      if (rc) goto done;
+      for (int64_t i = 0; i < n; ++i) F[i * K + k] = F[i * K + k] + eta * (float)v[i];
+    }
+    if (loss_out) loss_out[m - 1] = boost_ce(F, labels, n, K);
+  }
+done:
+  free(R);
+  free(v);
+  free(e);
+  return rc;
+}
+
+int ora_boost_predict_cls(const ora_params* p, const ora_tree* trees, int32_t M, int32_t K,
+                          float eta, const float* X, int64_t n, int32_t d, float* F,
+                          int32_t* class_out) {
+  if (!p || M < 0 || K < 2 || (M > 0 && !trees) || !X || !F || n < 0 || d < 1) return -1;
+  double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!v) return -2;
+  ora_params q = *p;
+  q.criterion = ORA_MSE;
+  q.n_classes = 0;
+  int rc = 0;
+  for (int64_t i = 0; i < n * K; ++i) F[i] = 0.0f;
+  for (int32_t m = 0; m < M && !rc; ++m)
+    for (int32_t k = 0; k < K && !rc; ++k) {
+      rc = ora_predict(&q, &trees[(int64_t)m * K + k], X, n, d, NULL, v, NULL);
+      for (int64_t i = 0; i < n && !rc; ++i) F[i * K + k] = F[i * K + k] + eta * (float)v[i];
+    }
+  if (class_out && !rc)
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t b = 0;
+      for (int32_t k = 1; k < K; ++k)
+        if (F[i * K + k] > F[i * K + b]) b = k;
+      class_out[i] = b;
+    }
+  free(v);
+  return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Learned swarm proposal: node statistics, a 3-layer network, its loss and  */
 /* gradient, Adam, and the seeded initial swarm. Written from the            */

@@ -319,6 +319,26 @@ int ora_train_boost(const ora_params* p, const float* X, int64_t n, int32_t d, c
 int ora_boost_predict(const ora_params* p, const ora_tree* trees, int32_t M, float base,
                       float eta, const float* X, int64_t n, int32_t d, float* out);
 
+/* SLM Boost (Sec. V: the boosting ensemble of SLM trees), read as K-class
+ * gradient boosting of the softmax cross-entropy with least-squares SLR
+ * trees: F[i*K + k] = 0; round m = 1..M: in double, p_ik = exp(F_ik - max_j
+ * F_ij) / (sum over j ascending of exp(F_ij - max_j F_ij)), and r_ik =
+ * (float)([labels_i == k] - p_ik); then for k = 0..K-1 tree (m-1)*K + k is
+ * grown by ora_train_tree (criterion ORA_MSE) on (X, r_.k) with the Philox
+ * key seed + (m-1)*K + k + 1 (tree id 0, no bootstrap), and F_ik = F_ik + eta
+ * * (float)v_ik (float). loss_out[m-1] (may be NULL): mean over i of
+ * -log p_{i,labels_i} after round m, in double (log-sum-exp form).
+ * trees[M*K] caller-allocated; p's criterion is ignored (trees use MSE). */
+int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t d,
+                        const int32_t* labels, int32_t K, int32_t M, float eta,
+                        ora_tree* trees, float* F, double* loss_out);
+
+/* F[i*K + k] = 0 plus the rounds' eta * (float)v in round order; class_out[i]
+ * = argmax over k of F_ik, ties to the lower class (either may be NULL). */
+int ora_boost_predict_cls(const ora_params* p, const ora_tree* trees, int32_t M, int32_t K,
+                          float eta, const float* X, int64_t n, int32_t d, float* F,
+                          int32_t* class_out);
+
 /* Route samples through a tree grown by ora_train_tree. */
 int ora_predict(const ora_params* p, const ora_tree* tree, const float* X,
                 int64_t n, int32_t d, int32_t* class_out, double* value_out,

@@ -12,6 +12,14 @@ trees; the rule is least-squares gradient boosting on residuals).
 * each round rebuilt from its definition: the residuals y - F in float and a
   tree grown with the key seed + m give that round's tree;
 * bad arguments are refused.
+
+SLM Boost (K-class softmax gradient boosting with least-squares SLR trees):
+* closed form on separable classes (K = 2 and 3): every sample keeps the
+  same margin g, which grows by eta (1 - p) K / (K - 1), and the loss is
+  log(1 + (K - 1) e^-g) (after the first round log(1 + (K - 1) e^-eta));
+* on a mixture the loss falls every round, the reported loss is the mean
+  cross-entropy of the returned scores, prediction reproduces them and the
+  class is their argmax; bad arguments are refused.
 """
 import numpy as np
 import pytest
@@ -88,3 +96,65 @@ def test_bad_arguments():
     for eta in (0.0, -0.1, 1.5):
         with pytest.raises(ValueError):
             O.train_boost(O.make_params("mse", 0, 8, 2, 16), X, y, 2, eta)
+
+
+# ---- SLM Boost (K-class softmax gradient boosting with least-squares trees) ----
+
+def clusters(K, n=2400, seed=2):
+    """K classes in separated intervals of feature 0 (gaps of width 1), and a
+    noise feature: trees of depth >= ceil(log2 K) fit every residual exactly."""
+    rng = np.random.default_rng(seed)
+    lab = rng.integers(0, K, n).astype(np.int32)
+    x0 = 3.0 * lab + 2.0 * rng.random(n)
+    X = np.stack([x0, rng.standard_normal(n)], 1).astype(np.float32)
+    return X, lab
+
+
+@pytest.mark.parametrize("K,depth", [(2, 1), (3, 2)])
+@pytest.mark.parametrize("eta", [1.0, 0.5])
+def test_cls_separable_closed_form(K, depth, eta):
+    # every round's trees predict the residuals exactly, and by symmetry every
+    # sample has the same margin g = F_true - F_other: the softmax gives
+    # p = e^g / (e^g + K - 1), the true class gains eta (1 - p), each other
+    # class loses eta (1 - p) / (K - 1), so g grows by eta (1 - p) K / (K - 1)
+    # and the cross-entropy is log(1 + (K - 1) e^-g)
+    X, lab = clusters(K)
+    p = O.make_params("mse", 0, 16, 10, 32, min_leaf=5, max_depth=depth)
+    b = O.train_boost_cls(p, X, lab, K, 4, eta)
+    g, want = 0.0, []
+    for _ in range(4):
+        pm = np.exp(g) / (np.exp(g) + K - 1)
+        g += eta * (1 - pm) * K / (K - 1)
+        want.append(np.log1p((K - 1) * np.exp(-g)))
+    assert np.allclose(b.train_loss, want, rtol=1e-6)
+    assert b.train_loss[0] == pytest.approx(np.log1p((K - 1) * np.exp(-eta)), rel=1e-6)
+    F, cls = O.boost_predict_cls(p, b, X)
+    assert np.array_equal(F, b.F) and np.array_equal(cls, lab)
+
+
+def test_cls_boosting_on_mixture():
+    wl = W.gmm(3000, 6, 4, seed=5)
+    p = O.make_params("mse", 0, 16, 10, 32, min_leaf=10, max_depth=3, seed=4)
+    b = O.train_boost_cls(p, wl.X, wl.labels, 4, 6, 0.3)
+    assert np.all(np.diff(b.train_loss) <= 0)
+    assert b.train_loss[0] < np.log(4)
+    F, cls = O.boost_predict_cls(p, b, wl.X)
+    assert np.array_equal(F, b.F)
+    assert np.array_equal(cls, np.argmax(F, axis=1))
+    assert np.mean(cls == wl.labels) > 0.5
+    # the reported loss is the mean cross-entropy of the returned scores
+    Fd = b.F.astype(np.float64)
+    lse = Fd.max(1) + np.log(np.exp(Fd - Fd.max(1, keepdims=True)).sum(1))
+    ce = np.mean(lse - Fd[np.arange(len(wl.labels)), wl.labels])
+    assert b.train_loss[-1] == pytest.approx(ce, rel=1e-12)
+
+
+def test_cls_bad_arguments():
+    X, lab = clusters(3, 200)
+    p = O.make_params("mse", 0, 8, 2, 16)
+    with pytest.raises(ValueError):
+        O.train_boost_cls(p, X, lab, 2, 2, 0.5)     # a label out of range
+    with pytest.raises(ValueError):
+        O.train_boost_cls(p, X, lab * 0, 1, 2, 0.5)  # K < 2
+    with pytest.raises(ValueError):
+        O.train_boost_cls(p, X, lab, 3, 2, 0.0)
