@@ -102,9 +102,10 @@ def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
     if cfg.get("apso"):
         d["swarm"] = "adaptive PSO (evolutionary-state estimation)"
     if cfg.get("rounds"):
+        kind = "SLR Boost" if wl.labels is None else "SLM Boost (%d trees a round)" % wl.n_classes
         d["boost"] = {"rounds": cfg["rounds"], "learning_rate": cfg["lr"],
-                      "step": "one SLR Boost training: every round's tree, residuals, "
-                              "predictions and F updates"}
+                      "step": "one %s training: every round's trees, residuals, "
+                              "predictions and score updates" % kind}
     if args_launch is not None:
         d["search_loop_graphs"] = args_launch.graphs
         d["projection_tile_mode"] = args_launch.tiles
@@ -182,13 +183,25 @@ def oracle_params(cfg, wl, proj, topk, iters):
                          topk=topk if proj == "bf16" else 0, top_n=cfg.get("top_n", 0))
 
 
+def oracle_targets(cfg, wl):
+    """(labels, y) of a root search of the workload: a boosting run's first
+    root search fits residuals (y minus its mean; for classes, class 0's
+    one-hot minus 1/K)."""
+    if not cfg.get("rounds"):
+        return wl.labels, wl.y
+    if wl.labels is None:
+        return None, (wl.y - np.float32(np.mean(wl.y.astype(np.float64)))).astype(np.float32)
+    K = wl.n_classes
+    return None, ((wl.labels == 0).astype(np.float64) - 1.0 / K).astype(np.float32)
+
+
 def oracle_root_sample(cfg, wl, proj, topk, iters):
     """Times the CPU oracle's swarm search of the root node (all n samples)
     with `iters` iterations; returns (evals/s, seconds, evaluations)."""
     import oracle as O
     p = oracle_params(cfg, wl, proj, topk, iters)
     t0 = time.perf_counter()
-    O.node_split(p, wl.X, wl.labels, wl.y, node_uid=0)
+    O.node_split(p, wl.X, *oracle_targets(cfg, wl), node_uid=0)
     dt = time.perf_counter() - t0
     evals = wl.n * cfg["n_particles"] * (iters + 1)
     return evals / dt, dt, evals
@@ -210,7 +223,7 @@ def cpu_baseline(cfg, wl, proj, topk):
     secs, reps = 0.0, 0
     while reps < 30 and (reps == 0 or secs < CPU_SAMPLE_S):
         t0 = time.perf_counter()
-        O.node_split(p, wl.X, wl.labels, wl.y, node_uid=reps)
+        O.node_split(p, wl.X, *oracle_targets(cfg, wl), node_uid=reps)
         secs += time.perf_counter() - t0
         reps += 1
     ev = wl.n * cfg["n_particles"] * (iters + 1) * reps
@@ -336,16 +349,23 @@ class BoostRun:
 def train_step(ctx, p, cfg, X, L, Y):
     """One step of the workload: a tree / forest, or a boosting run."""
     if cfg.get("rounds"):
-        return BoostRun(ctx.train_boost(p, X, Y, cfg["rounds"], cfg["lr"]))
+        return BoostRun(ctx.train_boost(p, X, y=Y, labels=L, n_rounds=cfg["rounds"],
+                                        learning_rate=cfg["lr"], n_classes=cfg.get("classes")))
     return ctx.train_tree(p, X, labels=L, y=Y)
 
 
 def step_loss(ctx, f, wl, X):
     if isinstance(f, BoostRun):
-        mse = f.b.train_mse
-        y = wl.y.astype(np.float64)
-        return {"boost_train_mse": float(mse[-1]), "mse_of_mean": float(np.var(y)),
-                "train_mse_by_round": [round(float(v), 6) for v in mse]}
+        loss = f.b.train_loss
+        by_round = [round(float(v), 6) for v in loss]
+        if wl.labels is None:
+            y = wl.y.astype(np.float64)
+            return {"boost_train_mse": float(loss[-1]), "mse_of_mean": float(np.var(y)),
+                    "train_mse_by_round": by_round}
+        _, cls = f.b.predict(X, want_class=True)
+        return {"boost_train_cross_entropy": float(loss[-1]),
+                "cross_entropy_by_round": by_round,
+                "train_error": float(np.mean(cls != wl.labels))}
     return tree_loss(ctx, f, wl, X)
 
 

@@ -288,37 +288,49 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
                        double* value_out, int32_t* leaf_out);
 
 
-/* ---- SLR Boost -----------------------------------------------------------
- * The boosting ensemble of SLR trees (Sec. V names SLR Boost beside SLR
- * Forest), read as least-squares gradient boosting on residuals, in float:
+/* ---- SLR / SLM Boost -----------------------------------------------------
+ * The boosting ensembles of SLR and SLM trees (Sec. V names SLR Boost and SLM
+ * Boost beside the forests), read as gradient boosting with least-squares
+ * SLR trees on residuals, in float. Regression (y):
  *   base = (float)(mean of y, summed in double);  F_i = base;
  *   round m = 1..n_rounds: r_i = y_i - F_i; one SLR tree grown on (X, r)
  *   with `params` and the Philox key params->seed + m (tree id 0);
  *   F_i = F_i + learning_rate * (float)v_i, v_i the tree's leaf value of x_i.
+ * Classification (labels, K = params->n_classes classes): F_ik = 0; round m:
+ *   in double p_ik = exp(F_ik - max_j F_ij) / sum_j (ascending) of the same,
+ *   r_ik = (float)([labels_i == k] - p_ik) (all k from the same F); for
+ *   k = 0..K-1 one SLR tree on (X, r_.k) with the key params->seed +
+ *   (m-1) K + k + 1, and F_ik = F_ik + learning_rate * (float)v_ik.
  * Each float operation is rounded once. */
 typedef struct slm_boost slm_boost;
 
-/* Trains n_rounds >= 0 rounds on X[n*d] and y[n] (host or device; the call
- * copies host inputs). params: criterion SLM_MSE, n_trees 1, bootstrap 0
- * (SLM_EINVAL / SLM_EUNSUPPORTED otherwise); 0 < learning_rate <= 1.
- * train_mse_out[n_rounds] (host, may be NULL): mean of (y - F)^2 in double
- * after each round. On success *out owns the trees (slm_boost_free). */
+/* Trains n_rounds >= 0 rounds on X[n*d] and exactly one of labels[n] (values
+ * in [0, K), 2 <= K <= 32) and y[n] (host or device; host inputs are
+ * copied). params: criterion SLM_MSE (the trees fit residuals), n_trees 1,
+ * bootstrap 0 (SLM_EINVAL / SLM_EUNSUPPORTED otherwise); 0 < learning_rate
+ * <= 1. train_loss_out[n_rounds] (host or device, may be NULL): after each
+ * round, in double, the mean of (y - F)^2, or the mean cross-entropy
+ * -log p_{i, labels_i} (log-sum-exp form). On success *out owns the trees
+ * (slm_boost_free). */
 slm_status slm_train_boost(slm_ctx* ctx, const slm_params* params, const float* X,
-                           int64_t n, int32_t d, const float* y, int32_t n_rounds,
-                           float learning_rate, double* train_mse_out,
+                           int64_t n, int32_t d, const int32_t* labels, const float* y,
+                           int32_t n_rounds, float learning_rate, double* train_loss_out,
                            slm_boost** out);
-/* value_out[n] (host or device): base plus the rounds' learning_rate *
- * (float) leaf values, added in round order (the training F for the
- * training rows). */
+/* value_out[n * n_outputs] (may be NULL): the scores F (base for regression,
+ * 0 for classification, plus the rounds' learning_rate * (float) leaf values
+ * in round order: the training F for the training rows); class_out[n]
+ * (classification, may be NULL): argmax over k of F_ik, ties to the lower
+ * class. Host or device pointers. */
 slm_status slm_boost_predict(slm_ctx* ctx, const slm_boost* boost, const float* X,
-                             int64_t n, int32_t d, float* value_out);
-/* Rounds, base and learning rate; any pointer may be NULL. */
-slm_status slm_boost_info(const slm_boost* boost, int32_t* n_rounds, float* base,
-                          float* learning_rate);
-/* The tree of round m + 1 (0 <= m < n_rounds), owned by the boost (read it
- * with slm_forest_export / slm_predict; do not free it); NULL if out of
- * range. */
-const slm_forest* slm_boost_tree(const slm_boost* boost, int32_t m);
+                             int64_t n, int32_t d, float* value_out, int32_t* class_out);
+/* Rounds, outputs (1 or K), base (regression) and learning rate; any
+ * pointer may be NULL. */
+slm_status slm_boost_info(const slm_boost* boost, int32_t* n_rounds, int32_t* n_outputs,
+                          float* base, float* learning_rate);
+/* Tree t = m * n_outputs + k (round m + 1, output k), owned by the boost
+ * (read it with slm_forest_export / slm_predict; do not free it); NULL if t
+ * is out of range. */
+const slm_forest* slm_boost_tree(const slm_boost* boost, int32_t t);
 void slm_boost_free(slm_boost* boost);
 
 /* ---- learned swarm proposal ----------------------------------------------

@@ -165,6 +165,9 @@ def lib():
             L.ora_train_boost.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                           C.c_void_p, C.c_int32, C.c_float, P(_Tree),
                                           P(C.c_float), C.c_void_p, C.c_void_p]
+            L.ora_softmax_residuals.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                                C.c_void_p]
+            L.ora_softmax_residuals.restype = None
             L.ora_train_boost_cls.argtypes = [P(Params), C.c_void_p, C.c_int64, C.c_int32,
                                               C.c_void_p, C.c_int32, C.c_int32, C.c_float,
                                               P(_Tree), C.c_void_p, C.c_void_p]
@@ -475,6 +478,16 @@ def train_boost_cls(params: Params, X, labels, n_classes, n_rounds, learning_rat
     if rc:
         raise ValueError(f"ora_train_boost_cls failed: {rc}")
     return BoostCls(trees, K, learning_rate, F, loss[:n_rounds])
+
+
+def softmax_residuals(F, labels, n_classes) -> np.ndarray:
+    """One round's residuals R[k, i] of the scores F[n, K]."""
+    F = np.ascontiguousarray(F, dtype=np.float32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    n = labels.size
+    R = np.empty((n_classes, n), np.float32)
+    lib().ora_softmax_residuals(_ptr(F), _ptr(labels), n, n_classes, _ptr(R))
+    return R
 
 
 def boost_predict_cls(params: Params, boost: BoostCls, X):

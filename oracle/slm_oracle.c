@@ -1360,6 +1360,19 @@ static double boost_ce(const float* F, const int32_t* labels, int64_t n, int32_t
   return tot / (double)n;
 }
 
+void ora_softmax_residuals(const float* F, const int32_t* labels, int64_t n, int32_t K,
+                           float* R) {
+  for (int64_t i = 0; i < n; ++i) {
+    const float* f = F + i * K;
+    double mx = (double)f[0];
+    for (int32_t k = 1; k < K; ++k) mx = (double)f[k] > mx ? (double)f[k] : mx;
+    double s = 0.0;
+    for (int32_t k = 0; k < K; ++k) s += exp((double)f[k] - mx);
+    for (int32_t k = 0; k < K; ++k)
+      R[(int64_t)k * n + i] = (float)((labels[i] == k ? 1.0 : 0.0) - exp((double)f[k] - mx) / s);
+  }
+}
+
 int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t d,
                         const int32_t* labels, int32_t K, int32_t M, float eta,
                         ora_tree* trees, float* F, double* loss_out) {
@@ -1370,9 +1383,8 @@ int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t 
     if (labels[i] < 0 || labels[i] >= K) return -1;
   float* R = (float*)malloc(sizeof(float) * (size_t)n * K);
   double* v = (double*)malloc(sizeof(double) * (size_t)n);
-  double* e = (double*)malloc(sizeof(double) * (size_t)K);
   int rc = 0;
-  if (!R || !v || !e) {
+  if (!R || !v) {
     rc = -2;
     goto done;
   }
@@ -1382,18 +1394,7 @@ int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t 
   q.n_classes = 0;
   for (int32_t m = 1; m <= M; ++m) {
     /* residuals of the softmax, all classes from the same F */
-    for (int64_t i = 0; i < n; ++i) {
-      const float* f = F + i * K;
-      double mx = (double)f[0];
-      for (int32_t k = 1; k < K; ++k) mx = (double)f[k] > mx ? (double)f[k] : mx;
-      double s = 0.0;
-      for (int32_t k = 0; k < K; ++k) {
-        e[k] = exp((double)f[k] - mx);
-        s += e[k];
-      }
-      for (int32_t k = 0; k < K; ++k)
-        R[(int64_t)k * n + i] = (float)((labels[i] == k ? 1.0 : 0.0) - e[k] / s);
-    }
+    ora_softmax_residuals(F, labels, n, K, R);
     for (int32_t k = 0; k < K; ++k) {
       ora_tree* t = &trees[(int64_t)(m - 1) * K + k];
       q.seed = p->seed + (uint64_t)((m - 1) * K + k + 1);
@@ -1408,7 +1409,6 @@ int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t 
 done:
   free(R);
   free(v);
-  free(e);
   return rc;
 }
 

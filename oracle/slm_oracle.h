@@ -329,6 +329,8 @@ int ora_boost_predict(const ora_params* p, const ora_tree* trees, int32_t M, flo
  * * (float)v_ik (float). loss_out[m-1] (may be NULL): mean over i of
  * -log p_{i,labels_i} after round m, in double (log-sum-exp form).
  * trees[M*K] caller-allocated; p's criterion is ignored (trees use MSE). */
+void ora_softmax_residuals(const float* F, const int32_t* labels, int64_t n, int32_t K,
+                           float* R);  /* R[k*n + i], the residuals of one round */
 int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t d,
                         const int32_t* labels, int32_t K, int32_t M, float eta,
                         ora_tree* trees, float* F, double* loss_out);

@@ -118,10 +118,10 @@ def lib():
                                    C.c_int),
             "slm_use_proposal": ([vp, vp], C.c_int),
             "slm_swarm_seed": ([vp, u64, u32, i32, i32, vp, vp, vp], C.c_int),
-            "slm_train_boost": ([vp, P(slm_params), vp, i64, i32, vp, i32, C.c_float, vp,
-                                 P(vp)], C.c_int),
-            "slm_boost_predict": ([vp, vp, vp, i64, i32, vp], C.c_int),
-            "slm_boost_info": ([vp, P(i32), P(C.c_float), P(C.c_float)], C.c_int),
+            "slm_train_boost": ([vp, P(slm_params), vp, i64, i32, vp, vp, i32, C.c_float,
+                                 vp, P(vp)], C.c_int),
+            "slm_boost_predict": ([vp, vp, vp, i64, i32, vp, vp], C.c_int),
+            "slm_boost_info": ([vp, P(i32), P(i32), P(C.c_float), P(C.c_float)], C.c_int),
             "slm_boost_tree": ([vp, i32], vp),
             "slm_boost_free": ([vp], None),
         }
@@ -219,30 +219,38 @@ class _RoundTree(Forest):
 
 
 class Boost:
-    """SLR Boost: trees fitted to residuals, owned by the library."""
+    """SLR / SLM Boost: trees fitted to residuals, owned by the library.
+    train_loss: training MSE (regression) or cross-entropy after each round."""
 
-    def __init__(self, ctx: "Context", handle, train_mse):
+    def __init__(self, ctx: "Context", handle, train_loss):
         self.ctx, self.handle = ctx, C.c_void_p(handle)
-        self.train_mse = train_mse
+        self.train_loss = train_loss
+        self.train_mse = train_loss
 
     def info(self) -> dict:
-        m, b, lr = C.c_int32(), C.c_float(), C.c_float()
-        self.ctx._check(lib().slm_boost_info(self.handle, C.byref(m), C.byref(b), C.byref(lr)))
-        return {"n_rounds": m.value, "base": b.value, "learning_rate": lr.value}
+        m, k, b, lr = C.c_int32(), C.c_int32(), C.c_float(), C.c_float()
+        self.ctx._check(lib().slm_boost_info(self.handle, C.byref(m), C.byref(k), C.byref(b),
+                                             C.byref(lr)))
+        return {"n_rounds": m.value, "n_outputs": k.value, "base": b.value,
+                "learning_rate": lr.value}
 
-    def tree(self, m: int) -> Forest:
-        h = lib().slm_boost_tree(self.handle, m)
+    def tree(self, t: int) -> Forest:
+        """Tree t = round * n_outputs + output."""
+        h = lib().slm_boost_tree(self.handle, t)
         if not h:
-            raise IndexError(m)
+            raise IndexError(t)
         return _RoundTree(self.ctx, h, self)
 
-    def predict(self, X) -> np.ndarray:
+    def predict(self, X, want_class=False):
+        """Scores [n] (regression) or [n, K]; with want_class also the argmax."""
         X = _as(X, np.float32)
         n, d = X.shape
-        out = np.empty(n, np.float32)
+        K = self.info()["n_outputs"]
+        out = np.empty((n, K) if K > 1 else n, np.float32)
+        cls = np.empty(n, np.int32) if want_class else None
         self.ctx._check(lib().slm_boost_predict(self.ctx.handle, self.handle, _ptr(X), n, d,
-                                                _ptr(out)))
-        return out
+                                                _ptr(out), _ptr(cls)))
+        return (out, cls) if want_class else out
 
     def free(self):
         if self.handle:
@@ -509,14 +517,24 @@ class Context:
                                          _ptr(labels), _ptr(y), C.byref(h)))
         return Forest(self, h.value)
 
-    def train_boost(self, params, X, y, n_rounds: int, learning_rate: float) -> Boost:
-        X, y = _as(X, np.float32), _as(y, np.float32)
+    def train_boost(self, params, X, y=None, n_rounds: int = 10, learning_rate: float = 0.3,
+                    labels=None, n_classes=None) -> Boost:
+        """SLR Boost (y) or SLM Boost (labels; n_classes, else params.n_classes
+        when >= 2, else the largest label + 1)."""
+        X, y, labels = _as(X, np.float32), _as(y, np.float32), _as(labels, np.int32)
         n, d = X.shape
-        mse = np.empty(max(1, n_rounds), np.float64)
+        if labels is not None:
+            params = slm_params.from_buffer_copy(params)
+            if n_classes is None:
+                n_classes = (params.n_classes if params.n_classes >= 2
+                             else int(labels.max()) + 1)
+            params.n_classes = n_classes
+        loss = np.empty(max(1, n_rounds), np.float64)
         h = C.c_void_p()
-        self._check(lib().slm_train_boost(self.handle, C.byref(params), _ptr(X), n, d, _ptr(y),
-                                          n_rounds, learning_rate, _ptr(mse), C.byref(h)))
-        return Boost(self, h.value, mse[:n_rounds])
+        self._check(lib().slm_train_boost(self.handle, C.byref(params), _ptr(X), n, d,
+                                          _ptr(labels), _ptr(y), n_rounds, learning_rate,
+                                          _ptr(loss), C.byref(h)))
+        return Boost(self, h.value, loss[:n_rounds])
 
     def predict(self, forest: Forest, X, want_leaf=False):
         X = _as(X, np.float32)

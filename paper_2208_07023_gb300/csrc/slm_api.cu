@@ -2156,9 +2156,10 @@ struct slm_boost {
   int device = 0;
   slm_params params{};
   int d = 0;
+  int K = 1;  // outputs: 1 (regression on y) or the classes (labels)
   float base = 0.0f;
   float eta = 0.0f;
-  std::vector<slm_forest*> trees;
+  std::vector<slm_forest*> trees;  // round-major: tree (m, k) at m * K + k
 };
 
 }  // extern "C"
@@ -2185,9 +2186,9 @@ void release_level_state(slm_forest* f) {
 
 // Device buffers of one boosting call, released on every exit.
 struct BoostWork {
-  DevBuf X, y, F, r, v, mse, base;
+  DevBuf X, y, lab, F, r, v, loss, base;
   ~BoostWork() {
-    for (DevBuf* b : {&X, &y, &F, &r, &v, &mse, &base}) release(*b);
+    for (DevBuf* b : {&X, &y, &lab, &F, &r, &v, &loss, &base}) release(*b);
   }
 };
 
@@ -2208,12 +2209,16 @@ slm_status own_copy(slm_ctx* c, const T* src, size_t count, DevBuf& buf, const T
 extern "C" {
 
 slm_status slm_train_boost(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
-                           int32_t d, const float* y, int32_t n_rounds, float learning_rate,
-                           double* train_mse_out, slm_boost** out) {
-  if (!c || !p || !X || !y || !out || n < 1 || d < 1 || n_rounds < 0)
-    return fail(c, SLM_EINVAL, "bad arguments to slm_train_boost");
+                           int32_t d, const int32_t* labels, const float* y, int32_t n_rounds,
+                           float learning_rate, double* train_loss_out, slm_boost** out) {
+  if (!c || !p || !X || !out || n < 1 || d < 1 || n_rounds < 0 || (!labels == !y))
+    return fail(c, SLM_EINVAL, "bad arguments to slm_train_boost (exactly one of labels, y)");
   *out = nullptr;
-  if (p->criterion != SLM_MSE) return fail(c, SLM_EINVAL, "boosting fits residuals: SLM_MSE");
+  if (p->criterion != SLM_MSE)
+    return fail(c, SLM_EINVAL, "boosting trees fit residuals: criterion SLM_MSE");
+  const int K = labels ? p->n_classes : 1;
+  if (labels && (K < 2 || K > kMaxClasses))
+    return fail(c, SLM_EINVAL, "classification boosting needs 2 <= n_classes <= 32");
   if (!(learning_rate > 0.0f && learning_rate <= 1.0f))
     return fail(c, SLM_EINVAL, "learning_rate must be in (0, 1]");
   if (p->n_trees != 1 || p->bootstrap)
@@ -2221,49 +2226,75 @@ slm_status slm_train_boost(slm_ctx* c, const slm_params* p, const float* X, int6
   CK(cudaSetDevice(c->device));
   BoostWork w;
   const float* dX;
-  const float* dy;
+  const float* dy = nullptr;
+  const int32_t* dl = nullptr;
   if (slm_status s = own_copy(c, X, (size_t)n * d, w.X, &dX)) return s;
-  if (slm_status s = own_copy(c, y, (size_t)n, w.y, &dy)) return s;
-  CK(ensure(w.F, sizeof(float) * (size_t)n));
-  CK(ensure(w.r, sizeof(float) * (size_t)n));
+  if (y) {
+    if (slm_status s = own_copy(c, y, (size_t)n, w.y, &dy)) return s;
+  } else {
+    if (slm_status s = own_copy(c, labels, (size_t)n, w.lab, &dl)) return s;
+    if (slm_status s = validate_inputs(c, dl, n, K, nullptr, 0)) return s;
+  }
+  CK(ensure(w.F, sizeof(float) * (size_t)n * K));
+  CK(ensure(w.r, sizeof(float) * (size_t)n * K));
   CK(ensure(w.v, sizeof(double) * (size_t)n));
-  CK(ensure(w.mse, sizeof(double) * (size_t)(n_rounds > 0 ? n_rounds : 1)));
+  CK(ensure(w.loss, sizeof(double) * (size_t)(n_rounds > 0 ? n_rounds : 1)));
   CK(ensure(w.base, sizeof(float)));
   float* F = static_cast<float*>(w.F.p);
   float* r = static_cast<float*>(w.r.p);
   double* v = static_cast<double*>(w.v.p);
-  double* mse = static_cast<double*>(w.mse.p);
-  CK(launch(c, SLM_K_OTHER, 0.0, [&] {
-    return launch_boost_init(dy, n, F, static_cast<float*>(w.base.p), c->stream);
-  }));
+  double* loss = static_cast<double*>(w.loss.p);
+  if (y)
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+      return launch_boost_init(dy, n, F, static_cast<float*>(w.base.p), c->stream);
+    }));
+  else
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_fill_f(F, 0.0f, n * K, c->stream); }));
   std::unique_ptr<slm_boost, void (*)(slm_boost*)> b(new (std::nothrow) slm_boost,
                                                      slm_boost_free);
   if (!b) return fail(c, SLM_ENOMEM, "boost handle");
   b->device = c->device;
   b->params = *p;
+  b->params.n_classes = 0;
   b->d = d;
+  b->K = K;
   b->eta = learning_rate;
   for (int32_t m = 1; m <= n_rounds; ++m) {
-    CK(launch(c, SLM_K_OTHER, 0.0,
-              [&] { return launch_boost_residual(dy, F, r, n, c->stream); }));
-    slm_params q = *p;
-    q.seed = p->seed + (uint64_t)m;
-    slm_forest* f = nullptr;
-    if (slm_status s = slm_train_tree(c, &q, dX, n, d, nullptr, r, &f)) return s;
-    b->trees.push_back(f);
-    release_level_state(f);
-    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
-      return launch_predict(dX, n, d, f->tr, 1, f->H, q.n_bins, 1, SLM_MSE, nullptr, v,
-                            nullptr, c->stream);
-    }));
-    CK(launch(c, SLM_K_OTHER, 0.0,
-              [&] { return launch_boost_update(F, v, learning_rate, n, c->stream); }));
-    CK(launch(c, SLM_K_OTHER, 0.0,
-              [&] { return launch_boost_mse(dy, F, n, mse + (m - 1), c->stream); }));
+    // residuals of every output from the same F
+    if (y)
+      CK(launch(c, SLM_K_OTHER, 0.0,
+                [&] { return launch_boost_residual(dy, F, r, n, c->stream); }));
+    else
+      CK(launch(c, SLM_K_OTHER, 0.0,
+                [&] { return launch_softmax_residual(F, dl, n, K, r, c->stream); }));
+    for (int k = 0; k < K; ++k) {
+      slm_params q = b->params;
+      q.seed = p->seed + (uint64_t)((m - 1) * K + k + 1);
+      slm_forest* f = nullptr;
+      if (slm_status s = slm_train_tree(c, &q, dX, n, d, nullptr, r + (int64_t)k * n, &f))
+        return s;
+      b->trees.push_back(f);
+      release_level_state(f);
+      CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+        return launch_predict(dX, n, d, f->tr, 1, f->H, q.n_bins, 1, SLM_MSE, nullptr, v,
+                              nullptr, c->stream);
+      }));
+      CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+        return launch_boost_update(F, v, learning_rate, n, c->stream, K, k);
+      }));
+    }
+    if (y)
+      CK(launch(c, SLM_K_OTHER, 0.0,
+                [&] { return launch_boost_mse(dy, F, n, loss + (m - 1), c->stream); }));
+    else
+      CK(launch(c, SLM_K_OTHER, 0.0,
+                [&] { return launch_boost_ce(F, dl, n, K, loss + (m - 1), c->stream); }));
   }
-  CK(cudaMemcpyAsync(&b->base, w.base.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-  if (train_mse_out && n_rounds > 0)
-    CK(cudaMemcpyAsync(train_mse_out, mse, sizeof(double) * n_rounds, cudaMemcpyDefault,
+  if (y)
+    CK(cudaMemcpyAsync(&b->base, w.base.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (train_loss_out && n_rounds > 0)
+    CK(cudaMemcpyAsync(train_loss_out, loss, sizeof(double) * n_rounds, cudaMemcpyDefault,
                        c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (slm_status s = check_kernel_errors(c)) return s;
@@ -2272,38 +2303,54 @@ slm_status slm_train_boost(slm_ctx* c, const slm_params* p, const float* X, int6
 }
 
 slm_status slm_boost_predict(slm_ctx* c, const slm_boost* b, const float* X, int64_t n,
-                             int32_t d, float* value_out) {
-  if (!c || !b || !X || !value_out || n < 0 || d != b->d)
+                             int32_t d, float* value_out, int32_t* class_out) {
+  if (!c || !b || !X || (!value_out && !class_out) || n < 0 || d != b->d ||
+      (class_out && b->K < 2))
     return fail(c, SLM_EINVAL, "bad arguments to slm_boost_predict");
   if (n == 0) return SLM_OK;
   CK(cudaSetDevice(c->device));
   const float* dX;
   if (slm_status s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX)) return s;
+  const int K = b->K;
   const size_t off_f = (sizeof(double) * (size_t)n + 15) & ~size_t(15);
-  CK(ensure(c->ws[S_OUT], off_f + sizeof(float) * (size_t)n));
+  const size_t off_c = (off_f + sizeof(float) * (size_t)n * K + 15) & ~size_t(15);
+  CK(ensure(c->ws[S_OUT], off_c + sizeof(int32_t) * (size_t)n));
   unsigned char* base = static_cast<unsigned char*>(c->ws[S_OUT].p);
   double* v = reinterpret_cast<double*>(base);
-  float* F = is_device_ptr(value_out) ? value_out : reinterpret_cast<float*>(base + off_f);
-  CK(launch(c, SLM_K_OTHER, 0.0, [&] { return launch_fill_f(F, b->base, n, c->stream); }));
-  for (const slm_forest* f : b->trees) {
+  float* F = value_out && is_device_ptr(value_out) ? value_out
+                                                   : reinterpret_cast<float*>(base + off_f);
+  int32_t* cls = class_out && is_device_ptr(class_out)
+                     ? class_out
+                     : reinterpret_cast<int32_t*>(base + off_c);
+  CK(launch(c, SLM_K_OTHER, 0.0,
+            [&] { return launch_fill_f(F, K == 1 ? b->base : 0.0f, n * K, c->stream); }));
+  for (size_t t = 0; t < b->trees.size(); ++t) {
+    const slm_forest* f = b->trees[t];
     CK(launch(c, SLM_K_OTHER, 0.0, [&] {
       return launch_predict(dX, n, d, f->tr, 1, f->H, b->params.n_bins, 1, SLM_MSE, nullptr,
                             v, nullptr, c->stream);
     }));
-    CK(launch(c, SLM_K_OTHER, 0.0,
-              [&] { return launch_boost_update(F, v, b->eta, n, c->stream); }));
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+      return launch_boost_update(F, v, b->eta, n, c->stream, K, (int)(t % K));
+    }));
   }
-  if (F != value_out)
-    CK(cudaMemcpyAsync(value_out, F, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost,
+  if (class_out)
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] { return launch_argmax_rows(F, n, K, cls, c->stream); }));
+  if (value_out && F != value_out)
+    CK(cudaMemcpyAsync(value_out, F, sizeof(float) * (size_t)n * K, cudaMemcpyDeviceToHost,
+                       c->stream));
+  if (class_out && cls != class_out)
+    CK(cudaMemcpyAsync(class_out, cls, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost,
                        c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return SLM_OK;
 }
 
-slm_status slm_boost_info(const slm_boost* b, int32_t* n_rounds, float* base,
-                          float* learning_rate) {
+slm_status slm_boost_info(const slm_boost* b, int32_t* n_rounds, int32_t* n_outputs,
+                          float* base, float* learning_rate) {
   if (!b) return SLM_EINVAL;
-  if (n_rounds) *n_rounds = (int32_t)b->trees.size();
+  if (n_rounds) *n_rounds = (int32_t)(b->trees.size() / b->K);
+  if (n_outputs) *n_outputs = b->K;
   if (base) *base = b->base;
   if (learning_rate) *learning_rate = b->eta;
   return SLM_OK;

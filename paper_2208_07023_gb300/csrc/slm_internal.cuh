@@ -366,9 +366,11 @@ cudaError_t launch_predict(const float* X, int64_t n, int d, TreeArrays tr,
                            int32_t* class_out, double* value_out,
                            int32_t* leaf_out, cudaStream_t st);
 
-// SLR Boost rounds: base = (float)(mean of y in double) and F[i] = base (one
+// Boosting rounds: base = (float)(mean of y in double) and F[i] = base (one
 // CTA, a fixed summation order); mean of (y - F)^2 in double (one CTA);
-// r = y - F; F += eta * (float)v; F = v.
+// r = y - F; F[i*K + k] += eta * (float)v_i; F = v; the softmax residuals
+// R[k*n + i] = (float)([labels_i == k] - p_ik) (double); the mean
+// cross-entropy (one CTA); the argmax of each row of F[n, K].
 cudaError_t launch_boost_init(const float* y, int64_t n, float* F, float* base_out,
                               cudaStream_t st);
 cudaError_t launch_boost_mse(const float* y, const float* F, int64_t n, double* out,
@@ -376,7 +378,13 @@ cudaError_t launch_boost_mse(const float* y, const float* F, int64_t n, double* 
 cudaError_t launch_boost_residual(const float* y, const float* F, float* r, int64_t n,
                                   cudaStream_t st);
 cudaError_t launch_boost_update(float* F, const double* v, float eta, int64_t n,
-                                cudaStream_t st);
+                                cudaStream_t st, int K = 1, int k = 0);
+cudaError_t launch_softmax_residual(const float* F, const int32_t* labels, int64_t n, int K,
+                                    float* R, cudaStream_t st);
+cudaError_t launch_boost_ce(const float* F, const int32_t* labels, int64_t n, int K,
+                            double* out, cudaStream_t st);
+cudaError_t launch_argmax_rows(const float* F, int64_t n, int K, int32_t* cls,
+                               cudaStream_t st);
 cudaError_t launch_fill_f(float* F, float v, int64_t n, cudaStream_t st);
 
 // ---- learned swarm proposal (mlp_kernels.cu) --------------------------------

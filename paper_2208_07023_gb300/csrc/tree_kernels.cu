@@ -633,11 +633,64 @@ __global__ void k_boost_residual(const float* __restrict__ y, const float* __res
     r[i] = __fsub_rn(y[i], F[i]);
 }
 
-// F_i += eta * (float)v_i, one rounding per operation.
-__global__ void k_boost_update(float* F, const double* __restrict__ v, float eta, int64_t n) {
+// F[i*K + k] += eta * (float)v_i, one rounding per operation.
+__global__ void k_boost_update(float* F, const double* __restrict__ v, float eta, int64_t n,
+                               int K, int k) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    F[i] = __fadd_rn(F[i], __fmul_rn(eta, (float)v[i]));
+    F[i * K + k] = __fadd_rn(F[i * K + k], __fmul_rn(eta, (float)v[i]));
+}
+
+// Softmax of one row of K scores in double: its maximum and the sum of
+// exp(F_k - max) over k ascending.
+__device__ __forceinline__ void softmax_row(const float* f, int K, double* mx, double* s) {
+  double m = (double)f[0];
+  for (int k = 1; k < K; ++k) m = (double)f[k] > m ? (double)f[k] : m;
+  double t = 0.0;
+  for (int k = 0; k < K; ++k) t += exp((double)f[k] - m);
+  *mx = m;
+  *s = t;
+}
+
+// R[k*n + i] = (float)([labels_i == k] - p_ik), p the softmax of F's row i.
+__global__ void k_softmax_residual(const float* __restrict__ F, const int32_t* __restrict__ lab,
+                                   int64_t n, int K, float* R) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float* f = F + i * K;
+    double mx, sum;
+    softmax_row(f, K, &mx, &sum);
+    const int y = lab[i];
+    for (int k = 0; k < K; ++k)
+      R[(int64_t)k * n + i] = (float)((y == k ? 1.0 : 0.0) - exp((double)f[k] - mx) / sum);
+  }
+}
+
+// Mean over i of -log p_{i, labels_i} (log-sum-exp form) in double.
+__global__ void __launch_bounds__(kBoostThreads)
+    k_boost_ce(const float* __restrict__ F, const int32_t* __restrict__ lab, int64_t n, int K,
+               double* out) {
+  double t = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kBoostThreads) {
+    const float* f = F + i * K;
+    double mx, sum;
+    softmax_row(f, K, &mx, &sum);
+    t += -(((double)f[lab[i]] - mx) - log(sum));
+  }
+  t = boost_block_sum(t);
+  if (threadIdx.x == 0) *out = t / (double)n;
+}
+
+// class_out[i] = argmax over k of F[i*K + k], ties to the lower class.
+__global__ void k_argmax_rows(const float* __restrict__ F, int64_t n, int K, int32_t* cls) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float* f = F + i * K;
+    int b = 0;
+    for (int k = 1; k < K; ++k)
+      if (f[k] > f[b]) b = k;
+    cls[i] = b;
+  }
 }
 
 __global__ void k_fill_f(float* F, float v, int64_t n) {
@@ -675,9 +728,30 @@ cudaError_t launch_boost_residual(const float* y, const float* F, float* r, int6
 }
 
 cudaError_t launch_boost_update(float* F, const double* v, float eta, int64_t n,
-                                cudaStream_t st) {
+                                cudaStream_t st, int K, int k) {
   if (n <= 0) return cudaSuccess;
-  k_boost_update<<<elementwise_blocks(n), 256, 0, st>>>(F, v, eta, n);
+  k_boost_update<<<elementwise_blocks(n), 256, 0, st>>>(F, v, eta, n, K, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_softmax_residual(const float* F, const int32_t* labels, int64_t n, int K,
+                                    float* R, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_softmax_residual<<<elementwise_blocks(n), 256, 0, st>>>(F, labels, n, K, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boost_ce(const float* F, const int32_t* labels, int64_t n, int K,
+                            double* out, cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  k_boost_ce<<<1, kBoostThreads, 0, st>>>(F, labels, n, K, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_rows(const float* F, int64_t n, int K, int32_t* cls,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_argmax_rows<<<elementwise_blocks(n), 256, 0, st>>>(F, n, K, cls);
   return cudaGetLastError();
 }
 

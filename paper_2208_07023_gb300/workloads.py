@@ -161,6 +161,12 @@ SETTINGS = {
         builder=lambda seed=1: tanh_regression(200_000, 128, 8, 0.1, seed),
         criterion="mse", n_particles=64, n_iters=40, n_bins=256,
         max_depth=6, min_leaf=20, n_trees=1, rounds=10, lr=0.3),
+    # SLM Boost: 5 rounds of 10 depth-4 SLR trees (one per class) fitted to
+    # the softmax residuals of the classification mixture, learning rate 0.5
+    "slmboost_n50k_d64_k10_r5": dict(
+        builder=lambda seed=1: gmm(50_000, 64, 10, seed),
+        criterion="mse", n_particles=64, n_iters=40, n_bins=128,
+        max_depth=4, min_leaf=20, n_trees=1, rounds=5, lr=0.5, classes=10),
     # bagged forest of 64 trees; every level of all trees searched as one
     # graph-captured launch
     "forest64_n100k_d32_k5": dict(

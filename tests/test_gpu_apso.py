@@ -83,6 +83,25 @@ def test_apso_tree_matches_oracle(ctx, bootstrap, graphs):
     f.free()
 
 
+def test_apso_with_feature_prescreen_matches_oracle(ctx):
+    # the pre-screen's subspace search runs adaptive PSO (its elite slot in the
+    # subspace's swarm); gB lifted back to d features
+    from paper_2208_07023_gb300 import binding as S
+    n, d, K, P, T, B, top_n = 3000, 24, 4, 24, 20, 64, 6
+    wl = W.gmm(n, d, K, seed=41)
+    gp = params(S, "gini", K, P, T, B, min_leaf=3, seed=9, top_n=top_n)
+    g = ctx.node_split(gp, wl.X, labels=wl.labels, node_uid=5, want_trace=True)
+    op = oparams("gini", K, P, T, B, min_leaf=3, seed=9)
+    op.top_n = top_n
+    r = O.node_split(op, wl.X, wl.labels, node_uid=5)
+    assert r.split["elite_tries"] > 0
+    assert np.array_equal(g["trace"], r.trace_loss)
+    assert np.array_equal(g["gbest"].astype(np.float64), r.gbest)
+    assert np.count_nonzero(g["gbest"]) <= top_n
+    assert (g["particle"], g["iter_of_best"], g["bin"]) == \
+        (r.split["particle"], r.split["iter_of_best"], r.split["bin"])
+
+
 def test_apso_changes_the_search_and_finds_the_planted_direction(ctx):
     from paper_2208_07023_gb300 import binding as S
     wl = W.single_node(2000, 16, 0.05, seed=9)

@@ -1,5 +1,5 @@
-"""GPU parity of SLR Boost (Sec. V; least-squares gradient boosting of SLR
-trees on residuals, in float) against the oracle.
+"""GPU parity of SLR Boost and SLM Boost (Sec. V; gradient boosting of SLR
+trees on residuals, in float) against the oracle. SLR Boost:
 
 * base, every round's tree (identical nodes, except below a node where the
   two searches part after a near-tie the oracle logged), training MSE and
@@ -9,6 +9,13 @@ trees on residuals, in float) against the oracle.
 * with one round and learning rate 1 the predictions are one tree's on the
   residuals of the mean; zero rounds predict the mean;
 * bad arguments are refused.
+
+SLM Boost (K-class softmax gradient boosting with least-squares SLR trees):
+* every tree of every round as the oracle's (up to a logged near-tie), the
+  residuals of each round taken from the oracle's scores, the training
+  cross-entropy, the scores and the classes;
+* the scores' cross-entropy is the reported loss, the class their argmax;
+  two targets, a label outside [0, K) and K < 2 are refused.
 """
 import numpy as np
 import pytest
@@ -117,3 +124,83 @@ def test_bad_boost_arguments(ctx):
         ctx.train_boost(gpu_params(S, "mse", 0, 8, 2, 16, n_trees=2, bootstrap=True),
                         wl.X, wl.y, 2, 0.5)
     assert e.value.status == S.SLM_EUNSUPPORTED
+
+
+# ---- SLM Boost ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d,K,depth,M,eta,seed", [
+    (3000, 6, 3, 3, 3, 0.5, 31),
+    (2500, 8, 4, 2, 2, 1.0, 32),
+])
+def test_cls_boost_matches_oracle(ctx, n, d, K, depth, M, eta, seed):
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(n, d, K, seed=seed)
+    gp = S.make_params("mse", K, n_particles=16, n_iters=10, n_bins=32, min_leaf=10,
+                       max_depth=depth, seed=2)
+    b = ctx.train_boost(gp, wl.X, labels=wl.labels, n_classes=K, n_rounds=M,
+                        learning_rate=eta)
+    op = oracle_params(O, "mse", 0, 16, 10, 32, min_leaf=10, max_depth=depth, seed=2)
+    r = O.train_boost_cls(op, wl.X, wl.labels, K, M, eta)
+    assert b.info()["n_outputs"] == K and b.info()["n_rounds"] == M
+    # the first round's residuals take two values (1 - 1/K, -1/K), so
+    # partitions with equal counts have exactly equal SSE: the GPU's exact
+    # fixed-point sums keep the tie (lower index wins) while the oracle's
+    # double sums part them by rounding and log a near-tie; below such a node
+    # the checker only requires the GPU's choice to be valid, and the later
+    # trees then fit other residuals
+    F = np.zeros((n, K), np.float32)
+    matched, compared = True, 0
+    for m in range(M):
+        R = O.softmax_residuals(F, wl.labels, K)
+        for k in range(K):
+            t = m * K + k
+            q = oracle_params(O, "mse", 0, 16, 10, 32, min_leaf=10, max_depth=depth,
+                              seed=2 + t + 1)
+            g = b.tree(t).export(0)
+            compared += 1
+            if _check_tree_up_to_near_ties(g, r.trees[t], q, wl.X, None, R[k]):
+                matched = False
+                break
+            _, v, _ = O.predict(q, r.trees[t], wl.X)
+            F[:, k] = (F[:, k] + np.float32(eta) * v.astype(np.float32)).astype(np.float32)
+        if not matched:
+            break
+        assert b.train_loss[m] == pytest.approx(r.train_loss[m], rel=1e-12)
+    assert compared >= 1
+    if matched:
+        assert np.array_equal(F, r.F)
+        scores, cls = b.predict(wl.X, want_class=True)
+        assert np.array_equal(scores, r.F)
+        _, rcls = O.boost_predict_cls(op, r, wl.X)
+        assert np.array_equal(cls, rcls)
+    b.free()
+
+
+def test_cls_boost_predictions_and_errors(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.gmm(4000, 8, 3, seed=33)
+    gp = S.make_params("mse", 3, n_particles=16, n_iters=8, n_bins=32, min_leaf=10,
+                       max_depth=3, seed=4)
+    b = ctx.train_boost(gp, wl.X, labels=wl.labels, n_classes=3, n_rounds=4,
+                        learning_rate=0.3)
+    scores, cls = b.predict(wl.X, want_class=True)
+    assert scores.shape == (4000, 3) and np.array_equal(cls, np.argmax(scores, axis=1))
+    assert np.all(np.diff(b.train_loss) <= 0) and b.train_loss[0] < np.log(3)
+    Fd = scores.astype(np.float64)
+    lse = Fd.max(1) + np.log(np.exp(Fd - Fd.max(1, keepdims=True)).sum(1))
+    ce = np.mean(lse - Fd[np.arange(4000), wl.labels])
+    assert b.train_loss[-1] == pytest.approx(ce, rel=1e-12)
+    assert np.mean(cls == wl.labels) > 0.5
+    b.free()
+    with pytest.raises(S.SlmError) as e:  # both targets
+        ctx.train_boost(gp, wl.X, y=wl.X[:, 0].copy(), labels=wl.labels, n_rounds=1)
+    assert e.value.status == S.SLM_EINVAL
+    bad = wl.labels.copy()
+    bad[7] = 3
+    with pytest.raises(S.SlmError) as e:  # a label outside [0, K)
+        ctx.train_boost(gp, wl.X, labels=bad, n_classes=3, n_rounds=1)
+    assert e.value.status == S.SLM_EINVAL
+    with pytest.raises(S.SlmError) as e:
+        ctx.train_boost(S.make_params("mse", 1, n_particles=8, n_iters=2, n_bins=16), wl.X,
+                        labels=wl.labels * 0, n_classes=1, n_rounds=1)
+    assert e.value.status == S.SLM_EINVAL
