@@ -109,6 +109,8 @@ def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
     if args_launch is not None:
         d["search_loop_graphs"] = args_launch.graphs
         d["projection_tile_mode"] = args_launch.tiles
+        d["projection_staging"] = ("tensor-map tile copies (cp.async.bulk.tensor)"
+                                   if args_launch.tma == "on" else "per-thread cp.async")
     if extra:
         d.update(extra)
     return d
@@ -444,6 +446,7 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
 
 def apply_launch_options(ctx, args):
     ctx.set_graphs(args.graphs == "on")
+    ctx.set_projection_tma(args.tma == "on")
     if args.tiles == "fixed":
         ctx.set_tuning(False)
     elif args.tiles != "auto":
@@ -829,6 +832,9 @@ def main():
     ap.add_argument("--proj", choices=["fp32", "bf16"], default=None)
     ap.add_argument("--topk", type=int, default=8)
     ap.add_argument("--compare-fp32", action="store_true")
+    ap.add_argument("--tma", choices=["on", "off"], default="on",
+                    help="FP32 projection staging: tensor-map tile copies (on) or "
+                         "per-thread asynchronous copies (off)")
     ap.add_argument("--apso", action="store_true",
                     help="adaptive PSO (FP32 form): the workload's searches adapt inertia "
                          "and learning factors to the swarm's evolutionary state")

@@ -509,7 +509,8 @@ slm_status slm_tuning_stats(slm_ctx* ctx, int64_t* shapes, int32_t* last_pg,
 /* The tuned shapes: *n receives their number; the first max are written to
  * the arrays (any may be NULL): features d, padded P, log2 of the row tiles,
  * the chosen particles per group, CTAs per SM and row source (1: gathered
- * from the base rows by sample id, 0: the level's entry-ordered copy), and
+ * from the base rows by sample id; the level's entry-ordered copy staged by
+ * per-thread copies: 0, by tensor-map tile copies: 2), and
  * the chosen candidate's time for two projections (ms). Bagged forests whose
  * base rows fit in a quarter of L2 keep a copy of them, which makes the
  * gathered source a candidate for their levels. */
@@ -528,6 +529,12 @@ slm_status slm_tuned_shapes(slm_ctx* ctx, int32_t max, int32_t* n, int32_t* d,
  * Results are identical either way; per-launch profiling (slm_profile)
  * always launches one by one. SLM_EINVAL for other values. */
 slm_status slm_set_graphs(slm_ctx* ctx, int32_t on);
+/* on != 0 (the default): the FP32 projection stages rows that are contiguous
+ * in memory (not gathered through sample ids), when d % 4 == 0 and the rows
+ * are 16-byte aligned, by tensor-map tile copies (cp.async.bulk.tensor, one
+ * issuing thread, 128-byte swizzle); on = 0: by per-thread asynchronous
+ * copies. The projected values are identical either way. */
+slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
 /* Graph launches of the context: in total, of kept graphs launched again
  * unchanged, updated in place, and instantiated anew (any may be NULL). */
 slm_status slm_graph_stats(slm_ctx* ctx, int64_t* launches, int64_t* reuses,

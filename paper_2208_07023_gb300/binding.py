@@ -95,6 +95,7 @@ def lib():
             "slm_kernel_stats": ([vp, i32, P(i64), P(C.c_double), P(C.c_double)], C.c_int),
             "slm_launch_count": ([vp, P(i64)], C.c_int),
             "slm_set_graphs": ([vp, i32], C.c_int),
+            "slm_set_projection_tma": ([vp, i32], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
             "slm_set_node_search": ([vp, i32], C.c_int),
@@ -440,6 +441,9 @@ class Context:
 
     def set_graphs(self, on: bool):
         self._check(lib().slm_set_graphs(self.handle, 1 if on else 0))
+
+    def set_projection_tma(self, on: bool):
+        self._check(lib().slm_set_projection_tma(self.handle, 1 if on else 0))
 
     def graph_stats(self) -> dict:
         a, r, b, c = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()

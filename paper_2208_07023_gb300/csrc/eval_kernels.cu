@@ -24,6 +24,8 @@
 //    written to an L2-resident buffer.
 //  * k_hist_scan: one CTA per (node, particle) bins the node's z into
 //    warp-private shared histograms, merges them and scans the edges.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <limits.h>
@@ -562,6 +564,201 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
     }
     __syncthreads();  // buffer s&1 is refilled by the next stage's copies
+  }
+}
+
+// ---- projection with tensor-map tile copies (TMA) ----------------------------------
+//
+// The same work units, arithmetic and epilogue as k_project, for rows that
+// are contiguous in pr.X (no gather) with d % 4 == 0: thread 0 fetches each
+// kKC-feature chunk of a unit as two 2D boxes of tensor maps (kTS rows x 32
+// features of X, PG positions x 32 features) into a two-stage ring, the
+// copies completing on an mbarrier; 128-byte swizzle (16-byte chunk c of
+// smem row r stored at c ^ (r mod 8)) keeps the float4 reads of 8 lanes on
+// 8 consecutive rows on distinct banks. Features past d and rows past the
+// tensor's end arrive as zeros. Every wait is bounded; a copy that does not
+// land sets the error word 3 and ends the kernel after the copies in flight.
+
+constexpr int kTmaRowBytes = kKC * 4;                   // one box row: 128 B
+constexpr int kTmaXBytes = kTS * kTmaRowBytes;          // 32 KB
+constexpr int kTmaABytes = kPGMax * kTmaRowBytes;       // 6 KB (room for PG <= 48)
+constexpr size_t kProjTmaSmem = 2 * (kTmaXBytes + kTmaABytes) + 1024;  // + alignment
+
+template <int PG>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_project_tma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap ta,
+                  Problem pr, Swarm sw, const WorkTile* __restrict__ tiles, int n_units) {
+  constexpr int PJ = PG / 4;
+  static_assert(PG % 8 == 0 && PG <= kPGMax, "particle group");
+  extern __shared__ unsigned char tsm_raw[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  // the swizzle pattern repeats every 1024 bytes: stage buffers start on it
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~uintptr_t(1023));
+  float* xs[2] = {reinterpret_cast<float*>(base),
+                  reinterpret_cast<float*>(base + kTmaXBytes)};
+  float* as[2] = {reinterpret_cast<float*>(base + 2 * kTmaXBytes),
+                  reinterpret_cast<float*>(base + 2 * kTmaXBytes + kTmaABytes)};
+  pdl_trigger();
+  pdl_wait();
+  if ((int)blockIdx.x >= n_units) return;
+  const int d = pr.d, G = pr.G;
+  const int nk = (d + kKC - 1) / kKC;
+  const int my_units = (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+  const int n_st = my_units * nk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sg = lane & 7, pg = lane >> 3;
+  const uint32_t stage_bytes = (uint32_t)(kTmaXBytes + PG * kTmaRowBytes);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int s) {
+    const int ui = s / nk, c = s - ui * nk;
+    const int u = blockIdx.x + ui * gridDim.x;
+    const WorkTile wt = tiles[u / G];
+    const int g = u % G;
+    uint64_t* bar = &s_bar[s & 1];
+    fence_proxy_async();
+    mbar_expect_tx(bar, stage_bytes);
+    tma_load_2d(xs[s & 1], &tx, c * kKC, (int)wt.row0, bar);
+    tma_load_2d(as[s & 1], &ta, c * kKC, wt.node * pr.Pp + g * PG, bar);
+  };
+  if (threadIdx.x == 0) issue(0);
+  float acc[4][PJ];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
+
+  for (int s = 0; s < n_st; ++s) {
+    const int ui = s / nk, c = s - ui * nk;
+    const int u = blockIdx.x + ui * gridDim.x;
+    // the other stage was released by the barrier that ended step s - 1
+    if (threadIdx.x == 0 && s + 1 < n_st) issue(s + 1);
+    const bool ok = mbar_wait(&s_bar[s & 1], (uint32_t)((s >> 1) & 1), kWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not land: record it, give the copies in flight a bounded
+      // chance to finish, and end
+      if (threadIdx.x == 0) {
+        if (sw.err) atomicExch(sw.err, 3);
+        if (s + 1 < n_st) mbar_wait(&s_bar[(s + 1) & 1], (uint32_t)(((s + 1) >> 1) & 1),
+                                    kWaitPolls);
+      }
+      return;
+    }
+    const float* xb = xs[s & 1];
+    const float* ab = as[s & 1];
+    const int kc4 = (min(kKC, d - c * kKC) + 3) & ~3;
+    // rows warp*32 + sg + 8i all have r mod 8 = sg; particle pg + 4j has
+    // (pg + 4j) mod 8 = pg + 4 (j & 1)
+    const float* xr = xb + (warp * 32 + sg) * kKC;
+    const float* ar = ab + pg * kKC;
+    if constexpr (PJ <= 4) {
+#pragma unroll 2
+      for (int k = 0; k < kc4; k += 4) {
+        const int ch = k >> 2;
+        float4 xv[4], av[PJ];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kKC + ((ch ^ sg) << 2));
+#pragma unroll
+        for (int j = 0; j < PJ; ++j)
+          av[j] = *reinterpret_cast<const float4*>(ar + j * 4 * kKC +
+                                                   ((ch ^ (pg + 4 * (j & 1))) << 2));
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].x, av[j].x, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].y, av[j].y, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].z, av[j].z, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < PJ; ++j) acc[i][j] = fmaf(xv[i].w, av[j].w, acc[i][j]);
+      }
+    } else {
+      for (int k = 0; k < kc4; k += 4) {
+        const int ch = k >> 2;
+        float4 xv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kKC + ((ch ^ sg) << 2));
+#pragma unroll
+        for (int j = 0; j < PJ; j += 2) {
+          const float4 a0 =
+              *reinterpret_cast<const float4*>(ar + j * 4 * kKC + ((ch ^ pg) << 2));
+          const float4 a1 = *reinterpret_cast<const float4*>(ar + (j + 1) * 4 * kKC +
+                                                             ((ch ^ (pg + 4)) << 2));
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].x, a0.x, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].x, a1.x, acc[i][j + 1]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].y, a0.y, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].y, a1.y, acc[i][j + 1]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].z, a0.z, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].z, a1.z, acc[i][j + 1]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fmaf(xv[i].w, a0.w, acc[i][j]);
+            acc[i][j + 1] = fmaf(xv[i].w, a1.w, acc[i][j + 1]);
+          }
+        }
+      }
+    }
+    if (c == nk - 1) {
+      // tile complete: fold the range, store z (k_project's epilogue)
+      const WorkTile wt = tiles[u / G];
+      const int g = u % G;
+#pragma unroll
+      for (int j = 0; j < PJ; ++j) {
+        const int p = g * PG + pg + 4 * j;
+        float lo = FLT_MAX, hi = -FLT_MAX;
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = warp * 32 + sg + 8 * i;
+          if (r < wt.rows) {
+            const float z = acc[i][j];
+            lo = z < lo ? z : lo;
+            hi = z > hi ? z : hi;
+            any = true;
+            if (p < pr.P) sw.z[(int64_t)p * pr.Ez + wt.row0 + r] = z;
+          }
+        }
+        int olo = any ? f2ord(lo) : INT_MAX, ohi = any ? f2ord(hi) : INT_MIN;
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+          olo = min(olo, __shfl_xor_sync(0xffffffffu, olo, off));
+          ohi = max(ohi, __shfl_xor_sync(0xffffffffu, ohi, off));
+        }
+        if (sg == 0 && olo != INT_MAX && p < pr.P) {
+          int* zz = sw.zmm + ((int64_t)wt.node * pr.Pp + p) * 2;
+          atomicMin(zz, olo);
+          atomicMax(zz + 1, ohi);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
+    }
+    __syncthreads();  // stage s & 1 is refilled by the copies issued at step s + 1
   }
 }
 
@@ -1984,6 +2181,12 @@ cudaError_t prepare_eval_kernels(const Problem& pr) {
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kProjSmem)))
       return e;
+  for (const void* f : {(const void*)k_project_tma<8>, (const void*)k_project_tma<16>,
+                        (const void*)k_project_tma<24>, (const void*)k_project_tma<32>,
+                        (const void*)k_project_tma<48>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kProjTmaSmem)))
+      return e;
   for (const void* f : {(const void*)k_node_search<SLM_GINI>,
                         (const void*)k_node_search<SLM_ENTROPY>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2035,8 +2238,76 @@ bool project_group_ok(const Problem& pr, int pg) {
   return (pg == 8 || pg == 16 || pg == 24 || pg == 32 || pg == 48) && pr.Pp % pg == 0;
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// A row-major [rows, d] float tensor as boxes of box_rows rows x kKC
+// features with 128-byte swizzle (d % 4 == 0, base 16-byte aligned). The
+// last few encodings are kept per host thread: a search launches the same
+// maps every iteration.
+bool encode_rows(CUtensorMap* m, const float* base, uint64_t rows, int d, uint32_t box_rows) {
+  struct Entry {
+    const float* base;
+    uint64_t rows;
+    int d;
+    uint32_t box_rows;
+    bool ok;
+    CUtensorMap map;
+  };
+  constexpr int kKeep = 8;
+  thread_local Entry kept[kKeep];
+  thread_local int n_kept = 0, next = 0;
+  for (int i = 0; i < n_kept; ++i) {
+    const Entry& e = kept[i];
+    if (e.base == base && e.rows == rows && e.d == d && e.box_rows == box_rows) {
+      if (e.ok) *m = e.map;
+      return e.ok;
+    }
+  }
+  Entry& e = kept[next];
+  next = (next + 1) % kKeep;
+  if (n_kept < kKeep) ++n_kept;
+  e.base = base;
+  e.rows = rows;
+  e.d = d;
+  e.box_rows = box_rows;
+  e.ok = false;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || rows == 0 || (d & 3) || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)d * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKC, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  e.ok = enc(&e.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+  if (e.ok) *m = e.map;
+  return e.ok;
+}
+
+}  // namespace
+
 cudaError_t launch_project(const Problem& pr_in, const Swarm& sw, const WorkTile* tiles,
-                           int n_tiles, int grid_cap, cudaStream_t st, int pg, bool gather) {
+                           int n_tiles, int grid_cap, cudaStream_t st, int pg, bool gather,
+                           int A) {
   Problem pr = pr_in;
   if (!gather || !pr.Xg) pr.gidx = nullptr;
   if (pg > 0) {
@@ -2056,6 +2327,22 @@ cudaError_t launch_project(const Problem& pr_in, const Swarm& sw, const WorkTile
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // contiguous rows: tensor-map tile copies (A > 0 names the batch's nodes,
+  // which bound the positions' tensor)
+  CUtensorMap tx, ta;
+  const int PG = pr.Pp / pr.G;
+  if (A > 0 && !pr.gidx && encode_rows(&tx, pr.X, (uint64_t)pr.E, pr.d, kTS) &&
+      encode_rows(&ta, sw.pos, (uint64_t)A * pr.Pp, pr.d, (uint32_t)PG)) {
+    cfg.dynamicSmemBytes = kProjTmaSmem;
+    switch (PG) {
+      case 8: return cudaLaunchKernelEx(&cfg, k_project_tma<8>, tx, ta, pr, sw, tiles, n_units);
+      case 16: return cudaLaunchKernelEx(&cfg, k_project_tma<16>, tx, ta, pr, sw, tiles, n_units);
+      case 24: return cudaLaunchKernelEx(&cfg, k_project_tma<24>, tx, ta, pr, sw, tiles, n_units);
+      case 32: return cudaLaunchKernelEx(&cfg, k_project_tma<32>, tx, ta, pr, sw, tiles, n_units);
+      case 48: return cudaLaunchKernelEx(&cfg, k_project_tma<48>, tx, ta, pr, sw, tiles, n_units);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (pr.Pp / pr.G) {
     case 8: return cudaLaunchKernelEx(&cfg, k_project<8>, pr, sw, tiles, n_units);
     case 16: return cudaLaunchKernelEx(&cfg, k_project<16>, pr, sw, tiles, n_units);

@@ -78,6 +78,7 @@ struct slm_ctx {
     int cps = 2;         // CTAs per SM of the persistent grid
     float ms = 0.f;      // tuned: time of two projections with these tiles
     bool gather = false; // rows gathered from the base rows by sample id
+    bool tma = true;     // contiguous rows staged by tensor-map tile copies
   };
   int tune = 1;
   // histogram clusters: CTAs per (node, particle), tuned per shape
@@ -100,6 +101,8 @@ struct slm_ctx {
   Tiles last{};  // tiles of the last search
   // a search's iteration loop as one CUDA graph launch (reused executable)
   bool graphs = false;
+  // FP32 projection of contiguous rows staged by tensor-map tile copies
+  bool tma = true;
   cudaStream_t cap_stream = nullptr;  // records graphs (the caller's stream may
                                       // be the legacy default stream)
   // executable graphs by launch signature (every kernel node's function,
@@ -689,7 +692,8 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
   }
   if (n_tiles)
     CK(launch(c, SLM_K_PROJECT, pairs, [&] {
-      return launch_project(pr, sw, dt, n_tiles, cap, c->stream, c->cur.pg, c->cur.gather);
+      return launch_project(pr, sw, dt, n_tiles, cap, c->stream, c->cur.pg, c->cur.gather,
+                            c->tma && c->cur.tma ? A : 0);
     }));
   if (hp && hp->on && !bins_out) {
     if (hp->n_large)
@@ -780,7 +784,7 @@ slm_status seed_swarms(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc
 // the fastest is kept for the shape. The candidates
 // compute the same z and ranges (each z is the same sequence of fused
 // multiply-adds), so the extra passes change nothing the search reads.
-slm_status pick_tiles(slm_ctx* c, const Problem& pr, const Swarm& sw, int n_tiles,
+slm_status pick_tiles(slm_ctx* c, const Problem& pr, const Swarm& sw, int n_tiles, int A,
                       slm_ctx::Tiles* out) {
   if (c->forced.pg) {
     if (!project_group_ok(pr, c->forced.pg))
@@ -794,7 +798,7 @@ slm_status pick_tiles(slm_ctx* c, const Problem& pr, const Swarm& sw, int n_tile
   while ((1 << lg) < n_tiles) ++lg;
   const bool can_gather = pr.Xg && pr.gidx;
   const uint64_t key = ((uint64_t)pr.d << 40) | ((uint64_t)pr.Pp << 16) |
-                       ((uint64_t)can_gather << 15) | (uint64_t)lg;
+                       ((uint64_t)can_gather << 15) | ((uint64_t)c->tma << 14) | (uint64_t)lg;
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
     *out = it->second;
@@ -809,13 +813,19 @@ slm_status pick_tiles(slm_ctx* c, const Problem& pr, const Swarm& sw, int n_tile
   slm_status s = SLM_OK;
   for (int pg : {8, 16, 24, 32, 48}) {
     if (!project_group_ok(pr, pg)) continue;
-    for (int v = 0; v < (can_gather ? 4 : 2) && !s; ++v) {
+    // CTAs per SM x row source (entry-ordered copy staged by tensor maps or
+    // per-thread copies; gathered rows, per-thread copies)
+    for (int v = 0; v < (can_gather ? 6 : 4) && !s; ++v) {
       const int cps = 1 + (v & 1);
-      const bool gather = v >= 2;
+      const bool gather = v >= 4;
+      const bool tma = v < 2;
+      if (tma && !c->tma) continue;
       cudaError_t e = cudaSuccess;
       for (int r = 0; r < 3 && !e; ++r) {
         if (r == 1) e = cudaEventRecord(e0, c->stream);
-        if (!e) e = launch_project(pr, sw, dt, n_tiles, cps * c->n_sm, c->stream, pg, gather);
+        if (!e)
+          e = launch_project(pr, sw, dt, n_tiles, cps * c->n_sm, c->stream, pg, gather,
+                             tma ? A : 0);
         c->launches += 1;
       }
       if (!e) e = cudaEventRecord(e1, c->stream);
@@ -828,7 +838,7 @@ slm_status pick_tiles(slm_ctx* c, const Problem& pr, const Swarm& sw, int n_tile
       }
       if (!have || ms < best) {
         best = ms;
-        pick = slm_ctx::Tiles{pg, cps, ms, gather};
+        pick = slm_ctx::Tiles{pg, cps, ms, gather, tma};
         have = true;
       }
     }
@@ -920,8 +930,8 @@ slm_status pick_split(slm_ctx* c, const Problem& pr, const Swarm& sw,
     float ms_min = 0.f;
     bool ok = true;
     for (int r = 0; r < 2 && ok; ++r) {
-      cudaError_t e =
-          launch_project(pr, sw, dt, n_tiles, tl.cps * c->n_sm, c->stream, tl.pg, tl.gather);
+      cudaError_t e = launch_project(pr, sw, dt, n_tiles, tl.cps * c->n_sm, c->stream, tl.pg,
+                                     tl.gather, c->tma && tl.tma ? A : 0);
       if (!e) e = cudaEventRecord(e0, c->stream);
       if (!e) e = launch_hist_scan(pr, sw, dn, A, S, nullptr, 0, 0, c->stream);
       if (!e) e = cudaEventRecord(e1, c->stream);
@@ -1175,7 +1185,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
   if (n_res < A) {
     int S = batch_split(c, pr, nodes);
     slm_ctx::Tiles tl{};
-    if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), &tl))) return s;
+    if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), A, &tl))) return s;
     HistPlan hp;
     if (!bp.on && (s = setup_hist_plan(c, pr, nodes, in, &hp))) return s;
     if (!bp.on && !hp.on && (s = pick_split(c, pr, sw, nodes, (int)tiles.size(), tl, &S)))
@@ -1190,7 +1200,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       kw.swarm(sw);
       kw.put(A); kw.put((int)tiles.size()); kw.put(S); kw.put(p->n_iters); kw.put(c->n_sm);
       kw.put(co.inertia); kw.put(co.c1); kw.put(co.c2); kw.put(co.seed);
-      kw.put(tl.pg); kw.put(tl.cps); kw.put(tl.gather); kw.put(pairs);
+      kw.put(tl.pg); kw.put(tl.cps); kw.put(tl.gather); kw.put(tl.tma); kw.put(c->tma);
+      kw.put(pairs);
       kw.put(dn); kw.put(ws_ptr<WorkTile>(c, S_TILES)); kw.put(ws_ptr<WorkTile>(c, S_MTILES));
       kw.put(bp.on); kw.put(bp.k); kw.put(bp.kp); kw.put(bp.n_mtiles); kw.put(bp.grid);
       kw.put(bp.S_k); kw.put(bp.pairs_k); kw.put(bp.posb); kw.put(bp.sel); kw.put(bp.inv);
@@ -2672,6 +2683,12 @@ slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
   return SLM_OK;
 }
 
+slm_status slm_set_projection_tma(slm_ctx* c, int32_t on) {
+  if (!c) return SLM_EINVAL;
+  c->tma = on != 0;
+  return SLM_OK;
+}
+
 slm_status slm_test_hooks(slm_ctx* c, int32_t first_wait_polls, int64_t fail_alloc_after) {
   if (!c || fail_alloc_after < 0) return fail(c, SLM_EINVAL, "bad test hook values");
   CK(cudaSetDevice(c->device));
@@ -2740,10 +2757,10 @@ slm_status slm_tuned_shapes(slm_ctx* c, int32_t max, int32_t* n, int32_t* d, int
     if (i < max) {
       if (d) d[i] = (int32_t)(kv.first >> 40);
       if (pp) pp[i] = (int32_t)((kv.first >> 16) & 0xFFFFFF);
-      if (tiles_log2) tiles_log2[i] = (int32_t)(kv.first & 0x7FFF);
+      if (tiles_log2) tiles_log2[i] = (int32_t)(kv.first & 0x3FFF);
       if (pg) pg[i] = kv.second.pg;
       if (ctas_per_sm) ctas_per_sm[i] = kv.second.cps;
-      if (gather) gather[i] = kv.second.gather ? 1 : 0;
+      if (gather) gather[i] = kv.second.gather ? 1 : (kv.second.tma && (kv.first >> 14 & 1)) ? 2 : 0;
       if (ms) ms[i] = kv.second.ms;
     }
     ++i;

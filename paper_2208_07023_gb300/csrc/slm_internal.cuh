@@ -175,9 +175,11 @@ cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
 // z and ranges of every (tile, particle group); grid_cap = CTAs launched at
 // most (the grid is persistent); pg = particles per group (0: pr.G's width);
 // gather: read rows through pr.gidx from pr.Xg (when set) instead of pr.X.
+// A > 0: the batch's node count (sw.pos holds A * pr.Pp rows); contiguous
+// rows with d % 4 == 0 are then staged by tensor-map tile copies.
 cudaError_t launch_project(const Problem& pr, const Swarm& sw,
                            const WorkTile* tiles, int n_tiles, int grid_cap,
-                           cudaStream_t st, int pg = 0, bool gather = false);
+                           cudaStream_t st, int pg = 0, bool gather = false, int A = 0);
 // Whether k_project has a pg-particle group variant dividing pr.Pp.
 bool project_group_ok(const Problem& pr, int pg);
 // Cluster split S of the histogram kernel for A nodes of at most max_len
