@@ -595,10 +595,11 @@ __global__ void __launch_bounds__(kThreads, 2)
   // the swizzle pattern repeats every 1024 bytes: stage buffers start on it
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~uintptr_t(1023));
-  float* xs[2] = {reinterpret_cast<float*>(base),
-                  reinterpret_cast<float*>(base + kTmaXBytes)};
-  float* as[2] = {reinterpret_cast<float*>(base + 2 * kTmaXBytes),
-                  reinterpret_cast<float*>(base + 2 * kTmaXBytes + kTmaABytes)};
+  // stage b: rows at base + b * kTmaXBytes, positions after both row stages
+  auto xstage = [&](int b) { return reinterpret_cast<float*>(base + b * kTmaXBytes); };
+  auto astage = [&](int b) {
+    return reinterpret_cast<float*>(base + 2 * kTmaXBytes + b * kTmaABytes);
+  };
   pdl_trigger();
   pdl_wait();
   if ((int)blockIdx.x >= n_units) return;
@@ -623,8 +624,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint64_t* bar = &s_bar[s & 1];
     fence_proxy_async();
     mbar_expect_tx(bar, stage_bytes);
-    tma_load_2d(xs[s & 1], &tx, c * kKC, (int)wt.row0, bar);
-    tma_load_2d(as[s & 1], &ta, c * kKC, wt.node * pr.Pp + g * PG, bar);
+    tma_load_2d(xstage(s & 1), &tx, c * kKC, (int)wt.row0, bar);
+    tma_load_2d(astage(s & 1), &ta, c * kKC, wt.node * pr.Pp + g * PG, bar);
   };
   if (threadIdx.x == 0) issue(0);
   float acc[4][PJ];
@@ -649,8 +650,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       return;
     }
-    const float* xb = xs[s & 1];
-    const float* ab = as[s & 1];
+    const float* xb = xstage(s & 1);
+    const float* ab = astage(s & 1);
     const int kc4 = (min(kKC, d - c * kKC) + 3) & ~3;
     // rows warp*32 + sg + 8i all have r mod 8 = sg; particle pg + 4j has
     // (pg + 4j) mod 8 = pg + 4 (j & 1)
@@ -1025,9 +1026,12 @@ __global__ void __launch_bounds__(256)
   // 2. the evolutionary state of the current positions
   float* xt = asm_;             // [d][Pq] current positions, feature-major
   float* rw = asm_ + d * Pq;    // [R][Pq + 1] square roots of a chunk of rows
+  // consecutive threads take consecutive particles of one feature: the
+  // shared-memory writes go to consecutive banks (the global reads are
+  // strided but hit L2: the positions were written by the last move)
   for (int e = threadIdx.x; e < Pq * d; e += blockDim.x) {
-    const int i = e / d, k = e - i * d;
-    xt[k * Pq + i] = i < P ? pos[e] : 0.0f;
+    const int k = e / Pq, i = e - k * Pq;
+    xt[e] = i < P ? pos[(int64_t)i * d + k] : 0.0f;
   }
   __syncthreads();
   const int nJ = Pq >> 2, ld = Pq + 1;

@@ -204,3 +204,25 @@ def test_cls_boost_predictions_and_errors(ctx):
         ctx.train_boost(S.make_params("mse", 1, n_particles=8, n_iters=2, n_bins=16), wl.X,
                         labels=wl.labels * 0, n_classes=1, n_rounds=1)
     assert e.value.status == S.SLM_EINVAL
+
+
+def test_degenerate_targets(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((500, 4)).astype(np.float32)
+    p = gpu_params(S, "mse", 0, 8, 4, 16, min_leaf=5, max_depth=3)
+    b = ctx.train_boost(p, X, np.full(500, 2.5, np.float32), 3, 0.5)
+    assert b.info()["base"] == 2.5 and np.all(b.predict(X) == np.float32(2.5))
+    assert np.all(b.train_mse == 0)
+    for m in range(3):
+        k = b.tree(m).export(0)["kind"]
+        assert k[0] == 0 and (k[1:] == -1).all()
+    c = ctx.train_boost(S.make_params("mse", 3, n_particles=8, n_iters=4, n_bins=16, min_leaf=5,
+                                      max_depth=3),
+                        X, labels=np.zeros(500, np.int32), n_classes=3, n_rounds=3,
+                        learning_rate=0.5)
+    r = O.train_boost_cls(oracle_params(O, "mse", 0, 8, 4, 16, min_leaf=5, max_depth=3), X,
+                          np.zeros(500, np.int32), 3, 3, 0.5)
+    scores, cls = c.predict(X, want_class=True)
+    assert np.array_equal(scores, r.F) and np.all(cls == 0)
+    assert np.allclose(c.train_loss, r.train_loss, rtol=1e-12)

@@ -158,3 +158,22 @@ def test_cls_bad_arguments():
         O.train_boost_cls(p, X, lab * 0, 1, 2, 0.5)  # K < 2
     with pytest.raises(ValueError):
         O.train_boost_cls(p, X, lab, 3, 2, 0.0)
+
+
+def test_degenerate_targets():
+    # a constant target: every residual is 0, every tree a single leaf of
+    # value 0, F stays the mean and the training MSE is 0
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((500, 4)).astype(np.float32)
+    y = np.full(500, 2.5, np.float32)
+    p = O.make_params("mse", 0, 8, 4, 16, min_leaf=5, max_depth=3)
+    b = O.train_boost(p, X, y, 3, 0.5)
+    assert b.base == 2.5 and np.all(b.F == np.float32(2.5)) and np.all(b.train_mse == 0)
+    assert all(t.kind[0] == 0 and (t.kind[1:] == -1).all() for t in b.trees)
+    # one class present among K = 3: each round's residuals are constant per
+    # class, so the trees are single leaves and every row gets the same scores
+    lab = np.zeros(500, np.int32)
+    c = O.train_boost_cls(p, X, lab, 3, 3, 0.5)
+    assert all(t.kind[0] == 0 for t in c.trees)
+    assert np.all(c.F == c.F[0]) and np.all(np.diff(c.train_loss) < 0)
+    assert c.train_loss[0] == pytest.approx(np.log1p(2 * np.exp(-0.5)), rel=1e-6)
