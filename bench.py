@@ -65,9 +65,9 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 # DRAM bytes per particle-sample pair from ncu captures of the default
 # workload (dram__bytes_read.sum + dram__bytes_write.sum, profiles/), valid
 # only for the kernel source they were taken from (sha256 of the .cu file).
-TRAFFIC = {"project": 12855040 / 3.2e6, "hist_scan": 13099776 / 3.2e6}
+TRAFFIC = {"project": 12843264 / 3.2e6, "hist_scan": 13079296 / 3.2e6}
 TRAFFIC_SOURCE = {"project": "eval_kernels.cu", "hist_scan": "eval_kernels.cu"}
-TRAFFIC_SOURCE_SHA = "24feb279d81ef2e48e98d8695386b960026bdc527015e90909aff142e2beee6e"
+TRAFFIC_SOURCE_SHA = "6f823aaf21af5bcca0d3bd7a799478bbd0946e8c832c21a8c30fab2e6bab67e2"
 
 
 def _kernel_source_sha(name):
