@@ -117,52 +117,90 @@ def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples of SM clock and throttle reasons, kept for the time
+    between mark_start() and mark_end(). Sampling starts before the region
+    (nvidia-smi needs a moment to print its first line) every 50 ms; each
+    sample carries nvidia-smi's own timestamp."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
         self.proc = None
+        self.out = ""
+        self.t0 = self.t1 = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
 
-    def __exit__(self, *a):
-        self.out = ""
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
         if self.proc:
             self.proc.terminate()
             try:
                 self.out, _ = self.proc.communicate(timeout=5)
             except Exception:
                 self.proc.kill()
+            self.proc = None
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        """Median SM clock and the throttle reasons seen in the marked region
+        (with half a period of slack on each side); if no sample falls in it,
+        the sample closest to its middle, flagged as such."""
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in (self.out or "").strip().splitlines():
             f = [t.strip() for t in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                rows.append((self._stamp(f[0]), float(f[2]), float(f[3]),
+                             {n for n, v in zip(names, f[6:10]) if v.lower().startswith("active")}))
             except ValueError:
                 continue
-            for name, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not rows:
+            return out
+        inside = rows
+        if self.t0 is not None and self.t1 is not None:
+            slack = self.PERIOD_MS / 2000.0
+            inside = [r for r in rows if r[0] is not None and
+                      self.t0 - slack <= r[0] <= self.t1 + slack]
+            if not inside:
+                mid = 0.5 * (self.t0 + self.t1)
+                timed = [r for r in rows if r[0] is not None]
+                if not timed:
+                    return out
+                inside = [min(timed, key=lambda r: abs(r[0] - mid))]
+                out["nearest_sample_outside_region"] = True
+        out["sm_mhz"] = statistics.median(r[1] for r in inside)
+        out["sm_max_mhz"] = inside[-1][2]
+        out["reasons"] = sorted(set().union(*[r[3] for r in inside]))
+        out["samples"] = len(inside)
+        return out
 
 
 def gpu_uuid(dev: int) -> str:
@@ -505,16 +543,20 @@ def run_ours(args):
     p = make_params(S, cfg, wl, proj, topk)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    clocks = ClockSampler(gpu_uuid(local)).start()  # running before the timed region
     for _ in range(args.warmup):
         train_step(ctx, p, cfg, X, L, Y).free()
 
     # timed region: K trees, device time per tree from events on the stream
-    clocks = ClockSampler(gpu_uuid(local))
     barrier()
     wall0 = time.perf_counter()
-    with clocks:
+    clocks.mark_start()
+    try:
         times, evals, launches = time_steps(ctx, p, X, L, Y, args.steps, flush, stream, cfg)
         barrier()
+    finally:
+        clocks.mark_end()
+        clocks.stop()
     wall = time.perf_counter() - wall0
 
     # per-kernel timing: the same K trees again, every launch bracketed by

@@ -53,3 +53,28 @@ def test_oracle_targets_of_boosting_workloads():
     for name, cfg in W.SETTINGS.items():
         if cfg.get("rounds"):
             assert cfg["criterion"] == "mse" and 0 < cfg["lr"] <= 1 and cfg["n_trees"] == 1
+
+
+def test_clock_sampler_keeps_the_marked_region():
+    import datetime
+
+    import bench
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(ms, mhz, power_cap="Not Active", thermal="Not Active"):
+        ts = (base + datetime.timedelta(milliseconds=ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.0, 0x0, Not Active, Not Active, {thermal}, {power_cap}"
+
+    s = bench.ClockSampler("GPU-x")
+    s.out = "\n".join([line(0, 1000, thermal="Active"), line(50, 2070), line(100, 2040),
+                       line(150, 2070, power_cap="Active"), line(200, 900)])
+    t = base.timestamp()
+    s.t0, s.t1 = t + 0.04, t + 0.16  # samples at 50, 100, 150 ms fall inside
+    r = s.summary()
+    assert r["samples"] == 3 and r["sm_mhz"] == 2070 and r["sm_max_mhz"] == 2070
+    assert r["reasons"] == ["sw_power_cap"]  # the thermal sample lies outside
+    s.t0, s.t1 = t + 0.060, t + 0.070  # shorter than a period: within the slack
+    assert s.summary()["samples"] == 1
+    s.t0, s.t1 = t + 1.0, t + 1.1  # no sample near: the closest one, flagged
+    r = s.summary()
+    assert r["samples"] == 1 and r["sm_mhz"] == 900 and r["nearest_sample_outside_region"]
