@@ -226,3 +226,41 @@ def test_degenerate_targets(ctx):
     scores, cls = c.predict(X, want_class=True)
     assert np.array_equal(scores, r.F) and np.all(cls == 0)
     assert np.allclose(c.train_loss, r.train_loss, rtol=1e-12)
+
+
+def test_boost_with_adaptive_pso_trees_matches_oracle(ctx):
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.tanh_regression(3000, 6, seed=15)
+    M, eta = 3, 0.5
+    gp = S.make_params("mse", 0, n_particles=16, n_iters=10, n_bins=32, min_leaf=10,
+                       max_depth=3, seed=2, apso=True)
+    b = ctx.train_boost(gp, wl.X, wl.y, M, eta)
+    op = oracle_params(O, "mse", 0, 16, 10, 32, min_leaf=10, max_depth=3, seed=2)
+    op.apso = 1
+    r = O.train_boost(op, wl.X, wl.y, M, eta)
+    F = np.full(len(wl.y), np.float32(r.base), np.float32)
+    for m in range(M):
+        q = oracle_params(O, "mse", 0, 16, 10, 32, min_leaf=10, max_depth=3, seed=2 + m + 1)
+        q.apso = 1
+        if _check_tree_up_to_near_ties(b.tree(m).export(0), r.trees[m], q, wl.X, None,
+                                       (wl.y - F).astype(np.float32)):
+            break
+        assert b.train_loss[m] == pytest.approx(r.train_mse[m], rel=1e-12)
+        _, v, _ = O.predict(q, r.trees[m], wl.X)
+        F = (F + np.float32(eta) * v.astype(np.float32)).astype(np.float32)
+    b.free()
+
+
+def test_boost_with_bf16_trees(ctx):
+    # the tensor-core form's trees: every split is scored in FP32, the loss
+    # falls every round and prediction reproduces the reported loss
+    from paper_2208_07023_gb300 import binding as S
+    wl = W.tanh_regression(20000, 32, seed=16)
+    gp = S.make_params("mse", 0, n_particles=32, n_iters=10, n_bins=64, min_leaf=20,
+                       max_depth=4, seed=3, proj=S.SLM_PROJ_BF16_TOPK, topk=8)
+    b = ctx.train_boost(gp, wl.X, wl.y, 4, 0.5)
+    assert np.all(np.diff(b.train_loss) < 0)
+    pred = b.predict(wl.X)
+    mse = np.mean((wl.y.astype(np.float64) - pred.astype(np.float64)) ** 2)
+    assert mse == pytest.approx(b.train_loss[-1], rel=1e-12)
+    b.free()
