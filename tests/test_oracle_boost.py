@@ -177,3 +177,7 @@ def test_degenerate_targets():
     assert all(t.kind[0] == 0 for t in c.trees)
     assert np.all(c.F == c.F[0]) and np.all(np.diff(c.train_loss) < 0)
     assert c.train_loss[0] == pytest.approx(np.log1p(2 * np.exp(-0.5)), rel=1e-6)
+    # zero rounds: every score 0, every class tied: the lowest class
+    z = O.train_boost_cls(p, X, lab, 3, 0, 0.5)
+    F, cls = O.boost_predict_cls(p, z, X)
+    assert np.all(F == 0) and np.all(cls == 0)
