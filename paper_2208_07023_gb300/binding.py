@@ -170,6 +170,7 @@ class Forest:
         self.handle = C.c_void_p(handle)
 
     def info(self):
+        """slm_forest_info: trees, heap size, features and evaluations so far."""
         nt, hs, d, ev = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
         self.ctx._check(lib().slm_forest_info(self.handle, C.byref(nt), C.byref(hs),
                                               C.byref(d), C.byref(ev)))
@@ -177,11 +178,13 @@ class Forest:
                 "evaluations": ev.value}
 
     def grow_level(self) -> int:
+        """slm_grow_level: grows every tree one level; returns the nodes split."""
         n = C.c_int32()
         self.ctx._check(lib().slm_grow_level(self.ctx.handle, self.handle, C.byref(n)))
         return n.value
 
     def export(self, tree: int = 0) -> dict:
+        """slm_forest_export: tree `tree`'s heap arrays as numpy arrays."""
         inf = self.info()
         H, d = inf["heap_size"], inf["d"]
         out = {"kind": np.empty(H, np.int32), "dir": np.empty((H, d), np.float32),
@@ -197,6 +200,7 @@ class Forest:
         return out
 
     def free(self):
+        """slm_forest_free (idempotent)."""
         if self.handle:
             lib().slm_forest_free(self.handle)
             self.handle = C.c_void_p(None)
@@ -216,6 +220,7 @@ class _RoundTree(Forest):
         self._owner = owner  # keeps the boost alive while the tree is used
 
     def free(self):
+        """The boost owns its trees: nothing to free here."""
         self.handle = C.c_void_p(None)
 
 
@@ -229,6 +234,7 @@ class Boost:
         self.train_mse = train_loss
 
     def info(self) -> dict:
+        """slm_boost_info: rounds, outputs, base and learning rate."""
         m, k, b, lr = C.c_int32(), C.c_int32(), C.c_float(), C.c_float()
         self.ctx._check(lib().slm_boost_info(self.handle, C.byref(m), C.byref(k), C.byref(b),
                                              C.byref(lr)))
@@ -254,6 +260,7 @@ class Boost:
         return (out, cls) if want_class else out
 
     def free(self):
+        """slm_boost_free (idempotent)."""
         if self.handle:
             lib().slm_boost_free(self.handle)
             self.handle = C.c_void_p(None)
@@ -279,23 +286,27 @@ class Proposal:
         self.ctx, self.handle = ctx, handle
 
     def free(self):
+        """slm_proposal_free (idempotent)."""
         if self.handle:
             lib().slm_proposal_free(self.handle)
             self.handle = C.c_void_p(None)
 
     def set(self, params: dict):
+        """slm_proposal_set: the network's weights from numpy arrays."""
         arrs = [_as(np.ascontiguousarray(params[k], dtype=np.float32), np.float32)
                 for k in _PROP_ORDER]
         self.ctx._check(lib().slm_proposal_set(self.ctx.handle, self.handle,
                                                *[_ptr(a) for a in arrs]))
 
     def get(self) -> dict:
+        """slm_proposal_get: the network's weights as numpy arrays."""
         out = {k: np.empty(PROP_SHAPES[k], np.float32) for k in _PROP_ORDER}
         self.ctx._check(lib().slm_proposal_get(self.ctx.handle, self.handle,
                                                *[_ptr(out[k]) for k in _PROP_ORDER]))
         return out
 
     def forward(self, stats) -> np.ndarray:
+        """slm_proposal_forward: outputs for a batch of node statistics."""
         stats = np.ascontiguousarray(stats, dtype=np.float32).reshape(-1, PROP_IN)
         out = np.empty((stats.shape[0], PROP_OUT), np.float32)
         self.ctx._check(lib().slm_proposal_forward(self.ctx.handle, self.handle, _ptr(stats),
@@ -303,6 +314,7 @@ class Proposal:
         return out
 
     def loss_grad(self, stats, dims, targets):
+        """slm_proposal_loss_grad: loss and gradients of a batch."""
         stats = np.ascontiguousarray(stats, dtype=np.float32).reshape(-1, PROP_IN)
         n = stats.shape[0]
         dims = np.ascontiguousarray(dims, dtype=np.int32)
@@ -315,6 +327,7 @@ class Proposal:
         return loss.value, g
 
     def train(self, stats, dims, targets, epochs=10, batch=64, lr=1e-3, seed=1):
+        """slm_proposal_train: Adam steps on (statistics, direction) pairs."""
         stats = _as(stats, np.float32)
         dims = _as(dims, np.int32)
         targets = _as(targets, np.float32)
@@ -343,6 +356,7 @@ class Context:
             raise SlmError(st, buf.value.decode(errors="replace"))
 
     def close(self):
+        """slm_destroy (idempotent)."""
         if self.handle:
             lib().slm_destroy(self.handle)
             self.handle = C.c_void_p(None)
@@ -355,6 +369,7 @@ class Context:
 
     # -- learned proposal ---------------------------------------------------
     def node_stats(self, X, labels=None, n_classes=0, y=None, sample_idx=None, weights=None):
+        """slm_node_stats: the proposal network's input statistics of nodes."""
         X = _as(X, np.float32)
         labels, y = _as(labels, np.int32), _as(y, np.float32)
         sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
@@ -367,14 +382,17 @@ class Context:
         return out
 
     def proposal(self, seed: int = 1) -> Proposal:
+        """slm_proposal_create: a network with Glorot-initialised weights."""
         h = C.c_void_p()
         self._check(lib().slm_proposal_create(self.handle, seed, C.byref(h)))
         return Proposal(self, h)
 
     def use_proposal(self, prop: Optional[Proposal]):
+        """slm_use_proposal: the network seeded searches use."""
         self._check(lib().slm_use_proposal(self.handle, prop.handle if prop else None))
 
     def swarm_seed(self, seed, node_uid, n_particles, d, mu_hat, rho) -> np.ndarray:
+        """slm_swarm_seed: seeded starting positions of one swarm."""
         mu_hat = np.ascontiguousarray(mu_hat, dtype=np.float32)
         rho = np.ascontiguousarray(rho, dtype=np.float32)
         pos = np.empty((n_particles, d), np.float32)
@@ -384,9 +402,11 @@ class Context:
 
     # -- diagnostics -------------------------------------------------------
     def profile(self, on: bool):
+        """slm_profile: per-launch timing with CUDA events on or off."""
         self._check(lib().slm_profile(self.handle, 1 if on else 0))
 
     def kernel_stats(self) -> dict:
+        """slm_kernel_stats: launches, pairs and milliseconds per kernel class."""
         out = {}
         for k, name in enumerate(KERNELS):
             n, ms, pairs = C.c_int64(), C.c_double(), C.c_double()
@@ -396,31 +416,39 @@ class Context:
         return out
 
     def launch_count(self) -> int:
+        """slm_launch_count: kernels launched by this context."""
         n = C.c_int64()
         self._check(lib().slm_launch_count(self.handle, C.byref(n)))
         return n.value
 
     def test_hooks(self, first_wait_polls: int = -1, fail_alloc_after: int = 0):
+        """slm_test_hooks: forced wait limit and allocation failure (tests only)."""
         self._check(lib().slm_test_hooks(self.handle, first_wait_polls, fail_alloc_after))
 
     def set_node_search(self, on: bool):
+        """slm_set_node_search: persistent whole-search kernel for small nodes."""
         self._check(lib().slm_set_node_search(self.handle, 1 if on else 0))
 
     def last_node_search(self) -> int:
+        """slm_last_node_search: CTAs per node of the last persistent search."""
         n = C.c_int32()
         self._check(lib().slm_last_node_search(self.handle, C.byref(n)))
         return n.value
 
     def set_small_nodes(self, max_entries: int = 4096, min_pairs: int = -1):
+        """slm_set_small_nodes: the warp-per-particle histogram's thresholds."""
         self._check(lib().slm_set_small_nodes(self.handle, max_entries, min_pairs))
 
     def set_tuning(self, on: bool):
+        """slm_set_tuning: projection tile and histogram cluster tuning on/off."""
         self._check(lib().slm_set_tuning(self.handle, 1 if on else 0))
 
     def force_tiles(self, pg: int = 0, ctas_per_sm: int = 0, gather: bool = False):
+        """slm_force_tiles: fixed projection tiles (pg = 0 releases them)."""
         self._check(lib().slm_force_tiles(self.handle, pg, ctas_per_sm, 1 if gather else 0))
 
     def tuning_stats(self) -> dict:
+        """slm_tuning_stats: tuner passes and the last tiles and cluster size."""
         n, pg, cps, hc = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
         self._check(lib().slm_tuning_stats(self.handle, C.byref(n), C.byref(pg), C.byref(cps),
                                            C.byref(hc)))
@@ -428,6 +456,7 @@ class Context:
                 "last_hist_cluster": hc.value}
 
     def tuned_shapes(self) -> list:
+        """slm_tuned_shapes: every tuned shape and its choice."""
         n = C.c_int32()
         self._check(lib().slm_tuned_shapes(self.handle, 0, C.byref(n), None, None, None, None,
                                            None, None, None))
@@ -440,12 +469,15 @@ class Context:
                 for i in range(m)]
 
     def set_graphs(self, on: bool):
+        """slm_set_graphs: CUDA-graph capture of the search loops."""
         self._check(lib().slm_set_graphs(self.handle, 1 if on else 0))
 
     def set_projection_tma(self, on: bool):
+        """slm_set_projection_tma: tensor-map staging as a tuned candidate."""
         self._check(lib().slm_set_projection_tma(self.handle, 1 if on else 0))
 
     def graph_stats(self) -> dict:
+        """slm_graph_stats: graph launches, reuses, updates, instantiations."""
         a, r, b, c = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
         self._check(lib().slm_graph_stats(self.handle, C.byref(a), C.byref(r), C.byref(b),
                                           C.byref(c)))
@@ -454,12 +486,14 @@ class Context:
 
     # -- raw draws -------------------------------------------------------
     def swarm_uniforms(self, seed, node_uid, t, n_particles, d, purpose):
+        """slm_swarm_uniforms: one swarm stream's uniforms [P, d]."""
         u = np.empty((n_particles, d), np.float32)
         self._check(lib().slm_swarm_uniforms(self.handle, seed, node_uid, t,
                                              n_particles, d, purpose, _ptr(u)))
         return u
 
     def bootstrap(self, seed, tree_id, n):
+        """slm_bootstrap: tree `tree_id`'s bootstrap multiplicities [n]."""
         w = np.empty(n, np.uint32)
         self._check(lib().slm_bootstrap(self.handle, seed, tree_id, n, _ptr(w)))
         return w
@@ -467,6 +501,7 @@ class Context:
     # -- scoring and search ------------------------------------------------
     def evaluate_swarm(self, params, X, positions, labels=None, y=None,
                        sample_idx=None, weights=None, want_bins=False):
+        """slm_evaluate_swarm: scores (and optionally bins) of given projections."""
         X = _as(X, np.float32)
         positions = _as(positions, np.float32)
         labels, y = _as(labels, np.int32), _as(y, np.float32)
@@ -484,6 +519,8 @@ class Context:
 
     def node_split(self, params, X, labels=None, y=None, sample_idx=None,
                    weights=None, node_uid=0, want_trace=False):
+        """slm_node_split: one node's swarm search; a dict of the split, gB, direction
+        and (want_trace) the gbest loss after every iteration."""
         X = _as(X, np.float32)
         labels, y = _as(labels, np.int32), _as(y, np.float32)
         sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
@@ -504,6 +541,7 @@ class Context:
         return res
 
     def forest_begin(self, params, X, labels=None, y=None) -> Forest:
+        """slm_forest_begin: a forest at its root level (grow with grow_level)."""
         X = _as(X, np.float32)
         labels, y = _as(labels, np.int32), _as(y, np.float32)
         n, d = X.shape
@@ -513,6 +551,7 @@ class Context:
         return Forest(self, h.value)
 
     def train_tree(self, params, X, labels=None, y=None) -> Forest:
+        """slm_train_tree: trees (params.n_trees) grown to completion."""
         X = _as(X, np.float32)
         labels, y = _as(labels, np.int32), _as(y, np.float32)
         n, d = X.shape
@@ -541,6 +580,7 @@ class Context:
         return Boost(self, h.value, loss[:n_rounds])
 
     def predict(self, forest: Forest, X, want_leaf=False):
+        """slm_predict: classes (vote), values (mean) and optionally leaf ids."""
         X = _as(X, np.float32)
         n, d = X.shape
         nt = forest.info()["n_trees"]
