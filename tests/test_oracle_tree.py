@@ -100,3 +100,75 @@ def test_majority_tie_goes_to_lowest_class():
     lab = np.array([2, 1] * 20, np.int32)
     t = O.train_tree(_params("gini", 3, 3, min_leaf=25), X, lab)
     assert t.kind[0] == 0 and t.leaf_class[0] == 1
+
+
+def _clusters(values_per_cluster):
+    """1-D rows at x = 0, 1, 2, ...: cluster c holds values_per_cluster[c]."""
+    xs, vs = [], []
+    for c, vals in enumerate(values_per_cluster):
+        xs += [float(c)] * len(vals)
+        vs += list(vals)
+    return np.array(xs, np.float32)[:, None], np.array(vs)
+
+
+def test_split_that_keeps_the_class_mix_is_not_made():
+    # Algorithm 2 grows a node only when its children are purer (Sec. II-A,
+    # Eq. 4). Four clusters on a line, each with 10 samples of class 0 and 10
+    # of class 1: with 4 bins every admissible edge leaves both children at
+    # the parent's 50/50 mix, so the best split has zero gain and the root
+    # must stay a leaf.
+    X, lab = _clusters([[0] * 10 + [1] * 10] * 4)
+    lab = lab.astype(np.int32)
+    p = _params("gini", 2, 3, n_bins=4, min_leaf=5)
+    sp = O.node_split(p, X, lab).split
+    # there is an admissible split, and it scores the parent's impurity
+    assert sp["valid"] == 1 and sp["loss"] == pytest.approx(0.5, abs=1e-15)
+    t = O.train_tree(p, X, lab)
+    assert t.kind[0] == 0 and np.all(t.kind[1:] == -1)
+    assert t.weight[0] == 80 and t.leaf_class[0] == 0
+
+
+def test_mse_split_that_does_not_lower_the_loss_is_not_made():
+    # Regression form of the same rule: every cluster has mean 0 and the
+    # same spread, so every admissible split keeps the parent's MSE (1.0).
+    X, y = _clusters([[-1.0, 1.0] * 10] * 4)
+    y = y.astype(np.float32)
+    p = _params("mse", 0, 3, n_bins=4, min_leaf=5)
+    sp = O.node_split(p, X, None, y).split
+    assert sp["valid"] == 1 and sp["loss"] == pytest.approx(1.0, abs=1e-15)
+    t = O.train_tree(p, X, None, y)
+    assert t.kind[0] == 0 and np.all(t.kind[1:] == -1)
+    assert t.leaf_value[0] == pytest.approx(0.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("flip", [False, True])
+def test_right_child_holds_the_samples_at_or_above_the_threshold(flip):
+    # Eqs. 3-4: the "+" side a^T x >= t_b, i.e. bin(z) >= b*, is the right
+    # child 2h+2. Sides are computed here from the stored gB, zmin, inv_w and
+    # b* with the float32 binning (one rounding per operation), not through
+    # the oracle's prediction. 30 samples of one class below 0, 70 of the
+    # other above, so the two children differ in size and class.
+    rng = np.random.default_rng(11)
+    neg = -rng.uniform(1.0, 2.0, 30)
+    pos = rng.uniform(1.0, 2.0, 70)
+    X = np.concatenate([neg, pos]).astype(np.float32)[:, None]
+    lab = np.array([1] * 30 + [0] * 70, np.int32)
+    if flip:
+        lab = 1 - lab
+    p = _params("gini", 2, 2, n_bins=16, min_leaf=5)
+    t = O.train_tree(p, X, lab)
+    assert t.kind[0] == 1
+    a = np.float32(t.dir[0, 0])
+    z = X[:, 0] * a  # d = 1: the fused multiply-add with 0 is one rounding
+    off = (z - np.float32(t.zmin[0])).astype(np.float32)
+    b = np.floor((off * np.float32(t.inv_w[0])).astype(np.float32)).astype(np.int64)
+    b = np.clip(b, 0, p.n_bins - 1)
+    right = b >= t.bin[0]
+    assert 0 < right.sum() < len(X)
+    assert t.weight[2] == right.sum() and t.weight[1] == (~right).sum()
+    assert t.n_right[0] == right.sum() and t.n_left[0] == (~right).sum()
+    # both children are pure: each predicts the class its own side holds
+    assert t.kind[1] == 0 and t.kind[2] == 0
+    assert t.leaf_class[2] == np.bincount(lab[right], minlength=2).argmax()
+    assert t.leaf_class[1] == np.bincount(lab[~right], minlength=2).argmax()
+    assert t.leaf_class[1] != t.leaf_class[2]
