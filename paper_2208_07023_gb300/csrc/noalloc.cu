@@ -103,6 +103,35 @@ __global__ void k_noalloc_iota(int32_t* idx, int64_t n) {
   if (i < n) idx[i] = (int32_t)i;
 }
 
+// Makes `device` current for the call and gives the caller's current device
+// back on every return path: the calling thread's device is the caller's
+// state, not this library's.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == device || cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (ok && prev >= 0) (void)cudaSetDevice(prev);
+  }
+};
+
+// A pointer the kernels of `device` may read or write: device or managed
+// memory visible to that device. Host memory (pageable or pinned) and other
+// GPUs' memory are refused before anything is launched.
+bool on_device(const void* ptr, int device) {
+  if (!ptr) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
 }  // namespace
 }  // namespace slm
 
@@ -121,6 +150,10 @@ extern "C" slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
   if (p->criterion < SLM_GINI || p->criterion > SLM_MSE || p->n_bins < 2 ||
       p->n_bins > kMaxBins || p->min_leaf < 1)
     return SLM_EINVAL;
+  // the FP32 projection only: the tensor-core form needs buffers that depend
+  // on the call's sizes, which this entry point does not have
+  if (p->proj != SLM_PROJ_FP32 && p->proj != SLM_PROJ_BF16_TOPK) return SLM_EINVAL;
+  if (p->proj == SLM_PROJ_BF16_TOPK) return SLM_EUNSUPPORTED;
   const bool mse = p->criterion == SLM_MSE;
   if (!mse && (p->n_classes < 2 || p->n_classes > kMaxClasses)) return SLM_EINVAL;
   if (!mse && (int64_t)p->n_bins * p->n_classes * 4 > kMaxHistBytesPerParticle)
@@ -134,7 +167,12 @@ extern "C" slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
   if (L.total > (size_t)SLM_NOALLOC_SCRATCH_BYTES) return SLM_EUNSUPPORTED;  // too large
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  if (cudaSetDevice(device) != cudaSuccess) return SLM_ECUDA;
+  const DeviceGuard guard(device);
+  if (!guard.ok) return SLM_ECUDA;
+  if (!on_device(X, device) || !on_device(labels, device) || !on_device(y, device) ||
+      !on_device(sample_idx, device) || !on_device(weights, device) ||
+      !on_device(positions, device) || !on_device(out, device))
+    return SLM_EINVAL;
   unsigned char* base = nullptr;
   if (scratch_address(device, &base) != cudaSuccess) return SLM_ECUDA;
   float* Xl = reinterpret_cast<float*>(base + L.xl);
@@ -226,5 +264,6 @@ extern "C" slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return SLM_ECUDA;
-  return err ? SLM_ETIMEOUT : SLM_OK;
+  if (err_is_timeout(err)) return SLM_ETIMEOUT;
+  return err ? SLM_ECUDA : SLM_OK;
 }
