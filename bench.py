@@ -485,6 +485,7 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
 def apply_launch_options(ctx, args):
     ctx.set_graphs(args.graphs == "on")
     ctx.set_projection_tma(args.tma == "on")
+    ctx.set_fused_step(args.fused == "on")
     if args.tiles == "fixed":
         ctx.set_tuning(False)
     elif args.tiles != "auto":
@@ -877,6 +878,9 @@ def main():
     ap.add_argument("--tma", choices=["on", "off"], default="on",
                     help="FP32 projection staging: tensor-map tile copies (on) or "
                          "per-thread asynchronous copies (off)")
+    ap.add_argument("--fused", choices=["on", "off"], default="on",
+                    help="plain FP32 searches: swarm move folded into the projection "
+                         "(two launches per iteration) or separate kernels (three)")
     ap.add_argument("--apso", action="store_true",
                     help="adaptive PSO (FP32 form): the workload's searches adapt inertia "
                          "and learning factors to the swarm's evolutionary state")

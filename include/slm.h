@@ -205,17 +205,24 @@ slm_status slm_evaluate_swarm(slm_ctx* ctx, const slm_params* params,
  * MSE (each part rounded up to 256 bytes); larger calls return
  * SLM_EUNSUPPORTED and do nothing.
  *
- * Same meaning as slm_evaluate_swarm, except: X, labels / y, sample_idx,
- * weights and positions must be device pointers, and out[n_pos] is a device
- * buffer the call fills; work runs on `cuda_stream` of `device`, and the call
- * returns after that stream has finished it. The first call on a device looks
- * up the array's device address (once per device); make that first call
- * before any stream capture. Every call overwrites the array (the call resets
- * what must start fresh), so calls whose work overlaps on the GPU -- on other
- * streams or from other host threads -- race and must be serialised by the
- * caller. Errors: SLM_EINVAL bad arguments, labels or sample indices;
- * SLM_EUNSUPPORTED sizes beyond the array; SLM_ECUDA a CUDA call failed;
- * SLM_ETIMEOUT a staged copy did not complete. */
+ * Same meaning as slm_evaluate_swarm with params->proj = SLM_PROJ_FP32
+ * (this entry point scores with the FP32 projection only:
+ * SLM_PROJ_BF16_TOPK returns SLM_EUNSUPPORTED, an unknown proj SLM_EINVAL),
+ * except: X, labels / y, sample_idx, weights and positions must be device
+ * (or managed) memory of `device`, and out[n_pos] is a device buffer the call
+ * fills; a host or another GPU's pointer returns SLM_EINVAL before anything
+ * is launched. Work runs on `cuda_stream` of `device`; the call synchronises
+ * that stream twice (it reads a validation word and the kernels' error word
+ * back) and returns after the stream has finished its work. The calling
+ * thread's current device is restored before the call returns. The first
+ * call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture. Every call overwrites the
+ * array (the call resets what must start fresh), so calls whose work
+ * overlaps on the GPU -- on other streams or from other host threads -- race
+ * and must be serialised by the caller. Errors: SLM_EINVAL bad arguments,
+ * pointers, labels or sample indices; SLM_EUNSUPPORTED sizes beyond the
+ * array or the BF16 form; SLM_ECUDA a CUDA call failed or a kernel reported
+ * an error; SLM_ETIMEOUT a staged copy did not complete. */
 slm_status slm_evaluate_swarm_noalloc(int device, void* cuda_stream,
                                       const slm_params* params, const float* X,
                                       int64_t n, int32_t d,
@@ -535,6 +542,18 @@ slm_status slm_set_graphs(slm_ctx* ctx, int32_t on);
  * issuing thread, 128-byte swizzle); on = 0: by per-thread asynchronous
  * copies. The projected values are identical either way. */
 slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
+/* on != 0 (the default): plain FP32 searches (no adaptive PSO, no BF16
+ * form, no persistent node search) whose padded swarm is 16, 32, 48 or 64
+ * particles, whose positions fit in 96 KB of shared memory and for which
+ * no projection tiles are forced (slm_force_tiles) fold the
+ * swarm move of Eq. pso-1 into the projection: one iteration is the
+ * projection (which first takes the gbest step of the previous evaluation,
+ * Algorithm 1, and moves every particle) and the histogram pass (which
+ * leaves the gB-independent terms of the next move), two launches instead
+ * of three, and each row tile is projected onto all particles at once.
+ * on = 0: the projection, histogram and move kernels. Results are identical
+ * either way. *searches (optional) = searches run folded so far. */
+slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
 /* Graph launches of the context: in total, of kept graphs launched again
  * unchanged, updated in place, and instantiated anew (any may be NULL). */
 slm_status slm_graph_stats(slm_ctx* ctx, int64_t* launches, int64_t* reuses,

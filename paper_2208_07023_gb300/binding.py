@@ -96,6 +96,7 @@ def lib():
             "slm_launch_count": ([vp, P(i64)], C.c_int),
             "slm_set_graphs": ([vp, i32], C.c_int),
             "slm_set_projection_tma": ([vp, i32], C.c_int),
+            "slm_set_fused_step": ([vp, i32, P(i64)], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
             "slm_set_node_search": ([vp, i32], C.c_int),
@@ -475,6 +476,13 @@ class Context:
     def set_projection_tma(self, on: bool):
         """slm_set_projection_tma: tensor-map staging as a tuned candidate."""
         self._check(lib().slm_set_projection_tma(self.handle, 1 if on else 0))
+
+    def set_fused_step(self, on: bool) -> int:
+        """slm_set_fused_step: fold the swarm move into the projection (plain FP32
+        searches); returns the searches run folded so far."""
+        n = C.c_int64()
+        self._check(lib().slm_set_fused_step(self.handle, 1 if on else 0, C.byref(n)))
+        return n.value
 
     def graph_stats(self) -> dict:
         """slm_graph_stats: graph launches, reuses, updates, instantiations."""

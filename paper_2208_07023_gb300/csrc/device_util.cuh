@@ -135,6 +135,72 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
 constexpr int kWaitPolls = 1 << 20;  // bounded: a lost copy ends the kernel, not the GPU
 
 
+// ---- per-thread async copies ---------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Row of entry e (e < pr.E): gathered from the base rows when pr.gidx is set.
+__device__ __forceinline__ const float* row_of(const Problem& pr, int64_t e) {
+  return pr.gidx ? pr.Xg + (int64_t)__ldg(pr.gidx + e) * pr.d : pr.X + e * pr.d;
+}
+
+// Algorithm 1, gbest step of node a after evaluation t, as seen by one warp:
+// the particle with the best score strictly better than gold (at t = 0 every
+// particle, gold unset), ties to the lower index; -1 if none. Lane 0 also
+// returns that particle's score in *best_res.
+__device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
+                            EvalRes* best_res) {
+  const int lane = threadIdx.x & 31;
+  int bi = -1;
+  EvalRes be = invalid_res();
+  for (int p = lane; p < pr.P; p += 32) {
+    const EvalRes e = cur[p];
+    if (!(t == 0 || better(e, gold, pr.crit))) continue;
+    if (bi < 0 || better(e, be, pr.crit)) {
+      bi = p;
+      be = e;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    const EvalRes o = shfl_res(be, lane ^ off);
+    bool take;
+    if (oi < 0)
+      take = false;
+    else if (bi < 0)
+      take = true;
+    else if (better(o, be, pr.crit))
+      take = true;
+    else if (better(be, o, pr.crit))
+      take = false;
+    else
+      take = oi < bi;
+    if (take) {
+      bi = oi;
+      be = o;
+    }
+  }
+  if (lane == 0) *best_res = be;
+  return bi;
+}
+
 // Algorithm 1, pbest step of particle p after evaluation t (one warp): strict
 // "<" against the particle's best so far; the position is kept on improvement.
 __device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, int a, int p,

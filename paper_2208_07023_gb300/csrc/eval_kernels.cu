@@ -344,34 +344,10 @@ __device__ EvalRes block_scan_mse(const uint32_t* cnt, const long long* s, const
   return sc.res;
 }
 
-// ---- async copies -------------------------------------------------------------
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src),
-               "r"(bytes));
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, int bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src),
-               "r"(bytes));
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::);
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
 // ---- projection -------------------------------------------------------------------
 
 constexpr size_t kProjSmem = sizeof(float) * 2 * (kTS * kXS + kPGMax * kXS);
 
-// Row of entry e (e < pr.E): gathered from the base rows when pr.gidx is set.
-__device__ __forceinline__ const float* row_of(const Problem& pr, int64_t e) {
-  return pr.gidx ? pr.Xg + (int64_t)__ldg(pr.gidx + e) * pr.d : pr.X + e * pr.d;
-}
 
 // Stages one kKC-feature chunk of a work unit's rows and PG positions.
 template <int PG>
@@ -577,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // smem row r stored at c ^ (r mod 8)) keeps the float4 reads of 8 lanes on
 // 8 consecutive rows on distinct banks. Features past d and rows past the
 // tensor's end arrive as zeros. Every wait is bounded; a copy that does not
-// land sets the error word 3 and ends the kernel after the copies in flight.
+// land sets the error word (kErrCopyTimeout) and ends the kernel after the copies in flight.
 
 constexpr int kTmaRowBytes = kKC * 4;                   // one box row: 128 B
 constexpr int kTmaXBytes = kTS * kTmaRowBytes;          // 32 KB
@@ -644,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // a copy did not land: record it, give the copies in flight a bounded
       // chance to finish, and end
       if (threadIdx.x == 0) {
-        if (sw.err) atomicExch(sw.err, 3);
+        if (sw.err) atomicExch(sw.err, kErrCopyTimeout);
         if (s + 1 < n_st) mbar_wait(&s_bar[(s + 1) & 1], (uint32_t)(((s + 1) >> 1) & 1),
                                     kWaitPolls);
       }
@@ -767,47 +743,6 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 
 
-// Algorithm 1, gbest step of node a after evaluation t, as seen by one warp:
-// the particle with the best score strictly better than gold (at t = 0 every
-// particle, gold unset), ties to the lower index; -1 if none. Lane 0 also
-// returns that particle's score in *best_res.
-__device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
-                            EvalRes* best_res) {
-  const int lane = threadIdx.x & 31;
-  int bi = -1;
-  EvalRes be = invalid_res();
-  for (int p = lane; p < pr.P; p += 32) {
-    const EvalRes e = cur[p];
-    if (!(t == 0 || better(e, gold, pr.crit))) continue;
-    if (bi < 0 || better(e, be, pr.crit)) {
-      bi = p;
-      be = e;
-    }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-    const EvalRes o = shfl_res(be, lane ^ off);
-    bool take;
-    if (oi < 0)
-      take = false;
-    else if (bi < 0)
-      take = true;
-    else if (better(o, be, pr.crit))
-      take = true;
-    else if (better(be, o, pr.crit))
-      take = false;
-    else
-      take = oi < bi;
-    if (take) {
-      bi = oi;
-      be = o;
-    }
-  }
-  if (lane == 0) *best_res = be;
-  return bi;
-}
-
 // The particle with the worst score of node a (invalid scores worst, ties
 // to the lower index), as seen by one warp; every lane returns it.
 __device__ int worst_argmax(const Problem& pr, const EvalRes* cur) {
@@ -876,6 +811,39 @@ __device__ __forceinline__ void move_item(const Problem& pr, const Swarm& sw, co
     pos[j] = xn[c];
   }
   if (sw.posb) store_posb4(sw.posb, Pp, pr.dp, a, pi, 4 * q, xn);
+}
+
+// The terms of Eq. pso-1 for particle pi of node a that do not depend on gB,
+// after the pbest step of evaluation t (one warp; t < T): for every feature j,
+// ic = omega v + (c1 r1)(pB - x) and s2 = c2 r2, r1 and r2 the draws of the
+// move to t + 1 (counter (uid, t + 1, pi, j/4)), each operation rounded as in
+// move_item; k_step finishes the move with v' = ic + s2 (gB - x), x' = x + v'.
+__device__ __forceinline__ void premove_particle(const Problem& pr, const Swarm& sw, uint32_t uid,
+                                                 int a, int t, int pi) {
+  const int lane = threadIdx.x & 31;
+  const int d = pr.d, d4 = (d + 3) >> 2;
+  const SwarmCoef& co = sw.co;
+  const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
+  const int64_t row = ((int64_t)a * pr.Pp + pi) * d;
+  const float* x = sw.pos + row;
+  const float* v = sw.vel + row;
+  const float* pb = sw.pbest + row;
+  for (int q = lane; q < d4; q += 32) {
+    const U4 r1 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
+                                (uint32_t)q | (kR1 << 24), k0, k1);
+    const U4 r2 = philox4x32_10(uid, (uint32_t)(t + 1), (uint32_t)pi,
+                                (uint32_t)q | (kR2 << 24), k0, k1);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = 4 * q + c;
+      if (j >= d) break;
+      const float xj = x[j];
+      const float inertia = __fmul_rn(co.inertia, v[j]);
+      const float cog = __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(pb[j], xj));
+      sw.ic[row + j] = __fadd_rn(inertia, cog);
+      sw.s2[row + j] = __fmul_rn(co.c2, uniform24(r2.v[c]));
+    }
+  }
 }
 
 // Fuzzy memberships of the evolutionary factor f in the adaptive PSO states
@@ -1418,7 +1386,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (!mbar_wait(&s_bar[k % kStages], parity, d_first_wait_polls)) {
       // a copy did not land: record it, give the copies in flight a bounded
       // chance to finish, and stop using the stages
-      if (threadIdx.x == 0 && sw.err) atomicExch(sw.err, 3);
+      if (threadIdx.x == 0 && sw.err) atomicExch(sw.err, kErrCopyTimeout);
       for (int j = k; j < n_pieces && j < k + kStages; ++j)
         mbar_wait(&s_bar[j % kStages], (uint32_t)((j / kStages) & 1), kWaitPolls);
       break;
@@ -1555,7 +1523,13 @@ __global__ void __launch_bounds__(kThreads, 3)
     zz[0] = INT_MAX;  // ready for the next iteration
     zz[1] = INT_MIN;
   }
-  if (do_update && warp == 0) pbest_step(pr, sw, a, p, t, res);
+  if (do_update && warp == 0) {
+    pbest_step(pr, sw, a, p, t, res);
+    if (sw.ic && t < sw.T) {
+      __syncwarp();  // the pbest row the lanes just wrote
+      premove_particle(pr, sw, nd.uid, a, t, p);
+    }
+  }
   if (sw.tk_sel) {
     // the last particle of the node to be scored selects the node's top k
     __shared__ int s_last;
@@ -1746,7 +1720,13 @@ __global__ void __launch_bounds__(kThreads)
     zz[0] = INT_MAX;  // ready for the next iteration
     zz[1] = INT_MIN;
   }
-  if (do_update) pbest_step(pr, sw, a, p, t, res);
+  if (do_update) {
+    pbest_step(pr, sw, a, p, t, res);
+    if (sw.ic && t < sw.T) {
+      __syncwarp();  // the pbest row the lanes just wrote
+      premove_particle(pr, sw, nd.uid, a, t, p);
+    }
+  }
 }
 
 // Persistent search of small classification nodes: all T + 1 iterations of

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kMmaThreads)
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, 2 * cols);
-  if (tid == 0 && s_err && sw.err) atomicExch(sw.err, 4);
+  if (tid == 0 && s_err && sw.err) atomicExch(sw.err, kErrMmaTimeout);
 }
 
 // ---- merge of the re-scored particles ----------------------------------------------------

@@ -47,6 +47,9 @@ enum Slot {
   S_FPOS, S_FEAT, W_XS, S_GFULL,
   // adaptive PSO state per node
   S_APSO,
+  // the projection with the move folded in: second position buffer, the
+  // gB-independent move terms, its row tiles
+  S_POS2, S_IC, S_S2, S_STILES,
   N_SLOTS
 };
 
@@ -103,6 +106,10 @@ struct slm_ctx {
   bool graphs = false;
   // FP32 projection of contiguous rows staged by tensor-map tile copies
   bool tma = true;
+  // plain FP32 searches with the swarm move folded into the projection
+  // (k_step: two launches per iteration instead of three)
+  bool fused_step = true;
+  int64_t fused_searches = 0;
   cudaStream_t cap_stream = nullptr;  // records graphs (the caller's stream may
                                       // be the legacy default stream)
   // executable graphs by launch signature (every kernel node's function,
@@ -645,16 +652,37 @@ slm_status setup_bf16(slm_ctx* c, const Problem& pr, const std::vector<NodeDesc>
   return SLM_OK;
 }
 
+// A plain FP32 search whose move is folded into the projection (k_step):
+// positions alternate between pos[0] and pos[1] by iteration parity.
+struct StepPlan {
+  bool on = false;
+  float* pos[2] = {nullptr, nullptr};
+  const WorkTile* tiles = nullptr;
+  int n_tiles = 0;
+  int grid = 0;
+};
+
 // One scoring pass of every (node, particle) of a batch; with a swarm
 // (co != null) the pass ends with the swarm update of iteration t.
-slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
+slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
                        const std::vector<NodeDesc>& nodes, int n_tiles, double pairs,
                        int32_t* bins_out, int t, const SwarmCoef* co, int S,
-                       const Bf16Plan* bp = nullptr, const HistPlan* hp = nullptr) {
+                       const Bf16Plan* bp = nullptr, const HistPlan* hp = nullptr,
+                       const StepPlan* sp = nullptr) {
   const int A = (int)nodes.size();
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
   const int cap = c->cur.cps * c->n_sm;
+  Swarm sw = sw_in;
+  if (sp && sp->on) {
+    // iteration t: move (t > 0) and project in one launch; the histogram
+    // kernels score x_t in pos[t & 1] and leave the next move's terms
+    sw.pos = sp->pos[t & 1];
+    const float* prev = sp->pos[t > 0 ? (t - 1) & 1 : 0];
+    CK(launch(c, SLM_K_PROJECT, pairs, [&] {
+      return launch_step(pr, sw, prev, dn, A, sp->tiles, sp->n_tiles, sp->grid, t, c->stream);
+    }));
+  }
   if (bp && bp->on) {
     // bfloat16 scores of every particle on the tensor cores
     const Bf16Plan& b = *bp;
@@ -690,7 +718,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
                 [&] { return launch_move(pr, sw, dn, A, t, *co, c->stream); }));
     return SLM_OK;
   }
-  if (n_tiles)
+  if (n_tiles && !(sp && sp->on))
     CK(launch(c, SLM_K_PROJECT, pairs, [&] {
       return launch_project(pr, sw, dt, n_tiles, cap, c->stream, c->cur.pg, c->cur.gather,
                             c->tma && c->cur.tma ? A : 0);
@@ -719,7 +747,9 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw,
       return launch_apso(psw, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
                          hp ? hp->n_moved : 0);
     }));
-  if (co && !sw.apso)  // k_apso moves the adaptive swarm itself
+  // k_apso moves the adaptive swarm itself; a folded move needs only the
+  // gbest step of the last evaluation
+  if (co && !sw.apso && (!(sp && sp->on) || t == sw.T))
     CK(launch(c, SLM_K_SWARM_UPDATE, 0.0, [&] {
       return launch_move(psw, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
                          hp ? hp->n_moved : 0);
@@ -1074,7 +1104,8 @@ struct KeyWriter {
     put(w.pos); put(w.vel); put(w.pbest); put(w.gbest); put(w.cur); put(w.pb); put(w.gb);
     put(w.gpart); put(w.giter); put(w.trace); put(w.zmm); put(w.z); put(w.done); put(w.err);
     put(w.T); put(w.sel); put(w.k); put(w.tk_sel); put(w.tk_inv); put(w.tk_pos);
-    put(w.tk_k); put(w.tk_kp); put(w.posb); put(w.apso);
+    put(w.tk_k); put(w.tk_kp); put(w.posb); put(w.apso); put(w.ic); put(w.s2);
+    put(w.co.inertia); put(w.co.c1); put(w.co.c2); put(w.co.seed);
   }
 };
 
@@ -1182,10 +1213,43 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     if (!joined) CK(cudaEventRecord(c->ev_join, st));
     c->last_node_search = S;
   }
+  // plain FP32 searches of whole batches: the move folded into the projection
+  StepPlan stp;
+  if (n_res == 0 && c->fused_step && !c->forced.pg && !bp.on && !p->apso && step_ok(pr)) {
+    const int rows = step_rows(pr);
+    std::vector<WorkTile> st;
+    bool every = true;
+    for (int a = 0; a < A; ++a) {
+      every = every && nodes[a].seg_len > 0;
+      for (int r = 0; r < nodes[a].seg_len; r += rows)
+        st.push_back(WorkTile{a, nodes[a].seg_start + r, std::min(rows, nodes[a].seg_len - r), 0});
+    }
+    CK(prepare_step_kernels(pr));
+    const int grid = step_grid(pr, c->n_sm);
+    if (every && grid > 0 && !st.empty()) {
+      const size_t apd = (size_t)A * pr.Pp * pr.d;
+      CK(ensure(c->ws[S_POS2], sizeof(float) * apd));
+      CK(ensure(c->ws[S_IC], sizeof(float) * apd));
+      CK(ensure(c->ws[S_S2], sizeof(float) * apd));
+      CK(ensure(c->ws[S_STILES], sizeof(WorkTile) * st.size()));
+      CK(cudaMemcpyAsync(c->ws[S_STILES].p, st.data(), sizeof(WorkTile) * st.size(),
+                         cudaMemcpyHostToDevice, c->stream));
+      stp.on = true;
+      stp.pos[0] = sw.pos;
+      stp.pos[1] = ws_ptr<float>(c, S_POS2);
+      stp.tiles = ws_ptr<WorkTile>(c, S_STILES);
+      stp.n_tiles = (int)st.size();
+      stp.grid = grid;
+      sw.ic = ws_ptr<float>(c, S_IC);
+      sw.s2 = ws_ptr<float>(c, S_S2);
+      sw.co = co;
+      c->fused_searches += 1;
+    }
+  }
   if (n_res < A) {
     int S = batch_split(c, pr, nodes);
     slm_ctx::Tiles tl{};
-    if (!bp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), A, &tl))) return s;
+    if (!bp.on && !stp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), A, &tl))) return s;
     HistPlan hp;
     if (!bp.on && (s = setup_hist_plan(c, pr, nodes, in, &hp))) return s;
     if (!bp.on && !hp.on && (s = pick_split(c, pr, sw, nodes, (int)tiles.size(), tl, &S)))
@@ -1208,6 +1272,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       kw.put(hp.on); kw.put(hp.large); kw.put(hp.n_large); kw.put(hp.S_large);
       kw.put(hp.pairs_large); kw.put(hp.small); kw.put(hp.n_small); kw.put(hp.pairs_small);
       kw.put(hp.moved); kw.put(hp.n_moved);
+      kw.put(stp.on); kw.put(stp.pos[1]); kw.put(stp.tiles); kw.put(stp.n_tiles);
+      kw.put(stp.grid);
       if (bp.on) {
         kw.problem(bp.pr_k);
         kw.swarm(bp.sw_k);
@@ -1216,7 +1282,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     }
     s = run_iterations(c, p->n_iters, key, [&](int t) {
       return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp,
-                         &hp);
+                         &hp, &stp);
     });
     c->cur = slm_ctx::Tiles{};
     if (!joined) {
@@ -1317,8 +1383,9 @@ slm_status check_kernel_errors(slm_ctx* c) {
   int32_t e = 0;
   CK(cudaMemcpyAsync(&e, c->ws[S_ERR].p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (e == 4) return fail(c, SLM_ETIMEOUT, "a tensor-core stage did not complete");
-  if (e) return fail(c, SLM_ETIMEOUT, "a bulk copy of the histogram kernel did not complete");
+  if (e == kErrMmaTimeout) return fail(c, SLM_ETIMEOUT, "a tensor-core stage did not complete");
+  if (e == kErrCopyTimeout) return fail(c, SLM_ETIMEOUT, "a staged copy did not complete");
+  if (e) return fail(c, SLM_ECUDA, "a kernel reported error word " + std::to_string(e));
   return SLM_OK;
 }
 
@@ -2680,6 +2747,13 @@ slm_status slm_kernel_stats(slm_ctx* c, int32_t kernel, int64_t* launches,
 slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
   if (!c || !launches) return SLM_EINVAL;
   *launches = c->launches;
+  return SLM_OK;
+}
+
+slm_status slm_set_fused_step(slm_ctx* c, int32_t on, int64_t* searches) {
+  if (!c) return SLM_EINVAL;
+  c->fused_step = on != 0;
+  if (searches) *searches = c->fused_searches;
   return SLM_OK;
 }
 

@@ -99,6 +99,20 @@ struct Problem {
   const double* mscale;
 };
 
+// Codes of the kernels' error word (Swarm::err). Both mean that a bounded
+// wait gave up: the host reports them as SLM_ETIMEOUT; any other non-zero
+// value is reported as SLM_ECUDA.
+constexpr int32_t kErrCopyTimeout = 3;  // a bulk / tensor-map copy did not land
+constexpr int32_t kErrMmaTimeout = 4;   // a tensor-core stage did not complete
+__host__ __device__ inline bool err_is_timeout(int32_t e) {
+  return e == kErrCopyTimeout || e == kErrMmaTimeout;
+}
+
+struct SwarmCoef {
+  float inertia, c1, c2;
+  uint64_t seed;
+};
+
 // Device swarm state of A nodes.
 struct Swarm {
   float* pos;     // [A, Pp, d]
@@ -114,8 +128,7 @@ struct Swarm {
   int32_t* zmm;   // [A, Pp, 2] ordered-int range of each projection
   float* z;       // [P, E] projections of the current iteration
   int32_t* done;  // [A] particle groups of the node scored in this iteration
-  int32_t* err;   // kernel error word (3: a bulk copy did not complete;
-                  // 4: a tensor-core stage did not complete)
+  int32_t* err;   // kernel error word (0, or a kErr* code)
   int32_t T;
   // SLM_PROJ_BF16_TOPK: sel[A, k] re-scored particles of each node in
   // increasing order; non-null when the gbest step runs in k_merge
@@ -138,6 +151,16 @@ struct Swarm {
   // P (the swarm's P) holds the elite candidate, and k_apso, not k_move,
   // takes the gbest step
   struct ApsoState* apso;
+  // the move folded into the next projection (k_step): when ic is set, the
+  // histogram kernels follow each particle's pbest step of evaluation t < T
+  // with the terms of Eq. pso-1 that do not depend on gB, for the move to
+  // t + 1 with the coefficients `co`: ic[A, Pp, d] = omega v + (c1 r1)(pB - x)
+  // and s2[A, Pp, d] = c2 r2; k_step then adds (s2 (gB - x)) after the gbest
+  // step. Positions alternate between two buffers by iteration parity (pos is
+  // the one of the iteration being scored)
+  float* ic;
+  float* s2;
+  SwarmCoef co;
 };
 
 // Adaptive PSO state of one node (Sec. III-B): evolutionary state 1..4
@@ -148,11 +171,6 @@ struct ApsoState {
   int32_t state;
   int32_t pending;
   float c1, c2, w;
-};
-
-struct SwarmCoef {
-  float inertia, c1, c2;
-  uint64_t seed;
 };
 
 // Nodes of at most this many entries are scored by the warp-per-particle
@@ -219,6 +237,23 @@ cudaError_t launch_hist_warp(const Problem& pr, const Swarm& sw, const NodeDesc*
 cudaError_t launch_apso(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
                         int t, SwarmCoef co, cudaStream_t st, const int32_t* list = nullptr,
                         int n_list = 0);
+// The projection of iteration t with the swarm move folded in (classification
+// or MSE searches in the FP32 form): for t > 0 every CTA first takes the gbest
+// step of evaluation t - 1 of each node it projects (the rule of k_move) and
+// forms the node's positions x_t = x + (ic + s2 (gB - x)) from pos_prev (the
+// positions of t - 1) in shared memory; the CTA holding the node's first row
+// tile writes x_t to sw.pos, v_t to sw.vel and the gbest records. Then z and
+// the ranges of every (row tile, all particles) unit, as k_project (the same
+// fused multiply-adds). tiles: step_rows(pr)-row tiles of the nodes in order,
+// every node with at least one. The gbest step of the last evaluation is left
+// to launch_move(t = T).
+bool step_ok(const Problem& pr);
+int step_rows(const Problem& pr);
+int step_grid(const Problem& pr, int n_sm);
+cudaError_t prepare_step_kernels(const Problem& pr);
+cudaError_t launch_step(const Problem& pr, const Swarm& sw, const float* pos_prev,
+                        const NodeDesc* nodes, int A, const WorkTile* tiles, int n_tiles,
+                        int grid, int t, cudaStream_t st);
 // gbest step of iteration t and (t < T) the Eq. pso-1 move of every particle
 // of A nodes to iteration t+1 (of the n_list nodes list[] names, when set).
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,

@@ -1,0 +1,385 @@
+// One iteration's projection of the FP32 swarm search with the swarm move
+// folded in (Sec. III-A, Eq. pso-1 and Algorithm 1; Sec. II-A, Eq. 1).
+//
+// A search iteration t is two launches: k_step (gbest step of evaluation t-1,
+// the move to x_t, z = X_node . x_t and the per-particle ranges) and a
+// histogram kernel (bins, threshold scan, pbest step, and the gB-independent
+// terms of the next move). k_step's unit is one tile of rows of one node with
+// ALL of the node's particles, so every row tile is read from L2 once per
+// iteration; the node's positions live in shared memory for the whole unit.
+//
+// The move needs gB, which needs every particle's score, so it cannot run in
+// the histogram kernel that produces those scores. Every CTA that projects a
+// node therefore takes the node's gbest step itself (a warp argmin over P
+// scores) and forms the node's new positions from the terms the histogram
+// kernel left: x' = x + (ic + s2 (gB - x)), three operations per element. The
+// CTA holding the node's first row tile writes x' and v' back (into the
+// other of two position buffers, so the other CTAs still read x) together
+// with the gbest records, exactly as k_move would.
+//
+// Thread tile: 4 rows (sg + 8i) x PJ particles (pg + 4j) per thread; a warp
+// covers 32 rows x 4 PJ particles; the CTA's 8 warps are RB = 8 / PB row
+// blocks x PB particle blocks, so a unit is 32 RB rows x 4 PJ PB = Pp
+// particles. Every z is the sequential fused multiply-add over the features
+// of k_project (bit-identical results).
+#include <cuda_runtime.h>
+#include <float.h>
+#include <limits.h>
+
+#include "device_util.cuh"
+#include "slm_internal.cuh"
+
+namespace slm {
+namespace {
+
+constexpr int kStepMaxPosBytes = 96 * 1024;  // the node's positions in shared memory
+
+// Row stride of the positions in shared memory: features rounded up to 4
+// (zero-padded) plus 4 floats, so the four particles a warp reads at one
+// feature fall on distinct banks.
+__host__ __device__ inline int step_ldp(int d) { return ((d + 3) & ~3) + 4; }
+
+template <int PJ, int PB>
+__global__ void __launch_bounds__(kThreads, 3)
+    k_step(Problem pr, Swarm sw, const float* __restrict__ pos_prev,
+           const NodeDesc* __restrict__ nodes, int A, const WorkTile* __restrict__ tiles,
+           int n_units, int t) {
+  constexpr int RB = 8 / PB;   // 32-row blocks of a unit
+  constexpr int RT = 32 * RB;  // rows of a unit
+  constexpr int PPB = 4 * PJ;  // particles of a particle block
+  static_assert(PJ % 2 == 0 && RB * PB == 8, "tile shape");
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_lo[64], s_hi[64];  // ordered-int range of each particle
+  __shared__ int s_best;
+  float* xs0 = sm;                // [RT][kXS] rows of a feature chunk, two stages
+  float* xs1 = sm + RT * kXS;
+  float* ps = sm + 2 * RT * kXS;  // [Pp][ldp] the node's positions
+  pdl_trigger();
+  const int d = pr.d, Pp = pr.Pp, P = pr.P;
+  const int ldp = step_ldp(d), dq = (d + 3) & ~3;
+  const int nk = (d + kKC - 1) / kKC;
+  const bool vec = (d & 3) == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sg = lane & 7, pg = lane >> 3;
+  const int rb = warp % RB, pbk = warp / RB;
+  const int my_units =
+      (int)blockIdx.x < n_units ? (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_st = my_units * nk;
+
+  // rows of step s (unit s / nk, feature chunk s % nk) into xb; rows past
+  // the tile and features past d arrive as zeros
+  auto stage = [&](int s, float* xb) {
+    const int ui = s / nk, c = s - ui * nk;
+    const WorkTile wt = tiles[blockIdx.x + ui * gridDim.x];
+    const int k0 = c * kKC, kc = min(kKC, d - k0);
+    if (vec) {
+      for (int q = threadIdx.x; q < RT * (kKC / 4); q += kThreads) {
+        const int r = q >> 3, cc = (q & 7) * 4;
+        const bool ok = r < wt.rows && cc < kc;
+        const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
+        cp_async16(xb + r * kXS + cc, src, ok ? 16 : 0);
+      }
+    } else {
+      for (int q = threadIdx.x; q < RT * kKC; q += kThreads) {
+        const int r = q >> 5, cc = q & 31;
+        const bool ok = r < wt.rows && cc < kc;
+        const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
+        cp_async4(xb + r * kXS + cc, src, ok ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+
+  if (threadIdx.x < 64) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = INT_MIN;
+  }
+  // Within a search the rows and tiles are written before the first
+  // iteration's launch, so iterations t > 0 start fetching them before the
+  // previous kernel's results are visible.
+  if (n_st > 0 && t > 0) stage(0, xs0);
+  pdl_wait();
+  if (n_st > 0 && t == 0) stage(0, xs0);
+
+  // The positions of node a for iteration t in ps (and, from the CTA that
+  // holds the node's first row tile, in sw.pos / sw.vel with the gbest
+  // records of evaluation t - 1).
+  auto node_positions = [&](int a, bool desig) {
+    const int64_t nb = (int64_t)a * Pp * d;
+    if (t == 0) {
+      for (int e = threadIdx.x; e < Pp * dq; e += kThreads) {
+        const int p = e / dq, j = e - p * dq;
+        ps[p * ldp + j] = (p < P && j < d) ? pos_prev[nb + (int64_t)p * d + j] : 0.0f;
+      }
+      __syncthreads();
+      return;
+    }
+    // gbest step of evaluation t - 1 (k_move's rule and double buffering)
+    if (warp == 0) {
+      const EvalRes gold = sw.gb[(int64_t)(t & 1) * A + a];
+      EvalRes be;
+      const int bi = gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t - 1, &be);
+      if (lane == 0) {
+        s_best = bi;
+        if (desig) {
+          const EvalRes g = bi >= 0 ? be : gold;
+          sw.gb[(int64_t)((t - 1) & 1) * A + a] = g;
+          if (bi >= 0) {
+            sw.gpart[a] = bi;
+            sw.giter[a] = t - 1;
+          }
+          if (sw.trace)
+            sw.trace[(int64_t)a * (sw.T + 1) + (t - 1)] =
+                g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
+        }
+      }
+    }
+    __syncthreads();
+    const int bi = s_best;
+    // a new best improved its pbest in evaluation t - 1: gB is that row
+    const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
+    if (desig && bi >= 0)
+      for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = gsrc[j];
+    // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
+    if (vec) {
+      const int d4 = d >> 2;
+      for (int e = threadIdx.x; e < Pp * d4; e += kThreads) {
+        const int p = e / d4, j = 4 * (e - p * d4);
+        float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < P) {
+          const int64_t o = nb + (int64_t)p * d + j;
+          const float4 x = *reinterpret_cast<const float4*>(pos_prev + o);
+          const float4 ic = *reinterpret_cast<const float4*>(sw.ic + o);
+          const float4 s2 = *reinterpret_cast<const float4*>(sw.s2 + o);
+          const float4 g = *reinterpret_cast<const float4*>(gsrc + j);
+          float4 vn;
+          vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
+          vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
+          vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g.z, x.z)));
+          vn.w = __fadd_rn(ic.w, __fmul_rn(s2.w, __fsub_rn(g.w, x.w)));
+          xn.x = __fadd_rn(x.x, vn.x);
+          xn.y = __fadd_rn(x.y, vn.y);
+          xn.z = __fadd_rn(x.z, vn.z);
+          xn.w = __fadd_rn(x.w, vn.w);
+          if (desig) {
+            *reinterpret_cast<float4*>(sw.pos + o) = xn;
+            *reinterpret_cast<float4*>(sw.vel + o) = vn;
+          }
+        }
+        *reinterpret_cast<float4*>(ps + p * ldp + j) = xn;
+      }
+    } else {
+      for (int e = threadIdx.x; e < Pp * dq; e += kThreads) {
+        const int p = e / dq, j = e - p * dq;
+        float xn = 0.0f;
+        if (p < P && j < d) {
+          const int64_t o = nb + (int64_t)p * d + j;
+          const float x = pos_prev[o];
+          const float vn = __fadd_rn(sw.ic[o], __fmul_rn(sw.s2[o], __fsub_rn(gsrc[j], x)));
+          xn = __fadd_rn(x, vn);
+          if (desig) {
+            sw.pos[o] = xn;
+            sw.vel[o] = vn;
+          }
+        }
+        ps[p * ldp + j] = xn;
+      }
+    }
+    __syncthreads();
+  };
+
+  // the CTA's range of each particle of node a, into the node's ranges
+  auto flush_ranges = [&](int a) {
+    if ((int)threadIdx.x < P && s_lo[threadIdx.x] != INT_MAX) {
+      int* zz = sw.zmm + ((int64_t)a * Pp + threadIdx.x) * 2;
+      atomicMin(zz, s_lo[threadIdx.x]);
+      atomicMax(zz + 1, s_hi[threadIdx.x]);
+    }
+    if (threadIdx.x < 64) {
+      s_lo[threadIdx.x] = INT_MAX;
+      s_hi[threadIdx.x] = INT_MIN;
+    }
+  };
+
+  float acc[4][PJ];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
+  int cur_a = -1;
+
+  for (int s = 0; s < n_st; ++s) {
+    const int ui = s / nk, c = s - ui * nk;
+    const WorkTile wt = tiles[blockIdx.x + ui * gridDim.x];
+    if (c == 0 && wt.node != cur_a) {
+      __syncthreads();  // the previous node's positions and ranges are done with
+      if (cur_a >= 0) flush_ranges(cur_a);
+      cur_a = wt.node;
+      node_positions(cur_a, wt.row0 == nodes[cur_a].seg_start);
+    }
+    if (s + 1 < n_st) {
+      stage(s + 1, (s & 1) ? xs0 : xs1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* xr = ((s & 1) ? xs1 : xs0) + (rb * 32 + sg) * kXS;
+    const float* ar = ps + (pbk * PPB + pg) * ldp + c * kKC;
+    const int kc4 = (min(kKC, d - c * kKC) + 3) & ~3;
+#pragma unroll 1
+    for (int k = 0; k < kc4; k += 4) {
+      float4 xv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
+      // feature-outer within each pair of particles: every accumulator takes
+      // features k..k+3 in increasing order
+#pragma unroll
+      for (int j = 0; j < PJ; j += 2) {
+        const float4 a0 = *reinterpret_cast<const float4*>(ar + j * 4 * ldp + k);
+        const float4 a1 = *reinterpret_cast<const float4*>(ar + (j + 1) * 4 * ldp + k);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[i][j] = fmaf(xv[i].x, a0.x, acc[i][j]);
+          acc[i][j + 1] = fmaf(xv[i].x, a1.x, acc[i][j + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[i][j] = fmaf(xv[i].y, a0.y, acc[i][j]);
+          acc[i][j + 1] = fmaf(xv[i].y, a1.y, acc[i][j + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[i][j] = fmaf(xv[i].z, a0.z, acc[i][j]);
+          acc[i][j + 1] = fmaf(xv[i].z, a1.z, acc[i][j + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[i][j] = fmaf(xv[i].w, a0.w, acc[i][j]);
+          acc[i][j + 1] = fmaf(xv[i].w, a1.w, acc[i][j + 1]);
+        }
+      }
+    }
+    if (c == nk - 1) {
+      // unit complete: store z, fold the ranges into the CTA's
+#pragma unroll
+      for (int j = 0; j < PJ; ++j) {
+        const int p = pbk * PPB + pg + 4 * j;
+        float lo = FLT_MAX, hi = -FLT_MAX;
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = rb * 32 + sg + 8 * i;
+          if (r < wt.rows) {
+            const float z = acc[i][j];
+            lo = z < lo ? z : lo;
+            hi = z > hi ? z : hi;
+            any = true;
+            if (p < P) sw.z[(int64_t)p * pr.Ez + wt.row0 + r] = z;
+          }
+        }
+        int olo = any ? f2ord(lo) : INT_MAX, ohi = any ? f2ord(hi) : INT_MIN;
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+          olo = min(olo, __shfl_xor_sync(0xffffffffu, olo, off));
+          ohi = max(ohi, __shfl_xor_sync(0xffffffffu, ohi, off));
+        }
+        if (sg == 0 && olo != INT_MAX && p < P) {
+          atomicMin(&s_lo[p], olo);
+          atomicMax(&s_hi[p], ohi);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
+    }
+    __syncthreads();  // this stage is refilled by the copies of step s + 2
+  }
+  if (cur_a >= 0) flush_ranges(cur_a);  // after the loop's last barrier
+}
+
+// Tile shape of a padded swarm: (PJ, PB).
+bool step_shape(int Pp, int* PJ, int* PB) {
+  switch (Pp) {
+    case 64: *PJ = 8; *PB = 2; return true;
+    case 48: *PJ = 6; *PB = 2; return true;
+    case 32: *PJ = 8; *PB = 1; return true;
+    case 16: *PJ = 4; *PB = 1; return true;
+    default: return false;
+  }
+}
+
+size_t step_smem(const Problem& pr) {
+  int PJ = 0, PB = 0;
+  if (!step_shape(pr.Pp, &PJ, &PB)) return 0;
+  const int RT = 32 * (8 / PB);
+  return sizeof(float) * ((size_t)2 * RT * kXS + (size_t)pr.Pp * step_ldp(pr.d));
+}
+
+const void* step_fn(int Pp) {
+  switch (Pp) {
+    case 64: return (const void*)k_step<8, 2>;
+    case 48: return (const void*)k_step<6, 2>;
+    case 32: return (const void*)k_step<8, 1>;
+    case 16: return (const void*)k_step<4, 1>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+bool step_ok(const Problem& pr) {
+  int PJ = 0, PB = 0;
+  return step_shape(pr.Pp, &PJ, &PB) &&
+         (size_t)pr.Pp * step_ldp(pr.d) * sizeof(float) <= (size_t)kStepMaxPosBytes;
+}
+
+int step_rows(const Problem& pr) {
+  int PJ = 0, PB = 0;
+  return step_shape(pr.Pp, &PJ, &PB) ? 32 * (8 / PB) : 0;
+}
+
+cudaError_t prepare_step_kernels(const Problem& pr) {
+  const void* f = step_fn(pr.Pp);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)step_smem(pr));
+}
+
+int step_grid(const Problem& pr, int n_sm) {
+  const void* f = step_fn(pr.Pp);
+  int per_sm = 0;
+  if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kThreads,
+                                                          step_smem(pr)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * n_sm;
+}
+
+cudaError_t launch_step(const Problem& pr, const Swarm& sw, const float* pos_prev,
+                        const NodeDesc* nodes, int A, const WorkTile* tiles, int n_tiles,
+                        int grid, int t, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  if (!step_ok(pr) || grid <= 0) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_tiles < grid ? n_tiles : grid), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = step_smem(pr);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (pr.Pp) {
+    case 64: return cudaLaunchKernelEx(&cfg, k_step<8, 2>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
+    case 48: return cudaLaunchKernelEx(&cfg, k_step<6, 2>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
+    case 32: return cudaLaunchKernelEx(&cfg, k_step<8, 1>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
+    case 16: return cudaLaunchKernelEx(&cfg, k_step<4, 1>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace slm

@@ -1,0 +1,111 @@
+"""The swarm move folded into the projection (k_step, the default for plain
+FP32 searches of 16, 32, 48 or 64 padded particles) gives the results of the
+projection / histogram / move kernels bit for bit: traces, gbest, splits,
+trees (classification and regression) and bagged forests, over feature
+counts that fill whole 32-feature chunks, end in a partial chunk or are not
+a multiple of 4, every supported padded swarm width, ragged tiles, levels
+whose small nodes take the warp-per-particle histogram, graph-captured
+loops, and zero iterations. The oracle comparisons of the other GPU tests run
+the folded path too, since it is the default."""
+import numpy as np
+import pytest
+
+from paper_2208_07023_gb300 import workloads as W
+from tests.gpu_util import context, gpu_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    a, b = context(), context()
+    b.set_fused_step(False)
+    yield a, b
+    a.close()
+    b.close()
+
+
+def same_tree(fa, fb, n_trees=1):
+    for t in range(n_trees):
+        ga, gb = fa.export(t), fb.export(t)
+        for k in ga:
+            assert np.array_equal(ga[k], gb[k]), (t, k)
+
+
+@pytest.mark.parametrize("n,d,P,T", [
+    (5000, 64, 64, 12),   # whole chunks, the widest swarm
+    (3001, 36, 45, 9),    # a partial chunk, ragged tail, 48 padded particles
+    (2000, 20, 32, 7),    # below one chunk
+    (1500, 30, 7, 6),     # d % 4 != 0, 16 padded particles
+    (7777, 128, 50, 5),
+    (900, 1, 16, 4),      # one feature
+    (2500, 16, 64, 0),    # zero iterations: the initial swarm only
+])
+def test_search_identical_folded_and_separate(ctxs, n, d, P, T):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    before = a.set_fused_step(True)
+    wl = W.gmm(n, d, 5, seed=d + P)
+    p = gpu_params(S, "gini", 5, P, T, 64, min_leaf=5, seed=3)
+    ra = a.node_split(p, wl.X, labels=wl.labels, node_uid=9, want_trace=True)
+    rb = b.node_split(p, wl.X, labels=wl.labels, node_uid=9, want_trace=True)
+    assert a.set_fused_step(True) == before + 1  # the search ran folded
+    assert np.array_equal(ra["trace"], rb["trace"])
+    assert np.array_equal(ra["gbest"], rb["gbest"])
+    for k in ("bin", "q_num", "q_den", "n_left", "n_right", "particle", "iter_of_best"):
+        assert ra[k] == rb[k], k
+
+
+@pytest.mark.parametrize("crit", ["entropy", "mse"])
+def test_search_identical_other_criteria(ctxs, crit):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    if crit == "mse":
+        wl = W.tanh_regression(6000, 24, seed=8)
+        kw = dict(y=wl.y)
+    else:
+        wl = W.gmm(6000, 24, 3, seed=8)
+        kw = dict(labels=wl.labels)
+    p = gpu_params(S, crit, 3, 40, 15, 128, min_leaf=5, seed=4)
+    ra = a.node_split(p, wl.X, node_uid=2, want_trace=True, **kw)
+    rb = b.node_split(p, wl.X, node_uid=2, want_trace=True, **kw)
+    assert np.array_equal(ra["trace"], rb["trace"])
+    assert np.array_equal(ra["gbest"], rb["gbest"]) and ra["bin"] == rb["bin"]
+
+
+@pytest.mark.parametrize("crit,K,P", [("gini", 6, 64), ("mse", 0, 32), ("entropy", 4, 48)])
+def test_tree_identical_folded_and_separate(ctxs, crit, K, P):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    if crit == "mse":
+        wl = W.tanh_regression(20000, 32, seed=4)
+        kw = dict(y=wl.y)
+    else:
+        wl = W.gmm(20000, 32, K, seed=4)
+        kw = dict(labels=wl.labels)
+    # depth 7: the deep levels' small nodes take the warp-per-particle kernel
+    p = gpu_params(S, crit, K, P, 10, 64, min_leaf=10, max_depth=7, seed=5)
+    fa, fb = a.train_tree(p, wl.X, **kw), b.train_tree(p, wl.X, **kw)
+    same_tree(fa, fb)
+    fa.free()
+    fb.free()
+
+
+def test_forest_and_graphs_identical_folded_and_separate(ctxs):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.gmm(30000, 16, 4, seed=6)
+    p = gpu_params(S, "gini", 4, 24, 8, 64, min_leaf=10, max_depth=5, seed=7, n_trees=8,
+                   bootstrap=True)
+    fb = b.train_tree(p, wl.X, labels=wl.labels)
+    fa = a.train_tree(p, wl.X, labels=wl.labels)
+    same_tree(fa, fb, 8)
+    fa.free()
+    a.set_graphs(True)
+    try:
+        fg = a.train_tree(p, wl.X, labels=wl.labels)
+        same_tree(fg, fb, 8)
+        fg.free()
+    finally:
+        a.set_graphs(False)
+    fb.free()

@@ -127,6 +127,7 @@ def test_every_tile_shape_gives_the_same_forest(ctx, P):
     p = gpu_params(S, "gini", 5, P, 8, 128, min_leaf=10, seed=4, max_depth=4, n_trees=3,
                    bootstrap=True)
     ctx.set_tuning(False)
+    ctx.set_fused_step(False)  # the tile shapes of the separate projection kernel
     ref = forest_arrays(ctx, p, wl)
     Pp = (P + 15) // 16 * 16
     for pg in (8, 16, 24, 32, 48):
@@ -145,6 +146,7 @@ def test_every_tile_shape_gives_the_same_forest(ctx, P):
     assert st["shapes"] > n0
     assert st["last_pg"] in (8, 16, 24, 32, 48) and Pp % st["last_pg"] == 0
     assert st["last_ctas_per_sm"] in (1, 2)
+    ctx.set_fused_step(True)
 
 
 @pytest.mark.parametrize("crit,bootstrap", [("gini", True), ("entropy", False),
