@@ -486,6 +486,7 @@ def apply_launch_options(ctx, args):
     ctx.set_graphs(args.graphs == "on")
     ctx.set_projection_tma(args.tma == "on")
     ctx.set_fused_step(args.fused == "on")
+    ctx.set_class_hist(args.class_hist == "on", args.node_step == "on")
     if args.tiles == "fixed":
         ctx.set_tuning(False)
     elif args.tiles != "auto":
@@ -881,6 +882,12 @@ def main():
     ap.add_argument("--fused", choices=["on", "off"], default="on",
                     help="plain FP32 searches: swarm move folded into the projection "
                          "(two launches per iteration) or separate kernels (three)")
+    ap.add_argument("--class-hist", choices=["on", "off"], default="on",
+                    help="classification histograms: latency-oriented kernel (on) or the "
+                         "staged-copy kernel (off)")
+    ap.add_argument("--node-step", choices=["on", "off"], default="off",
+                    help="folded classification searches: gbest step and move in the last "
+                         "histogram block of each node (on) or in every projection block (off)")
     ap.add_argument("--apso", action="store_true",
                     help="adaptive PSO (FP32 form): the workload's searches adapt inertia "
                          "and learning factors to the swarm's evolutionary state")

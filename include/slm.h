@@ -554,6 +554,18 @@ slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
  * on = 0: the projection, histogram and move kernels. Results are identical
  * either way. *searches (optional) = searches run folded so far. */
 slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
+/* on != 0 (the default): the classification searches of the FP32 form
+ * score each iteration with the latency-oriented histogram kernel (entries
+ * loaded 16 bytes at a time with several in flight, class-major histograms
+ * scanned one warp per class, the pbest step spread over the block); on = 0:
+ * with the staged-copy histogram kernel that also serves regression, bins
+ * output and the BF16 form. node_step != 0: in folded searches
+ * (slm_set_fused_step) whose nodes all take that kernel, the last block to
+ * score a node takes the node's gbest step (Algorithm 1) and moves its
+ * particles (Eq. pso-1) once, instead of every projection block doing it;
+ * node_step = 0 (the default): the projection blocks do it. Results are
+ * identical in every combination. */
+slm_status slm_set_class_hist(slm_ctx* ctx, int32_t on, int32_t node_step);
 /* Graph launches of the context: in total, of kept graphs launched again
  * unchanged, updated in place, and instantiated anew (any may be NULL). */
 slm_status slm_graph_stats(slm_ctx* ctx, int64_t* launches, int64_t* reuses,

@@ -97,6 +97,7 @@ def lib():
             "slm_set_graphs": ([vp, i32], C.c_int),
             "slm_set_projection_tma": ([vp, i32], C.c_int),
             "slm_set_fused_step": ([vp, i32, P(i64)], C.c_int),
+            "slm_set_class_hist": ([vp, i32, i32], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
             "slm_set_node_search": ([vp, i32], C.c_int),
@@ -483,6 +484,11 @@ class Context:
         n = C.c_int64()
         self._check(lib().slm_set_fused_step(self.handle, 1 if on else 0, C.byref(n)))
         return n.value
+
+    def set_class_hist(self, on: bool, node_step: bool = True):
+        """slm_set_class_hist: the latency-oriented classification histogram kernel,
+        and whether its last block per node takes the gbest step and the move."""
+        self._check(lib().slm_set_class_hist(self.handle, 1 if on else 0, 1 if node_step else 0))
 
     def graph_stats(self) -> dict:
         """slm_graph_stats: graph launches, reuses, updates, instantiations."""

@@ -77,6 +77,22 @@ __device__ __forceinline__ EvalRes shfl_res(const EvalRes& a, int src) {
 }
 
 
+// c ln c of a count, 0 ln 0 = 0 (natural logarithm, double precision).
+__device__ __forceinline__ double xlogx(uint32_t c) {
+  const double x = (double)c;
+  return c ? x * log(x) : 0.0;
+}
+
+// bin(z) = min(B - 1, floor((z - zmin) * inv_w)), clamped at 0; FP32 with one
+// rounding per operation (no contraction into a fused multiply-add).
+__device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
+  const float off = __fsub_rn(z, zmin);
+  const float pos = __fmul_rn(off, inv_w);
+  int b = (int)floorf(pos);
+  b = b > B - 1 ? B - 1 : b;
+  return b < 0 ? 0 : b;
+}
+
 // ---- bulk copies (TMA) with mbarrier completion -------------------------------
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -160,17 +176,28 @@ __device__ __forceinline__ const float* row_of(const Problem& pr, int64_t e) {
   return pr.gidx ? pr.Xg + (int64_t)__ldg(pr.gidx + e) * pr.d : pr.X + e * pr.d;
 }
 
+// Score written by another CTA of this grid: read through L2.
+__device__ __forceinline__ EvalRes ldcg_res(const EvalRes* r) {
+  EvalRes o;
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(r);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&o);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(EvalRes) / 8); ++i) d[i] = __ldcg(w + i);
+  return o;
+}
+
 // Algorithm 1, gbest step of node a after evaluation t, as seen by one warp:
 // the particle with the best score strictly better than gold (at t = 0 every
 // particle, gold unset), ties to the lower index; -1 if none. Lane 0 also
 // returns that particle's score in *best_res.
+// With l2, the scores are read through L2 (written by other CTAs of the grid).
 __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
-                            EvalRes* best_res) {
+                            EvalRes* best_res, bool l2 = false) {
   const int lane = threadIdx.x & 31;
   int bi = -1;
   EvalRes be = invalid_res();
   for (int p = lane; p < pr.P; p += 32) {
-    const EvalRes e = cur[p];
+    const EvalRes e = l2 ? ldcg_res(cur + p) : cur[p];
     if (!(t == 0 || better(e, gold, pr.crit))) continue;
     if (bi < 0 || better(e, be, pr.crit)) {
       bi = p;
@@ -218,15 +245,6 @@ __device__ __forceinline__ void pbest_step(const Problem& pr, const Swarm& sw, i
   for (int j = lane; j < pr.d; j += 32) sw.pbest[o + j] = sw.pos[o + j];
 }
 
-// Score written by another CTA of this grid: read through L2.
-__device__ __forceinline__ EvalRes ldcg_res(const EvalRes* r) {
-  EvalRes o;
-  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(r);
-  unsigned long long* d = reinterpret_cast<unsigned long long*>(&o);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(EvalRes) / 8); ++i) d[i] = __ldcg(w + i);
-  return o;
-}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);

@@ -44,10 +44,6 @@ namespace slm {
 
 namespace {
 
-__device__ __forceinline__ double xlogx(uint32_t c) {
-  const double x = (double)c;
-  return c ? x * log(x) : 0.0;
-}
 
 // Polls of the histogram kernel's first wait on each staged piece (the
 // drain of copies in flight after a failed wait keeps kWaitPolls). Lowered
@@ -70,13 +66,6 @@ __device__ __forceinline__ double xlogx_t(uint32_t c) {
   return (t && c < (uint32_t)kXlogxTab) ? __ldg(t + c) : xlogx(c);
 }
 
-__device__ __forceinline__ int bin_of(float z, float zmin, float inv_w, int B) {
-  const float off = __fsub_rn(z, zmin);
-  const float pos = __fmul_rn(off, inv_w);
-  int b = (int)floorf(pos);
-  b = b > B - 1 ? B - 1 : b;
-  return b < 0 ? 0 : b;
-}
 
 // ---- threshold scans (one warp, one particle) ----------------------------------
 
@@ -2199,10 +2188,12 @@ cudaError_t set_first_wait_polls(int polls) {
   return cudaMemcpyToSymbol(d_first_wait_polls, &v, sizeof(v));
 }
 
+static std::mutex g_xlogx_mu;
+static std::vector<const double*> g_xlogx_tabs;  // per device, under g_xlogx_mu
+
 cudaError_t ensure_xlogx_table(int device) {
-  static std::mutex mu;
   static std::vector<char> done;
-  std::lock_guard<std::mutex> lock(mu);
+  std::lock_guard<std::mutex> lock(g_xlogx_mu);
   if ((int)done.size() <= device) done.resize(device + 1, 0);
   if (done[device]) return cudaSuccess;
   double* tab = nullptr;
@@ -2214,8 +2205,17 @@ cudaError_t ensure_xlogx_table(int device) {
   if (!(e = cudaGetLastError())) e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   if (!e) e = cudaMemcpyToSymbol(d_xlogx_tab, &tab, sizeof(tab));
-  if (!e) done[device] = 1;
+  if (!e) {
+    done[device] = 1;
+    if ((int)g_xlogx_tabs.size() <= device) g_xlogx_tabs.resize(device + 1, nullptr);
+    g_xlogx_tabs[device] = tab;
+  }
   return e;
+}
+
+const double* xlogx_table(int device) {
+  std::lock_guard<std::mutex> lock(g_xlogx_mu);
+  return device >= 0 && device < (int)g_xlogx_tabs.size() ? g_xlogx_tabs[device] : nullptr;
 }
 
 bool project_group_ok(const Problem& pr, int pg) {

@@ -1,0 +1,565 @@
+// Histogram and threshold scan of classification searches in the FP32 form
+// (Sec. II-A, Eqs. 1, 3-4: bins of the projection, class counts, the
+// weighted Gini or entropy of every interior edge; Algorithm 1's pbest step).
+//
+// One CTA per (node, particle, slice); the S slices of a (node, particle)
+// form a cluster. The kernel is a chain of short phases, each built to keep
+// its latency off the critical path:
+//  * before the previous kernel's results are visible (programmatic
+//    dependent launch): the histogram copies are zeroed and, for the pbest
+//    rank, the Philox draws of the next move are taken;
+//  * binning: every thread keeps 16 entries in flight (four 16-byte loads of
+//    z, of labels, of multiplicities) before their shared-memory atomics,
+//    into the copy of its warp pair; histograms are class-major ([K][B]);
+//  * the copies are summed and rank 0 adds the other ranks' histograms
+//    through distributed shared memory, loads issued back to back;
+//  * the scan: one warp per class turns the class's row of B bins into its
+//    prefix sums (16-byte loads, a shuffle scan), then thread b scores edge
+//    b + 1 (bins <= b left) from the K prefixes at bin b (consecutive threads
+//    read consecutive words) and the class totals at bin B - 1. The edge
+//    rules and arithmetic are those of block_scan_cls
+//    (Gini: the exact rational by 128-bit cross-multiplication; entropy:
+//    c ln c summed in class order; repeated partitions skipped, ties to the
+//    lower edge), so the scores are identical;
+//  * the pbest step and the gB-independent move terms are spread over the
+//    CTA's threads; in a node-step search (Swarm::node_step) the last CTA to
+//    score a node then takes the node's gbest step and moves its particles
+//    (one CTA per node instead of every projection CTA), else k_step
+//    finishes the move.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <float.h>
+#include <limits.h>
+
+#include "device_util.cuh"
+#include "philox.cuh"
+#include "slm_internal.cuh"
+
+namespace slm {
+namespace {
+
+constexpr int kHcCopies = 4;  // histogram copies, one per pair of warps
+constexpr int kHcWarps = kThreads / 32;
+
+struct HcScratch {
+  uint64_t wn[kHcWarps], wd[kHcWarps];
+  double wl[kHcWarps];
+  int wb[kHcWarps];
+  uint32_t wnl[kHcWarps];
+  EvalRes res;
+  float zmin, inv_w;
+  int ok, imp;
+};
+
+__device__ __forceinline__ double xlogx_tab(const double* tab, uint32_t c) {
+  return (tab && c < (uint32_t)kXlogxTab) ? __ldg(tab + c) : xlogx(c);
+}
+
+// Edge order of the scan: a better score, ties to the lower edge (bb < 0:
+// none). Gini scores are rationals n / d (larger is better), entropy a loss.
+template <int CRIT>
+__device__ __forceinline__ bool hc_takes(uint64_t on, uint64_t od, double ol, int ob, uint64_t bn,
+                                         uint64_t bd, double bl, int bb) {
+  if (ob < 0) return false;
+  if (bb < 0) return true;
+  if (CRIT == SLM_GINI) return prod_gt(on, bd, bn, od) || (!prod_gt(bn, od, on, bd) && ob < bb);
+  return ol < bl || (!(bl < ol) && ob < bb);
+}
+
+template <int CRIT>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_hist_cls(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
+               const int32_t* __restrict__ list, int t, int do_update,
+               const double* __restrict__ xtab) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ HcScratch sc;
+  const cg::cluster_group cl = cg::this_cluster();
+  pdl_trigger();
+  const int S = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int a = list ? list[blockIdx.x / S] : (int)blockIdx.x / S;
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int B = pr.B, K = pr.K, W = B * K, d = pr.d;
+  const NodeDesc nd = nodes[a];
+  uint32_t* hc = reinterpret_cast<uint32_t*>(smem);           // [kHcCopies][W]
+  float* c1u = reinterpret_cast<float*>(hc + kHcCopies * W);  // [d] c1 r1 of the next move
+  float* s2u = c1u + d;                                       // [d] c2 r2
+  const bool premove = do_update && sw.ic && t < sw.T && rank == 0;
+
+  // work that does not wait for the projection: zero the copies, draw the
+  // next move's r1 and r2 (counter (uid, t + 1, p, j / 4), as move_item)
+  for (int i = threadIdx.x; i < kHcCopies * W; i += kThreads) hc[i] = 0u;
+  if (premove) {
+    const uint32_t k0 = (uint32_t)sw.co.seed, k1 = (uint32_t)(sw.co.seed >> 32);
+    for (int q = threadIdx.x; q < ((d + 3) >> 2); q += kThreads) {
+      const U4 r1 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)p,
+                                  (uint32_t)q | (kR1 << 24), k0, k1);
+      const U4 r2 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)p,
+                                  (uint32_t)q | (kR2 << 24), k0, k1);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * q + c < d) {
+          c1u[4 * q + c] = __fmul_rn(sw.co.c1, uniform24(r1.v[c]));
+          s2u[4 * q + c] = __fmul_rn(sw.co.c2, uniform24(r2.v[c]));
+        }
+    }
+  }
+  pdl_wait();
+  int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
+  if (threadIdx.x == 0) {
+    const int lo_o = __ldcg(zz), hi_o = __ldcg(zz + 1);
+    float zmin = 0.f, inv_w = 0.f;
+    int ok = 0;
+    if (lo_o != INT_MAX) {
+      const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+      inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+      zmin = lo;
+      ok = (hi > lo) && isfinite(inv_w);
+    }
+    sc.zmin = zmin;
+    sc.inv_w = inv_w;
+    sc.ok = ok;
+  }
+  __syncthreads();
+  const bool ok = sc.ok;
+  const float zmin = sc.zmin, inv_w = sc.inv_w;
+
+  // ---- binning of this rank's slice (starts on a multiple of 4 entries)
+  if (ok) {
+    const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
+    const int r_begin = min(nd.seg_len, rank * chunk);
+    const int r_end = min(nd.seg_len, r_begin + chunk);
+    const int64_t e0 = nd.seg_start + r_begin;
+    const float* zs = sw.z + (int64_t)p * pr.Ez + e0;
+    const int32_t* ls = pr.lab + e0;
+    const uint32_t* ws = pr.w ? pr.w + e0 : nullptr;
+    uint32_t* h = hc + (warp % kHcCopies) * W;  // class-major: h[label * B + bin]
+    const int n = r_end - r_begin;
+    int done = 0;
+    if ((e0 & 3) == 0) {  // 16-byte loads: groups of four entries
+      constexpr int U = 4;  // groups in flight per thread
+      const int n4 = n >> 2;
+      for (int g0 = threadIdx.x; g0 < n4; g0 += U * kThreads) {
+        float4 zv[U];
+        int4 lv[U];
+        uint4 wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int g = g0 + u * kThreads;
+          const bool in = g < n4;
+          zv[u] = in ? __ldcg(reinterpret_cast<const float4*>(zs) + g) : make_float4(0, 0, 0, 0);
+          lv[u] = in ? __ldg(reinterpret_cast<const int4*>(ls) + g) : make_int4(-1, -1, -1, -1);
+          wv[u] = in && ws ? __ldg(reinterpret_cast<const uint4*>(ws) + g) : make_uint4(1, 1, 1, 1);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (lv[u].x < 0) continue;  // past the slice (whole group)
+          atomicAdd(&h[lv[u].x * B + bin_of(zv[u].x, zmin, inv_w, B)], wv[u].x);
+          atomicAdd(&h[lv[u].y * B + bin_of(zv[u].y, zmin, inv_w, B)], wv[u].y);
+          atomicAdd(&h[lv[u].z * B + bin_of(zv[u].z, zmin, inv_w, B)], wv[u].z);
+          atomicAdd(&h[lv[u].w * B + bin_of(zv[u].w, zmin, inv_w, B)], wv[u].w);
+        }
+      }
+      done = n4 << 2;
+    }
+    for (int i = done + (int)threadIdx.x; i < n; i += kThreads) {
+      const int b = bin_of(__ldcg(zs + i), zmin, inv_w, B);
+      atomicAdd(&h[__ldg(ls + i) * B + b], ws ? __ldg(ws + i) : 1u);
+    }
+  }
+  __syncthreads();
+  // ---- the copies into copy 0
+  for (int i = threadIdx.x; i < W; i += kThreads) {
+    uint32_t v = hc[i];
+#pragma unroll
+    for (int c = 1; c < kHcCopies; ++c) v += hc[c * W + i];
+    hc[i] = v;
+  }
+  // ---- the other ranks' histograms into rank 0
+  if (S > 1) {
+    cl.sync();  // every rank's copy 0 is complete
+    if (rank == 0) {
+      for (int i0 = threadIdx.x; i0 < W; i0 += 4 * kThreads) {
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = i0 + u * kThreads < W ? hc[i0 + u * kThreads] : 0u;
+        for (int q = 1; q < S; ++q) {
+          const uint32_t* rh = cl.map_shared_rank(hc, q);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + u * kThreads < W) v[u] += rh[i0 + u * kThreads];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + u * kThreads < W) hc[i0 + u * kThreads] = v[u];
+      }
+    }
+    cl.sync();  // the other ranks' memory is no longer read
+    if (rank != 0) return;
+  }
+  __syncthreads();
+
+  // ---- threshold scan
+  EvalRes res = invalid_res();
+  if (ok) {
+    // 1. each class's row of bins into inclusive prefix sums, in place:
+    //    warp w takes classes w, w + 8, ...; lane l holds bins l*bpl ..
+    const int bpl = (B + 31) >> 5;
+    const bool vec4 = B == 32 * bpl && (bpl & 3) == 0;  // rows of 4-bin words
+    for (int k = warp; k < K; k += kHcWarps) {
+      uint32_t* row = hc + k * B;
+      uint32_t v[8];
+      uint32_t sum = 0;
+      if (vec4) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 4)
+          if (i < bpl) {
+            const uint4 q = *reinterpret_cast<const uint4*>(row + lane * bpl + i);
+            v[i] = q.x;
+            v[i + 1] = q.y;
+            v[i + 2] = q.z;
+            v[i + 3] = q.w;
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int j = lane * bpl + i;
+          v[i] = (i < bpl && j < B) ? row[j] : 0u;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < bpl) sum += v[i];
+      uint32_t incl = sum;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+      }
+      uint32_t run = incl - sum;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < bpl) {
+          run += v[i];
+          v[i] = run;
+        }
+      if (vec4) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 4)
+          if (i < bpl)
+            *reinterpret_cast<uint4*>(row + lane * bpl + i) =
+                make_uint4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int j = lane * bpl + i;
+          if (i < bpl && j < B) row[j] = v[i];
+        }
+      }
+    }
+    __syncthreads();
+    // 2. thread b scores edge e = b + 1 (bins <= b left); an empty bin b
+    //    repeats edge b's split and is skipped
+    const int b = threadIdx.x;
+    uint64_t bn = 0, bd = 0;
+    double bl = 0.0;
+    int bb = -1;
+    uint32_t bnl = 0, ntot = 0;
+    if (b <= B - 2) {
+      uint32_t nl = 0, prev = 0;
+      uint64_t sl = 0, sr = 0;
+      double hl = 0.0, hr = 0.0;
+#pragma unroll 4
+      for (int k = 0; k < K; ++k) {
+        const uint32_t* row = hc + k * B;
+        const uint32_t l = row[b], tk = row[B - 1], r = tk - l;
+        nl += l;
+        ntot += tk;
+        if (b > 0) prev += row[b - 1];
+        if (CRIT == SLM_GINI) {
+          sl += (uint64_t)l * l;
+          sr += (uint64_t)r * r;
+        } else {
+          hl += xlogx_tab(xtab, l);
+          hr += xlogx_tab(xtab, r);
+        }
+      }
+      const uint32_t nr = ntot - nl;
+      if (nl != prev && nl >= (uint32_t)pr.min_leaf && nr >= (uint32_t)pr.min_leaf) {
+        bb = b + 1;
+        bnl = nl;
+        if (CRIT == SLM_GINI) {
+          bn = sl * nr + sr * nl;
+          bd = (uint64_t)nl * nr;
+        } else {
+          bl = ((xlogx_tab(xtab, nl) - hl) + (xlogx_tab(xtab, nr) - hr)) / (double)ntot;
+        }
+      }
+    }
+    // block argmin over the edges (ties to the lower edge)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+      const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+      const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
+      const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
+      const uint32_t onl = __shfl_xor_sync(0xffffffffu, bnl, off);
+      if (hc_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
+        bn = on;
+        bd = od;
+        bl = ol;
+        bb = ob;
+        bnl = onl;
+      }
+    }
+    if (lane == 0) {
+      sc.wn[warp] = bn;
+      sc.wd[warp] = bd;
+      sc.wl[warp] = bl;
+      sc.wb[warp] = bb;
+      sc.wnl[warp] = bnl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const bool in = lane < kHcWarps;
+      bn = in ? sc.wn[lane] : 0;
+      bd = in ? sc.wd[lane] : 0;
+      bl = in ? sc.wl[lane] : 0.0;
+      bb = in ? sc.wb[lane] : -1;
+      bnl = in ? sc.wnl[lane] : 0u;
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) {
+        const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
+        const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
+        const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
+        const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        const uint32_t onl = __shfl_xor_sync(0xffffffffu, bnl, off);
+        if (hc_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
+          bn = on;
+          bd = od;
+          bl = ol;
+          bb = ob;
+          bnl = onl;
+        }
+      }
+      if (lane == 0 && bb >= 0) {
+        // the node's weight: every class's total at the last bin
+        uint32_t nt = 0;
+        for (int k = 0; k < K; ++k) nt += hc[k * B + B - 1];
+        res.valid = 1;
+        res.bin = bb;
+        res.nl = bnl;
+        res.nr = nt - bnl;
+        if (CRIT == SLM_GINI) {
+          res.num = bn;
+          res.den = bd;
+          const uint64_t nden = (uint64_t)nt * res.den;
+          res.loss = (double)(nden - res.num) / (double)nden;
+        } else {
+          res.loss = bl;
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      res.zmin = zmin;
+      res.inv_w = inv_w;
+    }
+  }
+
+  // ---- score, range reset, pbest step, the next move's gB-independent terms
+  const int64_t ci = (int64_t)a * pr.Pp + p;
+  if (threadIdx.x == 0) {
+    sw.cur[ci] = res;
+    zz[0] = INT_MAX;  // ready for the next iteration
+    zz[1] = INT_MIN;
+    int imp = 0;
+    if (do_update) {
+      imp = (t == 0) || better(res, sw.pb[ci], pr.crit);
+      if (imp) sw.pb[ci] = res;
+    }
+    sc.imp = imp;
+  }
+  if (!do_update) return;
+  __syncthreads();
+  const bool imp = sc.imp;
+  const int64_t row = ci * d;
+  if (imp || premove)
+    for (int j = threadIdx.x; j < d; j += kThreads) {
+      const float x = sw.pos[row + j];
+      if (imp) sw.pbest[row + j] = x;  // the position is kept on improvement
+      if (premove) {
+        // ic = omega v + (c1 r1)(pB - x); pB is x itself after an improvement
+        const float pbv = imp ? x : sw.pbest[row + j];
+        sw.ic[row + j] = __fadd_rn(__fmul_rn(sw.co.inertia, sw.vel[row + j]),
+                                   __fmul_rn(c1u[j], __fsub_rn(pbv, x)));
+        sw.s2[row + j] = s2u[j];
+      }
+    }
+  if (!sw.node_step) return;
+
+  // ---- the last particle of the node to be scored: the node's gbest step
+  // and (t < T) the move of its particles
+  __syncthreads();  // this CTA's score, pbest and move terms are written
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sc.ok = atomicAdd(&sw.done[a], 1) == pr.P - 1;
+  }
+  __syncthreads();
+  if (!sc.ok) return;
+  __threadfence();
+  const int A = sw.n_nodes, Pn = pr.P;
+  const int64_t nb = (int64_t)a * pr.Pp * d;
+  const bool move = t < sw.T;
+  const bool v4 = (d & 3) == 0;
+  const int d4 = d >> 2, items = move && v4 ? Pn * d4 : 0;
+  // the move terms do not depend on gB: their loads are in flight while
+  // warp 0 takes the gbest step (batches of kNsItems items per thread)
+  constexpr int kNsItems = 4;
+  float4 xa[kNsItems], ia[kNsItems], sa[kNsItems];
+  auto load_batch = [&](int e0) {
+#pragma unroll
+    for (int u = 0; u < kNsItems; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < items) {
+        const int64_t o = nb + 4 * (int64_t)e;  // item e: features 4 (e mod d4) .. of particle e / d4
+        xa[u] = __ldcg(reinterpret_cast<const float4*>(sw.pos + o));
+        ia[u] = __ldcg(reinterpret_cast<const float4*>(sw.ic + o));
+        sa[u] = __ldcg(reinterpret_cast<const float4*>(sw.s2 + o));
+      }
+    }
+  };
+  load_batch(threadIdx.x);
+  __shared__ int s_best;
+  if (warp == 0) {
+    const EvalRes gold = ldcg_res(sw.gb + (int64_t)((t + 1) & 1) * A + a);
+    EvalRes be;
+    const int bi = gbest_argmin(pr, sw.cur + (int64_t)a * pr.Pp, gold, t, &be, true);
+    if (lane == 0) {
+      const EvalRes g = bi >= 0 ? be : gold;
+      sw.gb[(int64_t)(t & 1) * A + a] = g;
+      if (bi >= 0) {
+        sw.gpart[a] = bi;
+        sw.giter[a] = t;
+      }
+      if (sw.trace)
+        sw.trace[(int64_t)a * (sw.T + 1) + t] =
+            g.valid ? g.loss : __longlong_as_double(0x7ff0000000000000LL);
+      s_best = bi;
+      sw.done[a] = 0;  // ready for the next evaluation
+    }
+  }
+  __syncthreads();
+  const int bi = s_best;
+  // a new best improved its pbest in this evaluation: gB is that row
+  const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
+  if (bi >= 0)
+    for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = __ldcg(gsrc + j);
+  if (!move) return;
+  // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
+  if (v4) {
+    for (int e0 = threadIdx.x; e0 < items; e0 += kNsItems * kThreads) {
+      if (e0 != (int)threadIdx.x) load_batch(e0);
+      float4 g[kNsItems];
+#pragma unroll
+      for (int u = 0; u < kNsItems; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e < items) g[u] = __ldcg(reinterpret_cast<const float4*>(gsrc) + (e % d4));
+      }
+#pragma unroll
+      for (int u = 0; u < kNsItems; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e >= items) break;
+        const float4 x = xa[u], ic = ia[u], s2 = sa[u];
+        float4 vn, xn;
+        vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g[u].x, x.x)));
+        vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g[u].y, x.y)));
+        vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g[u].z, x.z)));
+        vn.w = __fadd_rn(ic.w, __fmul_rn(s2.w, __fsub_rn(g[u].w, x.w)));
+        xn.x = __fadd_rn(x.x, vn.x);
+        xn.y = __fadd_rn(x.y, vn.y);
+        xn.z = __fadd_rn(x.z, vn.z);
+        xn.w = __fadd_rn(x.w, vn.w);
+        const int64_t o = nb + 4 * (int64_t)e;
+        *reinterpret_cast<float4*>(sw.pos_next + o) = xn;
+        *reinterpret_cast<float4*>(sw.vel + o) = vn;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < Pn * d; e += kThreads) {
+      const int pq = e / d, j = e - pq * d;
+      const int64_t o = nb + e;
+      const float x = __ldcg(sw.pos + o);
+      const float vn =
+          __fadd_rn(__ldcg(sw.ic + o), __fmul_rn(__ldcg(sw.s2 + o), __fsub_rn(__ldcg(gsrc + j), x)));
+      sw.pos_next[o] = __fadd_rn(x, vn);
+      sw.vel[o] = vn;
+    }
+  }
+}
+
+const void* hist_cls_fn(const Problem& pr) {
+  return pr.crit == SLM_GINI ? (const void*)k_hist_cls<SLM_GINI>
+                             : (const void*)k_hist_cls<SLM_ENTROPY>;
+}
+
+size_t hist_cls_smem(const Problem& pr) {
+  return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K + sizeof(float) * 2 * (size_t)pr.d;
+}
+
+}  // namespace
+
+bool hist_cls_ok(const Problem& pr) {
+  return pr.crit != SLM_MSE && pr.lab && pr.K >= 1 && pr.K <= kMaxClasses && pr.B >= 2 &&
+         pr.B <= kThreads && hist_cls_smem(pr) <= 200 * 1024;
+}
+
+cudaError_t prepare_hist_cls(const Problem& pr) {
+  const void* f = hist_cls_fn(pr);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)hist_cls_smem(pr));
+  if (e) return e;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+int hist_cls_split(const Problem& pr, int A, int64_t max_len, int n_sm) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_cls_fn(pr), kThreads,
+                                                    hist_cls_smem(pr)) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  // up to one wave of resident CTAs, slices of at least 1024 entries, at
+  // most 8 CTAs per cluster (the portable size)
+  const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * n_sm;
+  int S = 1;
+  while (2 * S <= 8 && (int64_t)A * pr.P * (2 * S) <= resident && max_len / (2 * S) >= 1024) S *= 2;
+  return S;
+}
+
+cudaError_t launch_hist_cls(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
+                            int S, int t, int do_update, const double* xtab, cudaStream_t st,
+                            const int32_t* list) {
+  if (A <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A * S), (unsigned)pr.P, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = hist_cls_smem(pr);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  const void* f = hist_cls_fn(pr);
+  void* args[] = {(void*)&pr, (void*)&sw, (void*)&nodes, (void*)&list, (void*)&t,
+                  (void*)&do_update, (void*)&xtab};
+  return cudaLaunchKernelExC(&cfg, f, args);
+}
+
+}  // namespace slm

@@ -110,6 +110,11 @@ struct slm_ctx {
   // (k_step: two launches per iteration instead of three)
   bool fused_step = true;
   int64_t fused_searches = 0;
+  // classification searches score with k_hist_cls (else k_hist_scan)
+  bool class_hist = true;
+  // folded searches whose nodes all take k_hist_cls: the move in its last
+  // CTA per node (else in every k_step CTA)
+  bool node_step = false;
   cudaStream_t cap_stream = nullptr;  // records graphs (the caller's stream may
                                       // be the legacy default stream)
   // executable graphs by launch signature (every kernel node's function,
@@ -514,6 +519,15 @@ struct HistPlan {
   double pairs_small = 0.0;
   const int32_t* moved = nullptr;  // the swarm update's nodes (null: all)
   int n_moved = 0;
+  int64_t max_large = 0;           // largest node of the cluster kernel's list
+};
+
+// Classification histograms by k_hist_cls: its cluster sizes for all nodes
+// of the batch and for a HistPlan's large list.
+struct ClsPlan {
+  bool on = false;
+  int S = 1, S_large = 1;
+  const double* xtab = nullptr;
 };
 
 // Lists of the histogram kernels and the swarm update for the nodes `in`
@@ -563,6 +577,7 @@ slm_status setup_hist_plan(slm_ctx* c, const Problem& pr, const std::vector<Node
   const int32_t* base = static_cast<const int32_t*>(c->ws[S_HLIST].p);
   plan->large = base;
   plan->n_large = (int)large.size();
+  plan->max_large = max_large;
   plan->small = base + large.size();
   plan->n_small = (int)small.size();
   if (subset) {
@@ -668,7 +683,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
                        const std::vector<NodeDesc>& nodes, int n_tiles, double pairs,
                        int32_t* bins_out, int t, const SwarmCoef* co, int S,
                        const Bf16Plan* bp = nullptr, const HistPlan* hp = nullptr,
-                       const StepPlan* sp = nullptr) {
+                       const StepPlan* sp = nullptr, const ClsPlan* cp = nullptr) {
   const int A = (int)nodes.size();
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
@@ -676,9 +691,11 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
   Swarm sw = sw_in;
   if (sp && sp->on) {
     // iteration t: move (t > 0) and project in one launch; the histogram
-    // kernels score x_t in pos[t & 1] and leave the next move's terms
+    // kernels score x_t in pos[t & 1] and leave the next move's terms (or,
+    // with node_step, move the swarm into pos[(t + 1) & 1] themselves)
     sw.pos = sp->pos[t & 1];
-    const float* prev = sp->pos[t > 0 ? (t - 1) & 1 : 0];
+    sw.pos_next = sp->pos[(t + 1) & 1];
+    const float* prev = sw.node_step ? sw.pos : sp->pos[t > 0 ? (t - 1) & 1 : 0];
     CK(launch(c, SLM_K_PROJECT, pairs, [&] {
       return launch_step(pr, sw, prev, dn, A, sp->tiles, sp->n_tiles, sp->grid, t, c->stream);
     }));
@@ -723,11 +740,14 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
       return launch_project(pr, sw, dt, n_tiles, cap, c->stream, c->cur.pg, c->cur.gather,
                             c->tma && c->cur.tma ? A : 0);
     }));
+  const bool cls = cp && cp->on && !bins_out;
   if (hp && hp->on && !bins_out) {
     if (hp->n_large)
       CK(launch(c, SLM_K_HIST_SCAN, hp->pairs_large, [&] {
-        return launch_hist_scan(pr, sw, dn, hp->n_large, hp->S_large, nullptr, t, co ? 1 : 0,
-                                c->stream, hp->large);
+        return cls ? launch_hist_cls(pr, sw, dn, hp->n_large, cp->S_large, t, co ? 1 : 0,
+                                     cp->xtab, c->stream, hp->large)
+                   : launch_hist_scan(pr, sw, dn, hp->n_large, hp->S_large, nullptr, t,
+                                      co ? 1 : 0, c->stream, hp->large);
       }));
     if (hp->n_small)
       CK(launch(c, SLM_K_HIST_SCAN, hp->pairs_small, [&] {
@@ -735,7 +755,8 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
       }));
   } else {
     CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
-      return launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
+      return cls ? launch_hist_cls(pr, sw, dn, A, cp->S, t, co ? 1 : 0, cp->xtab, c->stream)
+                 : launch_hist_scan(pr, sw, dn, A, S, bins_out, t, co ? 1 : 0, c->stream);
     }));
   }
   // with adaptive PSO the evaluation scored the swarm's particles and the
@@ -749,7 +770,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
     }));
   // k_apso moves the adaptive swarm itself; a folded move needs only the
   // gbest step of the last evaluation
-  if (co && !sw.apso && (!(sp && sp->on) || t == sw.T))
+  if (co && !sw.apso && (!(sp && sp->on) || (t == sw.T && !sw.node_step)))
     CK(launch(c, SLM_K_SWARM_UPDATE, 0.0, [&] {
       return launch_move(psw, sw, dn, A, t, *co, c->stream, hp ? hp->moved : nullptr,
                          hp ? hp->n_moved : 0);
@@ -930,25 +951,27 @@ slm_status check_kernel_errors(slm_ctx* c);
 
 slm_status pick_split(slm_ctx* c, const Problem& pr, const Swarm& sw,
                       const std::vector<NodeDesc>& nodes, int n_tiles,
-                      const slm_ctx::Tiles& tl, int* S_out) {
-  *S_out = batch_split(c, pr, nodes);
-  if (!c->tune || nodes.empty() || n_tiles <= 0) return SLM_OK;
+                      const slm_ctx::Tiles& tl, int* S_out, const ClsPlan* cp = nullptr) {
+  const bool cls = cp && cp->on;
   int64_t max_len = 0;
   for (const NodeDesc& nd : nodes) max_len = std::max<int64_t>(max_len, nd.seg_len);
+  *S_out = cls ? hist_cls_split(pr, (int)nodes.size(), max_len, c->n_sm)
+               : batch_split(c, pr, nodes);
+  if (!c->tune || nodes.empty() || n_tiles <= 0) return SLM_OK;
   auto lg = [](int64_t v) {
     int l = 0;
     while ((1LL << l) < v) ++l;
     return (int64_t)l;
   };
   const std::vector<int64_t> key{pr.crit, pr.B, pr.K, pr.P, pr.w != nullptr, lg(max_len),
-                                 lg((int64_t)nodes.size())};
+                                 lg((int64_t)nodes.size()), cls ? 1 : 0};
   auto it = c->tuned_split.find(key);
   if (it != c->tuned_split.end()) {
     *S_out = it->second.S;
     return SLM_OK;
   }
   const int A = (int)nodes.size();
-  const int smax = std::min(16, hist_max_cluster(pr));
+  const int smax = cls ? 16 : std::min(16, hist_max_cluster(pr));
   const WorkTile* dt = ws_ptr<WorkTile>(c, S_TILES);
   const NodeDesc* dn = ws_ptr<NodeDesc>(c, S_NODES);
   cudaEvent_t e0 = take_event(c), e1 = take_event(c);
@@ -957,13 +980,16 @@ slm_status pick_split(slm_ctx* c, const Problem& pr, const Swarm& sw,
   bool have = false;
   for (int S = 1; S <= smax; ++S) {
     if (S > 1 && max_len / S < 256) break;
+    if (cls && (S & (S - 1))) continue;  // powers of two
     float ms_min = 0.f;
     bool ok = true;
     for (int r = 0; r < 2 && ok; ++r) {
       cudaError_t e = launch_project(pr, sw, dt, n_tiles, tl.cps * c->n_sm, c->stream, tl.pg,
                                      tl.gather, c->tma && tl.tma ? A : 0);
       if (!e) e = cudaEventRecord(e0, c->stream);
-      if (!e) e = launch_hist_scan(pr, sw, dn, A, S, nullptr, 0, 0, c->stream);
+      if (!e)
+        e = cls ? launch_hist_cls(pr, sw, dn, A, S, 0, 0, cp->xtab, c->stream)
+                : launch_hist_scan(pr, sw, dn, A, S, nullptr, 0, 0, c->stream);
       if (!e) e = cudaEventRecord(e1, c->stream);
       if (!e) e = cudaEventSynchronize(e1);
       c->launches += 2;
@@ -1105,7 +1131,8 @@ struct KeyWriter {
     put(w.gpart); put(w.giter); put(w.trace); put(w.zmm); put(w.z); put(w.done); put(w.err);
     put(w.T); put(w.sel); put(w.k); put(w.tk_sel); put(w.tk_inv); put(w.tk_pos);
     put(w.tk_k); put(w.tk_kp); put(w.posb); put(w.apso); put(w.ic); put(w.s2);
-    put(w.co.inertia); put(w.co.c1); put(w.co.c2); put(w.co.seed);
+    put(w.co.inertia); put(w.co.c1); put(w.co.c2); put(w.co.seed); put(w.node_step);
+    put(w.n_nodes);
   }
 };
 
@@ -1252,8 +1279,24 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     if (!bp.on && !stp.on && (s = pick_tiles(c, pr, sw, (int)tiles.size(), A, &tl))) return s;
     HistPlan hp;
     if (!bp.on && (s = setup_hist_plan(c, pr, nodes, in, &hp))) return s;
-    if (!bp.on && !hp.on && (s = pick_split(c, pr, sw, nodes, (int)tiles.size(), tl, &S)))
+    ClsPlan cp;
+    if (c->class_hist && !bp.on && hist_cls_ok(pr)) {
+      CK(prepare_hist_cls(pr));
+      cp.on = true;
+      cp.xtab = xlogx_table(c->device);
+      if (hp.on && hp.n_large)
+        cp.S_large = hist_cls_split(pr, hp.n_large, hp.max_large, c->n_sm);
+    }
+    if (!bp.on && !hp.on &&
+        (s = pick_split(c, pr, sw, nodes, (int)tiles.size(), tl, &S, cp.on ? &cp : nullptr)))
       return s;
+    cp.S = S;
+    // every node scored by k_hist_cls: its last CTA per node takes the gbest
+    // step and moves the swarm
+    if (stp.on && cp.on && !hp.on && c->node_step) {
+      sw.node_step = 1;
+      sw.n_nodes = A;
+    }
     c->last_split = S;
     c->cur = tl;
     c->last = tl;
@@ -1273,7 +1316,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       kw.put(hp.pairs_large); kw.put(hp.small); kw.put(hp.n_small); kw.put(hp.pairs_small);
       kw.put(hp.moved); kw.put(hp.n_moved);
       kw.put(stp.on); kw.put(stp.pos[1]); kw.put(stp.tiles); kw.put(stp.n_tiles);
-      kw.put(stp.grid);
+      kw.put(stp.grid); kw.put(cp.on); kw.put(cp.S); kw.put(cp.S_large); kw.put(cp.xtab);
       if (bp.on) {
         kw.problem(bp.pr_k);
         kw.swarm(bp.sw_k);
@@ -1282,7 +1325,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     }
     s = run_iterations(c, p->n_iters, key, [&](int t) {
       return score_batch(c, pr, sw, nodes, (int)tiles.size(), pairs, nullptr, t, &co, S, &bp,
-                         &hp, &stp);
+                         &hp, &stp, &cp);
     });
     c->cur = slm_ctx::Tiles{};
     if (!joined) {
@@ -2754,6 +2797,13 @@ slm_status slm_set_fused_step(slm_ctx* c, int32_t on, int64_t* searches) {
   if (!c) return SLM_EINVAL;
   c->fused_step = on != 0;
   if (searches) *searches = c->fused_searches;
+  return SLM_OK;
+}
+
+slm_status slm_set_class_hist(slm_ctx* c, int32_t on, int32_t node_step) {
+  if (!c) return SLM_EINVAL;
+  c->class_hist = on != 0;
+  c->node_step = node_step != 0;
   return SLM_OK;
 }
 

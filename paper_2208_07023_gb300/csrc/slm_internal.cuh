@@ -161,6 +161,14 @@ struct Swarm {
   float* ic;
   float* s2;
   SwarmCoef co;
+  // with node_step set (classification searches whose nodes all go to
+  // k_hist_cls): the last CTA to score a node in evaluation t (counter
+  // done[a], left at 0) takes the node's gbest step (the rule of k_move)
+  // and, for t < T, moves its particles into pos_next; k_step then only
+  // loads positions. n_nodes: the batch's node count (stride of gb).
+  float* pos_next;
+  int32_t node_step;
+  int32_t n_nodes;
 };
 
 // Adaptive PSO state of one node (Sec. III-B): evolutionary state 1..4
@@ -184,6 +192,8 @@ cudaError_t set_first_wait_polls(int polls);
 constexpr int kXlogxTab = 1 << 20;
 // Builds the device's c ln c table once per process (synchronous).
 cudaError_t ensure_xlogx_table(int device);
+// The device's table (c ln c for c < kXlogxTab), null before it is built.
+const double* xlogx_table(int device);
 
 // ---- launchers (eval_kernels.cu) -------------------------------------------
 cudaError_t prepare_eval_kernels(const Problem& pr);
@@ -211,6 +221,15 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
                              const NodeDesc* nodes, int A, int S,
                              int32_t* bins_out, int t, int do_update,
                              cudaStream_t st, const int32_t* list = nullptr);
+// Classification histograms and scans of a search (no bins out, no top-k):
+// the same scores, pbest steps and move terms as launch_hist_scan, built for
+// latency (see hist_kernels.cu). xtab: the device's c ln c table.
+bool hist_cls_ok(const Problem& pr);
+cudaError_t prepare_hist_cls(const Problem& pr);
+int hist_cls_split(const Problem& pr, int A, int64_t max_len, int n_sm);
+cudaError_t launch_hist_cls(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,
+                            int S, int t, int do_update, const double* xtab, cudaStream_t st,
+                            const int32_t* list = nullptr);
 // Persistent search of classification nodes whose rows fit in shared memory:
 // all T + 1 iterations in one launch, a cluster of S (1..8) CTAs per node of
 // list[n_nodes] (A: the batch's node count, the gbest buffers' stride).
@@ -246,7 +265,8 @@ cudaError_t launch_apso(const Problem& pr, const Swarm& sw, const NodeDesc* node
 // the ranges of every (row tile, all particles) unit, as k_project (the same
 // fused multiply-adds). tiles: step_rows(pr)-row tiles of the nodes in order,
 // every node with at least one. The gbest step of the last evaluation is left
-// to launch_move(t = T).
+// to launch_move(t = T). With sw.node_step the histogram kernel has moved the
+// swarm already: k_step loads the positions of t from pos_prev.
 bool step_ok(const Problem& pr);
 int step_rows(const Problem& pr);
 int step_grid(const Problem& pr, int n_sm);

@@ -34,13 +34,17 @@ namespace {
 
 constexpr int kStepMaxPosBytes = 96 * 1024;  // the node's positions in shared memory
 
-// Row stride of the positions in shared memory: features rounded up to 4
-// (zero-padded) plus 4 floats, so the four particles a warp reads at one
-// feature fall on distinct banks.
-__host__ __device__ inline int step_ldp(int d) { return ((d + 3) & ~3) + 4; }
+// Positions in shared memory, chunk-major: feature j of particle p at
+// (j / kKC) * Pp * kXS + p * kXS + j % kKC, so that the particles a thread
+// reads sit at compile-time offsets and the four particles a warp reads at
+// one feature fall on distinct banks (rows kXS = 36 floats apart). Features
+// past d and particles past P stay zero.
+__host__ __device__ inline size_t step_pos_floats(int Pp, int d) {
+  return (size_t)((d + kKC - 1) / kKC) * Pp * kXS;
+}
 
 template <int PJ, int PB>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
     k_step(Problem pr, Swarm sw, const float* __restrict__ pos_prev,
            const NodeDesc* __restrict__ nodes, int A, const WorkTile* __restrict__ tiles,
            int n_units, int t) {
@@ -53,11 +57,11 @@ __global__ void __launch_bounds__(kThreads, 3)
   __shared__ int s_best;
   float* xs0 = sm;                // [RT][kXS] rows of a feature chunk, two stages
   float* xs1 = sm + RT * kXS;
-  float* ps = sm + 2 * RT * kXS;  // [Pp][ldp] the node's positions
+  float* ps = sm + 2 * RT * kXS;  // the node's positions, chunk-major
   pdl_trigger();
   const int d = pr.d, Pp = pr.Pp, P = pr.P;
-  const int ldp = step_ldp(d), dq = (d + 3) & ~3;
   const int nk = (d + kKC - 1) / kKC;
+  const int cstride = Pp * kXS;   // floats per feature chunk of the positions
   const bool vec = (d & 3) == 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sg = lane & 7, pg = lane >> 3;
@@ -98,6 +102,8 @@ __global__ void __launch_bounds__(kThreads, 3)
   // iteration's launch, so iterations t > 0 start fetching them before the
   // previous kernel's results are visible.
   if (n_st > 0 && t > 0) stage(0, xs0);
+  // padding features and particles of the positions stay zero
+  for (int i = threadIdx.x; i < nk * cstride; i += kThreads) ps[i] = 0.0f;
   pdl_wait();
   if (n_st > 0 && t == 0) stage(0, xs0);
 
@@ -106,14 +112,31 @@ __global__ void __launch_bounds__(kThreads, 3)
   // records of evaluation t - 1).
   auto node_positions = [&](int a, bool desig) {
     const int64_t nb = (int64_t)a * Pp * d;
-    if (t == 0) {
-      for (int e = threadIdx.x; e < Pp * dq; e += kThreads) {
-        const int p = e / dq, j = e - p * dq;
-        ps[p * ldp + j] = (p < P && j < d) ? pos_prev[nb + (int64_t)p * d + j] : 0.0f;
+    if (t == 0 || sw.node_step) {  // the histogram kernel moved the swarm
+      for (int e = threadIdx.x; e < P * d; e += kThreads) {
+        const int p = e / d, j = e - p * d;
+        ps[(j / kKC) * cstride + p * kXS + j % kKC] = pos_prev[nb + e];
       }
       __syncthreads();
       return;
     }
+    // the first move terms are requested before the gbest step (they do
+    // not depend on gB), so their latency overlaps the argmin
+    const int d4 = d >> 2, items = vec ? P * d4 : 0;
+    float4 xa[2], ia[2], sa[2];
+    auto load2 = [&](int e0) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e < items) {
+          const int64_t o = nb + 4 * (int64_t)e;  // element (p, 4q) of the node's rows
+          xa[u] = __ldcg(reinterpret_cast<const float4*>(pos_prev + o));
+          ia[u] = __ldcg(reinterpret_cast<const float4*>(sw.ic + o));
+          sa[u] = __ldcg(reinterpret_cast<const float4*>(sw.s2 + o));
+        }
+      }
+    };
+    load2(threadIdx.x);
     // gbest step of evaluation t - 1 (k_move's rule and double buffering)
     if (warp == 0) {
       const EvalRes gold = sw.gb[(int64_t)(t & 1) * A + a];
@@ -142,17 +165,16 @@ __global__ void __launch_bounds__(kThreads, 3)
       for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = gsrc[j];
     // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
     if (vec) {
-      const int d4 = d >> 2;
-      for (int e = threadIdx.x; e < Pp * d4; e += kThreads) {
-        const int p = e / d4, j = 4 * (e - p * d4);
-        float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p < P) {
-          const int64_t o = nb + (int64_t)p * d + j;
-          const float4 x = *reinterpret_cast<const float4*>(pos_prev + o);
-          const float4 ic = *reinterpret_cast<const float4*>(sw.ic + o);
-          const float4 s2 = *reinterpret_cast<const float4*>(sw.s2 + o);
-          const float4 g = *reinterpret_cast<const float4*>(gsrc + j);
-          float4 vn;
+      for (int e0 = threadIdx.x; e0 < items; e0 += 2 * kThreads) {
+        if (e0 != (int)threadIdx.x) load2(e0);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int e = e0 + u * kThreads;
+          if (e >= items) break;
+          const int p = e / d4, j = 4 * (e - p * d4);
+          const float4 x = xa[u], ic = ia[u], s2 = sa[u];
+          const float4 g = __ldcg(reinterpret_cast<const float4*>(gsrc + j));
+          float4 vn, xn;
           vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
           vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
           vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g.z, x.z)));
@@ -162,27 +184,25 @@ __global__ void __launch_bounds__(kThreads, 3)
           xn.z = __fadd_rn(x.z, vn.z);
           xn.w = __fadd_rn(x.w, vn.w);
           if (desig) {
+            const int64_t o = nb + 4 * (int64_t)e;
             *reinterpret_cast<float4*>(sw.pos + o) = xn;
             *reinterpret_cast<float4*>(sw.vel + o) = vn;
           }
+          *reinterpret_cast<float4*>(ps + (j / kKC) * cstride + p * kXS + j % kKC) = xn;
         }
-        *reinterpret_cast<float4*>(ps + p * ldp + j) = xn;
       }
     } else {
-      for (int e = threadIdx.x; e < Pp * dq; e += kThreads) {
-        const int p = e / dq, j = e - p * dq;
-        float xn = 0.0f;
-        if (p < P && j < d) {
-          const int64_t o = nb + (int64_t)p * d + j;
-          const float x = pos_prev[o];
-          const float vn = __fadd_rn(sw.ic[o], __fmul_rn(sw.s2[o], __fsub_rn(gsrc[j], x)));
-          xn = __fadd_rn(x, vn);
-          if (desig) {
-            sw.pos[o] = xn;
-            sw.vel[o] = vn;
-          }
+      for (int e = threadIdx.x; e < P * d; e += kThreads) {
+        const int p = e / d, j = e - p * d;
+        const int64_t o = nb + e;
+        const float x = pos_prev[o];
+        const float vn = __fadd_rn(sw.ic[o], __fmul_rn(sw.s2[o], __fsub_rn(gsrc[j], x)));
+        const float xn = __fadd_rn(x, vn);
+        if (desig) {
+          sw.pos[o] = xn;
+          sw.vel[o] = vn;
         }
-        ps[p * ldp + j] = xn;
+        ps[(j / kKC) * cstride + p * kXS + j % kKC] = xn;
       }
     }
     __syncthreads();
@@ -225,19 +245,20 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     __syncthreads();
     const float* xr = ((s & 1) ? xs1 : xs0) + (rb * 32 + sg) * kXS;
-    const float* ar = ps + (pbk * PPB + pg) * ldp + c * kKC;
-    const int kc4 = (min(kKC, d - c * kKC) + 3) & ~3;
+    const float* ar = ps + c * cstride + (pbk * PPB + pg) * kXS;
+    const int kc4 = (min(kKC, d - c * kKC) + 3) >> 2;  // 16-byte chunks of features
 #pragma unroll 1
-    for (int k = 0; k < kc4; k += 4) {
+    for (int ch = 0; ch < kc4; ++ch) {
       float4 xv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + k);
+      for (int i = 0; i < 4; ++i)
+        xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + 4 * ch);
       // feature-outer within each pair of particles: every accumulator takes
-      // features k..k+3 in increasing order
+      // features 4 ch .. 4 ch + 3 in increasing order
 #pragma unroll
       for (int j = 0; j < PJ; j += 2) {
-        const float4 a0 = *reinterpret_cast<const float4*>(ar + j * 4 * ldp + k);
-        const float4 a1 = *reinterpret_cast<const float4*>(ar + (j + 1) * 4 * ldp + k);
+        const float4 a0 = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + 4 * ch);
+        const float4 a1 = *reinterpret_cast<const float4*>(ar + (j + 1) * 4 * kXS + 4 * ch);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           acc[i][j] = fmaf(xv[i].x, a0.x, acc[i][j]);
@@ -314,7 +335,7 @@ size_t step_smem(const Problem& pr) {
   int PJ = 0, PB = 0;
   if (!step_shape(pr.Pp, &PJ, &PB)) return 0;
   const int RT = 32 * (8 / PB);
-  return sizeof(float) * ((size_t)2 * RT * kXS + (size_t)pr.Pp * step_ldp(pr.d));
+  return sizeof(float) * ((size_t)2 * RT * kXS + step_pos_floats(pr.Pp, pr.d));
 }
 
 const void* step_fn(int Pp) {
@@ -332,7 +353,7 @@ const void* step_fn(int Pp) {
 bool step_ok(const Problem& pr) {
   int PJ = 0, PB = 0;
   return step_shape(pr.Pp, &PJ, &PB) &&
-         (size_t)pr.Pp * step_ldp(pr.d) * sizeof(float) <= (size_t)kStepMaxPosBytes;
+         step_pos_floats(pr.Pp, pr.d) * sizeof(float) <= (size_t)kStepMaxPosBytes;
 }
 
 int step_rows(const Problem& pr) {

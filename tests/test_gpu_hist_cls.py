@@ -1,0 +1,101 @@
+"""The latency-oriented classification histogram kernel (k_hist_cls, the
+default for classification searches) scores exactly like the staged-copy
+kernel it replaces there: identical traces, gbest, splits, trees and bagged
+forests for Gini and entropy, class counts spanning every register-array
+width (2 .. 32), bin counts that are not multiples of 32 (down to 2),
+multiplicities, nodes too small for 16-byte loads of a whole slice, and
+levels whose small nodes go to the warp-per-particle kernel. The oracle
+comparisons of the other GPU tests run it too, since it is the default."""
+import numpy as np
+import pytest
+
+from paper_2208_07023_gb300 import workloads as W
+from tests.gpu_util import context, gpu_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    a, b = context(), context()
+    b.set_class_hist(False)
+    yield a, b
+    a.close()
+    b.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_step():
+    """The other placement of the gbest step and move (the default is the
+    projection blocks; this one takes the last histogram block per node)."""
+    c = context()
+    c.set_class_hist(True, node_step=True)
+    yield c
+    c.close()
+
+
+def same_tree(fa, fb, n_trees=1):
+    for t in range(n_trees):
+        ga, gb = fa.export(t), fb.export(t)
+        for k in ga:
+            assert np.array_equal(ga[k], gb[k]), (t, k)
+
+
+@pytest.mark.parametrize("crit", ["gini", "entropy"])
+@pytest.mark.parametrize("n,d,K,P,B", [
+    (6000, 24, 2, 32, 64),
+    (5003, 16, 5, 48, 50),    # bins not a multiple of 32, ragged slices
+    (9000, 32, 10, 64, 128),
+    (4000, 12, 20, 16, 128),
+    (3000, 8, 32, 24, 2),     # the most classes, two bins
+    (37, 4, 3, 16, 16),       # a node smaller than one 16-byte group per thread
+])
+def test_search_identical_with_both_histogram_kernels(ctxs, ctx_step, crit, n, d, K, P, B):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.gmm(n, d, K, seed=n % 97 + K)
+    p = gpu_params(S, crit, K, P, 10, B, min_leaf=3, seed=5)
+    rb = b.node_split(p, wl.X, labels=wl.labels, node_uid=4, want_trace=True)
+    for c in (a, ctx_step):  # the move in k_step, or in the last histogram block
+        ra = c.node_split(p, wl.X, labels=wl.labels, node_uid=4, want_trace=True)
+        assert np.array_equal(ra["trace"], rb["trace"])
+        assert np.array_equal(ra["gbest"], rb["gbest"])
+        for k in ("bin", "q_num", "q_den", "loss", "n_left", "n_right", "particle",
+                  "iter_of_best"):
+            assert ra[k] == rb[k], k
+
+
+@pytest.mark.parametrize("crit,bootstrap", [("gini", False), ("entropy", True), ("gini", True)])
+def test_forest_identical_with_both_histogram_kernels(ctxs, ctx_step, crit, bootstrap):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.gmm(24000, 20, 6, seed=11)
+    p = gpu_params(S, crit, 6, 32, 8, 128, min_leaf=10, max_depth=7, seed=3,
+                   n_trees=3 if bootstrap else 1, bootstrap=bootstrap)
+    fb = b.train_tree(p, wl.X, labels=wl.labels)
+    for c in (a, ctx_step):
+        fa = c.train_tree(p, wl.X, labels=wl.labels)
+        same_tree(fa, fb, p.n_trees)
+        fa.free()
+    # every level through the classification kernel (no warp-per-particle
+    # nodes), so each level's move runs in the last histogram blocks
+    ctx_step.set_small_nodes(0, 0)
+    try:
+        fa = ctx_step.train_tree(p, wl.X, labels=wl.labels)
+        same_tree(fa, fb, p.n_trees)
+        fa.free()
+    finally:
+        ctx_step.set_small_nodes()
+    fb.free()
+
+
+def test_unfused_search_identical_with_both_histogram_kernels(ctxs):
+    """The new kernel under the three-kernel iteration (no folded move)."""
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.gmm(8000, 20, 4, seed=12)
+    p = gpu_params(S, "gini", 4, 100, 8, 64, min_leaf=5, seed=9)  # 112 padded: not folded
+    ra = a.node_split(p, wl.X, labels=wl.labels, node_uid=1, want_trace=True)
+    rb = b.node_split(p, wl.X, labels=wl.labels, node_uid=1, want_trace=True)
+    assert np.array_equal(ra["trace"], rb["trace"])
+    assert np.array_equal(ra["gbest"], rb["gbest"]) and ra["bin"] == rb["bin"]
