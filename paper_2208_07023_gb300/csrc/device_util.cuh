@@ -176,6 +176,8 @@ __device__ __forceinline__ const float* row_of(const Problem& pr, int64_t e) {
   return pr.gidx ? pr.Xg + (int64_t)__ldg(pr.gidx + e) * pr.d : pr.X + e * pr.d;
 }
 
+
+
 // Score written by another CTA of this grid: read through L2.
 __device__ __forceinline__ EvalRes ldcg_res(const EvalRes* r) {
   EvalRes o;
@@ -189,8 +191,21 @@ __device__ __forceinline__ EvalRes ldcg_res(const EvalRes* r) {
 // Algorithm 1, gbest step of node a after evaluation t, as seen by one warp:
 // the particle with the best score strictly better than gold (at t = 0 every
 // particle, gold unset), ties to the lower index; -1 if none. Lane 0 also
-// returns that particle's score in *best_res.
-// With l2, the scores are read through L2 (written by other CTAs of the grid).
+// returns that particle's score in *best_res. With l2, the scores are read
+// through L2 (written by other CTAs of the grid).
+//
+// The reduction runs on the double loss, which every score carries and which
+// is a rounding of the exact loss (Gini: of 1 - Q / n), so it orders scores
+// like the exact comparison except, possibly, among losses within a few
+// units in the last place of each other. The candidates within 8 ulps of the
+// smallest loss are then compared exactly (better(), index ties), which gives
+// the result of an exact argmin over all candidates.
+__device__ __forceinline__ uint64_t loss_key(const EvalRes& e) {
+  // losses are >= 0: their bit patterns order like their values; invalid
+  // scores last
+  return e.valid ? (uint64_t)__double_as_longlong(e.loss) : ~0ull;
+}
+
 __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
                             EvalRes* best_res, bool l2 = false) {
   const int lane = threadIdx.x & 31;
@@ -204,29 +219,53 @@ __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes
       be = e;
     }
   }
+  const unsigned cand = __ballot_sync(0xffffffffu, bi >= 0);
+  if (!cand) {  // nobody beat gold
+    if (lane == 0) *best_res = be;
+    return -1;
+  }
+  // smallest double loss over the lanes' candidates
+  const uint64_t key = bi >= 0 ? loss_key(be) : ~0ull;
+  uint64_t kmin = key;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-    const EvalRes o = shfl_res(be, lane ^ off);
-    bool take;
-    if (oi < 0)
-      take = false;
-    else if (bi < 0)
-      take = true;
-    else if (better(o, be, pr.crit))
-      take = true;
-    else if (better(be, o, pr.crit))
-      take = false;
-    else
-      take = oi < bi;
-    if (take) {
-      bi = oi;
-      be = o;
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
+    kmin = o < kmin ? o : kmin;
+  }
+  // the candidates near the smallest loss (all of them when no candidate is
+  // valid), compared exactly in lane order
+  const bool near = bi >= 0 && (kmin == ~0ull || key <= kmin + 8);
+  unsigned m = __ballot_sync(0xffffffffu, near);
+  int wi = __ffs(m) - 1;
+  int wb = __shfl_sync(0xffffffffu, bi, wi);
+  m &= m - 1;
+  while (m) {  // rare: several candidates within a few ulps
+    const int li = __ffs(m) - 1;
+    m &= m - 1;
+    const int ob = __shfl_sync(0xffffffffu, bi, li);
+    const EvalRes o = shfl_res(be, li);
+    const EvalRes w = shfl_res(be, wi);
+    if (better(o, w, pr.crit) || (!better(w, o, pr.crit) && ob < wb)) {
+      wi = li;
+      wb = ob;
     }
   }
-  if (lane == 0) *best_res = be;
-  return bi;
+  const EvalRes w = shfl_res(be, wi);
+  if (lane == 0) *best_res = w;
+  return wb;
 }
+
+// Folded searches (Swarm::imp): records that score `res` of a particle of
+// node a in evaluation t beats the gbest score held after evaluation t - 1
+// (every valid score does at t = 0), the gbest step's rule (Algorithm 1).
+__device__ __forceinline__ void mark_improvement(const Problem& pr, const Swarm& sw, int a, int t,
+                                                 const EvalRes& res) {
+  if (!sw.imp || !res.valid) return;
+  const bool beats =
+      t == 0 || better(res, ldcg_res(sw.gb + (int64_t)((t + 1) & 1) * sw.n_nodes + a), pr.crit);
+  if (beats) atomicOr(sw.imp + (int64_t)(t & 1) * sw.n_nodes + a, 1);
+}
+
 
 // Algorithm 1, pbest step of particle p after evaluation t (one warp): strict
 // "<" against the particle's best so far; the position is kept on improvement.

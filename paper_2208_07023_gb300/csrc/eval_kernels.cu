@@ -1511,6 +1511,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     sw.cur[(int64_t)a * pr.Pp + p] = res;
     zz[0] = INT_MAX;  // ready for the next iteration
     zz[1] = INT_MIN;
+    if (do_update) mark_improvement(pr, sw, a, t, res);
   }
   if (do_update && warp == 0) {
     pbest_step(pr, sw, a, p, t, res);
@@ -1708,6 +1709,7 @@ __global__ void __launch_bounds__(kThreads)
     sw.cur[(int64_t)a * pr.Pp + p] = res;
     zz[0] = INT_MAX;  // ready for the next iteration
     zz[1] = INT_MIN;
+    if (do_update) mark_improvement(pr, sw, a, t, res);
   }
   if (do_update) {
     pbest_step(pr, sw, a, p, t, res);

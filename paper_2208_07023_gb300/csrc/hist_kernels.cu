@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     zz[1] = INT_MIN;
     int imp = 0;
     if (do_update) {
+      mark_improvement(pr, sw, a, t, res);
       imp = (t == 0) || better(res, sw.pb[ci], pr.crit);
       if (imp) sw.pb[ci] = res;
     }
@@ -414,17 +415,28 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool move = t < sw.T;
   const bool v4 = (d & 3) == 0;
   const int d4 = d >> 2, items = move && v4 ? Pn * d4 : 0;
-  // the move terms do not depend on gB: their loads are in flight while
-  // warp 0 takes the gbest step (batches of kNsItems items per thread)
-  constexpr int kNsItems = 4;
-  float4 xa[kNsItems], ia[kNsItems], sa[kNsItems];
+  // The positions and the recorded gB go to shared memory (the histograms
+  // are done with) by asynchronous copies, the first move terms to
+  // registers, all while warp 0 takes the gbest step: after a gbest change
+  // gB is the new best particle's position (it beat every pbest, so its own
+  // pbest became that position), so the move needs nothing more from memory.
+  float* xsm = reinterpret_cast<float*>(hc);
+  const bool in_smem = items > 0 && (Pn + 1) * d <= kHcCopies * W;
+  if (in_smem) {
+    for (int e = threadIdx.x; e < items; e += kThreads)
+      cp_async16(xsm + 4 * e, sw.pos + nb + 4 * (int64_t)e, 16);
+    for (int q = threadIdx.x; q < d4; q += kThreads)
+      cp_async16(xsm + Pn * d + 4 * q, sw.gbest + (int64_t)a * d + 4 * q, 16);
+    cp_async_commit();
+  }
+  constexpr int kNsItems = 4;  // move items per thread in flight
+  float4 ia[kNsItems], sa[kNsItems];
   auto load_batch = [&](int e0) {
 #pragma unroll
     for (int u = 0; u < kNsItems; ++u) {
       const int e = e0 + u * kThreads;
       if (e < items) {
         const int64_t o = nb + 4 * (int64_t)e;  // item e: features 4 (e mod d4) .. of particle e / d4
-        xa[u] = __ldcg(reinterpret_cast<const float4*>(sw.pos + o));
         ia[u] = __ldcg(reinterpret_cast<const float4*>(sw.ic + o));
         sa[u] = __ldcg(reinterpret_cast<const float4*>(sw.s2 + o));
       }
@@ -433,10 +445,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   load_batch(threadIdx.x);
   __shared__ int s_best;
   if (warp == 0) {
+    // the argmin only when a particle beat gB in this evaluation (every
+    // particle is a candidate at evaluation 0)
+    const int64_t fi = (int64_t)(t & 1) * A + a;
+    const bool any = t == 0 || __ldcg(sw.imp + fi) != 0;
     const EvalRes gold = ldcg_res(sw.gb + (int64_t)((t + 1) & 1) * A + a);
-    EvalRes be;
-    const int bi = gbest_argmin(pr, sw.cur + (int64_t)a * pr.Pp, gold, t, &be, true);
+    EvalRes be = gold;
+    const int bi = any ? gbest_argmin(pr, sw.cur + (int64_t)a * pr.Pp, gold, t, &be, true) : -1;
     if (lane == 0) {
+      sw.imp[fi] = 0;  // ready for evaluation t + 2
       const EvalRes g = bi >= 0 ? be : gold;
       sw.gb[(int64_t)(t & 1) * A + a] = g;
       if (bi >= 0) {
@@ -450,33 +467,35 @@ __global__ void __launch_bounds__(kThreads, 2)
       sw.done[a] = 0;  // ready for the next evaluation
     }
   }
+  if (in_smem) cp_async_wait<0>();
   __syncthreads();
   const int bi = s_best;
   // a new best improved its pbest in this evaluation: gB is that row
   const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
+  const float* gsm = bi >= 0 ? xsm + bi * d : xsm + Pn * d;
   if (bi >= 0)
-    for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = __ldcg(gsrc + j);
+    for (int j = threadIdx.x; j < d; j += kThreads)
+      sw.gbest[(int64_t)a * d + j] = in_smem ? gsm[j] : __ldcg(gsrc + j);
   if (!move) return;
   // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
   if (v4) {
     for (int e0 = threadIdx.x; e0 < items; e0 += kNsItems * kThreads) {
       if (e0 != (int)threadIdx.x) load_batch(e0);
-      float4 g[kNsItems];
-#pragma unroll
-      for (int u = 0; u < kNsItems; ++u) {
-        const int e = e0 + u * kThreads;
-        if (e < items) g[u] = __ldcg(reinterpret_cast<const float4*>(gsrc) + (e % d4));
-      }
 #pragma unroll
       for (int u = 0; u < kNsItems; ++u) {
         const int e = e0 + u * kThreads;
         if (e >= items) break;
-        const float4 x = xa[u], ic = ia[u], s2 = sa[u];
+        const int j = 4 * (e % d4);
+        const float4 x = in_smem ? *reinterpret_cast<const float4*>(xsm + 4 * e)
+                                 : __ldcg(reinterpret_cast<const float4*>(sw.pos + nb) + e);
+        const float4 g = in_smem ? *reinterpret_cast<const float4*>(gsm + j)
+                                 : __ldcg(reinterpret_cast<const float4*>(gsrc + j));
+        const float4 ic = ia[u], s2 = sa[u];
         float4 vn, xn;
-        vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g[u].x, x.x)));
-        vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g[u].y, x.y)));
-        vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g[u].z, x.z)));
-        vn.w = __fadd_rn(ic.w, __fmul_rn(s2.w, __fsub_rn(g[u].w, x.w)));
+        vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
+        vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
+        vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g.z, x.z)));
+        vn.w = __fadd_rn(ic.w, __fmul_rn(s2.w, __fsub_rn(g.w, x.w)));
         xn.x = __fadd_rn(x.x, vn.x);
         xn.y = __fadd_rn(x.y, vn.y);
         xn.z = __fadd_rn(x.z, vn.z);

@@ -49,7 +49,7 @@ enum Slot {
   S_APSO,
   // the projection with the move folded in: second position buffer, the
   // gB-independent move terms, its row tiles
-  S_POS2, S_IC, S_S2, S_STILES,
+  S_POS2, S_IC, S_S2, S_STILES, S_IMP,
   N_SLOTS
 };
 
@@ -1132,7 +1132,7 @@ struct KeyWriter {
     put(w.T); put(w.sel); put(w.k); put(w.tk_sel); put(w.tk_inv); put(w.tk_pos);
     put(w.tk_k); put(w.tk_kp); put(w.posb); put(w.apso); put(w.ic); put(w.s2);
     put(w.co.inertia); put(w.co.c1); put(w.co.c2); put(w.co.seed); put(w.node_step);
-    put(w.n_nodes);
+    put(w.n_nodes); put(w.imp);
   }
 };
 
@@ -1259,6 +1259,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       CK(ensure(c->ws[S_IC], sizeof(float) * apd));
       CK(ensure(c->ws[S_S2], sizeof(float) * apd));
       CK(ensure(c->ws[S_STILES], sizeof(WorkTile) * st.size()));
+      CK(ensure(c->ws[S_IMP], sizeof(int32_t) * 2 * (size_t)A));
+      CK(cudaMemsetAsync(c->ws[S_IMP].p, 0, sizeof(int32_t) * 2 * (size_t)A, c->stream));
       CK(cudaMemcpyAsync(c->ws[S_STILES].p, st.data(), sizeof(WorkTile) * st.size(),
                          cudaMemcpyHostToDevice, c->stream));
       stp.on = true;
@@ -1270,6 +1272,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       sw.ic = ws_ptr<float>(c, S_IC);
       sw.s2 = ws_ptr<float>(c, S_S2);
       sw.co = co;
+      sw.imp = ws_ptr<int32_t>(c, S_IMP);
+      sw.n_nodes = A;
       c->fused_searches += 1;
     }
   }
@@ -1293,10 +1297,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     cp.S = S;
     // every node scored by k_hist_cls: its last CTA per node takes the gbest
     // step and moves the swarm
-    if (stp.on && cp.on && !hp.on && c->node_step) {
-      sw.node_step = 1;
-      sw.n_nodes = A;
-    }
+    if (stp.on && cp.on && !hp.on && c->node_step) sw.node_step = 1;
     c->last_split = S;
     c->cur = tl;
     c->last = tl;

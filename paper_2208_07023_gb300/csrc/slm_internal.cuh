@@ -169,6 +169,11 @@ struct Swarm {
   float* pos_next;
   int32_t node_step;
   int32_t n_nodes;
+  // folded searches: imp[(t & 1) * n_nodes + a] != 0 iff some particle of
+  // node a scored strictly better than gB in evaluation t (set by the
+  // histogram kernels, reset by the kernel that takes the gbest step); the
+  // gbest step skips its argmin when it is 0, since gB then stays
+  int32_t* imp;
 };
 
 // Adaptive PSO state of one node (Sec. III-B): evolutionary state 1..4

@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   // The positions of node a for iteration t in ps (and, from the CTA that
   // holds the node's first row tile, in sw.pos / sw.vel with the gbest
-  // records of evaluation t - 1).
-  auto node_positions = [&](int a, bool desig) {
+  // records of evaluation t - 1). scratch[cap]: shared memory free during
+  // the call (a row-tile stage buffer).
+  auto node_positions = [&](int a, bool desig, float* scratch, int cap) {
     const int64_t nb = (int64_t)a * Pp * d;
     if (t == 0 || sw.node_step) {  // the histogram kernel moved the swarm
       for (int e = threadIdx.x; e < P * d; e += kThreads) {
@@ -120,17 +121,27 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       return;
     }
-    // the first move terms are requested before the gbest step (they do
-    // not depend on gB), so their latency overlaps the argmin
+    // Positions of t - 1 and the recorded gB go to shared memory by
+    // asynchronous copies, the first move terms to registers, all before
+    // the gbest step: after a gbest change gB is the new best particle's
+    // position of t - 1 (it beat every pbest, so its own pbest became that
+    // position), so the move then needs nothing from global memory.
     const int d4 = d >> 2, items = vec ? P * d4 : 0;
-    float4 xa[2], ia[2], sa[2];
+    const bool in_smem = vec && (P + 1) * d <= cap;
+    if (in_smem) {
+      for (int e = threadIdx.x; e < items; e += kThreads)
+        cp_async16(scratch + 4 * e, pos_prev + nb + 4 * (int64_t)e, 16);
+      for (int q = threadIdx.x; q < d4; q += kThreads)
+        cp_async16(scratch + P * d + 4 * q, sw.gbest + (int64_t)a * d + 4 * q, 16);
+      cp_async_commit();
+    }
+    float4 ia[2], sa[2];
     auto load2 = [&](int e0) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = e0 + u * kThreads;
         if (e < items) {
           const int64_t o = nb + 4 * (int64_t)e;  // element (p, 4q) of the node's rows
-          xa[u] = __ldcg(reinterpret_cast<const float4*>(pos_prev + o));
           ia[u] = __ldcg(reinterpret_cast<const float4*>(sw.ic + o));
           sa[u] = __ldcg(reinterpret_cast<const float4*>(sw.s2 + o));
         }
@@ -139,11 +150,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     load2(threadIdx.x);
     // gbest step of evaluation t - 1 (k_move's rule and double buffering)
     if (warp == 0) {
+      // the argmin only when a particle beat gB in evaluation t - 1 (every
+      // particle is a candidate at evaluation 0)
+      const bool any = t == 1 || !sw.imp || __ldcg(sw.imp + (int64_t)((t - 1) & 1) * A + a) != 0;
       const EvalRes gold = sw.gb[(int64_t)(t & 1) * A + a];
-      EvalRes be;
-      const int bi = gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t - 1, &be);
+      EvalRes be = gold;
+      const int bi = any ? gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t - 1, &be) : -1;
       if (lane == 0) {
         s_best = bi;
+        if (desig && sw.imp) sw.imp[(int64_t)(t & 1) * A + a] = 0;  // evaluation t's flag
         if (desig) {
           const EvalRes g = bi >= 0 ? be : gold;
           sw.gb[(int64_t)((t - 1) & 1) * A + a] = g;
@@ -157,12 +172,15 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
+    if (in_smem) cp_async_wait<0>();
     __syncthreads();
     const int bi = s_best;
     // a new best improved its pbest in evaluation t - 1: gB is that row
     const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
+    const float* gsm = bi >= 0 ? scratch + bi * d : scratch + P * d;
     if (desig && bi >= 0)
-      for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = gsrc[j];
+      for (int j = threadIdx.x; j < d; j += kThreads)
+        sw.gbest[(int64_t)a * d + j] = in_smem ? gsm[j] : gsrc[j];
     // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
     if (vec) {
       for (int e0 = threadIdx.x; e0 < items; e0 += 2 * kThreads) {
@@ -172,8 +190,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           const int e = e0 + u * kThreads;
           if (e >= items) break;
           const int p = e / d4, j = 4 * (e - p * d4);
-          const float4 x = xa[u], ic = ia[u], s2 = sa[u];
-          const float4 g = __ldcg(reinterpret_cast<const float4*>(gsrc + j));
+          const float4 x = in_smem ? *reinterpret_cast<const float4*>(scratch + 4 * e)
+                                   : __ldcg(reinterpret_cast<const float4*>(pos_prev + nb) + e);
+          const float4 ic = ia[u], s2 = sa[u];
+          const float4 g = in_smem ? *reinterpret_cast<const float4*>(gsm + j)
+                                   : __ldcg(reinterpret_cast<const float4*>(gsrc + j));
           float4 vn, xn;
           vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
           vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
@@ -235,7 +256,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();  // the previous node's positions and ranges are done with
       if (cur_a >= 0) flush_ranges(cur_a);
       cur_a = wt.node;
-      node_positions(cur_a, wt.row0 == nodes[cur_a].seg_start);
+      // stage buffer (s + 1) & 1 is free until the copies of step s + 1
+      node_positions(cur_a, wt.row0 == nodes[cur_a].seg_start, (s & 1) ? xs0 : xs1, RT * kXS);
     }
     if (s + 1 < n_st) {
       stage(s + 1, (s & 1) ? xs0 : xs1);
