@@ -327,6 +327,86 @@ def tree_loss(ctx, f, wl, X):
             "ensemble_error": float(np.mean(cls != wl.labels))}
 
 
+def split_loss(f, n_trees=1):
+    """Summed weighted child impurity of every split (Eq. 4: each split's
+    loss times the weight of the node it splits), over the root's weight."""
+    tot = 0.0
+    for t in range(n_trees):
+        g = f.export(t)
+        inner = g["kind"] == 1
+        tot += float(np.sum(g["loss"][inner] * g["weight"][inner]) / max(1, g["weight"][0]))
+    return tot / n_trees
+
+
+def vs_plain_fp32(ctx, S, cfg, wl, X, L, Y, flush, stream, steps, plain):
+    """The default classification tree in the combined form beside plain FP32
+    PSO: level-batched searches with BF16 tensor-core projections and FP32
+    re-scoring of the top 8 particles, without and with the learned swarm
+    proposal (trained first, on (node statistics, PSO-best direction) pairs
+    from nodes of the same mixture drawn with disjoint sample seeds), at T
+    and at T / 4 iterations, and the seeded FP32 form; tree time (device
+    events, mean of the steps), training Gini and summed split loss of each
+    beside the plain FP32 form's."""
+    rng = np.random.default_rng(77)
+    stats, dims, targets = [], [], []
+    t0 = time.perf_counter()
+    K, d = wl.n_classes, wl.d
+    for i in range(160):
+        w2 = W.gmm(6000, d, K, seed=1, sample_seed=900_000 + i)
+        keep = rng.choice(K, rng.integers(2, K + 1), replace=False)
+        m = np.isin(w2.labels, keep)
+        remap = np.full(K, -1, np.int32)
+        remap[np.sort(keep)] = np.arange(keep.size)
+        Xs, ls = w2.X[m], remap[w2.labels[m]]
+        r = ctx.node_split(S.make_params("gini", K, n_particles=cfg["n_particles"], n_iters=50,
+                                         n_bins=cfg["n_bins"], min_leaf=cfg["min_leaf"],
+                                         seed=i + 3), Xs, labels=ls, node_uid=i)
+        stats.append(ctx.node_stats(Xs, labels=ls, n_classes=K))
+        dims.append(d)
+        tg = np.zeros(256, np.float32)
+        tg[:d] = r["direction"]
+        targets.append(tg)
+    t_pairs = time.perf_counter() - t0
+    prop = ctx.proposal(seed=11)
+    t0 = time.perf_counter()
+    prop.train(np.array(stats, np.float32), np.array(dims, np.int32),
+               np.array(targets, np.float32), epochs=30, batch=64, lr=1e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    ctx.use_proposal(prop)
+    out = {"plain_fp32": plain}
+    T = cfg["n_iters"]
+    try:
+        for key, proj, seeded, iters in (("bf16_top8", "bf16", False, T),
+                                         ("seeded_bf16_top8", "bf16", True, T),
+                                         ("seeded_bf16_top8_T/4", "bf16", True, T // 4),
+                                         ("seeded_fp32", "fp32", True, T),
+                                         ("seeded_fp32_T/4", "fp32", True, T // 4)):
+            pp = make_params(S, dict(cfg, n_iters=iters), wl, proj, 8)
+            pp.seeded = 1 if seeded else 0
+            ctx.train_tree(pp, X, labels=L, y=Y).free()  # warm-up (tiles, graphs)
+            tp, ep, _ = time_steps(ctx, pp, X, L, Y, steps, flush, stream)
+            f = ctx.train_tree(pp, X, labels=L, y=Y)
+            out[key] = {"tree_train_ms": sum(tp) / len(tp), "iters": iters,
+                        "evaluations": ep // steps, "train_loss": tree_loss(ctx, f, wl, X),
+                        "split_loss_sum": split_loss(f)}
+            f.free()
+    finally:
+        ctx.use_proposal(None)
+        prop.free()
+    gini = lambda k: out[k]["train_loss"]["tree0_gini"]
+    for k in out:
+        if k != "plain_fp32":
+            out[k]["time_vs_plain"] = out[k]["tree_train_ms"] / plain["tree_train_ms"]
+            out[k]["loss_le_plain"] = bool(gini(k) <= gini("plain_fp32") + 1e-12 and
+                                          out[k]["split_loss_sum"] <=
+                                          plain["split_loss_sum"] + 1e-12)
+    out["proposal"] = {"training_pairs": len(dims), "pair_generation_s": t_pairs,
+                       "train_s": t_train,
+                       "pairs": "class subsets of the tree's mixture (same means and "
+                                "covariance), 6,000 samples with disjoint sample seeds"}
+    return out
+
+
 def leaf_gini(leaf, labels, K):
     """Weighted Gini impurity of a partition into leaves: sum over leaves of
     n_leaf (1 - sum_k p_k^2), divided by n."""
@@ -428,9 +508,30 @@ def time_steps(ctx, p, X, L, Y, steps, flush, stream, cfg=None):
     return times, evals, ctx.launch_count() - launches0
 
 
-def rooflines(kst, wl, cfg, proj, topk, workload):
+def measured_roofs(device, stream):
+    """FP32 FFMA and L2-read roofs from the library's microbenchmarks
+    (slm_measure_peaks), or the derived FFMA rate and HBM copy when they fail."""
+    from paper_2208_07023_gb300 import binding as S
+    try:
+        m = S.measure_peaks(device, stream)
+        return {"ffma_tflops": m["ffma_tflops"], "l2_gbs": m["l2_read_gbs"],
+                "ffma_source": "measured: slm_measure_peaks FFMA chains (16 per thread, "
+                               "64 warps per SM), best of 3 launches",
+                "l2_source": "measured: slm_measure_peaks 48 MB L2-resident buffer, "
+                             "16-byte cache-global loads, best of 3 launches"}
+    except Exception as e:  # noqa: BLE001
+        return {"ffma_tflops": FP32_PEAK_TFLOPS, "l2_gbs": HBM_PEAK_GBS,
+                "ffma_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (%s)" % e,
+                "l2_source": "HBM copy (%s)" % PEAK_SOURCE}
+
+
+def rooflines(kst, wl, cfg, proj, topk, workload, roofs_in=None):
     """Per-kernel roofline from the profiled pass."""
     P, d = cfg["n_particles"], wl.d
+    mr = roofs_in or {"ffma_tflops": FP32_PEAK_TFLOPS, "l2_gbs": HBM_PEAK_GBS,
+                      "ffma_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                      "l2_source": "HBM copy"}
+    ffma, l2 = mr["ffma_tflops"], mr["l2_gbs"]
     dp = (d + 15) // 16 * 16
     roofs = {}
     kp, kh, km = kst["project"], kst["hist_scan"], kst["project_mma"]
@@ -440,19 +541,19 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
         # particle-sample evaluation (the kernel projects twice: range, bins)
         ach = 2.0 * d * kn["pairs"] / (kn["ms"] / 1e3) / 1e12
         roofs["node_search"] = {"kernel": "node_search", "bound": "alu", "achieved": ach,
-                                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                                "peak": ffma, "unit": "TFLOP/s",
+                                "frac": ach / ffma, "traffic": None,
                                 "avg_launch_ms": kn["ms"] / max(1, kn["launches"]),
-                                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+                                "peak_source": mr["ffma_source"]}
     if kp["ms"] > 0:
         # FP32 FFMA: 2 d flop per particle-sample pair
         ach = 2.0 * d * kp["pairs"] / (kp["ms"] / 1e3) / 1e12
         roofs["project"] = {"kernel": "project", "bound": "alu", "achieved": ach,
-                            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach / FP32_PEAK_TFLOPS,
+                            "peak": ffma, "unit": "TFLOP/s",
+                            "frac": ach / ffma,
                             "traffic": traffic_per_launch("project", kp, workload),
                             "avg_launch_ms": kp["ms"] / max(1, kp["launches"]),
-                            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+                            "peak_source": mr["ffma_source"]}
     if kh["ms"] > 0:
         # z (4 B per pair) + per entry and pass its label (4 B) or, for MSE,
         # its two 8-byte fixed-point moments (+ a 4-byte multiplicity when
@@ -462,11 +563,12 @@ def rooflines(kst, wl, cfg, proj, topk, workload):
         entry_b = (16.0 if cfg["criterion"] == "mse" else 4.0) + (4.0 if weighted else 0.0)
         algo = kh["pairs"] * (4.0 + entry_b / per_entry)
         ach = algo / (kh["ms"] / 1e3) / 1e9
-        roofs["hist_scan"] = {"kernel": "hist_scan", "bound": "hbm", "achieved": ach,
-                              "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
+        # the projections, labels and moments it reads are L2-resident
+        roofs["hist_scan"] = {"kernel": "hist_scan", "bound": "l2", "achieved": ach,
+                              "peak": l2, "unit": "GB/s", "frac": ach / l2,
                               "traffic": traffic_per_launch("hist_scan", kh, workload),
                               "avg_launch_ms": kh["ms"] / max(1, kh["launches"]),
-                              "peak_source": f"{PEAK_SOURCE} (MEASURED_PEAKS.json hbm_gbs)"}
+                              "peak_source": mr["l2_source"]}
     if km["ms"] > 0:
         # bf16 rows read once per launch: dp * 2 bytes per entry = pairs / P
         algo = km["pairs"] / P * dp * 2.0
@@ -546,6 +648,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     clocks = ClockSampler(gpu_uuid(local)).start()  # running before the timed region
+    roofs_measured = measured_roofs(local, stream.cuda_stream)
     for _ in range(args.warmup):
         train_step(ctx, p, cfg, X, L, Y).free()
 
@@ -578,6 +681,7 @@ def run_ours(args):
     # training loss of the trees this form grows
     f = train_step(ctx, p, cfg, X, L, Y)
     loss = step_loss(ctx, f, wl, X)
+    sl = None if isinstance(f, BoostRun) else split_loss(f, cfg["n_trees"])
     f.free()
 
     extra = {"tree_train_ms": tot_ms_max / args.steps, "evals_per_step": evals // args.steps,
@@ -586,7 +690,15 @@ def run_ours(args):
                  "one CUDA graph launch per level search" if args.graphs == "on"
                  else "PDL-chained stream launches")),
              "projection_tiles": ctx.tuned_shapes(),
-             "last_hist_cluster": ctx.tuning_stats()["last_hist_cluster"]}
+             "last_hist_cluster": ctx.tuning_stats()["last_hist_cluster"],
+             "measured_roofs": roofs_measured}
+    if sl is not None:
+        extra["split_loss_sum"] = sl
+    if (name == DEFAULT_WORKLOAD and proj == "fp32" and world == 1 and args.vs_plain == "on"):
+        extra["vs_plain_fp32"] = vs_plain_fp32(
+            ctx, S, cfg, wl, X, L, Y, flush, stream, args.steps,
+            {"tree_train_ms": tot_ms / args.steps, "iters": cfg["n_iters"],
+             "evaluations": evals // args.steps, "train_loss": loss, "split_loss_sum": sl})
     if args.compare_plain and (cfg.get("top_n") or cfg.get("apso")):
         # the same tree without the pre-screen / adaptive PSO, same harness
         pp = make_params(S, dict(cfg, top_n=0, apso=False), wl, proj, topk)
@@ -637,7 +749,7 @@ def run_ours(args):
     e2e_value = e2e_ev / sum(e2e_t)
     h2d = wl.X.nbytes + (wl.labels.nbytes if wl.labels is not None else wl.y.nbytes)
 
-    roofs = rooflines(kst, wl, cfg, proj, topk, name)
+    roofs = rooflines(kst, wl, cfg, proj, topk, name, roofs_measured)
     dom = max(roofs, key=lambda k: kst[k]["ms"])
     roofline = dict(roofs[dom])
     roofline["timing"] = "per-launch CUDA events in a second K-step pass"
@@ -888,6 +1000,9 @@ def main():
     ap.add_argument("--node-step", choices=["on", "off"], default="off",
                     help="folded classification searches: gbest step and move in the last "
                          "histogram block of each node (on) or in every projection block (off)")
+    ap.add_argument("--vs-plain", choices=["on", "off"], default="on",
+                    help="default workload: also time the BF16 top-8 and learned-seeded forms "
+                         "beside plain FP32 (config.vs_plain_fp32)")
     ap.add_argument("--apso", action="store_true",
                     help="adaptive PSO (FP32 form): the workload's searches adapt inertia "
                          "and learning factors to the swarm's evolutionary state")

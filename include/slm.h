@@ -566,6 +566,19 @@ slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
  * node_step = 0 (the default): the projection blocks do it. Results are
  * identical in every combination. */
 slm_status slm_set_class_hist(slm_ctx* ctx, int32_t on, int32_t node_step);
+/* Roofline measurement (not part of the method): on `device`, with CUDA
+ * events on `cuda_stream` (NULL = legacy default stream), *ffma_tflops
+ * receives the FP32 fused multiply-add throughput of a kernel of independent
+ * FMA chains filling every SM (2 flop per FMA; best of three timed launches
+ * after a warm-up), the roof of the projection, whose rows stay in L2
+ * across a search's iterations; *l2_read_gbs receives the read bandwidth of
+ * a 48 MB L2-resident buffer streamed with 16-byte cache-global loads, the
+ * roof of the histogram kernels, which read what the projection wrote.
+ * Either pointer may be NULL (not both). The call allocates and frees its
+ * own buffers, synchronises the stream, and restores the calling thread's
+ * current device. Errors: SLM_EINVAL, SLM_ECUDA. */
+slm_status slm_measure_peaks(int device, void* cuda_stream, double* ffma_tflops,
+                             double* l2_read_gbs);
 /* Graph launches of the context: in total, of kept graphs launched again
  * unchanged, updated in place, and instantiated anew (any may be NULL). */
 slm_status slm_graph_stats(slm_ctx* ctx, int64_t* launches, int64_t* reuses,

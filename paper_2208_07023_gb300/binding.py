@@ -98,6 +98,7 @@ def lib():
             "slm_set_projection_tma": ([vp, i32], C.c_int),
             "slm_set_fused_step": ([vp, i32, P(i64)], C.c_int),
             "slm_set_class_hist": ([vp, i32, i32], C.c_int),
+            "slm_measure_peaks": ([C.c_int, vp, P(C.c_double), P(C.c_double)], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
             "slm_set_node_search": ([vp, i32], C.c_int),
@@ -134,6 +135,16 @@ def lib():
             f.restype = res
         _lib = L
     return _lib
+
+
+def measure_peaks(device: int = 0, stream=None) -> dict:
+    """slm_measure_peaks: measured FP32 FFMA throughput (TFLOP/s) and L2 read
+    bandwidth (GB/s) of `device`."""
+    f, g = C.c_double(), C.c_double()
+    st = lib().slm_measure_peaks(device, stream, C.byref(f), C.byref(g))
+    if st != SLM_OK:
+        raise SlmError(st, "slm_measure_peaks")
+    return {"ffma_tflops": f.value, "l2_read_gbs": g.value}
 
 
 def make_params(criterion="gini", n_classes=2, n_particles=32, n_iters=50,
