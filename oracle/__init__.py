@@ -147,6 +147,11 @@ def lib():
                                          C.c_uint32, C.c_void_p, C.c_void_p, P(Split),
                                          C.c_void_p, C.c_void_p]
             L.ora_node_split.restype = C.c_int
+            L.ora_node_split_from.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                              C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              P(Split), C.c_void_p, C.c_void_p]
+            L.ora_node_split_from.restype = C.c_int
             L.ora_select_features.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                               C.c_int32, C.c_void_p, C.c_void_p,
@@ -373,6 +378,29 @@ def node_split(params: Params, X, labels=None, y=None, idx=None, wts=None,
                               _ptr(dr), C.byref(sp), _ptr(tl), _ptr(tp))
     if rc:
         raise ValueError(f"ora_node_split failed: {rc}")
+    return SplitResult(_struct_dict(sp), gb, dr, tl, tp)
+
+
+def node_split_from(params: Params, X, init_x, labels=None, y=None, idx=None, wts=None,
+                    node_uid=0) -> SplitResult:
+    """node_split starting from the positions init_x[P, d] (float32) instead of
+    the uniform draws (a learned seed's start); velocities as usual."""
+    X, labels, y, idx, wts = _node_arrays(X, labels, y, idx, wts)
+    d = X.shape[1]
+    init_x = np.ascontiguousarray(init_x, dtype=np.float32)
+    if init_x.shape != (params.n_particles, d):
+        raise ValueError("init_x must be [n_particles, d]")
+    gb = np.zeros(d, dtype=np.float64)
+    dr = np.zeros(d, dtype=np.float64)
+    T = params.n_iters
+    tl = np.zeros(T + 1, dtype=np.float64)
+    tp = np.zeros(T + 1, dtype=np.int32)
+    sp = Split()
+    rc = lib().ora_node_split_from(C.byref(params), _ptr(X), d, _ptr(labels), _ptr(y),
+                                   _ptr(idx), _ptr(wts), idx.size, node_uid, _ptr(init_x),
+                                   _ptr(gb), _ptr(dr), C.byref(sp), _ptr(tl), _ptr(tp))
+    if rc:
+        raise ValueError(f"ora_node_split_from failed: {rc}")
     return SplitResult(_struct_dict(sp), gb, dr, tl, tp)
 
 

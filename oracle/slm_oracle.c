@@ -792,8 +792,8 @@ static void copy_eval_to_split(const ora_eval* e, ora_split* s) {
 static int node_split_full(const ora_params* p, const float* X, int32_t d,
                            const int32_t* labels, const float* y, const int32_t* idx,
                            const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
-                           double* gbest_out, double* dir_out, ora_split* out,
-                           double* trace_loss, int32_t* trace_particle) {
+                           const float* init_x, double* gbest_out, double* dir_out,
+                           ora_split* out, double* trace_loss, int32_t* trace_particle) {
   if (check_params(p, d) || p->n_particles < 1 || p->n_iters < 0 || n_idx < 0 ||
       !X || !idx || !out || (p->precision == ORA_BF16_TOPK && p->topk < 1) ||
       (p->apso && p->precision == ORA_BF16_TOPK))
@@ -823,9 +823,10 @@ static int node_split_full(const ora_params* p, const float* X, int32_t d,
   memset(out, 0, sizeof(*out));
   out->first_near_tie = -1;
 
-  /* Initial swarm: x ~ U[-1,1)^d, v ~ 0.1 * U[-1,1)^d. */
+  /* Initial swarm: x ~ U[-1,1)^d (or the given start, e.g. a learned seed),
+   * v ~ 0.1 * U[-1,1)^d. */
   ora_swarm_uniforms(p->seed, node_uid, 0, P, d, ORA_PURPOSE_INIT_X, u);
-  for (int64_t e = 0; e < PD; ++e) x[e] = (double)(2.0f * u[e] - 1.0f);
+  for (int64_t e = 0; e < PD; ++e) x[e] = init_x ? (double)init_x[e] : (double)(2.0f * u[e] - 1.0f);
   ora_swarm_uniforms(p->seed, node_uid, 0, P, d, ORA_PURPOSE_INIT_V, u);
   for (int64_t e = 0; e < PD; ++e) {
     if (p->precision != ORA_F64)
@@ -1043,8 +1044,8 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
                    double* trace_loss, int32_t* trace_particle) {
   const int32_t n = p ? p->top_n : 0;
   if (n <= 0 || n >= d)
-    return node_split_full(p, X, d, labels, y, idx, wts, n_idx, node_uid, gbest_out, dir_out,
-                           out, trace_loss, trace_particle);
+    return node_split_full(p, X, d, labels, y, idx, wts, n_idx, node_uid, NULL, gbest_out,
+                           dir_out, out, trace_loss, trace_particle);
   /* the swarm searches the n-dimensional subspace of the selected features;
    * its direction is lifted back with zeros elsewhere */
   if (check_params(p, d) || !X || !idx || n_idx < 0 || !out) return -1;
@@ -1066,8 +1067,8 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
     const int64_t r = idx[i];
     for (int32_t j = 0; j < n; ++j) Xs[r * n + j] = X[r * d + feat[j]];
   }
-  rc = node_split_full(p, Xs, n, labels, y, idx, wts, n_idx, node_uid, gs, ds, out, trace_loss,
-                       trace_particle);
+  rc = node_split_full(p, Xs, n, labels, y, idx, wts, n_idx, node_uid, NULL, gs, ds, out,
+                       trace_loss, trace_particle);
   if (rc) goto done;
   if (gbest_out)
     for (int32_t k = 0; k < d; ++k) gbest_out[k] = 0.0;
@@ -1084,6 +1085,16 @@ done:
   free(gs);
   free(ds);
   return rc;
+}
+
+int ora_node_split_from(const ora_params* p, const float* X, int32_t d,
+                        const int32_t* labels, const float* y, const int32_t* idx,
+                        const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
+                        const float* init_x, double* gbest_out, double* dir_out,
+                        ora_split* out, double* trace_loss, int32_t* trace_particle) {
+  if (!init_x || (p && p->top_n > 0 && p->top_n < d)) return -1;
+  return node_split_full(p, X, d, labels, y, idx, wts, n_idx, node_uid, init_x, gbest_out,
+                         dir_out, out, trace_loss, trace_particle);
 }
 
 int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,

@@ -234,6 +234,15 @@ int ora_node_split(const ora_params* p, const float* X, int32_t d,
                    double* gbest_out, double* dir_out, ora_split* out,
                    double* trace_loss, int32_t* trace_particle);
 
+/* ora_node_split (without the feature pre-screen) from a given initial
+ * swarm: init_x[P*d] (float) replaces the uniform initial positions of Sec.
+ * III-A, as a learned seed does; the velocities are the random start's. */
+int ora_node_split_from(const ora_params* p, const float* X, int32_t d,
+                        const int32_t* labels, const float* y, const int32_t* idx,
+                        const uint32_t* wts, int64_t n_idx, uint32_t node_uid,
+                        const float* init_x, double* gbest_out, double* dir_out,
+                        ora_split* out, double* trace_loss, int32_t* trace_particle);
+
 /* Grow one tree (Algorithm 2, breadth-first). bootstrap != 0 draws the
  * tree's bag with ora_bootstrap(seed, tree_id, n). */
 int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,

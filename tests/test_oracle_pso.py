@@ -141,3 +141,20 @@ def test_one_iteration_follows_documented_streams(precision):
                 gb, ge, g = x[i].copy(), ev[i], i
     assert np.array_equal(r.gbest, gb)
     assert r.split["particle"] == g and r.split["loss"] == ge["loss"]
+
+
+def test_search_from_given_start_equals_search_from_its_own_draws():
+    """A search started from the positions the uniform draws give is the
+    plain search; a different start changes the trajectory."""
+    import oracle as O
+    from paper_2208_07023_gb300 import workloads as W
+    wl = W.gmm(800, 6, 3, seed=4)
+    p = O.make_params("gini", 3, n_particles=12, n_iters=8, n_bins=32, min_leaf=3,
+                      precision=O.F32_MIRROR, seed=5)
+    u = O.swarm_uniforms(5, 7, 0, 12, 6, 1)
+    x0 = (2.0 * u - 1.0).astype(np.float32)
+    a = O.node_split(p, wl.X, wl.labels, node_uid=7)
+    b = O.node_split_from(p, wl.X, x0, wl.labels, node_uid=7)
+    assert np.array_equal(a.trace_loss, b.trace_loss) and np.array_equal(a.gbest, b.gbest)
+    c = O.node_split_from(p, wl.X, -x0, wl.labels, node_uid=7)
+    assert not np.array_equal(c.gbest, a.gbest)
