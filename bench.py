@@ -613,8 +613,17 @@ def reduce_over_ranks(ms, evals, world, device):
 
 
 def rank_seed(rank):
-    """Workload seed of a rank: every rank trains on its own data."""
+    """Workload seed of a rank for single-tree workloads: every rank trains
+    its own tree on its own data (independent problems, weak scaling)."""
     return 1 + rank
+
+
+def rank_forest_share(n_trees, rank, world):
+    """Trees of one forest that rank `rank` of `world` grows: r, r + N, ...
+    as (first global tree id, stride, count). The ranks share the data; each
+    tree's bootstrap draw and swarm streams are keyed by its global id, so
+    the ranks' trees together are exactly the forest one rank would grow."""
+    return rank, world, len(range(rank, n_trees, world))
 
 
 def run_ours(args):
@@ -637,13 +646,22 @@ def run_ours(args):
 
     name, proj, topk = args.workload, args.proj, args.topk
     cfg = W.SETTINGS[name]
-    wl = cfg["builder"](rank_seed(rank))  # each rank: its own tree
+    forest_split = cfg["n_trees"] > 1 and world > 1 and not cfg.get("rounds")
+    if forest_split:
+        # one forest split across the ranks: the same data, trees r, r + N, ...
+        wl = cfg["builder"](1)
+        first, stride, count = rank_forest_share(cfg["n_trees"], rank, world)
+        cfg = dict(cfg, n_trees=max(1, count))
+    else:
+        wl = cfg["builder"](rank_seed(rank))  # each rank: its own tree
     X = torch.from_numpy(wl.X).cuda()
     L = torch.from_numpy(wl.labels).cuda() if wl.labels is not None else None
     Y = torch.from_numpy(wl.y).cuda() if wl.y is not None else None
     stream = torch.cuda.current_stream()
     ctx = S.Context(local, stream.cuda_stream)
     apply_launch_options(ctx, args)
+    if forest_split:
+        ctx.set_tree_ids(first, stride)
     p = make_params(S, cfg, wl, proj, topk)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -682,6 +700,19 @@ def run_ours(args):
     f = train_step(ctx, p, cfg, X, L, Y)
     loss = step_loss(ctx, f, wl, X)
     sl = None if isinstance(f, BoostRun) else split_loss(f, cfg["n_trees"])
+    split_info = None
+    if forest_split:
+        # only the tree arrays travel: rank 0 assembles the whole forest in
+        # global tree order (outside the timed region)
+        mine = [(first + t * stride, f.export(t)) for t in range(count)]
+        parts = [None] * world
+        dist.all_gather_object(parts, mine)
+        forest = dict(kv for part in parts for kv in part)
+        split_info = {"ranks": world, "trees_of_rank": [len(x) for x in parts],
+                      "trees_gathered": len(forest),
+                      "tree_ids_complete": sorted(forest) == list(range(W.SETTINGS[name]["n_trees"])),
+                      "rule": "rank r grows trees r, r + N, ... of one forest on the shared "
+                              "data; tree t's bootstrap and swarm streams are keyed by t"}
     f.free()
 
     extra = {"tree_train_ms": tot_ms_max / args.steps, "evals_per_step": evals // args.steps,
@@ -692,6 +723,8 @@ def run_ours(args):
              "projection_tiles": ctx.tuned_shapes(),
              "last_hist_cluster": ctx.tuning_stats()["last_hist_cluster"],
              "measured_roofs": roofs_measured}
+    if split_info:
+        extra["forest_split"] = split_info
     if sl is not None:
         extra["split_loss_sum"] = sl
     if (name == DEFAULT_WORKLOAD and proj == "fp32" and world == 1 and args.vs_plain == "on"):
@@ -767,7 +800,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            # one forest split across the ranks: fixed total work
+            "scaling": "strong" if forest_split else "weak", "vs_baseline": None,
             "dtype": "bf16+f32" if proj == "bf16" else "f32",
             "data": "synthetic (seeded, workloads.py)",
             "config": config_dict(name, cfg, wl, proj, topk, extra, args),

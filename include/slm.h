@@ -260,6 +260,15 @@ slm_status slm_forest_begin(slm_ctx* ctx, const slm_params* params,
                             slm_forest** out);
 slm_status slm_grow_level(slm_ctx* ctx, slm_forest* forest,
                           int32_t* n_split_out);
+/* Global tree ids of the forests the context begins from now on: local
+ * tree t of a forest is tree first + t * stride of a larger forest, whose
+ * bootstrap draw (slm_bootstrap, tree_id) and node uids (tree_id << 16 |
+ * heap index) it uses, so that N processes growing trees r, r + N, ... of
+ * one forest (Sec. V, SLM Forest) with first = r, stride = N together grow
+ * exactly the trees one process would. Defaults 0, 1. SLM_EINVAL unless
+ * 0 <= first <= 65535 and 1 <= stride <= 65535; a forest whose ids would
+ * pass 65535 is refused by slm_forest_begin. */
+slm_status slm_set_tree_ids(slm_ctx* ctx, int64_t first, int64_t stride);
 /* forest_begin + grow_level until complete. */
 slm_status slm_train_tree(slm_ctx* ctx, const slm_params* params,
                           const float* X, int64_t n, int32_t d,
@@ -423,6 +432,17 @@ slm_status slm_use_proposal(slm_ctx* ctx, const slm_proposal* prop);
 slm_status slm_swarm_seed(slm_ctx* ctx, uint64_t seed, uint32_t node_uid,
                           int32_t n_particles, int32_t d, const float* mu_hat,
                           const float* rho, float* pos);
+/* The start a seeded search (params.seeded = 1, the context's proposal)
+ * gives node (X rows sample_idx, labels / y, weights, node_uid; arguments as
+ * slm_node_split): pos_out[n_particles x d] (host or device) receives the
+ * positions of the node's initial swarm, computed by the search's own
+ * kernels (node statistics, network forward, slm_swarm_seed's rule) as the
+ * search would. SLM_EINVAL without a proposal in use or params.seeded != 1;
+ * the seeded limits of slm_use_proposal apply. */
+slm_status slm_seeded_start(slm_ctx* ctx, const slm_params* params, const float* X, int64_t n,
+                            int32_t d, const int32_t* labels, const float* y,
+                            const int32_t* sample_idx, const uint32_t* weights, int64_t n_idx,
+                            uint32_t node_uid, float* pos_out);
 
 /* ---- diagnostics --------------------------------------------------------
  * Kernels of this library, for per-kernel timing. */

@@ -98,6 +98,9 @@ def lib():
             "slm_set_projection_tma": ([vp, i32], C.c_int),
             "slm_set_fused_step": ([vp, i32, P(i64)], C.c_int),
             "slm_set_class_hist": ([vp, i32, i32], C.c_int),
+            "slm_set_tree_ids": ([vp, i64, i64], C.c_int),
+            "slm_seeded_start": ([vp, P(slm_params), vp, i64, i32, vp, vp, vp, vp, i64, u32,
+                                  vp], C.c_int),
             "slm_measure_peaks": ([C.c_int, vp, P(C.c_double), P(C.c_double)], C.c_int),
             "slm_set_tuning": ([vp, i32], C.c_int),
             "slm_set_small_nodes": ([vp, i32, i64], C.c_int),
@@ -496,6 +499,11 @@ class Context:
         self._check(lib().slm_set_fused_step(self.handle, 1 if on else 0, C.byref(n)))
         return n.value
 
+    def set_tree_ids(self, first: int = 0, stride: int = 1):
+        """slm_set_tree_ids: local tree t of later forests is global tree
+        first + t * stride (bootstrap draw and node uids)."""
+        self._check(lib().slm_set_tree_ids(self.handle, first, stride))
+
     def set_class_hist(self, on: bool, node_step: bool = True):
         """slm_set_class_hist: the latency-oriented classification histogram kernel,
         and whether its last block per node takes the gbest step and the move."""
@@ -541,6 +549,21 @@ class Context:
             _ptr(sample_idx), _ptr(weights), n_idx, _ptr(positions), n_pos, out,
             _ptr(bins)))
         return [_eval_dict(e) for e in out], bins
+
+    def seeded_start(self, params, X, labels=None, y=None, sample_idx=None, weights=None,
+                     node_uid=0):
+        """slm_seeded_start: the initial positions [P, d] a seeded search of this
+        node starts from."""
+        X = _as(X, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
+        n, d = X.shape
+        n_idx = n if sample_idx is None else sample_idx.shape[0]
+        pos = np.empty((params.n_particles, d), np.float32)
+        self._check(lib().slm_seeded_start(
+            self.handle, C.byref(params), _ptr(X), n, d, _ptr(labels), _ptr(y),
+            _ptr(sample_idx), _ptr(weights), n_idx, node_uid, _ptr(pos)))
+        return pos
 
     def node_split(self, params, X, labels=None, y=None, sample_idx=None,
                    weights=None, node_uid=0, want_trace=False):

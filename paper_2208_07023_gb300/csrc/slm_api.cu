@@ -115,6 +115,9 @@ struct slm_ctx {
   // folded searches whose nodes all take k_hist_cls: the move in its last
   // CTA per node (else in every k_step CTA)
   bool node_step = false;
+  // global tree id of a forest's local tree t: tree_id0 + t * tree_stride
+  // (a forest split across processes grows trees r, r + N, ... on rank r)
+  int64_t tree_id0 = 0, tree_stride = 1;
   cudaStream_t cap_stream = nullptr;  // records graphs (the caller's stream may
                                       // be the legacy default stream)
   // executable graphs by launch signature (every kernel node's function,
@@ -164,6 +167,8 @@ struct slm_forest {
   DevBuf lX[2], lab[2], ly[2], lw[2], lidx[2], side;
   DevBuf lXb;     // bfloat16 rows of the current level (SLM_PROJ_BF16_TOPK)
   int align = 4;  // node segments start on multiples of this many entries
+  int64_t tree_id0 = 0, tree_stride = 1;  // global id of local tree t
+  uint32_t tree_id(int t) const { return (uint32_t)(tree_id0 + (int64_t)t * tree_stride); }
   int cur = 0;
   bool weighted = false;
   std::vector<LevelNode> level;  // nodes of the level to grow next
@@ -1716,6 +1721,32 @@ slm_status slm_evaluate_swarm(slm_ctx* c, const slm_params* p, const float* X,
   return SLM_OK;
 }
 
+slm_status slm_seeded_start(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                            int32_t d, const int32_t* labels, const float* y,
+                            const int32_t* sample_idx, const uint32_t* weights, int64_t n_idx,
+                            uint32_t node_uid, float* pos_out) {
+  if (!c) return SLM_EINVAL;
+  if (slm_status s = check_node_args(c, p, X, n, d, labels, y, sample_idx, &n_idx, true))
+    return s;
+  if (!pos_out || !p->seeded || !c->prop)
+    return fail(c, SLM_EINVAL, "needs pos_out, params.seeded = 1 and a proposal in use");
+  CK(cudaSetDevice(c->device));
+  Problem pr;
+  if (slm_status s = prepare_node(c, p, X, n, d, labels, y, sample_idx, weights, n_idx,
+                                  p->n_particles, &pr))
+    return s;
+  std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, node_uid, -1}};
+  const std::vector<WorkTile> tiles = plan_tiles(nodes);
+  Swarm sw;
+  if (slm_status s = setup_swarm(c, pr, 1, 0, false, nodes, tiles, &sw)) return s;
+  const SwarmCoef co{p->inertia, p->c1, p->c2, p->seed};
+  if (slm_status s = seed_swarms(c, pr, nodes, sw, co)) return s;
+  CK(cudaMemcpyAsync(pos_out, sw.pos, sizeof(float) * (size_t)p->n_particles * d,
+                     cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SLM_OK;
+}
+
 slm_status slm_node_split(slm_ctx* c, const slm_params* p, const float* X,
                           int64_t n, int32_t d, const int32_t* labels,
                           const float* y, const int32_t* sample_idx,
@@ -1825,6 +1856,8 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
     return fail(c, SLM_EINVAL, "max_depth must be in [0, 15]");
   if (p->n_trees < 1 || p->n_trees > 65535)
     return fail(c, SLM_EINVAL, "n_trees must be in [1, 65535]");
+  if (c->tree_id0 + (int64_t)(p->n_trees - 1) * c->tree_stride > 65535)
+    return fail(c, SLM_EINVAL, "global tree ids (slm_set_tree_ids) pass 65535");
   if (p->criterion == SLM_GINI && n >= (int64_t(1) << 22))
     return fail(c, SLM_EUNSUPPORTED, "Gini needs fewer than 2^22 samples per tree");
   if ((int64_t)n * p->n_trees > INT32_MAX)
@@ -1835,6 +1868,8 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   f->ctx = c;
   f->device = c->device;
   f->params = *p;
+  f->tree_id0 = c->tree_id0;
+  f->tree_stride = c->tree_stride;
   f->n = n;
   f->d = d;
   f->H = (1 << (p->max_depth + 1)) - 1;
@@ -1886,7 +1921,7 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
     for (int t = 0; t < f->n_trees; ++t) {
       off[t] = (int64_t)t * n;
       c->launches += 1;
-      e = launch_bootstrap(p->seed, (uint32_t)t, n, static_cast<uint32_t*>(wall.p) + off[t],
+      e = launch_bootstrap(p->seed, f->tree_id(t), n, static_cast<uint32_t*>(wall.p) + off[t],
                            c->stream);
       if (e) {
         cleanup();
@@ -2062,7 +2097,7 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     const LevelNode& ln = f->level[l];
     const int tree = ln.slot / f->H, h = ln.slot % f->H;
     snodes.push_back(NodeDesc{ln.seg_start, ln.seg_len,
-                              ((uint32_t)tree << 16) | (uint32_t)h, ln.slot});
+                              (f->tree_id(tree) << 16) | (uint32_t)h, ln.slot});
     smap.push_back(l);
     stile0.push_back(n_st);
     n_st += (ln.seg_len + kTS - 1) / kTS;  // the tiles plan_tiles makes
@@ -2798,6 +2833,13 @@ slm_status slm_set_fused_step(slm_ctx* c, int32_t on, int64_t* searches) {
   if (!c) return SLM_EINVAL;
   c->fused_step = on != 0;
   if (searches) *searches = c->fused_searches;
+  return SLM_OK;
+}
+
+slm_status slm_set_tree_ids(slm_ctx* c, int64_t first, int64_t stride) {
+  if (!c || first < 0 || stride < 1 || first > 65535 || stride > 65535) return SLM_EINVAL;
+  c->tree_id0 = first;
+  c->tree_stride = stride;
   return SLM_OK;
 }
 

@@ -93,3 +93,66 @@ def test_bench_line_keys_of_reference_arm():
         assert k in j, k
     assert j["impl"] == "reference" and j["value"] > 0
     assert j["config"]["workload"] == "node_n2000_d16"
+
+
+def forest_rank_main(rank, world, port, out):
+    """Rank r grows trees r, r + N, ... of one small bagged forest with the
+    oracle (every tree keyed by its global id) and the ranks gather them."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import oracle as O
+    from paper_2208_07023_gb300 import workloads as W
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        wl = W.gmm(600, 4, 3, seed=5)
+        p = O.make_params("gini", 3, n_particles=8, n_iters=4, n_bins=16, max_depth=3,
+                          min_leaf=5, precision=O.F32_MIRROR)
+        first, stride, count = bench.rank_forest_share(5, rank, world)
+        mine = []
+        for t in range(count):
+            tid = first + t * stride
+            tr = O.train_tree(p, wl.X, wl.labels, tree_id=tid, bootstrap=True)
+            mine.append((tid, {k: np.asarray(getattr(tr, k)).tolist()
+                               for k in ("kind", "bin", "leaf_class", "weight", "dir")}))
+        parts = [None] * world
+        dist.all_gather_object(parts, mine)
+        out[rank] = sorted(kv for part in parts for kv in part)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_forest_split_across_two_gloo_ranks_equals_one_rank():
+    import numpy as np
+
+    import oracle as O
+    from paper_2208_07023_gb300 import workloads as W
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        out = man.dict()
+        mp.start_processes(forest_rank_main, args=(2, free_port(), out), nprocs=2, join=True,
+                           start_method="spawn")
+        got = out[0]
+        assert out[1] == got
+    assert [tid for tid, _ in got] == [0, 1, 2, 3, 4]
+    wl = W.gmm(600, 4, 3, seed=5)
+    p = O.make_params("gini", 3, n_particles=8, n_iters=4, n_bins=16, max_depth=3,
+                      min_leaf=5, precision=O.F32_MIRROR)
+    for tid, arrays in got:
+        ref = O.train_tree(p, wl.X, wl.labels, tree_id=tid, bootstrap=True)
+        for k, v in arrays.items():
+            assert np.array_equal(np.asarray(v), np.asarray(getattr(ref, k))), (tid, k)
+
+
+def test_forest_share_covers_every_tree_once():
+    sys.path.insert(0, ROOT)
+    import bench
+    for n_trees in (1, 5, 64):
+        for world in (1, 2, 3, 8):
+            ids = []
+            for r in range(world):
+                first, stride, count = bench.rank_forest_share(n_trees, r, world)
+                ids += [first + t * stride for t in range(count)]
+            assert sorted(ids) == list(range(n_trees))
