@@ -81,6 +81,12 @@ MLP_SHAPES = {"W1": (MLP_IN, MLP_H), "b1": (MLP_H,), "W2": (MLP_H, MLP_H), "b2":
 PURPOSE_SEED = 6
 
 
+class Prob(C.Structure):
+    _fields_ = [("n_candidates", C.c_int32), ("R", C.c_int32), ("gamma", C.c_double),
+                ("alpha0", C.c_double), ("alpha", C.c_double), ("batch", C.c_int32),
+                ("q", C.c_int32), ("cos_num", C.c_int32), ("cos_den", C.c_int32)]
+
+
 class _Tree(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in (
         "kind", "dir", "zmin", "inv_w", "bin", "leaf_class", "leaf_value",
@@ -152,6 +158,14 @@ def lib():
                                               C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
                                               P(Split), C.c_void_p, C.c_void_p]
             L.ora_node_split_from.restype = C.c_int
+            L.ora_prob_candidate.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32,
+                                             C.c_void_p, P(Prob), C.c_void_p]
+            L.ora_prob_candidate.restype = None
+            L.ora_prob_search.argtypes = [P(Params), P(Prob), C.c_void_p, C.c_int32, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                          C.c_uint32, C.c_void_p, P(Split), C.c_void_p,
+                                          C.c_void_p, C.c_void_p, P(C.c_int32)]
+            L.ora_prob_search.restype = C.c_int
             L.ora_select_features.argtypes = [P(Params), C.c_void_p, C.c_int32, C.c_void_p,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                               C.c_int32, C.c_void_p, C.c_void_p,
@@ -402,6 +416,48 @@ def node_split_from(params: Params, X, init_x, labels=None, y=None, idx=None, wt
     if rc:
         raise ValueError(f"ora_node_split_from failed: {rc}")
     return SplitResult(_struct_dict(sp), gb, dr, tl, tp)
+
+
+def make_prob(n_candidates=1000, R=4, gamma=0.8, alpha0=8.0, alpha=0.05, batch=64, q=4,
+              cos_num=9, cos_den=10) -> Prob:
+    return Prob(n_candidates, R, gamma, alpha0, alpha, batch, q, cos_num, cos_den)
+
+
+def prob_candidate(seed, node_uid, c, rank_feat, pp: Prob) -> np.ndarray:
+    rank_feat = np.ascontiguousarray(rank_feat, dtype=np.int32)
+    a = np.zeros(rank_feat.size, np.float64)
+    lib().ora_prob_candidate(seed, node_uid, c, rank_feat.size, _ptr(rank_feat), C.byref(pp),
+                             _ptr(a))
+    return a
+
+
+@dataclass
+class ProbResult:
+    split: dict
+    best: np.ndarray
+    trace_loss: np.ndarray
+    rank_feat: np.ndarray
+    kept: np.ndarray
+
+
+def prob_search(params: Params, pp: Prob, X, labels=None, y=None, idx=None, wts=None,
+                node_uid=0) -> ProbResult:
+    """The probabilistic search of the original SLM on one node (Sec. II-B)."""
+    X, labels, y, idx, wts = _node_arrays(X, labels, y, idx, wts)
+    d = X.shape[1]
+    best = np.zeros(d, np.float64)
+    nb = (pp.n_candidates + pp.batch - 1) // pp.batch
+    tl = np.zeros(nb, np.float64)
+    rf = np.zeros(d, np.int32)
+    kept = np.zeros(max(1, pp.q), np.int32)
+    nk = C.c_int32()
+    sp = Split()
+    rc = lib().ora_prob_search(C.byref(params), C.byref(pp), _ptr(X), d, _ptr(labels), _ptr(y),
+                               _ptr(idx), _ptr(wts), idx.size, node_uid, _ptr(best),
+                               C.byref(sp), _ptr(tl), _ptr(rf), _ptr(kept), C.byref(nk))
+    if rc:
+        raise ValueError(f"ora_prob_search failed: {rc}")
+    return ProbResult(_struct_dict(sp), best, tl, rf, kept[:nk.value].copy())
 
 
 @dataclass

@@ -1097,6 +1097,168 @@ int ora_node_split_from(const ora_params* p, const float* X, int32_t d,
                          dir_out, out, trace_loss, trace_particle);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Probabilistic search (Sec. II-B).                                        */
+
+void ora_prob_candidate(uint64_t seed, uint32_t node_uid, uint32_t c, int32_t d,
+                        const int32_t* rank_feat, const ora_prob* pp, double* a_out) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  const int32_t R = pp->R < d ? pp->R : d;
+  double* w = (double*)malloc(sizeof(double) * (size_t)d);
+  char* used = (char*)calloc((size_t)d, 1);
+  int32_t* chosen = (int32_t*)malloc(sizeof(int32_t) * (size_t)(R > 0 ? R : 1));
+  for (int32_t j = 0; j < d; ++j) a_out[j] = 0.0;
+  if (!w || !used || !chosen) goto done;
+  w[0] = 1.0;
+  for (int32_t r = 1; r < d; ++r) w[r] = w[r - 1] * pp->gamma;  /* P_r, rank r + 1 */
+  for (int32_t k = 0; k < 2 * R; ++k) {
+    uint32_t ctr[4] = {node_uid, c, (uint32_t)k >> 2, (uint32_t)ORA_PURPOSE_PROB << 24};
+    uint32_t rr[4];
+    ora_philox4x32_10(ctr, key, rr);
+    const double u = (double)u01(rr[k & 3]);
+    if (k < R) {
+      double total = 0.0;
+      for (int32_t r = 0; r < d; ++r)
+        if (!used[r]) total += w[r];
+      const double target = u * total;
+      double run = 0.0;
+      int32_t pick = -1, last = -1;
+      for (int32_t r = 0; r < d; ++r) {
+        if (used[r]) continue;
+        last = r;
+        run += w[r];
+        if (run > target) {
+          pick = r;
+          break;
+        }
+      }
+      if (pick < 0) pick = last;
+      used[pick] = 1;
+      chosen[k] = pick;
+    } else {
+      const int32_t r = chosen[k - R];  /* 0-based rank: A of rank r + 1 */
+      const double m = floor(pp->alpha0 * exp(-pp->alpha * (double)(r + 1)));
+      a_out[rank_feat[r]] = floor(u * (2.0 * m + 1.0)) - m;
+    }
+  }
+done:
+  free(w);
+  free(used);
+  free(chosen);
+}
+
+int ora_prob_search(const ora_params* p, const ora_prob* pp, const float* X, int32_t d,
+                    const int32_t* labels, const float* y, const int32_t* idx,
+                    const uint32_t* wts, int64_t n_idx, uint32_t node_uid, double* best_out,
+                    ora_split* out, double* trace_loss, int32_t* rank_feat_out, int32_t* kept,
+                    int32_t* n_kept) {
+  if (check_params(p, d) || !pp || pp->n_candidates < 1 || pp->R < 1 || pp->batch < 1 ||
+      !(pp->gamma > 0.0 && pp->gamma <= 1.0) || pp->q < 0 || pp->cos_den < 1 ||
+      pp->cos_num < 0 || !X || !idx || n_idx < 0 || !out || p->precision == ORA_BF16_TOPK)
+    return -1;
+  const int32_t I = pp->n_candidates;
+  double* eye = (double*)calloc((size_t)d * d, sizeof(double));
+  ora_eval* fe = (ora_eval*)calloc((size_t)d, sizeof(ora_eval));
+  int32_t* rank_feat = (int32_t*)malloc(sizeof(int32_t) * (size_t)d);
+  char* taken = (char*)calloc((size_t)d, 1);
+  double* cand = (double*)malloc(sizeof(double) * (size_t)I * d);
+  ora_eval* ev = (ora_eval*)calloc((size_t)I, sizeof(ora_eval));
+  char* pruned = (char*)calloc((size_t)I, 1);
+  int rc = 0;
+  if (!eye || !fe || !rank_feat || !taken || !cand || !ev || !pruned) {
+    rc = -2;
+    goto done;
+  }
+  memset(out, 0, sizeof(*out));
+  out->first_near_tie = -1;
+  /* rank the features by their own split loss, better first */
+  for (int32_t k = 0; k < d; ++k) eye[(int64_t)k * d + k] = 1.0;
+  rc = eval_all(p, proj_of(p), X, d, labels, y, idx, wts, n_idx, eye, NULL, d, fe, NULL, NULL,
+                NULL, NULL);
+  if (rc) goto done;
+  for (int32_t r = 0; r < d; ++r) {
+    int32_t best = -1;
+    for (int32_t k = 0; k < d; ++k) {
+      if (taken[k]) continue;
+      if (best < 0 || better(p->criterion, fe[k].valid, fe[k].loss, fe[k].q_num, fe[k].q_den,
+                             fe[best].valid, fe[best].loss, fe[best].q_num, fe[best].q_den))
+        best = k;
+    }
+    taken[best] = 1;
+    rank_feat[r] = best;
+  }
+  if (rank_feat_out) memcpy(rank_feat_out, rank_feat, sizeof(int32_t) * (size_t)d);
+  /* generate and score the candidates; the best so far after each batch */
+  for (int32_t c = 0; c < I; ++c)
+    ora_prob_candidate(p->seed, node_uid, (uint32_t)c, d, rank_feat, pp, cand + (int64_t)c * d);
+  rc = eval_all(p, proj_of(p), X, d, labels, y, idx, wts, n_idx, cand, NULL, I, ev, NULL, NULL,
+                NULL, NULL);
+  if (rc) goto done;
+  int32_t bi = 0;
+  for (int32_t c = 0; c < I; ++c) {
+    if (c > 0 && better(p->criterion, ev[c].valid, ev[c].loss, ev[c].q_num, ev[c].q_den,
+                        ev[bi].valid, ev[bi].loss, ev[bi].q_num, ev[bi].q_den))
+      bi = c;
+    if (trace_loss && ((c + 1) % pp->batch == 0 || c == I - 1))
+      trace_loss[c / pp->batch] = ev[bi].valid ? ev[bi].loss : INFINITY;
+  }
+  copy_eval_to_split(&ev[bi], out);
+  out->particle = bi;
+  out->iter_of_best = bi / pp->batch;
+  if (ev[bi].valid) {
+    if (p->precision != ORA_F64)
+      out->threshold = (double)((float)ev[bi].zmin + (float)ev[bi].bin / (float)ev[bi].inv_w);
+    else
+      out->threshold = ev[bi].zmin + (double)ev[bi].bin / ev[bi].inv_w;
+  }
+  if (best_out) memcpy(best_out, cand + (int64_t)bi * d, sizeof(double) * d);
+  /* cosine pruning: the best remaining, then drop its close neighbours */
+  int32_t nk = 0;
+  const int64_t cn2 = (int64_t)pp->cos_num * pp->cos_num, cd2 = (int64_t)pp->cos_den * pp->cos_den;
+  while (nk < pp->q) {
+    int32_t b = -1;
+    for (int32_t c = 0; c < I; ++c) {
+      if (pruned[c]) continue;
+      int64_t nrm = 0;
+      for (int32_t j = 0; j < d; ++j) nrm += (int64_t)cand[(int64_t)c * d + j] * (int64_t)cand[(int64_t)c * d + j];
+      if (nrm == 0) {
+        pruned[c] = 1;
+        continue;
+      }
+      if (b < 0 || better(p->criterion, ev[c].valid, ev[c].loss, ev[c].q_num, ev[c].q_den,
+                          ev[b].valid, ev[b].loss, ev[b].q_num, ev[b].q_den))
+        b = c;
+    }
+    if (b < 0) break;
+    if (kept) kept[nk] = b;
+    ++nk;
+    const double* ab = cand + (int64_t)b * d;
+    int64_t na = 0;
+    for (int32_t j = 0; j < d; ++j) na += (int64_t)ab[j] * (int64_t)ab[j];
+    for (int32_t c = 0; c < I; ++c) {
+      if (pruned[c]) continue;
+      const double* ac = cand + (int64_t)c * d;
+      int64_t dot = 0, nc = 0;
+      for (int32_t j = 0; j < d; ++j) {
+        dot += (int64_t)ab[j] * (int64_t)ac[j];
+        nc += (int64_t)ac[j] * (int64_t)ac[j];
+      }
+      if (c == b || cd2 * dot * dot > cn2 * na * nc) pruned[c] = 1;
+    }
+  }
+  if (n_kept) *n_kept = nk;
+done:
+  free(eye);
+  free(fe);
+  free(rank_feat);
+  free(taken);
+  free(cand);
+  free(ev);
+  free(pruned);
+  return rc;
+}
+
 int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,
                    const int32_t* labels, const float* y, uint32_t tree_id,
                    int32_t bootstrap, ora_tree* out) {

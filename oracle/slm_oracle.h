@@ -243,6 +243,54 @@ int ora_node_split_from(const ora_params* p, const float* X, int32_t d,
                         const float* init_x, double* gbest_out, double* dir_out,
                         ora_split* out, double* trace_loss, int32_t* trace_particle);
 
+/* ---- probabilistic search (Sec. II-B: the projection search of the
+ * original SLM, the baseline the swarm search replaces) -------------------
+ * The node's features are ranked by their own split loss (each feature's
+ * unit vector scored like any projection; better first, ties to the lower
+ * feature): rank r (1-based) is feature rank_feat[r-1]. Each candidate
+ * vector selects R of the D ranks and gives each selected rank r an integer
+ * coefficient in [-floor(A_r), floor(A_r)], A_r = alpha0 exp(-alpha r)
+ * (Eqs. dynamic, exp_a); the others are 0. */
+enum { ORA_PURPOSE_PROB = 9 };
+typedef struct {
+  int32_t n_candidates;  /* I: candidates generated and scored */
+  int32_t R;             /* coefficients selected per candidate, 1 <= R <= d */
+  double gamma;          /* P_r: rank r is drawn with weight gamma^(r-1),
+                            0 < gamma <= 1 (gamma^(r-1) by repeated products) */
+  double alpha0, alpha;  /* the dynamic range A_r = alpha0 exp(-alpha r) */
+  int32_t batch;         /* candidates per trace entry (>= 1) */
+  int32_t q;             /* projections kept by the cosine pruning */
+  int32_t cos_num, cos_den;  /* pruning threshold tau = cos_num / cos_den */
+} ora_prob;
+
+/* Candidate c of node node_uid: a_out[d] (integer values). Draw k is lane
+ * k mod 4 of Philox4x32-10(seed, {node_uid, c, k / 4, 9 << 24}), as a
+ * uniform u = (r >> 8) 2^-24. Draws 0..R-1 choose ranks without replacement:
+ * target = u * (sum of the remaining ranks' weights, in rank order), the
+ * first remaining rank whose running weight sum in rank order exceeds the
+ * target (the last remaining one if none does). Draws R..2R-1 give the
+ * chosen ranks' coefficients in order of choice: floor(u (2m + 1)) - m,
+ * m = floor(A_r). All in double. */
+void ora_prob_candidate(uint64_t seed, uint32_t node_uid, uint32_t c, int32_t d,
+                        const int32_t* rank_feat, const ora_prob* pp, double* a_out);
+
+/* The probabilistic search on one node: rank the features, score candidates
+ * 0..I-1 with the projection arithmetic of p->precision (F64 or F32_MIRROR),
+ * keep the best (strictly better replaces, so ties go to the lower
+ * candidate). out: the best candidate's split (particle = its index,
+ * iter_of_best = its batch); best_out[d]: its vector; trace_loss[ceil(I /
+ * batch)] (optional): best loss after each batch; rank_feat_out[d]
+ * (optional). Cosine pruning (diversity of the kept projections): repeatedly
+ * the best candidate not yet pruned and not the zero vector is kept and
+ * every candidate with cos^2 > tau^2 to it (exact integer test: cos_den^2
+ * dot^2 > cos_num^2 |a|^2 |b|^2), itself included, is pruned, until q are
+ * kept: kept[q] (optional), *n_kept. */
+int ora_prob_search(const ora_params* p, const ora_prob* pp, const float* X, int32_t d,
+                    const int32_t* labels, const float* y, const int32_t* idx,
+                    const uint32_t* wts, int64_t n_idx, uint32_t node_uid, double* best_out,
+                    ora_split* out, double* trace_loss, int32_t* rank_feat_out, int32_t* kept,
+                    int32_t* n_kept);
+
 /* Grow one tree (Algorithm 2, breadth-first). bootstrap != 0 draws the
  * tree's bag with ora_bootstrap(seed, tree_id, n). */
 int ora_train_tree(const ora_params* p, const float* X, int64_t n, int32_t d,
