@@ -260,6 +260,49 @@ slm_status slm_forest_begin(slm_ctx* ctx, const slm_params* params,
                             slm_forest** out);
 slm_status slm_grow_level(slm_ctx* ctx, slm_forest* forest,
                           int32_t* n_split_out);
+/* Probabilistic search (Sec. II-B: the projection search of the original
+ * SLM, which the swarm search replaces; kept as a baseline). The node's
+ * features are ranked by their own split loss (each unit vector scored like
+ * a projection; better first, ties to the lower feature). Each of
+ * n_candidates vectors selects R of the d ranks without replacement, rank r
+ * (1-based) with weight gamma^(r-1) (the exponentially falling P_d), and
+ * gives each an integer coefficient drawn uniformly from -m_r .. m_r,
+ * m_r = floor(alpha0 exp(-alpha r)) (Eqs. dynamic, exp_a); the other
+ * coefficients are 0. Draw k of candidate c is lane k mod 4 of
+ * Philox4x32-10(seed, {node_uid, c, k / 4, 9 << 24}) as (r >> 8) 2^-24:
+ * draws 0..R-1 choose ranks (target u * (sum of the remaining weights), the
+ * first remaining rank, in rank order, whose running weight sum passes it),
+ * draws R..2R-1 the chosen ranks' coefficients, floor(u (2 m + 1)) - m, in
+ * double. Candidates are scored in batches of `batch` like swarm particles
+ * (FP32 projection) and the best is kept (a later candidate replaces it only
+ * when strictly better). Cosine pruning keeps up to q diverse projections:
+ * repeatedly the best candidate not yet pruned and not zero, then every
+ * candidate b with cos_den^2 (a.b)^2 > cos_num^2 |a|^2 |b|^2 to it (exact
+ * integers) is pruned, itself included. */
+typedef struct {
+  int32_t n_candidates;  /* 1 .. 2^20 */
+  int32_t R;             /* 1 .. min(d, 64) */
+  double gamma;          /* (0, 1] */
+  double alpha0, alpha;  /* 0 <= alpha0 <= 100, alpha >= 0 */
+  int32_t batch;         /* 1 .. 256: candidates per scoring pass and trace entry */
+  int32_t q;             /* >= 0 */
+  int32_t cos_num, cos_den;  /* 0 <= cos_num <= cos_den <= 100, cos_den >= 1 */
+} slm_prob;
+/* On one node (arguments as slm_node_split; params: criterion, n_classes,
+ * n_bins, min_leaf, seed, proj = SLM_PROJ_FP32): *out the best candidate's
+ * split (particle = its index, iter_of_best = its batch), best_out[d]
+ * (optional) its vector, direction_out[d] the vector normalised;
+ * trace_out[ceil(n_candidates / batch)] (optional) the best loss after each
+ * batch; rank_feat_out[d] (optional) the features in rank order;
+ * kept_out[q] (optional) and *n_kept_out (optional) the pruning's kept
+ * candidates. SLM_EINVAL for arguments outside the ranges above. */
+slm_status slm_prob_search(slm_ctx* ctx, const slm_params* params, const slm_prob* prob,
+                           const float* X, int64_t n, int32_t d, const int32_t* labels,
+                           const float* y, const int32_t* sample_idx, const uint32_t* weights,
+                           int64_t n_idx, uint32_t node_uid, float* direction_out,
+                           float* best_out, slm_split* out, double* trace_out,
+                           int32_t* rank_feat_out, int32_t* kept_out, int32_t* n_kept_out);
+
 /* Global tree ids of the forests the context begins from now on: local
  * tree t of a forest is tree first + t * stride of a larger forest, whose
  * bootstrap draw (slm_bootstrap, tree_id) and node uids (tree_id << 16 |

@@ -54,6 +54,23 @@ class slm_split(C.Structure):
     ]
 
 
+class slm_prob(C.Structure):
+    _fields_ = [
+        ("n_candidates", C.c_int32), ("R", C.c_int32), ("gamma", C.c_double),
+        ("alpha0", C.c_double), ("alpha", C.c_double), ("batch", C.c_int32),
+        ("q", C.c_int32), ("cos_num", C.c_int32), ("cos_den", C.c_int32),
+    ]
+
+
+def make_prob(n_candidates=1000, R=4, gamma=0.8, alpha0=8.0, alpha=0.05, batch=64, q=4,
+              cos_num=9, cos_den=10) -> slm_prob:
+    """Parameters of the probabilistic search (Sec. II-B): candidates, ranks
+    chosen per candidate, the rank weight ratio gamma, the coefficient range
+    alpha0 exp(-alpha r), candidates per scoring batch, vectors kept by the
+    cosine pruning and its threshold cos_num / cos_den."""
+    return slm_prob(n_candidates, R, gamma, alpha0, alpha, batch, q, cos_num, cos_den)
+
+
 class SlmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"libslm status {status}: {msg}")
@@ -84,6 +101,8 @@ def lib():
                                     i64, vp, i32, vp, vp], C.c_int),
             "slm_node_split": ([vp, P(slm_params), vp, i64, i32, vp, vp, vp, vp, i64,
                                 u32, vp, vp, P(slm_split), vp], C.c_int),
+            "slm_prob_search": ([vp, P(slm_params), P(slm_prob), vp, i64, i32, vp, vp, vp, vp,
+                                 i64, u32, vp, vp, P(slm_split), vp, vp, vp, P(i32)], C.c_int),
             "slm_forest_begin": ([vp, P(slm_params), vp, i64, i32, vp, vp, P(vp)], C.c_int),
             "slm_grow_level": ([vp, vp, P(i32)], C.c_int),
             "slm_train_tree": ([vp, P(slm_params), vp, i64, i32, vp, vp, P(vp)], C.c_int),
@@ -586,6 +605,36 @@ class Context:
         res.update(particle=sp.particle, iter_of_best=sp.iter_of_best,
                    threshold=sp.threshold, norm=sp.norm, direction=direction,
                    gbest=gbest, trace=trace)
+        return res
+
+    def prob_search(self, params, prob, X, labels=None, y=None, sample_idx=None,
+                    weights=None, node_uid=0):
+        """slm_prob_search: the probabilistic search on one node; a dict of the
+        best candidate's split, its vector (\"best\") and direction, the best
+        loss after each batch, the feature ranking and the pruning's kept
+        candidates."""
+        X = _as(X, np.float32)
+        labels, y = _as(labels, np.int32), _as(y, np.float32)
+        sample_idx, weights = _as(sample_idx, np.int32), _as(weights, np.uint32)
+        n, d = X.shape
+        n_idx = n if sample_idx is None else sample_idx.shape[0]
+        direction = np.empty(d, np.float32)
+        best = np.empty(d, np.float32)
+        # arguments out of range are rejected by the call before it writes
+        ok = 1 <= prob.n_candidates <= 1 << 20 and prob.batch >= 1
+        trace = np.empty(-(-prob.n_candidates // prob.batch) if ok else 1, np.float64)
+        rank_feat = np.empty(d, np.int32)
+        kept = np.empty(max(prob.q, 1), np.int32)
+        n_kept = C.c_int32(0)
+        sp = slm_split()
+        self._check(lib().slm_prob_search(
+            self.handle, C.byref(params), C.byref(prob), _ptr(X), n, d, _ptr(labels), _ptr(y),
+            _ptr(sample_idx), _ptr(weights), n_idx, node_uid, _ptr(direction), _ptr(best),
+            C.byref(sp), _ptr(trace), _ptr(rank_feat), _ptr(kept), C.byref(n_kept)))
+        res = _eval_dict(sp.eval)
+        res.update(particle=sp.particle, iter_of_best=sp.iter_of_best,
+                   threshold=sp.threshold, norm=sp.norm, direction=direction, best=best,
+                   trace=trace, rank_feat=rank_feat, kept=kept[:n_kept.value])
         return res
 
     def forest_begin(self, params, X, labels=None, y=None) -> Forest:

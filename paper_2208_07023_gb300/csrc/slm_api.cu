@@ -50,6 +50,9 @@ enum Slot {
   // the projection with the move folded in: second position buffer, the
   // gB-independent move terms, its row tiles
   S_POS2, S_IC, S_S2, S_STILES, S_IMP,
+  // probabilistic search: every candidate's vector and score, the rank
+  // tables, the best so far, the pruning's state
+  S_PRALL, S_PRSC, S_PRTAB, S_PRBEST, S_PRUNE,
   N_SLOTS
 };
 
@@ -1790,6 +1793,170 @@ slm_status slm_node_split(slm_ctx* c, const slm_params* p, const float* X,
   for (int j = 0; j < d; ++j) dir[j] = nrm > 0.0 ? (float)(g[j] / nrm) : 0.0f;
   CK(cudaMemcpy(direction_out, dir.data(), sizeof(float) * d, cudaMemcpyDefault));
   if (gbest_out) CK(cudaMemcpy(gbest_out, g.data(), sizeof(float) * d, cudaMemcpyDefault));
+  return SLM_OK;
+}
+
+// Probabilistic search (Sec. II-B). The candidates are scored like a
+// swarm's particles, `batch` at a time, by the same projection and
+// histogram kernels; the feature ranking scores the unit vectors the same
+// way, up to 256 at a time.
+slm_status slm_prob_search(slm_ctx* c, const slm_params* p, const slm_prob* pp, const float* X,
+                           int64_t n, int32_t d, const int32_t* labels, const float* y,
+                           const int32_t* sample_idx, const uint32_t* weights, int64_t n_idx,
+                           uint32_t node_uid, float* direction_out, float* best_out,
+                           slm_split* out, double* trace_out, int32_t* rank_feat_out,
+                           int32_t* kept_out, int32_t* n_kept_out) {
+  if (!c) return SLM_EINVAL;
+  if (slm_status s = check_node_args(c, p, X, n, d, labels, y, sample_idx, &n_idx, false))
+    return s;
+  if (!pp || !out || !direction_out) return fail(c, SLM_EINVAL, "NULL prob, out or direction_out");
+  if (p->proj != SLM_PROJ_FP32) return fail(c, SLM_EINVAL, "proj must be SLM_PROJ_FP32");
+  const int I = pp->n_candidates;
+  if (I < 1 || I > (1 << 20) || (int64_t)I * d > (int64_t(1) << 28))
+    return fail(c, SLM_EINVAL, "n_candidates must be in [1, 2^20] with n_candidates * d <= 2^28");
+  if (pp->R < 1 || pp->R > kProbMaxR) return fail(c, SLM_EINVAL, "R must be in [1, 64]");
+  if (!(pp->gamma > 0.0 && pp->gamma <= 1.0)) return fail(c, SLM_EINVAL, "gamma must be in (0, 1]");
+  if (!(pp->alpha0 >= 0.0 && pp->alpha0 <= 100.0) || !(pp->alpha >= 0.0) ||
+      !std::isfinite(pp->alpha))
+    return fail(c, SLM_EINVAL, "alpha0 must be in [0, 100], alpha finite and >= 0");
+  if (pp->batch < 1 || pp->batch > kMaxParticles)
+    return fail(c, SLM_EINVAL, "batch must be in [1, 256]");
+  if (pp->q < 0 || pp->cos_den < 1 || pp->cos_den > 100 || pp->cos_num < 0 ||
+      pp->cos_num > pp->cos_den)
+    return fail(c, SLM_EINVAL, "q >= 0 and 0 <= cos_num <= cos_den <= 100, cos_den >= 1");
+  CK(cudaSetDevice(c->device));
+  const int R = std::min<int>(pp->R, d);
+  const int chunk = std::min<int>(d, kMaxParticles);
+  const int Pmax = std::max(chunk, (int)pp->batch);
+  Problem pr;
+  if (slm_status s = prepare_node(c, p, X, n, d, labels, y, sample_idx, weights, n_idx, Pmax,
+                                  &pr))
+    return s;
+  std::vector<NodeDesc> nodes{NodeDesc{0, (int32_t)n_idx, node_uid, -1}};
+  const std::vector<WorkTile> tiles = plan_tiles(nodes);
+  Swarm su{};
+  if (slm_status s = setup_scoring(c, pr, 1, nodes, tiles, &su)) return s;
+  CK(ensure(c->ws[S_FPOS], sizeof(float) * (size_t)pr.Pp * d));
+  su.pos = ws_ptr<float>(c, S_FPOS);
+  // scores rows 0 .. P - 1 of su.pos into su.cur
+  auto score = [&](int P) -> slm_status {
+    Problem pu = pr;
+    pu.P = P;
+    pu.Pp = (P + kPG - 1) / kPG * kPG;
+    pu.G = pu.Pp / kPG;
+    CK(launch(c, SLM_K_OTHER, 0.0,
+              [&] { return launch_range_reset(su.zmm, (int64_t)pu.Pp, c->stream); }));
+    return score_batch(c, pu, su, nodes, (int)tiles.size(), (double)n_idx * P, nullptr, 0,
+                       nullptr, batch_split(c, pu, nodes));
+  };
+  // rank the features by their own split loss (better first, ties to the
+  // lower feature)
+  std::vector<EvalRes> fe(d);
+  for (int f0 = 0; f0 < d; f0 += chunk) {
+    const int cnt = std::min(chunk, d - f0);
+    const int Pp = (cnt + kPG - 1) / kPG * kPG;
+    CK(launch(c, SLM_K_SWARM_INIT, 0.0,
+              [&] { return launch_prob_units(f0, cnt, Pp, d, su.pos, c->stream); }));
+    if (slm_status s = score(cnt)) return s;
+    CK(cudaMemcpyAsync(fe.data() + f0, su.cur, sizeof(EvalRes) * cnt, cudaMemcpyDeviceToHost,
+                       c->stream));
+  }
+  if (slm_status s = check_kernel_errors(c)) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<int32_t> rank_feat(d);
+  std::iota(rank_feat.begin(), rank_feat.end(), 0);
+  std::stable_sort(rank_feat.begin(), rank_feat.end(),
+                   [&](int a, int b) { return better_host(fe[a], fe[b], pr.crit); });
+  // rank weights gamma^r by repeated products (rank r + 1) and coefficient
+  // ranges floor(alpha0 exp(-alpha (r + 1)))
+  const size_t tab_bytes = sizeof(double) * d + 2 * sizeof(int32_t) * d;
+  std::vector<unsigned char> tab(tab_bytes);
+  double* w = reinterpret_cast<double*>(tab.data());
+  int32_t* m = reinterpret_cast<int32_t*>(tab.data() + sizeof(double) * d);
+  int32_t* rf = m + d;
+  w[0] = 1.0;
+  for (int r = 1; r < d; ++r) w[r] = w[r - 1] * pp->gamma;
+  for (int r = 0; r < d; ++r) {
+    m[r] = (int32_t)std::floor(pp->alpha0 * std::exp(-pp->alpha * (double)(r + 1)));
+    rf[r] = rank_feat[r];
+  }
+  CK(ensure(c->ws[S_PRTAB], tab_bytes));
+  CK(cudaMemcpyAsync(c->ws[S_PRTAB].p, tab.data(), tab_bytes, cudaMemcpyHostToDevice,
+                     c->stream));
+  const double* dw = ws_ptr<double>(c, S_PRTAB);
+  const int32_t* dm = reinterpret_cast<const int32_t*>(dw + d);
+  const int32_t* drf = dm + d;
+  const int nb = (I + pp->batch - 1) / pp->batch;
+  CK(ensure(c->ws[S_PRALL], sizeof(float) * (size_t)I * d));
+  CK(ensure(c->ws[S_PRSC], sizeof(EvalRes) * (size_t)I));
+  // best score, its index, trace[nb], best vector[d], kept[q], n_kept
+  const size_t off_idx = 64, off_trace = 128, off_pos = off_trace + round_up(8 * (size_t)nb, 64),
+               off_kept = off_pos + round_up(4 * (size_t)d, 64),
+               off_nk = off_kept + round_up(4 * (size_t)std::max(pp->q, 1), 64);
+  CK(ensure(c->ws[S_PRBEST], off_nk + 64));
+  CK(ensure(c->ws[S_PRUNE], (size_t)I));
+  char* bb = static_cast<char*>(c->ws[S_PRBEST].p);
+  EvalRes* dbest = reinterpret_cast<EvalRes*>(bb);
+  int32_t* dbest_idx = reinterpret_cast<int32_t*>(bb + off_idx);
+  double* dtrace = reinterpret_cast<double*>(bb + off_trace);
+  float* dbest_pos = reinterpret_cast<float*>(bb + off_pos);
+  int32_t* dkept = reinterpret_cast<int32_t*>(bb + off_kept);
+  int32_t* dnk = reinterpret_cast<int32_t*>(bb + off_nk);
+  float* all_pos = ws_ptr<float>(c, S_PRALL);
+  EvalRes* all_sc = ws_ptr<EvalRes>(c, S_PRSC);
+  CK(cudaMemsetAsync(dbest_pos, 0, sizeof(float) * d, c->stream));
+  CK(launch(c, SLM_K_OTHER, 0.0, [&] { return launch_prob_init(dbest, dbest_idx, c->stream); }));
+  for (int b = 0; b < nb; ++b) {
+    const int c0 = b * pp->batch, cnt = std::min<int>(pp->batch, I - c0);
+    const int Pp = (cnt + kPG - 1) / kPG * kPG;
+    CK(launch(c, SLM_K_SWARM_INIT, 0.0, [&] {
+      return launch_prob_candidates(p->seed, node_uid, c0, cnt, Pp, d, drf, dw, dm, R, su.pos,
+                                    all_pos, c->stream);
+    }));
+    if (slm_status s = score(cnt)) return s;
+    Problem pb = pr;
+    pb.P = cnt;
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+      return launch_prob_best(pb, su.cur, c0, b, dbest, dbest_idx, all_pos, dbest_pos, dtrace,
+                              all_sc, c->stream);
+    }));
+  }
+  if (pp->q > 0)
+    CK(launch(c, SLM_K_OTHER, 0.0, [&] {
+      return launch_prob_prune(pr.crit, I, d, all_pos, all_sc, pp->q, pp->cos_num,
+                               pp->cos_den, ws_ptr<uint8_t>(c, S_PRUNE), dkept, dnk,
+                               c->stream);
+    }));
+  else
+    CK(cudaMemsetAsync(dnk, 0, sizeof(int32_t), c->stream));
+  if (slm_status s = check_kernel_errors(c)) return s;
+  EvalRes gb;
+  int32_t bidx = 0, nk = 0;
+  std::vector<float> g(d);
+  CK(cudaMemcpyAsync(&gb, dbest, sizeof(EvalRes), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&bidx, dbest_idx, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&nk, dnk, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(g.data(), dbest_pos, sizeof(float) * d, cudaMemcpyDeviceToHost, c->stream));
+  if (trace_out)
+    CK(cudaMemcpyAsync(trace_out, dtrace, sizeof(double) * nb, cudaMemcpyDefault, c->stream));
+  if (kept_out && pp->q > 0)
+    CK(cudaMemcpyAsync(kept_out, dkept, sizeof(int32_t) * pp->q, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (n_kept_out) *n_kept_out = nk;
+  if (rank_feat_out)
+    CK(cudaMemcpy(rank_feat_out, rank_feat.data(), sizeof(int32_t) * d, cudaMemcpyDefault));
+  std::memcpy(&out->eval, &gb, sizeof(EvalRes));
+  out->particle = bidx;
+  out->iter_of_best = bidx / pp->batch;
+  out->threshold = gb.valid ? gb.zmin + (float)gb.bin / gb.inv_w : 0.0f;
+  double nrm = 0.0;
+  for (int j = 0; j < d; ++j) nrm += (double)g[j] * g[j];
+  nrm = std::sqrt(nrm);
+  out->norm = (float)nrm;
+  std::vector<float> dir(d);
+  for (int j = 0; j < d; ++j) dir[j] = nrm > 0.0 ? (float)(g[j] / nrm) : 0.0f;
+  CK(cudaMemcpy(direction_out, dir.data(), sizeof(float) * d, cudaMemcpyDefault));
+  if (best_out) CK(cudaMemcpy(best_out, g.data(), sizeof(float) * d, cudaMemcpyDefault));
   return SLM_OK;
 }
 

@@ -23,6 +23,7 @@ constexpr int kMaxClasses = 32;
 constexpr int kMaxHistBytesPerParticle = 10240;  // B*K*4 (classification)
 constexpr int kMaxParticles = 256;
 constexpr int kMaxD = 1024;
+constexpr int kProbMaxR = 64;  // coefficients per candidate of the probabilistic search
 // bfloat16 projection on the tensor cores (SLM_PROJ_BF16_TOPK)
 constexpr int kMmaRows = 128;                // rows per MMA tile = TMEM lanes
 constexpr int kMmaMaxBBytes = 128 * 1024;    // staged positions: Pp * dp * 2
@@ -284,6 +285,23 @@ cudaError_t launch_step(const Problem& pr, const Swarm& sw, const float* pos_pre
 cudaError_t launch_move(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                         int A, int t, SwarmCoef co, cudaStream_t st,
                         const int32_t* list = nullptr, int n_list = 0);
+// ---- probabilistic search (prob_kernels.cu; Sec. II-B) ---------------------
+cudaError_t launch_prob_init(EvalRes* best, int32_t* best_idx, cudaStream_t st);
+// Unit vectors e_{c0 + i} as rows i < count of pos[Pp, d], other rows zero.
+cudaError_t launch_prob_units(int c0, int count, int Pp, int d, float* pos, cudaStream_t st);
+// Candidates c0 .. c0 + count - 1 into pos[Pp, d] (rows past count zero) and
+// all_pos[I, d]; rank_feat[d], w[d] (gamma^r), m[d] (floor(A_{r+1})).
+cudaError_t launch_prob_candidates(uint64_t seed, uint32_t uid, int c0, int count, int Pp, int d,
+                                   const int32_t* rank_feat, const double* w, const int32_t* m,
+                                   int R, float* pos, float* all_pos, cudaStream_t st);
+// Best so far after batch b (pr.P = the batch's candidates, scored in cur).
+cudaError_t launch_prob_best(const Problem& pr, const EvalRes* cur, int c0, int b, EvalRes* best,
+                             int32_t* best_idx, const float* all_pos, float* best_pos,
+                             double* trace, EvalRes* all_scores, cudaStream_t st);
+cudaError_t launch_prob_prune(int crit, int I, int d, const float* all_pos, const EvalRes* sc,
+                              int q, int64_t cos_num, int64_t cos_den, uint8_t* pruned,
+                              int32_t* kept, int32_t* n_kept, cudaStream_t st);
+
 // ---- bfloat16 projection on the tensor cores (mma_kernels.cu) -------------
 // Converts n_blocks blocks of R rows of src[*, d] (float, row stride d; rows
 // at or past n_src_rows read as 0) to bfloat16 in the K-major, unswizzled
