@@ -63,11 +63,15 @@ def _measured_peaks():
 HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 
 # DRAM bytes per particle-sample pair from ncu captures of the default
-# workload (dram__bytes_read.sum + dram__bytes_write.sum, profiles/), valid
-# only for the kernel source they were taken from (sha256 of the .cu file).
-TRAFFIC = {"project": 12843264 / 3.2e6, "hist_scan": 13079296 / 3.2e6}
-TRAFFIC_SOURCE = {"project": "eval_kernels.cu", "hist_scan": "eval_kernels.cu"}
-TRAFFIC_SOURCE_SHA = "6f823aaf21af5bcca0d3bd7a799478bbd0946e8c832c21a8c30fab2e6bab67e2"
+# workload's root search (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch over its pairs, profiles/), each valid only for the kernel source it
+# was taken from: (bytes per pair, source file, sha256 of that file).
+TRAFFIC = {
+    "project": (12926976 / 3.2e6, "step_kernels.cu",
+                "21499f5d607675a722e8d624998a9db8d83bf2872fd794e6c51f8d8fbeee6b31"),
+    "hist_scan": (13066752 / 3.2e6, "hist_kernels.cu",
+                  "1b32a60db5458013d34d0298c08b454c00051688bf9fb1a9d51c83a13fcc47f0"),
+}
 
 
 def _kernel_source_sha(name):
@@ -83,9 +87,10 @@ def traffic_per_launch(name, ks, workload):
     one."""
     if workload != DEFAULT_WORKLOAD or name not in TRAFFIC:
         return None
-    if TRAFFIC_SOURCE_SHA != _kernel_source_sha(TRAFFIC_SOURCE[name]):
+    per_pair, src, sha = TRAFFIC[name]
+    if sha != _kernel_source_sha(src):
         return None
-    return TRAFFIC[name] * ks["pairs"] / max(1, ks["launches"])
+    return per_pair * ks["pairs"] / max(1, ks["launches"])
 
 
 def config_dict(name, cfg, wl, proj, topk, extra=None, args_launch=None):
@@ -404,6 +409,62 @@ def vs_plain_fp32(ctx, S, cfg, wl, X, L, Y, flush, stream, steps, plain):
                        "train_s": t_train,
                        "pairs": "class subsets of the tree's mixture (same means and "
                                 "covariance), 6,000 samples with disjoint sample seeds"}
+    return out
+
+
+def vs_probabilistic(ctx, S, cfg, wl, X, L, Y, n_ids=8):
+    """Root searches of the swarm (P particles, T iterations: P (T + 1)
+    evaluations) beside the probabilistic search of the original SLM
+    (Sec. II-B) with 1000 candidates (the count the paper quotes), the same
+    P (T + 1) evaluations, and ten times that, on node ids 0..n_ids-1: wall
+    time of each call (device-resident inputs, synchronised), final loss,
+    and the candidates the probabilistic search needed to reach the swarm's
+    final loss (None if it never did). Candidates: R = 4 of the ranked
+    features, weights 0.8^(r-1), ranges floor(8 exp(-0.05 r)), batches of
+    256."""
+    import torch
+    P, T = cfg["n_particles"], cfg["n_iters"]
+    pso = make_params(S, dict(cfg, max_depth=1), wl, "fp32", 0)
+    counts = {"1000": 1000, "equal_evals": P * (T + 1), "10x_evals": 10 * P * (T + 1)}
+    res = {"pso": {"ms": [], "loss": []}}
+    res.update({k: {"candidates": v, "ms": [], "loss": [], "to_pso_loss": []}
+                for k, v in counts.items()})
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) * 1e3
+
+    ctx.node_split(pso, X, labels=L, y=Y, node_uid=0)  # warm-up
+    for k, I in counts.items():
+        ctx.prob_search(pso, S.make_prob(I, batch=256, q=4), X, labels=L, y=Y, node_uid=0)
+    for uid in range(n_ids):
+        r, ms = timed(lambda: ctx.node_split(pso, X, labels=L, y=Y, node_uid=uid))
+        res["pso"]["ms"].append(ms)
+        res["pso"]["loss"].append(float(r["loss"]))
+        for k, I in counts.items():
+            pp = S.make_prob(I, batch=256, q=4)
+            g, ms = timed(lambda: ctx.prob_search(pso, pp, X, labels=L, y=Y, node_uid=uid))
+            reach = np.flatnonzero(g["trace"] <= r["loss"])
+            res[k]["ms"].append(ms)
+            res[k]["loss"].append(float(g["loss"]))
+            res[k]["to_pso_loss"].append(min(I, int(reach[0] + 1) * 256) if reach.size else None)
+    out = {"searches": n_ids, "node": "root", "pso_evaluations": P * (T + 1),
+           "prob_params": {"R": 4, "gamma": 0.8, "alpha0": 8.0, "alpha": 0.05,
+                           "batch": 256, "q": 4, "cos": "9/10"},
+           "pso": {"median_ms": float(np.median(res["pso"]["ms"])),
+                   "median_loss": float(np.median(res["pso"]["loss"]))}}
+    for k in counts:
+        got = [h for h in res[k]["to_pso_loss"] if h is not None]
+        out["prob_" + k] = {
+            "candidates": counts[k], "median_ms": float(np.median(res[k]["ms"])),
+            "median_loss": float(np.median(res[k]["loss"])),
+            "reached_pso_loss": len(got) / n_ids,
+            "median_candidates_to_pso_loss": float(np.median(got)) if got else None,
+            "loss_le_pso": float(np.mean(np.array(res[k]["loss"]) <=
+                                         np.array(res["pso"]["loss"])))}
     return out
 
 
@@ -732,6 +793,8 @@ def run_ours(args):
             ctx, S, cfg, wl, X, L, Y, flush, stream, args.steps,
             {"tree_train_ms": tot_ms / args.steps, "iters": cfg["n_iters"],
              "evaluations": evals // args.steps, "train_loss": loss, "split_loss_sum": sl})
+    if (name == DEFAULT_WORKLOAD and proj == "fp32" and world == 1 and args.vs_prob == "on"):
+        extra["vs_probabilistic"] = vs_probabilistic(ctx, S, cfg, wl, X, L, Y)
     if args.compare_plain and (cfg.get("top_n") or cfg.get("apso")):
         # the same tree without the pre-screen / adaptive PSO, same harness
         pp = make_params(S, dict(cfg, top_n=0, apso=False), wl, proj, topk)
@@ -1037,6 +1100,9 @@ def main():
     ap.add_argument("--vs-plain", choices=["on", "off"], default="on",
                     help="default workload: also time the BF16 top-8 and learned-seeded forms "
                          "beside plain FP32 (config.vs_plain_fp32)")
+    ap.add_argument("--vs-prob", choices=["on", "off"], default="on",
+                    help="default workload: also run root searches of the probabilistic search "
+                         "(Sec. II-B) beside the swarm (config.vs_probabilistic)")
     ap.add_argument("--apso", action="store_true",
                     help="adaptive PSO (FP32 form): the workload's searches adapt inertia "
                          "and learning factors to the swarm's evolutionary state")
