@@ -648,7 +648,7 @@ def rooflines(kst, wl, cfg, proj, topk, workload, roofs_in=None):
 def apply_launch_options(ctx, args):
     ctx.set_graphs(args.graphs == "on")
     ctx.set_projection_tma(args.tma == "on")
-    ctx.set_fused_step(args.fused == "on")
+    ctx.set_fused_step(args.fused != "off", always=args.fused == "always")
     ctx.set_class_hist(args.class_hist == "on", args.node_step == "on")
     if args.tiles == "fixed":
         ctx.set_tuning(False)
@@ -1088,9 +1088,10 @@ def main():
     ap.add_argument("--tma", choices=["on", "off"], default="on",
                     help="FP32 projection staging: tensor-map tile copies (on) or "
                          "per-thread asynchronous copies (off)")
-    ap.add_argument("--fused", choices=["on", "off"], default="on",
+    ap.add_argument("--fused", choices=["on", "always", "off"], default="on",
                     help="plain FP32 searches: swarm move folded into the projection "
-                         "(two launches per iteration) or separate kernels (three)")
+                         "(two launches per iteration) where a level's projection is a "
+                         "few waves (on), wherever possible (always), or never (off)")
     ap.add_argument("--class-hist", choices=["on", "off"], default="on",
                     help="classification histograms: latency-oriented kernel (on) or the "
                          "staged-copy kernel (off)")

@@ -605,7 +605,7 @@ slm_status slm_set_graphs(slm_ctx* ctx, int32_t on);
  * issuing thread, 128-byte swizzle); on = 0: by per-thread asynchronous
  * copies. The projected values are identical either way. */
 slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
-/* on != 0 (the default): plain FP32 searches (no adaptive PSO, no BF16
+/* on = 1 (the default) or 2: plain FP32 searches (no adaptive PSO, no BF16
  * form, no persistent node search) whose padded swarm is 16, 32, 48 or 64
  * particles, whose positions fit in 96 KB of shared memory and for which
  * no projection tiles are forced (slm_force_tiles) fold the
@@ -614,8 +614,14 @@ slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
  * Algorithm 1, and moves every particle) and the histogram pass (which
  * leaves the gB-independent terms of the next move), two launches instead
  * of three, and each row tile is projected onto all particles at once.
- * on = 0: the projection, histogram and move kernels. Results are identical
- * either way. *searches (optional) = searches run folded so far. */
+ * With on = 1 only a batch whose projection is at most 4 waves of row
+ * tiles (of 128 or 256 rows) on the GPU is folded: there the iteration is
+ * latency-bound and the saved launch pays; longer projections (many nodes,
+ * or one very large node) run faster unfolded, with the tuned projection.
+ * on = 2 folds every eligible batch; on = 0 none (the projection,
+ * histogram and move kernels). Results are identical either way.
+ * *searches (optional) = searches run folded so far. SLM_EINVAL for other
+ * values of on. */
 slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
 /* on != 0 (the default): the classification searches of the FP32 form
  * score each iteration with the latency-oriented histogram kernel (entries

@@ -511,11 +511,13 @@ class Context:
         """slm_set_projection_tma: tensor-map staging as a tuned candidate."""
         self._check(lib().slm_set_projection_tma(self.handle, 1 if on else 0))
 
-    def set_fused_step(self, on: bool) -> int:
+    def set_fused_step(self, on: bool = True, always: bool = False) -> int:
         """slm_set_fused_step: fold the swarm move into the projection (plain FP32
-        searches); returns the searches run folded so far."""
+        searches) where the level's projection is short, or (always) wherever
+        possible; returns the searches run folded so far."""
         n = C.c_int64()
-        self._check(lib().slm_set_fused_step(self.handle, 1 if on else 0, C.byref(n)))
+        mode = 0 if not on else (2 if always else 1)
+        self._check(lib().slm_set_fused_step(self.handle, mode, C.byref(n)))
         return n.value
 
     def set_tree_ids(self, first: int = 0, stride: int = 1):

@@ -28,6 +28,10 @@ struct DevBuf {
   size_t cap = 0;
 };
 
+// A level's search folds the move into the projection when its projection
+// is at most this many waves of row-tile units (slm_set_fused_step, on = 1).
+constexpr int kFusedMaxWaves = 4;
+
 enum Slot {
   W_X, W_LAB, W_Y, W_IDX, W_W, W_BINS, W_XL, W_LABL, W_YL,
   S_POS, S_VEL, S_PBEST, S_GBEST, S_CUR, S_PB, S_GB, S_GPART, S_GITER,
@@ -111,7 +115,7 @@ struct slm_ctx {
   bool tma = true;
   // plain FP32 searches with the swarm move folded into the projection
   // (k_step: two launches per iteration instead of three)
-  bool fused_step = true;
+  int fused_step = 1;  // 0 off, 1 when the level's projection is short, 2 always
   int64_t fused_searches = 0;
   // classification searches score with k_hist_cls (else k_hist_scan)
   bool class_hist = true;
@@ -1261,7 +1265,13 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     }
     CK(prepare_step_kernels(pr));
     const int grid = step_grid(pr, c->n_sm);
-    if (every && grid > 0 && !st.empty()) {
+    // Folding pays where the chain is latency-bound: a level whose
+    // projection is a few waves of units (a tree's levels of one or a few
+    // large nodes). Long projections (many nodes, or one very large node)
+    // keep the tuned projection and the separate move, where each row tile
+    // is not paired with the re-formed positions of its node.
+    const bool short_level = (int64_t)st.size() <= (int64_t)kFusedMaxWaves * grid;
+    if (every && grid > 0 && !st.empty() && (c->fused_step == 2 || short_level)) {
       const size_t apd = (size_t)A * pr.Pp * pr.d;
       CK(ensure(c->ws[S_POS2], sizeof(float) * apd));
       CK(ensure(c->ws[S_IC], sizeof(float) * apd));
@@ -2998,7 +3008,8 @@ slm_status slm_launch_count(slm_ctx* c, int64_t* launches) {
 
 slm_status slm_set_fused_step(slm_ctx* c, int32_t on, int64_t* searches) {
   if (!c) return SLM_EINVAL;
-  c->fused_step = on != 0;
+  if (on < 0 || on > 2) return fail(c, SLM_EINVAL, "on must be 0, 1 or 2");
+  c->fused_step = on;
   if (searches) *searches = c->fused_searches;
   return SLM_OK;
 }

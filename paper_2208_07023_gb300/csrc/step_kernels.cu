@@ -17,6 +17,9 @@
 // other of two position buffers, so the other CTAs still read x) together
 // with the gbest records, exactly as k_move would.
 //
+// Each CTA of the persistent grid takes a contiguous run of units; it forms a
+// node's positions once for all its consecutive units of that node.
+//
 // Thread tile: 4 rows (sg + 8i) x PJ particles (pg + 4j) per thread; a warp
 // covers 32 rows x 4 PJ particles; the CTA's 8 warps are RB = 8 / PB row
 // blocks x PB particle blocks, so a unit is 32 RB rows x 4 PJ PB = Pp
@@ -66,15 +69,17 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sg = lane & 7, pg = lane >> 3;
   const int rb = warp % RB, pbk = warp / RB;
-  const int my_units =
-      (int)blockIdx.x < n_units ? (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // a contiguous run of units per CTA (the tiles are in node order), so that
+  // consecutive units of a CTA mostly share a node and its moved positions
+  const int u0 = (int)(((int64_t)blockIdx.x * n_units) / gridDim.x);
+  const int my_units = (int)(((int64_t)(blockIdx.x + 1) * n_units) / gridDim.x) - u0;
   const int n_st = my_units * nk;
 
   // rows of step s (unit s / nk, feature chunk s % nk) into xb; rows past
   // the tile and features past d arrive as zeros
   auto stage = [&](int s, float* xb) {
     const int ui = s / nk, c = s - ui * nk;
-    const WorkTile wt = tiles[blockIdx.x + ui * gridDim.x];
+    const WorkTile wt = tiles[u0 + ui];
     const int k0 = c * kKC, kc = min(kKC, d - k0);
     if (vec) {
       for (int q = threadIdx.x; q < RT * (kKC / 4); q += kThreads) {
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   for (int s = 0; s < n_st; ++s) {
     const int ui = s / nk, c = s - ui * nk;
-    const WorkTile wt = tiles[blockIdx.x + ui * gridDim.x];
+    const WorkTile wt = tiles[u0 + ui];
     if (c == 0 && wt.node != cur_a) {
       __syncthreads();  // the previous node's positions and ranges are done with
       if (cur_a >= 0) flush_ranges(cur_a);

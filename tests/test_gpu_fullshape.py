@@ -60,7 +60,7 @@ def test_forest_of_the_forest_workload_shape_matches_oracle_trees():
     ctx = context()
     try:
         for fused in (True, False):
-            ctx.set_fused_step(fused)
+            ctx.set_fused_step(fused, always=True)
             if not fused:
                 ctx.force_tiles(48, 2, False)
             f = ctx.train_tree(gp, wl.X, labels=labels)

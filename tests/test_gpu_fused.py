@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctxs():
     a, b = context(), context()
+    a.set_fused_step(True, always=True)  # fold every eligible batch, however long
     b.set_fused_step(False)
     yield a, b
     a.close()
@@ -44,12 +45,12 @@ def same_tree(fa, fb, n_trees=1):
 def test_search_identical_folded_and_separate(ctxs, n, d, P, T):
     from paper_2208_07023_gb300 import binding as S
     a, b = ctxs
-    before = a.set_fused_step(True)
+    before = a.set_fused_step(True, always=True)
     wl = W.gmm(n, d, 5, seed=d + P)
     p = gpu_params(S, "gini", 5, P, T, 64, min_leaf=5, seed=3)
     ra = a.node_split(p, wl.X, labels=wl.labels, node_uid=9, want_trace=True)
     rb = b.node_split(p, wl.X, labels=wl.labels, node_uid=9, want_trace=True)
-    assert a.set_fused_step(True) == before + 1  # the search ran folded
+    assert a.set_fused_step(True, always=True) == before + 1  # the search ran folded
     assert np.array_equal(ra["trace"], rb["trace"])
     assert np.array_equal(ra["gbest"], rb["gbest"])
     for k in ("bin", "q_num", "q_den", "n_left", "n_right", "particle", "iter_of_best"):
@@ -109,3 +110,27 @@ def test_forest_and_graphs_identical_folded_and_separate(ctxs):
     finally:
         a.set_graphs(False)
     fb.free()
+
+
+def test_default_folds_short_levels_only():
+    """The default folds a batch whose projection is a few waves of row
+    tiles and leaves a long one to the separate kernels; results match."""
+    from paper_2208_07023_gb300 import binding as S
+    c = context()
+    try:
+        ref = context()
+        ref.set_fused_step(False)
+        p = gpu_params(S, "gini", 4, 64, 3, 64, min_leaf=5, seed=2)
+        for n, folded in ((20000, True), (400000, False)):  # 157 / 3125 tiles of 128 rows
+            wl = W.gmm(n, 16, 4, seed=5)
+            before = c.set_fused_step(True)
+            r = c.node_split(p, wl.X, labels=wl.labels, node_uid=3, want_trace=True)
+            assert c.set_fused_step(True) == before + int(folded)
+            q = ref.node_split(p, wl.X, labels=wl.labels, node_uid=3, want_trace=True)
+            assert np.array_equal(r["trace"], q["trace"]) and r["bin"] == q["bin"]
+            assert np.array_equal(r["gbest"], q["gbest"])
+        with pytest.raises(S.SlmError):
+            c._check(S.lib().slm_set_fused_step(c.handle, 3, None))
+        ref.close()
+    finally:
+        c.close()

@@ -29,6 +29,7 @@ def ctx_step():
     """The other placement of the gbest step and move (the default is the
     projection blocks; this one takes the last histogram block per node)."""
     c = context()
+    c.set_fused_step(True, always=True)
     c.set_class_hist(True, node_step=True)
     yield c
     c.close()
