@@ -118,6 +118,7 @@ def lib():
             "slm_set_fused_step": ([vp, i32, P(i64)], C.c_int),
             "slm_set_class_hist": ([vp, i32, i32], C.c_int),
             "slm_set_tree_ids": ([vp, i64, i64], C.c_int),
+            "slm_set_step_shape": ([vp, i32, P(i32)], C.c_int),
             "slm_seeded_start": ([vp, P(slm_params), vp, i64, i32, vp, vp, vp, vp, i64, u32,
                                   vp], C.c_int),
             "slm_measure_peaks": ([C.c_int, vp, P(C.c_double), P(C.c_double)], C.c_int),
@@ -519,6 +520,13 @@ class Context:
         mode = 0 if not on else (2 if always else 1)
         self._check(lib().slm_set_fused_step(self.handle, mode, C.byref(n)))
         return n.value
+
+    def set_step_shape(self, shape: int = -1) -> int:
+        """slm_set_step_shape: tile shape of the folded projection (-1: chosen
+        per batch); returns the shape of the last folded batch."""
+        last = C.c_int32()
+        self._check(lib().slm_set_step_shape(self.handle, shape, C.byref(last)))
+        return last.value
 
     def set_tree_ids(self, first: int = 0, stride: int = 1):
         """slm_set_tree_ids: local tree t of later forests is global tree

@@ -211,13 +211,21 @@ __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes
   const int lane = threadIdx.x & 31;
   int bi = -1;
   EvalRes be = invalid_res();
-  for (int p = lane; p < pr.P; p += 32) {
-    const EvalRes e = l2 ? ldcg_res(cur + p) : cur[p];
-    if (!(t == 0 || better(e, gold, pr.crit))) continue;
+  auto consider = [&](int p, const EvalRes& e) {
+    if (!(t == 0 || better(e, gold, pr.crit))) return;
     if (bi < 0 || better(e, be, pr.crit)) {
       bi = p;
       be = e;
     }
+  };
+  // two records per lane in flight, considered in particle order
+  for (int p = lane; p < pr.P; p += 64) {
+    const bool two = p + 32 < pr.P;
+    const EvalRes e0 = l2 ? ldcg_res(cur + p) : cur[p];
+    EvalRes e1 = e0;
+    if (two) e1 = l2 ? ldcg_res(cur + p + 32) : cur[p + 32];
+    consider(p, e0);
+    if (two) consider(p + 32, e1);
   }
   const unsigned cand = __ballot_sync(0xffffffffu, bi >= 0);
   if (!cand) {  // nobody beat gold

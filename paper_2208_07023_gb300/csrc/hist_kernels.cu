@@ -47,9 +47,13 @@ struct HcScratch {
   int wb[kHcWarps];
   uint32_t wnl[kHcWarps];
   EvalRes res;
+  EvalRes pb, gb;  // the particle's pbest score and the node's gbest score (prefetched)
   float zmin, inv_w;
   int ok, imp;
 };
+
+// Floats of one d-vector in the kernel's shared memory (16-byte multiples).
+__host__ __device__ inline int hc_dvec(int d) { return (d + 3) & ~3; }
 
 __device__ __forceinline__ double xlogx_tab(const double* tab, uint32_t c) {
   return (tab && c < (uint32_t)kXlogxTab) ? __ldg(tab + c) : xlogx(c);
@@ -83,9 +87,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B = pr.B, K = pr.K, W = B * K, d = pr.d;
   const NodeDesc nd = nodes[a];
+  const int dv = hc_dvec(d);
   uint32_t* hc = reinterpret_cast<uint32_t*>(smem);           // [kHcCopies][W]
   float* c1u = reinterpret_cast<float*>(hc + kHcCopies * W);  // [d] c1 r1 of the next move
-  float* s2u = c1u + d;                                       // [d] c2 r2
+  float* s2u = c1u + dv;                                      // [d] c2 r2
+  float* xrow = s2u + dv;                                     // [d] the particle's x, v, pB
+  float* vrow = xrow + dv;
+  float* prow = vrow + dv;
   const bool premove = do_update && sw.ic && t < sw.T && rank == 0;
 
   // work that does not wait for the projection: zero the copies, draw the
@@ -108,6 +116,55 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   pdl_wait();
   int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
+  const int64_t ci = (int64_t)a * pr.Pp + p;
+  // this rank's slice (starts on a multiple of 4 entries)
+  const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
+  const int r_begin = min(nd.seg_len, rank * chunk);
+  const int r_end = min(nd.seg_len, r_begin + chunk);
+  const int64_t e0 = nd.seg_start + r_begin;
+  const float* zs = sw.z + (int64_t)p * pr.Ez + e0;
+  const int32_t* ls = pr.lab + e0;
+  const uint32_t* ws = pr.w ? pr.w + e0 : nullptr;
+  const int n = r_end - r_begin;
+  const bool g16 = (e0 & 3) == 0;  // 16-byte loads: groups of four entries
+  const int n4 = g16 ? n >> 2 : 0;
+  constexpr int U = 4;  // groups in flight per thread
+  float4 zv[U];
+  int4 lv[U];
+  uint4 wv[U];
+  auto load_groups = [&](int g0) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int g = g0 + u * kThreads;
+      const bool in = g < n4;
+      zv[u] = in ? __ldcg(reinterpret_cast<const float4*>(zs) + g) : make_float4(0, 0, 0, 0);
+      lv[u] = in ? __ldg(reinterpret_cast<const int4*>(ls) + g) : make_int4(-1, -1, -1, -1);
+      wv[u] = in && ws ? __ldg(reinterpret_cast<const uint4*>(ws) + g) : make_uint4(1, 1, 1, 1);
+    }
+  };
+  // the first groups are in flight while the range is read
+  load_groups(threadIdx.x);
+  // the tail's inputs, also in flight from here: the particle's pbest score
+  // and the node's gbest score (evaluation t - 1), its x, v and pB rows
+  const int64_t prow0 = ci * d;
+  if (do_update && rank == 0) {
+    constexpr int kResWords = (int)(sizeof(EvalRes) / 4);
+    const int64_t gi = (int64_t)((t + 1) & 1) * sw.n_nodes + a;
+    if (threadIdx.x < kResWords)
+      cp_async4(reinterpret_cast<uint32_t*>(&sc.pb) + threadIdx.x,
+                reinterpret_cast<const uint32_t*>(sw.pb + ci) + threadIdx.x, 4);
+    else if (threadIdx.x >= 32 && threadIdx.x < 32 + kResWords && sw.imp)
+      cp_async4(reinterpret_cast<uint32_t*>(&sc.gb) + (threadIdx.x - 32),
+                reinterpret_cast<const uint32_t*>(sw.gb + gi) + (threadIdx.x - 32), 4);
+    for (int j = threadIdx.x; j < d; j += kThreads) {
+      cp_async4(xrow + j, sw.pos + prow0 + j, 4);
+      if (premove) {
+        cp_async4(vrow + j, sw.vel + prow0 + j, 4);
+        cp_async4(prow + j, sw.pbest + prow0 + j, 4);
+      }
+    }
+    cp_async_commit();
+  }
   if (threadIdx.x == 0) {
     const int lo_o = __ldcg(zz), hi_o = __ldcg(zz + 1);
     float zmin = 0.f, inv_w = 0.f;
@@ -126,33 +183,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool ok = sc.ok;
   const float zmin = sc.zmin, inv_w = sc.inv_w;
 
-  // ---- binning of this rank's slice (starts on a multiple of 4 entries)
+  // ---- binning of this rank's slice
   if (ok) {
-    const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
-    const int r_begin = min(nd.seg_len, rank * chunk);
-    const int r_end = min(nd.seg_len, r_begin + chunk);
-    const int64_t e0 = nd.seg_start + r_begin;
-    const float* zs = sw.z + (int64_t)p * pr.Ez + e0;
-    const int32_t* ls = pr.lab + e0;
-    const uint32_t* ws = pr.w ? pr.w + e0 : nullptr;
     uint32_t* h = hc + (warp % kHcCopies) * W;  // class-major: h[label * B + bin]
-    const int n = r_end - r_begin;
     int done = 0;
-    if ((e0 & 3) == 0) {  // 16-byte loads: groups of four entries
-      constexpr int U = 4;  // groups in flight per thread
-      const int n4 = n >> 2;
+    if (g16) {
       for (int g0 = threadIdx.x; g0 < n4; g0 += U * kThreads) {
-        float4 zv[U];
-        int4 lv[U];
-        uint4 wv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int g = g0 + u * kThreads;
-          const bool in = g < n4;
-          zv[u] = in ? __ldcg(reinterpret_cast<const float4*>(zs) + g) : make_float4(0, 0, 0, 0);
-          lv[u] = in ? __ldg(reinterpret_cast<const int4*>(ls) + g) : make_int4(-1, -1, -1, -1);
-          wv[u] = in && ws ? __ldg(reinterpret_cast<const uint4*>(ws) + g) : make_uint4(1, 1, 1, 1);
-        }
+        if (g0 != (int)threadIdx.x) load_groups(g0);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (lv[u].x < 0) continue;  // past the slice (whole group)
@@ -199,6 +236,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     cl.sync();  // the other ranks' memory is no longer read
     if (rank != 0) return;
   }
+  cp_async_wait<0>();  // the tail's prefetched inputs
   __syncthreads();
 
   // ---- threshold scan
@@ -369,15 +407,16 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 
   // ---- score, range reset, pbest step, the next move's gB-independent terms
-  const int64_t ci = (int64_t)a * pr.Pp + p;
   if (threadIdx.x == 0) {
     sw.cur[ci] = res;
     zz[0] = INT_MAX;  // ready for the next iteration
     zz[1] = INT_MIN;
     int imp = 0;
     if (do_update) {
-      mark_improvement(pr, sw, a, t, res);
-      imp = (t == 0) || better(res, sw.pb[ci], pr.crit);
+      // mark_improvement's rule on the prefetched gbest score
+      if (sw.imp && res.valid && (t == 0 || better(res, sc.gb, pr.crit)))
+        atomicOr(sw.imp + (int64_t)(t & 1) * sw.n_nodes + a, 1);
+      imp = (t == 0) || better(res, sc.pb, pr.crit);
       if (imp) sw.pb[ci] = res;
     }
     sc.imp = imp;
@@ -385,15 +424,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (!do_update) return;
   __syncthreads();
   const bool imp = sc.imp;
-  const int64_t row = ci * d;
+  const int64_t row = prow0;
   if (imp || premove)
     for (int j = threadIdx.x; j < d; j += kThreads) {
-      const float x = sw.pos[row + j];
+      const float x = xrow[j];
       if (imp) sw.pbest[row + j] = x;  // the position is kept on improvement
       if (premove) {
         // ic = omega v + (c1 r1)(pB - x); pB is x itself after an improvement
-        const float pbv = imp ? x : sw.pbest[row + j];
-        sw.ic[row + j] = __fadd_rn(__fmul_rn(sw.co.inertia, sw.vel[row + j]),
+        const float pbv = imp ? x : prow[j];
+        sw.ic[row + j] = __fadd_rn(__fmul_rn(sw.co.inertia, vrow[j]),
                                    __fmul_rn(c1u[j], __fsub_rn(pbv, x)));
         sw.s2[row + j] = s2u[j];
       }
@@ -524,7 +563,8 @@ const void* hist_cls_fn(const Problem& pr) {
 }
 
 size_t hist_cls_smem(const Problem& pr) {
-  return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K + sizeof(float) * 2 * (size_t)pr.d;
+  return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K +
+         sizeof(float) * 5 * (size_t)hc_dvec(pr.d);
 }
 
 }  // namespace

@@ -31,6 +31,8 @@ struct DevBuf {
 // A level's search folds the move into the projection when its projection
 // is at most this many waves of row-tile units (slm_set_fused_step, on = 1).
 constexpr int kFusedMaxWaves = 4;
+// The fixed cost of one folded projection unit, in rows of work.
+constexpr int kStepUnitRows = 80;
 
 enum Slot {
   W_X, W_LAB, W_Y, W_IDX, W_W, W_BINS, W_XL, W_LABL, W_YL,
@@ -116,6 +118,8 @@ struct slm_ctx {
   // plain FP32 searches with the swarm move folded into the projection
   // (k_step: two launches per iteration instead of three)
   int fused_step = 1;  // 0 off, 1 when the level's projection is short, 2 always
+  int step_shape = -1;      // k_step tile shape forced (-1: chosen per batch)
+  int last_step_shape = -1;
   int64_t fused_searches = 0;
   // classification searches score with k_hist_cls (else k_hist_scan)
   bool class_hist = true;
@@ -687,6 +691,7 @@ struct StepPlan {
   const WorkTile* tiles = nullptr;
   int n_tiles = 0;
   int grid = 0;
+  int sh = 0;  // tile shape of k_step
 };
 
 // One scoring pass of every (node, particle) of a batch; with a swarm
@@ -709,7 +714,8 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
     sw.pos_next = sp->pos[(t + 1) & 1];
     const float* prev = sw.node_step ? sw.pos : sp->pos[t > 0 ? (t - 1) & 1 : 0];
     CK(launch(c, SLM_K_PROJECT, pairs, [&] {
-      return launch_step(pr, sw, prev, dn, A, sp->tiles, sp->n_tiles, sp->grid, t, c->stream);
+      return launch_step(pr, sw, prev, dn, A, sp->tiles, sp->n_tiles, sp->grid, sp->sh, t,
+                         c->stream);
     }));
   }
   if (bp && bp->on) {
@@ -1255,22 +1261,49 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
   // plain FP32 searches of whole batches: the move folded into the projection
   StepPlan stp;
   if (n_res == 0 && c->fused_step && !c->forced.pg && !bp.on && !p->apso && step_ok(pr)) {
-    const int rows = step_rows(pr);
-    std::vector<WorkTile> st;
     bool every = true;
-    for (int a = 0; a < A; ++a) {
-      every = every && nodes[a].seg_len > 0;
-      for (int r = 0; r < nodes[a].seg_len; r += rows)
-        st.push_back(WorkTile{a, nodes[a].seg_start + r, std::min(rows, nodes[a].seg_len - r), 0});
+    for (int a = 0; a < A; ++a) every = every && nodes[a].seg_len > 0;
+    auto units = [&](int rows) {
+      int64_t u = 0;
+      for (int a = 0; a < A; ++a) u += (nodes[a].seg_len + rows - 1) / rows;
+      return u;
+    };
+    // Tile shape: the least estimated time per CTA, units per CTA x (rows
+    // per unit + a unit's fixed cost, about kStepUnitRows rows' worth:
+    // staging, z stores, range reductions), larger row tiles on ties; a
+    // short node is spread over more CTAs by smaller tiles. Every shape gives
+    // the same z (the same fused multiply-adds per z).
+    int sh = 0, grid = 0;
+    int64_t best = -1;
+    const int want = c->step_shape >= 0 && step_rows(pr, c->step_shape) <= 0 ? 0 : c->step_shape;
+    for (int k = 0; k < kStepShapeCount; ++k) {
+      const int rows = step_rows(pr, k);
+      if (rows <= 0 || (want >= 0 && k != want)) continue;
+      CK(prepare_step_kernels(pr, k));
+      const int g = step_grid(pr, k, c->n_sm);
+      if (g <= 0) continue;
+      const int64_t u = units(rows), per = (u + g - 1) / g * (rows + kStepUnitRows);
+      if (best < 0 || per < best) {
+        best = per;
+        sh = k;
+        grid = g;
+      }
     }
-    CK(prepare_step_kernels(pr));
-    const int grid = step_grid(pr, c->n_sm);
+    const int rows = step_rows(pr, sh);
+    std::vector<WorkTile> st;
+    if (grid > 0)
+      for (int a = 0; a < A; ++a)
+        for (int r = 0; r < nodes[a].seg_len; r += rows)
+          st.push_back(
+              WorkTile{a, nodes[a].seg_start + r, std::min(rows, nodes[a].seg_len - r), 0});
     // Folding pays where the chain is latency-bound: a level whose
     // projection is a few waves of units (a tree's levels of one or a few
     // large nodes). Long projections (many nodes, or one very large node)
     // keep the tuned projection and the separate move, where each row tile
-    // is not paired with the re-formed positions of its node.
-    const bool short_level = (int64_t)st.size() <= (int64_t)kFusedMaxWaves * grid;
+    // is not paired with the re-formed positions of its node. Measured in
+    // waves of the largest tile shape.
+    const int g0 = step_grid(pr, 0, c->n_sm);
+    const bool short_level = g0 > 0 && units(step_rows(pr, 0)) <= (int64_t)kFusedMaxWaves * g0;
     if (every && grid > 0 && !st.empty() && (c->fused_step == 2 || short_level)) {
       const size_t apd = (size_t)A * pr.Pp * pr.d;
       CK(ensure(c->ws[S_POS2], sizeof(float) * apd));
@@ -1287,6 +1320,8 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       stp.tiles = ws_ptr<WorkTile>(c, S_STILES);
       stp.n_tiles = (int)st.size();
       stp.grid = grid;
+      stp.sh = sh;
+      c->last_step_shape = sh;
       sw.ic = ws_ptr<float>(c, S_IC);
       sw.s2 = ws_ptr<float>(c, S_S2);
       sw.co = co;
@@ -3011,6 +3046,14 @@ slm_status slm_set_fused_step(slm_ctx* c, int32_t on, int64_t* searches) {
   if (on < 0 || on > 2) return fail(c, SLM_EINVAL, "on must be 0, 1 or 2");
   c->fused_step = on;
   if (searches) *searches = c->fused_searches;
+  return SLM_OK;
+}
+
+slm_status slm_set_step_shape(slm_ctx* c, int32_t shape, int32_t* last) {
+  if (!c) return SLM_EINVAL;
+  if (shape < -1 || shape >= kStepShapeCount) return fail(c, SLM_EINVAL, "shape must be -1, 0, 1 or 2");
+  c->step_shape = shape;
+  if (last) *last = c->last_step_shape;
   return SLM_OK;
 }
 

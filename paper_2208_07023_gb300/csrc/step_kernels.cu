@@ -126,33 +126,40 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       return;
     }
-    // Positions of t - 1 and the recorded gB go to shared memory by
-    // asynchronous copies, the first move terms to registers, all before
-    // the gbest step: after a gbest change gB is the new best particle's
-    // position of t - 1 (it beat every pbest, so its own pbest became that
-    // position), so the move then needs nothing from global memory.
+    // Positions of t - 1 go by asynchronous copies straight into ps (moved
+    // there in place) and the recorded gB into scratch; the move terms to
+    // registers; all before the gbest step. After a gbest change gB is the
+    // new best particle's position of t - 1 (it beat every pbest, so its own
+    // pbest became that position), which ps then holds: the move needs
+    // nothing more from global memory.
     const int d4 = d >> 2, items = vec ? P * d4 : 0;
-    const bool in_smem = vec && (P + 1) * d <= cap;
-    if (in_smem) {
-      for (int e = threadIdx.x; e < items; e += kThreads)
-        cp_async16(scratch + 4 * e, pos_prev + nb + 4 * (int64_t)e, 16);
+    if (vec) {
+      for (int e = threadIdx.x; e < items; e += kThreads) {
+        const int p = e / d4, j = 4 * (e - p * d4);
+        cp_async16(ps + (j / kKC) * cstride + p * kXS + j % kKC, pos_prev + nb + 4 * (int64_t)e,
+                   16);
+      }
       for (int q = threadIdx.x; q < d4; q += kThreads)
-        cp_async16(scratch + P * d + 4 * q, sw.gbest + (int64_t)a * d + 4 * q, 16);
+        cp_async16(scratch + 4 * q, sw.gbest + (int64_t)a * d + 4 * q, 16);
       cp_async_commit();
     }
-    float4 ia[2], sa[2];
-    auto load2 = [&](int e0) {
+    // the move terms: every element of the thread in flight at once when
+    // they fit kPre float4 per thread, else two at a time
+    constexpr int kPre = 4;
+    const bool pre = items <= kPre * kThreads;
+    float4 ia[kPre], sa[kPre];
+    auto load_terms = [&](int e0, int n) {
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kPre; ++u) {
         const int e = e0 + u * kThreads;
-        if (e < items) {
+        if (u < n && e < items) {
           const int64_t o = nb + 4 * (int64_t)e;  // element (p, 4q) of the node's rows
           ia[u] = __ldcg(reinterpret_cast<const float4*>(sw.ic + o));
           sa[u] = __ldcg(reinterpret_cast<const float4*>(sw.s2 + o));
         }
       }
     };
-    load2(threadIdx.x);
+    load_terms(threadIdx.x, pre ? kPre : 2);
     // gbest step of evaluation t - 1 (k_move's rule and double buffering)
     if (warp == 0) {
       // the argmin only when a particle beat gB in evaluation t - 1 (every
@@ -177,47 +184,60 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
-    if (in_smem) cp_async_wait<0>();
+    if (vec) cp_async_wait<0>();
     __syncthreads();
     const int bi = s_best;
-    // a new best improved its pbest in evaluation t - 1: gB is that row
-    const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
-    const float* gsm = bi >= 0 ? scratch + bi * d : scratch + P * d;
-    if (desig && bi >= 0)
-      for (int j = threadIdx.x; j < d; j += kThreads)
-        sw.gbest[(int64_t)a * d + j] = in_smem ? gsm[j] : gsrc[j];
-    // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
     if (vec) {
-      for (int e0 = threadIdx.x; e0 < items; e0 += 2 * kThreads) {
-        if (e0 != (int)threadIdx.x) load2(e0);
+      // gB into scratch before any position is overwritten
+      if (bi >= 0)
+        for (int j = threadIdx.x; j < d; j += kThreads)
+          scratch[j] = ps[(j / kKC) * cstride + bi * kXS + j % kKC];
+      __syncthreads();
+      if (desig && bi >= 0)
+        for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = scratch[j];
+      // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
+      auto move4 = [&](int e, const float4& ic, const float4& s2) {
+        const int p = e / d4, j = 4 * (e - p * d4);
+        float* xp = ps + (j / kKC) * cstride + p * kXS + j % kKC;
+        const float4 x = *reinterpret_cast<const float4*>(xp);
+        const float4 g = *reinterpret_cast<const float4*>(scratch + j);
+        float4 vn, xn;
+        vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
+        vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
+        vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g.z, x.z)));
+        vn.w = __fadd_rn(ic.w, __fmul_rn(s2.w, __fsub_rn(g.w, x.w)));
+        xn.x = __fadd_rn(x.x, vn.x);
+        xn.y = __fadd_rn(x.y, vn.y);
+        xn.z = __fadd_rn(x.z, vn.z);
+        xn.w = __fadd_rn(x.w, vn.w);
+        if (desig) {
+          const int64_t o = nb + 4 * (int64_t)e;
+          *reinterpret_cast<float4*>(sw.pos + o) = xn;
+          *reinterpret_cast<float4*>(sw.vel + o) = vn;
+        }
+        *reinterpret_cast<float4*>(xp) = xn;
+      };
+      if (pre) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int e = e0 + u * kThreads;
-          if (e >= items) break;
-          const int p = e / d4, j = 4 * (e - p * d4);
-          const float4 x = in_smem ? *reinterpret_cast<const float4*>(scratch + 4 * e)
-                                   : __ldcg(reinterpret_cast<const float4*>(pos_prev + nb) + e);
-          const float4 ic = ia[u], s2 = sa[u];
-          const float4 g = in_smem ? *reinterpret_cast<const float4*>(gsm + j)
-                                   : __ldcg(reinterpret_cast<const float4*>(gsrc + j));
-          float4 vn, xn;
-          vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
-          vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
-          vn.z = __fadd_rn(ic.z, __fmul_rn(s2.z, __fsub_rn(g.z, x.z)));
-          vn.w = __fadd_rn(ic.w, __fmul_rn(s2.w, __fsub_rn(g.w, x.w)));
-          xn.x = __fadd_rn(x.x, vn.x);
-          xn.y = __fadd_rn(x.y, vn.y);
-          xn.z = __fadd_rn(x.z, vn.z);
-          xn.w = __fadd_rn(x.w, vn.w);
-          if (desig) {
-            const int64_t o = nb + 4 * (int64_t)e;
-            *reinterpret_cast<float4*>(sw.pos + o) = xn;
-            *reinterpret_cast<float4*>(sw.vel + o) = vn;
+        for (int u = 0; u < kPre; ++u) {
+          const int e = threadIdx.x + u * kThreads;
+          if (e < items) move4(e, ia[u], sa[u]);
+        }
+      } else {
+        for (int e0 = threadIdx.x; e0 < items; e0 += 2 * kThreads) {
+          if (e0 != (int)threadIdx.x) load_terms(e0, 2);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * kThreads;
+            if (e < items) move4(e, ia[u], sa[u]);
           }
-          *reinterpret_cast<float4*>(ps + (j / kKC) * cstride + p * kXS + j % kKC) = xn;
         }
       }
     } else {
+      // a new best improved its pbest in evaluation t - 1: gB is that row
+      const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
+      if (desig && bi >= 0)
+        for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = gsrc[j];
       for (int e = threadIdx.x; e < P * d; e += kThreads) {
         const int p = e / d, j = e - p * d;
         const int64_t o = nb + e;
@@ -248,10 +268,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   };
 
   float acc[4][PJ];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
   int cur_a = -1;
 
   for (int s = 0; s < n_st; ++s) {
@@ -263,6 +279,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       cur_a = wt.node;
       // stage buffer (s + 1) & 1 is free until the copies of step s + 1
       node_positions(cur_a, wt.row0 == nodes[cur_a].seg_start, (s & 1) ? xs0 : xs1, RT * kXS);
+    }
+    if (c == 0) {  // a unit starts (zeroed here, so nothing is live through the move)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
     }
     if (s + 1 < n_st) {
       stage(s + 1, (s & 1) ? xs0 : xs1);
@@ -337,41 +359,51 @@ __global__ void __launch_bounds__(kThreads, 2)
           atomicMax(&s_hi[p], ohi);
         }
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
     }
     __syncthreads();  // this stage is refilled by the copies of step s + 2
   }
   if (cur_a >= 0) flush_ranges(cur_a);  // after the loop's last barrier
 }
 
-// Tile shape of a padded swarm: (PJ, PB).
-bool step_shape(int Pp, int* PJ, int* PB) {
-  switch (Pp) {
-    case 64: *PJ = 8; *PB = 2; return true;
-    case 48: *PJ = 6; *PB = 2; return true;
-    case 32: *PJ = 8; *PB = 1; return true;
-    case 16: *PJ = 4; *PB = 1; return true;
-    default: return false;
-  }
+// Tile shapes of a padded swarm, largest row tile first: (PJ, PB), rows per
+// unit 32 (8 / PB). The smaller tiles spread a short node over more CTAs.
+constexpr int kStepShapes = 3;
+
+bool step_shape(int Pp, int sh, int* PJ, int* PB) {
+  static const int tab[4][kStepShapes][2] = {
+      {{4, 1}, {2, 2}, {0, 0}},   // Pp = 16
+      {{8, 1}, {4, 2}, {2, 4}},   // Pp = 32
+      {{6, 2}, {0, 0}, {0, 0}},   // Pp = 48
+      {{8, 2}, {4, 4}, {2, 8}}};  // Pp = 64
+  if (Pp % 16 || Pp < 16 || Pp > 64 || sh < 0 || sh >= kStepShapes) return false;
+  const int* e = tab[Pp / 16 - 1][sh];
+  *PJ = e[0];
+  *PB = e[1];
+  return e[0] > 0;
 }
 
-size_t step_smem(const Problem& pr) {
+size_t step_smem(const Problem& pr, int sh) {
   int PJ = 0, PB = 0;
-  if (!step_shape(pr.Pp, &PJ, &PB)) return 0;
+  if (!step_shape(pr.Pp, sh, &PJ, &PB)) return 0;
   const int RT = 32 * (8 / PB);
   return sizeof(float) * ((size_t)2 * RT * kXS + step_pos_floats(pr.Pp, pr.d));
 }
 
-const void* step_fn(int Pp) {
-  switch (Pp) {
-    case 64: return (const void*)k_step<8, 2>;
-    case 48: return (const void*)k_step<6, 2>;
-    case 32: return (const void*)k_step<8, 1>;
-    case 16: return (const void*)k_step<4, 1>;
-    default: return nullptr;
+template <class F>
+cudaError_t step_dispatch(int Pp, int sh, F&& f) {
+  int PJ = 0, PB = 0;
+  if (!step_shape(Pp, sh, &PJ, &PB)) return cudaErrorInvalidValue;
+  switch (PJ * 16 + PB) {
+    case 4 * 16 + 1: return f(k_step<4, 1>);
+    case 2 * 16 + 2: return f(k_step<2, 2>);
+    case 8 * 16 + 1: return f(k_step<8, 1>);
+    case 4 * 16 + 2: return f(k_step<4, 2>);
+    case 2 * 16 + 4: return f(k_step<2, 4>);
+    case 6 * 16 + 2: return f(k_step<6, 2>);
+    case 8 * 16 + 2: return f(k_step<8, 2>);
+    case 4 * 16 + 4: return f(k_step<4, 4>);
+    case 2 * 16 + 8: return f(k_step<2, 8>);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -379,27 +411,29 @@ const void* step_fn(int Pp) {
 
 bool step_ok(const Problem& pr) {
   int PJ = 0, PB = 0;
-  return step_shape(pr.Pp, &PJ, &PB) &&
+  return step_shape(pr.Pp, 0, &PJ, &PB) &&
          step_pos_floats(pr.Pp, pr.d) * sizeof(float) <= (size_t)kStepMaxPosBytes;
 }
 
-int step_rows(const Problem& pr) {
+int step_rows(const Problem& pr, int sh) {
   int PJ = 0, PB = 0;
-  return step_shape(pr.Pp, &PJ, &PB) ? 32 * (8 / PB) : 0;
+  return step_shape(pr.Pp, sh, &PJ, &PB) ? 32 * (8 / PB) : 0;
 }
 
-cudaError_t prepare_step_kernels(const Problem& pr) {
-  const void* f = step_fn(pr.Pp);
-  if (!f) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)step_smem(pr));
+cudaError_t prepare_step_kernels(const Problem& pr, int sh) {
+  return step_dispatch(pr.Pp, sh, [&](auto fn) {
+    return cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem(pr, sh));
+  });
 }
 
-int step_grid(const Problem& pr, int n_sm) {
-  const void* f = step_fn(pr.Pp);
+int step_grid(const Problem& pr, int sh, int n_sm) {
   int per_sm = 0;
-  if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kThreads,
-                                                          step_smem(pr)) != cudaSuccess) {
+  const cudaError_t e = step_dispatch(pr.Pp, sh, [&](auto fn) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads,
+                                                         step_smem(pr, sh));
+  });
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -408,26 +442,22 @@ int step_grid(const Problem& pr, int n_sm) {
 
 cudaError_t launch_step(const Problem& pr, const Swarm& sw, const float* pos_prev,
                         const NodeDesc* nodes, int A, const WorkTile* tiles, int n_tiles,
-                        int grid, int t, cudaStream_t st) {
+                        int grid, int sh, int t, cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
   if (!step_ok(pr) || grid <= 0) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_tiles < grid ? n_tiles : grid), 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = step_smem(pr);
+  cfg.dynamicSmemBytes = step_smem(pr, sh);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  switch (pr.Pp) {
-    case 64: return cudaLaunchKernelEx(&cfg, k_step<8, 2>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
-    case 48: return cudaLaunchKernelEx(&cfg, k_step<6, 2>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
-    case 32: return cudaLaunchKernelEx(&cfg, k_step<8, 1>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
-    case 16: return cudaLaunchKernelEx(&cfg, k_step<4, 1>, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
-    default: return cudaErrorInvalidValue;
-  }
+  return step_dispatch(pr.Pp, sh, [&](auto fn) {
+    return cudaLaunchKernelEx(&cfg, fn, pr, sw, pos_prev, nodes, A, tiles, n_tiles, t);
+  });
 }
 
 }  // namespace slm
