@@ -55,6 +55,12 @@ struct HcScratch {
 // Floats of one d-vector in the kernel's shared memory (16-byte multiples).
 __host__ __device__ inline int hc_dvec(int d) { return (d + 3) & ~3; }
 
+// A double's total order as an unsigned key (negative values below 0).
+__device__ __forceinline__ uint64_t hc_key(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  return (u >> 63) ? ~u : u | 0x8000000000000000ull;
+}
+
 __device__ __forceinline__ double xlogx_tab(const double* tab, uint32_t c) {
   return (tab && c < (uint32_t)kXlogxTab) ? __ldg(tab + c) : xlogx(c);
 }
@@ -336,21 +342,57 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
-    // block argmin over the edges (ties to the lower edge)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
-      const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
-      const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
-      const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
-      const uint32_t onl = __shfl_xor_sync(0xffffffffu, bnl, off);
-      if (hc_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
-        bn = on;
-        bd = od;
-        bl = ol;
-        bb = ob;
-        bnl = onl;
+    // block argmin over the edges (ties to the lower edge), on the double
+    // loss each edge would report (Gini: (n d - q) / (n d) from the exact
+    // rational, as the score below), with edges within 8 ulps of the
+    // smallest compared exactly in edge order: the rounding of the loss is
+    // far below 8 ulps, so the choice is the exact one
+    uint64_t key = ~0ull;
+    if (bb >= 0) {
+      if (CRIT == SLM_GINI) {
+        const uint64_t nden = (uint64_t)ntot * bd;
+        bl = (double)(nden - bn) / (double)nden;
       }
+      key = hc_key(bl);
+    }
+    // the exact winner among this warp's lanes in `cand` (lane order =
+    // edge order), into lane 0's bn, bd, bl, bb, bnl
+    auto resolve = [&](unsigned cand) {
+      int wi = cand ? __ffs(cand) - 1 : 0;
+      uint64_t wn = __shfl_sync(0xffffffffu, bn, wi), wd = __shfl_sync(0xffffffffu, bd, wi);
+      double wl = __shfl_sync(0xffffffffu, bl, wi);
+      int wb = cand ? __shfl_sync(0xffffffffu, bb, wi) : -1;
+      uint32_t wnl = __shfl_sync(0xffffffffu, bnl, wi);
+      unsigned m = cand ? cand & (cand - 1) : 0u;
+      while (m) {  // rare: several edges within a few ulps
+        const int li = __ffs(m) - 1;
+        m &= m - 1;
+        const uint64_t on = __shfl_sync(0xffffffffu, bn, li), od = __shfl_sync(0xffffffffu, bd, li);
+        const double ol = __shfl_sync(0xffffffffu, bl, li);
+        const int ob = __shfl_sync(0xffffffffu, bb, li);
+        const uint32_t onl = __shfl_sync(0xffffffffu, bnl, li);
+        if (hc_takes<CRIT>(on, od, ol, ob, wn, wd, wl, wb)) {
+          wn = on;
+          wd = od;
+          wl = ol;
+          wb = ob;
+          wnl = onl;
+        }
+      }
+      bn = wn;
+      bd = wd;
+      bl = wl;
+      bb = wb;
+      bnl = wnl;
+    };
+    {
+      uint64_t kmin = key;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
+        kmin = o < kmin ? o : kmin;
+      }
+      resolve(__ballot_sync(0xffffffffu, bb >= 0 && key <= kmin + 8));
     }
     if (lane == 0) {
       sc.wn[warp] = bn;
@@ -362,30 +404,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (warp == 0) {
       const bool in = lane < kHcWarps;
+      const uint32_t nt = ntot;  // every edge's thread summed the class totals
       bn = in ? sc.wn[lane] : 0;
       bd = in ? sc.wd[lane] : 0;
       bl = in ? sc.wl[lane] : 0.0;
       bb = in ? sc.wb[lane] : -1;
       bnl = in ? sc.wnl[lane] : 0u;
+      key = bb >= 0 ? hc_key(bl) : ~0ull;
+      uint64_t kmin = key;
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) {
-        const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
-        const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
-        const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
-        const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
-        const uint32_t onl = __shfl_xor_sync(0xffffffffu, bnl, off);
-        if (hc_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
-          bn = on;
-          bd = od;
-          bl = ol;
-          bb = ob;
-          bnl = onl;
-        }
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
+        kmin = o < kmin ? o : kmin;
       }
+      resolve(__ballot_sync(0xffffffffu, bb >= 0 && key <= kmin + 8));
       if (lane == 0 && bb >= 0) {
-        // the node's weight: every class's total at the last bin
-        uint32_t nt = 0;
-        for (int k = 0; k < K; ++k) nt += hc[k * B + B - 1];
         res.valid = 1;
         res.bin = bb;
         res.nl = bnl;
@@ -393,11 +426,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (CRIT == SLM_GINI) {
           res.num = bn;
           res.den = bd;
-          const uint64_t nden = (uint64_t)nt * res.den;
-          res.loss = (double)(nden - res.num) / (double)nden;
-        } else {
-          res.loss = bl;
         }
+        res.loss = bl;
       }
     }
     if (threadIdx.x == 0) {
