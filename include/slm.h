@@ -625,7 +625,7 @@ slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
 slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
 /* Tile shape of the folded projection: shape = -1 (the default) picks, per
  * batch, the shape with the least estimated work per CTA (units per CTA x
- * (rows per unit + a fixed cost of 80 rows per unit); larger row tiles on
+ * (rows per unit + a fixed cost of 32 rows per unit); larger row tiles on
  * ties), so a short node is spread over more CTAs; 0, 1, 2 force 128-256, 64-128 or 32-64 rows per tile (by swarm
  * width; a width without the forced shape takes shape 0). Results are
  * identical for every shape. *last (optional) = the

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
     }
   }
+  __syncthreads();  // the zeroed copies, before any binning
   pdl_wait();
   int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
   const int64_t ci = (int64_t)a * pr.Pp + p;
@@ -171,23 +172,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     cp_async_commit();
   }
-  if (threadIdx.x == 0) {
+  // the particle's range, read and turned into the bin width by every
+  // thread (the same values everywhere; thread 0 resets the range only
+  // after the barriers below)
+  float zmin = 0.f, inv_w = 0.f;
+  bool ok = false;
+  {
     const int lo_o = __ldcg(zz), hi_o = __ldcg(zz + 1);
-    float zmin = 0.f, inv_w = 0.f;
-    int ok = 0;
     if (lo_o != INT_MAX) {
       const float lo = ord2f(lo_o), hi = ord2f(hi_o);
       inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
       zmin = lo;
       ok = (hi > lo) && isfinite(inv_w);
     }
-    sc.zmin = zmin;
-    sc.inv_w = inv_w;
-    sc.ok = ok;
   }
-  __syncthreads();
-  const bool ok = sc.ok;
-  const float zmin = sc.zmin, inv_w = sc.inv_w;
 
   // ---- binning of this rank's slice
   if (ok) {
@@ -252,10 +250,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     //    warp w takes classes w, w + 8, ...; lane l holds bins l*bpl ..
     const int bpl = (B + 31) >> 5;
     const bool vec4 = B == 32 * bpl && (bpl & 3) == 0;  // rows of 4-bin words
-    for (int k = warp; k < K; k += kHcWarps) {
-      uint32_t* row = hc + k * B;
-      uint32_t v[8];
-      uint32_t sum = 0;
+    // two classes per warp at a time (k and k + 8), their scans interleaved
+    auto load_row = [&](const uint32_t* row, uint32_t* v) {
       if (vec4) {
 #pragma unroll
         for (int i = 0; i < 8; i += 4)
@@ -273,22 +269,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           v[i] = (i < bpl && j < B) ? row[j] : 0u;
         }
       }
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i < bpl) sum += v[i];
-      uint32_t incl = sum;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += u;
-      }
-      uint32_t run = incl - sum;
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i < bpl) {
-          run += v[i];
-          v[i] = run;
-        }
+    };
+    auto store_row = [&](uint32_t* row, const uint32_t* v) {
       if (vec4) {
 #pragma unroll
         for (int i = 0; i < 8; i += 4)
@@ -302,6 +284,41 @@ __global__ void __launch_bounds__(kThreads, 2)
           if (i < bpl && j < B) row[j] = v[i];
         }
       }
+    };
+    for (int k0 = warp; k0 < K; k0 += 2 * kHcWarps) {
+      const int k1 = k0 + kHcWarps;
+      const bool two = k1 < K;
+      uint32_t v0[8] = {}, v1[8] = {};
+      load_row(hc + k0 * B, v0);
+      if (two) load_row(hc + k1 * B, v1);
+      uint32_t s0 = 0, s1 = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < bpl) {
+          s0 += v0[i];
+          s1 += v1[i];
+        }
+      uint32_t in0 = s0, in1 = s1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t u0 = __shfl_up_sync(0xffffffffu, in0, off);
+        const uint32_t u1 = __shfl_up_sync(0xffffffffu, in1, off);
+        if (lane >= off) {
+          in0 += u0;
+          in1 += u1;
+        }
+      }
+      uint32_t r0 = in0 - s0, r1 = in1 - s1;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < bpl) {
+          r0 += v0[i];
+          v0[i] = r0;
+          r1 += v1[i];
+          v1[i] = r1;
+        }
+      store_row(hc + k0 * B, v0);
+      if (two) store_row(hc + k1 * B, v1);
     }
     __syncthreads();
     // 2. thread b scores edge e = b + 1 (bins <= b left); an empty bin b

@@ -32,7 +32,7 @@ struct DevBuf {
 // is at most this many waves of row-tile units (slm_set_fused_step, on = 1).
 constexpr int kFusedMaxWaves = 4;
 // The fixed cost of one folded projection unit, in rows of work.
-constexpr int kStepUnitRows = 80;
+constexpr int kStepUnitRows = 32;
 
 enum Slot {
   W_X, W_LAB, W_Y, W_IDX, W_W, W_BINS, W_XL, W_LABL, W_YL,
