@@ -632,12 +632,14 @@ slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
  * shape of the last folded batch (-1 before the first). SLM_EINVAL for
  * other values of shape. */
 slm_status slm_set_step_shape(slm_ctx* ctx, int32_t shape, int32_t* last);
-/* on != 0 (the default): the classification searches of the FP32 form
- * score each iteration with the latency-oriented histogram kernel (entries
- * loaded 16 bytes at a time with several in flight, class-major histograms
- * scanned one warp per class, the pbest step spread over the block); on = 0:
- * with the staged-copy histogram kernel that also serves regression, bins
- * output and the BF16 form. node_step != 0: in folded searches
+/* on != 0 (the default): the searches of the FP32 form score each
+ * iteration with the latency-oriented histogram kernels (entries loaded 16
+ * bytes at a time with several in flight; classification: class-major
+ * histograms scanned one warp per class; regression, for nodes of at most
+ * 523,256 entries: the fixed-point bin moments added as 32-bit pieces into
+ * lane-private copies; the pbest step spread over the block); on = 0: with
+ * the staged-copy histogram kernel that also serves bins output and the
+ * BF16 form. node_step != 0: in folded classification searches
  * (slm_set_fused_step) whose nodes all take that kernel, the last block to
  * score a node takes the node's gbest step (Algorithm 1) and moves its
  * particles (Eq. pso-1) once, instead of every projection block doing it;

@@ -33,6 +33,7 @@
 
 #include "device_util.cuh"
 #include "philox.cuh"
+#include "scan_util.cuh"
 #include "slm_internal.cuh"
 
 namespace slm {
@@ -604,21 +605,276 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+// Histogram and threshold scan of regression searches in the FP32 form
+// (Sec. II-A, Eqs. 3-4 with the squared error): per bin the weight and the
+// fixed-point sums of w (y - c) and w (y - c)^2. Shared-memory atomics are
+// 32-bit only (64-bit ones run several times slower on this GPU): each
+// 64-bit moment v is added as three pieces, v mod 2^16, (v >> 16) mod 2^16
+// (each sum stays below 2^32 for up to 65535 entries per counter) and the
+// signed v >> 32, and the bin's sum is rebuilt exactly as
+// hi 2^32 + mid 2^16 + lo. Lane l adds into copy l mod kMseCopies (entries
+// of one warp that fall in the same bin rarely meet at one address; rows
+// padded by one word so equal bins of different copies sit in different
+// banks). Entries are read straight from L2 with several 16-byte groups in
+// flight per thread; the copies are summed, the cluster's ranks merged
+// through distributed shared memory, and the scan is block_scan_mse:
+// integer sums are order-free, so the scores are those of the staged-copy
+// kernel. The tail (score, pbest step, the next move's gB-independent
+// terms) is k_hist_cls's, with its inputs prefetched.
+constexpr int kMseCopies = 8;
+constexpr int kMseWords = 7;  // weight; lo, mid, hi of each of the two moments
+// Largest slice of one CTA: at most 65535 entries reach one counter.
+constexpr int kMseMaxSlice = 8 * 65535 - 4 * kThreads;
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_hist_mse(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
+               const int32_t* __restrict__ list, int t, int do_update,
+               const double* /* c ln c table: unused by the squared error */) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ HcScratch sc;
+  __shared__ ScanScratch ss;
+  const cg::cluster_group cl = cg::this_cluster();
+  pdl_trigger();
+  const int S = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int a = list ? list[blockIdx.x / S] : (int)blockIdx.x / S;
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int B = pr.B, d = pr.d, BS = B + 1;  // copy stride (padded)
+  const NodeDesc nd = nodes[a];
+  const int dv = hc_dvec(d);
+  // counters [kMseWords][copies][BS]: weight, then lo / mid / hi of each moment
+  uint32_t* hcnt = reinterpret_cast<uint32_t*>(smem);
+  const int plane = kMseCopies * BS;
+  // the merged bins for the scan: [B] weight, [B] two moments (64-bit)
+  float* c1u = reinterpret_cast<float*>(hcnt + ((kMseWords * plane + 3) & ~3));
+  float* s2u = c1u + dv;
+  float* xrow = s2u + dv;
+  float* vrow = xrow + dv;
+  float* prow = vrow + dv;
+  const bool premove = do_update && sw.ic && t < sw.T && rank == 0;
+
+  for (int i = threadIdx.x; i < kMseWords * plane; i += kThreads) hcnt[i] = 0u;
+  if (premove) {
+    const uint32_t k0 = (uint32_t)sw.co.seed, k1 = (uint32_t)(sw.co.seed >> 32);
+    for (int q = threadIdx.x; q < ((d + 3) >> 2); q += kThreads) {
+      const U4 r1 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)p,
+                                  (uint32_t)q | (kR1 << 24), k0, k1);
+      const U4 r2 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)p,
+                                  (uint32_t)q | (kR2 << 24), k0, k1);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * q + c < d) {
+          c1u[4 * q + c] = __fmul_rn(sw.co.c1, uniform24(r1.v[c]));
+          s2u[4 * q + c] = __fmul_rn(sw.co.c2, uniform24(r2.v[c]));
+        }
+    }
+  }
+  __syncthreads();  // the zeroed copies, before any binning
+  pdl_wait();
+  int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
+  const int64_t ci = (int64_t)a * pr.Pp + p;
+  const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
+  const int r_begin = min(nd.seg_len, rank * chunk);
+  const int r_end = min(nd.seg_len, r_begin + chunk);
+  const int64_t e0 = nd.seg_start + r_begin;
+  const float* zs = sw.z + (int64_t)p * pr.Ez + e0;
+  const long long* m1 = pr.m1 + e0;
+  const long long* m2 = pr.m2 + e0;
+  const uint32_t* ws = pr.w ? pr.w + e0 : nullptr;
+  const int n = r_end - r_begin;
+  const bool g16 = (e0 & 3) == 0;
+  const int n4 = g16 ? n >> 2 : 0;
+  constexpr int U = 2;  // groups of four entries in flight per thread
+  float4 zv[U];
+  longlong2 a1[U][2], a2[U][2];
+  uint4 wv[U];
+  auto load_groups = [&](int g0) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int g = g0 + u * kThreads;
+      if (g < n4) {
+        zv[u] = __ldcg(reinterpret_cast<const float4*>(zs) + g);
+        a1[u][0] = __ldg(reinterpret_cast<const longlong2*>(m1) + 2 * g);
+        a1[u][1] = __ldg(reinterpret_cast<const longlong2*>(m1) + 2 * g + 1);
+        a2[u][0] = __ldg(reinterpret_cast<const longlong2*>(m2) + 2 * g);
+        a2[u][1] = __ldg(reinterpret_cast<const longlong2*>(m2) + 2 * g + 1);
+        wv[u] = ws ? __ldg(reinterpret_cast<const uint4*>(ws) + g) : make_uint4(1, 1, 1, 1);
+      }
+    }
+  };
+  load_groups(threadIdx.x);
+  const int64_t prow0 = ci * d;
+  if (do_update && rank == 0) {
+    constexpr int kResWords = (int)(sizeof(EvalRes) / 4);
+    const int64_t gi = (int64_t)((t + 1) & 1) * sw.n_nodes + a;
+    if (threadIdx.x < kResWords)
+      cp_async4(reinterpret_cast<uint32_t*>(&sc.pb) + threadIdx.x,
+                reinterpret_cast<const uint32_t*>(sw.pb + ci) + threadIdx.x, 4);
+    else if (threadIdx.x >= 32 && threadIdx.x < 32 + kResWords && sw.imp)
+      cp_async4(reinterpret_cast<uint32_t*>(&sc.gb) + (threadIdx.x - 32),
+                reinterpret_cast<const uint32_t*>(sw.gb + gi) + (threadIdx.x - 32), 4);
+    for (int j = threadIdx.x; j < d; j += kThreads) {
+      cp_async4(xrow + j, sw.pos + prow0 + j, 4);
+      if (premove) {
+        cp_async4(vrow + j, sw.vel + prow0 + j, 4);
+        cp_async4(prow + j, sw.pbest + prow0 + j, 4);
+      }
+    }
+    cp_async_commit();
+  }
+  float zmin = 0.f, inv_w = 0.f;
+  bool ok = false;
+  {
+    const int lo_o = __ldcg(zz), hi_o = __ldcg(zz + 1);
+    if (lo_o != INT_MAX) {
+      const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+      inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+      zmin = lo;
+      ok = (hi > lo) && isfinite(inv_w);
+    }
+  }
+  // ---- binning of this rank's slice
+  if (ok) {
+    const int cpy = (lane % kMseCopies) * BS;
+    auto add = [&](float z, long long v1, long long v2, uint32_t w) {
+      uint32_t* h = hcnt + cpy + bin_of(z, zmin, inv_w, B);
+      const unsigned long long u1 = (unsigned long long)v1, u2 = (unsigned long long)v2;
+      atomicAdd(h, w);
+      atomicAdd(h + plane, (uint32_t)(u1 & 0xffffu));
+      atomicAdd(h + 2 * plane, (uint32_t)((u1 >> 16) & 0xffffu));
+      atomicAdd(h + 3 * plane, (uint32_t)(u1 >> 32));  // the signed high word, mod 2^32
+      atomicAdd(h + 4 * plane, (uint32_t)(u2 & 0xffffu));
+      atomicAdd(h + 5 * plane, (uint32_t)((u2 >> 16) & 0xffffu));
+      atomicAdd(h + 6 * plane, (uint32_t)(u2 >> 32));
+    };
+    for (int g0 = threadIdx.x; g0 < n4; g0 += U * kThreads) {
+      if (g0 != (int)threadIdx.x) load_groups(g0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (g0 + u * kThreads >= n4) break;
+        add(zv[u].x, a1[u][0].x, a2[u][0].x, wv[u].x);
+        add(zv[u].y, a1[u][0].y, a2[u][0].y, wv[u].y);
+        add(zv[u].z, a1[u][1].x, a2[u][1].x, wv[u].z);
+        add(zv[u].w, a1[u][1].y, a2[u][1].y, wv[u].w);
+      }
+    }
+    for (int i = (n4 << 2) + (int)threadIdx.x; i < n; i += kThreads)
+      add(__ldcg(zs + i), __ldg(m1 + i), __ldg(m2 + i), ws ? __ldg(ws + i) : 1u);
+  }
+  __syncthreads();
+  // ---- the copies into bin sums (thread b: bin b), written after every
+  // thread has read the copies: the weight into copy 0's row, the moments
+  // rebuilt exactly as 64-bit integers (two's complement: signed sums wrap
+  // exactly) over the first piece plane
+  uint32_t w = 0;
+  unsigned long long v[2] = {0ull, 0ull};
+  const int bi = threadIdx.x;  // B <= kThreads
+  if (bi < B) {
+#pragma unroll
+    for (int c = 0; c < kMseCopies; ++c) {
+      const uint32_t* h = hcnt + c * BS + bi;
+      w += h[0];
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+        v[m] += (unsigned long long)h[(1 + 3 * m) * plane] +
+                ((unsigned long long)h[(2 + 3 * m) * plane] << 16) +
+                ((unsigned long long)(long long)(int32_t)h[(3 + 3 * m) * plane] << 32);
+    }
+  }
+  __syncthreads();
+  uint32_t* hw = hcnt;                                                                 // [B]
+  unsigned long long* hs = reinterpret_cast<unsigned long long*>(hcnt + ((plane + 1) & ~1));  // [2][B]
+  if (bi < B) {
+    hw[bi] = w;
+    hs[bi] = v[0];
+    hs[B + bi] = v[1];
+  }
+  // ---- the other ranks' bins into rank 0
+  if (S > 1) {
+    cl.sync();  // every rank's bin sums are complete
+    if (rank == 0)
+      for (int i = threadIdx.x; i < B; i += kThreads) {
+        uint32_t w = hw[i];
+        unsigned long long v1 = hs[i], v2 = hs[B + i];
+        for (int q = 1; q < S; ++q) {
+          w += cl.map_shared_rank(hw, q)[i];
+          v1 += cl.map_shared_rank(hs, q)[i];
+          v2 += cl.map_shared_rank(hs, q)[B + i];
+        }
+        hw[i] = w;
+        hs[i] = v1;
+        hs[B + i] = v2;
+      }
+    cl.sync();  // the other ranks' memory is no longer read
+    if (rank != 0) return;
+  }
+  cp_async_wait<0>();  // the tail's prefetched inputs
+  __syncthreads();
+  EvalRes res = invalid_res();
+  if (ok) {
+    res = block_scan_mse(hw, reinterpret_cast<const long long*>(hs),
+                         reinterpret_cast<const long long*>(hs + B), pr.mscale[2 * a],
+                         pr.mscale[2 * a + 1], B, pr.min_leaf, ss);
+    res.zmin = zmin;
+    res.inv_w = inv_w;
+  }
+  // ---- score, range reset, pbest step, the next move's gB-independent terms
+  if (threadIdx.x == 0) {
+    sw.cur[ci] = res;
+    zz[0] = INT_MAX;  // ready for the next iteration
+    zz[1] = INT_MIN;
+    int imp = 0;
+    if (do_update) {
+      if (sw.imp && res.valid && (t == 0 || better(res, sc.gb, pr.crit)))
+        atomicOr(sw.imp + (int64_t)(t & 1) * sw.n_nodes + a, 1);
+      imp = (t == 0) || better(res, sc.pb, pr.crit);
+      if (imp) sw.pb[ci] = res;
+    }
+    sc.imp = imp;
+  }
+  if (!do_update) return;
+  __syncthreads();
+  const bool imp = sc.imp;
+  if (imp || premove)
+    for (int j = threadIdx.x; j < d; j += kThreads) {
+      const float x = xrow[j];
+      if (imp) sw.pbest[prow0 + j] = x;  // the position is kept on improvement
+      if (premove) {
+        const float pbv = imp ? x : prow[j];
+        sw.ic[prow0 + j] = __fadd_rn(__fmul_rn(sw.co.inertia, vrow[j]),
+                                     __fmul_rn(c1u[j], __fsub_rn(pbv, x)));
+        sw.s2[prow0 + j] = s2u[j];
+      }
+    }
+}
+
 const void* hist_cls_fn(const Problem& pr) {
-  return pr.crit == SLM_GINI ? (const void*)k_hist_cls<SLM_GINI>
-                             : (const void*)k_hist_cls<SLM_ENTROPY>;
+  return pr.crit == SLM_GINI      ? (const void*)k_hist_cls<SLM_GINI>
+         : pr.crit == SLM_ENTROPY ? (const void*)k_hist_cls<SLM_ENTROPY>
+                                  : (const void*)k_hist_mse;
 }
 
 size_t hist_cls_smem(const Problem& pr) {
-  return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K +
-         sizeof(float) * 5 * (size_t)hc_dvec(pr.d);
+  const size_t tail = sizeof(float) * 5 * (size_t)hc_dvec(pr.d);
+  if (pr.crit == SLM_MSE) {
+    const size_t cells = (size_t)kMseWords * kMseCopies * (pr.B + 1);
+    return ((cells + 3) & ~(size_t)3) * 4 + tail;
+  }
+  return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K + tail;
 }
 
 }  // namespace
 
 bool hist_cls_ok(const Problem& pr) {
-  return pr.crit != SLM_MSE && pr.lab && pr.K >= 1 && pr.K <= kMaxClasses && pr.B >= 2 &&
-         pr.B <= kThreads && hist_cls_smem(pr) <= 200 * 1024;
+  if (pr.B < 2 || pr.B > kThreads || hist_cls_smem(pr) > 200 * 1024) return false;
+  if (pr.crit == SLM_MSE) return pr.m1 && pr.m2 && pr.mscale;
+  return pr.lab && pr.K >= 1 && pr.K <= kMaxClasses;
+}
+
+bool hist_cls_fits(const Problem& pr, int64_t max_len) {
+  return pr.crit != SLM_MSE || max_len <= kMseMaxSlice;
 }
 
 cudaError_t prepare_hist_cls(const Problem& pr) {

@@ -1337,7 +1337,9 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     HistPlan hp;
     if (!bp.on && (s = setup_hist_plan(c, pr, nodes, in, &hp))) return s;
     ClsPlan cp;
-    if (c->class_hist && !bp.on && hist_cls_ok(pr)) {
+    int64_t max_len = 0;
+    for (const NodeDesc& nd : nodes) max_len = std::max<int64_t>(max_len, nd.seg_len);
+    if (c->class_hist && !bp.on && hist_cls_ok(pr) && hist_cls_fits(pr, max_len)) {
       CK(prepare_hist_cls(pr));
       cp.on = true;
       cp.xtab = xlogx_table(c->device);
@@ -1350,7 +1352,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     cp.S = S;
     // every node scored by k_hist_cls: its last CTA per node takes the gbest
     // step and moves the swarm
-    if (stp.on && cp.on && !hp.on && c->node_step) sw.node_step = 1;
+    if (stp.on && cp.on && !hp.on && c->node_step && pr.crit != SLM_MSE) sw.node_step = 1;
     c->last_split = S;
     c->cur = tl;
     c->last = tl;

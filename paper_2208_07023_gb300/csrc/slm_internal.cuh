@@ -227,10 +227,14 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw,
                              const NodeDesc* nodes, int A, int S,
                              int32_t* bins_out, int t, int do_update,
                              cudaStream_t st, const int32_t* list = nullptr);
-// Classification histograms and scans of a search (no bins out, no top-k):
-// the same scores, pbest steps and move terms as launch_hist_scan, built for
-// latency (see hist_kernels.cu). xtab: the device's c ln c table.
+// Histograms and scans of an FP32 search (no bins out, no top-k):
+// classification (k_hist_cls) or the squared error (k_hist_mse), the same
+// scores, pbest steps and move terms as launch_hist_scan, built for latency
+// (see hist_kernels.cu). xtab: the device's c ln c table. hist_cls_fits:
+// nodes of at most max_len entries stay within the regression kernel's
+// 32-bit counters.
 bool hist_cls_ok(const Problem& pr);
+bool hist_cls_fits(const Problem& pr, int64_t max_len);
 cudaError_t prepare_hist_cls(const Problem& pr);
 int hist_cls_split(const Problem& pr, int A, int64_t max_len, int n_sm);
 cudaError_t launch_hist_cls(const Problem& pr, const Swarm& sw, const NodeDesc* nodes, int A,

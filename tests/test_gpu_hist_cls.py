@@ -1,11 +1,12 @@
-"""The latency-oriented classification histogram kernel (k_hist_cls, the
-default for classification searches) scores exactly like the staged-copy
-kernel it replaces there: identical traces, gbest, splits, trees and bagged
-forests for Gini and entropy, class counts spanning every register-array
-width (2 .. 32), bin counts that are not multiples of 32 (down to 2),
-multiplicities, nodes too small for 16-byte loads of a whole slice, and
-levels whose small nodes go to the warp-per-particle kernel. The oracle
-comparisons of the other GPU tests run it too, since it is the default."""
+"""The latency-oriented histogram kernels (k_hist_cls for classification,
+k_hist_mse for regression; the defaults of FP32 searches) score exactly like
+the staged-copy kernel they replace there: identical traces, gbest, splits,
+trees and bagged forests for Gini, entropy and the squared error, class
+counts spanning every register-array width (2 .. 32), bin counts that are
+not multiples of 32 (down to 2, up to 256), multiplicities, nodes too small
+for 16-byte loads of a whole slice, and levels whose small nodes go to the
+warp-per-particle kernel. The oracle comparisons of the other GPU tests run
+them too, since they are the default."""
 import numpy as np
 import pytest
 
@@ -100,3 +101,44 @@ def test_unfused_search_identical_with_both_histogram_kernels(ctxs):
     rb = b.node_split(p, wl.X, labels=wl.labels, node_uid=1, want_trace=True)
     assert np.array_equal(ra["trace"], rb["trace"])
     assert np.array_equal(ra["gbest"], rb["gbest"]) and ra["bin"] == rb["bin"]
+
+
+@pytest.mark.parametrize("n,d,P,B,weighted", [
+    (6000, 24, 32, 64, False),
+    (5003, 16, 48, 256, False),   # the most bins, ragged slices
+    (20000, 12, 64, 128, False),  # a cluster of slices per particle
+    (37, 4, 16, 16, False),       # a node smaller than one 16-byte group per thread
+    (9000, 20, 40, 100, True),    # multiplicities (bagging)
+])
+def test_regression_identical_with_both_histogram_kernels(ctxs, n, d, P, B, weighted):
+    """The squared-error kernel (lane-private copies of the fixed-point bin
+    moments) scores exactly like the staged-copy counting-sort kernel."""
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.tanh_regression(n, d, seed=n % 89)
+    p = gpu_params(S, "mse", 0, P, 8, B, min_leaf=3, seed=7)
+    kw = {}
+    if weighted:
+        rng = np.random.default_rng(3)
+        idx, w = np.unique(rng.integers(0, n, n), return_counts=True)
+        kw = dict(sample_idx=idx.astype(np.int32), weights=w.astype(np.uint32))
+    ra = a.node_split(p, wl.X, y=wl.y, node_uid=6, want_trace=True, **kw)
+    rb = b.node_split(p, wl.X, y=wl.y, node_uid=6, want_trace=True, **kw)
+    assert np.array_equal(ra["trace"], rb["trace"])
+    assert np.array_equal(ra["gbest"], rb["gbest"])
+    for k in ("bin", "loss", "n_left", "n_right", "particle", "iter_of_best"):
+        assert ra[k] == rb[k], k
+
+
+@pytest.mark.parametrize("bootstrap", [False, True])
+def test_regression_trees_identical_with_both_histogram_kernels(ctxs, bootstrap):
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.tanh_regression(30000, 16, seed=4)
+    p = gpu_params(S, "mse", 0, 32, 6, 128, min_leaf=10, max_depth=7, seed=2,
+                   n_trees=3 if bootstrap else 1, bootstrap=bootstrap)
+    fa = a.train_tree(p, wl.X, y=wl.y)
+    fb = b.train_tree(p, wl.X, y=wl.y)
+    same_tree(fa, fb, p.n_trees)
+    fa.free()
+    fb.free()
