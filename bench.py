@@ -67,10 +67,10 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 # launch over its pairs, profiles/), each valid only for the kernel source it
 # was taken from: (bytes per pair, source file, sha256 of that file).
 TRAFFIC = {
-    "project": (12926976 / 3.2e6, "step_kernels.cu",
-                "21499f5d607675a722e8d624998a9db8d83bf2872fd794e6c51f8d8fbeee6b31"),
+    "project": (12932608 / 3.2e6, "step_kernels.cu",
+                "7df29d69e65fd86852afe5a4704fb3dc38455802ca6e5c12e701260157d12685"),
     "hist_scan": (13066752 / 3.2e6, "hist_kernels.cu",
-                  "1b32a60db5458013d34d0298c08b454c00051688bf9fb1a9d51c83a13fcc47f0"),
+                  "8b8f94a389cabf789cd7740c9efa7637b83dc092378a81b9557dc2f3d8fc12ea"),
 }
 
 
