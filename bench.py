@@ -650,6 +650,8 @@ def apply_launch_options(ctx, args):
     ctx.set_projection_tma(args.tma == "on")
     ctx.set_fused_step(args.fused != "off", always=args.fused == "always")
     ctx.set_class_hist(args.class_hist == "on", args.node_step == "on")
+    if args.node_search != "default":
+        ctx.set_node_search(args.node_search == "on")
     if args.tiles == "fixed":
         ctx.set_tuning(False)
     elif args.tiles != "auto":
@@ -1098,6 +1100,9 @@ def main():
     ap.add_argument("--node-step", choices=["on", "off"], default="off",
                     help="folded classification searches: gbest step and move in the last "
                          "histogram block of each node (on) or in every projection block (off)")
+    ap.add_argument("--node-search", choices=["default", "on", "off"], default="default",
+                    help="classification nodes whose rows fit in shared memory: the whole "
+                         "search in one persistent cluster launch (on) or per-iteration kernels")
     ap.add_argument("--vs-plain", choices=["on", "off"], default="on",
                     help="default workload: also time the BF16 top-8 and learned-seeded forms "
                          "beside plain FP32 (config.vs_plain_fp32)")

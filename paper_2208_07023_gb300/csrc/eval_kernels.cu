@@ -1412,29 +1412,35 @@ __device__ EvalRes warp_scan_cls(uint32_t* h, int B, int K, int min_leaf) {
   for (int b = 1 + lane; b < B; b += 32) {
     const uint32_t* row = h + (b - 1) * K;
     uint32_t nl = 0, prev = 0;
-    uint64_t sl = 0, sr = 0;
-    double hl = 0.0, hr = 0.0;
     for (int k = 0; k < K; ++k) {
-      const uint32_t l = row[k], r = tot[k] - l;
-      nl += l;
+      nl += row[k];
       if (b >= 2) prev += row[k - K];
-      if (CRIT == SLM_GINI) {
-        sl += (uint64_t)l * l;
-        sr += (uint64_t)r * r;
-      } else {
-        hl += xlogx_t(l);
-        hr += xlogx_t(r);
-      }
     }
     const uint32_t nr = ntot - nl;
+    // only an admissible edge is scored (the c ln c terms are table reads)
     if (nl != prev && nl >= (uint32_t)min_leaf && nr >= (uint32_t)min_leaf) {
       uint64_t cn = 0, cd = 0;
       double cl = 0.0;
       if (CRIT == SLM_GINI) {
+        uint64_t sl = 0, sr = 0;
+        for (int k = 0; k < K; ++k) {
+          const uint32_t l = row[k], r = tot[k] - l;
+          sl += (uint64_t)l * l;
+          sr += (uint64_t)r * r;
+        }
         cn = sl * nr + sr * nl;
         cd = (uint64_t)nl * nr;
       } else {
-        cl = ((xlogx_t(nl) - hl) + (xlogx_t(nr) - hr)) / (double)ntot;
+        // the class terms summed in class order, several table reads in flight
+        const double tl = xlogx_t(nl), tr = xlogx_t(nr);
+        double hl = 0.0, hr = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+          const uint32_t l = row[k], r = tot[k] - l;
+          hl += xlogx_t(l);
+          hr += xlogx_t(r);
+        }
+        cl = ((tl - hl) + (tr - hr)) / (double)ntot;
       }
       if (edge_takes<CRIT>(cn, cd, cl, b, bn, bd, bl, bb)) {
         bn = cn;
@@ -1556,22 +1562,26 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // Persistent search of small classification nodes: all T + 1 iterations of
-// Algorithm 1 in one launch. A cluster of S CTAs per node (grid (S, nodes));
-// rank r evaluates the particle groups g = r, r + S, ... (particles
-// 8g .. 8g+7). Every CTA keeps the node's rows, labels and multiplicities in
-// shared memory. Per group, the whole CTA projects the group's 8 particles
-// onto every row (each thread 4 rows x 8 particles in registers; rows as
-// 16-byte chunks, XOR-swizzled so that lanes on consecutive rows read
-// distinct banks; every z is the sequential fused multiply-add over the
-// features of k_project) into a shared z buffer, folding in each particle's
-// exact range; then warps 2j and 2j+1 bin particle 8g + j's halves of the
-// rows into their own histograms, warp 2j adds them and runs warp_scan_cls
-// (the scores of the per-iteration kernels) and the pbest step. A cluster
-// barrier, the gbest step of k_move (every CTA finds it; rank 0 records it),
-// the move of each CTA's own particles (move_item), and a second barrier
-// before any score or pbest row is written again. The swarm state stays in
-// global memory with the per-iteration kernels' layout and meaning. d must
-// be a multiple of 4.
+// Algorithm 1 in one launch, the swarm kept on chip. A cluster of S CTAs per
+// node (grid (S, nodes)); rank r owns the particle groups g = r, r + S, ...
+// (particles 8g .. 8g+7) and keeps their positions, velocities, pbest rows
+// and pbest scores in its shared memory for the whole search, with the
+// node's rows, labels and multiplicities. Per group, the whole CTA projects
+// the group's 8 particles onto every row (each thread 4 rows x 8 particles
+// in registers; rows as 16-byte chunks, XOR-swizzled so that lanes on
+// consecutive rows read distinct banks; every z is the sequential fused
+// multiply-add over the features of k_project) into a shared z buffer,
+// folding in each particle's exact range; warps 2j and 2j+1 bin particle
+// 8g + j's halves of the rows into its histogram, warp 2j runs warp_scan_cls (the scores of the per-iteration kernels) and takes the
+// pbest step in shared memory. After a cluster barrier every CTA gathers all
+// particles' scores through distributed shared memory and takes the gbest
+// step of k_move (the same argmin, the same gold), reads a new gB row from
+// its owner's pbest rows, and moves its own particles with move_item's
+// arithmetic and draws; a second barrier keeps scores and pbest rows from
+// being rewritten while other CTAs read them. The search's results (gbest
+// score, particle, iteration and row, trace, and each particle's final
+// position, velocity, pbest and score) go to global memory with the
+// per-iteration kernels' layout and meaning. d must be a multiple of 4.
 
 // Position in a row of 16-byte chunk c (C chunks per row) of row r: rows r
 // .. r+7 then fall in distinct bank groups.
@@ -1580,15 +1590,24 @@ __device__ __forceinline__ int node_chunk(int r, int c, int C) {
   return c ^ x;
 }
 
+// Words of one score record (copied between shared memories word by word).
+constexpr int kResWords = (int)(sizeof(EvalRes) / 4);
+
+// Particle slots a CTA of an S-CTA cluster owns: 8 per owned group.
+__host__ __device__ inline int node_search_slots(int P, int S) {
+  return 8 * ((((P + 7) >> 3) + S - 1) / S);
+}
+
 template <int CRIT>
 __global__ void __launch_bounds__(kNodeThreads)
     k_node_search(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
                   const int32_t* __restrict__ list, int A, SwarmCoef co) {
   namespace cg = cooperative_groups;
-  constexpr int kW = kNodeThreads / 32;  // 16 warps: two per particle of a group
   extern __shared__ __align__(16) float nsm[];
   __shared__ int s_best;
   __shared__ int s_lo[8], s_hi[8];
+  __shared__ EvalRes s_gold;  // the gbest score after the last evaluation
+  __shared__ int s_gpart, s_giter;
   const cg::cluster_group cl = cg::this_cluster();
   pdl_trigger();
   pdl_wait();
@@ -1599,13 +1618,29 @@ __global__ void __launch_bounds__(kNodeThreads)
   const int d4 = (d + 3) >> 2;
   const bool weighted = pr.w != nullptr;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* xs = nsm;                                  // [n][d], swizzled chunks
-  float* zb = xs + (size_t)n * d;                   // [8][n]
-  float* apos = zb + (size_t)8 * n;                 // [8][d]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(apos + 8 * d);  // [16][B * K]
-  int32_t* ls = reinterpret_cast<int32_t*>(hist + kW * B * K);
-  uint32_t* wsm = reinterpret_cast<uint32_t*>(ls + n);
+  const int n_groups = (P + 7) >> 3;
+  const int my_groups = rank < n_groups ? (n_groups - 1 - rank) / S + 1 : 0;
+  // shared memory (node_search_smem; d is a multiple of 4, so every
+  // float array starts on 16 bytes): rows, z, the owned particles' state
+  // (8 per owned group), gB, scores, histograms, labels, multiplicities
+  float* xs = nsm;                                             // [n][d], swizzled chunks
+  float* zb = xs + (size_t)n * d;                              // [8][n]
+  const int slots = node_search_slots(P, S);                  // owned particle slots
+  float* ppos = zb + (size_t)8 * n;                            // [slots][d]
+  float* pvel = ppos + (size_t)slots * d;                      // [slots][d]
+  float* ppb = pvel + (size_t)slots * d;                       // [slots][d] pbest rows
+  float* gbr = ppb + (size_t)slots * d;                        // [d] gB
+  EvalRes* spb = reinterpret_cast<EvalRes*>(gbr + d);          // [slots] pbest scores
+  EvalRes* scur = spb + slots;                                 // [slots] this evaluation's
+  EvalRes* sall = scur + slots;                                // [P] every particle's
+  uint32_t* hist = reinterpret_cast<uint32_t*>(sall + P);      // [8][B * K]
+  int32_t* ls = reinterpret_cast<int32_t*>(hist + 8 * B * K);   // [n]
+  uint32_t* wsm = reinterpret_cast<uint32_t*>(ls + n);          // [n] (weighted)
   const int64_t e0 = nd.seg_start;
+  const int64_t nb = (int64_t)a * Pp;  // the node's first particle row
+  // owned slot s = 8 (group / S) + (p mod 8) of particle p in group g = p / 8
+  auto owner = [&](int p) { return (p >> 3) % S; };
+  auto slot = [&](int p) { return ((p >> 3) / S) * 8 + (p & 7); };
   for (int q = threadIdx.x; q < n * C; q += kNodeThreads) {
     const int r = q / C, c = q - r * C;
     *reinterpret_cast<float4*>(xs + (size_t)r * d + 4 * node_chunk(r, c, C)) =
@@ -1615,26 +1650,32 @@ __global__ void __launch_bounds__(kNodeThreads)
     ls[i] = pr.lab[e0 + i];
     if (weighted) wsm[i] = pr.w[e0 + i];
   }
+  // the owned particles' start (zero rows past P stay zero: they project to 0)
+  for (int q = threadIdx.x; q < my_groups * 8 * d; q += kNodeThreads) {
+    const int sl = q / d, k = q - sl * d;
+    const int p = 8 * (rank + (sl >> 3) * S) + (sl & 7);
+    const bool in = p < P;
+    ppos[q] = in ? sw.pos[(nb + p) * d + k] : 0.0f;
+    pvel[q] = in ? sw.vel[(nb + p) * d + k] : 0.0f;
+    ppb[q] = 0.0f;
+  }
+  if (threadIdx.x == 0) {
+    s_gold = invalid_res();
+    s_gpart = 0;
+    s_giter = 0;
+  }
   __syncthreads();
-  uint32_t* h = hist + warp * B * K;
   const int j = warp >> 1, half = warp & 1;  // particle of the group, half of the rows
-  const EvalRes* cur = sw.cur + (int64_t)a * Pp;
-  const float* pbp = sw.pbest + (int64_t)a * Pp * d;
-  float* gbp = sw.gbest + (int64_t)a * d;
-  const int n_groups = (P + 7) >> 3;
+  uint32_t* h = hist + j * B * K;            // particle j's histogram (both halves add in)
   for (int t = 0; t <= sw.T; ++t) {
-    for (int g = rank; g < n_groups; g += S) {
-      // the group's positions (zero past P); ranges reset; histograms zeroed
-      for (int q = threadIdx.x; q < 8 * d; q += kNodeThreads) {
-        const int jj = q / d, k = q - jj * d;
-        const int p = 8 * g + jj;
-        apos[q] = p < P ? sw.pos[((int64_t)a * Pp + p) * d + k] : 0.0f;
-      }
+    for (int lg = 0; lg < my_groups; ++lg) {
+      const int g = rank + lg * S;
+      const float* apos = ppos + (size_t)lg * 8 * d;  // the group's positions, [8][d]
       if (threadIdx.x < 8) {
         s_lo[threadIdx.x] = INT_MAX;
         s_hi[threadIdx.x] = INT_MIN;
       }
-      for (int i = lane; i < B * K; i += 32) h[i] = 0u;
+      for (int i = threadIdx.x; i < 8 * B * K; i += kNodeThreads) hist[i] = 0u;
       __syncthreads();
       // z of the group's 8 particles on every row, 4 rows per thread at once;
       // the exact range of each particle folded in as ordered integers
@@ -1659,17 +1700,28 @@ __global__ void __launch_bounds__(kNodeThreads)
                                                              4 * node_chunk(r, c, C))
                           : make_float4(0.f, 0.f, 0.f, 0.f);
           }
+          // feature by feature over all 32 accumulators: each accumulator
+          // still takes the chunk's features in increasing order
+          float4 pv[8];
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const float4 pv = *reinterpret_cast<const float4*>(apos + jj * d + 4 * c);
+          for (int jj = 0; jj < 8; ++jj)
+            pv[jj] = *reinterpret_cast<const float4*>(apos + jj * d + 4 * c);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              acc[i][jj] = fmaf(xv[i].x, pv.x, acc[i][jj]);
-              acc[i][jj] = fmaf(xv[i].y, pv.y, acc[i][jj]);
-              acc[i][jj] = fmaf(xv[i].z, pv.z, acc[i][jj]);
-              acc[i][jj] = fmaf(xv[i].w, pv.w, acc[i][jj]);
-            }
-          }
+          for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i][jj] = fmaf(xv[i].x, pv[jj].x, acc[i][jj]);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i][jj] = fmaf(xv[i].y, pv[jj].y, acc[i][jj]);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i][jj] = fmaf(xv[i].z, pv[jj].z, acc[i][jj]);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i][jj] = fmaf(xv[i].w, pv[jj].w, acc[i][jj]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -1708,8 +1760,8 @@ __global__ void __launch_bounds__(kNodeThreads)
         ok = (hi > lo) && isfinite(inv_w);
       }
       if (ok && p < P) {
-        // this warp's half of the rows into its own histogram, four entries
-        // per lane in flight
+        // this warp's half of the rows into the particle's histogram, four
+        // entries per lane in flight
         const float* zp = zb + (size_t)j * n;
         for (int r0 = half * 32 + lane; r0 < n; r0 += 256) {
 #pragma unroll
@@ -1724,62 +1776,115 @@ __global__ void __launch_bounds__(kNodeThreads)
       if (half == 0 && p < P) {
         EvalRes res = invalid_res();
         if (ok) {
-          const uint32_t* h2 = h + B * K;  // the odd warp's half
-          for (int i = lane; i < B * K; i += 32) h[i] += h2[i];
-          __syncwarp();
           res = warp_scan_cls<CRIT>(h, B, K, pr.min_leaf);
           res.zmin = zmin;
           res.inv_w = inv_w;
         }
-        if (lane == 0) sw.cur[(int64_t)a * Pp + p] = res;
-        pbest_step(pr, sw, a, p, t, res);
+        // the score, and the pbest step (Algorithm 1: strict "<"; the
+        // position is kept on improvement) in shared memory
+        const int sl = lg * 8 + j;
+        int imp = 0;
+        if (lane == 0) {
+          scur[sl] = res;
+          imp = (t == 0) || better(res, spb[sl], pr.crit);
+          if (imp) spb[sl] = res;
+        }
+        imp = __shfl_sync(0xffffffffu, imp, 0);
+        if (imp)
+          for (int k = lane; k < d; k += 32) ppb[(size_t)sl * d + k] = ppos[(size_t)sl * d + k];
       }
-      __syncthreads();  // zb, apos, ranges and histograms are reset for the next group
+      __syncthreads();  // zb, ranges and histograms are reset for the next group
     }
-    // every score and pbest row of iteration t is written (one CTA: a block
-    // barrier orders its own global writes)
-    if (S > 1)
-      cl.sync();
-    else
-      __syncthreads();
-    const EvalRes* gold_buf = sw.gb + (int64_t)((t + 1) & 1) * A;
-    EvalRes* gnew_buf = sw.gb + (int64_t)(t & 1) * A;
+    // every CTA's scores and pbest rows of evaluation t are in place
+    cl.sync();
+    // every particle's score, in particle order, from its owner
+    for (int q = threadIdx.x; q < P * kResWords; q += kNodeThreads) {
+      const int pp = q / kResWords, w = q - pp * kResWords;
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(
+          cl.map_shared_rank(scur + slot(pp), owner(pp)));
+      reinterpret_cast<uint32_t*>(sall + pp)[w] = src[w];
+    }
+    __syncthreads();
+    // gbest step (k_move's rule: the argmin against the gbest of the last
+    // evaluation, every particle a candidate at evaluation 0)
     if (warp == 0) {
-      const EvalRes gold = gold_buf[a];
+      const EvalRes gold = s_gold;
       EvalRes be;
-      const int bi = gbest_argmin(pr, cur, gold, t, &be);
+      const int bi = gbest_argmin(pr, sall, gold, t, &be);
       if (lane == 0) {
         s_best = bi;
-        if (rank == 0) {
-          gnew_buf[a] = bi >= 0 ? be : gold;
-          if (bi >= 0) {
-            sw.gpart[a] = bi;
-            sw.giter[a] = t;
-          }
-          if (sw.trace) {
-            const EvalRes gr = bi >= 0 ? be : gold;
-            sw.trace[(int64_t)a * (sw.T + 1) + t] =
-                gr.valid ? gr.loss : __longlong_as_double(0x7ff0000000000000LL);
-          }
+        if (bi >= 0) {
+          s_gold = be;
+          s_gpart = bi;
+          s_giter = t;
+        }
+        if (rank == 0 && sw.trace) {
+          const EvalRes gr = bi >= 0 ? be : gold;
+          sw.trace[(int64_t)a * (sw.T + 1) + t] =
+              gr.valid ? gr.loss : __longlong_as_double(0x7ff0000000000000LL);
         }
       }
     }
     __syncthreads();
     const int best = s_best;
-    const float* gsrc = best >= 0 ? pbp + (int64_t)best * d : gbp;
-    if (rank == 0 && best >= 0)
-      for (int jj = threadIdx.x; jj < d; jj += kNodeThreads) gbp[jj] = gsrc[jj];
-    if (t < sw.T)
-      for (int item = threadIdx.x; item < P * d4; item += kNodeThreads) {
-        const int pp = item / d4;
-        if ((pp >> 3) % S != rank) continue;  // another CTA's particle
-        move_item(pr, sw, co, nd.uid, a, t, pp, item - pp * d4, pbp, gsrc);
+    // a new best improved its pbest in this evaluation: gB is that row
+    if (best >= 0) {
+      const float* src = cl.map_shared_rank(ppb + (size_t)slot(best) * d, owner(best));
+      for (int k = threadIdx.x; k < d; k += kNodeThreads) gbr[k] = src[k];
+    }
+    __syncthreads();
+    if (t < sw.T) {
+      // the owned particles' move (move_item's draws and roundings)
+      const uint32_t k0 = (uint32_t)co.seed, k1 = (uint32_t)(co.seed >> 32);
+      for (int item = threadIdx.x; item < my_groups * 8 * d4; item += kNodeThreads) {
+        const int sl = item / d4, q = item - sl * d4;
+        const int pi = 8 * (rank + (sl >> 3) * S) + (sl & 7);
+        if (pi >= P) continue;
+        const U4 r1 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)pi,
+                                    (uint32_t)q | (kR1 << 24), k0, k1);
+        const U4 r2 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)pi,
+                                    (uint32_t)q | (kR2 << 24), k0, k1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int k = 4 * q + c;
+          if (k >= d) break;
+          const size_t o = (size_t)sl * d + k;
+          const float x = ppos[o], v = pvel[o];
+          const float inertia = __fmul_rn(co.inertia, v);
+          const float cog =
+              __fmul_rn(__fmul_rn(co.c1, uniform24(r1.v[c])), __fsub_rn(ppb[o], x));
+          const float soc = __fmul_rn(__fmul_rn(co.c2, uniform24(r2.v[c])), __fsub_rn(gbr[k], x));
+          const float vn = __fadd_rn(__fadd_rn(inertia, cog), soc);
+          pvel[o] = vn;
+          ppos[o] = __fadd_rn(x, vn);
+        }
       }
-    // moves done before scores and pbest rows are rewritten
-    if (S > 1)
-      cl.sync();
-    else
-      __syncthreads();
+    }
+    // no score or pbest row is rewritten while another CTA may read it
+    cl.sync();
+  }
+  // the search's results, with the per-iteration kernels' layout
+  for (int q = threadIdx.x; q < my_groups * 8 * d; q += kNodeThreads) {
+    const int sl = q / d, k = q - sl * d;
+    const int p = 8 * (rank + (sl >> 3) * S) + (sl & 7);
+    if (p >= P) continue;
+    sw.pos[(nb + p) * d + k] = ppos[q];
+    sw.vel[(nb + p) * d + k] = pvel[q];
+    sw.pbest[(nb + p) * d + k] = ppb[q];
+  }
+  for (int sl = threadIdx.x; sl < my_groups * 8; sl += kNodeThreads) {
+    const int p = 8 * (rank + (sl >> 3) * S) + (sl & 7);
+    if (p >= P) continue;
+    sw.pb[nb + p] = spb[sl];
+    sw.cur[nb + p] = scur[sl];
+  }
+  if (rank == 0) {
+    for (int k = threadIdx.x; k < d; k += kNodeThreads) sw.gbest[(int64_t)a * d + k] = gbr[k];
+    if (threadIdx.x == 0) {
+      sw.gb[(int64_t)(sw.T & 1) * A + a] = s_gold;
+      sw.gpart[a] = s_gpart;
+      sw.giter[a] = s_giter;
+    }
   }
 }
 
@@ -2228,11 +2333,12 @@ cudaError_t launch_hist_scan(const Problem& pr, const Swarm& sw, const NodeDesc*
   return cudaLaunchKernelEx(&cfg, k_hist_scan, pr, sw, nodes, list, bins_out, t, do_update);
 }
 
-size_t node_search_smem(const Problem& pr, int n) {
-  if (pr.d % 4) return SIZE_MAX;  // 16-byte row chunks
-  const size_t words = (size_t)n * pr.d + (size_t)8 * n + (size_t)8 * pr.d +
-                       (size_t)(kNodeThreads / 32) * pr.B * pr.K + (size_t)n * (pr.w ? 2 : 1);
-  return (words * 4 + 15) & ~(size_t)15;
+size_t node_search_smem(const Problem& pr, int n, int S) {
+  if (pr.d % 4 || S < 1) return SIZE_MAX;  // 16-byte row chunks
+  const size_t slots = node_search_slots(pr.P, S);
+  const size_t floats = (size_t)n * pr.d + (size_t)8 * n + 3 * slots * pr.d + pr.d;
+  const size_t words = (size_t)8 * pr.B * pr.K + (size_t)n * (pr.w ? 2 : 1);
+  return (floats * 4 + sizeof(EvalRes) * (2 * slots + pr.P) + words * 4 + 15) & ~(size_t)15;
 }
 
 cudaError_t launch_node_search(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,

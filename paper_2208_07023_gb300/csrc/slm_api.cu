@@ -1180,15 +1180,25 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
   std::vector<char> resident(A, 0);
   int n_res = 0;
   size_t smax = 0;
-  if (c->node_search && p->proj != SLM_PROJ_BF16_TOPK && p->criterion != SLM_MSE && !p->apso)
-    for (int a = 0; a < A; ++a) {
-      const size_t sm = node_search_smem(pr, nodes[a].seg_len);
+  int S_res = 1;  // CTAs per resident node
+  if (c->node_search && p->proj != SLM_PROJ_BF16_TOPK && p->criterion != SLM_MSE && !p->apso) {
+    // candidates: rows and the swarm share fit with the node spread widest;
+    // then CTAs per node, up to one particle per warp while the GPU has
+    // room; then the nodes that fit at that spread
+    const int want = std::min(8, (pr.P + 7) / 8);
+    int n_cand = 0;
+    for (int a = 0; a < A; ++a)
+      n_cand += node_search_smem(pr, nodes[a].seg_len, want) <= kNodeSearchMaxSmem;
+    while (S_res * 2 <= want && (int64_t)n_cand * S_res * 2 <= c->n_sm) S_res *= 2;
+    for (int a = 0; n_cand > 0 && a < A; ++a) {
+      const size_t sm = node_search_smem(pr, nodes[a].seg_len, S_res);
       if (sm <= kNodeSearchMaxSmem) {
         resident[a] = 1;
         ++n_res;
         smax = std::max(smax, sm);
       }
     }
+  }
   std::vector<char> in;
   if (n_res > 0 && n_res < A) {
     in.resize(A);
@@ -1231,10 +1241,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
   c->last_node_search = 0;
   bool joined = true;
   if (n_res > 0) {
-    // CTAs per node: up to one particle per warp while the GPU has room
-    int S = 1;
-    const int want = std::min(8, (pr.P + 7) / 8);
-    while (S * 2 <= want && (int64_t)n_res * S * 2 <= c->n_sm) S *= 2;
+    const int S = S_res;
     std::vector<int32_t> lst;
     for (int a = 0; a < A; ++a)
       if (resident[a]) lst.push_back(a);

@@ -245,7 +245,9 @@ cudaError_t launch_hist_cls(const Problem& pr, const Swarm& sw, const NodeDesc* 
 // list[n_nodes] (A: the batch's node count, the gbest buffers' stride).
 constexpr size_t kNodeSearchMaxSmem = 226 * 1024;
 constexpr int kNodeThreads = 512;  // threads per CTA of the persistent search
-size_t node_search_smem(const Problem& pr, int n);
+// Dynamic shared memory of one CTA of an S-CTA cluster searching a node of
+// n rows (SIZE_MAX when d is not a multiple of 4).
+size_t node_search_smem(const Problem& pr, int n, int S);
 cudaError_t launch_node_search(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                                const int32_t* list, int n_nodes, int A, int S, size_t smem,
                                SwarmCoef co, cudaStream_t st);
