@@ -22,6 +22,7 @@ def test_readme_example_runs():
     q = float(np.mean(scope["wl"].labels == 0))
     root_entropy = -(q * np.log(q) + (1 - q) * np.log(1 - q))
     assert scope["r"]["loss"] < root_entropy
+    assert scope["q"]["valid"] and scope["q"]["loss"] < root_entropy
     loss = scope["boost"].train_loss
     assert len(loss) == 10 and np.all(np.diff(loss) <= 0)
     scope["tree"].free()
