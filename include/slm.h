@@ -625,12 +625,15 @@ slm_status slm_set_projection_tma(slm_ctx* ctx, int32_t on);
 slm_status slm_set_fused_step(slm_ctx* ctx, int32_t on, int64_t* searches);
 /* Tile shape of the folded projection: shape = -1 (the default) picks, per
  * batch, the shape with the least estimated work per CTA (units per CTA x
- * (rows per unit + a fixed cost of 32 rows per unit); larger row tiles on
- * ties), so a short node is spread over more CTAs; 0, 1, 2 force 128-256, 64-128 or 32-64 rows per tile (by swarm
- * width; a width without the forced shape takes shape 0). Results are
- * identical for every shape. *last (optional) = the
- * shape of the last folded batch (-1 before the first). SLM_EINVAL for
- * other values of shape. */
+ * (rows per unit x particles per unit / swarm width + a fixed cost of 32
+ * rows per unit); on ties, half-swarm units where each CTA takes one unit,
+ * else larger row tiles), so a short node is spread over
+ * more CTAs; 0, 1, 2 force 128-256, 64-128 or 32-64 rows per tile with every
+ * particle in a unit, 3, 4, 5 the same with half the particles of a swarm of
+ * 32 or 64 (by swarm width; a width without the forced shape takes shape
+ * 0). Results are identical for every shape. *last (optional) = the shape
+ * of the last folded batch (-1 before the first). SLM_EINVAL for other
+ * values of shape. */
 slm_status slm_set_step_shape(slm_ctx* ctx, int32_t shape, int32_t* last);
 /* on != 0 (the default): the searches of the FP32 form score each
  * iteration with the latency-oriented histogram kernels (entries loaded 16

@@ -1275,12 +1275,13 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       for (int a = 0; a < A; ++a) u += (nodes[a].seg_len + rows - 1) / rows;
       return u;
     };
+    // a unit of half the particles costs half the rows' work
     // Tile shape: the least estimated time per CTA, units per CTA x (rows
     // per unit + a unit's fixed cost, about kStepUnitRows rows' worth:
     // staging, z stores, range reductions), larger row tiles on ties; a
     // short node is spread over more CTAs by smaller tiles. Every shape gives
     // the same z (the same fused multiply-adds per z).
-    int sh = 0, grid = 0;
+    int sh = 0, grid = 0, best_tie = 0;
     int64_t best = -1;
     const int want = c->step_shape >= 0 && step_rows(pr, c->step_shape) <= 0 ? 0 : c->step_shape;
     for (int k = 0; k < kStepShapeCount; ++k) {
@@ -1289,20 +1290,27 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       CK(prepare_step_kernels(pr, k));
       const int g = step_grid(pr, k, c->n_sm);
       if (g <= 0) continue;
-      const int64_t u = units(rows), per = (u + g - 1) / g * (rows + kStepUnitRows);
-      if (best < 0 || per < best) {
+      const int sl = step_slices(pr, k);
+      const int64_t u = units(rows) * sl, runs = (u + g - 1) / g;
+      const int64_t per = runs * (rows / sl + kStepUnitRows);
+      // equal estimates: where every CTA takes one unit, the half-swarm
+      // units (each CTA moves half the particles); else the larger tiles
+      const int tie = runs == 1 ? (sl > 1 ? 0 : 1) : (sl > 1 ? 1 : 0);
+      if (best < 0 || per < best || (per == best && tie < best_tie)) {
         best = per;
+        best_tie = tie;
         sh = k;
         grid = g;
       }
     }
-    const int rows = step_rows(pr, sh);
+    const int rows = step_rows(pr, sh), slices = step_slices(pr, sh);
     std::vector<WorkTile> st;
     if (grid > 0)
       for (int a = 0; a < A; ++a)
-        for (int r = 0; r < nodes[a].seg_len; r += rows)
-          st.push_back(
-              WorkTile{a, nodes[a].seg_start + r, std::min(rows, nodes[a].seg_len - r), 0});
+        for (int q = 0; q < slices; ++q)
+          for (int r = 0; r < nodes[a].seg_len; r += rows)
+            st.push_back(WorkTile{a, nodes[a].seg_start + r, std::min(rows, nodes[a].seg_len - r),
+                                  q * (pr.Pp / slices)});
     // Folding pays where the chain is latency-bound: a level whose
     // projection is a few waves of units (a tree's levels of one or a few
     // large nodes). Long projections (many nodes, or one very large node)
@@ -3060,7 +3068,8 @@ slm_status slm_set_fused_step(slm_ctx* c, int32_t on, int64_t* searches) {
 
 slm_status slm_set_step_shape(slm_ctx* c, int32_t shape, int32_t* last) {
   if (!c) return SLM_EINVAL;
-  if (shape < -1 || shape >= kStepShapeCount) return fail(c, SLM_EINVAL, "shape must be -1, 0, 1 or 2");
+  if (shape < -1 || shape >= kStepShapeCount)
+    return fail(c, SLM_EINVAL, "shape must be -1 or 0 .. 5");
   c->step_shape = shape;
   if (last) *last = c->last_step_shape;
   return SLM_OK;

@@ -275,15 +275,19 @@ cudaError_t launch_apso(const Problem& pr, const Swarm& sw, const NodeDesc* node
 // positions of t - 1) in shared memory; the CTA holding the node's first row
 // tile writes x_t to sw.pos, v_t to sw.vel and the gbest records. Then z and
 // the ranges of every (row tile, all particles) unit, as k_project (the same
-// fused multiply-adds). tiles: step_rows(pr, sh)-row tiles of the nodes in
-// order, every node with at least one; sh picks the tile shape (0: the
-// largest row tile; 1, 2: smaller ones, for short batches; step_rows 0 when
-// the swarm width has no such shape). The gbest step of the last evaluation
-// is left to launch_move(t = T). With sw.node_step the histogram kernel has
-// moved the swarm already: k_step loads the positions of t from pos_prev.
-constexpr int kStepShapeCount = 3;
+// fused multiply-adds). tiles: for every node in order, for each of its
+// step_slices(pr, sh) particle slices (WorkTile::pad = the slice's first
+// particle), its step_rows(pr, sh)-row tiles; every node with at least one.
+// sh picks the tile shape (0: the largest row tile with every particle;
+// 1, 2: smaller row tiles; 3-5: the same with half the particles per unit;
+// step_rows 0 when the swarm width has no such shape). The gbest step of
+// the last evaluation is left to launch_move(t = T). With sw.node_step the
+// histogram kernel has moved the swarm already: k_step loads the positions
+// of t from pos_prev.
+constexpr int kStepShapeCount = 6;
 bool step_ok(const Problem& pr);
 int step_rows(const Problem& pr, int sh);
+int step_slices(const Problem& pr, int sh);
 int step_grid(const Problem& pr, int sh, int n_sm);
 cudaError_t prepare_step_kernels(const Problem& pr, int sh);
 cudaError_t launch_step(const Problem& pr, const Swarm& sw, const float* pos_prev,

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int RB = 8 / PB;   // 32-row blocks of a unit
   constexpr int RT = 32 * RB;  // rows of a unit
   constexpr int PPB = 4 * PJ;  // particles of a particle block
+  constexpr int PU = PPB * PB;  // particles of a unit (a slice of the swarm, or all of it)
   static_assert(PJ % 2 == 0 && RB * PB == 8, "tile shape");
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_lo[64], s_hi[64];  // ordered-int range of each particle
@@ -116,8 +117,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   // holds the node's first row tile, in sw.pos / sw.vel with the gbest
   // records of evaluation t - 1). scratch[cap]: shared memory free during
   // the call (a row-tile stage buffer).
-  auto node_positions = [&](int a, bool desig, float* scratch, int cap) {
+  // desig: this CTA holds the first row tile of its slice (particles pg0 ..
+  // pg0 + PU - 1) of node a; the slice's positions go back to memory from
+  // there, and the node's gbest records from slice 0's
+  auto node_positions = [&](int a, int pg0, bool desig, float* scratch, int cap) {
     const int64_t nb = (int64_t)a * Pp * d;
+    const bool desig0 = desig && pg0 == 0;
+    const int p_lo = min(pg0, P), p_hi = min(P, pg0 + PU);  // the slice's particles
     if (t == 0 || sw.node_step) {  // the histogram kernel moved the swarm
       for (int e = threadIdx.x; e < P * d; e += kThreads) {
         const int p = e / d, j = e - p * d;
@@ -133,6 +139,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     // pbest became that position), which ps then holds: the move needs
     // nothing more from global memory.
     const int d4 = d >> 2, items = vec ? P * d4 : 0;
+    // the slice's elements (the positions of every particle are copied: gB
+    // may be any particle's)
+    const int e_lo = vec ? p_lo * d4 : 0, e_hi = vec ? p_hi * d4 : 0;
     if (vec) {
       for (int e = threadIdx.x; e < items; e += kThreads) {
         const int p = e / d4, j = 4 * (e - p * d4);
@@ -146,20 +155,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     // the move terms: every element of the thread in flight at once when
     // they fit kPre float4 per thread, else two at a time
     constexpr int kPre = 4;
-    const bool pre = items <= kPre * kThreads;
+    const bool pre = e_hi - e_lo <= kPre * kThreads;
     float4 ia[kPre], sa[kPre];
     auto load_terms = [&](int e0, int n) {
 #pragma unroll
       for (int u = 0; u < kPre; ++u) {
         const int e = e0 + u * kThreads;
-        if (u < n && e < items) {
+        if (u < n && e < e_hi) {
           const int64_t o = nb + 4 * (int64_t)e;  // element (p, 4q) of the node's rows
           ia[u] = __ldcg(reinterpret_cast<const float4*>(sw.ic + o));
           sa[u] = __ldcg(reinterpret_cast<const float4*>(sw.s2 + o));
         }
       }
     };
-    load_terms(threadIdx.x, pre ? kPre : 2);
+    load_terms(e_lo + threadIdx.x, pre ? kPre : 2);
     // gbest step of evaluation t - 1 (k_move's rule and double buffering)
     if (warp == 0) {
       // the argmin only when a particle beat gB in evaluation t - 1 (every
@@ -170,8 +179,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int bi = any ? gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t - 1, &be) : -1;
       if (lane == 0) {
         s_best = bi;
-        if (desig && sw.imp) sw.imp[(int64_t)(t & 1) * A + a] = 0;  // evaluation t's flag
-        if (desig) {
+        if (desig0 && sw.imp) sw.imp[(int64_t)(t & 1) * A + a] = 0;  // evaluation t's flag
+        if (desig0) {
           const EvalRes g = bi >= 0 ? be : gold;
           sw.gb[(int64_t)((t - 1) & 1) * A + a] = g;
           if (bi >= 0) {
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int j = threadIdx.x; j < d; j += kThreads)
           scratch[j] = ps[(j / kKC) * cstride + bi * kXS + j % kKC];
       __syncthreads();
-      if (desig && bi >= 0)
+      if (desig0 && bi >= 0)
         for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = scratch[j];
       // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
       auto move4 = [&](int e, const float4& ic, const float4& s2) {
@@ -220,25 +229,25 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (pre) {
 #pragma unroll
         for (int u = 0; u < kPre; ++u) {
-          const int e = threadIdx.x + u * kThreads;
-          if (e < items) move4(e, ia[u], sa[u]);
+          const int e = e_lo + threadIdx.x + u * kThreads;
+          if (e < e_hi) move4(e, ia[u], sa[u]);
         }
       } else {
-        for (int e0 = threadIdx.x; e0 < items; e0 += 2 * kThreads) {
-          if (e0 != (int)threadIdx.x) load_terms(e0, 2);
+        for (int e0 = e_lo + threadIdx.x; e0 < e_hi; e0 += 2 * kThreads) {
+          if (e0 != e_lo + (int)threadIdx.x) load_terms(e0, 2);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const int e = e0 + u * kThreads;
-            if (e < items) move4(e, ia[u], sa[u]);
+            if (e < e_hi) move4(e, ia[u], sa[u]);
           }
         }
       }
     } else {
       // a new best improved its pbest in evaluation t - 1: gB is that row
       const float* gsrc = bi >= 0 ? sw.pbest + nb + (int64_t)bi * d : sw.gbest + (int64_t)a * d;
-      if (desig && bi >= 0)
+      if (desig0 && bi >= 0)
         for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = gsrc[j];
-      for (int e = threadIdx.x; e < P * d; e += kThreads) {
+      for (int e = p_lo * d + (int)threadIdx.x; e < p_hi * d; e += kThreads) {
         const int p = e / d, j = e - p * d;
         const int64_t o = nb + e;
         const float x = pos_prev[o];
@@ -268,17 +277,19 @@ __global__ void __launch_bounds__(kThreads, 2)
   };
 
   float acc[4][PJ];
-  int cur_a = -1;
+  int cur_a = -1, cur_pg = -1;
 
   for (int s = 0; s < n_st; ++s) {
     const int ui = s / nk, c = s - ui * nk;
     const WorkTile wt = tiles[u0 + ui];
-    if (c == 0 && wt.node != cur_a) {
+    if (c == 0 && (wt.node != cur_a || wt.pad != cur_pg)) {
       __syncthreads();  // the previous node's positions and ranges are done with
       if (cur_a >= 0) flush_ranges(cur_a);
       cur_a = wt.node;
+      cur_pg = wt.pad;
       // stage buffer (s + 1) & 1 is free until the copies of step s + 1
-      node_positions(cur_a, wt.row0 == nodes[cur_a].seg_start, (s & 1) ? xs0 : xs1, RT * kXS);
+      node_positions(cur_a, cur_pg, wt.row0 == nodes[cur_a].seg_start, (s & 1) ? xs0 : xs1,
+                     RT * kXS);
     }
     if (c == 0) {  // a unit starts (zeroed here, so nothing is live through the move)
 #pragma unroll
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
     const float* xr = ((s & 1) ? xs1 : xs0) + (rb * 32 + sg) * kXS;
-    const float* ar = ps + c * cstride + (pbk * PPB + pg) * kXS;
+    const float* ar = ps + c * cstride + (cur_pg + pbk * PPB + pg) * kXS;
     const int kc4 = (min(kKC, d - c * kKC) + 3) >> 2;  // 16-byte chunks of features
 #pragma unroll 1
     for (int ch = 0; ch < kc4; ++ch) {
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // unit complete: store z, fold the ranges into the CTA's
 #pragma unroll
       for (int j = 0; j < PJ; ++j) {
-        const int p = pbk * PPB + pg + 4 * j;
+        const int p = cur_pg + pbk * PPB + pg + 4 * j;
         float lo = FLT_MAX, hi = -FLT_MAX;
         bool any = false;
 #pragma unroll
@@ -366,17 +377,22 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // Tile shapes of a padded swarm, largest row tile first: (PJ, PB), rows per
-// unit 32 (8 / PB). The smaller tiles spread a short node over more CTAs.
-constexpr int kStepShapes = 3;
+// unit 32 (8 / PB), particles per unit 4 PJ PB. Shapes 0-2 take every
+// particle in a unit; shapes 3-5 take half of them (two slices of a swarm of
+// 32 or 64), so a short node is spread over twice the CTAs with half the
+// move and projection each. The smaller tiles spread a short node further.
+constexpr int kStepShapes = 6;
 
 bool step_shape(int Pp, int sh, int* PJ, int* PB) {
-  static const int tab[4][kStepShapes][2] = {
-      {{4, 1}, {2, 2}, {0, 0}},   // Pp = 16
-      {{8, 1}, {4, 2}, {2, 4}},   // Pp = 32
-      {{6, 2}, {0, 0}, {0, 0}},   // Pp = 48
-      {{8, 2}, {4, 4}, {2, 8}}};  // Pp = 64
+  static const int tab[4][3][2] = {
+      {{4, 1}, {2, 2}, {0, 0}},   // 16 particles per unit
+      {{8, 1}, {4, 2}, {2, 4}},   // 32
+      {{6, 2}, {0, 0}, {0, 0}},   // 48
+      {{8, 2}, {4, 4}, {2, 8}}};  // 64
   if (Pp % 16 || Pp < 16 || Pp > 64 || sh < 0 || sh >= kStepShapes) return false;
-  const int* e = tab[Pp / 16 - 1][sh];
+  const int pu = sh < 3 ? Pp : Pp / 2;  // particles per unit
+  if (pu % 16) return false;
+  const int* e = tab[pu / 16 - 1][sh % 3];
   *PJ = e[0];
   *PB = e[1];
   return e[0] > 0;
@@ -418,6 +434,11 @@ bool step_ok(const Problem& pr) {
 int step_rows(const Problem& pr, int sh) {
   int PJ = 0, PB = 0;
   return step_shape(pr.Pp, sh, &PJ, &PB) ? 32 * (8 / PB) : 0;
+}
+
+int step_slices(const Problem& pr, int sh) {
+  int PJ = 0, PB = 0;
+  return step_shape(pr.Pp, sh, &PJ, &PB) ? pr.Pp / (4 * PJ * PB) : 0;
 }
 
 cudaError_t prepare_step_kernels(const Problem& pr, int sh) {

@@ -138,8 +138,9 @@ def test_default_folds_short_levels_only():
 
 @pytest.mark.parametrize("P,d", [(64, 64), (32, 20), (16, 30), (48, 12)])
 def test_every_tile_shape_gives_the_same_search(ctxs, P, d):
-    """The folded projection's tile shapes (rows per unit 32-256) project the
-    same z: searches identical to the unfolded kernels for each shape, and a
+    """The folded projection's tile shapes (rows per unit 32-256, every
+    particle or half of them per unit) project the same z and move the same
+    swarm: searches identical to the unfolded kernels for each shape, and a
     swarm width without a shape falls back to shape 0."""
     from paper_2208_07023_gb300 import binding as S
     a, b = ctxs
@@ -147,15 +148,17 @@ def test_every_tile_shape_gives_the_same_search(ctxs, P, d):
     p = gpu_params(S, "gini", 4, P, 6, 64, min_leaf=5, seed=7)
     rb = b.node_split(p, wl.X, labels=wl.labels, node_uid=5, want_trace=True)
     try:
-        for sh in (0, 1, 2):
+        # shapes each swarm width has (3-5: half the particles per unit)
+        have = {64: {0, 1, 2, 3, 4, 5}, 32: {0, 1, 2, 3, 4}, 16: {0, 1}, 48: {0}}[P]
+        for sh in range(6):
             a.set_step_shape(sh)
             ra = a.node_split(p, wl.X, labels=wl.labels, node_uid=5, want_trace=True)
             used = a.set_step_shape(sh)
-            assert used == (sh if P != 48 and not (P == 16 and sh == 2) else 0)
+            assert used == (sh if sh in have else 0)
             assert np.array_equal(ra["trace"], rb["trace"])
             assert np.array_equal(ra["gbest"], rb["gbest"]) and ra["bin"] == rb["bin"]
         fa = None
-        a.set_step_shape(2)
+        a.set_step_shape(5 if P == 64 else 2)
         pt = gpu_params(S, "gini", 4, P, 4, 64, min_leaf=5, max_depth=5, seed=2)
         fa = a.train_tree(pt, wl.X, labels=wl.labels)
         fb = b.train_tree(pt, wl.X, labels=wl.labels)
@@ -165,4 +168,4 @@ def test_every_tile_shape_gives_the_same_search(ctxs, P, d):
     finally:
         a.set_step_shape(-1)
     with pytest.raises(S.SlmError):
-        a.set_step_shape(3)
+        a.set_step_shape(6)
