@@ -1022,46 +1022,6 @@ __global__ void __launch_bounds__(128)
 
 // ---- top-k selection (SLM_PROJ_BF16_TOPK) ------------------------------------------
 
-// The whole CTA selects node a's tk_k best particles by sw.cur (ties to the
-// lower index; rank = particles strictly better, or equal and lower) and
-// gathers their positions. scratch: P EvalRes + 2 P ints of shared memory.
-__device__ __noinline__ void topk_select(const Problem& pr, const Swarm& sw, int a,
-                                         unsigned char* scratch) {
-  EvalRes* s_sc = reinterpret_cast<EvalRes*>(scratch);
-  int* s_take = reinterpret_cast<int*>(s_sc + pr.P);
-  int* s_sel = s_take + pr.P;
-  const int P = pr.P, Pp = pr.Pp, d = pr.d, k = sw.tk_k, kp = sw.tk_kp;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s_sc[p] = ldcg_res(sw.cur + (int64_t)a * Pp + p);
-  __syncthreads();
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const EvalRes me = s_sc[p];
-    int rank = 0;
-    for (int q = 0; q < P; ++q) {
-      if (q == p) continue;
-      const EvalRes o = s_sc[q];
-      if (better(o, me, pr.crit) || (q < p && !better(me, o, pr.crit))) ++rank;
-    }
-    s_take[p] = rank < k;
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < Pp; p += blockDim.x) {
-    int q = -1;
-    if (p < P && s_take[p]) {
-      q = 0;
-      for (int j = 0; j < p; ++j) q += s_take[j];
-      s_sel[q] = p;
-      sw.tk_sel[(int64_t)a * k + q] = p;
-    }
-    sw.tk_inv[(int64_t)a * Pp + p] = q;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kp * d; e += blockDim.x) {
-    const int q = e / d, j = e - q * d;
-    sw.tk_pos[((int64_t)a * kp + q) * d + j] =
-        q < k ? sw.pos[((int64_t)a * Pp + s_sel[q]) * d + j] : 0.0f;
-  }
-}
-
 // ---- histogram and scan -------------------------------------------------------------
 
 constexpr int kCopies = 4;  // histogram copies, each shared by a pair of warps

@@ -626,6 +626,14 @@ constexpr int kMseWords = 7;  // weight; lo, mid, hi of each of the two moments
 // Largest slice of one CTA: at most 65535 entries reach one counter.
 constexpr int kMseMaxSlice = 8 * 65535 - 4 * kThreads;
 
+// 32-bit words of the counters, also the top-k selection's scratch (P
+// scores and 2 P ints), a multiple of 4.
+__host__ __device__ inline int mse_count_words(int B, int P) {
+  const int cells = kMseWords * kMseCopies * (B + 1);
+  const int topk = (int)((sizeof(EvalRes) + 8) * P / 4);
+  return ((cells > topk ? cells : topk) + 3) & ~3;
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
     k_hist_mse(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
                const int32_t* __restrict__ list, int t, int do_update,
@@ -648,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint32_t* hcnt = reinterpret_cast<uint32_t*>(smem);
   const int plane = kMseCopies * BS;
   // the merged bins for the scan: [B] weight, [B] two moments (64-bit)
-  float* c1u = reinterpret_cast<float*>(hcnt + ((kMseWords * plane + 3) & ~3));
+  float* c1u = reinterpret_cast<float*>(hcnt + mse_count_words(B, pr.P));
   float* s2u = c1u + dv;
   float* xrow = s2u + dv;
   float* vrow = xrow + dv;
@@ -834,6 +842,19 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     sc.imp = imp;
   }
+  if (sw.tk_sel) {
+    // the reduced pass of the BF16 form: the last particle of the node to be
+    // scored selects the node's top k (the counters are free by now)
+    __threadfence();  // this CTA's score write before the count
+    __syncthreads();
+    if (threadIdx.x == 0) sc.ok = atomicAdd(&sw.done[a], 1) == pr.P - 1;
+    __syncthreads();
+    if (sc.ok) {
+      __threadfence();
+      topk_select(pr, sw, a, reinterpret_cast<unsigned char*>(hcnt));
+      if (threadIdx.x == 0) sw.done[a] = 0;
+    }
+  }
   if (!do_update) return;
   __syncthreads();
   const bool imp = sc.imp;
@@ -858,10 +879,7 @@ const void* hist_cls_fn(const Problem& pr) {
 
 size_t hist_cls_smem(const Problem& pr) {
   const size_t tail = sizeof(float) * 5 * (size_t)hc_dvec(pr.d);
-  if (pr.crit == SLM_MSE) {
-    const size_t cells = (size_t)kMseWords * kMseCopies * (pr.B + 1);
-    return ((cells + 3) & ~(size_t)3) * 4 + tail;
-  }
+  if (pr.crit == SLM_MSE) return (size_t)mse_count_words(pr.B, pr.P) * 4 + tail;
   return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K + tail;
 }
 

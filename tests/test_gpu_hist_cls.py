@@ -142,3 +142,25 @@ def test_regression_trees_identical_with_both_histogram_kernels(ctxs, bootstrap)
     same_tree(fa, fb, p.n_trees)
     fa.free()
     fb.free()
+
+
+def test_bf16_regression_identical_with_both_histogram_kernels(ctxs):
+    """The BF16 form's reduced pass (its last CTA per node selecting the top
+    k) and FP32 re-scoring pass on the squared-error kernel: the same search
+    and tree as with the staged-copy kernel."""
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.tanh_regression(20000, 32, seed=6)
+    p = S.make_params("mse", 0, n_particles=64, n_iters=6, n_bins=128, min_leaf=5, seed=3,
+                      max_depth=6, proj=S.SLM_PROJ_BF16_TOPK, topk=8)
+    ra = a.node_split(p, wl.X, y=wl.y, node_uid=2, want_trace=True)
+    rb = b.node_split(p, wl.X, y=wl.y, node_uid=2, want_trace=True)
+    assert np.array_equal(ra["trace"], rb["trace"])
+    assert np.array_equal(ra["gbest"], rb["gbest"])
+    for k in ("bin", "loss", "n_left", "n_right", "particle", "iter_of_best"):
+        assert ra[k] == rb[k], k
+    fa = a.train_tree(p, wl.X, y=wl.y)
+    fb = b.train_tree(p, wl.X, y=wl.y)
+    same_tree(fa, fb)
+    fa.free()
+    fb.free()
