@@ -639,8 +639,9 @@ slm_status slm_set_step_shape(slm_ctx* ctx, int32_t shape, int32_t* last);
  * iteration with the latency-oriented histogram kernels (entries loaded 16
  * bytes at a time with several in flight; classification: class-major
  * histograms scanned one warp per class; regression, for nodes of at most
- * 523,256 entries: the fixed-point bin moments added as 32-bit pieces into
- * lane-private copies; the pbest step spread over the block); on = 0: with
+ * 257,740 entries: two particles per block, the fixed-point bin moments
+ * added as 32-bit pieces into lane copies; the pbest step spread over the
+ * block; the BF16 form's regression passes too); on = 0: with
  * the staged-copy histogram kernel that also serves bins output and the
  * BF16 form. node_step != 0: in folded classification searches
  * (slm_set_fused_step) whose nodes all take that kernel, the last block to

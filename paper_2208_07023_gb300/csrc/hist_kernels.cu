@@ -612,82 +612,103 @@ __global__ void __launch_bounds__(kThreads, 2)
 // 64-bit moment v is added as three pieces, v mod 2^16, (v >> 16) mod 2^16
 // (each sum stays below 2^32 for up to 65535 entries per counter) and the
 // signed v >> 32, and the bin's sum is rebuilt exactly as
-// hi 2^32 + mid 2^16 + lo. Lane l adds into copy l mod kMseCopies (entries
-// of one warp that fall in the same bin rarely meet at one address; rows
+// hi 2^32 + mid 2^16 + lo. Lane l adds into its particle's copy l mod
+// kMseCopies (entries of one warp that fall in the same bin rarely meet at
+// one address; rows
 // padded by one word so equal bins of different copies sit in different
 // banks). Entries are read straight from L2 with several 16-byte groups in
 // flight per thread; the copies are summed, the cluster's ranks merged
 // through distributed shared memory, and the scan is block_scan_mse:
 // integer sums are order-free, so the scores are those of the staged-copy
-// kernel. The tail (score, pbest step, the next move's gB-independent
+// kernel. In batches of many nodes each CTA scores two particles: the
+// entries' moments are read once for both (they are the same for every
+// particle, only the bins differ), and the fewer CTAs carry less fixed cost
+// each. The tail (score, pbest step, the next move's gB-independent
 // terms) is k_hist_cls's, with its inputs prefetched.
-constexpr int kMseCopies = 8;
 constexpr int kMseWords = 7;  // weight; lo, mid, hi of each of the two moments
-// Largest slice of one CTA: at most 65535 entries reach one counter.
-constexpr int kMseMaxSlice = 8 * 65535 - 4 * kThreads;
+// Particles per CTA: 1 (8 copies per particle, lane mod 8), or 2 (4 copies,
+// lane mod 4) for batches of many nodes, where fewer, fuller CTAs pay.
+__host__ __device__ constexpr int mse_copies(int NP) { return NP == 1 ? 8 : 4; }
+// CTAs (node x particle) from which a batch takes two particles per CTA.
+constexpr int64_t kMsePairFrom = 4096;
+__host__ __device__ inline int mse_np(const Problem& pr, int A) {
+  return (int64_t)A * pr.P >= kMsePairFrom ? 2 : 1;
+}
+// Largest node: a counter takes the entries of one lane in mse_copies(NP)
+// (plus at most about 1,100 of rounding), at most 65535 (the smaller bound).
+constexpr int kMseMaxSlice = 4 * (65535 - 1100);
 
-// 32-bit words of the counters, also the top-k selection's scratch (P
-// scores and 2 P ints), a multiple of 4.
-__host__ __device__ inline int mse_count_words(int B, int P) {
-  const int cells = kMseWords * kMseCopies * (B + 1);
+// 32-bit words of one particle's counters [kMseWords][copies][B + 1].
+__host__ __device__ inline int mse_particle_words(int B, int NP) {
+  return kMseWords * mse_copies(NP) * (B + 1);
+}
+// 32-bit words of the CTA's counters, also the top-k selection's scratch
+// (P scores and 2 P ints), a multiple of 4.
+__host__ __device__ inline int mse_count_words(int B, int P, int NP) {
+  const int cells = NP * mse_particle_words(B, NP);
   const int topk = (int)((sizeof(EvalRes) + 8) * P / 4);
   return ((cells > topk ? cells : topk) + 3) & ~3;
 }
 
+template <int NP>
 __global__ void __launch_bounds__(kThreads, 2)
     k_hist_mse(Problem pr, Swarm sw, const NodeDesc* __restrict__ nodes,
                const int32_t* __restrict__ list, int t, int do_update,
                const double* /* c ln c table: unused by the squared error */) {
   namespace cg = cooperative_groups;
+  constexpr int kMseCopies = mse_copies(NP);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ HcScratch sc;
   __shared__ ScanScratch ss;
+  __shared__ EvalRes s_pb[NP];
+  __shared__ int s_imp[NP];
   const cg::cluster_group cl = cg::this_cluster();
   pdl_trigger();
   const int S = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int a = list ? list[blockIdx.x / S] : (int)blockIdx.x / S;
-  const int p = blockIdx.y;
+  const int p0 = blockIdx.y * NP;
+  const int np = min(NP, pr.P - p0);  // the CTA's particles p0 .. p0 + np - 1
   const int lane = threadIdx.x & 31;
   const int B = pr.B, d = pr.d, BS = B + 1;  // copy stride (padded)
   const NodeDesc nd = nodes[a];
   const int dv = hc_dvec(d);
-  // counters [kMseWords][copies][BS]: weight, then lo / mid / hi of each moment
+  // counters of particle q: [kMseWords][copies][BS] at hcnt + q * pwords
   uint32_t* hcnt = reinterpret_cast<uint32_t*>(smem);
-  const int plane = kMseCopies * BS;
-  // the merged bins for the scan: [B] weight, [B] two moments (64-bit)
-  float* c1u = reinterpret_cast<float*>(hcnt + mse_count_words(B, pr.P));
-  float* s2u = c1u + dv;
-  float* xrow = s2u + dv;
-  float* vrow = xrow + dv;
-  float* prow = vrow + dv;
-  const bool premove = do_update && sw.ic && t < sw.T && rank == 0;
+  const int plane = kMseCopies * BS, pwords = mse_particle_words(B, NP);
+  // per particle: c1 r1, c2 r2 of its next move, its x, v and pB rows
+  float* rows0 = reinterpret_cast<float*>(hcnt + mse_count_words(B, pr.P, NP));
+  auto row = [&](int q, int k) { return rows0 + (size_t)(5 * q + k) * dv; };
+  const bool upd = do_update && rank == 0;
+  const bool premove = upd && sw.ic && t < sw.T;
 
-  for (int i = threadIdx.x; i < kMseWords * plane; i += kThreads) hcnt[i] = 0u;
+  for (int i = threadIdx.x; i < NP * pwords; i += kThreads) hcnt[i] = 0u;
   if (premove) {
     const uint32_t k0 = (uint32_t)sw.co.seed, k1 = (uint32_t)(sw.co.seed >> 32);
-    for (int q = threadIdx.x; q < ((d + 3) >> 2); q += kThreads) {
-      const U4 r1 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)p,
-                                  (uint32_t)q | (kR1 << 24), k0, k1);
-      const U4 r2 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)p,
-                                  (uint32_t)q | (kR2 << 24), k0, k1);
+    for (int i = threadIdx.x; i < np * ((d + 3) >> 2); i += kThreads) {
+      const int q = i / ((d + 3) >> 2), qq = i - q * ((d + 3) >> 2);
+      const U4 r1 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)(p0 + q),
+                                  (uint32_t)qq | (kR1 << 24), k0, k1);
+      const U4 r2 = philox4x32_10(nd.uid, (uint32_t)(t + 1), (uint32_t)(p0 + q),
+                                  (uint32_t)qq | (kR2 << 24), k0, k1);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        if (4 * q + c < d) {
-          c1u[4 * q + c] = __fmul_rn(sw.co.c1, uniform24(r1.v[c]));
-          s2u[4 * q + c] = __fmul_rn(sw.co.c2, uniform24(r2.v[c]));
+        if (4 * qq + c < d) {
+          row(q, 0)[4 * qq + c] = __fmul_rn(sw.co.c1, uniform24(r1.v[c]));
+          row(q, 1)[4 * qq + c] = __fmul_rn(sw.co.c2, uniform24(r2.v[c]));
         }
     }
   }
   __syncthreads();  // the zeroed copies, before any binning
   pdl_wait();
-  int* zz = sw.zmm + ((int64_t)a * pr.Pp + p) * 2;
-  const int64_t ci = (int64_t)a * pr.Pp + p;
+  const int64_t ci0 = (int64_t)a * pr.Pp + p0;
+  int* zz0 = sw.zmm + ci0 * 2;
   const int chunk = ((nd.seg_len + S - 1) / S + 3) & ~3;
   const int r_begin = min(nd.seg_len, rank * chunk);
   const int r_end = min(nd.seg_len, r_begin + chunk);
   const int64_t e0 = nd.seg_start + r_begin;
-  const float* zs = sw.z + (int64_t)p * pr.Ez + e0;
+  const float* zs0 = sw.z + (int64_t)p0 * pr.Ez + e0;
+  const float* zs1 = np > 1 ? zs0 + pr.Ez : zs0;
   const long long* m1 = pr.m1 + e0;
   const long long* m2 = pr.m2 + e0;
   const uint32_t* ws = pr.w ? pr.w + e0 : nullptr;
@@ -695,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool g16 = (e0 & 3) == 0;
   const int n4 = g16 ? n >> 2 : 0;
   constexpr int U = 2;  // groups of four entries in flight per thread
-  float4 zv[U];
+  float4 zv[U][NP];
   longlong2 a1[U][2], a2[U][2];
   uint4 wv[U];
   auto load_groups = [&](int g0) {
@@ -703,7 +724,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int u = 0; u < U; ++u) {
       const int g = g0 + u * kThreads;
       if (g < n4) {
-        zv[u] = __ldcg(reinterpret_cast<const float4*>(zs) + g);
+        zv[u][0] = __ldcg(reinterpret_cast<const float4*>(zs0) + g);
+        if (NP > 1) zv[u][NP - 1] = __ldcg(reinterpret_cast<const float4*>(zs1) + g);
         a1[u][0] = __ldg(reinterpret_cast<const longlong2*>(m1) + 2 * g);
         a1[u][1] = __ldg(reinterpret_cast<const longlong2*>(m1) + 2 * g + 1);
         a2[u][0] = __ldg(reinterpret_cast<const longlong2*>(m2) + 2 * g);
@@ -713,41 +735,55 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
   };
   load_groups(threadIdx.x);
-  const int64_t prow0 = ci * d;
-  if (do_update && rank == 0) {
+  // the tail's inputs, in flight from here: the particles' pbest scores and
+  // the node's gbest score (evaluation t - 1), their x, v and pB rows
+  if (upd) {
     constexpr int kResWords = (int)(sizeof(EvalRes) / 4);
     const int64_t gi = (int64_t)((t + 1) & 1) * sw.n_nodes + a;
-    if (threadIdx.x < kResWords)
-      cp_async4(reinterpret_cast<uint32_t*>(&sc.pb) + threadIdx.x,
-                reinterpret_cast<const uint32_t*>(sw.pb + ci) + threadIdx.x, 4);
-    else if (threadIdx.x >= 32 && threadIdx.x < 32 + kResWords && sw.imp)
-      cp_async4(reinterpret_cast<uint32_t*>(&sc.gb) + (threadIdx.x - 32),
-                reinterpret_cast<const uint32_t*>(sw.gb + gi) + (threadIdx.x - 32), 4);
-    for (int j = threadIdx.x; j < d; j += kThreads) {
-      cp_async4(xrow + j, sw.pos + prow0 + j, 4);
+    if (threadIdx.x < np * kResWords) {
+      const int q = threadIdx.x / kResWords, w = threadIdx.x - q * kResWords;
+      cp_async4(reinterpret_cast<uint32_t*>(s_pb + q) + w,
+                reinterpret_cast<const uint32_t*>(sw.pb + ci0 + q) + w, 4);
+    } else if (threadIdx.x >= 128 && threadIdx.x < 128 + kResWords && sw.imp) {
+      cp_async4(reinterpret_cast<uint32_t*>(&sc.gb) + (threadIdx.x - 128),
+                reinterpret_cast<const uint32_t*>(sw.gb + gi) + (threadIdx.x - 128), 4);
+    }
+    for (int i = threadIdx.x; i < np * d; i += kThreads) {
+      const int q = i / d, j = i - q * d;
+      const int64_t o = (ci0 + q) * d + j;
+      cp_async4(row(q, 2) + j, sw.pos + o, 4);
       if (premove) {
-        cp_async4(vrow + j, sw.vel + prow0 + j, 4);
-        cp_async4(prow + j, sw.pbest + prow0 + j, 4);
+        cp_async4(row(q, 3) + j, sw.vel + o, 4);
+        cp_async4(row(q, 4) + j, sw.pbest + o, 4);
       }
     }
     cp_async_commit();
   }
-  float zmin = 0.f, inv_w = 0.f;
-  bool ok = false;
-  {
-    const int lo_o = __ldcg(zz), hi_o = __ldcg(zz + 1);
-    if (lo_o != INT_MAX) {
-      const float lo = ord2f(lo_o), hi = ord2f(hi_o);
-      inv_w = __fdiv_rn((float)B, __fsub_rn(hi, lo));
-      zmin = lo;
-      ok = (hi > lo) && isfinite(inv_w);
+  // the particles' ranges and bin widths, read by every thread (thread 0
+  // resets the ranges only after the barriers below)
+  float zmin[NP], inv_w[NP];
+  bool ok[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    zmin[q] = 0.f;
+    inv_w[q] = 0.f;
+    ok[q] = false;
+    if (q < np) {
+      const int lo_o = __ldcg(zz0 + 2 * q), hi_o = __ldcg(zz0 + 2 * q + 1);
+      if (lo_o != INT_MAX) {
+        const float lo = ord2f(lo_o), hi = ord2f(hi_o);
+        inv_w[q] = __fdiv_rn((float)B, __fsub_rn(hi, lo));
+        zmin[q] = lo;
+        ok[q] = (hi > lo) && isfinite(inv_w[q]);
+      }
     }
   }
-  // ---- binning of this rank's slice
-  if (ok) {
+  // ---- binning of this rank's slice, both particles from one read of the
+  // entries' moments
+  {
     const int cpy = (lane % kMseCopies) * BS;
-    auto add = [&](float z, long long v1, long long v2, uint32_t w) {
-      uint32_t* h = hcnt + cpy + bin_of(z, zmin, inv_w, B);
+    auto add = [&](int q, float z, long long v1, long long v2, uint32_t w) {
+      uint32_t* h = hcnt + q * pwords + cpy + bin_of(z, zmin[q], inv_w[q], B);
       const unsigned long long u1 = (unsigned long long)v1, u2 = (unsigned long long)v2;
       atomicAdd(h, w);
       atomicAdd(h + plane, (uint32_t)(u1 & 0xffffu));
@@ -757,97 +793,124 @@ __global__ void __launch_bounds__(kThreads, 2)
       atomicAdd(h + 5 * plane, (uint32_t)((u2 >> 16) & 0xffffu));
       atomicAdd(h + 6 * plane, (uint32_t)(u2 >> 32));
     };
-    for (int g0 = threadIdx.x; g0 < n4; g0 += U * kThreads) {
-      if (g0 != (int)threadIdx.x) load_groups(g0);
+    if (ok[0] || ok[NP - 1]) {
+      for (int g0 = threadIdx.x; g0 < n4; g0 += U * kThreads) {
+        if (g0 != (int)threadIdx.x) load_groups(g0);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (g0 + u * kThreads >= n4) break;
-        add(zv[u].x, a1[u][0].x, a2[u][0].x, wv[u].x);
-        add(zv[u].y, a1[u][0].y, a2[u][0].y, wv[u].y);
-        add(zv[u].z, a1[u][1].x, a2[u][1].x, wv[u].z);
-        add(zv[u].w, a1[u][1].y, a2[u][1].y, wv[u].w);
+        for (int u = 0; u < U; ++u) {
+          if (g0 + u * kThreads >= n4) break;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            if (!ok[q]) continue;
+            add(q, zv[u][q].x, a1[u][0].x, a2[u][0].x, wv[u].x);
+            add(q, zv[u][q].y, a1[u][0].y, a2[u][0].y, wv[u].y);
+            add(q, zv[u][q].z, a1[u][1].x, a2[u][1].x, wv[u].z);
+            add(q, zv[u][q].w, a1[u][1].y, a2[u][1].y, wv[u].w);
+          }
+        }
+      }
+      for (int i = (n4 << 2) + (int)threadIdx.x; i < n; i += kThreads) {
+        const long long v1 = __ldg(m1 + i), v2 = __ldg(m2 + i);
+        const uint32_t w = ws ? __ldg(ws + i) : 1u;
+        if (ok[0]) add(0, __ldcg(zs0 + i), v1, v2, w);
+        if (NP > 1 && ok[NP - 1]) add(NP - 1, __ldcg(zs1 + i), v1, v2, w);
       }
     }
-    for (int i = (n4 << 2) + (int)threadIdx.x; i < n; i += kThreads)
-      add(__ldcg(zs + i), __ldg(m1 + i), __ldg(m2 + i), ws ? __ldg(ws + i) : 1u);
   }
   __syncthreads();
-  // ---- the copies into bin sums (thread b: bin b), written after every
-  // thread has read the copies: the weight into copy 0's row, the moments
-  // rebuilt exactly as 64-bit integers (two's complement: signed sums wrap
-  // exactly) over the first piece plane
-  uint32_t w = 0;
-  unsigned long long v[2] = {0ull, 0ull};
+  // ---- each particle's copies into bin sums (thread b: bin b), written
+  // after every thread has read the copies: the weight into the particle's
+  // first row, the moments rebuilt exactly as 64-bit integers (two's
+  // complement: signed sums wrap exactly) over its first piece plane
+  uint32_t w[NP];
+  unsigned long long v[NP][2];
   const int bi = threadIdx.x;  // B <= kThreads
-  if (bi < B) {
 #pragma unroll
-    for (int c = 0; c < kMseCopies; ++c) {
-      const uint32_t* h = hcnt + c * BS + bi;
-      w += h[0];
+  for (int q = 0; q < NP; ++q) {
+    w[q] = 0;
+    v[q][0] = v[q][1] = 0ull;
+    if (bi < B && q < np) {
 #pragma unroll
-      for (int m = 0; m < 2; ++m)
-        v[m] += (unsigned long long)h[(1 + 3 * m) * plane] +
-                ((unsigned long long)h[(2 + 3 * m) * plane] << 16) +
-                ((unsigned long long)(long long)(int32_t)h[(3 + 3 * m) * plane] << 32);
+      for (int c = 0; c < kMseCopies; ++c) {
+        const uint32_t* h = hcnt + q * pwords + c * BS + bi;
+        w[q] += h[0];
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+          v[q][m] += (unsigned long long)h[(1 + 3 * m) * plane] +
+                     ((unsigned long long)h[(2 + 3 * m) * plane] << 16) +
+                     ((unsigned long long)(long long)(int32_t)h[(3 + 3 * m) * plane] << 32);
+      }
     }
   }
   __syncthreads();
-  uint32_t* hw = hcnt;                                                                 // [B]
-  unsigned long long* hs = reinterpret_cast<unsigned long long*>(hcnt + ((plane + 1) & ~1));  // [2][B]
-  if (bi < B) {
-    hw[bi] = w;
-    hs[bi] = v[0];
-    hs[B + bi] = v[1];
-  }
+  auto hw_of = [&](int q) { return hcnt + q * pwords; };  // [B]
+  auto hs_of = [&](int q) {                                  // [2][B]
+    return reinterpret_cast<unsigned long long*>(hcnt + q * pwords + ((plane + 1) & ~1));
+  };
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+    if (bi < B && q < np) {
+      hw_of(q)[bi] = w[q];
+      hs_of(q)[bi] = v[q][0];
+      hs_of(q)[B + bi] = v[q][1];
+    }
   // ---- the other ranks' bins into rank 0
   if (S > 1) {
     cl.sync();  // every rank's bin sums are complete
     if (rank == 0)
-      for (int i = threadIdx.x; i < B; i += kThreads) {
-        uint32_t w = hw[i];
-        unsigned long long v1 = hs[i], v2 = hs[B + i];
-        for (int q = 1; q < S; ++q) {
-          w += cl.map_shared_rank(hw, q)[i];
-          v1 += cl.map_shared_rank(hs, q)[i];
-          v2 += cl.map_shared_rank(hs, q)[B + i];
+      for (int q = 0; q < np; ++q)
+        for (int i = threadIdx.x; i < B; i += kThreads) {
+          uint32_t ww = hw_of(q)[i];
+          unsigned long long v1 = hs_of(q)[i], v2 = hs_of(q)[B + i];
+          for (int r = 1; r < S; ++r) {
+            ww += cl.map_shared_rank(hw_of(q), r)[i];
+            v1 += cl.map_shared_rank(hs_of(q), r)[i];
+            v2 += cl.map_shared_rank(hs_of(q), r)[B + i];
+          }
+          hw_of(q)[i] = ww;
+          hs_of(q)[i] = v1;
+          hs_of(q)[B + i] = v2;
         }
-        hw[i] = w;
-        hs[i] = v1;
-        hs[B + i] = v2;
-      }
     cl.sync();  // the other ranks' memory is no longer read
     if (rank != 0) return;
   }
   cp_async_wait<0>();  // the tail's prefetched inputs
   __syncthreads();
-  EvalRes res = invalid_res();
-  if (ok) {
-    res = block_scan_mse(hw, reinterpret_cast<const long long*>(hs),
-                         reinterpret_cast<const long long*>(hs + B), pr.mscale[2 * a],
-                         pr.mscale[2 * a + 1], B, pr.min_leaf, ss);
-    res.zmin = zmin;
-    res.inv_w = inv_w;
-  }
-  // ---- score, range reset, pbest step, the next move's gB-independent terms
-  if (threadIdx.x == 0) {
-    sw.cur[ci] = res;
-    zz[0] = INT_MAX;  // ready for the next iteration
-    zz[1] = INT_MIN;
-    int imp = 0;
-    if (do_update) {
-      if (sw.imp && res.valid && (t == 0 || better(res, sc.gb, pr.crit)))
-        atomicOr(sw.imp + (int64_t)(t & 1) * sw.n_nodes + a, 1);
-      imp = (t == 0) || better(res, sc.pb, pr.crit);
-      if (imp) sw.pb[ci] = res;
+  EvalRes res[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    res[q] = invalid_res();
+    if (q < np && ok[q]) {  // the same branch in every thread (block_scan_mse syncs)
+      res[q] = block_scan_mse(hw_of(q), reinterpret_cast<const long long*>(hs_of(q)),
+                              reinterpret_cast<const long long*>(hs_of(q) + B),
+                              pr.mscale[2 * a], pr.mscale[2 * a + 1], B, pr.min_leaf, ss);
+      res[q].zmin = zmin[q];
+      res[q].inv_w = inv_w[q];
     }
-    sc.imp = imp;
+  }
+  // ---- scores, range resets, pbest steps, the next moves' gB-independent terms
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < np; ++q) {
+      const int64_t ci = ci0 + q;
+      sw.cur[ci] = res[q];
+      zz0[2 * q] = INT_MAX;  // ready for the next iteration
+      zz0[2 * q + 1] = INT_MIN;
+      int imp = 0;
+      if (do_update) {
+        if (sw.imp && res[q].valid && (t == 0 || better(res[q], sc.gb, pr.crit)))
+          atomicOr(sw.imp + (int64_t)(t & 1) * sw.n_nodes + a, 1);
+        imp = (t == 0) || better(res[q], s_pb[q], pr.crit);
+        if (imp) sw.pb[ci] = res[q];
+      }
+      s_imp[q] = imp;
+    }
   }
   if (sw.tk_sel) {
-    // the reduced pass of the BF16 form: the last particle of the node to be
-    // scored selects the node's top k (the counters are free by now)
-    __threadfence();  // this CTA's score write before the count
+    // the reduced pass of the BF16 form: the last CTA of the node to score
+    // its particles selects the node's top k (the counters are free by now)
+    __threadfence();  // this CTA's score writes before the count
     __syncthreads();
-    if (threadIdx.x == 0) sc.ok = atomicAdd(&sw.done[a], 1) == pr.P - 1;
+    if (threadIdx.x == 0) sc.ok = atomicAdd(&sw.done[a], np) + np == pr.P;
     __syncthreads();
     if (sc.ok) {
       __threadfence();
@@ -857,36 +920,42 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   if (!do_update) return;
   __syncthreads();
-  const bool imp = sc.imp;
-  if (imp || premove)
-    for (int j = threadIdx.x; j < d; j += kThreads) {
-      const float x = xrow[j];
-      if (imp) sw.pbest[prow0 + j] = x;  // the position is kept on improvement
-      if (premove) {
-        const float pbv = imp ? x : prow[j];
-        sw.ic[prow0 + j] = __fadd_rn(__fmul_rn(sw.co.inertia, vrow[j]),
-                                     __fmul_rn(c1u[j], __fsub_rn(pbv, x)));
-        sw.s2[prow0 + j] = s2u[j];
-      }
+  for (int i = threadIdx.x; i < np * d; i += kThreads) {
+    const int q = i / d, j = i - q * d;
+    const bool imp = s_imp[q];
+    if (!imp && !premove) continue;
+    const int64_t o = (ci0 + q) * d + j;
+    const float x = row(q, 2)[j];
+    if (imp) sw.pbest[o] = x;  // the position is kept on improvement
+    if (premove) {
+      // ic = omega v + (c1 r1)(pB - x); pB is x itself after an improvement
+      const float pbv = imp ? x : row(q, 4)[j];
+      sw.ic[o] = __fadd_rn(__fmul_rn(sw.co.inertia, row(q, 3)[j]),
+                           __fmul_rn(row(q, 0)[j], __fsub_rn(pbv, x)));
+      sw.s2[o] = row(q, 1)[j];
     }
+  }
 }
 
-const void* hist_cls_fn(const Problem& pr) {
+const void* hist_cls_fn(const Problem& pr, int np = 1) {
   return pr.crit == SLM_GINI      ? (const void*)k_hist_cls<SLM_GINI>
          : pr.crit == SLM_ENTROPY ? (const void*)k_hist_cls<SLM_ENTROPY>
-                                  : (const void*)k_hist_mse;
+         : np == 2                ? (const void*)k_hist_mse<2>
+                                  : (const void*)k_hist_mse<1>;
 }
 
-size_t hist_cls_smem(const Problem& pr) {
+size_t hist_cls_smem(const Problem& pr, int np = 1) {
   const size_t tail = sizeof(float) * 5 * (size_t)hc_dvec(pr.d);
-  if (pr.crit == SLM_MSE) return (size_t)mse_count_words(pr.B, pr.P) * 4 + tail;
+  if (pr.crit == SLM_MSE) return (size_t)mse_count_words(pr.B, pr.P, np) * 4 + np * tail;
   return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K + tail;
 }
 
 }  // namespace
 
 bool hist_cls_ok(const Problem& pr) {
-  if (pr.B < 2 || pr.B > kThreads || hist_cls_smem(pr) > 200 * 1024) return false;
+  if (pr.B < 2 || pr.B > kThreads || hist_cls_smem(pr, 1) > 200 * 1024 ||
+      hist_cls_smem(pr, 2) > 200 * 1024)
+    return false;
   if (pr.crit == SLM_MSE) return pr.m1 && pr.m2 && pr.mscale;
   return pr.lab && pr.K >= 1 && pr.K <= kMaxClasses;
 }
@@ -896,17 +965,21 @@ bool hist_cls_fits(const Problem& pr, int64_t max_len) {
 }
 
 cudaError_t prepare_hist_cls(const Problem& pr) {
-  const void* f = hist_cls_fn(pr);
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)hist_cls_smem(pr));
-  if (e) return e;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int np = 1; np <= (pr.crit == SLM_MSE ? 2 : 1); ++np) {
+    const void* f = hist_cls_fn(pr, np);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)hist_cls_smem(pr, np));
+    if (!e) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e) return e;
+  }
+  return cudaSuccess;
 }
 
 int hist_cls_split(const Problem& pr, int A, int64_t max_len, int n_sm) {
+  const int np = pr.crit == SLM_MSE ? mse_np(pr, A) : 1;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_cls_fn(pr), kThreads,
-                                                    hist_cls_smem(pr)) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_cls_fn(pr, np), kThreads,
+                                                    hist_cls_smem(pr, np)) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -914,7 +987,8 @@ int hist_cls_split(const Problem& pr, int A, int64_t max_len, int n_sm) {
   // most 8 CTAs per cluster (the portable size)
   const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * n_sm;
   int S = 1;
-  while (2 * S <= 8 && (int64_t)A * pr.P * (2 * S) <= resident && max_len / (2 * S) >= 1024) S *= 2;
+  const int64_t ctas = (pr.P + np - 1) / np;  // per node and slice
+  while (2 * S <= 8 && (int64_t)A * ctas * (2 * S) <= resident && max_len / (2 * S) >= 1024) S *= 2;
   return S;
 }
 
@@ -922,10 +996,11 @@ cudaError_t launch_hist_cls(const Problem& pr, const Swarm& sw, const NodeDesc* 
                             int S, int t, int do_update, const double* xtab, cudaStream_t st,
                             const int32_t* list) {
   if (A <= 0) return cudaSuccess;
+  const int np = pr.crit == SLM_MSE ? mse_np(pr, A) : 1;  // particles per CTA
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(A * S), (unsigned)pr.P, 1);
+  cfg.gridDim = dim3((unsigned)(A * S), (unsigned)((pr.P + np - 1) / np), 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = hist_cls_smem(pr);
+  cfg.dynamicSmemBytes = hist_cls_smem(pr, np);
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -936,7 +1011,7 @@ cudaError_t launch_hist_cls(const Problem& pr, const Swarm& sw, const NodeDesc* 
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  const void* f = hist_cls_fn(pr);
+  const void* f = hist_cls_fn(pr, np);
   void* args[] = {(void*)&pr, (void*)&sw, (void*)&nodes, (void*)&list, (void*)&t,
                   (void*)&do_update, (void*)&xtab};
   return cudaLaunchKernelExC(&cfg, f, args);
