@@ -67,10 +67,10 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 # launch over its pairs, profiles/), each valid only for the kernel source it
 # was taken from: (bytes per pair, source file, sha256 of that file).
 TRAFFIC = {
-    "project": (12932608 / 3.2e6, "step_kernels.cu",
-                "7df29d69e65fd86852afe5a4704fb3dc38455802ca6e5c12e701260157d12685"),
-    "hist_scan": (13066752 / 3.2e6, "hist_kernels.cu",
-                  "8b8f94a389cabf789cd7740c9efa7637b83dc092378a81b9557dc2f3d8fc12ea"),
+    "project": (12932864 / 3.2e6, "step_kernels.cu",
+                "db60b334ad0975b64e5cf1065519cdd9a551d020d7698e83f22f2606cbbd142e"),
+    "hist_scan": (13067008 / 3.2e6, "hist_kernels.cu",
+                  "793ddd4ff6abd0d104d6907b8793a988d6e07779a1f0e13c910c1c20d85c15a3"),
 }
 
 

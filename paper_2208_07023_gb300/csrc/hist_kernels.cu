@@ -360,19 +360,21 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
-    // block argmin over the edges (ties to the lower edge), on the double
+    // block argmin over the edges (ties to the lower edge), on a key of the
     // loss each edge would report (Gini: (n d - q) / (n d) from the exact
-    // rational, as the score below), with edges within 8 ulps of the
-    // smallest compared exactly in edge order: the rounding of the loss is
-    // far below 8 ulps, so the choice is the exact one
-    uint64_t key = ~0ull;
-    if (bb >= 0) {
+    // rational, in float, so no double division per edge; entropy: the
+    // double loss), with edges within 8 ulps of the key's smallest compared
+    // exactly in edge order: the key's rounding is far below 8 ulps, so the
+    // choice is the exact one
+    auto edge_key = [&](uint64_t n_, uint64_t d_, double l_, int b_) -> uint64_t {
+      if (b_ < 0) return ~0ull;
       if (CRIT == SLM_GINI) {
-        const uint64_t nden = (uint64_t)ntot * bd;
-        bl = (double)(nden - bn) / (double)nden;
+        const uint64_t nden = (uint64_t)ntot * d_;
+        return __float_as_uint(__fdiv_rn((float)(nden - n_), (float)nden));  // >= 0
       }
-      key = hc_key(bl);
-    }
+      return hc_key(l_);
+    };
+    uint64_t key = edge_key(bn, bd, bl, bb);
     // the exact winner among this warp's lanes in `cand` (lane order =
     // edge order), into lane 0's bn, bd, bl, bb, bnl
     auto resolve = [&](unsigned cand) {
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       bl = in ? sc.wl[lane] : 0.0;
       bb = in ? sc.wb[lane] : -1;
       bnl = in ? sc.wnl[lane] : 0u;
-      key = bb >= 0 ? hc_key(bl) : ~0ull;
+      key = edge_key(bn, bd, bl, bb);
       uint64_t kmin = key;
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) {
@@ -444,8 +446,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (CRIT == SLM_GINI) {
           res.num = bn;
           res.den = bd;
+          const uint64_t nden = (uint64_t)nt * bd;
+          res.loss = (double)(nden - bn) / (double)nden;
+        } else {
+          res.loss = bl;
         }
-        res.loss = bl;
       }
     }
     if (threadIdx.x == 0) {

@@ -164,3 +164,20 @@ def test_bf16_regression_identical_with_both_histogram_kernels(ctxs):
     same_tree(fa, fb)
     fa.free()
     fb.free()
+
+
+def test_regression_pairs_of_particles_per_block(ctxs):
+    """Wide regression levels (at least 4,096 node-particle pairs) score two
+    particles per block, here with an odd swarm (the last block one
+    particle): the same trees as the staged-copy kernel."""
+    from paper_2208_07023_gb300 import binding as S
+    a, b = ctxs
+    wl = W.tanh_regression(40000, 12, seed=9)
+    p = gpu_params(S, "mse", 0, 127, 3, 64, min_leaf=8, max_depth=8, seed=5)
+    fa = a.train_tree(p, wl.X, y=wl.y)
+    fb = b.train_tree(p, wl.X, y=wl.y)
+    same_tree(fa, fb)
+    g = fa.export(0)
+    assert (g["kind"] == 1).sum() >= 64  # levels of 32+ nodes x 127 particles were scored
+    fa.free()
+    fb.free()
