@@ -11,8 +11,8 @@
 //  * binning: every thread keeps 16 entries in flight (four 16-byte loads of
 //    z, of labels, of multiplicities) before their shared-memory atomics,
 //    into the copy of its warp pair; histograms are class-major ([K][B]);
-//  * the copies are summed and rank 0 adds the other ranks' histograms
-//    through distributed shared memory, loads issued back to back;
+//  * the copies are summed, and the cluster's ranks sum one slice each of
+//    every rank's counters through distributed shared memory into rank 0;
 //  * the scan: one warp per class turns the class's row of B bins into its
 //    prefix sums (16-byte loads, a shuffle scan), then thread b scores edge
 //    b + 1 (bins <= b left) from the K prefixes at bin b (consecutive threads
@@ -219,26 +219,22 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int c = 1; c < kHcCopies; ++c) v += hc[c * W + i];
     hc[i] = v;
   }
-  // ---- the other ranks' histograms into rank 0
+  // ---- the cluster's histograms into rank 0: rank r sums the r-th of S
+  // slices of the counters over every rank (all loads in flight at once)
+  // and stores the sums into rank 0's copy (the slices are disjoint)
   if (S > 1) {
     cl.sync();  // every rank's copy 0 is complete
-    if (rank == 0) {
-      for (int i0 = threadIdx.x; i0 < W; i0 += 4 * kThreads) {
-        uint32_t v[4];
+    const int per = (W + S - 1) / S;
+    const int lo = rank * per, hi = min(W, lo + per);
+    uint32_t* h0 = cl.map_shared_rank(hc, 0);
+    for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
+      uint32_t v = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = i0 + u * kThreads < W ? hc[i0 + u * kThreads] : 0u;
-        for (int q = 1; q < S; ++q) {
-          const uint32_t* rh = cl.map_shared_rank(hc, q);
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (i0 + u * kThreads < W) v[u] += rh[i0 + u * kThreads];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (i0 + u * kThreads < W) hc[i0 + u * kThreads] = v[u];
-      }
+      for (int q = 0; q < 16; ++q)
+        if (q < S) v += cl.map_shared_rank(hc, q)[i];
+      h0[i] = v;
     }
-    cl.sync();  // the other ranks' memory is no longer read
+    cl.sync();  // rank 0's counters are complete; no rank reads another's
     if (rank != 0) return;
   }
   cp_async_wait<0>();  // the tail's prefetched inputs
@@ -859,24 +855,28 @@ __global__ void __launch_bounds__(kThreads, 2)
       hs_of(q)[bi] = v[q][0];
       hs_of(q)[B + bi] = v[q][1];
     }
-  // ---- the other ranks' bins into rank 0
+  // ---- the cluster's bins into rank 0: rank r sums the r-th of S slices
+  // of the bins over every rank and stores the sums into rank 0's
   if (S > 1) {
     cl.sync();  // every rank's bin sums are complete
-    if (rank == 0)
-      for (int q = 0; q < np; ++q)
-        for (int i = threadIdx.x; i < B; i += kThreads) {
-          uint32_t ww = hw_of(q)[i];
-          unsigned long long v1 = hs_of(q)[i], v2 = hs_of(q)[B + i];
-          for (int r = 1; r < S; ++r) {
+    const int per = (B + S - 1) / S;
+    const int lo = rank * per, hi = min(B, lo + per);
+    for (int q = 0; q < np; ++q)
+      for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
+        uint32_t ww = 0;
+        unsigned long long v1 = 0ull, v2 = 0ull;
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          if (r < S) {
             ww += cl.map_shared_rank(hw_of(q), r)[i];
             v1 += cl.map_shared_rank(hs_of(q), r)[i];
             v2 += cl.map_shared_rank(hs_of(q), r)[B + i];
           }
-          hw_of(q)[i] = ww;
-          hs_of(q)[i] = v1;
-          hs_of(q)[B + i] = v2;
-        }
-    cl.sync();  // the other ranks' memory is no longer read
+        cl.map_shared_rank(hw_of(q), 0)[i] = ww;
+        cl.map_shared_rank(hs_of(q), 0)[i] = v1;
+        cl.map_shared_rank(hs_of(q), 0)[B + i] = v2;
+      }
+    cl.sync();  // rank 0's bins are complete; no rank reads another's
     if (rank != 0) return;
   }
   cp_async_wait<0>();  // the tail's prefetched inputs
