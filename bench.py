@@ -69,8 +69,8 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 TRAFFIC = {
     "project": (12932864 / 3.2e6, "step_kernels.cu",
                 "db60b334ad0975b64e5cf1065519cdd9a551d020d7698e83f22f2606cbbd142e"),
-    "hist_scan": (13067008 / 3.2e6, "hist_kernels.cu",
-                  "793ddd4ff6abd0d104d6907b8793a988d6e07779a1f0e13c910c1c20d85c15a3"),
+    "hist_scan": (13066752 / 3.2e6, "hist_kernels.cu",
+                  "6f68b7d4d74b33aa1829e342c7bd6e53d04dfa1930446620722c161afca598a7"),
 }
 
 
