@@ -1411,20 +1411,51 @@ __device__ EvalRes warp_scan_cls(uint32_t* h, int B, int K, int min_leaf) {
       }
     }
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const int ob = __shfl_xor_sync(0xffffffffu, bb, off);
-    const uint64_t on = __shfl_xor_sync(0xffffffffu, bn, off);
-    const uint64_t od = __shfl_xor_sync(0xffffffffu, bd, off);
-    const double ol = __shfl_xor_sync(0xffffffffu, bl, off);
-    const uint32_t onl = __shfl_xor_sync(0xffffffffu, bnl, off);
-    if (edge_takes<CRIT>(on, od, ol, ob, bn, bd, bl, bb)) {
-      bn = on;
-      bd = od;
-      bl = ol;
-      bb = ob;
-      bnl = onl;
+  // the warp argmin on a 32-bit key of each lane's best loss (one warp
+  // reduction), the lanes within 8 ulps of the smallest key compared
+  // exactly in lane order (= edge order within each lane's stride): the
+  // key's rounding is far below 8 ulps, so the choice is the exact one
+  uint32_t key = 0xffffffffu;
+  if (bb >= 0) {
+    float lf;
+    if (CRIT == SLM_GINI) {
+      const uint64_t nden = (uint64_t)ntot * bd;
+      lf = __fdiv_rn((float)(nden - bn), (float)nden);
+    } else {
+      lf = (float)bl;
     }
+    const uint32_t u = __float_as_uint(lf);
+    key = (u >> 31) ? ~u : (u | 0x80000000u);  // the float order as unsigned
+  }
+  {
+    const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
+    unsigned m = __ballot_sync(0xffffffffu, bb >= 0 && key - kmin <= 8u);
+    int wi = m ? __ffs(m) - 1 : 0;
+    uint64_t wn = __shfl_sync(0xffffffffu, bn, wi), wd = __shfl_sync(0xffffffffu, bd, wi);
+    double wl = __shfl_sync(0xffffffffu, bl, wi);
+    int wb = m ? __shfl_sync(0xffffffffu, bb, wi) : -1;
+    uint32_t wnl = __shfl_sync(0xffffffffu, bnl, wi);
+    m = m ? m & (m - 1) : 0u;
+    while (m) {  // rare: several lanes within a few ulps
+      const int li = __ffs(m) - 1;
+      m &= m - 1;
+      const uint64_t on = __shfl_sync(0xffffffffu, bn, li), od = __shfl_sync(0xffffffffu, bd, li);
+      const double ol = __shfl_sync(0xffffffffu, bl, li);
+      const int ob = __shfl_sync(0xffffffffu, bb, li);
+      const uint32_t onl = __shfl_sync(0xffffffffu, bnl, li);
+      if (edge_takes<CRIT>(on, od, ol, ob, wn, wd, wl, wb)) {
+        wn = on;
+        wd = od;
+        wl = ol;
+        wb = ob;
+        wnl = onl;
+      }
+    }
+    bn = wn;
+    bd = wd;
+    bl = wl;
+    bb = wb;
+    bnl = wnl;
   }
   EvalRes res = invalid_res();
   if (bb >= 0) {
@@ -1698,12 +1729,8 @@ __global__ void __launch_bounds__(kNodeThreads)
       }
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        int lo = lo_t[jj], hi = hi_t[jj];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-          hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-        }
+        const int lo = __reduce_min_sync(0xffffffffu, lo_t[jj]);
+        const int hi = __reduce_max_sync(0xffffffffu, hi_t[jj]);
         if (lane == 0 && lo != INT_MAX) {
           atomicMin(&s_lo[jj], lo);
           atomicMax(&s_hi[jj], hi);
