@@ -67,10 +67,10 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 # launch over its pairs, profiles/), each valid only for the kernel source it
 # was taken from: (bytes per pair, source file, sha256 of that file).
 TRAFFIC = {
-    "project": (12932864 / 3.2e6, "step_kernels.cu",
-                "db60b334ad0975b64e5cf1065519cdd9a551d020d7698e83f22f2606cbbd142e"),
+    "project": (12944384 / 3.2e6, "step_kernels.cu",
+                "d169c12dbdfa6585462cb9b162f2f161141c64e5be5c333e95fcb0a03f8b32b6"),
     "hist_scan": (13066752 / 3.2e6, "hist_kernels.cu",
-                  "6f68b7d4d74b33aa1829e342c7bd6e53d04dfa1930446620722c161afca598a7"),
+                  "1d003482bab0f586acce410d1c2604f54159dbf817b5986a96886f72c7ad7126"),
 }
 
 

@@ -206,27 +206,12 @@ __device__ __forceinline__ uint64_t loss_key(const EvalRes& e) {
   return e.valid ? (uint64_t)__double_as_longlong(e.loss) : ~0ull;
 }
 
-__device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
-                            EvalRes* best_res, bool l2 = false) {
+// The warp's choice among its lanes' candidates: lane l proposes particle bi
+// (-1: none) with score be; returns the chosen particle (-1 when no lane has
+// a candidate) and, in lane 0, its score into *best_res (be of lane 0 when
+// there is none).
+__device__ int gbest_select(const Problem& pr, int bi, const EvalRes& be, EvalRes* best_res) {
   const int lane = threadIdx.x & 31;
-  int bi = -1;
-  EvalRes be = invalid_res();
-  auto consider = [&](int p, const EvalRes& e) {
-    if (!(t == 0 || better(e, gold, pr.crit))) return;
-    if (bi < 0 || better(e, be, pr.crit)) {
-      bi = p;
-      be = e;
-    }
-  };
-  // two records per lane in flight, considered in particle order
-  for (int p = lane; p < pr.P; p += 64) {
-    const bool two = p + 32 < pr.P;
-    const EvalRes e0 = l2 ? ldcg_res(cur + p) : cur[p];
-    EvalRes e1 = e0;
-    if (two) e1 = l2 ? ldcg_res(cur + p + 32) : cur[p + 32];
-    consider(p, e0);
-    if (two) consider(p + 32, e1);
-  }
   const unsigned cand = __ballot_sync(0xffffffffu, bi >= 0);
   if (!cand) {  // nobody beat gold
     if (lane == 0) *best_res = be;
@@ -261,6 +246,35 @@ __device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes
   const EvalRes w = shfl_res(be, wi);
   if (lane == 0) *best_res = w;
   return wb;
+}
+
+// Lane l's candidate among particles l and l + 32 (scores e0, e1; in that
+// order), against the gbest score gold of the previous step (every valid
+// score is a candidate at t = 0).
+__device__ __forceinline__ void gbest_consider(const Problem& pr, const EvalRes& gold, int t,
+                                               int p, const EvalRes& e, int* bi, EvalRes* be) {
+  if (!(t == 0 || better(e, gold, pr.crit))) return;
+  if (*bi < 0 || better(e, *be, pr.crit)) {
+    *bi = p;
+    *be = e;
+  }
+}
+
+__device__ int gbest_argmin(const Problem& pr, const EvalRes* cur, const EvalRes& gold, int t,
+                            EvalRes* best_res, bool l2 = false) {
+  const int lane = threadIdx.x & 31;
+  int bi = -1;
+  EvalRes be = invalid_res();
+  // two records per lane in flight, considered in particle order
+  for (int p = lane; p < pr.P; p += 64) {
+    const bool two = p + 32 < pr.P;
+    const EvalRes e0 = l2 ? ldcg_res(cur + p) : cur[p];
+    EvalRes e1 = e0;
+    if (two) e1 = l2 ? ldcg_res(cur + p + 32) : cur[p + 32];
+    gbest_consider(pr, gold, t, p, e0, &bi, &be);
+    if (two) gbest_consider(pr, gold, t, p + 32, e1, &bi, &be);
+  }
+  return gbest_select(pr, bi, be, best_res);
 }
 
 // Folded searches (Swarm::imp): records that score `res` of a particle of

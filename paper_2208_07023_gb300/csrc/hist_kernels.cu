@@ -402,11 +402,16 @@ __global__ void __launch_bounds__(kThreads, 2)
       bnl = wnl;
     };
     {
-      uint64_t kmin = key;
+      uint64_t kmin;
+      if (CRIT == SLM_GINI) {  // a 32-bit key: one reduction
+        kmin = __reduce_min_sync(0xffffffffu, bb >= 0 ? (uint32_t)key : 0xffffffffu);
+      } else {
+        kmin = key;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
-        kmin = o < kmin ? o : kmin;
+        for (int off = 16; off > 0; off >>= 1) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
+          kmin = o < kmin ? o : kmin;
+        }
       }
       resolve(__ballot_sync(0xffffffffu, bb >= 0 && key <= kmin + 8));
     }
@@ -427,11 +432,16 @@ __global__ void __launch_bounds__(kThreads, 2)
       bb = in ? sc.wb[lane] : -1;
       bnl = in ? sc.wnl[lane] : 0u;
       key = edge_key(bn, bd, bl, bb);
-      uint64_t kmin = key;
+      uint64_t kmin;
+      if (CRIT == SLM_GINI) {
+        kmin = __reduce_min_sync(0xffffffffu, bb >= 0 ? (uint32_t)key : 0xffffffffu);
+      } else {
+        kmin = key;
 #pragma unroll
-      for (int off = 4; off > 0; off >>= 1) {
-        const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
-        kmin = o < kmin ? o : kmin;
+        for (int off = 4; off > 0; off >>= 1) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, kmin, off);
+          kmin = o < kmin ? o : kmin;
+        }
       }
       resolve(__ballot_sync(0xffffffffu, bb >= 0 && key <= kmin + 8));
       if (lane == 0 && bb >= 0) {

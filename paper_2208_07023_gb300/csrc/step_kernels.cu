@@ -18,7 +18,11 @@
 // with the gbest records, exactly as k_move would.
 //
 // Each CTA of the persistent grid takes a contiguous run of units; it forms a
-// node's positions once for all its consecutive units of that node.
+// node's positions once for all its consecutive units of that node. The row
+// tiles stream through a ring of shared-memory stages (the copies of the next
+// NS - 1 feature chunks in flight, one barrier per chunk), and a finished
+// unit's z leaves through per-warp staging rows, so that each store writes
+// whole 128-byte rows of a particle.
 //
 // Thread tile: 4 rows (sg + 8i) x PJ particles (pg + 4j) per thread; a warp
 // covers 32 rows x 4 PJ particles; the CTA's 8 warps are RB = 8 / PB row
@@ -36,6 +40,9 @@ namespace slm {
 namespace {
 
 constexpr int kStepMaxPosBytes = 96 * 1024;  // the node's positions in shared memory
+// Floats per particle of a warp's z staging rows: 32 rows and 8 of padding,
+// so that the four particles a warp stages fall on distinct banks.
+constexpr int kZS = 40;
 
 // Positions in shared memory, chunk-major: feature j of particle p at
 // (j / kKC) * Pp * kXS + p * kXS + j % kKC, so that the particles a thread
@@ -46,6 +53,11 @@ __host__ __device__ inline size_t step_pos_floats(int Pp, int d) {
   return (size_t)((d + kKC - 1) / kKC) * Pp * kXS;
 }
 
+// Row-tile stages in the ring: the copies of the next NS - 1 steps are in
+// flight while a step computes (fewer for the larger row tiles, so that two
+// CTAs still fit on an SM).
+__host__ __device__ constexpr int step_stages(int RT) { return RT <= 64 ? 4 : RT <= 128 ? 3 : 2; }
+
 template <int PJ, int PB>
 __global__ void __launch_bounds__(kThreads, 2)
     k_step(Problem pr, Swarm sw, const float* __restrict__ pos_prev,
@@ -55,15 +67,17 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int RT = 32 * RB;  // rows of a unit
   constexpr int PPB = 4 * PJ;  // particles of a particle block
   constexpr int PU = PPB * PB;  // particles of a unit (a slice of the swarm, or all of it)
-  static_assert(PJ % 2 == 0 && RB * PB == 8, "tile shape");
+  constexpr int NS = step_stages(RT);
+  static_assert(PJ % 2 == 0 && RB * PB == 8 && NS >= 2, "tile shape");
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_lo[64], s_hi[64];  // ordered-int range of each particle
   __shared__ int s_best;
-  float* xs0 = sm;                // [RT][kXS] rows of a feature chunk, two stages
-  float* xs1 = sm + RT * kXS;
-  float* ps = sm + 2 * RT * kXS;  // the node's positions, chunk-major
-  pdl_trigger();
   const int d = pr.d, Pp = pr.Pp, P = pr.P;
+  float* xs = sm;                                   // [NS][RT][kXS] row-tile stages
+  float* ps = sm + NS * RT * kXS;                   // the node's positions, chunk-major
+  float* gs = ps + step_pos_floats(Pp, d);          // the node's gB (d floats, padded to 4)
+  float* zst = gs + ((d + 3) & ~3);                 // [8 warps][4][kZS] z staging rows
+  pdl_trigger();
   const int nk = (d + kKC - 1) / kKC;
   const int cstride = Pp * kXS;   // floats per feature chunk of the positions
   const bool vec = (d & 3) == 0;
@@ -76,25 +90,29 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int my_units = (int)(((int64_t)(blockIdx.x + 1) * n_units) / gridDim.x) - u0;
   const int n_st = my_units * nk;
 
-  // rows of step s (unit s / nk, feature chunk s % nk) into xb; rows past
-  // the tile and features past d arrive as zeros
-  auto stage = [&](int s, float* xb) {
-    const int ui = s / nk, c = s - ui * nk;
-    const WorkTile wt = tiles[u0 + ui];
-    const int k0 = c * kKC, kc = min(kKC, d - k0);
-    if (vec) {
-      for (int q = threadIdx.x; q < RT * (kKC / 4); q += kThreads) {
-        const int r = q >> 3, cc = (q & 7) * 4;
-        const bool ok = r < wt.rows && cc < kc;
-        const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
-        cp_async16(xb + r * kXS + cc, src, ok ? 16 : 0);
-      }
-    } else {
-      for (int q = threadIdx.x; q < RT * kKC; q += kThreads) {
-        const int r = q >> 5, cc = q & 31;
-        const bool ok = r < wt.rows && cc < kc;
-        const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
-        cp_async4(xb + r * kXS + cc, src, ok ? 4 : 0);
+  // rows of step s (unit s / nk, feature chunk s % nk) into its ring stage;
+  // rows past the tile and features past d arrive as zeros. One commit group
+  // per step, empty past the last.
+  auto stage = [&](int s) {
+    if (s < n_st) {
+      float* xb = xs + (s % NS) * (RT * kXS);
+      const int ui = s / nk, c = s - ui * nk;
+      const WorkTile wt = tiles[u0 + ui];
+      const int k0 = c * kKC, kc = min(kKC, d - k0);
+      if (vec) {
+        for (int q = threadIdx.x; q < RT * (kKC / 4); q += kThreads) {
+          const int r = q >> 3, cc = (q & 7) * 4;
+          const bool ok = r < wt.rows && cc < kc;
+          const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
+          cp_async16(xb + r * kXS + cc, src, ok ? 16 : 0);
+        }
+      } else {
+        for (int q = threadIdx.x; q < RT * kKC; q += kThreads) {
+          const int r = q >> 5, cc = q & 31;
+          const bool ok = r < wt.rows && cc < kc;
+          const float* src = ok ? row_of(pr, wt.row0 + r) + k0 + cc : pr.X;
+          cp_async4(xb + r * kXS + cc, src, ok ? 4 : 0);
+        }
       }
     }
     cp_async_commit();
@@ -107,20 +125,21 @@ __global__ void __launch_bounds__(kThreads, 2)
   // Within a search the rows and tiles are written before the first
   // iteration's launch, so iterations t > 0 start fetching them before the
   // previous kernel's results are visible.
-  if (n_st > 0 && t > 0) stage(0, xs0);
+  if (t > 0)
+    for (int s = 0; s < NS - 1; ++s) stage(s);
   // padding features and particles of the positions stay zero
   for (int i = threadIdx.x; i < nk * cstride; i += kThreads) ps[i] = 0.0f;
   pdl_wait();
-  if (n_st > 0 && t == 0) stage(0, xs0);
+  if (t == 0)
+    for (int s = 0; s < NS - 1; ++s) stage(s);
 
   // The positions of node a for iteration t in ps (and, from the CTA that
   // holds the node's first row tile, in sw.pos / sw.vel with the gbest
-  // records of evaluation t - 1). scratch[cap]: shared memory free during
-  // the call (a row-tile stage buffer).
+  // records of evaluation t - 1).
   // desig: this CTA holds the first row tile of its slice (particles pg0 ..
   // pg0 + PU - 1) of node a; the slice's positions go back to memory from
   // there, and the node's gbest records from slice 0's
-  auto node_positions = [&](int a, int pg0, bool desig, float* scratch, int cap) {
+  auto node_positions = [&](int a, int pg0, bool desig) {
     const int64_t nb = (int64_t)a * Pp * d;
     const bool desig0 = desig && pg0 == 0;
     const int p_lo = min(pg0, P), p_hi = min(P, pg0 + PU);  // the slice's particles
@@ -133,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       return;
     }
     // Positions of t - 1 go by asynchronous copies straight into ps (moved
-    // there in place) and the recorded gB into scratch; the move terms to
+    // there in place) and the recorded gB into gs; the move terms to
     // registers; all before the gbest step. After a gbest change gB is the
     // new best particle's position of t - 1 (it beat every pbest, so its own
     // pbest became that position), which ps then holds: the move needs
@@ -149,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                    16);
       }
       for (int q = threadIdx.x; q < d4; q += kThreads)
-        cp_async16(scratch + 4 * q, sw.gbest + (int64_t)a * d + 4 * q, 16);
+        cp_async16(gs + 4 * q, sw.gbest + (int64_t)a * d + 4 * q, 16);
       cp_async_commit();
     }
     // the move terms: every element of the thread in flight at once when
@@ -169,14 +188,26 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     };
     load_terms(e_lo + threadIdx.x, pre ? kPre : 2);
-    // gbest step of evaluation t - 1 (k_move's rule and double buffering)
+    // gbest step of evaluation t - 1 (k_move's rule and double buffering),
+    // its inputs loaded together: the node's scores (two per lane), the
+    // improvement flag and the recorded gbest score
     if (warp == 0) {
+      const EvalRes* cur = sw.cur + (int64_t)a * Pp;
+      const EvalRes e0 = lane < P ? cur[lane] : invalid_res();
+      const EvalRes e1 = lane + 32 < P ? cur[lane + 32] : invalid_res();
       // the argmin only when a particle beat gB in evaluation t - 1 (every
       // particle is a candidate at evaluation 0)
       const bool any = t == 1 || !sw.imp || __ldcg(sw.imp + (int64_t)((t - 1) & 1) * A + a) != 0;
       const EvalRes gold = sw.gb[(int64_t)(t & 1) * A + a];
       EvalRes be = gold;
-      const int bi = any ? gbest_argmin(pr, sw.cur + (int64_t)a * Pp, gold, t - 1, &be) : -1;
+      int bi = -1;
+      if (any) {
+        int ci = -1;
+        EvalRes ce = invalid_res();
+        if (lane < P) gbest_consider(pr, gold, t - 1, lane, e0, &ci, &ce);
+        if (lane + 32 < P) gbest_consider(pr, gold, t - 1, lane + 32, e1, &ci, &ce);
+        bi = gbest_select(pr, ci, ce, &be);
+      }
       if (lane == 0) {
         s_best = bi;
         if (desig0 && sw.imp) sw.imp[(int64_t)(t & 1) * A + a] = 0;  // evaluation t's flag
@@ -197,19 +228,19 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     const int bi = s_best;
     if (vec) {
-      // gB into scratch before any position is overwritten
+      // gB into gs before any position is overwritten
       if (bi >= 0)
         for (int j = threadIdx.x; j < d; j += kThreads)
-          scratch[j] = ps[(j / kKC) * cstride + bi * kXS + j % kKC];
+          gs[j] = ps[(j / kKC) * cstride + bi * kXS + j % kKC];
       __syncthreads();
       if (desig0 && bi >= 0)
-        for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = scratch[j];
+        for (int j = threadIdx.x; j < d; j += kThreads) sw.gbest[(int64_t)a * d + j] = gs[j];
       // x' = x + (ic + s2 (gB - x)), v' = ic + s2 (gB - x), one rounding each
       auto move4 = [&](int e, const float4& ic, const float4& s2) {
         const int p = e / d4, j = 4 * (e - p * d4);
         float* xp = ps + (j / kKC) * cstride + p * kXS + j % kKC;
         const float4 x = *reinterpret_cast<const float4*>(xp);
-        const float4 g = *reinterpret_cast<const float4*>(scratch + j);
+        const float4 g = *reinterpret_cast<const float4*>(gs + j);
         float4 vn, xn;
         vn.x = __fadd_rn(ic.x, __fmul_rn(s2.x, __fsub_rn(g.x, x.x)));
         vn.y = __fadd_rn(ic.y, __fmul_rn(s2.y, __fsub_rn(g.y, x.y)));
@@ -278,43 +309,38 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   float acc[4][PJ];
   int cur_a = -1, cur_pg = -1;
+  float* zw = zst + warp * (4 * kZS);  // this warp's staging rows
+  const bool z16 = ((reinterpret_cast<uintptr_t>(sw.z) | (uintptr_t)pr.Ez * 4) & 15) == 0;
 
   for (int s = 0; s < n_st; ++s) {
     const int ui = s / nk, c = s - ui * nk;
     const WorkTile wt = tiles[u0 + ui];
-    if (c == 0 && (wt.node != cur_a || wt.pad != cur_pg)) {
-      __syncthreads();  // the previous node's positions and ranges are done with
-      if (cur_a >= 0) flush_ranges(cur_a);
-      cur_a = wt.node;
-      cur_pg = wt.pad;
-      // stage buffer (s + 1) & 1 is free until the copies of step s + 1
-      node_positions(cur_a, cur_pg, wt.row0 == nodes[cur_a].seg_start, (s & 1) ? xs0 : xs1,
-                     RT * kXS);
-    }
-    if (c == 0) {  // a unit starts (zeroed here, so nothing is live through the move)
+    cp_async_wait<NS - 2>();
+    // step s's rows are in place, and every warp is done with step s - 1
+    // (its stage, the positions of its node, its ranges)
+    __syncthreads();
+    if (c == 0) {  // a unit starts (no sum is live through the move)
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < PJ; ++j) acc[i][j] = 0.0f;
+      if (wt.node != cur_a || wt.pad != cur_pg) {
+        if (cur_a >= 0) flush_ranges(cur_a);
+        cur_a = wt.node;
+        cur_pg = wt.pad;
+        node_positions(cur_a, cur_pg, wt.row0 == nodes[cur_a].seg_start);
+      }
     }
-    if (s + 1 < n_st) {
-      stage(s + 1, (s & 1) ? xs0 : xs1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const float* xr = ((s & 1) ? xs1 : xs0) + (rb * 32 + sg) * kXS;
+    stage(s + NS - 1);  // into the stage step s - 1 read
+    const float* xr = xs + (s % NS) * (RT * kXS) + (rb * 32 + sg) * kXS;
     const float* ar = ps + c * cstride + (cur_pg + pbk * PPB + pg) * kXS;
-    const int kc4 = (min(kKC, d - c * kKC) + 3) >> 2;  // 16-byte chunks of features
-#pragma unroll 1
-    for (int ch = 0; ch < kc4; ++ch) {
+    // features 4 ch .. 4 ch + 3 of the chunk: feature-outer within each pair
+    // of particles, so every accumulator takes the features in increasing order
+    auto fma4 = [&](int ch) {
       float4 xv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         xv[i] = *reinterpret_cast<const float4*>(xr + i * 8 * kXS + 4 * ch);
-      // feature-outer within each pair of particles: every accumulator takes
-      // features 4 ch .. 4 ch + 3 in increasing order
 #pragma unroll
       for (int j = 0; j < PJ; j += 2) {
         const float4 a0 = *reinterpret_cast<const float4*>(ar + j * 4 * kXS + 4 * ch);
@@ -340,23 +366,36 @@ __global__ void __launch_bounds__(kThreads, 2)
           acc[i][j + 1] = fmaf(xv[i].w, a1.w, acc[i][j + 1]);
         }
       }
+    };
+    const int kc4 = (min(kKC, d - c * kKC) + 3) >> 2;  // 16-byte chunks of features
+    if (kc4 == kKC / 4) {
+#pragma unroll(PJ <= 4 ? 2 : 1)
+      for (int ch = 0; ch < kKC / 4; ++ch) fma4(ch);
+    } else {
+#pragma unroll 1
+      for (int ch = 0; ch < kc4; ++ch) fma4(ch);
     }
     if (c == nk - 1) {
-      // unit complete: store z, fold the ranges into the CTA's
+      // unit complete: the ranges into the CTA's; z out through the warp's
+      // staging rows, so that every store writes whole rows of a particle
+      // (four 128-byte rows per 16-byte store when aligned, else one per
+      // 4-byte store) instead of 32-byte pieces of four rows
+      const int rw = wt.rows - rb * 32;  // rows of the warp's block in the tile
+      const int64_t zrow = wt.row0 + rb * 32;
+      const bool v16 = z16 && rw >= 32 && (zrow & 3) == 0;
 #pragma unroll
       for (int j = 0; j < PJ; ++j) {
-        const int p = cur_pg + pbk * PPB + pg + 4 * j;
+        const int pb0 = cur_pg + pbk * PPB + 4 * j;  // the warp's particles pb0 .. pb0 + 3
+        const int p = pb0 + pg;
         float lo = FLT_MAX, hi = -FLT_MAX;
         bool any = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int r = rb * 32 + sg + 8 * i;
-          if (r < wt.rows) {
+          if (sg + 8 * i < rw) {
             const float z = acc[i][j];
             lo = z < lo ? z : lo;
             hi = z > hi ? z : hi;
             any = true;
-            if (p < P) sw.z[(int64_t)p * pr.Ez + wt.row0 + r] = z;
           }
         }
         int olo = any ? f2ord(lo) : INT_MAX, ohi = any ? f2ord(hi) : INT_MIN;
@@ -369,11 +408,24 @@ __global__ void __launch_bounds__(kThreads, 2)
           atomicMin(&s_lo[p], olo);
           atomicMax(&s_hi[p], ohi);
         }
+        __syncwarp();  // the previous particles' staging rows are read
+#pragma unroll
+        for (int i = 0; i < 4; ++i) zw[pg * kZS + sg + 8 * i] = acc[i][j];
+        __syncwarp();
+        if (v16) {
+          const int q = lane >> 3, r4 = 4 * (lane & 7);
+          const float4 v = *reinterpret_cast<const float4*>(zw + q * kZS + r4);
+          if (pb0 + q < P) *reinterpret_cast<float4*>(sw.z + (int64_t)(pb0 + q) * pr.Ez + zrow + r4) = v;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (lane < rw && pb0 + q < P) sw.z[(int64_t)(pb0 + q) * pr.Ez + zrow + lane] = zw[q * kZS + lane];
+        }
       }
     }
-    __syncthreads();  // this stage is refilled by the copies of step s + 2
   }
-  if (cur_a >= 0) flush_ranges(cur_a);  // after the loop's last barrier
+  __syncthreads();  // every warp's ranges are in
+  if (cur_a >= 0) flush_ranges(cur_a);
 }
 
 // Tile shapes of a padded swarm, largest row tile first: (PJ, PB), rows per
@@ -402,7 +454,8 @@ size_t step_smem(const Problem& pr, int sh) {
   int PJ = 0, PB = 0;
   if (!step_shape(pr.Pp, sh, &PJ, &PB)) return 0;
   const int RT = 32 * (8 / PB);
-  return sizeof(float) * ((size_t)2 * RT * kXS + step_pos_floats(pr.Pp, pr.d));
+  return sizeof(float) * ((size_t)step_stages(RT) * RT * kXS + step_pos_floats(pr.Pp, pr.d) +
+                          (size_t)((pr.d + 3) & ~3) + (size_t)8 * 4 * kZS);
 }
 
 template <class F>
