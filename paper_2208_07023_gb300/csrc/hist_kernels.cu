@@ -56,6 +56,15 @@ struct HcScratch {
 // Floats of one d-vector in the kernel's shared memory (16-byte multiples).
 __host__ __device__ inline int hc_dvec(int d) { return (d + 3) & ~3; }
 
+// Words of the histogram region: the copies, or (reused by the BF16 form's
+// top-k selection) P scores and 2 P indices when those need more; a
+// multiple of 4.
+__host__ __device__ inline int hc_words(int B, int K, int P) {
+  const int copies = kHcCopies * B * K;
+  const int topk = (int)((sizeof(EvalRes) + 8) * P / 4);
+  return ((copies > topk ? copies : topk) + 3) & ~3;
+}
+
 // A double's total order as an unsigned key (negative values below 0).
 __device__ __forceinline__ uint64_t hc_key(double x) {
   const uint64_t u = (uint64_t)__double_as_longlong(x);
@@ -96,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const NodeDesc nd = nodes[a];
   const int dv = hc_dvec(d);
   uint32_t* hc = reinterpret_cast<uint32_t*>(smem);           // [kHcCopies][W]
-  float* c1u = reinterpret_cast<float*>(hc + kHcCopies * W);  // [d] c1 r1 of the next move
+  float* c1u = reinterpret_cast<float*>(hc + hc_words(B, K, pr.P));  // [d] c1 r1 of the next move
   float* s2u = c1u + dv;                                      // [d] c2 r2
   float* xrow = s2u + dv;                                     // [d] the particle's x, v, pB
   float* vrow = xrow + dv;
@@ -479,6 +488,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (imp) sw.pb[ci] = res;
     }
     sc.imp = imp;
+  }
+  if (sw.tk_sel) {
+    // the reduced pass of the BF16 form: the last CTA of the node to score
+    // its particle selects the node's top k (the histogram copies are free)
+    __threadfence();  // this CTA's score write before the count
+    __syncthreads();
+    if (threadIdx.x == 0) sc.ok = atomicAdd(&sw.done[a], 1) + 1 == pr.P;
+    __syncthreads();
+    if (sc.ok) {
+      __threadfence();
+      topk_select(pr, sw, a, reinterpret_cast<unsigned char*>(hc));
+      if (threadIdx.x == 0) sw.done[a] = 0;
+    }
   }
   if (!do_update) return;
   __syncthreads();
@@ -962,7 +984,7 @@ const void* hist_cls_fn(const Problem& pr, int np = 1) {
 size_t hist_cls_smem(const Problem& pr, int np = 1) {
   const size_t tail = sizeof(float) * 5 * (size_t)hc_dvec(pr.d);
   if (pr.crit == SLM_MSE) return (size_t)mse_count_words(pr.B, pr.P, np) * 4 + np * tail;
-  return sizeof(uint32_t) * (size_t)kHcCopies * pr.B * pr.K + tail;
+  return sizeof(uint32_t) * (size_t)hc_words(pr.B, pr.K, pr.P) + tail;
 }
 
 }  // namespace

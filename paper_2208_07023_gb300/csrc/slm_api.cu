@@ -520,11 +520,12 @@ struct Bf16Plan {
   uint16_t* posb = nullptr;
   int32_t* sel = nullptr;
   int32_t* inv = nullptr;
-  // regression: both passes on the squared-error histogram kernel (the
-  // reduced pass's last CTA per node selecting the top k), splits S_fast /
-  // S_fast_k
+  // both passes on the histogram kernels of k_hist_cls (squared error or
+  // class counts; the reduced pass's last CTA per node selecting the top
+  // k), splits S_fast / S_fast_k, the c ln c table of entropy scans
   bool fast = false;
   int S_fast = 1, S_fast_k = 1;
+  const double* xtab = nullptr;
 };
 
 // Histogram kernels of a classification search: the nodes of at most
@@ -738,7 +739,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
       }));
     CK(launch(c, SLM_K_HIST_SCAN, pairs, [&] {
       return b.fast && !bins_out
-                 ? launch_hist_cls(pr, sw, dn, A, b.S_fast, t, 0, nullptr, c->stream)
+                 ? launch_hist_cls(pr, sw, dn, A, b.S_fast, t, 0, b.xtab, c->stream)
                  : launch_hist_scan(pr, sw, dn, A, S, bins_out, t, 0, c->stream);
     }));
     if (b.k > 0) {
@@ -750,7 +751,7 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
         }));
       CK(launch(c, SLM_K_HIST_SCAN, b.pairs_k, [&] {
         return b.fast
-                   ? launch_hist_cls(b.pr_k, b.sw_k, dn, A, b.S_fast_k, t, 0, nullptr, c->stream)
+                   ? launch_hist_cls(b.pr_k, b.sw_k, dn, A, b.S_fast_k, t, 0, b.xtab, c->stream)
                    : launch_hist_scan(b.pr_k, b.sw_k, dn, A, b.S_k, nullptr, t, 0, c->stream);
       }));
       CK(launch(c, SLM_K_TOPK, 0.0, [&] {
@@ -1241,14 +1242,14 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
   if (p->proj == SLM_PROJ_BF16_TOPK &&
       (s = setup_bf16(c, pr, nodes, std::min(p->topk, p->n_particles), true, &sw, &bp)))
     return s;
-  if (bp.on && bp.k > 0 && pr.crit == SLM_MSE && c->class_hist && hist_cls_ok(pr) &&
-      hist_cls_ok(bp.pr_k)) {
+  if (bp.on && bp.k > 0 && c->class_hist && hist_cls_ok(pr) && hist_cls_ok(bp.pr_k)) {
     int64_t len = 0;
     for (const NodeDesc& nd : nodes) len = std::max<int64_t>(len, nd.seg_len);
     if (hist_cls_fits(pr, len)) {
       CK(prepare_hist_cls(bp.pr_k));  // the larger swarm's shared memory last
       CK(prepare_hist_cls(pr));
       bp.fast = true;
+      if (pr.crit == SLM_ENTROPY) bp.xtab = xlogx_table(c->device);
       bp.S_fast = hist_cls_split(pr, A, len, c->n_sm);
       bp.S_fast_k = hist_cls_split(bp.pr_k, A, len, c->n_sm);
     }
@@ -1404,7 +1405,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
       kw.put(dn); kw.put(ws_ptr<WorkTile>(c, S_TILES)); kw.put(ws_ptr<WorkTile>(c, S_MTILES));
       kw.put(bp.on); kw.put(bp.k); kw.put(bp.kp); kw.put(bp.n_mtiles); kw.put(bp.grid);
       kw.put(bp.S_k); kw.put(bp.pairs_k); kw.put(bp.posb); kw.put(bp.sel); kw.put(bp.inv);
-      kw.put(bp.fast); kw.put(bp.S_fast); kw.put(bp.S_fast_k);
+      kw.put(bp.fast); kw.put(bp.S_fast); kw.put(bp.S_fast_k); kw.put(bp.xtab);
       kw.put(hp.on); kw.put(hp.large); kw.put(hp.n_large); kw.put(hp.S_large);
       kw.put(hp.pairs_large); kw.put(hp.small); kw.put(hp.n_small); kw.put(hp.pairs_small);
       kw.put(hp.moved); kw.put(hp.n_moved);
