@@ -69,8 +69,8 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 TRAFFIC = {
     "project": (12944384 / 3.2e6, "step_kernels.cu",
                 "d169c12dbdfa6585462cb9b162f2f161141c64e5be5c333e95fcb0a03f8b32b6"),
-    "hist_scan": (13066752 / 3.2e6, "hist_kernels.cu",
-                  "1d003482bab0f586acce410d1c2604f54159dbf817b5986a96886f72c7ad7126"),
+    "hist_scan": (13067008 / 3.2e6, "hist_kernels.cu",
+                  "33590747f2afc8b008f79e8f23ba5e04ff8d532b7ceca158b410075672bf12d2"),
 }
 
 
