@@ -67,10 +67,10 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAK_SOURCE = _measured_peaks()
 # launch over its pairs, profiles/), each valid only for the kernel source it
 # was taken from: (bytes per pair, source file, sha256 of that file).
 TRAFFIC = {
-    "project": (12944384 / 3.2e6, "step_kernels.cu",
-                "d169c12dbdfa6585462cb9b162f2f161141c64e5be5c333e95fcb0a03f8b32b6"),
-    "hist_scan": (13067008 / 3.2e6, "hist_kernels.cu",
-                  "33590747f2afc8b008f79e8f23ba5e04ff8d532b7ceca158b410075672bf12d2"),
+    "project": (12945152 / 3.2e6, "step_kernels.cu",
+                "6f7aa4390ba6326c3a0f7e2e133cae0165c0f104276e7fc53b374ce71d178241"),
+    "hist_scan": (13066496 / 3.2e6, "hist_kernels.cu",
+                  "503a69c3a12c5b8fac4578b88d018a05729810e190770abfa551f1af9538117e"),
 }
 
 

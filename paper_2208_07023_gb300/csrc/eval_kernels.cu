@@ -2080,28 +2080,23 @@ cudaError_t prepare_eval_kernels(const Problem& pr) {
   for (const void* f : {(const void*)k_project<8>, (const void*)k_project<16>,
                         (const void*)k_project<24>, (const void*)k_project<32>,
                         (const void*)k_project<48>})
-    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kProjSmem)))
+    if ((e = allow_smem((const void*)f, (int)kProjSmem)))
       return e;
   for (const void* f : {(const void*)k_project_tma<8>, (const void*)k_project_tma<16>,
                         (const void*)k_project_tma<24>, (const void*)k_project_tma<32>,
                         (const void*)k_project_tma<48>})
-    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kProjTmaSmem)))
+    if ((e = allow_smem((const void*)f, (int)kProjTmaSmem)))
       return e;
   for (const void* f : {(const void*)k_node_search<SLM_GINI>,
                         (const void*)k_node_search<SLM_ENTROPY>})
-    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kNodeSearchMaxSmem)))
+    if ((e = allow_smem((const void*)f, (int)kNodeSearchMaxSmem)))
       return e;
   for (const void* f : {(const void*)k_hist_warp<SLM_GINI>, (const void*)k_hist_warp<SLM_ENTROPY>})
-    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kHistWarpMaxSmem)))
+    if ((e = allow_smem((const void*)f, (int)kHistWarpMaxSmem)))
       return e;
-  if ((e = cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)hist_smem_bytes(pr))))
+  if ((e = allow_smem((const void*)k_hist_scan, (int)hist_smem_bytes(pr))))
     return e;
-  return cudaFuncSetAttribute(k_hist_scan, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return allow_cluster((const void*)k_hist_scan);
 }
 
 cudaError_t launch_swarm_init(const Problem& pr, const Swarm& sw,
@@ -2270,8 +2265,8 @@ int hist_split(const Problem& pr, int A, int64_t max_len, int n_sm, int max_clus
   // clusters of S CTAs per (node, particle): as many as keep the whole grid
   // resident in one wave, with slices of at least one staged piece
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist_scan, kThreads,
-                                                    hist_smem_bytes(pr)) != cudaSuccess) {
+  if (occupancy(&per_sm, (const void*)k_hist_scan, kThreads, hist_smem_bytes(pr)) !=
+      cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -2391,8 +2386,7 @@ cudaError_t launch_apso(const Problem& pr, const Swarm& sw, const NodeDesc* node
   const int R = apso_rows(pr.P, pr.d);
   if (R == 0) return cudaErrorInvalidValue;
   const size_t smem = apso_smem(pr.P, pr.d, R);
-  cudaError_t e = cudaFuncSetAttribute(k_apso, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_smem((const void*)k_apso, (int)smem);
   if (e) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)n_nodes, 1, 1);

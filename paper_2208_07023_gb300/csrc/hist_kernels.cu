@@ -1004,9 +1004,8 @@ bool hist_cls_fits(const Problem& pr, int64_t max_len) {
 cudaError_t prepare_hist_cls(const Problem& pr) {
   for (int np = 1; np <= (pr.crit == SLM_MSE ? 2 : 1); ++np) {
     const void* f = hist_cls_fn(pr, np);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)hist_cls_smem(pr, np));
-    if (!e) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = allow_smem((const void*)f, (int)hist_cls_smem(pr, np));
+    if (!e) e = allow_cluster((const void*)f);
     if (e) return e;
   }
   return cudaSuccess;
@@ -1015,8 +1014,7 @@ cudaError_t prepare_hist_cls(const Problem& pr) {
 int hist_cls_split(const Problem& pr, int A, int64_t max_len, int n_sm) {
   const int np = pr.crit == SLM_MSE ? mse_np(pr, A) : 1;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_cls_fn(pr, np), kThreads,
-                                                    hist_cls_smem(pr, np)) != cudaSuccess) {
+  if (occupancy(&per_sm, hist_cls_fn(pr, np), kThreads, hist_cls_smem(pr, np)) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }

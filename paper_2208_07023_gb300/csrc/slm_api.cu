@@ -59,6 +59,10 @@ enum Slot {
   // probabilistic search: every candidate's vector and score, the rank
   // tables, the best so far, the pruning's state
   S_PRALL, S_PRSC, S_PRTAB, S_PRBEST, S_PRUNE,
+  // a level's growth (slm_grow_level): node list, statistics, split flags,
+  // per-tile accumulators, the partition's lists (reused by every forest)
+  S_GLVLNODES, S_GLVLSPLIT, S_GLVLCLS, S_GLVLPAR, S_GSMAP, S_GOUT3, S_GDST, S_GLTILES, S_GLTILE0,
+  S_GACCW, S_GACCY, S_GTILESUM, S_GSTILE0, S_GTILELEFT, S_GTILEBASE, S_GPLK, S_GPWL,
   N_SLOTS
 };
 
@@ -186,8 +190,6 @@ struct slm_forest {
   int depth = 0;
   bool done = false;
   int64_t evaluations = 0;
-  DevBuf lvl_nodes, lvl_split, lvl_cls, lvl_par, smap, out3, dst;
-  DevBuf ltiles, ltile0, acc_w, acc_y, tile_s, stile0, tile_left, tile_base, p_lk, p_wl;
 };
 
 namespace {
@@ -1246,7 +1248,7 @@ slm_status run_search(slm_ctx* c, const slm_params* p, Problem& pr_in,
     int64_t len = 0;
     for (const NodeDesc& nd : nodes) len = std::max<int64_t>(len, nd.seg_len);
     if (hist_cls_fits(pr, len)) {
-      CK(prepare_hist_cls(bp.pr_k));  // the larger swarm's shared memory last
+      CK(prepare_hist_cls(bp.pr_k));  // (shared-memory limits are only raised)
       CK(prepare_hist_cls(pr));
       bp.fast = true;
       if (pr.crit == SLM_ENTROPY) bp.xtab = xlogx_table(c->device);
@@ -2078,11 +2080,7 @@ static slm_status forest_alloc_trees(slm_ctx* c, slm_forest* f) {
 void slm_forest_free(slm_forest* f) {
   if (!f) return;
   cudaSetDevice(f->device);
-  DevBuf* bufs[] = {&f->own_X,     &f->tree_mem, &f->side,      &f->lvl_nodes, &f->lvl_split,
-                    &f->lvl_cls,   &f->lvl_par,  &f->smap,      &f->out3,      &f->dst,
-                    &f->ltiles,    &f->ltile0,   &f->acc_w,     &f->acc_y,     &f->tile_s,
-                    &f->stile0,    &f->tile_left, &f->tile_base, &f->p_lk,     &f->p_wl,
-                    &f->lXb};
+  DevBuf* bufs[] = {&f->own_X, &f->tree_mem, &f->side, &f->lXb};
   for (DevBuf* b : bufs) release(*b);
   for (int i = 0; i < 2; ++i) {
     release(f->lX[i]);
@@ -2296,46 +2294,46 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   }
   ltile0[L] = (int32_t)ltiles.size();
   const int n_lt = (int)ltiles.size();
-  CK(ensure(f->lvl_nodes, sizeof(LevelNode) * L));
-  CK(ensure(f->lvl_split, sizeof(int32_t) * L));
-  CK(ensure(f->lvl_cls, sizeof(unsigned long long) * (size_t)L * K));
-  CK(ensure(f->lvl_par, sizeof(double) * 2 * (size_t)L));
-  CK(ensure(f->ltiles, sizeof(WorkTile) * n_lt));
-  CK(ensure(f->ltile0, sizeof(int32_t) * (L + 1)));
-  CK(ensure(f->acc_w, sizeof(unsigned long long) * L));
-  CK(ensure(f->acc_y, sizeof(int32_t) * 2 * L));
-  CK(ensure(f->tile_s, sizeof(double) * 2 * (size_t)n_lt));
-  CK(cudaMemcpyAsync(f->lvl_nodes.p, f->level.data(), sizeof(LevelNode) * L,
+  CK(ensure(c->ws[S_GLVLNODES], sizeof(LevelNode) * L));
+  CK(ensure(c->ws[S_GLVLSPLIT], sizeof(int32_t) * L));
+  CK(ensure(c->ws[S_GLVLCLS], sizeof(unsigned long long) * (size_t)L * K));
+  CK(ensure(c->ws[S_GLVLPAR], sizeof(double) * 2 * (size_t)L));
+  CK(ensure(c->ws[S_GLTILES], sizeof(WorkTile) * n_lt));
+  CK(ensure(c->ws[S_GLTILE0], sizeof(int32_t) * (L + 1)));
+  CK(ensure(c->ws[S_GACCW], sizeof(unsigned long long) * L));
+  CK(ensure(c->ws[S_GACCY], sizeof(int32_t) * 2 * L));
+  CK(ensure(c->ws[S_GTILESUM], sizeof(double) * 2 * (size_t)n_lt));
+  CK(cudaMemcpyAsync(c->ws[S_GLVLNODES].p, f->level.data(), sizeof(LevelNode) * L,
                      cudaMemcpyHostToDevice, c->stream));
   if (n_lt)
-    CK(cudaMemcpyAsync(f->ltiles.p, ltiles.data(), sizeof(WorkTile) * n_lt,
+    CK(cudaMemcpyAsync(c->ws[S_GLTILES].p, ltiles.data(), sizeof(WorkTile) * n_lt,
                        cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(f->ltile0.p, ltile0.data(), sizeof(int32_t) * (L + 1),
+  CK(cudaMemcpyAsync(c->ws[S_GLTILE0].p, ltile0.data(), sizeof(int32_t) * (L + 1),
                      cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemsetAsync(f->lvl_cls.p, 0, sizeof(unsigned long long) * (size_t)L * K, c->stream));
-  CK(cudaMemsetAsync(f->acc_w.p, 0, sizeof(unsigned long long) * L, c->stream));
+  CK(cudaMemsetAsync(c->ws[S_GLVLCLS].p, 0, sizeof(unsigned long long) * (size_t)L * K, c->stream));
+  CK(cudaMemsetAsync(c->ws[S_GACCW].p, 0, sizeof(unsigned long long) * L, c->stream));
   {
     std::vector<int32_t> yinit(2 * (size_t)L);
     for (int l = 0; l < L; ++l) {
       yinit[l] = INT32_MAX;
       yinit[L + l] = INT32_MIN;
     }
-    CK(cudaMemcpyAsync(f->acc_y.p, yinit.data(), sizeof(int32_t) * 2 * L,
+    CK(cudaMemcpyAsync(c->ws[S_GACCY].p, yinit.data(), sizeof(int32_t) * 2 * L,
                        cudaMemcpyHostToDevice, c->stream));
   }
-  LevelAcc lacc{static_cast<unsigned long long*>(f->lvl_cls.p),
-                static_cast<unsigned long long*>(f->acc_w.p), static_cast<int32_t*>(f->acc_y.p),
-                static_cast<int32_t*>(f->acc_y.p) + L, static_cast<double*>(f->tile_s.p)};
+  LevelAcc lacc{static_cast<unsigned long long*>(c->ws[S_GLVLCLS].p),
+                static_cast<unsigned long long*>(c->ws[S_GACCW].p), static_cast<int32_t*>(c->ws[S_GACCY].p),
+                static_cast<int32_t*>(c->ws[S_GACCY].p) + L, static_cast<double*>(c->ws[S_GTILESUM].p)};
   CK(launch(c, SLM_K_NODE_STATS, 0.0, [&] {
-    return launch_node_stats(pr, static_cast<LevelNode*>(f->lvl_nodes.p), L,
-                             static_cast<WorkTile*>(f->ltiles.p), n_lt,
-                             static_cast<int32_t*>(f->ltile0.p), lacc, f->tr, p->max_depth,
-                             static_cast<double*>(f->lvl_par.p),
-                             static_cast<int32_t*>(f->lvl_split.p), c->stream);
+    return launch_node_stats(pr, static_cast<LevelNode*>(c->ws[S_GLVLNODES].p), L,
+                             static_cast<WorkTile*>(c->ws[S_GLTILES].p), n_lt,
+                             static_cast<int32_t*>(c->ws[S_GLTILE0].p), lacc, f->tr, p->max_depth,
+                             static_cast<double*>(c->ws[S_GLVLPAR].p),
+                             static_cast<int32_t*>(c->ws[S_GLVLSPLIT].p), c->stream);
   }));
   c->launches += 1;  // the per-node finishing kernel
   std::vector<int32_t> splittable(L);
-  CK(cudaMemcpyAsync(splittable.data(), f->lvl_split.p, sizeof(int32_t) * L,
+  CK(cudaMemcpyAsync(splittable.data(), c->ws[S_GLVLSPLIT].p, sizeof(int32_t) * L,
                      cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
 
@@ -2379,20 +2377,20 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     f->evaluations += (int64_t)nd.seg_len * p->n_particles * (p->n_iters + 1);
 
   // 3. partition on gB (per tile), zero-gain test and tree fields (per node)
-  CK(ensure(f->smap, sizeof(int32_t) * A));
-  CK(ensure(f->out3, sizeof(int32_t) * 3 * A));
-  CK(ensure(f->dst, sizeof(int32_t) * 2 * A));
-  CK(ensure(f->stile0, sizeof(int32_t) * (A + 1)));
-  CK(ensure(f->tile_left, sizeof(int32_t) * (size_t)n_st));
-  CK(ensure(f->tile_base, sizeof(int32_t) * (size_t)n_st));
-  CK(ensure(f->p_lk, sizeof(unsigned long long) * (size_t)A * K));
-  CK(ensure(f->p_wl, sizeof(unsigned long long) * A));
-  CK(cudaMemcpyAsync(f->smap.p, smap.data(), sizeof(int32_t) * A, cudaMemcpyHostToDevice,
+  CK(ensure(c->ws[S_GSMAP], sizeof(int32_t) * A));
+  CK(ensure(c->ws[S_GOUT3], sizeof(int32_t) * 3 * A));
+  CK(ensure(c->ws[S_GDST], sizeof(int32_t) * 2 * A));
+  CK(ensure(c->ws[S_GSTILE0], sizeof(int32_t) * (A + 1)));
+  CK(ensure(c->ws[S_GTILELEFT], sizeof(int32_t) * (size_t)n_st));
+  CK(ensure(c->ws[S_GTILEBASE], sizeof(int32_t) * (size_t)n_st));
+  CK(ensure(c->ws[S_GPLK], sizeof(unsigned long long) * (size_t)A * K));
+  CK(ensure(c->ws[S_GPWL], sizeof(unsigned long long) * A));
+  CK(cudaMemcpyAsync(c->ws[S_GSMAP].p, smap.data(), sizeof(int32_t) * A, cudaMemcpyHostToDevice,
                      c->stream));
-  CK(cudaMemcpyAsync(f->stile0.p, stile0.data(), sizeof(int32_t) * (A + 1),
+  CK(cudaMemcpyAsync(c->ws[S_GSTILE0].p, stile0.data(), sizeof(int32_t) * (A + 1),
                      cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemsetAsync(f->p_lk.p, 0, sizeof(unsigned long long) * (size_t)A * K, c->stream));
-  CK(cudaMemsetAsync(f->p_wl.p, 0, sizeof(unsigned long long) * A, c->stream));
+  CK(cudaMemsetAsync(c->ws[S_GPLK].p, 0, sizeof(unsigned long long) * (size_t)A * K, c->stream));
+  CK(cudaMemsetAsync(c->ws[S_GPWL].p, 0, sizeof(unsigned long long) * A, c->stream));
   if (slm_status s = reset_status(c)) return s;
   const NodeDesc* dsn = ws_ptr<NodeDesc>(c, S_NODES);
   // every searched node's tiles (the search uploads only the tiles of the
@@ -2403,24 +2401,24 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
     CK(cudaMemcpyAsync(c->ws[S_TILES].p, ptiles.data(), sizeof(WorkTile) * ptiles.size(),
                        cudaMemcpyHostToDevice, c->stream));
   const WorkTile* dst_tiles = ws_ptr<WorkTile>(c, S_TILES);
-  PartAcc pacc{static_cast<unsigned long long*>(f->p_lk.p),
-               static_cast<unsigned long long*>(f->p_wl.p)};
+  PartAcc pacc{static_cast<unsigned long long*>(c->ws[S_GPLK].p),
+               static_cast<unsigned long long*>(c->ws[S_GPWL].p)};
   CK(launch(c, SLM_K_PARTITION, 0.0, [&] {
     return launch_partition(pr, sw, dst_tiles, n_st, static_cast<uint8_t*>(f->side.p),
-                            static_cast<int32_t*>(f->tile_left.p), pacc, c->stream);
+                            static_cast<int32_t*>(c->ws[S_GTILELEFT].p), pacc, c->stream);
   }));
   CK(launch(c, SLM_K_PARTITION, 0.0, [&] {
-    return launch_decide(pr, sw, dsn, static_cast<int32_t*>(f->smap.p),
-                         static_cast<int32_t*>(f->stile0.p), A,
-                         static_cast<int32_t*>(f->tile_left.p),
-                         static_cast<int32_t*>(f->tile_base.p),
-                         static_cast<unsigned long long*>(f->lvl_cls.p),
-                         static_cast<double*>(f->lvl_par.p), pacc, f->tr,
-                         static_cast<int32_t*>(f->out3.p), ws_ptr<int32_t>(c, S_STATUS),
+    return launch_decide(pr, sw, dsn, static_cast<int32_t*>(c->ws[S_GSMAP].p),
+                         static_cast<int32_t*>(c->ws[S_GSTILE0].p), A,
+                         static_cast<int32_t*>(c->ws[S_GTILELEFT].p),
+                         static_cast<int32_t*>(c->ws[S_GTILEBASE].p),
+                         static_cast<unsigned long long*>(c->ws[S_GLVLCLS].p),
+                         static_cast<double*>(c->ws[S_GLVLPAR].p), pacc, f->tr,
+                         static_cast<int32_t*>(c->ws[S_GOUT3].p), ws_ptr<int32_t>(c, S_STATUS),
                          c->stream);
   }));
   std::vector<int32_t> o3(3 * (size_t)A);
-  CK(cudaMemcpyAsync(o3.data(), f->out3.p, sizeof(int32_t) * 3 * A, cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(o3.data(), c->ws[S_GOUT3].p, sizeof(int32_t) * 3 * A, cudaMemcpyDeviceToHost,
                      c->stream));
   int32_t st = 0;
   if (slm_status s = read_status(c, &st)) return s;
@@ -2451,13 +2449,13 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
                    mse ? static_cast<float*>(f->ly[nx].p) : nullptr,
                    f->weighted ? static_cast<uint32_t*>(f->lw[nx].p) : nullptr,
                    static_cast<int32_t*>(f->lidx[nx].p)};
-    CK(cudaMemcpyAsync(f->dst.p, dst.data(), sizeof(int32_t) * 2 * A, cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(c->ws[S_GDST].p, dst.data(), sizeof(int32_t) * 2 * A, cudaMemcpyHostToDevice,
                        c->stream));
     CK(launch(c, SLM_K_COMPACT, 0.0, [&] {
       return launch_scatter(pr, dst_tiles, n_st, static_cast<uint8_t*>(f->side.p),
-                            static_cast<int32_t*>(f->dst.p),
-                            static_cast<int32_t*>(f->tile_base.p),
-                            static_cast<int32_t*>(f->stile0.p),
+                            static_cast<int32_t*>(c->ws[S_GDST].p),
+                            static_cast<int32_t*>(c->ws[S_GTILEBASE].p),
+                            static_cast<int32_t*>(c->ws[S_GSTILE0].p),
                             static_cast<int32_t*>(f->lidx[cu].p), la, c->stream);
     }));
     f->cur = nx;
@@ -2577,10 +2575,7 @@ namespace {
 
 // A finished tree keeps only its arrays: the level state of its growth goes.
 void release_level_state(slm_forest* f) {
-  DevBuf* bufs[] = {&f->own_X,     &f->side,     &f->lvl_nodes, &f->lvl_split, &f->lvl_cls,
-                    &f->lvl_par,   &f->smap,     &f->out3,      &f->dst,       &f->ltiles,
-                    &f->ltile0,    &f->acc_w,    &f->acc_y,     &f->tile_s,    &f->stile0,
-                    &f->tile_left, &f->tile_base, &f->p_lk,     &f->p_wl,      &f->lXb};
+  DevBuf* bufs[] = {&f->own_X, &f->side, &f->lXb};
   for (DevBuf* b : bufs) release(*b);
   for (int i = 0; i < 2; ++i) {
     release(f->lX[i]);

@@ -6,6 +6,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "slm.h"
 
 namespace slm {
@@ -534,5 +538,83 @@ cudaError_t launch_seed_positions(uint64_t seed, uint32_t uid, int P, int d,
 // Initial swarms of A nodes seeded from the network outputs prop[A, OUT].
 cudaError_t launch_swarm_seed_init(const Problem& pr, const Swarm& sw, const NodeDesc* nodes,
                                    int A, SwarmCoef co, const float* prop, cudaStream_t st);
+
+// ---- kernel attributes and occupancy, remembered per device --------------
+// Searches plan their launches again at every level; the runtime calls that
+// set a kernel's dynamic shared-memory limit or query its occupancy cost
+// microseconds each, so their results are kept: a limit is raised only when
+// a larger one is needed, an occupancy is queried once per (kernel, block,
+// shared memory) that gives a nonzero answer.
+
+struct KernelAttrCache {
+  std::mutex mu;
+  std::map<std::pair<int, const void*>, int> smem;      // largest limit set
+  std::map<std::pair<int, const void*>, bool> cluster;  // non-portable sizes allowed
+  std::map<std::tuple<int, const void*, int, size_t>, int> occ;
+};
+
+inline KernelAttrCache& kernel_attr_cache() {
+  static KernelAttrCache c;
+  return c;
+}
+
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) unless this
+// device already allows fn at least bytes.
+inline cudaError_t allow_smem(const void* fn, int bytes) {
+  int dev = 0;
+  if (cudaError_t e = cudaGetDevice(&dev)) return e;
+  KernelAttrCache& c = kernel_attr_cache();
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    const auto it = c.smem.find({dev, fn});
+    if (it != c.smem.end() && it->second >= bytes) return cudaSuccess;
+  }
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> g(c.mu);
+    int& v = c.smem[{dev, fn}];
+    if (bytes > v) v = bytes;
+  }
+  return e;
+}
+
+// cudaFuncSetAttribute(fn, NonPortableClusterSizeAllowed, 1), once per device.
+inline cudaError_t allow_cluster(const void* fn) {
+  int dev = 0;
+  if (cudaError_t e = cudaGetDevice(&dev)) return e;
+  KernelAttrCache& c = kernel_attr_cache();
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    if (c.cluster.count({dev, fn})) return cudaSuccess;
+  }
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> g(c.mu);
+    c.cluster[{dev, fn}] = true;
+  }
+  return e;
+}
+
+// cudaOccupancyMaxActiveBlocksPerMultiprocessor, remembered per device.
+inline cudaError_t occupancy(int* per_sm, const void* fn, int threads, size_t smem) {
+  int dev = 0;
+  if (cudaError_t e = cudaGetDevice(&dev)) return e;
+  KernelAttrCache& c = kernel_attr_cache();
+  const auto key = std::make_tuple(dev, fn, threads, smem);
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    const auto it = c.occ.find(key);
+    if (it != c.occ.end()) {
+      *per_sm = it->second;
+      return cudaSuccess;
+    }
+  }
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, smem);
+  if (e == cudaSuccess && *per_sm > 0) {  // (zero: perhaps a limit not yet raised)
+    std::lock_guard<std::mutex> g(c.mu);
+    c.occ[key] = *per_sm;
+  }
+  return e;
+}
 
 }  // namespace slm

@@ -496,16 +496,14 @@ int step_slices(const Problem& pr, int sh) {
 
 cudaError_t prepare_step_kernels(const Problem& pr, int sh) {
   return step_dispatch(pr.Pp, sh, [&](auto fn) {
-    return cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem(pr, sh));
+    return allow_smem((const void*)fn, (int)step_smem(pr, sh));
   });
 }
 
 int step_grid(const Problem& pr, int sh, int n_sm) {
   int per_sm = 0;
   const cudaError_t e = step_dispatch(pr.Pp, sh, [&](auto fn) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads,
-                                                         step_smem(pr, sh));
+    return occupancy(&per_sm, (const void*)fn, kThreads, step_smem(pr, sh));
   });
   if (e != cudaSuccess) {
     cudaGetLastError();
