@@ -520,7 +520,8 @@ class BoostRun:
         self.b = boost
 
     def info(self):
-        m = self.b.info()["n_rounds"]
+        inf = self.b.info()
+        m = inf["n_rounds"] * inf["n_outputs"]  # every tree of every round
         return {"evaluations": sum(self.b.tree(i).info()["evaluations"] for i in range(m))}
 
     def free(self):

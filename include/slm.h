@@ -357,9 +357,11 @@ slm_status slm_predict(slm_ctx* ctx, const slm_forest* forest, const float* X,
  *   F_i = F_i + learning_rate * (float)v_i, v_i the tree's leaf value of x_i.
  * Classification (labels, K = params->n_classes classes): F_ik = 0; round m:
  *   in double p_ik = exp(F_ik - max_j F_ij) / sum_j (ascending) of the same,
- *   r_ik = (float)([labels_i == k] - p_ik) (all k from the same F); for
- *   k = 0..K-1 one SLR tree on (X, r_.k) with the key params->seed +
- *   (m-1) K + k + 1, and F_ik = F_ik + learning_rate * (float)v_ik.
+ *   r_ik = (float)([labels_i == k] - p_ik) (all k from the same F); the
+ *   K trees of the round, tree k on (X, r_.k), grown together as one forest
+ *   (every level of all K searched in one batch) with the key params->seed
+ *   + m and tree ids 0..K-1 (node uids (k << 16) | h); then for k =
+ *   0..K-1 F_ik = F_ik + learning_rate * (float)v_ik.
  * Each float operation is rounded once. */
 typedef struct slm_boost slm_boost;
 

@@ -1568,10 +1568,12 @@ int ora_train_boost_cls(const ora_params* p, const float* X, int64_t n, int32_t 
   for (int32_t m = 1; m <= M; ++m) {
     /* residuals of the softmax, all classes from the same F */
     ora_softmax_residuals(F, labels, n, K, R);
+    /* the round's key is seed + m; class k's tree has tree id k (node uids
+       (k << 16) | h), so the K trees of a round draw distinct streams */
+    q.seed = p->seed + (uint64_t)m;
     for (int32_t k = 0; k < K; ++k) {
       ora_tree* t = &trees[(int64_t)(m - 1) * K + k];
-      q.seed = p->seed + (uint64_t)((m - 1) * K + k + 1);
-      rc = ora_train_tree(&q, X, n, d, NULL, R + (int64_t)k * n, 0, 0, t);
+      rc = ora_train_tree(&q, X, n, d, NULL, R + (int64_t)k * n, (uint32_t)k, 0, t);
       if (rc) goto done;
       rc = ora_predict(&q, t, X, n, d, NULL, v, NULL);
       if (rc) goto done;

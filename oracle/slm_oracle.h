@@ -382,8 +382,9 @@ int ora_boost_predict(const ora_params* p, const ora_tree* trees, int32_t M, flo
  * F_ij) / (sum over j ascending of exp(F_ij - max_j F_ij)), and r_ik =
  * (float)([labels_i == k] - p_ik); then for k = 0..K-1 tree (m-1)*K + k is
  * grown by ora_train_tree (criterion ORA_MSE) on (X, r_.k) with the Philox
- * key seed + (m-1)*K + k + 1 (tree id 0, no bootstrap), and F_ik = F_ik + eta
- * * (float)v_ik (float). loss_out[m-1] (may be NULL): mean over i of
+ * key seed + m and tree id k (node uids (k << 16) | h; no bootstrap: the K
+ * trees of a round are a forest of K trees on K targets), and F_ik = F_ik +
+ * eta * (float)v_ik (float). loss_out[m-1] (may be NULL): mean over i of
  * -log p_{i,labels_i} after round m, in double (log-sum-exp form).
  * trees[M*K] caller-allocated; p's criterion is ignored (trees use MSE). */
 void ora_softmax_residuals(const float* F, const int32_t* labels, int64_t n, int32_t K,

@@ -190,6 +190,7 @@ struct slm_forest {
   int depth = 0;
   bool done = false;
   int64_t evaluations = 0;
+  std::vector<int64_t> tree_evals;  // evaluations per tree
 };
 
 namespace {
@@ -2092,9 +2093,26 @@ void slm_forest_free(slm_forest* f) {
   delete f;
 }
 
+namespace {
+// A forest's start (slm_forest_begin). y_per_tree: y holds n_trees target
+// vectors of n samples, tree t fitting y[t n .. t n + n) (boosting's class
+// trees of one round; no bootstrap); tree t takes the global id id0 + t stride.
+slm_status forest_begin_impl(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                             int32_t d, const int32_t* labels, const float* y, bool y_per_tree,
+                             int64_t id0, int64_t stride, slm_forest** out);
+}  // namespace
+
 slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
                             int64_t n, int32_t d, const int32_t* labels,
                             const float* y, slm_forest** out) {
+  if (!c) return SLM_EINVAL;
+  return forest_begin_impl(c, p, X, n, d, labels, y, false, c->tree_id0, c->tree_stride, out);
+}
+
+namespace {
+slm_status forest_begin_impl(slm_ctx* c, const slm_params* p, const float* X, int64_t n,
+                             int32_t d, const int32_t* labels, const float* y, bool y_per_tree,
+                             int64_t id0, int64_t stride, slm_forest** out) {
   if (!c || !out) return fail(c, SLM_EINVAL, "NULL context or output");
   *out = nullptr;
   if (slm_status s = check_params(c, p, d, true)) return s;
@@ -2106,8 +2124,10 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
     return fail(c, SLM_EINVAL, "max_depth must be in [0, 15]");
   if (p->n_trees < 1 || p->n_trees > 65535)
     return fail(c, SLM_EINVAL, "n_trees must be in [1, 65535]");
-  if (c->tree_id0 + (int64_t)(p->n_trees - 1) * c->tree_stride > 65535)
+  if (id0 + (int64_t)(p->n_trees - 1) * stride > 65535)
     return fail(c, SLM_EINVAL, "global tree ids (slm_set_tree_ids) pass 65535");
+  if (y_per_tree && (!y || p->bootstrap))
+    return fail(c, SLM_EINVAL, "per-tree targets need y and no bootstrap");
   if (p->criterion == SLM_GINI && n >= (int64_t(1) << 22))
     return fail(c, SLM_EUNSUPPORTED, "Gini needs fewer than 2^22 samples per tree");
   if ((int64_t)n * p->n_trees > INT32_MAX)
@@ -2118,12 +2138,13 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   f->ctx = c;
   f->device = c->device;
   f->params = *p;
-  f->tree_id0 = c->tree_id0;
-  f->tree_stride = c->tree_stride;
+  f->tree_id0 = id0;
+  f->tree_stride = stride;
   f->n = n;
   f->d = d;
   f->H = (1 << (p->max_depth + 1)) - 1;
   f->n_trees = p->n_trees;
+  f->tree_evals.assign((size_t)p->n_trees, 0);
   f->K = p->criterion == SLM_MSE ? 1 : p->n_classes;
   const bool bf16 = p->proj == SLM_PROJ_BF16_TOPK;
   f->align = bf16 ? kMmaRows : 4;
@@ -2136,7 +2157,8 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   const int32_t* dlab;
   if ((s = stage_in(c, X, (size_t)n * d, c->ws[W_X], &dX))) return bail(s);
   if ((s = stage_in(c, labels, (size_t)n, c->ws[W_LAB], &dlab))) return bail(s);
-  if ((s = stage_in(c, y, (size_t)n, c->ws[W_Y], &dy))) return bail(s);
+  if ((s = stage_in(c, y, (size_t)n * (y_per_tree ? p->n_trees : 1), c->ws[W_Y], &dy)))
+    return bail(s);
   if ((s = validate_inputs(c, dlab, n, p->n_classes, nullptr, 0))) return bail(s);
   if ((s = forest_alloc_trees(c, f))) return bail(s);
   int l2 = 0;
@@ -2250,13 +2272,21 @@ slm_status slm_forest_begin(slm_ctx* c, const slm_params* p, const float* X,
   if ((e = launch_gather(dX, dlab, dy, static_cast<int32_t*>(f->lidx[0].p), ecap, d,
                          static_cast<float*>(f->lX[0].p),
                          dlab ? static_cast<int32_t*>(f->lab[0].p) : nullptr,
-                         dy ? static_cast<float*>(f->ly[0].p) : nullptr, c->stream)) ||
-      (e = cudaStreamSynchronize(c->stream)))
+                         dy ? static_cast<float*>(f->ly[0].p) : nullptr, c->stream)))
     return bail(cuda_fail(c, e, "root gather"));
+  // per-tree targets: tree t's entries (samples 0 .. n - 1 in order, from
+  // entry t n4) take its own vector
+  const int64_t n4 = round_up(n, f->align);
+  for (int t = 1; y_per_tree && t < f->n_trees; ++t)
+    if ((e = cudaMemcpyAsync(static_cast<float*>(f->ly[0].p) + t * n4, dy + (int64_t)t * n,
+                             sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream)))
+      return bail(cuda_fail(c, e, "per-tree targets"));
+  if ((e = cudaStreamSynchronize(c->stream))) return bail(cuda_fail(c, e, "root gather"));
   f->cur = 0;
   *out = f;
   return SLM_OK;
 }
+}  // namespace
 
 slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   if (!c || !f) return fail(c, SLM_EINVAL, "NULL context or forest");
@@ -2373,8 +2403,11 @@ slm_status slm_grow_level(slm_ctx* c, slm_forest* f, int32_t* n_split_out) {
   Swarm sw;
   if (slm_status s = run_search(c, p, pr, snodes, false, &sw)) return s;
   if (slm_status s = check_kernel_errors(c)) return s;
-  for (const NodeDesc& nd : snodes)
-    f->evaluations += (int64_t)nd.seg_len * p->n_particles * (p->n_iters + 1);
+  for (const NodeDesc& nd : snodes) {
+    const int64_t ev = (int64_t)nd.seg_len * p->n_particles * (p->n_iters + 1);
+    f->evaluations += ev;
+    f->tree_evals[(size_t)(nd.slot / f->H)] += ev;
+  }
 
   // 3. partition on gB (per tile), zero-gain test and tree fields (per node)
   CK(ensure(c->ws[S_GSMAP], sizeof(int32_t) * A));
@@ -2567,6 +2600,9 @@ struct slm_boost {
   float base = 0.0f;
   float eta = 0.0f;
   std::vector<slm_forest*> trees;  // round-major: tree (m, k) at m * K + k
+  // classification: each round's K trees grown as one forest, which owns
+  // their arrays; `trees` then holds views of its trees
+  std::vector<slm_forest*> rounds;
 };
 
 }  // extern "C"
@@ -2586,6 +2622,33 @@ void release_level_state(slm_forest* f) {
   }
   f->X = nullptr;
   f->level.clear();
+}
+
+// Tree t of a finished forest as a one-tree forest that owns nothing: its
+// arrays stay the forest's (which must outlive the view).
+slm_forest* tree_view(const slm_forest* f, int t) {
+  slm_forest* v = new (std::nothrow) slm_forest();
+  if (!v) return nullptr;
+  v->ctx = f->ctx;
+  v->device = f->device;
+  v->params = f->params;
+  v->params.n_trees = 1;
+  v->n = f->n;
+  v->d = f->d;
+  v->H = f->H;
+  v->n_trees = 1;
+  v->K = f->K;
+  v->align = f->align;
+  v->tree_id0 = f->tree_id(t);
+  const size_t o = (size_t)t * f->H;
+  v->tr = TreeArrays{f->tr.kind + o,       f->tr.dir + o * f->d,  f->tr.zmin + o,
+                     f->tr.inv_w + o,      f->tr.bin + o,         f->tr.leaf_class + o,
+                     f->tr.leaf_value + o, f->tr.weight + o,      f->tr.loss + o,
+                     f->tr.n_left + o,     f->tr.n_right + o};
+  v->done = true;
+  v->evaluations = f->tree_evals[(size_t)t];
+  v->tree_evals.assign(1, v->evaluations);
+  return v;
 }
 
 // Device buffers of one boosting call, released on every exit.
@@ -2672,14 +2735,34 @@ slm_status slm_train_boost(slm_ctx* c, const slm_params* p, const float* X, int6
     else
       CK(launch(c, SLM_K_OTHER, 0.0,
                 [&] { return launch_softmax_residual(F, dl, n, K, r, c->stream); }));
+    // the round's trees: one tree on y (regression), or the K class trees
+    // grown together as one forest (tree k fits class k's residuals, global
+    // tree id k, the round's key seed + m), every level of all K searched in
+    // one batch
+    slm_forest* round = nullptr;
+    if (K > 1) {
+      slm_params q = b->params;
+      q.seed = p->seed + (uint64_t)m;
+      q.n_trees = K;
+      if (slm_status s = forest_begin_impl(c, &q, dX, n, d, nullptr, r, true, 0, 1, &round))
+        return s;
+      b->rounds.push_back(round);
+      for (int level = 0; level <= q.max_depth + 1 && !round->done; ++level)
+        if (slm_status s = slm_grow_level(c, round, nullptr)) return s;
+      release_level_state(round);
+    }
     for (int k = 0; k < K; ++k) {
       slm_params q = b->params;
-      q.seed = p->seed + (uint64_t)((m - 1) * K + k + 1);
+      q.seed = p->seed + (uint64_t)m;
       slm_forest* f = nullptr;
-      if (slm_status s = slm_train_tree(c, &q, dX, n, d, nullptr, r + (int64_t)k * n, &f))
+      if (round) {
+        f = tree_view(round, k);
+        if (!f) return fail(c, SLM_ENOMEM, "host allocation failed");
+      } else if (slm_status s = slm_train_tree(c, &q, dX, n, d, nullptr, r, &f)) {
         return s;
+      }
       b->trees.push_back(f);
-      release_level_state(f);
+      if (!round) release_level_state(f);
       CK(launch(c, SLM_K_OTHER, 0.0, [&] {
         return launch_predict(dX, n, d, f->tr, 1, f->H, q.n_bins, 1, SLM_MSE, nullptr, v,
                               nullptr, c->stream);
@@ -2767,7 +2850,8 @@ const slm_forest* slm_boost_tree(const slm_boost* b, int32_t m) {
 
 void slm_boost_free(slm_boost* b) {
   if (!b) return;
-  for (slm_forest* f : b->trees) slm_forest_free(f);
+  for (slm_forest* f : b->trees) slm_forest_free(f);  // (views first)
+  for (slm_forest* f : b->rounds) slm_forest_free(f);
   delete b;
 }
 

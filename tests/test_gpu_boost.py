@@ -154,11 +154,13 @@ def test_cls_boost_matches_oracle(ctx, n, d, K, depth, M, eta, seed):
         R = O.softmax_residuals(F, wl.labels, K)
         for k in range(K):
             t = m * K + k
+            # the round's key seed + m, tree id k (the K trees of a round are
+            # one forest)
             q = oracle_params(O, "mse", 0, 16, 10, 32, min_leaf=10, max_depth=depth,
-                              seed=2 + t + 1)
+                              seed=2 + m + 1)
             g = b.tree(t).export(0)
             compared += 1
-            if _check_tree_up_to_near_ties(g, r.trees[t], q, wl.X, None, R[k]):
+            if _check_tree_up_to_near_ties(g, r.trees[t], q, wl.X, None, R[k], tree_id=k):
                 matched = False
                 break
             _, v, _ = O.predict(q, r.trees[t], wl.X)

@@ -302,9 +302,10 @@ def _same_node(g, r, h):
             and g["zmin"][h] == np.float32(r.zmin[h]))
 
 
-def _check_tree_up_to_near_ties(g, r, op, X, labels, y):
+def _check_tree_up_to_near_ties(g, r, op, X, labels, y, tree_id=0):
     """Identical nodes, except below a node where the two searches part after
-    a near-tie that the oracle logged (double sums in another order)."""
+    a near-tie that the oracle logged (double sums in another order); tree_id:
+    the tree's global id (node uids (tree_id << 16) | h)."""
     _, _, leaf = O.predict(op, r, X)
     H = len(r.kind)
     diverged = 0
@@ -316,7 +317,7 @@ def _check_tree_up_to_near_ties(g, r, op, X, labels, y):
         if not ok or r.kind[h] == -1 or _same_node(g, r, h):
             continue
         idx = _members(leaf, h)
-        rs = O.node_split(op, X, labels, y, idx=idx, node_uid=h)
+        rs = O.node_split(op, X, labels, y, idx=idx, node_uid=(tree_id << 16) | h)
         assert rs.split["first_near_tie"] >= 0, f"node {h} differs without a near-tie"
         diverged += 1
     return diverged
