@@ -1512,15 +1512,48 @@ __global__ void __launch_bounds__(kThreads)
     const float* zs = sw.z + (int64_t)p * pr.Ez + nd.seg_start;
     const int32_t* ls = pr.lab + nd.seg_start;
     const uint32_t* ws = pr.w ? pr.w + nd.seg_start : nullptr;
-    // four entries per lane in flight before their shared atomics
-    for (int i0 = lane; i0 < nd.seg_len; i0 += 128) {
+    const int n = nd.seg_len;
+    int done = 0;
+    if (((reinterpret_cast<uintptr_t>(zs) | reinterpret_cast<uintptr_t>(ls) |
+          reinterpret_cast<uintptr_t>(ws)) & 15) == 0) {
+      // sixteen entries per lane in flight (four 16-byte groups of z, labels
+      // and multiplicities) before their shared atomics: the node's z has
+      // often left L2 by now, and each round trip is then a DRAM one
+      constexpr int U = 4;
+      const int n4 = n >> 2;
+      for (int g0 = lane; g0 < n4; g0 += 32 * U) {
+        float4 zv[U];
+        int4 lv[U];
+        uint4 wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int g = g0 + 32 * u;
+          const bool in = g < n4;
+          zv[u] = in ? __ldcg(reinterpret_cast<const float4*>(zs) + g) : make_float4(0, 0, 0, 0);
+          lv[u] = in ? __ldg(reinterpret_cast<const int4*>(ls) + g) : make_int4(-1, -1, -1, -1);
+          wv[u] = in && ws ? __ldg(reinterpret_cast<const uint4*>(ws) + g) : make_uint4(1, 1, 1, 1);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (lv[u].x < 0) continue;  // past the node (whole group)
+          atomicAdd(&h[bin_of(zv[u].x, zmin, inv_w, B) * K + lv[u].x], wv[u].x);
+          atomicAdd(&h[bin_of(zv[u].y, zmin, inv_w, B) * K + lv[u].y], wv[u].y);
+          atomicAdd(&h[bin_of(zv[u].z, zmin, inv_w, B) * K + lv[u].z], wv[u].z);
+          atomicAdd(&h[bin_of(zv[u].w, zmin, inv_w, B) * K + lv[u].w], wv[u].w);
+        }
+      }
+      done = n4 << 2;
+    }
+    // the rest (or every entry where the arrays are not 16-byte aligned),
+    // four per lane in flight
+    for (int i0 = done + lane; i0 < n; i0 += 128) {
       float zv[4];
       int32_t lv[4];
       uint32_t wv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + 32 * u;
-        const bool in = i < nd.seg_len;
+        const bool in = i < n;
         zv[u] = in ? __ldcg(zs + i) : 0.f;
         lv[u] = in ? __ldg(ls + i) : -1;
         wv[u] = in && ws ? __ldg(ws + i) : 1u;
