@@ -856,6 +856,7 @@ def run_ours(args):
     share = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kst.values())), 4)
              for k, v in kst.items() if v["launches"]}
     extra["kernel_share"] = share
+    extra["launches_per_step"] = launches / max(1, args.steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
