@@ -750,7 +750,8 @@ slm_status score_batch(slm_ctx* c, const Problem& pr, const Swarm& sw_in,
       // histogram CTA of the node) replace theirs
       if (n_tiles)
         CK(launch(c, SLM_K_PROJECT, b.pairs_k, [&] {
-          return launch_project(b.pr_k, b.sw_k, dt, n_tiles, cap, c->stream);
+          return launch_project(b.pr_k, b.sw_k, dt, n_tiles, cap, c->stream, 0, false,
+                                c->tma ? A : 0);
         }));
       CK(launch(c, SLM_K_HIST_SCAN, b.pairs_k, [&] {
         return b.fast
