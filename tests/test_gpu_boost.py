@@ -266,3 +266,46 @@ def test_boost_with_bf16_trees(ctx):
     mse = np.mean((wl.y.astype(np.float64) - pred.astype(np.float64)) ** 2)
     assert mse == pytest.approx(b.train_loss[-1], rel=1e-12)
     b.free()
+
+
+def test_cls_boost_round_forest_views(ctx):
+    """Each round's K class trees are grown as one forest; every tree the
+    boosting object returns is a one-tree view of it: tree ids 0..K-1 (node
+    uids (k << 16) | h) under the round's key, its own evaluations (the
+    searched entries of its internal nodes x P x (T + 1)), and it predicts
+    on its own like the oracle's tree of that round and class."""
+    from paper_2208_07023_gb300 import binding as S
+    K, M, P, T = 3, 2, 16, 6
+    wl = W.gmm(2500, 6, K, seed=41)
+    gp = S.make_params("mse", K, n_particles=P, n_iters=T, n_bins=32, min_leaf=10,
+                       max_depth=3, seed=9)
+    b = ctx.train_boost(gp, wl.X, labels=wl.labels, n_classes=K, n_rounds=M,
+                        learning_rate=0.5)
+    r = O.train_boost_cls(oracle_params(O, "mse", 0, P, T, 32, min_leaf=10, max_depth=3,
+                                        seed=9), wl.X, wl.labels, K, M, 0.5)
+    F = np.zeros((len(wl.labels), K), np.float32)
+    for m in range(M):
+        R = O.softmax_residuals(F, wl.labels, K)
+        for k in range(K):
+            t = b.tree(m * K + k)
+            inf = t.info()
+            assert inf["n_trees"] == 1
+            g = t.export(0)
+            # searched nodes: every internal node, and at most every node
+            # above the last level (a searched node may become a leaf)
+            H = len(g["kind"])
+            depth = np.floor(np.log2(np.arange(H) + 1)).astype(int)
+            lo = int(g["weight"][g["kind"] == 1].sum())
+            hi = int(g["weight"][(g["kind"] >= 0) & (depth < 3)].sum())
+            ev = inf["evaluations"]
+            assert ev % (P * (T + 1)) == 0 and lo <= ev // (P * (T + 1)) <= hi
+            q = oracle_params(O, "mse", 0, P, T, 32, min_leaf=10, max_depth=3, seed=9 + m + 1)
+            if _check_tree_up_to_near_ties(g, r.trees[m * K + k], q, wl.X, None, R[k],
+                                          tree_id=k):
+                b.free()
+                return  # a logged near-tie: the rest of the run fits other residuals
+            _, vg, _ = ctx.predict(t, wl.X)
+            _, vo, _ = O.predict(q, r.trees[m * K + k], wl.X)
+            assert np.allclose(vg, vo, rtol=1e-12, atol=1e-12)
+            F[:, k] = (F[:, k] + np.float32(0.5) * vo.astype(np.float32)).astype(np.float32)
+    b.free()
