@@ -19,7 +19,10 @@ SLM Boost (K-class softmax gradient boosting with least-squares SLR trees):
   log(1 + (K - 1) e^-g) (after the first round log(1 + (K - 1) e^-eta));
 * on a mixture the loss falls every round, the reported loss is the mean
   cross-entropy of the returned scores, prediction reproduces them and the
-  class is their argmax; bad arguments are refused.
+  class is their argmax; bad arguments are refused;
+* each round rebuilt from its definition: the softmax residuals of the
+  scores so far and class k's tree grown with the round's key seed + m and
+  tree id k give that round's trees.
 """
 import numpy as np
 import pytest
@@ -147,6 +150,34 @@ def test_cls_boosting_on_mixture():
     lse = Fd.max(1) + np.log(np.exp(Fd - Fd.max(1, keepdims=True)).sum(1))
     ce = np.mean(lse - Fd[np.arange(len(wl.labels)), wl.labels])
     assert b.train_loss[-1] == pytest.approx(ce, rel=1e-12)
+
+
+def test_cls_rounds_rebuilt_from_their_definition():
+    # round m: the softmax residuals of the scores so far, then class k's
+    # tree grown with the round's key seed + m and tree id k (the K trees of
+    # a round are one forest), then F_k += eta v_k in class order
+    wl = W.gmm(2000, 5, 3, seed=12)
+    eta = np.float32(0.5)
+    p = O.make_params("mse", 0, 12, 6, 32, min_leaf=10, max_depth=2, seed=5)
+    b = O.train_boost_cls(p, wl.X, wl.labels, 3, 2, float(eta))
+    F = np.zeros((len(wl.labels), 3), np.float32)
+    for m in range(1, 3):
+        R = O.softmax_residuals(F, wl.labels, 3)
+        q = O.make_params("mse", 0, 12, 6, 32, min_leaf=10, max_depth=2, seed=5 + m)
+        for k in range(3):
+            t = O.train_tree(q, wl.X, None, R[k], tree_id=k)
+            bt = b.trees[(m - 1) * 3 + k]
+            assert np.array_equal(t.kind, bt.kind) and np.array_equal(t.dir, bt.dir)
+            assert np.array_equal(t.bin, bt.bin)
+            _, v, _ = O.predict(q, t, wl.X)
+            F[:, k] = (F[:, k] + eta * v.astype(np.float32)).astype(np.float32)
+    assert np.array_equal(F, b.F)
+    # the class trees of one round draw distinct streams: grown as tree 0
+    # instead, class 1's first tree differs from the boosting run's
+    R = O.softmax_residuals(np.zeros_like(F), wl.labels, 3)
+    q = O.make_params("mse", 0, 12, 6, 32, min_leaf=10, max_depth=2, seed=6)
+    t0 = O.train_tree(q, wl.X, None, R[1], tree_id=0)
+    assert not (np.array_equal(t0.dir, b.trees[1].dir))
 
 
 def test_cls_bad_arguments():
