@@ -1,5 +1,5 @@
 // slm_measure_peaks: the two roofs the search's kernels are held against
-// that the driver's measured peaks (HBM copy, BF16 GEMM) do not give.
+// that peaks measured by an HBM copy and a BF16 GEMM do not give.
 //  * FP32 fused multiply-add throughput: the projection (z = X_node x_p,
 //    one fmaf per feature, Sec. II-A Eq. 1) is bound by it, not by memory:
 //    its rows stay in L2 across a search's iterations.
